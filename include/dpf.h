@@ -1,0 +1,190 @@
+/*
+ * dpf.h - C ABI of the GB300 look-ahead decentralized particle filter.
+ *
+ * The method is the look-ahead decentralized particle filter (LA-DPF) of
+ * "Decentralized, Adaptive, Look-Ahead Particle Filtering" (Ahmed, Bibalan,
+ * de Freitas, Fauvel; arXiv:1203.2394): an outer particle filter over the first
+ * state block x with N particles, each carrying M inner particles of the second
+ * block z (Section 2, eq. filteringProblem), advanced by the four steps of
+ * Fig. 4 with the Monte Carlo optimal-proposal weights of eq. weightsMC.
+ *
+ * Conventions for every entry point:
+ *  - The return value is a dpf_status; no call aborts, traps or exits.
+ *  - "device" pointers are CUDA device (or managed) memory on the current
+ *    device; "host" pointers are ordinary host memory. The caller owns every
+ *    buffer it passes; a context owns its own device state.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is ordered on that stream.
+ *  - On failure, dpf_last_error() returns a thread-local message.
+ */
+#ifndef DPF_H
+#define DPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DPF_OK = 0,
+  DPF_E_INVALID = 1,     /* bad argument (null pointer, size out of range, bad model) */
+  DPF_E_NOMEM = 2,       /* a device allocation failed; nothing leaked */
+  DPF_E_CUDA = 3,        /* a CUDA runtime call failed */
+  DPF_E_TIMEOUT = 4,     /* a bounded device-side wait gave up (the scan look-back) */
+  DPF_E_NUMERIC = 5,     /* all weights zero, or a NaN weight */
+  DPF_E_UNSUPPORTED = 6  /* a valid request outside the compiled configurations */
+} dpf_status;
+
+enum { DPF_F32 = 0, DPF_F64 = 1 };          /* precision / dtype codes */
+enum { DPF_MODEL_CLG = 1 };                 /* conditionally linear-Gaussian family */
+enum { DPF_SYS_GLOBAL = 0, DPF_SYS_LOCAL = 1 }; /* resampling rules, see dpf_resample */
+
+typedef struct dpf_ctx dpf_ctx; /* opaque; created by dpf_create, freed by dpf_destroy */
+
+/*
+ * The state-space model of eq. mainDPF (Section 2), in the conditionally
+ * linear-Gaussian family, on a state s of dimension d observed through y of
+ * dimension dy. With x = the first d1 coordinates of s in the order given by
+ * perm and z = the remaining d2 = d - d1:
+ *   x_{t+1} = g(x_t, t) + A_xx x_t + A_xz z_t + v^x
+ *   z_{t+1} =             A_zx x_t + A_zz z_t + v^z      [v^x; v^z] ~ N(0, Q)
+ *   y_t     = qc x_t.^2 + H_x x_t + H_z z_t + e_t        e_t ~ N(0, R)
+ *   s_0 ~ N(m0, P0)
+ * g(x, t) = growth[0] x + growth[1] x / (1 + x^2) + growth[2] cos(growth[3] t)
+ * per coordinate when growth_x is set (the growth map of Table 1), else 0; the
+ * qc x.^2 term is present when quad_obs is set (then dy must equal d1).
+ * All matrices are host, row-major, in the user's coordinate order, read once
+ * by dpf_create (the caller keeps ownership). Q must have no x/z cross terms
+ * after the permutation; H_z Q_z H_z^T must be positive definite.
+ */
+typedef struct {
+  int32_t kind;        /* DPF_MODEL_CLG */
+  int32_t d;           /* state dimension */
+  int32_t dy;          /* observation dimension */
+  int32_t precision;   /* DPF_F32 or DPF_F64: the arithmetic of the step */
+  int32_t growth_x;    /* 0/1 */
+  int32_t quad_obs;    /* 0/1 */
+  const int32_t* perm; /* d entries: internal coordinate c is user coordinate perm[c]
+                          (x block first); NULL = identity */
+  const double* A;     /* d x d */
+  const double* Q;     /* d x d, symmetric positive definite */
+  const double* H;     /* dy x d */
+  const double* R;     /* dy x dy, symmetric positive definite */
+  const double* m0;    /* d */
+  const double* P0;    /* d x d, symmetric positive definite */
+  double growth[4];
+  double qc;
+} dpf_model_desc;
+
+/*
+ * Create a filter: N outer particles of the x block (d1 coordinates), each with
+ * M inner particles of the z block (d2 coordinates), and L look-ahead draws per
+ * outer particle (the N_x' of Fig. 4 step 1). Allocates the device state and
+ * draws the initial particles (Fig. 4, "Initialize": x_0 ~ p(x_0),
+ * z_0 ~ p(z_0 | x_0), equal inner weights) on `stream`.
+ * Limits: 1 <= M <= 1024, 1 <= L <= 64, 1 <= N < 2^31, d1 + d2 == model->d.
+ * Random numbers: Philox4x32-10 keyed by (seed, filter id 0) and counted by
+ * (step, outer index, purpose | inner index, block), so results depend only on
+ * the seed, not on the launch configuration.
+ * Returns DPF_E_UNSUPPORTED for a (precision, d1, d2, dy) with no compiled kernel.
+ * On success *out owns the state until dpf_destroy.
+ */
+dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, int32_t M,
+                      int32_t L, uint64_t seed, void* stream, dpf_ctx** out);
+
+/*
+ * One LA-DPF step t = (number of previous steps) + 1 with observation y_t
+ * (Fig. 4 steps 1-4): look-ahead draws and eq. weightsMC weights for every
+ * outer particle, global systematic resampling of the outer set, selection of
+ * x_t from the ancestor's look-ahead draws, local systematic resampling and
+ * propagation of each inner set.
+ *  y_t:         dy values of the context's precision (float or double); host
+ *               memory when y_on_device == 0, device memory otherwise.
+ *  out_mean:    host, d doubles, or NULL: the filtered mean E[s_t | y_1..t] in
+ *               the user's coordinate order.
+ *  out_logZ:    host, 1 double, or NULL: the running log-evidence estimate
+ *               log p(y_1..t) (sum over steps of the outer evidence of eq. weightsopt).
+ * With both outputs NULL the call only enqueues work (no synchronisation);
+ * otherwise it synchronises the stream and reports device-side errors.
+ */
+dpf_status dpf_step(dpf_ctx* ctx, const void* y_t, int32_t y_on_device, double* out_mean,
+                    double* out_logZ);
+
+/*
+ * The same step with every input and output in device memory, fully
+ * stream-ordered and never synchronising: y_t (dy values of the context's
+ * precision), mean_out (d doubles) and logZ_out (1 double) are device pointers;
+ * either output may be NULL. Device-side errors are reported by the next
+ * synchronising call (dpf_step with outputs, dpf_sync).
+ */
+dpf_status dpf_step_async(dpf_ctx* ctx, const void* y_t_device, double* mean_out_device,
+                          double* logZ_out_device);
+
+/* Wait for the context's stream and report any latched device-side error. */
+dpf_status dpf_sync(dpf_ctx* ctx);
+
+/*
+ * Systematic resampling ("standard resampling", DPF steps 2 and 6; LA-DPF step
+ * 3) in an exact integer form, so results are identical on any hardware:
+ *   e = floor(log2(max W)), B = ceil(log2 n), c_i = floor(W_i 2^(S-e)),
+ *   cum_i = c_0 + ... + c_i, C = cum_{n-1},
+ *   out[k] = min{ i : cum_i * n * 2^b > (k * 2^b + u_b) * C },  k = 0..n-1.
+ * DPF_SYS_GLOBAL: S = 62 - B, b = 32, u_b = u (128-bit products; any n < 2^31).
+ * DPF_SYS_LOCAL:  S = 31 - B, b = 16, u_b = u >> 16 (64-bit; segment length <= 1024).
+ *  w:       device, n_total weights of `dtype` (DPF_F32/DPF_F64), >= 0, finite,
+ *           unnormalised; n_seg consecutive segments of n_total / n_seg each.
+ *  n_seg:   number of segments (>= 1; must divide n_total). Each segment is
+ *           resampled independently with its own uniform word u[s].
+ *  u:       device, n_seg 32-bit words.
+ *  out_idx: device, n_total int32 ancestor indices, local to each segment.
+ * DPF_SYS_GLOBAL accepts n_seg == 1 only. A segment whose weights are all zero,
+ * or any negative/NaN/infinite weight, gives DPF_E_NUMERIC (after synchronising).
+ * Allocates temporary device memory for the scan state; synchronises `stream`.
+ */
+dpf_status dpf_resample(const void* w, int32_t dtype, int64_t n_total, int64_t n_seg, int32_t rule,
+                        const uint32_t* u, int32_t* out_idx, void* stream);
+
+/* Diagnostics of the last step: outer effective sample size 1/sum W^2 (with
+ * normalised W), the step counter t, and the last step's log p(y_t | y_1..t-1). */
+dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ_step);
+
+/*
+ * Read an internal device array into host memory (tests and checkpoints).
+ * `which` names the array; `bytes` must equal its size exactly:
+ *   "lw" (N), "lwhat" (N*L), "xbb" (N*L*d1, [n][m][c]), "anc" (N int32),
+ *   "sel" (N int32), "wout" (N, the outer weights fed to the resampler),
+ *   "x" (d1*N, [c][n], the newest materialised x), "z" (d2*N*M, [c][n][j]),
+ *   "lq" (N*M) - x/z/lq are the newest materialised state, which is step t-1
+ *   after step t (the inner update of step t runs at the start of step t+1),
+ *   "xsel" (d1*N, [c][n]: x_t after step t), "bidx" (N*M int32, only when
+ *   debug recording is on). Element type: the context's precision (or int32).
+ * Synchronises the context's stream.
+ */
+dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t bytes);
+
+/* Record per-step debug arrays ("bidx") when enable != 0. */
+dpf_status dpf_set_debug(dpf_ctx* ctx, int32_t enable);
+
+/*
+ * Time the main step kernel: when enable != 0, every later step brackets that
+ * kernel with CUDA events on the context's stream; dpf_profile_read returns the
+ * summed milliseconds and the number of timed launches, and resets them.
+ */
+dpf_status dpf_profile(dpf_ctx* ctx, int32_t enable);
+dpf_status dpf_profile_read(dpf_ctx* ctx, double* kernel_ms, int64_t* launches);
+
+/* Device bytes held by the context. */
+dpf_status dpf_memory(dpf_ctx* ctx, size_t* bytes);
+
+/* Free everything the context owns (NULL is a no-op). */
+void dpf_destroy(dpf_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dpf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPF_H */

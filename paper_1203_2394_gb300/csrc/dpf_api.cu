@@ -1,0 +1,502 @@
+// Host side of the C ABI: model preparation (double precision), the filter
+// context, step sequencing and the small utility entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dpf_internal.h"
+
+namespace dpf {
+
+static thread_local std::string g_err;
+
+dpf_status set_error(dpf_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+void clear_error() { g_err.clear(); }
+dpf_status cuda_error(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DPF_OK;
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(DPF_E_NOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+  return set_error(DPF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static dpf_status err_word_status(int w, const char* what) {
+  if (w & 2) return set_error(DPF_E_TIMEOUT, std::string(what) + ": a device wait timed out");
+  if (w & 1) return set_error(DPF_E_NUMERIC, std::string(what) + ": no positive or a NaN weight");
+  if (w) return set_error(DPF_E_CUDA, std::string(what) + ": device bounds check failed");
+  return DPF_OK;
+}
+
+dpf_status scratch_alloc(Scratch& sc, long long tiles, cudaStream_t s) {
+  const size_t head = 64;
+  const size_t bytes = head + (size_t)tiles * (4 + 8 + 8) + 16;
+  cudaError_t e = cudaMallocAsync(&sc.block, bytes, s);
+  if (e != cudaSuccess) {
+    sc.block = nullptr;
+    return cuda_error(e, "scratch allocation");
+  }
+  e = cudaMemsetAsync(sc.block, 0, bytes, s);
+  if (e != cudaSuccess) return cuda_error(e, "scratch memset");
+  unsigned char* b = (unsigned char*)sc.block;
+  sc.maxkey = (unsigned long long*)(b + 0);
+  sc.C = (unsigned long long*)(b + 8);
+  sc.scan.ticket = (unsigned long long*)(b + 16);
+  sc.shift = (int*)(b + 24);
+  sc.err = (int*)(b + 28);
+  sc.scan.agg = (unsigned long long*)(b + head);
+  sc.scan.incl = sc.scan.agg + tiles;
+  sc.scan.flags = (uint32_t*)(sc.scan.incl + tiles);
+  return DPF_OK;
+}
+
+void scratch_free(Scratch& sc, cudaStream_t s) {
+  if (sc.block) cudaFreeAsync(sc.block, s);
+  sc.block = nullptr;
+}
+
+dpf_status scratch_finish(Scratch& sc, cudaStream_t s, const char* what) {
+  int w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  scratch_free(sc, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, what);
+  return err_word_status(w, what);
+}
+
+// ---------------------------------------------------------------------------
+// Small dense linear algebra in double (row-major), for the model constants.
+// ---------------------------------------------------------------------------
+static bool chol(const std::vector<double>& S, int n, std::vector<double>& Lo) {
+  Lo.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = S[i * n + j];
+      for (int k = 0; k < j; ++k) s -= Lo[i * n + k] * Lo[j * n + k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        Lo[i * n + i] = std::sqrt(s);
+      } else {
+        Lo[i * n + j] = s / Lo[j * n + j];
+      }
+    }
+  return true;
+}
+// Inverse of a lower-triangular matrix (column by column forward substitution).
+static std::vector<double> tri_inv(const std::vector<double>& Lo, int n) {
+  std::vector<double> X((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c)
+    for (int i = c; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) s -= Lo[i * n + k] * X[k * n + c];
+      X[i * n + c] = s / Lo[i * n + i];
+    }
+  return X;
+}
+static std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B, int n,
+                                  int k, int m) {
+  std::vector<double> C((size_t)n * m, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s += A[i * k + q] * B[q * m + j];
+      C[i * m + j] = s;
+    }
+  return C;
+}
+static std::vector<double> transpose(const std::vector<double>& A, int n, int m) {
+  std::vector<double> T((size_t)n * m);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) T[j * n + i] = A[i * m + j];
+  return T;
+}
+// S^{-1} for SPD S via its Cholesky factor: S^{-1} = Lo^{-T} Lo^{-1}.
+static bool spd_inv(const std::vector<double>& S, int n, std::vector<double>& out) {
+  std::vector<double> Lo;
+  if (!chol(S, n, Lo)) return false;
+  std::vector<double> Li = tri_inv(Lo, n);
+  out = matmul(transpose(Li, n, n), Li, n, n, n);
+  return true;
+}
+static std::vector<double> block(const std::vector<double>& A, int lda, int r0, int nr, int c0,
+                                 int nc) {
+  std::vector<double> B((size_t)nr * nc);
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nc; ++j) B[i * nc + j] = A[(r0 + i) * lda + c0 + j];
+  return B;
+}
+
+static dpf_status prepare_model(const dpf_model_desc* m, int d1, int d2, std::vector<int>& perm,
+                                HostModel& h) {
+  const int d = m->d, dy = m->dy;
+  if (m->kind != DPF_MODEL_CLG) return set_error(DPF_E_INVALID, "model kind must be DPF_MODEL_CLG");
+  if (d < 2 || d1 < 1 || d2 < 1 || d1 + d2 != d || dy < 1 || d > 128 || dy > 64)
+    return set_error(DPF_E_INVALID, "model dimensions out of range (d1 + d2 == d, all >= 1)");
+  if (!m->A || !m->Q || !m->H || !m->R || !m->m0 || !m->P0)
+    return set_error(DPF_E_INVALID, "model matrices must be non-null");
+  if (m->quad_obs && dy != d1) return set_error(DPF_E_INVALID, "quad_obs needs dy == d1");
+  perm.resize(d);
+  std::vector<int> seen(d, 0);
+  for (int c = 0; c < d; ++c) {
+    perm[c] = m->perm ? m->perm[c] : c;
+    if (perm[c] < 0 || perm[c] >= d || seen[perm[c]]++)
+      return set_error(DPF_E_INVALID, "perm is not a permutation of 0..d-1");
+  }
+  std::vector<double> A(d * d), Q(d * d), H(dy * d), P0(d * d), m0(d), R(m->R, m->R + dy * dy);
+  for (int r = 0; r < d; ++r) {
+    m0[r] = m->m0[perm[r]];
+    for (int c = 0; c < d; ++c) {
+      A[r * d + c] = m->A[perm[r] * d + perm[c]];
+      Q[r * d + c] = m->Q[perm[r] * d + perm[c]];
+      P0[r * d + c] = m->P0[perm[r] * d + perm[c]];
+    }
+  }
+  for (int q = 0; q < dy; ++q)
+    for (int c = 0; c < d; ++c) H[q * d + c] = m->H[q * d + perm[c]];
+  for (int r = 0; r < d1; ++r)
+    for (int c = d1; c < d; ++c)
+      if (Q[r * d + c] != 0.0 || Q[c * d + r] != 0.0)
+        return set_error(DPF_E_INVALID, "Q must have no x/z cross-covariance");
+  h.d1 = d1;
+  h.d2 = d2;
+  h.dy = dy;
+  h.growth = m->growth_x ? 1 : 0;
+  h.quad = m->quad_obs ? 1 : 0;
+  h.ga = m->growth[0];
+  h.gb = m->growth[1];
+  h.gc = m->growth[2];
+  h.gw = m->growth[3];
+  h.qc = m->qc;
+  h.Axx = block(A, d, 0, d1, 0, d1);
+  h.Axz = block(A, d, 0, d1, d1, d2);
+  h.Azx = block(A, d, d1, d2, 0, d1);
+  h.Azz = block(A, d, d1, d2, d1, d2);
+  h.Hx = block(H, d, 0, dy, 0, d1);
+  h.Hz = block(H, d, 0, dy, d1, d2);
+  std::vector<double> Qx = block(Q, d, 0, d1, 0, d1), Qz = block(Q, d, d1, d2, d1, d2), Lr;
+  if (!chol(Qx, d1, h.Lqx) || !chol(Qz, d2, h.Lqz) || !chol(R, dy, Lr))
+    return set_error(DPF_E_INVALID, "Q and R must be symmetric positive definite");
+  h.LqxInv = tri_inv(h.Lqx, d1);
+  h.LrInv = tri_inv(Lr, dy);
+  h.lognorm_y = -0.5 * dy * std::log(2.0 * M_PI);
+  for (int q = 0; q < dy; ++q) h.lognorm_y -= std::log(Lr[q * dy + q]);
+  h.WAxz = matmul(h.LqxInv, h.Axz, d1, d1, d2);
+  std::vector<double> QHt = matmul(Qz, transpose(h.Hz, dy, d2), d2, d2, dy);
+  std::vector<double> S = matmul(h.Hz, QHt, dy, d2, dy), Sinv;
+  if (!chol(S, dy, h.Ls) || !spd_inv(S, dy, Sinv))
+    return set_error(DPF_E_INVALID, "H_z Q_z H_z^T must be positive definite");
+  h.K = matmul(QHt, Sinv, d2, dy, dy);
+  h.HzAzz = matmul(h.Hz, h.Azz, dy, d2, d2);
+  h.HzAzx = matmul(h.Hz, h.Azx, dy, d2, d1);
+  h.m0x.assign(m0.begin(), m0.begin() + d1);
+  h.m0z.assign(m0.begin() + d1, m0.end());
+  std::vector<double> Pxx = block(P0, d, 0, d1, 0, d1), Pzx = block(P0, d, d1, d2, 0, d1),
+                      Pxz = block(P0, d, 0, d1, d1, d2), Pzz = block(P0, d, d1, d2, d1, d2), Pxxi;
+  if (!chol(Pxx, d1, h.Lp0x) || !spd_inv(Pxx, d1, Pxxi))
+    return set_error(DPF_E_INVALID, "P0 must be symmetric positive definite");
+  h.G0 = matmul(Pzx, Pxxi, d2, d1, d1);
+  std::vector<double> GP = matmul(h.G0, Pxz, d2, d1, d2);
+  for (size_t q = 0; q < Pzz.size(); ++q) Pzz[q] -= GP[q];
+  if (!chol(Pzz, d2, h.Lp0c)) return set_error(DPF_E_INVALID, "P0 must be positive definite");
+  h.xz = false;
+  for (double v : h.Axz) h.xz |= (v != 0.0);
+  return DPF_OK;
+}
+
+template <class P>
+static dpf_status dalloc(Ctx& x, P*& p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(DPF_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  x.allocs.push_back(q);
+  x.bytes += bytes;
+  p = (P*)q;
+  return DPF_OK;
+}
+
+static void free_all(Ctx* x) {
+  for (void* p : x->allocs) cudaFree(p);
+  x->allocs.clear();
+  for (cudaEvent_t e : x->pev) cudaEventDestroy(e);
+  x->pev.clear();
+}
+
+static dpf_status read_err(Ctx& x, const char* what) {
+  int w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, x.err, sizeof(int), cudaMemcpyDeviceToHost, x.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x.stream);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  if (w) {
+    cudaMemsetAsync(x.err, 0, sizeof(int), x.stream);
+    return err_word_status(w, what);
+  }
+  return DPF_OK;
+}
+
+}  // namespace dpf
+
+using namespace dpf;
+
+extern "C" {
+
+const char* dpf_last_error(void) { return g_err.c_str(); }
+
+dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, int32_t M,
+                      int32_t L, uint64_t seed, void* stream, dpf_ctx** out) {
+  clear_error();
+  if (!model || !out) return set_error(DPF_E_INVALID, "dpf_create: null argument");
+  *out = nullptr;
+  if (N < 1 || N >= (1ll << 31) || M < 1 || M > 1024 || L < 1 || L > 64)
+    return set_error(DPF_E_INVALID, "dpf_create: need 1 <= N < 2^31, 1 <= M <= 1024, 1 <= L <= 64");
+  if (model->precision != DPF_F32 && model->precision != DPF_F64)
+    return set_error(DPF_E_INVALID, "dpf_create: precision must be DPF_F32 or DPF_F64");
+  Ctx* x = new Ctx();
+  x->prec = model->precision;
+  x->d = model->d;
+  x->d1 = d1;
+  x->d2 = d2;
+  x->dy = model->dy;
+  x->N = N;
+  x->M = M;
+  x->L = L;
+  x->seed = seed;
+  x->stream = (cudaStream_t)stream;
+  dpf_status st = prepare_model(model, d1, d2, x->perm, x->hm);
+  if (st) {
+    delete x;
+    return st;
+  }
+  x->var = find_variant(x->prec, d1, d2, x->dy);
+  if (!x->var) {
+    delete x;
+    return set_error(DPF_E_UNSUPPORTED,
+                     "dpf_create: no compiled kernel for (precision, d1, d2, dy) = (" +
+                         std::to_string(model->precision) + ", " + std::to_string(d1) + ", " +
+                         std::to_string(d2) + ", " + std::to_string(model->dy) + ")");
+  }
+  const size_t sm = x->var->step_smem(M, L);
+  if (sm > 200 * 1024) {
+    delete x;
+    return set_error(DPF_E_UNSUPPORTED, "dpf_create: M * L too large for the step's shared memory");
+  }
+  x->var->make_const(x->hm, x->mconst);
+  const size_t s = x->prec == DPF_F64 ? 8 : 4;
+  const size_t NM = (size_t)N * M;
+  const int d = x->d;
+  x->n_red_blocks = (int)std::min<long long>((N + 1023) / 1024, 304);
+  const long long tiles = (N + 2047) / 2048;
+  const size_t ssz = sizeof(double) * (4 + 2 * d);
+  bool ok = true;
+  for (int q = 0; q < 2 && ok; ++q) {
+    ok &= !dalloc(*x, x->z[q], s * NM * d2);
+    ok &= !dalloc(*x, x->lq[q], s * NM);
+    ok &= !dalloc(*x, x->x[q], s * N * d1);
+    ok &= !dalloc(*x, x->lwh[q], s * N * L);
+    ok &= !dalloc(*x, x->xbb[q], s * N * L * d1);
+  }
+  ok = ok && !dalloc(*x, x->lw, s * N) && !dalloc(*x, x->xm, s * N * d1) &&
+       !dalloc(*x, x->zm, s * N * d2) && !dalloc(*x, x->wout, s * N) &&
+       !dalloc(*x, x->yb, s * 2 * x->dy) && !dalloc(*x, x->anc, 4 * N) && !dalloc(*x, x->sel, 4 * N) &&
+       !dalloc(*x, x->stats, ssz) && !dalloc(*x, x->lwmax_t, 8) && !dalloc(*x, x->lwmax_key, 8) &&
+       !dalloc(*x, x->Csum, 8) && !dalloc(*x, x->done, 8) && !dalloc(*x, x->err, 8) &&
+       !dalloc(*x, x->partials, sizeof(double) * x->n_red_blocks * (4 + d)) &&
+       !dalloc(*x, x->flags, 4 * tiles) && !dalloc(*x, x->agg, 8 * tiles) &&
+       !dalloc(*x, x->incl, 8 * tiles) && !dalloc(*x, x->ticket, 8);
+  if (!ok) {
+    std::string msg = g_err;
+    free_all(x);
+    delete x;
+    return set_error(DPF_E_NOMEM, "dpf_create: " + msg);
+  }
+  cudaStream_t sr = x->stream;
+  cudaMemsetAsync(x->stats, 0, ssz, sr);
+  cudaMemcpyAsync((int*)(x->stats + 4 + d), x->perm.data(), sizeof(int) * d, cudaMemcpyHostToDevice, sr);
+  cudaMemsetAsync(x->lwmax_key, 0, 8, sr);
+  cudaMemsetAsync(x->Csum, 0, 8, sr);
+  cudaMemsetAsync(x->done, 0, 8, sr);
+  cudaMemsetAsync(x->err, 0, 8, sr);
+  cudaMemsetAsync(x->flags, 0, 4 * tiles, sr);
+  cudaMemsetAsync(x->ticket, 0, 8, sr);
+  cudaMemsetAsync(x->anc, 0, 4 * N, sr);
+  cudaMemsetAsync(x->sel, 0, 4 * N, sr);
+  st = x->var->init(*x);
+  if (!st) st = read_err(*x, "dpf_create");
+  if (st) {
+    std::string msg = g_err;
+    free_all(x);
+    delete x;
+    return set_error(st, msg);
+  }
+  *out = x;
+  return DPF_OK;
+}
+
+static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
+  const long long t = x->t + 1;
+  if (x->profiling) {
+    if (x->pev_used + 2 > x->pev.size()) {
+      for (int q = 0; q < 64; ++q) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return cuda_error(cudaGetLastError(), "event");
+        x->pev.push_back(ev);
+      }
+    }
+    cudaEventRecord(x->pev[x->pev_used], x->stream);
+  }
+  dpf_status st = x->var->step(*x, 0);
+  if (st) return st;
+  if (x->profiling) {
+    cudaEventRecord(x->pev[x->pev_used + 1], x->stream);
+    x->pev_used += 2;
+  }
+  st = x->var->outer(*x, mean_out, logz_out);
+  if (st) return st;
+  x->t = t;
+  return DPF_OK;
+}
+
+dpf_status dpf_step_async(dpf_ctx* x, const void* y_dev, double* mean_out, double* logz_out) {
+  clear_error();
+  if (!x || !y_dev) return set_error(DPF_E_INVALID, "dpf_step_async: null argument");
+  const size_t s = x->prec == DPF_F64 ? 8 : 4;
+  const long long t = x->t + 1;
+  cudaError_t e = cudaMemcpyAsync((char*)x->yb + (t % 2) * x->dy * s, y_dev, x->dy * s,
+                                  cudaMemcpyDeviceToDevice, x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_step_async: y copy");
+  return step_enqueue(x, mean_out, logz_out);
+}
+
+dpf_status dpf_step(dpf_ctx* x, const void* y_t, int32_t y_on_device, double* out_mean,
+                    double* out_logZ) {
+  clear_error();
+  if (!x || !y_t) return set_error(DPF_E_INVALID, "dpf_step: null argument");
+  const size_t s = x->prec == DPF_F64 ? 8 : 4;
+  const long long t = x->t + 1;
+  void* slot = (char*)x->yb + (t % 2) * x->dy * s;
+  cudaError_t e = cudaMemcpyAsync(slot, y_t, x->dy * s,
+                                  y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_step: y copy");
+  dpf_status st = step_enqueue(x, nullptr, nullptr);
+  if (st) return st;
+  if (!out_mean && !out_logZ) return DPF_OK;
+  std::vector<double> h(4 + x->d);
+  e = cudaMemcpyAsync(h.data(), x->stats, sizeof(double) * (4 + x->d), cudaMemcpyDeviceToHost,
+                      x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_step: output copy");
+  st = read_err(*x, "dpf_step");
+  if (st) return st;
+  if (out_mean) memcpy(out_mean, h.data() + 4, sizeof(double) * x->d);
+  if (out_logZ) *out_logZ = h[0];
+  return DPF_OK;
+}
+
+dpf_status dpf_sync(dpf_ctx* x) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_sync: null context");
+  return read_err(*x, "dpf_sync");
+}
+
+dpf_status dpf_diag(dpf_ctx* x, double* ess, int64_t* step, double* logz_step) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_diag: null context");
+  double h[4];
+  cudaError_t e = cudaMemcpyAsync(h, x->stats, sizeof(h), cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_diag");
+  if (ess) *ess = h[2];
+  if (step) *step = x->t;
+  if (logz_step) *logz_step = h[1];
+  return DPF_OK;
+}
+
+dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
+  clear_error();
+  if (!x || !which || !dst) return set_error(DPF_E_INVALID, "dpf_read: null argument");
+  const size_t s = x->prec == DPF_F64 ? 8 : 4;
+  const long long N = x->N, M = x->M, L = x->L;
+  const long long t = x->t;
+  const int cur = (int)(t % 2);                   // look-ahead products of step t
+  const int mat = t >= 2 ? (int)((t - 1) % 2) : 0;  // newest materialised state
+  const void* src = nullptr;
+  size_t need = 0;
+  std::string w(which);
+  if (w == "lw") { src = x->lw; need = s * N; }
+  else if (w == "lwhat") { src = x->lwh[cur]; need = s * N * L; }
+  else if (w == "xbb") { src = x->xbb[cur]; need = s * N * L * x->d1; }
+  else if (w == "anc") { src = x->anc; need = 4 * N; }
+  else if (w == "sel") { src = x->sel; need = 4 * N; }
+  else if (w == "wout") { src = x->wout; need = s * N; }
+  else if (w == "x") { src = x->x[mat]; need = s * N * x->d1; }
+  else if (w == "z") { src = x->z[mat]; need = s * N * M * x->d2; }
+  else if (w == "lq") { src = x->lq[mat]; need = s * N * M; }
+  else if (w == "bidx") {
+    if (!x->dbg_b) return set_error(DPF_E_INVALID, "dpf_read: bidx needs dpf_set_debug(ctx, 1)");
+    src = x->dbg_b; need = 4 * N * M;
+  } else return set_error(DPF_E_INVALID, "dpf_read: unknown array '" + w + "'");
+  if (bytes != need)
+    return set_error(DPF_E_INVALID, "dpf_read: '" + w + "' needs " + std::to_string(need) + " bytes");
+  cudaError_t e = cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return cuda_error(e, "dpf_read");
+}
+
+dpf_status dpf_set_debug(dpf_ctx* x, int32_t enable) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_set_debug: null context");
+  if (enable && !x->dbg_b) {
+    dpf_status st = dalloc(*x, x->dbg_b, (size_t)4 * x->N * x->M);
+    if (st) return st;
+  }
+  x->debug = enable != 0;
+  return DPF_OK;
+}
+
+dpf_status dpf_profile(dpf_ctx* x, int32_t enable) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_profile: null context");
+  x->profiling = enable != 0;
+  return DPF_OK;
+}
+
+dpf_status dpf_profile_read(dpf_ctx* x, double* ms, int64_t* launches) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_profile_read: null context");
+  cudaError_t e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_profile_read");
+  double tot = 0.0;
+  for (size_t q = 0; q + 1 < x->pev_used; q += 2) {
+    float f = 0.f;
+    e = cudaEventElapsedTime(&f, x->pev[q], x->pev[q + 1]);
+    if (e != cudaSuccess) return cuda_error(e, "dpf_profile_read: elapsed time");
+    tot += f;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = (int64_t)(x->pev_used / 2);
+  x->pev_used = 0;
+  return DPF_OK;
+}
+
+dpf_status dpf_memory(dpf_ctx* x, size_t* bytes) {
+  clear_error();
+  if (!x || !bytes) return set_error(DPF_E_INVALID, "dpf_memory: null argument");
+  *bytes = x->bytes;
+  return DPF_OK;
+}
+
+void dpf_destroy(dpf_ctx* x) {
+  if (!x) return;
+  cudaStreamSynchronize(x->stream);
+  free_all(x);
+  delete x;
+}
+
+}  // extern "C"

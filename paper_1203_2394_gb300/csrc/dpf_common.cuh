@@ -1,0 +1,217 @@
+// Device building blocks of the GB300 LA-DPF: counter-based random numbers,
+// warp/block reductions and scans, and the exact integer systematic-resampling
+// rules. Everything here is __device__ code for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dpf.h"
+
+namespace dpf {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Purposes of random draws: the counter's third word carries purpose << 24.
+enum Purpose : uint32_t {
+  P_INIT_X = 1, P_INIT_Z = 2, P_LA_J = 3, P_LA_X = 4, P_LA_Z = 5,
+  P_OUTER = 6, P_SEL = 7, P_INNER = 8, P_PROP = 9
+};
+
+// Device error word bits (latched with atomicOr, read by the host after a sync).
+enum ErrBit : int { ERR_NUMERIC = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 4 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products whose high halves are xor-ed with the other counter
+// words and the round key; the key advances by the Weyl constants each round.
+// ---------------------------------------------------------------------------
+struct Key {
+  uint32_t k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox(uint4 c, Key key) {
+  uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Counter of draw (t, i, purpose, sub, block).
+__device__ __forceinline__ uint4 ctr(uint32_t t, uint32_t i, uint32_t purpose, uint32_t sub,
+                                     uint32_t block) {
+  return make_uint4(t, i, (purpose << 24) | (sub & 0xFFFFFFu), block);
+}
+
+__device__ __forceinline__ uint32_t rand_word(Key k, uint32_t t, uint32_t i, uint32_t purpose,
+                                              uint32_t sub) {
+  return philox(ctr(t, i, purpose, sub, 0), k).x;
+}
+
+// Uniform on (0,1): ((w >> 9) + 1/2) 2^-23, exact in binary32 and binary64.
+__device__ __forceinline__ float u01(uint32_t w, float) {
+  return fmaf((float)(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+__device__ __forceinline__ double u01(uint32_t w, double) {
+  return fma((double)(w >> 9), 0x1p-23, 0x1p-24);
+}
+
+// Box-Muller: two words -> two independent standard normals.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
+  const float ua = u01(wa, 0.f), ub = u01(wb, 0.f);
+  const float r = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  n0 = r * c;
+  n1 = r * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
+  const double ua = u01(wa, 0.0), ub = u01(wb, 0.0);
+  const double r = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  n0 = r * c;
+  n1 = r * s;
+}
+
+// N standard normals of draw (t, i, purpose, sub): pair p uses words
+// 2(p mod 2), 2(p mod 2)+1 of block p/2.
+template <int N, typename T>
+__device__ __forceinline__ void normals(Key k, uint32_t t, uint32_t i, uint32_t purpose,
+                                        uint32_t sub, T (&out)[N]) {
+#pragma unroll
+  for (int b = 0; b < (N + 3) / 4; ++b) {
+    const uint4 w = philox(ctr(t, i, purpose, sub, (uint32_t)b), k);
+    T a0, a1, a2, a3;
+    box_muller(w.x, w.y, a0, a1);
+    if (4 * b + 0 < N) out[4 * b + 0] = a0;
+    if (4 * b + 1 < N) out[4 * b + 1] = a1;
+    if (4 * b + 2 < N) {
+      box_muller(w.z, w.w, a2, a3);
+      out[4 * b + 2] = a2;
+      if (4 * b + 3 < N) out[4 * b + 3] = a3;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions and scans.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T neg_inf();
+template <>
+__device__ __forceinline__ float neg_inf<float>() { return -__int_as_float(0x7f800000); }
+template <>
+__device__ __forceinline__ double neg_inf<double>() {
+  return -__longlong_as_double(0x7ff0000000000000ll);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Block-wide max / sum over NT threads. `red` holds >= NT/32 elements of
+// shared memory; the result is returned to every thread.
+template <int NT, typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T r = red[0];
+#pragma unroll
+  for (int q = 1; q < NT / 32; ++q) r = fmax(r, red[q]);
+  return r;
+}
+template <int NT, typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T r = red[0];
+#pragma unroll
+  for (int q = 1; q < NT / 32; ++q) r += red[q];
+  return r;
+}
+
+// Inclusive block scan of one uint32 per thread; `red` holds >= NT/32 words.
+template <int NT>
+__device__ __forceinline__ uint32_t block_incl_scan_u32(uint32_t v, uint32_t* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += n;
+  }
+  __syncthreads();
+  if (lane == 31) red[w] = v;
+  __syncthreads();
+  uint32_t add = 0;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q)
+    if (q < w) add += red[q];
+  return v + add;
+}
+
+// ---------------------------------------------------------------------------
+// Exact systematic resampling, local rule (segments of n <= 1024 weights):
+//   S = 31 - ceil(log2 n), c_i = floor(W_i 2^(S-e)), C = sum c_i < 2^32,
+//   out[k] = min{ i : cum_i * n_out * 2^b > (k 2^b + u_b) C },
+// with b = 16, u_b = u >> 16 for n_out > 1 and b = 32, u_b = u for one draw.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int ceil_log2_i(long long n) {
+  int b = 0;
+  while ((1ll << b) < n) ++b;
+  return b;
+}
+
+// c = floor(W 2^shift): an exact power-of-two scaling, then a floor.
+__device__ __forceinline__ uint32_t quantize_u32(float W, int shift) {
+  return (uint32_t)floorf(ldexpf(W, shift));
+}
+__device__ __forceinline__ uint32_t quantize_u32(double W, int shift) {
+  return (uint32_t)floor(ldexp(W, shift));
+}
+
+// min i in [0, n) with cum[i] * scale > rhs; cum is non-decreasing and
+// cum[n-1] * scale > rhs is guaranteed by the callers.
+__device__ __forceinline__ int search_cum(const uint32_t* cum, int n, uint64_t scale,
+                                          uint64_t rhs) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((uint64_t)cum[mid] * scale > rhs)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+// k-th output of the local rule with n_out outputs.
+__device__ __forceinline__ int sys_local_pick(const uint32_t* cum, int n, uint32_t C, int n_out,
+                                              int k, uint32_t u) {
+  if (n_out == 1) return search_cum(cum, n, 1ull << 32, (uint64_t)u * C);
+  const uint64_t rhs = (((uint64_t)k << 16) + (u >> 16)) * (uint64_t)C;
+  return search_cum(cum, n, (uint64_t)n_out << 16, rhs);
+}
+
+}  // namespace dpf

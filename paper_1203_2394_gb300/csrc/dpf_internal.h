@@ -1,0 +1,123 @@
+// Host-side internals of the library: error reporting, temporary scratch for
+// the standalone resampler, the filter context and the kernel-variant table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dpf.h"
+
+namespace dpf {
+
+dpf_status set_error(dpf_status st, const std::string& msg);
+void clear_error();
+dpf_status cuda_error(cudaError_t e, const char* what);
+
+// Look-back state of one scan: per-tile flag words and values, and the
+// monotone ticket counter that hands out tile indices in launch order.
+struct ScanState {
+  uint32_t* flags;           // n_tiles words: (epoch << 2) | state, state 1 = aggregate, 2 = prefix
+  unsigned long long* agg;   // n_tiles
+  unsigned long long* incl;  // n_tiles
+  unsigned long long* ticket;
+};
+
+// Temporary device memory of one dpf_resample call (stream-ordered allocation).
+struct Scratch {
+  void* block = nullptr;
+  unsigned long long* maxkey = nullptr;
+  unsigned long long* C = nullptr;
+  int* shift = nullptr;
+  int* err = nullptr;
+  ScanState scan{};
+};
+dpf_status scratch_alloc(Scratch& sc, long long tiles, cudaStream_t s);
+void scratch_free(Scratch& sc, cudaStream_t s);
+// Synchronise, read the device error word, free, and map it to a status.
+dpf_status scratch_finish(Scratch& sc, cudaStream_t s, const char* what);
+
+// Model constants prepared on the host in double precision, in the internal
+// (x-first) coordinate order. Matrices are row-major.
+struct HostModel {
+  int d1, d2, dy;
+  int growth, quad;
+  double ga, gb, gc, gw, qc;
+  std::vector<double> Axx, Axz, Azx, Azz, Hx, Hz;
+  std::vector<double> Lqx, Lqz, LqxInv, LrInv, Ls, K;
+  std::vector<double> WAxz, HzAzz, HzAzx;
+  std::vector<double> m0x, m0z, Lp0x, G0, Lp0c;
+  double lognorm_y;
+  bool xz;  // x transition depends on z (A_xz != 0)
+};
+
+// Device buffers and state of one filter (defined below).
+using Ctx = ::dpf_ctx;
+
+// Per-variant launchers, one set per compiled (precision, d1, d2, dy).
+struct Variant {
+  int prec, d1, d2, dy;
+  dpf_status (*make_const)(const HostModel&, std::vector<unsigned char>&);
+  dpf_status (*init)(Ctx&);
+  dpf_status (*step)(Ctx&, int profile_slot);
+  dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out);
+  size_t (*step_smem)(int M, int L);
+};
+const Variant* find_variant(int prec, int d1, int d2, int dy);
+
+}  // namespace dpf
+
+struct dpf_ctx {
+  // sizes
+  int prec = 0, d = 0, d1 = 0, d2 = 0, dy = 0;
+  long long N = 0;
+  int M = 0, L = 0;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<int> perm;
+  dpf::HostModel hm;
+  const dpf::Variant* var = nullptr;
+  std::vector<unsigned char> mconst;  // device-constant model block (variant layout)
+  // device state (element type = precision)
+  void* z[2] = {nullptr, nullptr};
+  void* lq[2] = {nullptr, nullptr};
+  void* x[2] = {nullptr, nullptr};
+  void* lwh[2] = {nullptr, nullptr};
+  void* xbb[2] = {nullptr, nullptr};
+  void* lw = nullptr;
+  void* xm = nullptr;
+  void* zm = nullptr;
+  void* wout = nullptr;
+  void* yb = nullptr;   // 2 x dy observations (slot t % 2 holds y_t)
+  int32_t* anc = nullptr;
+  int32_t* sel = nullptr;
+  int32_t* dbg_b = nullptr;
+  // small device block: reduction partials, statistics, counters, error word
+  void* small = nullptr;
+  double* stats = nullptr;          // [logZ_total, logZ_step, ess, s1, mean[d]]
+  void* lwmax_t = nullptr;          // the largest log-weight of the step, as T
+  unsigned long long* lwmax_key = nullptr;
+  unsigned long long* Csum = nullptr;
+  unsigned int* done = nullptr;
+  double* partials = nullptr;       // per reduction block
+  int n_red_blocks = 0;
+  int* err = nullptr;
+  // scan state of the outer resampling
+  uint32_t* flags = nullptr;
+  unsigned long long* agg = nullptr;
+  unsigned long long* incl = nullptr;
+  unsigned long long* ticket = nullptr;
+  unsigned long long ticket_next = 0;
+  uint32_t epoch = 0;
+  // step counter (number of completed steps)
+  long long t = 0;
+  bool debug = false;
+  // profiling of the main kernel
+  bool profiling = false;
+  std::vector<cudaEvent_t> pev;  // pairs bracketing the step kernel
+  size_t pev_used = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};

@@ -1,0 +1,168 @@
+// dpf_resample: the standalone systematic-resampling entry point (global rule
+// over one segment, or the local rule over many short segments).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "dpf_internal.h"
+#include "dpf_resample.cuh"
+
+namespace dpf {
+
+// Largest weight as an order-preserving 64-bit key (weights are >= 0, so the
+// IEEE bit pattern orders like the value); flags negative, NaN and inf.
+template <typename T>
+__global__ void wmax_kernel(const T* w, long long n, unsigned long long* maxkey, int* err) {
+  unsigned long long best = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T W = w[i];
+    if (!(W >= T(0)) || isinf(W)) atomicOr(err, ERR_NUMERIC);
+    const unsigned long long k = sizeof(T) == 8 ? (unsigned long long)__double_as_longlong((double)W)
+                                                : (unsigned long long)__float_as_uint((float)W);
+    best = k > best ? k : best;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(FULL, best, o);
+    best = v > best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(maxkey, best);
+}
+
+// C = sum floor(W_i 2^(S - e)) with e from the largest weight; also publishes S - e.
+template <typename T>
+__global__ void sumc_kernel(const T* w, long long n, int S, const unsigned long long* maxkey,
+                            unsigned long long* C, int* shift_out, int* err) {
+  const unsigned long long k = *maxkey;
+  if (k == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERR_NUMERIC);
+    return;
+  }
+  const int e = sizeof(T) == 8 ? ilogb(__longlong_as_double((long long)k))
+                               : ilogbf(__uint_as_float((uint32_t)k));
+  const int shift = S - e;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *shift_out = shift;
+  unsigned long long s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += quantize_u64(w[i], shift);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(C, s);
+}
+
+// Local rule: one block per segment of n <= NT weights.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) local_resample_kernel(const T* w, int n, const uint32_t* u,
+                                                            int32_t* out, int* err) {
+  __shared__ uint32_t cum[NT];
+  __shared__ T redT[NT / 32];
+  __shared__ uint32_t redU[NT / 32];
+  const long long seg = blockIdx.x;
+  const int j = threadIdx.x;
+  T W = T(0);
+  if (j < n) W = w[seg * n + j];
+  const int bad = __syncthreads_or(j < n && (!(W >= T(0)) || isinf(W)));
+  if (bad) {
+    if (j == 0) atomicOr(err, ERR_NUMERIC);
+    return;
+  }
+  const T mx = block_max<NT>(W, redT);
+  if (!(mx > T(0))) {
+    if (j == 0) atomicOr(err, ERR_NUMERIC);
+    return;
+  }
+  const int e = sizeof(T) == 8 ? ilogb((double)mx) : ilogbf((float)mx);
+  const int shift = (31 - ceil_log2_i(n)) - e;
+  const uint32_t c = j < n ? quantize_u32(W, shift) : 0u;
+  const uint32_t incl = block_incl_scan_u32<NT>(c, redU);
+  cum[j] = incl;
+  __syncthreads();
+  const uint32_t C = cum[n - 1];
+  if (j < n) out[seg * n + j] = sys_local_pick(cum, n, C, n, j, u[seg]);
+}
+
+template <typename T>
+static dpf_status launch_local(const T* w, int n, long long nseg, const uint32_t* u, int32_t* out,
+                               int* err, cudaStream_t s) {
+#define DPF_LOCAL_CASE(NTV)                                                      \
+  if (n <= NTV) {                                                                \
+    local_resample_kernel<T, NTV><<<(unsigned)nseg, NTV, 0, s>>>(w, n, u, out, err); \
+    return DPF_OK;                                                               \
+  }
+  DPF_LOCAL_CASE(32)
+  DPF_LOCAL_CASE(64)
+  DPF_LOCAL_CASE(128)
+  DPF_LOCAL_CASE(256)
+  DPF_LOCAL_CASE(512)
+  DPF_LOCAL_CASE(1024)
+#undef DPF_LOCAL_CASE
+  return set_error(DPF_E_INVALID, "dpf_resample: local segments hold at most 1024 weights");
+}
+
+template <typename T>
+static void launch_global(const T* w, long long n, const uint32_t* u, int32_t* out, Scratch& sc,
+                          cudaStream_t s) {
+  const int S = 62 - ceil_log2_i(n);
+  const int grid = (int)std::min<long long>((n + 1023) / 1024, 4 * 152);
+  wmax_kernel<T><<<grid, 256, 0, s>>>(w, n, sc.maxkey, sc.err);
+  sumc_kernel<T><<<grid, 256, 0, s>>>(w, n, S, sc.maxkey, sc.C, sc.shift, sc.err);
+  GlobalArgs<T> a{};
+  a.w = w;
+  a.n = n;
+  a.shift_dev = sc.shift;
+  a.C = sc.C;
+  a.u_ptr = u;
+  a.out = out;
+  a.st = sc.scan;
+  a.ticket_base = 0;
+  a.epoch = 1;
+  a.err = sc.err;
+  const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  global_scan_scatter<T, false><<<(unsigned)tiles, SCAN_NT, 0, s>>>(a);
+}
+
+}  // namespace dpf
+
+using namespace dpf;
+
+extern "C" dpf_status dpf_resample(const void* w, int32_t dtype, int64_t n_total, int64_t n_seg,
+                                   int32_t rule, const uint32_t* u, int32_t* out_idx,
+                                   void* stream) {
+  clear_error();
+  if (n_total < 0 || n_seg < 1) return set_error(DPF_E_INVALID, "dpf_resample: bad sizes");
+  if (n_total == 0) return DPF_OK;
+  if (!w || !u || !out_idx) return set_error(DPF_E_INVALID, "dpf_resample: null pointer");
+  if (dtype != DPF_F32 && dtype != DPF_F64) return set_error(DPF_E_INVALID, "dpf_resample: dtype");
+  if (n_total % n_seg) return set_error(DPF_E_INVALID, "dpf_resample: n_seg must divide n_total");
+  if (n_total >= (1ll << 31)) return set_error(DPF_E_INVALID, "dpf_resample: n_total >= 2^31");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long seglen = n_total / n_seg;
+  if (rule == DPF_SYS_GLOBAL) {
+    if (n_seg != 1) return set_error(DPF_E_INVALID, "dpf_resample: global rule needs n_seg == 1");
+    const long long tiles = (n_total + SCAN_TILE - 1) / SCAN_TILE;
+    Scratch sc;
+    dpf_status st = scratch_alloc(sc, tiles, s);
+    if (st) return st;
+    if (dtype == DPF_F32)
+      launch_global<float>((const float*)w, n_total, u, out_idx, sc, s);
+    else
+      launch_global<double>((const double*)w, n_total, u, out_idx, sc, s);
+    return scratch_finish(sc, s, "dpf_resample");
+  }
+  if (rule != DPF_SYS_LOCAL) return set_error(DPF_E_INVALID, "dpf_resample: unknown rule");
+  if (seglen > 1024) return set_error(DPF_E_INVALID, "dpf_resample: local segments hold <= 1024");
+  Scratch sc;
+  dpf_status st = scratch_alloc(sc, 0, s);
+  if (st) return st;
+  st = dtype == DPF_F32
+           ? launch_local<float>((const float*)w, (int)seglen, n_seg, u, out_idx, sc.err, s)
+           : launch_local<double>((const double*)w, (int)seglen, n_seg, u, out_idx, sc.err, s);
+  if (st) {
+    scratch_free(sc, s);
+    return st;
+  }
+  return scratch_finish(sc, s, "dpf_resample");
+}

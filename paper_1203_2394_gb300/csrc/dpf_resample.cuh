@@ -1,0 +1,194 @@
+// Global systematic resampling on the GPU: a reduction for the quantised total
+// C, then one pass that scans the quantised counts with a decoupled look-back
+// (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled
+// Look-back", 2016) and scatters each tile's share of the ancestor indices.
+#pragma once
+
+#include <cuda/atomic>
+
+#include "dpf_common.cuh"
+#include "dpf_internal.h"
+
+namespace dpf {
+
+constexpr int SCAN_NT = 256;   // threads per scan tile
+constexpr int SCAN_IPT = 8;    // items per thread
+constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
+constexpr int SPIN_LIMIT = 1 << 22;  // bounded look-back wait (~0.3 s with the back-off)
+
+typedef unsigned __int128 u128;
+
+// K(c) = #{ k in [0, n) : (k 2^32 + u) C < c n 2^32 }: the number of systematic
+// points below the cumulative count c (global rule).
+__device__ __forceinline__ long long points_below(unsigned long long c, long long n, uint32_t u,
+                                                  unsigned long long C) {
+  if (c == 0) return 0;
+  const u128 X = ((u128)c * (u128)(unsigned long long)n) << 32;
+  const u128 uC = (u128)u * (u128)C;
+  if (X <= uC) return 0;
+  const u128 Y = (X - uC - 1) >> 32;  // ceil((X - uC) / (C 2^32)) = floor(Y / C) + 1
+  const u128 q = Y / (u128)C + 1;
+  return q >= (u128)n ? n : (long long)q;
+}
+
+// Inputs of the scan-and-scatter pass. With from_log the weights are
+// W_i = exp(lw_i - lwmax) (so max W = 1 exactly and e = 0); otherwise they are
+// read directly and e = floor(log2 max W) is given.
+template <typename T>
+struct GlobalArgs {
+  const T* w;              // n weights, or log-weights when from_log
+  const T* lwmax;          // device scalar (from_log)
+  T* w_out;                // from_log: the W fed to the rule (may be null)
+  long long n;
+  int shift;               // S - e (from_log: S, since e = 0)
+  const int* shift_dev;    // if non-null, read S - e from here instead
+  const unsigned long long* C;  // device scalar: the quantised total
+  const uint32_t* u_ptr;   // device scalar uniform word, or null
+  Key key;                 // else u = rand_word(key, t, 0, P_OUTER, 0)
+  uint32_t t;
+  int32_t* out;
+  ScanState st;
+  unsigned long long ticket_base;
+  uint32_t epoch;
+  int* err;
+};
+
+template <typename T>
+__device__ __forceinline__ T exp_t(T v);
+template <>
+__device__ __forceinline__ float exp_t<float>(float v) { return expf(v); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double v) { return exp(v); }
+
+// c = floor(W 2^shift) as a 64-bit count (exact: power-of-two scaling, floor).
+__device__ __forceinline__ unsigned long long quantize_u64(float W, int shift) {
+  return (unsigned long long)floorf(ldexpf(W, shift));
+}
+__device__ __forceinline__ unsigned long long quantize_u64(double W, int shift) {
+  return (unsigned long long)floor(ldexp(W, shift));
+}
+
+template <typename T, bool FROM_LOG>
+__global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) {
+  __shared__ unsigned long long cum[SCAN_TILE];
+  __shared__ unsigned long long wsum[SCAN_NT / 32];
+  __shared__ unsigned long long s_prefix;
+  __shared__ long long s_tile;
+  __shared__ long long s_klo, s_khi;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  if (tid == 0) {
+    const unsigned long long tk = atomicAdd(a.st.ticket, 1ull) - a.ticket_base;
+    s_tile = tk < (unsigned long long)gridDim.x ? (long long)tk : -1;
+    if (s_tile < 0) atomicOr(a.err, ERR_BOUNDS);
+  }
+  __syncthreads();
+  const long long tile = s_tile;
+  if (tile < 0) return;
+  const long long base = tile * SCAN_TILE;
+  const unsigned long long C = *a.C;
+  const int shift = a.shift_dev ? *a.shift_dev : a.shift;
+  const uint32_t u = a.u_ptr ? *a.u_ptr : rand_word(a.key, a.t, 0, P_OUTER, 0);
+  T lwmax = T(0);
+  if (FROM_LOG) lwmax = *a.lwmax;
+
+  // quantise this thread's items (blocked arrangement) and sum them
+  unsigned long long c[SCAN_IPT];
+  unsigned long long tsum = 0;
+#pragma unroll
+  for (int q = 0; q < SCAN_IPT; ++q) {
+    const long long i = base + (long long)tid * SCAN_IPT + q;
+    unsigned long long ci = 0;
+    if (i < a.n) {
+      T W = a.w[i];
+      if (FROM_LOG) {
+        W = exp_t<T>(W - lwmax);
+        if (a.w_out) a.w_out[i] = W;
+      }
+      ci = quantize_u64(W, shift);
+    }
+    c[q] = ci;
+    tsum += ci;
+  }
+  // block exclusive scan of the per-thread sums
+  unsigned long long v = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long nb = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += nb;
+  }
+  if (lane == 31) wsum[wid] = v;
+  __syncthreads();
+  unsigned long long wpre = 0, agg = 0;
+#pragma unroll
+  for (int q = 0; q < SCAN_NT / 32; ++q) {
+    if (q < wid) wpre += wsum[q];
+    agg += wsum[q];
+  }
+  const unsigned long long texcl = v - tsum + wpre;
+
+  // decoupled look-back for the tile's exclusive prefix
+  if (tid == 0) {
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> my_flag(a.st.flags[tile]);
+    unsigned long long prefix = 0;
+    if (tile == 0) {
+      a.st.incl[0] = agg;
+      my_flag.store((a.epoch << 2) | 2u, cuda::memory_order_release);
+    } else {
+      a.st.agg[tile] = agg;
+      my_flag.store((a.epoch << 2) | 1u, cuda::memory_order_release);
+      long long j = tile - 1;
+      while (j >= 0) {
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(a.st.flags[j]);
+        uint32_t fv = f.load(cuda::memory_order_acquire);
+        int spins = 0;
+        while ((fv >> 2) != (a.epoch & 0x3FFFFFFFu) || (fv & 3u) == 0u) {
+          if (++spins > SPIN_LIMIT) break;
+          __nanosleep(64);
+          fv = f.load(cuda::memory_order_acquire);
+        }
+        if (spins > SPIN_LIMIT) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          break;
+        }
+        if ((fv & 3u) == 2u) {
+          prefix += a.st.incl[j];
+          break;
+        }
+        prefix += a.st.agg[j];
+        --j;
+      }
+      a.st.incl[tile] = prefix + agg;
+      my_flag.store((a.epoch << 2) | 2u, cuda::memory_order_release);
+    }
+    s_prefix = prefix;
+    s_klo = points_below(prefix, a.n, u, C);
+    s_khi = points_below(prefix + agg, a.n, u, C);
+  }
+  __syncthreads();
+  // global inclusive cumulative counts of this tile into shared memory
+  unsigned long long run = s_prefix + texcl;
+#pragma unroll
+  for (int q = 0; q < SCAN_IPT; ++q) {
+    run += c[q];
+    cum[tid * SCAN_IPT + q] = run;
+  }
+  __syncthreads();
+  // scatter: output k takes the first item of this tile with cum * n 2^32 > (k 2^32 + u) C
+  const long long len = (a.n - base) < SCAN_TILE ? (a.n - base) : SCAN_TILE;
+  const u128 scale = (u128)(unsigned long long)a.n << 32;
+  for (long long k = s_klo + tid; k < s_khi; k += SCAN_NT) {
+    const u128 rhs = ((u128)(unsigned long long)k << 32 | u) * (u128)C;
+    int lo = 0, hi = (int)len - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((u128)cum[mid] * scale > rhs)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    a.out[k] = (int32_t)(base + lo);
+  }
+}
+
+}  // namespace dpf

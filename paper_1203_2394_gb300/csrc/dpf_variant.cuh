@@ -1,0 +1,179 @@
+// Launchers of one compiled (precision, d1, d2, dy) variant of the step.
+#pragma once
+
+#include <cmath>
+#include <cstring>
+
+#include "dpf_step.cuh"
+
+namespace dpf {
+
+inline int threads_for(int M) { return ((M + 31) / 32) * 32; }
+
+template <typename T, int D1, int D2, int DY>
+struct VariantImpl {
+  typedef MC<T, D1, D2, DY> Const;
+
+  static dpf_status make_const(const HostModel& h, std::vector<unsigned char>& out) {
+    Const c;
+    memset(&c, 0, sizeof(c));
+    auto cp = [](const std::vector<double>& src, T* dst, int n) {
+      for (int q = 0; q < n; ++q) dst[q] = (T)src[q];
+    };
+    cp(h.Axx, &c.Axx[0][0], D1 * D1);
+    cp(h.Azx, &c.Azx[0][0], D2 * D1);
+    cp(h.Azz, &c.Azz[0][0], D2 * D2);
+    cp(h.Lqx, &c.Lqx[0][0], D1 * D1);
+    cp(h.LqxInv, &c.LqxInv[0][0], D1 * D1);
+    cp(h.Lqz, &c.Lqz[0][0], D2 * D2);
+    cp(h.WAxz, &c.WAxz[0][0], D1 * D2);
+    cp(h.Hx, &c.Hx[0][0], DY * D1);
+    cp(h.Hz, &c.Hz[0][0], DY * D2);
+    cp(h.LrInv, &c.LrInv[0][0], DY * DY);
+    cp(h.HzAzz, &c.HzAzz[0][0], DY * D2);
+    cp(h.HzAzx, &c.HzAzx[0][0], DY * D1);
+    cp(h.Ls, &c.Ls[0][0], DY * DY);
+    cp(h.K, &c.K[0][0], D2 * DY);
+    cp(h.m0x, c.m0x, D1);
+    cp(h.m0z, c.m0z, D2);
+    cp(h.Lp0x, &c.Lp0x[0][0], D1 * D1);
+    cp(h.G0, &c.G0[0][0], D2 * D1);
+    cp(h.Lp0c, &c.Lp0c[0][0], D2 * D2);
+    c.ga = (T)h.ga;
+    c.gb = (T)h.gb;
+    c.qc = (T)h.qc;
+    c.lognorm_y = (T)h.lognorm_y;
+    c.growth = h.growth;
+    c.quad = h.quad;
+    out.resize(sizeof(c));
+    memcpy(out.data(), &c, sizeof(c));
+    return DPF_OK;
+  }
+
+  static const Const& cst(const Ctx& x) { return *reinterpret_cast<const Const*>(x.mconst.data()); }
+
+  static size_t smem(int M, int L) {
+    return step_smem<T, D1, D2, DY>(M, L, threads_for(M)).total;
+  }
+
+  static dpf_status init(Ctx& x) {
+    const Key key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    init_kernel<T, D1, D2, DY><<<(unsigned)x.N, threads_for(x.M), 0, x.stream>>>(
+        cst(x), (T*)x.z[0], (T*)x.lq[0], (T*)x.x[0], x.N, x.M, key);
+    return cuda_error(cudaGetLastError(), "init kernel launch");
+  }
+
+  template <bool XZ, int MAXNT>
+  static dpf_status launch_step(Ctx& x, const StepArgs<T>& a, size_t sm) {
+    auto k = step_kernel<T, D1, D2, DY, XZ, MAXNT>;
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+      attr_done = true;
+    }
+    k<<<(unsigned)x.N, threads_for(x.M), sm, x.stream>>>(cst(x), a);
+    return cuda_error(cudaGetLastError(), "step kernel launch");
+  }
+
+  static dpf_status step(Ctx& x, int) {
+    const long long t = x.t + 1;  // the step being taken
+    const int so = (int)((t + 2) % 2), sn = (int)((t + 1) % 2);  // slots of t-2 and t-1
+    StepArgs<T> a{};
+    const bool first = (t == 1);
+    a.z_old = (const T*)x.z[first ? 0 : so];
+    a.lq_old = (const T*)x.lq[first ? 0 : so];
+    a.x_old = (const T*)x.x[first ? 0 : so];
+    a.z_new = (T*)x.z[sn];
+    a.lq_new = (T*)x.lq[sn];
+    a.x_new = (T*)x.x[sn];
+    a.lwh_old = (const T*)x.lwh[(t + 1) % 2];
+    a.xbb_old = (const T*)x.xbb[(t + 1) % 2];
+    a.lwh_new = (T*)x.lwh[t % 2];
+    a.xbb_new = (T*)x.xbb[t % 2];
+    a.anc = x.anc;
+    a.sel = x.sel;
+    a.lw = (T*)x.lw;
+    a.xm = (T*)x.xm;
+    a.zm = (T*)x.zm;
+    a.y_prev = (const T*)x.yb + ((t + 1) % 2) * x.dy;
+    a.y_cur = (const T*)x.yb + (t % 2) * x.dy;
+    a.lwmax_key = x.lwmax_key;
+    a.Csum = x.Csum;
+    a.dbg_b = x.debug ? x.dbg_b : nullptr;
+    a.err = x.err;
+    a.N = x.N;
+    a.M = x.M;
+    a.L = x.L;
+    a.t = (uint32_t)t;
+    a.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    const HostModel& h = x.hm;
+    a.gcos_prev = h.growth ? (T)(h.gc * std::cos(h.gw * (double)(t - 2))) : T(0);
+    a.gcos_cur = h.growth ? (T)(h.gc * std::cos(h.gw * (double)(t - 1))) : T(0);
+    a.first = first ? 1 : 0;
+    const size_t sm = smem(x.M, x.L);
+    const int nt = threads_for(x.M);
+    if (h.xz) return nt <= 256 ? launch_step<true, 256>(x, a, sm) : launch_step<true, 1024>(x, a, sm);
+    return nt <= 256 ? launch_step<false, 256>(x, a, sm) : launch_step<false, 1024>(x, a, sm);
+  }
+
+  static dpf_status outer(Ctx& x, double* mean_out, double* logz_out) {
+    OuterArgs<T> o{};
+    o.lw = (const T*)x.lw;
+    o.xm = (const T*)x.xm;
+    o.zm = (const T*)x.zm;
+    o.N = x.N;
+    o.d1 = x.d1;
+    o.d2 = x.d2;
+    o.lwmax_key = x.lwmax_key;
+    o.lwmax_t = (T*)x.lwmax_t;
+    o.Csum = x.Csum;
+    o.done = x.done;
+    o.partials = x.partials;
+    o.stats = x.stats;
+    o.perm = (const int*)(x.stats + 4 + x.d);  // the permutation lives after the statistics
+    o.mean_out = mean_out;
+    o.logz_out = logz_out;
+    o.err = x.err;
+    outer_reduce_kernel<T><<<x.n_red_blocks, RED_NT, 0, x.stream>>>(o);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
+    const long long t = x.t + 1;
+    const long long tiles = (x.N + SCAN_TILE - 1) / SCAN_TILE;
+    GlobalArgs<T> g{};
+    g.w = (const T*)x.lw;
+    g.lwmax = (const T*)x.lwmax_t;
+    g.w_out = (T*)x.wout;
+    g.n = x.N;
+    g.shift = 62 - ceil_log2_i(x.N);
+    g.shift_dev = nullptr;
+    g.C = x.Csum;
+    g.u_ptr = nullptr;
+    g.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    g.t = (uint32_t)t;
+    g.out = x.anc;
+    g.st = ScanState{x.flags, x.agg, x.incl, x.ticket};
+    g.ticket_base = x.ticket_next;
+    g.epoch = ++x.epoch;
+    g.err = x.err;
+    x.ticket_next += (unsigned long long)tiles;
+    global_scan_scatter<T, true><<<(unsigned)tiles, SCAN_NT, 0, x.stream>>>(g);
+    return cuda_error(cudaGetLastError(), "outer resample launch");
+  }
+
+  static Variant make(int prec) {
+    Variant v;
+    v.prec = prec;
+    v.d1 = D1;
+    v.d2 = D2;
+    v.dy = DY;
+    v.make_const = &make_const;
+    v.init = &init;
+    v.step = &step;
+    v.outer = &outer;
+    v.step_smem = &smem;
+    return v;
+  }
+};
+
+}  // namespace dpf

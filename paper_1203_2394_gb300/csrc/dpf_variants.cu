@@ -1,0 +1,17 @@
+// The table of compiled (precision, d1, d2, dy) variants.
+#include "dpf_internal.h"
+
+namespace dpf {
+
+Variant make_v_f32_2_8_2();
+Variant make_v_f64_2_2_2();
+Variant make_v_f32_2_2_2();
+
+const Variant* find_variant(int prec, int d1, int d2, int dy) {
+  static const Variant table[] = {make_v_f32_2_8_2(), make_v_f64_2_2_2(), make_v_f32_2_2_2()};
+  for (const Variant& v : table)
+    if (v.prec == prec && v.d1 == d1 && v.d2 == d2 && v.dy == dy) return &v;
+  return nullptr;
+}
+
+}  // namespace dpf
