@@ -1,0 +1,342 @@
+"""Benchmark of the GB300 look-ahead decentralized particle filter step.
+
+Workload: the growth/conditionally-linear-Gaussian model (x of dim 2 with the
+growth map, z of dim 8, y = x.^2/20 + C z + noise) with N = 65536 outer
+particles, M = 128 inner particles each and L = 16 look-ahead draws, FP32,
+T = 200 synthetic observations. One "step" is one full LA-DPF step (the fused
+inner-step/look-ahead kernel, the outer reduction and the outer resampling).
+
+Metric: particle-updates/s = N * M * steps / time, the inputs (all y_t)
+resident in device memory. The state (2 x 302 MB) is larger than the 129 MB
+L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent filter (weak scaling,
+replicas; no collective on the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "growth_clg10"
+METRIC = "particle-updates/s (N*M per step)"
+UNIT = "particle-updates/s"
+KERNEL_SOURCES = ["paper_1203_2394_gb300/csrc/dpf_step.cuh", "paper_1203_2394_gb300/csrc/dpf_common.cuh",
+                  "paper_1203_2394_gb300/csrc/dpf_variant.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_growth_clg10_traffic.json")
+
+
+def b_alg(d1, d2, M, s):
+    """Algorithmic bytes per particle update: read and write z and lq once, plus the
+    per-outer-particle x (read + write), weight, ancestor and selection."""
+    return 2 * (d2 + 1) * s + (2 * d1 * s + 12) / M
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def stop(self, window=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, ln in self.lines:
+            if window is not None and not (window[0] <= ts <= window[1] + 0.2):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_rate(spec, N, M, L, budget_s=12.0, n_sample=2048, seed=0):
+    """The FP64 C oracle, as it stands, on a bounded sample of the workload: the
+    first steps of a filter with n_sample outer particles (same M, L and model),
+    all host cores. Returns (particle-updates/s, threads, sample description)."""
+    from oracle import oracle
+    from paper_1203_2394_gb300 import workloads
+    threads = os.cpu_count() or 1
+    _, ys = workloads.simulate(spec, 8, 0)
+    o = oracle.Oracle(oracle.OracleModel.from_spec(spec), n_sample, M, L, seed, nthreads=threads)
+    x, z, lq = o.init()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 8:
+        r = o.step(steps + 1, ys[steps], x, z, lq)
+        x, z, lq = r["x"], r["z"], r["lq"]
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    sample = (f"{steps} full LA-DPF steps of a {n_sample}-outer-particle filter (M={M}, L={L}, same "
+              f"model), {threads} OpenMP threads, {dt:.1f} s wall")
+    return n_sample * M * steps / dt, threads, sample
+
+
+def run_reference(args):
+    """The reference arm: the FP64 C oracle, as it stands, on the host cores. Each
+    step is one full LA-DPF step of a bounded sample of the workload (1024 outer
+    particles with the workload's M, L and model); the run stops after 150 s."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_1203_2394_gb300 import workloads
+    spec = workloads.make_model(WORKLOAD, 0)
+    sz = spec.sizes
+    n_sample, M, L = 1024, sz["M"], sz["L"]
+    threads = os.cpu_count() or 1
+    _, ys = workloads.simulate(spec, args.warmup + args.steps + 1, 0)
+    o = oracle.Oracle(oracle.OracleModel.from_spec(spec), n_sample, M, L, 0, nthreads=threads)
+    x, z, lq = o.init()
+    for t in range(1, args.warmup + 1):
+        r = o.step(t, ys[t - 1], x, z, lq)
+        x, z, lq = r["x"], r["z"], r["lq"]
+    t0 = time.perf_counter()
+    done = 0
+    for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+        r = o.step(t, ys[t - 1], x, z, lq)
+        x, z, lq = r["x"], r["z"], r["lq"]
+        done += 1
+        if time.perf_counter() - t0 > 150:
+            break
+    dt = time.perf_counter() - t0
+    value = n_sample * M * done / dt
+    sample = (f"{done} timed LA-DPF steps of a {n_sample}-outer-particle filter (M={M}, L={L}, same "
+              f"model) after {args.warmup} warm-up steps, {threads} OpenMP threads, {dt:.1f} s")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": done, "warmup": args.warmup, "ms_per_step": dt / done * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: growth-map x (d1=2), linear-Gaussian z (d2=8), dy=2, "
+                               f"N={sz['N']}, M={M}, L={L}",
+                   "reference": f"FP64 C oracle on a {n_sample}-outer-particle sample per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run(args):
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = workloads.make_model(WORKLOAD, 0)
+    sz = spec.sizes
+    N, M, L, T = sz["N"], sz["M"], sz["L"], sz["T"]
+    K, W = args.steps, args.warmup
+    _, ys = workloads.simulate(spec, max(T, K + W + 1), 0)
+    stream = torch.cuda.Stream(device=dev)
+    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    f = dpf.Filter(model, spec.d1, spec.d2, N, M, L, seed=rank, stream=stream)
+    y_dev = torch.tensor(ys.astype(np.float32), device=dev)
+    assert N * M * (K + W) > 0
+    means = torch.zeros((K + W, spec.d), dtype=torch.float64, device=dev)
+    logz = torch.zeros(K + W, dtype=torch.float64, device=dev)
+    ystep = y_dev.stride(0) * 4
+
+    # ---- device-resident timing ----
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            f.step_device(y_dev.data_ptr() + k * ystep, means[k].data_ptr(), logz[k].data_ptr())
+        f.sync()
+        f.profile(True)
+        f.profile_read()  # reset
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.monotonic()
+        e0.record(stream)
+        for k in range(W, W + K):
+            f.step_device(y_dev.data_ptr() + k * ystep, means[k].data_ptr(), logz[k].data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        w1 = time.monotonic()
+        f.sync()
+        ms = e0.elapsed_time(e1)
+        kern_ms, kern_n = f.profile_read()
+        f.profile(False)
+        clk = clocks.stop(window=(w0, w1))
+    barrier(ws)
+    ms_max = max_over_ranks(ms, ws, dev)
+    value = ws * N * M * K / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    f2 = dpf.Filter(model, spec.d1, spec.d2, N, M, L, seed=rank + 1000, stream=stream)
+    y_pinned = torch.tensor(ys.astype(np.float32)).pin_memory()
+    ynp = y_pinned.numpy()
+    for k in range(W):
+        f2.step(ynp[k])
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(W, W + K):
+        f2.step(ynp[k])
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, ws, dev)
+    e2e_value = ws * N * M * K / t_e2e
+    f2.close()
+
+    if rank != 0:
+        f.close()
+        return 0
+    peak, peak_kind = measured_peaks()
+    per = b_alg(spec.d1, spec.d2, M, 4)
+    kern_avg_s = kern_ms / 1e3 / max(1, kern_n)
+    achieved = per * N * M / kern_avg_s / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        tj = json.load(open(TRAFFIC_FILE))
+        if tj.get("kernel_hash") == kernel_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        r, threads, sample = cpu_oracle_rate(spec, N, M, L)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: growth-map x (d1=2), linear-Gaussian z (d2=8), dy=2, "
+                               f"N={N}, M={M}, L={L}, FP32",
+                   "N": N, "M": M, "L": L, "d1": spec.d1, "d2": spec.d2, "dy": spec.dy,
+                   "l2": "state (2 x 302 MB) larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "step_kernel", "kernel_ms": kern_avg_s * 1e3,
+                     "bytes_per_update": per, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spec.dy * 4,
+                "d2h_bytes_per_step": (4 + spec.d) * 8 + 4},
+        "gpu_launches": 3 * K,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    f.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -146,6 +146,18 @@ dpf_status dpf_sync(dpf_ctx* ctx);
 dpf_status dpf_resample(const void* w, int32_t dtype, int64_t n_total, int64_t n_seg, int32_t rule,
                         const uint32_t* u, int32_t* out_idx, void* stream);
 
+/*
+ * The library's Box-Muller transform (the normal draws of every step) applied
+ * to given 32-bit words, for verifying its accuracy against the exact formula
+ * n0 = sqrt(-2 ln u_a) cos(2 pi u_b), n1 = sqrt(-2 ln u_a) sin(2 pi u_b) with
+ * u = ((w >> 9) + 1/2) 2^-23: out[2p] and out[2p+1] come from words[2p] (u_a)
+ * and words[2p+1] (u_b). words: device, 2 n_pairs words; out: device, 2 n_pairs
+ * values of `dtype` (DPF_F32 or DPF_F64, selecting the FP32 or FP64 transform).
+ * Stream-ordered; does not synchronise.
+ */
+dpf_status dpf_box_muller(const uint32_t* words, int64_t n_pairs, int32_t dtype, void* out,
+                          void* stream);
+
 /* Diagnostics of the last step: outer effective sample size 1/sum W^2 (with
  * normalised W), the step counter t, and the last step's log p(y_t | y_1..t-1). */
 dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ_step);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -193,6 +194,7 @@ static dpf_status prepare_model(const dpf_model_desc* m, int d1, int d2, std::ve
   h.K = matmul(QHt, Sinv, d2, dy, dy);
   h.HzAzz = matmul(h.Hz, h.Azz, dy, d2, d2);
   h.HzAzx = matmul(h.Hz, h.Azx, dy, d2, d1);
+  h.LrHz = matmul(h.LrInv, h.Hz, dy, dy, d2);
   h.m0x.assign(m0.begin(), m0.begin() + d1);
   h.m0z.assign(m0.begin() + d1, m0.end());
   std::vector<double> Pxx = block(P0, d, 0, d1, 0, d1), Pzx = block(P0, d, d1, d2, 0, d1),
@@ -282,12 +284,15 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
                          std::to_string(model->precision) + ", " + std::to_string(d1) + ", " +
                          std::to_string(d2) + ", " + std::to_string(model->dy) + ")");
   }
-  const size_t sm = x->var->step_smem(M, L);
+  x->ppt = M >= 64 ? 2 : 1;
+  if (const char* e = getenv("DPF_PPT")) x->ppt = atoi(e) == 2 ? 2 : 1;
+  const size_t sm = x->var->step_smem(M, L, x->hm.xz, ((M + x->ppt - 1) / x->ppt + 31) / 32 * 32);
   if (sm > 200 * 1024) {
     delete x;
     return set_error(DPF_E_UNSUPPORTED, "dpf_create: M * L too large for the step's shared memory");
   }
   x->var->make_const(x->hm, x->mconst);
+  x->xp = x->var->xpad();
   const size_t s = x->prec == DPF_F64 ? 8 : 4;
   const size_t NM = (size_t)N * M;
   const int d = x->d;
@@ -298,7 +303,7 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   for (int q = 0; q < 2 && ok; ++q) {
     ok &= !dalloc(*x, x->z[q], s * NM * d2);
     ok &= !dalloc(*x, x->lq[q], s * NM);
-    ok &= !dalloc(*x, x->x[q], s * N * d1);
+    ok &= !dalloc(*x, x->x[q], s * N * x->xp);
     ok &= !dalloc(*x, x->lwh[q], s * N * L);
     ok &= !dalloc(*x, x->xbb[q], s * N * L * d1);
   }
@@ -435,7 +440,14 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   else if (w == "anc") { src = x->anc; need = 4 * N; }
   else if (w == "sel") { src = x->sel; need = 4 * N; }
   else if (w == "wout") { src = x->wout; need = s * N; }
-  else if (w == "x") { src = x->x[mat]; need = s * N * x->d1; }
+  else if (w == "x") {  // rows are padded to xp elements on the device; returned packed
+    if (bytes != s * N * x->d1)
+      return set_error(DPF_E_INVALID, "dpf_read: 'x' needs " + std::to_string(s * N * x->d1) + " bytes");
+    cudaError_t e = cudaMemcpy2DAsync(dst, s * x->d1, x->x[mat], s * x->xp, s * x->d1, N,
+                                      cudaMemcpyDeviceToHost, x->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+    return cuda_error(e, "dpf_read");
+  }
   else if (w == "z") { src = x->z[mat]; need = s * N * M * x->d2; }
   else if (w == "lq") { src = x->lq[mat]; need = s * N * M; }
   else if (w == "bidx") {

@@ -62,14 +62,59 @@ __device__ __forceinline__ double u01(uint32_t w, double) {
   return fma((double)(w >> 9), 0x1p-23, 0x1p-24);
 }
 
-// Box-Muller: two words -> two independent standard normals.
+// Hardware approximations (PTX .approx instructions) used by the FP32 path.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Box-Muller: two words -> two independent standard normals,
+//   n0 = r cos(2 pi u_b), n1 = r sin(2 pi u_b),  r = sqrt(-2 ln u_a).
+// FP32: the radius uses the hardware log2 except for u_a > 1 - 1/64, where
+// -ln u_a = -ln(1 - v) with v = 1 - u_a (exact) is summed as its Taylor series
+// v + v^2/2 + v^3/3 + v^4/4 + v^5/5 (truncation below 2e-10 relative); the
+// angle uses the identity cos(2 pi u) = -cos(2 pi (u - 1/2)) (and likewise sin)
+// so the hardware sine and cosine see arguments in (-pi, pi). The accuracy is
+// verified exhaustively over all 2^23 values of each uniform.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
-  const float ua = u01(wa, 0.f), ub = u01(wb, 0.f);
-  const float r = sqrtf(-2.0f * logf(ua));
-  float s, c;
-  sincospif(2.0f * ub, &s, &c);
-  n0 = r * c;
-  n1 = r * s;
+  const uint32_t ka = wa >> 9;
+  float r2;
+  if (ka >= (1u << 23) - (1u << 17)) {
+    const float v = fmaf((float)((1u << 23) - 1u - ka), 0x1p-23f, 0x1p-24f);
+    float s = fmaf(v, 0.2f, 0.25f);
+    s = fmaf(v, s, 0.333333333f);
+    s = fmaf(v, s, 0.5f);
+    s = fmaf(v, s, 1.0f);
+    r2 = 2.0f * v * s;
+  } else {
+    r2 = -1.38629436f * lg2_approx(fmaf((float)ka, 0x1p-23f, 0x1p-24f));  // -2 ln 2 log2 u
+  }
+  const float r = sqrt_approx(r2);
+  const float h = fmaf((float)(wb >> 9), 0x1p-23f, 0x1p-24f - 0.5f);  // u_b - 1/2, exact
+  const float th = h * 6.28318531f;
+  n0 = -r * cos_approx(th);
+  n1 = -r * sin_approx(th);
 }
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
   const double ua = u01(wa, 0.0), ub = u01(wb, 0.0);

@@ -47,7 +47,7 @@ struct HostModel {
   double ga, gb, gc, gw, qc;
   std::vector<double> Axx, Axz, Azx, Azz, Hx, Hz;
   std::vector<double> Lqx, Lqz, LqxInv, LrInv, Ls, K;
-  std::vector<double> WAxz, HzAzz, HzAzx;
+  std::vector<double> WAxz, HzAzz, HzAzx, LrHz;
   std::vector<double> m0x, m0z, Lp0x, G0, Lp0c;
   double lognorm_y;
   bool xz;  // x transition depends on z (A_xz != 0)
@@ -63,7 +63,8 @@ struct Variant {
   dpf_status (*init)(Ctx&);
   dpf_status (*step)(Ctx&, int profile_slot);
   dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out);
-  size_t (*step_smem)(int M, int L);
+  size_t (*step_smem)(int M, int L, bool xz, int nt);
+  int (*xpad)();
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
 
@@ -114,6 +115,9 @@ struct dpf_ctx {
   // step counter (number of completed steps)
   long long t = 0;
   bool debug = false;
+  int ppt = 1;        // inner particles per thread of the step kernel
+  int xp = 4;         // padded x row length (elements; 16-byte rows)
+  int grid_step = 0;  // persistent grid of the step kernel (0 = not yet sized)
   // profiling of the main kernel
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // pairs bracketing the step kernel

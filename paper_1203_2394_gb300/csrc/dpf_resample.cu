@@ -124,9 +124,35 @@ static void launch_global(const T* w, long long n, const uint32_t* u, int32_t* o
   global_scan_scatter<T, false><<<(unsigned)tiles, SCAN_NT, 0, s>>>(a);
 }
 
+template <typename T>
+__global__ void box_muller_kernel(const uint32_t* words, long long n_pairs, T* out) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pairs;
+       p += (long long)gridDim.x * blockDim.x) {
+    T a, b;
+    box_muller(words[2 * p], words[2 * p + 1], a, b);
+    out[2 * p] = a;
+    out[2 * p + 1] = b;
+  }
+}
+
 }  // namespace dpf
 
 using namespace dpf;
+
+extern "C" dpf_status dpf_box_muller(const uint32_t* words, int64_t n_pairs, int32_t dtype,
+                                     void* out, void* stream) {
+  clear_error();
+  if (n_pairs < 0 || (n_pairs > 0 && (!words || !out)))
+    return set_error(DPF_E_INVALID, "dpf_box_muller: bad arguments");
+  if (dtype != DPF_F32 && dtype != DPF_F64) return set_error(DPF_E_INVALID, "dpf_box_muller: dtype");
+  if (n_pairs == 0) return DPF_OK;
+  const int grid = (int)std::min<long long>((n_pairs + 255) / 256, 152 * 8);
+  if (dtype == DPF_F32)
+    box_muller_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(words, n_pairs, (float*)out);
+  else
+    box_muller_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(words, n_pairs, (double*)out);
+  return cuda_error(cudaGetLastError(), "dpf_box_muller");
+}
 
 extern "C" dpf_status dpf_resample(const void* w, int32_t dtype, int64_t n_total, int64_t n_seg,
                                    int32_t rule, const uint32_t* u, int32_t* out_idx,

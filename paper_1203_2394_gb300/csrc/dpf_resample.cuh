@@ -127,43 +127,66 @@ __global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) 
   }
   const unsigned long long texcl = v - tsum + wpre;
 
-  // decoupled look-back for the tile's exclusive prefix
-  if (tid == 0) {
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> my_flag(a.st.flags[tile]);
+  // decoupled look-back for the tile's exclusive prefix: warp 0 publishes the
+  // tile's aggregate, then reads its predecessors' flags 32 at a time until it
+  // meets an inclusive prefix (every wait is bounded)
+  if (wid == 0) {
+    const uint32_t ep = a.epoch & 0x3FFFFFFFu;
     unsigned long long prefix = 0;
     if (tile == 0) {
-      a.st.incl[0] = agg;
-      my_flag.store((a.epoch << 2) | 2u, cuda::memory_order_release);
-    } else {
-      a.st.agg[tile] = agg;
-      my_flag.store((a.epoch << 2) | 1u, cuda::memory_order_release);
-      long long j = tile - 1;
-      while (j >= 0) {
-        cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(a.st.flags[j]);
-        uint32_t fv = f.load(cuda::memory_order_acquire);
-        int spins = 0;
-        while ((fv >> 2) != (a.epoch & 0x3FFFFFFFu) || (fv & 3u) == 0u) {
-          if (++spins > SPIN_LIMIT) break;
-          __nanosleep(64);
-          fv = f.load(cuda::memory_order_acquire);
-        }
-        if (spins > SPIN_LIMIT) {
-          atomicOr(a.err, ERR_TIMEOUT);
-          break;
-        }
-        if ((fv & 3u) == 2u) {
-          prefix += a.st.incl[j];
-          break;
-        }
-        prefix += a.st.agg[j];
-        --j;
+      if (lane == 0) {
+        a.st.incl[0] = agg;
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(a.st.flags[0])
+            .store((ep << 2) | 2u, cuda::memory_order_release);
       }
-      a.st.incl[tile] = prefix + agg;
-      my_flag.store((a.epoch << 2) | 2u, cuda::memory_order_release);
+    } else {
+      if (lane == 0) {
+        a.st.agg[tile] = agg;
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(a.st.flags[tile])
+            .store((ep << 2) | 1u, cuda::memory_order_release);
+      }
+      long long hi = tile - 1;
+      while (true) {
+        const long long j = hi - lane;
+        uint32_t fv = 0;
+        bool ready = true;
+        if (j >= 0) {
+          cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(a.st.flags[j]);
+          fv = f.load(cuda::memory_order_acquire);
+          ready = (fv >> 2) == ep && (fv & 3u) != 0u;
+          int spins = 0;
+          while (!ready && spins < SPIN_LIMIT) {
+            __nanosleep(64);
+            fv = f.load(cuda::memory_order_acquire);
+            ready = (fv >> 2) == ep && (fv & 3u) != 0u;
+            ++spins;
+          }
+        }
+        if (!__all_sync(FULL, ready)) {
+          if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+          break;
+        }
+        const unsigned inc = __ballot_sync(FULL, j >= 0 && (fv & 3u) == 2u);
+        const int first = inc ? __ffs(inc) - 1 : 32;
+        unsigned long long val = 0;
+        if (j >= 0 && lane <= first) val = lane == first ? a.st.incl[j] : a.st.agg[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(FULL, val, o);
+        prefix += val;
+        if (inc || hi < 32) break;
+        hi -= 32;
+      }
+      if (lane == 0) {
+        a.st.incl[tile] = prefix + agg;
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(a.st.flags[tile])
+            .store((ep << 2) | 2u, cuda::memory_order_release);
+      }
     }
-    s_prefix = prefix;
-    s_klo = points_below(prefix, a.n, u, C);
-    s_khi = points_below(prefix + agg, a.n, u, C);
+    if (lane == 0) {
+      s_prefix = prefix;
+      s_klo = points_below(prefix, a.n, u, C);
+      s_khi = points_below(prefix + agg, a.n, u, C);
+    }
   }
   __syncthreads();
   // global inclusive cumulative counts of this tile into shared memory

@@ -34,12 +34,12 @@ struct MC {
   T Axx[D1][D1], Azx[D2][D1], Azz[D2][D2];
   T Lqx[D1][D1], LqxInv[D1][D1], Lqz[D2][D2];
   T WAxz[D1][D2];  // Lqx^{-1} A_xz
-  T Hx[DY][D1], Hz[DY][D2], LrInv[DY][DY];
+  T Hx[DY][D1], Hz[DY][D2], LrInv[DY][DY], LrHz[DY][D2];  // LrHz = R^{-1/2} H_z
   T HzAzz[DY][D2], HzAzx[DY][D1], Ls[DY][DY];
   T K[D2][DY];     // Q_z H_z^T (H_z Q_z H_z^T)^{-1}
   T m0x[D1], m0z[D2], Lp0x[D1][D1], G0[D2][D1], Lp0c[D2][D2];
   T ga, gb, qc, lognorm_y;
-  int growth, quad;
+  int growth, quad, diag_qz;
 };
 
 template <typename T>
@@ -72,6 +72,13 @@ struct StepArgs {
   T gcos_prev;  // growth cosine term of the transition into step t-1
   T gcos_cur;   // ... into step t
   int first;    // t == 1: the state is the initial one, no inner step to run
+  // launch geometry, computed on the host (see step_geometry)
+  int tpm, rows, stride;
+  int xp;        // padded length of an x row (16-byte rows)
+  T scaleM, scaleL;  // 2^(31 - ceil(log2 M)) and 2^(31 - ceil(log2 L)): the local-rule scalings
+  uint32_t stage_bytes, stage_tx;
+  uint32_t off_stage, off_sz, off_slq, off_sx, off_slwh, off_sxbb;
+  uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
 };
 
 // Order-preserving unsigned keys of floating-point values (for atomicMax).
@@ -96,49 +103,61 @@ __device__ __forceinline__ float log_t(float v) { return logf(v); }
 __device__ __forceinline__ double log_t(double v) { return log(v); }
 
 // Threads per look-ahead row: a power of two <= 32 with rows * TPM <= NT.
-__host__ __device__ inline int rows_tpm(int nt, int L) {
+inline int rows_tpm(int nt, int L) {
   int tpm = 1;
   while (tpm * 2 <= 32 && tpm * 2 * L <= nt) tpm *= 2;
   return tpm;
 }
 
-// Shared-memory carve-up of step_kernel (bytes), identical on host and device.
-struct StepSmem {
-  size_t zs, cum, ft, gt, lqs, E, xt, ct, xbs, rowS, rowA, shS, shA, coef, red, redU, part, total;
-  int stride;
-};
-template <typename T, int D1, int D2, int DY>
-__host__ __device__ inline StepSmem step_smem(int M, int L, int nt) {
-  StepSmem s;
+// Floats per packed look-ahead record of one inner particle:
+// [a_k, g'_k (DY), f'_k (D1, when x depends on z)], padded to 16 bytes.
+template <typename T, int D1, int DY, bool XZ>
+constexpr int rec_len() {
+  return ((1 + DY + (XZ ? D1 : 0)) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+}
+
+// Shared-memory carve-up and row mapping of step_kernel, on the host: two
+// input stages (the source rows of a group), then the work buffers.
+template <typename T, int D1, int D2, int DY, bool XZ>
+inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = false) {
   const int tpm = rows_tpm(nt, L);
   int stride = M;
   while (stride % 32 != tpm % 32) ++stride;
-  s.stride = stride;
+  const int xp = (int)((D1 * sizeof(T) + 15) / 16 * 16 / sizeof(T));
+  auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  // stage layout
+  size_t so = 0;
+  const uint32_t sz = (uint32_t)so; so += r16(sizeof(T) * D2 * M);
+  const uint32_t slq = (uint32_t)so; so += r16(sizeof(T) * M);
+  const uint32_t sx = (uint32_t)so; so += r16(sizeof(T) * xp);
+  const uint32_t slwh = (uint32_t)so; so += r16(sizeof(T) * L);
+  const uint32_t sxbb = (uint32_t)so; so += r16(sizeof(T) * L * D1);
+  const size_t stage = so;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
-    o += (bytes + 15) & ~(size_t)15;
-    return at;
+    o += r16(bytes);
+    return (uint32_t)at;
   };
-  s.zs = take(sizeof(T) * D2 * M);
-  s.cum = take(sizeof(uint32_t) * M);
-  s.ft = take(sizeof(T) * D1 * M);
-  s.gt = take(sizeof(T) * DY * M);
-  s.lqs = take(sizeof(T) * M);
-  s.E = take(sizeof(T) * (size_t)L * stride);
-  s.xt = take(sizeof(T) * L * D1);
-  s.ct = take(sizeof(T) * L * DY);
-  s.xbs = take(sizeof(T) * L * D1);
-  s.rowS = take(sizeof(T) * L);
-  s.rowA = take(sizeof(T) * L);
-  s.shS = take(sizeof(T) * L);
-  s.shA = take(sizeof(T) * L);
-  s.coef = take(sizeof(T) * L);
-  s.red = take(sizeof(T) * 32);
-  s.redU = take(sizeof(uint32_t) * 32);
-  s.part = take(sizeof(T) * 32 * (D2 + DY + 1));
-  s.total = o;
-  return s;
+  const uint32_t st0 = take(2 * stage), cum = take(sizeof(uint32_t) * M),
+                 kd = take(sizeof(T) * rec_len<T, D1, DY, XZ>() * M),
+                 E = take(sizeof(T) * (size_t)L * stride), xw = take(sizeof(T) * L * D1),
+                 cw = take(sizeof(T) * L * DY), xbs = take(sizeof(T) * L * D1),
+                 row = take(sizeof(T) * L * 5), red = take(sizeof(T) * 32 + sizeof(uint32_t) * 64),
+                 part = take(sizeof(T) * 32 * (D2 + DY));
+  if (a) {
+    a->tpm = tpm;
+    a->rows = nt / tpm;
+    a->stride = stride;
+    a->xp = xp;
+    a->stage_bytes = (uint32_t)stage;
+    a->stage_tx = (uint32_t)(sizeof(T) * (D2 * M + M + xp + (first ? 0 : L + L * D1)));
+    a->off_stage = st0; a->off_sz = sz; a->off_slq = slq; a->off_sx = sx; a->off_slwh = slwh;
+    a->off_sxbb = sxbb;
+    a->off_cum = cum; a->off_kd = kd; a->off_E = E; a->off_xw = xw;
+    a->off_cw = cw; a->off_xbs = xbs; a->off_row = row; a->off_red = red; a->off_part = part;
+  }
+  return o;
 }
 
 // Runtime-width block reductions (blockDim.x is a multiple of 32).
@@ -209,7 +228,7 @@ __device__ __forceinline__ void h_x(const MC<T, D1, D2, DY>& mc, const T (&x)[D1
 // conditional Gaussian, lq = -log M. One CTA per outer particle.
 template <typename T, int D1, int D2, int DY>
 __global__ void init_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, T* z, T* lq, T* x,
-                            long long N, int M, Key key) {
+                            long long N, int M, int xp, Key key) {
   const long long i = blockIdx.x;
   const int j = threadIdx.x;
   if (j >= M) return;
@@ -236,465 +255,685 @@ __global__ void init_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, T* z, 
   lq[i * M + j] = -log_t((T)M);
   if (j == 0) {
 #pragma unroll
-    for (int r = 0; r < D1; ++r) x[(long long)r * N + i] = xi[r];
+    for (int r = 0; r < xp; ++r) x[i * xp + r] = r < D1 ? xi[r < D1 ? r : 0] : T(0);
   }
 }
 
-template <typename T, int D1, int D2, int DY, bool XZ, int MAXNT>
+__device__ __forceinline__ float exp2_t(float x) { return ex2_approx(x); }
+__device__ __forceinline__ double exp2_t(double x) { return exp2(x); }
+__device__ __forceinline__ float log2_t(float x) { return log2f(x); }
+__device__ __forceinline__ double log2_t(double x) { return log2(x); }
+
+constexpr int MBAR_SPIN_LIMIT = 1 << 16;  // bounded wait on a stage's barrier
+constexpr double LOG2E_D = 1.4426950408889634;
+constexpr double LN2_D = 0.6931471805599453;
+constexpr double SQ_D = 0.84932180028801907;  // sqrt(log2(e) / 2): -x^2/2 in log2 units is -(SQ x)^2
+
+// Inclusive scan over the particle index j = tid + p * NT of one uint32 per
+// particle (PPT planes); `red` holds 32 * PPT words.
+template <int PPT>
+__device__ __forceinline__ void bscan_planes(const uint32_t (&c)[PPT], uint32_t (&incl)[PPT],
+                                             uint32_t* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t v[PPT];
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) v[p] = c[p];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const uint32_t n = __shfl_up_sync(FULL, v[p], o);
+      if (lane >= o) v[p] += n;
+    }
+  }
+  __syncthreads();
+  if (lane == 31) {
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) red[p * 32 + w] = v[p];
+  }
+  __syncthreads();
+  uint32_t run = 0;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    uint32_t before = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) {
+      const uint32_t r = red[p * 32 + q];
+      before += q < w ? r : 0u;
+      tot += r;
+    }
+    incl[p] = v[p] + before + run;
+    run += tot;
+  }
+}
+
+// ---- mbarrier and bulk-copy (TMA, non-tensor) wrappers ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(b))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Stage the source rows of one group (its ancestor's, or its own on the first
+// step): the inner set z (d2 rows of M), its log-weights, its x row and the
+// ancestor's look-ahead products. BULK: one thread issues bulk copies that
+// complete on the stage's mbarrier; otherwise all threads copy directly.
+template <typename T, int D1, int D2, bool BULK>
+__device__ __forceinline__ void stage_group(const StepArgs<T>& a, unsigned char* st, uint64_t* bar,
+                                            long long src) {
+  const int M = a.M, L = a.L;
+  T* sz = (T*)(st + a.off_sz);
+  T* slq = (T*)(st + a.off_slq);
+  T* sx = (T*)(st + a.off_sx);
+  T* slwh = (T*)(st + a.off_slwh);
+  T* sxbb = (T*)(st + a.off_sxbb);
+  const long long NM = a.N * (long long)M;
+  if (BULK) {
+    if (threadIdx.x == 0) {
+      mbar_arrive_tx(bar, a.stage_tx);
+#pragma unroll
+      for (int c = 0; c < D2; ++c)
+        bulk_load(sz + c * M, a.z_old + c * NM + src * M, (uint32_t)(M * sizeof(T)), bar);
+      bulk_load(slq, a.lq_old + src * M, (uint32_t)(M * sizeof(T)), bar);
+      bulk_load(sx, a.x_old + src * a.xp, (uint32_t)(a.xp * sizeof(T)), bar);
+      if (!a.first) {
+        bulk_load(slwh, a.lwh_old + src * L, (uint32_t)(L * sizeof(T)), bar);
+        bulk_load(sxbb, a.xbb_old + src * L * D1, (uint32_t)(L * D1 * sizeof(T)), bar);
+      }
+    }
+  } else {
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < D2; ++c) sz[c * M + j] = a.z_old[c * NM + src * M + j];
+      slq[j] = a.lq_old[src * M + j];
+    }
+    for (int c = threadIdx.x; c < D1; c += blockDim.x) sx[c] = a.x_old[src * a.xp + c];
+    if (!a.first) {
+      for (int m = threadIdx.x; m < L; m += blockDim.x) slwh[m] = a.lwh_old[src * L + m];
+      for (int q = threadIdx.x; q < L * D1; q += blockDim.x) sxbb[q] = a.xbb_old[src * L * D1 + q];
+    }
+  }
+}
+
+template <typename T, int D1, int D2, int DY, bool XZ, int PPT, int MAXNT, bool BULK>
 __global__ void __launch_bounds__(MAXNT)
     step_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, const __grid_constant__ StepArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int REC = rec_len<T, D1, DY, XZ>();
   const int NT = blockDim.x;
   const int M = a.M, L = a.L;
   const long long N = a.N;
-  const StepSmem lay = step_smem<T, D1, D2, DY>(M, L, NT);
-  T* zs = (T*)(smem_raw + lay.zs);
-  uint32_t* cum = (uint32_t*)(smem_raw + lay.cum);
-  T* ft = (T*)(smem_raw + lay.ft);
-  T* gt = (T*)(smem_raw + lay.gt);
-  T* lqs = (T*)(smem_raw + lay.lqs);
-  T* E = (T*)(smem_raw + lay.E);
-  T* xt = (T*)(smem_raw + lay.xt);
-  T* ct = (T*)(smem_raw + lay.ct);
-  T* xbs = (T*)(smem_raw + lay.xbs);
-  T* rowS = (T*)(smem_raw + lay.rowS);
-  T* rowA = (T*)(smem_raw + lay.rowA);
-  T* shS = (T*)(smem_raw + lay.shS);
-  T* shA = (T*)(smem_raw + lay.shA);
-  T* coef = (T*)(smem_raw + lay.coef);
-  T* red = (T*)(smem_raw + lay.red);
-  uint32_t* redU = (uint32_t*)(smem_raw + lay.redU);
-  T* part = (T*)(smem_raw + lay.part);
-  __shared__ int s_m;
-  __shared__ int s_fallback;
+  const long long NM = N * (long long)M;
+  unsigned char* const stage0 = smem_raw + a.off_stage;  // two stages of a.stage_bytes
+  uint32_t* cum = (uint32_t*)(smem_raw + a.off_cum);
+  T* kd = (T*)(smem_raw + a.off_kd);
+  T* E = (T*)(smem_raw + a.off_E);
+  T* xw = (T*)(smem_raw + a.off_xw);
+  T* cw = (T*)(smem_raw + a.off_cw);
+  T* xbs = (T*)(smem_raw + a.off_xbs);
+  T* rowS = (T*)(smem_raw + a.off_row);
+  T* rowA = rowS + L;
+  T* shS = rowA + L;
+  T* shA = shS + L;
+  T* coef = shA + L;
+  T* red = (T*)(smem_raw + a.off_red);
+  uint32_t* redU = (uint32_t*)(red + 32);
+  T* part = (T*)(smem_raw + a.off_part);
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_m, s_fallback;
+  __shared__ uint32_t s_uin;
 
-  const long long i = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int j = tid;
-  const bool act = j < M;
   const T NEG = neg_inf<T>();
-  if (i == 0 && tid == 0) *a.Csum = 0ull;
+  const T LOG2E = (T)LOG2E_D, SQ = (T)SQ_D;
+  if (blockIdx.x == 0 && tid == 0) *a.Csum = 0ull;
+  if (BULK && tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
 
-  T x[D1];     // x_{t-1}^(i): the group's outer particle
-  T zr[D2];    // this thread's inner particle z_{t-1}^(i,j)
-  T lqr = NEG; // and its normalised log-weight
-
-  if (a.first) {
-#pragma unroll
-    for (int c = 0; c < D1; ++c) x[c] = a.x_old[(long long)c * N + i];
-    if (act) {
-#pragma unroll
-      for (int c = 0; c < D2; ++c) zr[c] = a.z_old[((long long)c * N + i) * M + j];
-      lqr = a.lq_old[i * M + j];
-    }
-  } else {
-    // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws ----
-    const int anc = a.anc[i];
-    if (tid < 32) {
-      const T l0 = lane < L ? a.lwh_old[(long long)anc * L + lane] : NEG;
-      const T l1 = lane + 32 < L ? a.lwh_old[(long long)anc * L + lane + 32] : NEG;
-      const T mx = warp_max(fmax(l0, l1));
-      const int shift = 31 - ceil_log2_i(L);
-      const uint32_t c0 = lane < L ? quantize_u32(exp_t<T>(l0 - mx), shift) : 0u;
-      const uint32_t c1 = lane + 32 < L ? quantize_u32(exp_t<T>(l1 - mx), shift) : 0u;
-      uint32_t s0 = c0, s1 = c1;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
-        if (lane >= o) {
-          s0 += n0;
-          s1 += n1;
+  // prologue (bulk path): stage the first group; thread 0 keeps the next group's
+  // source index in flight
+  long long g = blockIdx.x;
+  long long src_next = -1;
+  if (BULK && g < N) {
+    const long long src0 = a.first ? g : (long long)a.anc[g];
+    stage_group<T, D1, D2, BULK>(a, stage0, &bars[0], src0);
+    if (tid == 0 && g + gridDim.x < N) src_next = a.first ? g + gridDim.x : (long long)a.anc[g + gridDim.x];
+  }
+  for (int k = 0; g < N; g += gridDim.x, ++k) {
+    const long long i = g;
+    const int sidx = k & 1;
+    unsigned char* st = stage0 + sidx * a.stage_bytes;
+    if (BULK) {
+      // prefetch the next group into the other stage (released at the end of the last group)
+      if (tid == 0 && g + gridDim.x < N) {
+        stage_group<T, D1, D2, BULK>(a, stage0 + (sidx ^ 1) * a.stage_bytes, &bars[sidx ^ 1], src_next);
+        const long long g2 = g + 2 * (long long)gridDim.x;
+        if (g2 < N) src_next = a.first ? g2 : (long long)a.anc[g2];
+      }
+      int spins = 0;
+      while (!mbar_test(&bars[sidx], (uint32_t)((k >> 1) & 1))) {
+        if (++spins > MBAR_SPIN_LIMIT) {
+          if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+          break;
         }
       }
-      const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
-      const uint64_t C = (uint64_t)tot0 + tot1;
-      const uint32_t u = rand_word(a.key, a.t - 1, (uint32_t)i, P_SEL, 0u);
-      const uint64_t rhs = (uint64_t)u * C;
-      const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
-      const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
-      if (lane == 0) {
-        int m = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
-        if (C == 0 || m >= L) {  // no positive weight (NaN or -inf look-ahead weights)
-          atomicOr(a.err, ERR_NUMERIC);
-          m = L - 1;
+    } else {
+      const long long src = a.first ? g : (long long)a.anc[g];
+      stage_group<T, D1, D2, BULK>(a, st, nullptr, src);
+      __syncthreads();
+    }
+    T* sz = (T*)(st + a.off_sz);
+    T* slq = (T*)(st + a.off_slq);
+    T* sx = (T*)(st + a.off_sx);
+    T* slwh = (T*)(st + a.off_slwh);
+    T* sxbb = (T*)(st + a.off_sxbb);
+
+    T x[D1];         // x_{t-1}^(i): the group's outer particle
+    T zr[PPT][D2];   // this thread's inner particles z_{t-1}^(i,j), j = tid + p NT
+    T lqr[PPT];      // and their normalised log-weights
+    T sigma, SA0;    // the largest inner log-weight, and sum_k exp(lq_k - sigma)
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) lqr[p] = NEG;
+
+    if (a.first) {
+#pragma unroll
+      for (int c = 0; c < D1; ++c) x[c] = sx[c];
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        const int j = tid + p * NT;
+        if (j < M) {
+#pragma unroll
+          for (int c = 0; c < D2; ++c) zr[p][c] = sz[c * M + j];
+          lqr[p] = slq[j];
         }
-        s_m = m;
-        a.sel[i] = m;
       }
-    }
-    __syncthreads();
-    const int msel = s_m;
-    T xa[D1];
+      sigma = -log_t((T)M);
+      SA0 = (T)M;
+    } else {
+      // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws ----
+      if (tid < 32) {
+        const T l0 = lane < L ? slwh[lane] : NEG;
+        const T l1 = lane + 32 < L ? slwh[lane + 32] : NEG;
+        const T mx = warp_max(fmax(l0, l1));
+        const T s2 = a.scaleL;
+        const uint32_t c0 = lane < L ? (uint32_t)floor(exp2_t((l0 - mx) * LOG2E) * s2) : 0u;
+        const uint32_t c1 = lane + 32 < L ? (uint32_t)floor(exp2_t((l1 - mx) * LOG2E) * s2) : 0u;
+        uint32_t s0 = c0, s1 = c1;
 #pragma unroll
-    for (int c = 0; c < D1; ++c) {
-      x[c] = a.xbb_old[((long long)anc * L + msel) * D1 + c];
-      xa[c] = a.x_old[(long long)c * N + anc];
-    }
-    // ---- local resampling of the ancestor's inner set (eq. qnobar weights) ----
-    T za[D2];
-    T alpha = NEG;
-    if (act) {
-#pragma unroll
-      for (int c = 0; c < D2; ++c) {
-        za[c] = a.z_old[((long long)c * N + anc) * M + j];
-        zs[c * M + j] = za[c];
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
+          if (lane >= o) {
+            s0 += n0;
+            s1 += n1;
+          }
+        }
+        const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
+        const uint64_t C = (uint64_t)tot0 + tot1;
+        // lanes 0 and 1 draw the two per-group words (selection and local resampling)
+        const uint32_t wsel = philox(ctr(a.t - 1, (uint32_t)i, lane == 0 ? P_SEL : P_INNER, 0u, 0u), a.key).x;
+        const uint32_t usel = __shfl_sync(FULL, wsel, 0);
+        const uint64_t rhs = (uint64_t)usel * C;
+        const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
+        const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
+        if (lane == 0) {
+          int m = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
+          if (C == 0 || m >= L) {  // no positive weight (NaN or -inf look-ahead weights)
+            atomicOr(a.err, ERR_NUMERIC);
+            m = L - 1;
+          }
+          s_m = m;
+          a.sel[i] = m;
+        }
+        if (lane == 1) s_uin = wsel;
       }
-      alpha = a.lq_old[(long long)anc * M + j];
+      __syncthreads();
+      const int msel = s_m;
+      T xa[D1];
+#pragma unroll
+      for (int c = 0; c < D1; ++c) {
+        x[c] = sxbb[msel * D1 + c];
+        xa[c] = sx[c];
+      }
+      // ---- local resampling of the ancestor's inner set (eq. qnobar weights) ----
+      T wres[D1];  // whitened x_{t-1} - (g + A_xx x_a): the z-free part of the residual
       if (XZ) {
         T mxa[D1];
         mu_x(mc, xa, a.gcos_prev, mxa);
-        T q = T(0);
 #pragma unroll
         for (int r = 0; r < D1; ++r) {
           T v = T(0);
 #pragma unroll
           for (int c = 0; c <= r; ++c) v += mc.LqxInv[r][c] * (x[c] - mxa[c]);
-#pragma unroll
-          for (int c = 0; c < D2; ++c) v -= mc.WAxz[r][c] * za[c];
-          q += v * v;
+          wres[r] = v;
         }
-        alpha -= T(0.5) * q;
       }
-    }
-    const T amax = bmax(alpha, red);
-    const int shiftM = 31 - ceil_log2_i(M);
-    const uint32_t cw = act ? quantize_u32(exp_t<T>(alpha - amax), shiftM) : 0u;
-    const uint32_t incl = bscan_u32(cw, redU);
-    if (act) cum[j] = incl;
-    __syncthreads();
-    // ---- propagation and y_{t-1} update (eq. qbar) ----
-    T ell = NEG;
-    if (act) {
+      T alpha[PPT];
+      T amax = NEG;
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        const int j = tid + p * NT;
+        alpha[p] = NEG;
+        if (j < M) {
+          T al = slq[j];
+          if (XZ) {
+            T q = T(0);
+#pragma unroll
+            for (int r = 0; r < D1; ++r) {
+              T v = wres[r];
+#pragma unroll
+              for (int c = 0; c < D2; ++c) v -= mc.WAxz[r][c] * sz[c * M + j];
+              q += v * v;
+            }
+            al -= T(0.5) * q;
+          }
+          alpha[p] = al;
+          amax = fmax(amax, al);
+        }
+      }
+      amax = bmax(amax, red);
+      uint32_t cw_[PPT], incl[PPT];
+#pragma unroll
+      for (int p = 0; p < PPT; ++p)
+        cw_[p] = tid + p * NT < M ? (uint32_t)floor(exp2_t((alpha[p] - amax) * LOG2E) * a.scaleM) : 0u;
+      bscan_planes<PPT>(cw_, incl, redU);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p)
+        if (tid + p * NT < M) cum[tid + p * NT] = incl[p];
+      __syncthreads();
+      // ---- propagation and the y_{t-1} update (eq. qbar) ----
       const uint32_t C = cum[M - 1];
-      const uint32_t u = rand_word(a.key, a.t - 1, (uint32_t)i, P_INNER, 0u);
-      const int b = sys_local_pick(cum, M, C, M, j, u);
-      if (a.dbg_b) a.dbg_b[i * M + j] = b;
-      T eps[D2];
-      normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
+      const uint32_t uin = s_uin;
+      T azx[D2];
 #pragma unroll
       for (int r = 0; r < D2; ++r) {
         T v = T(0);
 #pragma unroll
         for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+        azx[r] = v;
+      }
+      T yh[DY];  // whitened y_{t-1} - q x.^2 - H_x x
+      {
+        T hx[DY], res[DY];
+        h_x(mc, x, hx);
 #pragma unroll
-        for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * zs[c * M + b];
+        for (int q = 0; q < DY; ++q) res[q] = a.y_prev[q] - hx[q];
 #pragma unroll
-        for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
-        zr[r] = v;
+        for (int q = 0; q < DY; ++q) {
+          T v = T(0);
+#pragma unroll
+          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+          yh[q] = v;
+        }
+      }
+      T ell[PPT];
+      T lmax = NEG;
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        const int j = tid + p * NT;
+        ell[p] = NEG;
+        if (j < M) {
+          const int b = sys_local_pick(cum, M, C, M, j, uin);
+          if (a.dbg_b) a.dbg_b[i * M + j] = b;
+          T eps[D2];
+          normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
+          T zb2[D2];
+#pragma unroll
+          for (int c = 0; c < D2; ++c) zb2[c] = sz[c * M + b];
+#pragma unroll
+          for (int r = 0; r < D2; ++r) {
+            T v = azx[r];
+#pragma unroll
+            for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * zb2[c];
+            if (mc.diag_qz) {
+              v += mc.Lqz[r][r] * eps[r];
+            } else {
+#pragma unroll
+              for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+            }
+            zr[p][r] = v;
+          }
+          T qf = T(0);
+#pragma unroll
+          for (int q = 0; q < DY; ++q) {
+            T v = yh[q];
+#pragma unroll
+            for (int c = 0; c < D2; ++c) v -= mc.LrHz[q][c] * zr[p][c];
+            qf += v * v;
+          }
+          ell[p] = T(-0.5) * qf;
+          lmax = fmax(lmax, ell[p]);
+        }
+      }
+      lmax = bmax(lmax, red);
+      T ls = T(0);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p)
+        if (tid + p * NT < M) ls += exp2_t((ell[p] - lmax) * LOG2E);
+      const T lsum = bsum(ls, red);
+      const T llsum = log_t(lsum);
+      T* zn = a.z_new + i * M + tid;
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        if (tid + p * NT < M) {
+          lqr[p] = ell[p] - lmax - llsum;
+#pragma unroll
+          for (int c = 0; c < D2; ++c) zn[c * NM + p * NT] = zr[p][c];
+          a.lq_new[i * M + tid + p * NT] = lqr[p];
+        }
+      }
+      if (tid < D1) a.x_new[i * a.xp + tid] = x[tid];
+      sigma = -llsum;  // the largest lq: its ell equals lmax
+      SA0 = lsum;      // sum_k exp(lq_k - sigma)
+    }
+
+    // ======== look-ahead of step t from (x, z, lq) with y_t ========
+    T ep[PPT][DY];  // projected look-ahead noise (chol of H_z Q_z H_z^T) eps
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int j = tid + p * NT;
+      if (j < M) {
+        T* rec = kd + j * REC;
+        rec[0] = (lqr[p] - sigma) * LOG2E;
+        T e2[DY];
+        normals<DY>(a.key, a.t, (uint32_t)i, P_LA_Z, (uint32_t)j, e2);
+        T g_[DY];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) {
+          T e = T(0);
+#pragma unroll
+          for (int c = 0; c <= q; ++c) e += mc.Ls[q][c] * e2[c];
+          ep[p][q] = e;
+          T v = e;
+#pragma unroll
+          for (int c = 0; c < D1; ++c) v += mc.HzAzx[q][c] * x[c];
+#pragma unroll
+          for (int c = 0; c < D2; ++c) v += mc.HzAzz[q][c] * zr[p][c];
+          g_[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < DY; ++q) {
+          T v = T(0);
+#pragma unroll
+          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * g_[c];
+          rec[1 + q] = SQ * v;
+        }
+        if (XZ) {
+#pragma unroll
+          for (int r = 0; r < D1; ++r) {
+            T v = T(0);
+#pragma unroll
+            for (int c = 0; c < D2; ++c) v += mc.WAxz[r][c] * zr[p][c];
+            rec[1 + DY + r] = SQ * v;
+          }
+        }
+      }
+    }
+    if (XZ) {  // cumulative weights for the categorical draws of the mixture components
+      uint32_t cw_[PPT], incl[PPT];
+#pragma unroll
+      for (int p = 0; p < PPT; ++p)
+        cw_[p] = tid + p * NT < M ? (uint32_t)floor(exp2_t((lqr[p] - sigma) * LOG2E) * a.scaleM) : 0u;
+      bscan_planes<PPT>(cw_, incl, redU);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p)
+        if (tid + p * NT < M) cum[tid + p * NT] = incl[p];
+    }
+    __syncthreads();
+    // ---- L look-ahead draws xbb^(m) (eq. approx1) ----
+    if (tid < L) {
+      const int m = tid;
+      T mux[D1];
+      mu_x(mc, x, a.gcos_cur, mux);
+      T e1[D1], xwm[D1];
+      normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, (uint32_t)m, e1);
+      int jm = 0;
+      if (XZ)
+        jm = sys_local_pick(cum, M, cum[M - 1], 1, 0,
+                            rand_word(a.key, a.t, (uint32_t)i, P_LA_J, (uint32_t)m));
+#pragma unroll
+      for (int c = 0; c < D1; ++c) xwm[c] = (XZ ? kd[jm * REC + 1 + DY + c] / SQ : T(0)) + e1[c];
+      T xb[D1];
+#pragma unroll
+      for (int r = 0; r < D1; ++r) {
+        T v = mux[r];
+#pragma unroll
+        for (int c = 0; c <= r; ++c) v += mc.Lqx[r][c] * xwm[c];
+        xb[r] = v;
+        a.xbb_new[((long long)i * L + m) * D1 + r] = v;
+        xbs[m * D1 + r] = v;
+        xw[m * D1 + r] = SQ * xwm[r];
       }
       T hx[DY], res[DY];
-      h_x(mc, x, hx);
+      h_x(mc, xb, hx);
 #pragma unroll
-      for (int q = 0; q < DY; ++q) {
-        T v = a.y_prev[q] - hx[q];
-#pragma unroll
-        for (int c = 0; c < D2; ++c) v -= mc.Hz[q][c] * zr[c];
-        res[q] = v;
-      }
-      T qf = T(0);
+      for (int q = 0; q < DY; ++q) res[q] = a.y_cur[q] - hx[q];
 #pragma unroll
       for (int q = 0; q < DY; ++q) {
         T v = T(0);
 #pragma unroll
         for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
-        qf += v * v;
-      }
-      ell = T(-0.5) * qf;
-    }
-    const T lmax = bmax(ell, red);
-    const T lsum = bsum(act ? exp_t<T>(ell - lmax) : T(0), red);
-    if (act) {
-      lqr = ell - lmax - log_t(lsum);
-#pragma unroll
-      for (int c = 0; c < D2; ++c) a.z_new[((long long)c * N + i) * M + j] = zr[c];
-      a.lq_new[i * M + j] = lqr;
-    }
-    if (tid == 0) {
-#pragma unroll
-      for (int c = 0; c < D1; ++c) a.x_new[(long long)c * N + i] = x[c];
-    }
-  }
-
-  // ======== look-ahead of step t from (x, z, lq) with y_t ========
-  T ep[DY];  // projected look-ahead noise Ls eps of this inner particle
-  if (act) {
-    lqs[j] = lqr;
-    if (XZ) {
-#pragma unroll
-      for (int r = 0; r < D1; ++r) {
-        T v = T(0);
-#pragma unroll
-        for (int c = 0; c < D2; ++c) v += mc.WAxz[r][c] * zr[c];
-        ft[r * M + j] = v;
-      }
-    }
-    T e2[DY];
-    normals<DY>(a.key, a.t, (uint32_t)i, P_LA_Z, (uint32_t)j, e2);
-    T g[DY];
-#pragma unroll
-    for (int q = 0; q < DY; ++q) {
-      T e = T(0);
-#pragma unroll
-      for (int c = 0; c <= q; ++c) e += mc.Ls[q][c] * e2[c];
-      ep[q] = e;
-      T v = e;
-#pragma unroll
-      for (int c = 0; c < D1; ++c) v += mc.HzAzx[q][c] * x[c];
-#pragma unroll
-      for (int c = 0; c < D2; ++c) v += mc.HzAzz[q][c] * zr[c];
-      g[q] = v;
-    }
-#pragma unroll
-    for (int q = 0; q < DY; ++q) {
-      T v = T(0);
-#pragma unroll
-      for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * g[c];
-      gt[q * M + j] = v;
-    }
-  }
-  // the shift of every exponent: the largest inner log-weight
-  const T sigma = bmax(lqr, red);
-  const T w_lq = act ? exp_t<T>(lqr - sigma) : T(0);
-  T SA0 = T(0);
-  if (!XZ) SA0 = bsum(w_lq, red);
-  if (XZ) {  // categorical draws of the mixture components need the cumulative weights
-    const uint32_t cw = act ? quantize_u32(w_lq, 31 - ceil_log2_i(M)) : 0u;
-    const uint32_t incl = bscan_u32(cw, redU);
-    if (act) cum[j] = incl;
-  }
-  __syncthreads();
-  // ---- L look-ahead draws xbb^(m) (eq. approx1) ----
-  T mux[D1];
-  mu_x(mc, x, a.gcos_cur, mux);
-  for (int m = tid; m < L; m += NT) {
-    T e1[D1], xw[D1];
-    normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, (uint32_t)m, e1);
-    int jm = 0;
-    if (XZ) jm = sys_local_pick(cum, M, cum[M - 1], 1, 0, rand_word(a.key, a.t, (uint32_t)i, P_LA_J, (uint32_t)m));
-#pragma unroll
-    for (int c = 0; c < D1; ++c) xw[c] = (XZ ? ft[c * M + jm] : T(0)) + e1[c];
-    T xb[D1];
-#pragma unroll
-    for (int r = 0; r < D1; ++r) {
-      T v = mux[r];
-#pragma unroll
-      for (int c = 0; c <= r; ++c) v += mc.Lqx[r][c] * xw[c];
-      xb[r] = v;
-      a.xbb_new[((long long)i * L + m) * D1 + r] = v;
-      xbs[m * D1 + r] = v;
-      xt[m * D1 + r] = xw[r];
-    }
-    T hx[DY];
-    h_x(mc, xb, hx);
-    T res[DY];
-#pragma unroll
-    for (int q = 0; q < DY; ++q) res[q] = a.y_cur[q] - hx[q];
-#pragma unroll
-    for (int q = 0; q < DY; ++q) {
-      T v = T(0);
-#pragma unroll
-      for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
-      ct[m * DY + q] = v;
-    }
-  }
-  __syncthreads();
-  // ---- the L x M weights (eq. weightsMC, alpha of eq. qnobar) ----
-  const int tpm = rows_tpm(NT, L);
-  const int rows = NT / tpm;
-  const int stride = lay.stride;
-  for (int m0 = 0; m0 < L; m0 += rows) {
-    const int m = m0 + tid / tpm;
-    const int s = tid % tpm;
-    T Sa = T(0), Sal = T(0);
-    if (m < L) {
-      T cm[DY], xm_[D1];
-#pragma unroll
-      for (int q = 0; q < DY; ++q) cm[q] = ct[m * DY + q];
-#pragma unroll
-      for (int c = 0; c < D1; ++c) xm_[c] = xt[m * D1 + c];
-      for (int k = s; k < M; k += tpm) {
-        T v = lqs[k] - sigma;
-        if (XZ) {
-          T q = T(0);
-#pragma unroll
-          for (int c = 0; c < D1; ++c) {
-            const T d = xm_[c] - ft[c * M + k];
-            q += d * d;
-          }
-          v -= T(0.5) * q;
-          Sa += exp_t<T>(v);
-        }
-        T q2 = T(0);
-#pragma unroll
-        for (int c = 0; c < DY; ++c) {
-          const T d = cm[c] - gt[c * M + k];
-          q2 += d * d;
-        }
-        const T e = exp_t<T>(v - T(0.5) * q2);
-        Sal += e;
-        E[m * stride + k] = e;
-      }
-    }
-    for (int o = tpm >> 1; o > 0; o >>= 1) {
-      Sa += __shfl_xor_sync(FULL, Sa, o);
-      Sal += __shfl_xor_sync(FULL, Sal, o);
-    }
-    if (m < L && s == 0) {
-      rowS[m] = Sal;
-      rowA[m] = XZ ? Sa : SA0;
-      shS[m] = T(0);
-      shA[m] = T(0);
-    }
-  }
-  __syncthreads();
-  // Rows whose sums fell below the normal range are redone with their own maxima.
-  const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-290);
-  if (tid == 0) {
-    int fb = 0;
-    for (int m = 0; m < L; ++m) fb |= (rowS[m] < tiny) || (XZ && rowA[m] < tiny);
-    s_fallback = fb;
-  }
-  __syncthreads();
-  if (s_fallback) {
-    for (int m0 = 0; m0 < L; m0 += rows) {
-      const int m = m0 + tid / tpm;
-      const int s = tid % tpm;
-      const bool need = m < L && ((rowS[m] < tiny) || (XZ && rowA[m] < tiny));
-      T mxa = NEG, mxs = NEG;
-      if (need) {
-        for (int k = s; k < M; k += tpm) {
-          T v = lqs[k] - sigma;
-          if (XZ) {
-            T q = T(0);
-#pragma unroll
-            for (int c = 0; c < D1; ++c) {
-              const T d = xt[m * D1 + c] - ft[c * M + k];
-              q += d * d;
-            }
-            v -= T(0.5) * q;
-          }
-          T q2 = T(0);
-#pragma unroll
-          for (int c = 0; c < DY; ++c) {
-            const T d = ct[m * DY + c] - gt[c * M + k];
-            q2 += d * d;
-          }
-          mxa = fmax(mxa, v);
-          mxs = fmax(mxs, v - T(0.5) * q2);
-        }
-      }
-      for (int o = tpm >> 1; o > 0; o >>= 1) {
-        mxa = fmax(mxa, __shfl_xor_sync(FULL, mxa, o));
-        mxs = fmax(mxs, __shfl_xor_sync(FULL, mxs, o));
-      }
-      T Sa = T(0), Sal = T(0);
-      if (need) {
-        for (int k = s; k < M; k += tpm) {
-          T v = lqs[k] - sigma;
-          if (XZ) {
-            T q = T(0);
-#pragma unroll
-            for (int c = 0; c < D1; ++c) {
-              const T d = xt[m * D1 + c] - ft[c * M + k];
-              q += d * d;
-            }
-            v -= T(0.5) * q;
-            Sa += exp_t<T>(v - mxa);
-          }
-          T q2 = T(0);
-#pragma unroll
-          for (int c = 0; c < DY; ++c) {
-            const T d = ct[m * DY + c] - gt[c * M + k];
-            q2 += d * d;
-          }
-          const T e = exp_t<T>(v - T(0.5) * q2 - mxs);
-          Sal += e;
-          E[m * stride + k] = e;
-        }
-      }
-      for (int o = tpm >> 1; o > 0; o >>= 1) {
-        Sa += __shfl_xor_sync(FULL, Sa, o);
-        Sal += __shfl_xor_sync(FULL, Sal, o);
-      }
-      __syncwarp();
-      if (need && s == 0) {
-        rowS[m] = Sal;
-        shS[m] = mxs;
-        if (XZ) {
-          rowA[m] = Sa;
-          shA[m] = mxa;
-        }
+        cw[m * DY + q] = SQ * v;
       }
     }
     __syncthreads();
-  }
-  // ---- per-draw weights, the outer weight and the estimator coefficients ----
-  if (tid < 32) {
-    T lw0 = NEG, lw1 = NEG;
-    if (lane < L)
-      lw0 = mc.lognorm_y + (log_t(rowS[lane]) + shS[lane]) - (log_t(rowA[lane]) + shA[lane]);
-    if (lane + 32 < L)
-      lw1 = mc.lognorm_y + (log_t(rowS[lane + 32]) + shS[lane + 32]) -
-            (log_t(rowA[lane + 32]) + shA[lane + 32]);
-    if (lane < L) a.lwh_new[i * L + lane] = lw0;
-    if (lane + 32 < L) a.lwh_new[i * L + lane + 32] = lw1;
-    const T mx = warp_max(fmax(lw0, lw1));
-    const T p0 = lane < L ? exp_t<T>(lw0 - mx) : T(0);
-    const T p1 = lane + 32 < L ? exp_t<T>(lw1 - mx) : T(0);
-    const T ps = warp_sum(p0 + p1);
-    const T lwi = mx + log_t(ps) - log_t((T)L);
-    if (lane < L) coef[lane] = p0 / ps / rowS[lane];
-    if (lane + 32 < L) coef[lane + 32] = p1 / ps / rowS[lane + 32];
-    // x part of the filtered mean
+    // ---- the L x M weights (eq. weightsMC with alpha of eq. qnobar), log2 units ----
+    const int tpm = a.tpm, rows = a.rows, stride = a.stride;
+    for (int m0 = 0; m0 < L; m0 += rows) {
+      const int m = m0 + tid / tpm;
+      const int s = tid % tpm;
+      T Sa = T(0), Sal = T(0);
+      if (m < L) {
+        T cm[DY], xm_[D1];
 #pragma unroll
-    for (int c = 0; c < D1; ++c) {
-      T v = (lane < L ? p0 * xbs[lane * D1 + c] : T(0)) +
-            (lane + 32 < L ? p1 * xbs[(lane + 32) * D1 + c] : T(0));
-      v = warp_sum(v) / ps;
-      if (lane == 0) a.xm[(long long)c * N + i] = v;
+        for (int q = 0; q < DY; ++q) cm[q] = cw[m * DY + q];
+#pragma unroll
+        for (int c = 0; c < D1; ++c) xm_[c] = xw[m * D1 + c];
+        T* Erow = E + m * stride;
+#pragma unroll 4
+        for (int k2 = s; k2 < M; k2 += tpm) {
+          const T* rec = kd + k2 * REC;
+          T v = rec[0];
+          if (XZ) {
+#pragma unroll
+            for (int c = 0; c < D1; ++c) {
+              const T d = xm_[c] - rec[1 + DY + c];
+              v = fma(-d, d, v);
+            }
+            Sa += exp2_t(v);
+          }
+#pragma unroll
+          for (int q = 0; q < DY; ++q) {
+            const T d = cm[q] - rec[1 + q];
+            v = fma(-d, d, v);
+          }
+          const T e = exp2_t(v);
+          Sal += e;
+          Erow[k2] = e;
+        }
+      }
+      for (int o = tpm >> 1; o > 0; o >>= 1) {
+        if (XZ) Sa += __shfl_xor_sync(FULL, Sa, o);
+        Sal += __shfl_xor_sync(FULL, Sal, o);
+      }
+      if (m < L && s == 0) {
+        rowS[m] = Sal;
+        rowA[m] = XZ ? Sa : SA0;
+        shS[m] = T(0);
+        shA[m] = T(0);
+      }
     }
+    __syncthreads();
+    // Rows whose sums fell below the normal range are redone with their own maxima.
+    const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-290);
+    if (tid < 32) {
+      int fb = 0;
+      for (int m = lane; m < L; m += 32) fb |= (rowS[m] < tiny) || (XZ && rowA[m] < tiny);
+      fb = __any_sync(FULL, fb);
+      if (lane == 0) s_fallback = fb;
+    }
+    __syncthreads();
+    if (s_fallback) {
+      for (int m0 = 0; m0 < L; m0 += rows) {
+        const int m = m0 + tid / tpm;
+        const int s = tid % tpm;
+        const bool need = m < L && ((rowS[m] < tiny) || (XZ && rowA[m] < tiny));
+        T mxa = NEG, mxs = NEG;
+        for (int pass = 0; pass < 2; ++pass) {
+          T Sa = T(0), Sal = T(0);
+          if (need) {
+            for (int k2 = s; k2 < M; k2 += tpm) {
+              const T* rec = kd + k2 * REC;
+              T v = rec[0];
+              if (XZ) {
+#pragma unroll
+                for (int c = 0; c < D1; ++c) {
+                  const T d = xw[m * D1 + c] - rec[1 + DY + c];
+                  v = fma(-d, d, v);
+                }
+              }
+              T vl = v;
+#pragma unroll
+              for (int q = 0; q < DY; ++q) {
+                const T d = cw[m * DY + q] - rec[1 + q];
+                vl = fma(-d, d, vl);
+              }
+              if (pass == 0) {
+                mxa = fmax(mxa, v);
+                mxs = fmax(mxs, vl);
+              } else {
+                if (XZ) Sa += exp2_t(v - mxa);
+                const T e = exp2_t(vl - mxs);
+                Sal += e;
+                E[m * stride + k2] = e;
+              }
+            }
+          }
+          for (int o = tpm >> 1; o > 0; o >>= 1) {
+            if (pass == 0) {
+              mxa = fmax(mxa, __shfl_xor_sync(FULL, mxa, o));
+              mxs = fmax(mxs, __shfl_xor_sync(FULL, mxs, o));
+            } else {
+              Sa += __shfl_xor_sync(FULL, Sa, o);
+              Sal += __shfl_xor_sync(FULL, Sal, o);
+            }
+          }
+          if (pass == 1 && need && s == 0) {
+            rowS[m] = Sal;
+            shS[m] = mxs;
+            if (XZ) {
+              rowA[m] = Sa;
+              shA[m] = mxa;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- per-draw weights, the outer weight and the estimator coefficients ----
+    if (tid < 32) {
+      const T LN2 = (T)LN2_D;
+      T lw0 = NEG, lw1 = NEG;
+      if (lane < L)
+        lw0 = mc.lognorm_y + LN2 * ((log2_t(rowS[lane]) + shS[lane]) - (log2_t(rowA[lane]) + shA[lane]));
+      if (lane + 32 < L)
+        lw1 = mc.lognorm_y + LN2 * ((log2_t(rowS[lane + 32]) + shS[lane + 32]) -
+                                    (log2_t(rowA[lane + 32]) + shA[lane + 32]));
+      if (lane < L) a.lwh_new[i * L + lane] = lw0;
+      if (lane + 32 < L) a.lwh_new[i * L + lane + 32] = lw1;
+      const T mx = warp_max(fmax(lw0, lw1));
+      const T p0 = lane < L ? exp_t<T>(lw0 - mx) : T(0);
+      const T p1 = lane + 32 < L ? exp_t<T>(lw1 - mx) : T(0);
+      const T ps = warp_sum(p0 + p1);
+      const T lwi = mx + log_t(ps) - log_t((T)L);
+      if (lane < L) coef[lane] = p0 / ps / rowS[lane];
+      if (lane + 32 < L) coef[lane + 32] = p1 / ps / rowS[lane + 32];
+#pragma unroll
+      for (int c = 0; c < D1; ++c) {
+        T v = (lane < L ? p0 * xbs[lane * D1 + c] : T(0)) +
+              (lane + 32 < L ? p1 * xbs[(lane + 32) * D1 + c] : T(0));
+        v = warp_sum(v) / ps;
+        if (lane == 0) a.xm[(long long)c * N + i] = v;
+      }
+      if (lane == 0) {
+        a.lw[i] = lwi;
+        if (lwi != lwi) atomicOr(a.err, ERR_NUMERIC);
+        const unsigned long long key = order_key(lwi);
+        if (lwi == lwi && key > *(volatile unsigned long long*)a.lwmax_key)
+          atomicMax(a.lwmax_key, key);
+      }
+    }
+    __syncthreads();
+    // ---- z part: beta_k = sum_m coef_m E[m][k]; z-mean = A_zx x + A_zz sum beta z + K sum beta ep ----
+    T acc[D2 + DY];
+#pragma unroll
+    for (int c = 0; c < D2 + DY; ++c) acc[c] = T(0);
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int j = tid + p * NT;
+      if (j < M) {
+        T beta = T(0);
+        for (int m = 0; m < L; ++m) beta += coef[m] * E[m * stride + j];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) acc[c] += beta * zr[p][c];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) acc[D2 + q] += beta * ep[p][q];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D2 + DY; ++c) acc[c] = warp_sum(acc[c]);
+    const int w = tid >> 5, nw = NT >> 5;
     if (lane == 0) {
-      a.lw[i] = lwi;
-      if (lwi != lwi) atomicOr(a.err, ERR_NUMERIC);
-      const unsigned long long key = order_key(lwi);
-      if (lwi == lwi && key > *(volatile unsigned long long*)a.lwmax_key)
-        atomicMax(a.lwmax_key, key);
+#pragma unroll
+      for (int c = 0; c < D2 + DY; ++c) part[c * 32 + w] = acc[c];
     }
-  }
-  __syncthreads();
-  // ---- z part: beta_k = sum_m coef_m E[m][k]; z-mean = A_zx x + A_zz sum beta z + K sum beta ep ----
-  T beta = T(0);
-  if (act)
-    for (int m = 0; m < L; ++m) beta += coef[m] * E[m * stride + j];
-  T acc[D2 + DY];
+    __syncthreads();
+    if (tid < D2) {
+      const int r = tid;
+      T sb[D2 + DY];
 #pragma unroll
-  for (int c = 0; c < D2; ++c) acc[c] = act ? beta * zr[c] : T(0);
+      for (int c = 0; c < D2 + DY; ++c) {
+        T v = T(0);
+        for (int q = 0; q < nw; ++q) v += part[c * 32 + q];
+        sb[c] = v;
+      }
+      T v = T(0);
 #pragma unroll
-  for (int q = 0; q < DY; ++q) acc[D2 + q] = act ? beta * ep[q] : T(0);
+      for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * x[c];
 #pragma unroll
-  for (int c = 0; c < D2 + DY; ++c) acc[c] = warp_sum(acc[c]);
-  const int w = tid >> 5, nw = NT >> 5;
-  if (lane == 0) {
+      for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * sb[c];
 #pragma unroll
-    for (int c = 0; c < D2 + DY; ++c) part[c * 32 + w] = acc[c];
-  }
-  __syncthreads();
-  if (tid < D2 + DY) {
-    T v = T(0);
-    for (int q = 0; q < nw; ++q) v += part[tid * 32 + q];
-    part[tid * 32] = v;
-  }
-  __syncthreads();
-  if (tid < D2) {
-    const int r = tid;
-    T v = T(0);
-#pragma unroll
-    for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * x[c];
-#pragma unroll
-    for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * part[c * 32];
-#pragma unroll
-    for (int q = 0; q < DY; ++q) v += mc.K[r][q] * part[(D2 + q) * 32];
-    a.zm[(long long)r * N + i] = v;
+      for (int q = 0; q < DY; ++q) v += mc.K[r][q] * sb[D2 + q];
+      a.zm[(long long)r * N + i] = v;
+    }
+    __syncthreads();  // the stage and the work buffers are free for the next group
   }
 }
 
@@ -720,44 +959,45 @@ struct OuterArgs {
 
 constexpr int RED_NT = 256;
 
-template <typename T>
+template <typename T, int D1, int D2>
 __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
-  __shared__ double sh[RED_NT / 32][4 + 128];
+  constexpr int D = D1 + D2, NV = 2 + D;  // sum W, sum W^2, sum W * mean pieces
+  __shared__ double sh[NV][RED_NT / 32];
   __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int d = a.d1 + a.d2;
   T lwmax;
   order_decode(*a.lwmax_key, lwmax);
-  const int S = 62 - ceil_log2_i(a.N);
-  double s1 = 0, s2 = 0;
-  double sm[128];
-  for (int c = 0; c < d; ++c) sm[c] = 0;
+  const T sS = (T)ldexp(1.0, 62 - ceil_log2_i(a.N));
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
   unsigned long long cc = 0;
   for (long long i = blockIdx.x * (long long)RED_NT + tid; i < a.N; i += (long long)gridDim.x * RED_NT) {
     const T W = exp_t<T>(a.lw[i] - lwmax);
-    cc += quantize_u64(W, S);
+    cc += (unsigned long long)floor(W * sS);  // exact: a power-of-two scaling, then a floor
     const double Wd = (double)W;
-    s1 += Wd;
-    s2 += Wd * Wd;
-    for (int c = 0; c < a.d1; ++c) sm[c] += Wd * (double)a.xm[(long long)c * a.N + i];
-    for (int c = 0; c < a.d2; ++c) sm[a.d1 + c] += Wd * (double)a.zm[(long long)c * a.N + i];
+    v[0] += Wd;
+    v[1] += Wd * Wd;
+#pragma unroll
+    for (int c = 0; c < D1; ++c) v[2 + c] += Wd * (double)a.xm[(long long)c * a.N + i];
+#pragma unroll
+    for (int c = 0; c < D2; ++c) v[2 + D1 + c] += Wd * (double)a.zm[(long long)c * a.N + i];
   }
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  for (int c = 0; c < d; ++c) sm[c] = warp_sum(sm[c]);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(FULL, cc, o);
   if (lane == 0) {
-    sh[w][0] = s1;
-    sh[w][1] = s2;
-    for (int c = 0; c < d; ++c) sh[w][4 + c] = sm[c];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
     if (cc) atomicAdd(a.Csum, cc);
   }
   __syncthreads();
-  if (tid < 4 + d && tid != 2 && tid != 3) {
-    double v = 0;
-    for (int q = 0; q < RED_NT / 32; ++q) v += sh[q][tid];
-    a.partials[(long long)blockIdx.x * (4 + d) + tid] = v;
+  if (tid < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < RED_NT / 32; ++q) s += sh[tid][q];
+    a.partials[(long long)blockIdx.x * NV + tid] = s;
   }
   __threadfence();
   __syncthreads();
@@ -765,16 +1005,29 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the last block combines the per-block partials in parallel (fixed order)
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += RED_NT) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += a.partials[(long long)b * NV + q];
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  }
+  __syncthreads();
   if (tid == 0) {
-    double t1 = 0, t2 = 0;
-    double mean[128];
-    for (int c = 0; c < d; ++c) mean[c] = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      const double* p = a.partials + (long long)b * (4 + d);
-      t1 += p[0];
-      t2 += p[1];
-      for (int c = 0; c < d; ++c) mean[c] += p[4 + c];
+    double tot[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      tot[q] = 0.0;
+      for (int u = 0; u < RED_NT / 32; ++u) tot[q] += sh[q][u];
     }
+    const double t1 = tot[0], t2 = tot[1];
     const bool bad = !(lwmax > neg_inf<T>()) || lwmax != lwmax || !(t1 > 0);
     if (bad) atomicOr(a.err, ERR_NUMERIC);
     const double lz = (double)lwmax + log(t1) - log((double)a.N);
@@ -782,10 +1035,11 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
     a.stats[1] = lz;
     a.stats[2] = t1 * t1 / t2;
     a.stats[3] = t1;
-    for (int c = 0; c < d; ++c) a.stats[4 + a.perm[c]] = mean[c] / t1;
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.stats[4 + a.perm[c]] = tot[2 + c] / t1;
     *a.lwmax_t = lwmax;
     if (a.mean_out)
-      for (int c = 0; c < d; ++c) a.mean_out[c] = a.stats[4 + c];
+      for (int c = 0; c < D; ++c) a.mean_out[c] = a.stats[4 + c];
     if (a.logz_out) *a.logz_out = a.stats[0];
     *a.lwmax_key = 0ull;
     *a.done = 0u;

@@ -1,0 +1,777 @@
+// The step kernel in its warp-per-group form (M <= 256): one warp owns one
+// outer particle i at a time and each lane owns PPL of its inner particles
+// (k = lane + 32 p) in registers, so every reduction and scan of the step is a
+// warp shuffle and no block-wide barrier is needed. The warps are persistent;
+// each has one shared-memory stage into which the next group's source rows are
+// bulk-copied (cp.async.bulk + mbarrier) as soon as the current group has
+// consumed them, overlapping the gather with the look-ahead arithmetic.
+//
+// The arithmetic is that of step_kernel (the same Fig. 4 steps, the same
+// random-number keys and resampling rules). For a model whose x transition does
+// not depend on z, the z-mean weights simplify: with alpha = lq + const_m the
+// outer-and-draw weight of draw m is S_m / sum_m' S_m' (S_m = sum_k e^(m,k)), so
+// beta_k = sum_m pi_m e^(m,k) / S_m = sum_m e^(m,k) / sum_(m,k) e^(m,k), one pass.
+#pragma once
+
+#include <cstring>
+
+#include "dpf_step.cuh"
+
+namespace dpf {
+
+constexpr int WARPS_PER_CTA = 4;
+
+// Philox4x32-10 with the round keys precomputed (they are kernel-uniform).
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ RoundKeys round_keys(Key key) {
+  RoundKeys r;
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    r.k0[q] = key.k0 + (uint32_t)q * 0x9E3779B9u;
+    r.k1[q] = key.k1 + (uint32_t)q * 0xBB67AE85u;
+  }
+  return r;
+}
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r], (uint32_t)p0);
+  }
+  return c;
+}
+template <int N, typename T>
+__device__ __forceinline__ void normals_rk(const RoundKeys& rk, uint32_t t, uint32_t i,
+                                           uint32_t purpose, uint32_t sub, T (&out)[N]) {
+#pragma unroll
+  for (int b = 0; b < (N + 3) / 4; ++b) {
+    const uint4 w = philox_rk(ctr(t, i, purpose, sub, (uint32_t)b), rk);
+    T a0, a1, a2, a3;
+    box_muller(w.x, w.y, a0, a1);
+    if (4 * b + 0 < N) out[4 * b + 0] = a0;
+    if (4 * b + 1 < N) out[4 * b + 1] = a1;
+    if (4 * b + 2 < N) {
+      box_muller(w.z, w.w, a2, a3);
+      out[4 * b + 2] = a2;
+      if (4 * b + 3 < N) out[4 * b + 3] = a3;
+    }
+  }
+}
+
+// Per-warp shared-memory carve-up (bytes from the warp's region), on the host.
+template <typename T, int D1, int D2, int DY, bool XZ>
+inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
+  auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const int xp = (int)((D1 * sizeof(T) + 15) / 16 * 16 / sizeof(T));
+  size_t so = 0;
+  const uint32_t sz = (uint32_t)so; so += r16(sizeof(T) * D2 * M);
+  const uint32_t slq = (uint32_t)so; so += r16(sizeof(T) * M);
+  const uint32_t sx = (uint32_t)so; so += r16(sizeof(T) * xp);
+  const uint32_t slwh = (uint32_t)so; so += r16(sizeof(T) * L);
+  const uint32_t sxbb = (uint32_t)so; so += r16(sizeof(T) * L * D1);
+  size_t o = so;  // the stage comes first
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += r16(bytes);
+    return (uint32_t)at;
+  };
+  const uint32_t cum = take(sizeof(uint32_t) * M), fs = take(XZ ? sizeof(T) * D1 * M : 0),
+                 xw = take(sizeof(T) * L * D1), cw = take(sizeof(T) * L * DY),
+                 xbs = take(sizeof(T) * L * D1), row = take(sizeof(T) * L * 5),
+                 part = take(sizeof(T) * 2 * 33 * L);
+  const size_t warp_bytes = r16(o);
+  if (a) {
+    a->xp = xp;
+    a->stage_bytes = (uint32_t)warp_bytes;  // per-warp region size
+    a->stage_tx = (uint32_t)(sizeof(T) * (D2 * M + M + xp + (first ? 0 : L + L * D1)));
+    a->off_stage = 0; a->off_sz = sz; a->off_slq = slq; a->off_sx = sx; a->off_slwh = slwh;
+    a->off_sxbb = sxbb;
+    a->off_cum = cum; a->off_kd = fs; a->off_xw = xw; a->off_cw = cw; a->off_xbs = xbs;
+    a->off_row = row; a->off_part = part;
+  }
+  return warp_bytes * WARPS_PER_CTA;
+}
+
+// Vector moves of P consecutive elements (16-byte chunks where possible).
+template <typename T, int P>
+__device__ __forceinline__ void vld(const T* src, T (&out)[P]) {
+  constexpr int B = (int)sizeof(T) * P;
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < B / 16; ++q) {
+      const uint4 v = reinterpret_cast<const uint4*>(src)[q];
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      memcpy(reinterpret_cast<char*>(out) + 16 * q, w, 16);
+    }
+  } else if constexpr (B == 8) {
+    const uint2 v = *reinterpret_cast<const uint2*>(src);
+    const uint32_t w[2] = {v.x, v.y};
+    memcpy(out, w, 8);
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) out[q] = src[q];
+  }
+}
+template <typename T, int P>
+__device__ __forceinline__ void vst(T* dst, const T (&in)[P]) {
+  constexpr int B = (int)sizeof(T) * P;
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < B / 16; ++q) {
+      uint32_t w[4];
+      memcpy(w, reinterpret_cast<const char*>(in) + 16 * q, 16);
+      reinterpret_cast<uint4*>(dst)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else if constexpr (B == 8) {
+    uint32_t w[2];
+    memcpy(w, in, 8);
+    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) dst[q] = in[q];
+  }
+}
+
+// acc[p] += a * x[p] for all p: packed FP32x2 FMAs on float pairs, scalar otherwise.
+template <typename T, int P>
+__device__ __forceinline__ void axpy(T a, const T (&x)[P], T (&acc)[P]) {
+  if constexpr (sizeof(T) == 4 && P % 2 == 0) {
+#pragma unroll
+    for (int p = 0; p < P; p += 2) {
+      const float2 r = __ffma2_rn(make_float2(a, a), make_float2(x[p], x[p + 1]),
+                                  make_float2(acc[p], acc[p + 1]));
+      acc[p] = r.x;
+      acc[p + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) acc[p] = fma(a, x[p], acc[p]);
+  }
+}
+// acc[p] -= d[p]^2 with d[p] = c + g[p] (c broadcast): the quadratic-form step
+template <typename T, int P>
+__device__ __forceinline__ void sub_sq(T c, const T (&g)[P], T (&acc)[P]) {
+  if constexpr (sizeof(T) == 4 && P % 2 == 0) {
+#pragma unroll
+    for (int p = 0; p < P; p += 2) {
+      const float2 d = __fadd2_rn(make_float2(c, c), make_float2(g[p], g[p + 1]));
+      const float2 r = __ffma2_rn(make_float2(-d.x, -d.y), d, make_float2(acc[p], acc[p + 1]));
+      acc[p] = r.x;
+      acc[p + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const T d = c + g[p];
+      acc[p] = fma(-d, d, acc[p]);
+    }
+  }
+}
+
+// Issue the bulk copies of one group's source rows into a warp's stage (lane 0).
+template <typename T, int D1, int D2>
+__device__ __forceinline__ void warp_stage(const StepArgs<T>& a, unsigned char* st, uint64_t* bar,
+                                           long long src) {
+  const int M = a.M, L = a.L;
+  const long long NM = a.N * (long long)M;
+  mbar_arrive_tx(bar, a.stage_tx);
+#pragma unroll
+  for (int c = 0; c < D2; ++c)
+    bulk_load(st + a.off_sz + (size_t)c * M * sizeof(T), a.z_old + c * NM + src * M,
+              (uint32_t)(M * sizeof(T)), bar);
+  bulk_load(st + a.off_slq, a.lq_old + src * M, (uint32_t)(M * sizeof(T)), bar);
+  bulk_load(st + a.off_sx, a.x_old + src * a.xp, (uint32_t)(a.xp * sizeof(T)), bar);
+  if (!a.first) {
+    bulk_load(st + a.off_slwh, a.lwh_old + src * L, (uint32_t)(L * sizeof(T)), bar);
+    bulk_load(st + a.off_sxbb, a.xbb_old + src * L * D1, (uint32_t)(L * D1 * sizeof(T)), bar);
+  }
+}
+
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
+    step_warp_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc,
+                     const __grid_constant__ StepArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int M = a.M, L = a.L;
+  const long long N = a.N;
+  const long long NM = N * (long long)M;
+  unsigned char* ws = smem_raw + (size_t)wib * a.stage_bytes;
+  T* sz = (T*)(ws + a.off_sz);
+  T* slq = (T*)(ws + a.off_slq);
+  T* sx = (T*)(ws + a.off_sx);
+  T* slwh = (T*)(ws + a.off_slwh);
+  T* sxbb = (T*)(ws + a.off_sxbb);
+  uint32_t* cum = (uint32_t*)(ws + a.off_cum);
+  T* fs = (T*)(ws + a.off_kd);
+  T* xw = (T*)(ws + a.off_xw);
+  T* cw = (T*)(ws + a.off_cw);
+  T* xbs = (T*)(ws + a.off_xbs);
+  T* rowS = (T*)(ws + a.off_row);
+  T* rowA = rowS + L;
+  T* shS = rowA + L;
+  T* shA = shS + L;
+  T* coef = shA + L;
+  T* part = (T*)(ws + a.off_part);  // [2L][33] lane partials (row stride 33: no bank conflicts)
+  uint64_t* bar = &bars[wib];
+  const T NEG = neg_inf<T>();
+  const T LOG2E = (T)LOG2E_D, SQ = (T)SQ_D, LN2 = (T)LN2_D;
+  const RoundKeys rk = round_keys(a.key);
+  // this lane's inner particles are k0 .. k0 + PPL - 1 (consecutive)
+  const int k0 = PPL * lane;
+  const bool act = k0 < M;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.Csum = 0ull;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+
+  const long long W = (long long)gridDim.x * WARPS_PER_CTA;
+  long long g = (long long)blockIdx.x * WARPS_PER_CTA + wib;
+  long long src_next = -1;
+  if (g < N && lane == 0) {
+    warp_stage<T, D1, D2>(a, ws, bar, a.first ? g : (long long)a.anc[g]);
+    if (g + W < N) src_next = a.first ? g + W : (long long)a.anc[g + W];
+  }
+  uint32_t phase = 0;
+  for (; g < N; g += W, phase ^= 1u) {
+    const long long i = g;
+    {  // wait for this group's rows (bounded)
+      int spins = 0;
+      while (!mbar_test(bar, phase)) {
+        if (++spins > MBAR_SPIN_LIMIT) {
+          if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    T x[D1];
+    T zr[D2][PPL];  // this lane's inner particles z_{t-1}^(i, k0 + p)
+    T lqr[PPL];     // and their normalised log-weights
+    T sigma, SA0;
+
+    if (a.first) {
+#pragma unroll
+      for (int c = 0; c < D1; ++c) x[c] = sx[c];
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) lqr[p] = NEG;
+      if (act) {
+#pragma unroll
+        for (int c = 0; c < D2; ++c) vld<T, PPL>(sz + c * M + k0, zr[c]);
+        vld<T, PPL>(slq + k0, lqr);
+      }
+      sigma = -log_t((T)M);
+      SA0 = (T)M;
+    } else {
+      // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws ----
+      int msel;
+      uint32_t uin;
+      {
+        const T l0 = lane < L ? slwh[lane] : NEG;
+        const T l1 = lane + 32 < L ? slwh[lane + 32] : NEG;
+        const T mx = warp_max(fmax(l0, l1));
+        const uint32_t c0 = lane < L ? (uint32_t)floor(exp2_t((l0 - mx) * LOG2E) * a.scaleL) : 0u;
+        const uint32_t c1 =
+            lane + 32 < L ? (uint32_t)floor(exp2_t((l1 - mx) * LOG2E) * a.scaleL) : 0u;
+        uint32_t s0 = c0, s1 = c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
+          if (lane >= o) {
+            s0 += n0;
+            s1 += n1;
+          }
+        }
+        const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
+        const uint64_t C = (uint64_t)tot0 + tot1;
+        const uint32_t w =
+            philox_rk(ctr(a.t - 1, (uint32_t)i, lane == 0 ? P_SEL : P_INNER, 0u, 0u), rk).x;
+        const uint32_t usel = __shfl_sync(FULL, w, 0);
+        uin = __shfl_sync(FULL, w, 1);
+        const uint64_t rhs = (uint64_t)usel * C;
+        const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
+        const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
+        msel = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
+        if (C == 0 || msel >= L) {
+          if (lane == 0) atomicOr(a.err, ERR_NUMERIC);
+          msel = L - 1;
+        }
+        if (lane == 0) a.sel[i] = msel;
+      }
+      T xa[D1];
+#pragma unroll
+      for (int c = 0; c < D1; ++c) {
+        x[c] = sxbb[msel * D1 + c];
+        xa[c] = sx[c];
+      }
+      // ---- local resampling of the ancestor's inner set (eq. qnobar weights) ----
+      T alpha[PPL];
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) alpha[p] = NEG;
+      if (act) {
+        vld<T, PPL>(slq + k0, alpha);
+        if (XZ) {
+          T mxa[D1], wres[D1];
+          mu_x(mc, xa, a.gcos_prev, mxa);
+#pragma unroll
+          for (int r = 0; r < D1; ++r) {
+            T v = T(0);
+#pragma unroll
+            for (int c = 0; c <= r; ++c) v += mc.LqxInv[r][c] * (x[c] - mxa[c]);
+            wres[r] = v;
+          }
+          T res[D1][PPL];
+#pragma unroll
+          for (int r = 0; r < D1; ++r)
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) res[r][p] = wres[r];
+#pragma unroll
+          for (int c = 0; c < D2; ++c) {
+            T zc[PPL];
+            vld<T, PPL>(sz + c * M + k0, zc);
+#pragma unroll
+            for (int r = 0; r < D1; ++r) axpy<T, PPL>(-mc.WAxz[r][c], zc, res[r]);
+          }
+#pragma unroll
+          for (int r = 0; r < D1; ++r)
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) alpha[p] -= T(0.5) * res[r][p] * res[r][p];
+        }
+      }
+      T amax = NEG;
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) amax = fmax(amax, alpha[p]);
+      amax = warp_max(amax);
+      {
+        uint32_t loc[PPL];
+        uint32_t run = 0;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          run += act ? (uint32_t)floor(exp2_t((alpha[p] - amax) * LOG2E) * a.scaleM) : 0u;
+          loc[p] = run;
+        }
+        uint32_t v = run;  // inclusive warp scan of the lane totals
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t n = __shfl_up_sync(FULL, v, o);
+          if (lane >= o) v += n;
+        }
+        const uint32_t base = v - run;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) loc[p] += base;
+        if (act) vst<uint32_t, PPL>(cum + k0, loc);
+      }
+      __syncwarp();
+      // ---- propagation and the y_{t-1} update (eq. qbar) ----
+      const uint32_t C = cum[M - 1];
+      T azx[D2];
+#pragma unroll
+      for (int r = 0; r < D2; ++r) {
+        T v = T(0);
+#pragma unroll
+        for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+        azx[r] = v;
+      }
+      T yh[DY];
+      {
+        T hx[DY], res[DY];
+        h_x(mc, x, hx);
+#pragma unroll
+        for (int q = 0; q < DY; ++q) res[q] = a.y_prev[q] - hx[q];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) {
+          T v = T(0);
+#pragma unroll
+          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+          yh[q] = v;
+        }
+      }
+      // ancestors of the lane's destinations: a binary search for the first, then
+      // a forward walk (the systematic points are increasing)
+      int bidx[PPL];
+      {
+        const uint64_t scale = (uint64_t)M << 16;
+        const uint64_t u16 = uin >> 16;
+        int b = act ? search_cum(cum, M, scale, (((uint64_t)k0 << 16) + u16) * C) : 0;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          if (p > 0 && act) {
+            const uint64_t rhs = (((uint64_t)(k0 + p) << 16) + u16) * C;
+            while ((uint64_t)cum[b] * scale <= rhs) ++b;
+          }
+          bidx[p] = b;
+        }
+      }
+      if (a.dbg_b && act) vst<int, PPL>(a.dbg_b + i * M + k0, bidx);
+      T eps[D2][PPL];
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) {
+        T e[D2];
+        normals_rk<D2>(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)(k0 + p), e);
+#pragma unroll
+        for (int c = 0; c < D2; ++c) eps[c][p] = e[c];
+      }
+      T zb[D2][PPL];
+#pragma unroll
+      for (int c = 0; c < D2; ++c)
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) zb[c][p] = sz[c * M + bidx[p]];
+#pragma unroll
+      for (int r = 0; r < D2; ++r) {
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) zr[r][p] = azx[r];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) axpy<T, PPL>(mc.Azz[r][c], zb[c], zr[r]);
+        if (mc.diag_qz) {
+          axpy<T, PPL>(mc.Lqz[r][r], eps[r], zr[r]);
+        } else {
+#pragma unroll
+          for (int c = 0; c <= r; ++c) axpy<T, PPL>(mc.Lqz[r][c], eps[c], zr[r]);
+        }
+      }
+      T ell[PPL];
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) ell[p] = T(0);
+#pragma unroll
+      for (int q = 0; q < DY; ++q) {
+        T rq[PPL];
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) rq[p] = yh[q];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) axpy<T, PPL>(-mc.LrHz[q][c], zr[c], rq);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) ell[p] = fma(rq[p], rq[p], ell[p]);
+      }
+      T lmax = NEG;
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) {
+        ell[p] = act ? T(-0.5) * ell[p] : NEG;
+        lmax = fmax(lmax, ell[p]);
+      }
+      lmax = warp_max(lmax);
+      T ls = T(0);
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) ls += act ? exp2_t((ell[p] - lmax) * LOG2E) : T(0);
+      const T lsum = warp_sum(ls);
+      const T llsum = log_t(lsum);
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) lqr[p] = ell[p] - lmax - llsum;
+      if (act) {
+#pragma unroll
+        for (int c = 0; c < D2; ++c) vst<T, PPL>(a.z_new + c * NM + i * M + k0, zr[c]);
+        vst<T, PPL>(a.lq_new + i * M + k0, lqr);
+      }
+      if (lane < D1) a.x_new[i * a.xp + lane] = x[lane < D1 ? lane : 0];
+      sigma = -llsum;
+      SA0 = lsum;
+    }
+    // the stage is consumed: prefetch the next group's rows into it
+    __syncwarp();
+    if (lane == 0 && g + W < N) {
+      warp_stage<T, D1, D2>(a, ws, bar, src_next);
+      const long long g2 = g + 2 * W;
+      if (g2 < N) src_next = a.first ? g2 : (long long)a.anc[g2];
+    }
+
+    // ======== look-ahead of step t from (x, z, lq) with y_t ========
+    T ak[PPL];      // (lq - sigma) log2(e)
+    T ngk[DY][PPL]; // minus the scaled whitened projected draws
+    T ep[DY][PPL];  // projected look-ahead noise
+    T nfk[D1][PPL]; // minus the scaled whitened A_xz z (x transition depends on z)
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) ak[p] = act ? (lqr[p] - sigma) * LOG2E : NEG;
+    {
+      T e2[DY][PPL];
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) {
+        T e[DY];
+        normals_rk<DY>(rk, a.t, (uint32_t)i, P_LA_Z, (uint32_t)(k0 + p), e);
+#pragma unroll
+        for (int q = 0; q < DY; ++q) e2[q][p] = e[q];
+      }
+      T gg[DY][PPL];
+#pragma unroll
+      for (int q = 0; q < DY; ++q) {
+        T hx = T(0);
+#pragma unroll
+        for (int c = 0; c < D1; ++c) hx += mc.HzAzx[q][c] * x[c];
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) ep[q][p] = T(0);
+#pragma unroll
+        for (int c = 0; c <= q; ++c) axpy<T, PPL>(mc.Ls[q][c], e2[c], ep[q]);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) gg[q][p] = ep[q][p] + hx;
+#pragma unroll
+        for (int c = 0; c < D2; ++c) axpy<T, PPL>(mc.HzAzz[q][c], zr[c], gg[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < DY; ++q) {
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) ngk[q][p] = T(0);
+#pragma unroll
+        for (int c = 0; c <= q; ++c) axpy<T, PPL>(-SQ * mc.LrInv[q][c], gg[c], ngk[q]);
+      }
+      if (XZ) {
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          T f[PPL];
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) f[p] = T(0);
+#pragma unroll
+          for (int c = 0; c < D2; ++c) axpy<T, PPL>(mc.WAxz[r][c], zr[c], f);
+          if (act) vst<T, PPL>(fs + r * M + k0, f);
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) nfk[r][p] = -SQ * f[p];
+        }
+      }
+    }
+    if (XZ) {  // cumulative weights for the categorical draws of the mixture components
+      uint32_t loc[PPL];
+      uint32_t run = 0;
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) {
+        run += act ? (uint32_t)floor(exp2_t(ak[p]) * a.scaleM) : 0u;
+        loc[p] = run;
+      }
+      uint32_t v = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += n;
+      }
+      const uint32_t base = v - run;
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) loc[p] += base;
+      if (act) vst<uint32_t, PPL>(cum + k0, loc);
+    }
+    __syncwarp();
+    // ---- L look-ahead draws xbb^(m) (eq. approx1) ----
+    {
+      T mux[D1];
+      mu_x(mc, x, a.gcos_cur, mux);
+      for (int m = lane; m < L; m += 32) {
+        T e1[D1], xwm[D1];
+        normals_rk<D1>(rk, a.t, (uint32_t)i, P_LA_X, (uint32_t)m, e1);
+        int jm = 0;
+        if (XZ)
+          jm = sys_local_pick(cum, M, cum[M - 1], 1, 0,
+                              philox_rk(ctr(a.t, (uint32_t)i, P_LA_J, (uint32_t)m, 0u), rk).x);
+#pragma unroll
+        for (int c = 0; c < D1; ++c) xwm[c] = (XZ ? fs[c * M + jm] : T(0)) + e1[c];
+        T xb[D1];
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          T v = mux[r];
+#pragma unroll
+          for (int c = 0; c <= r; ++c) v += mc.Lqx[r][c] * xwm[c];
+          xb[r] = v;
+          a.xbb_new[((long long)i * L + m) * D1 + r] = v;
+          xbs[m * D1 + r] = v;
+          xw[m * D1 + r] = SQ * xwm[r];
+        }
+        T hx[DY], res[DY];
+        h_x(mc, xb, hx);
+#pragma unroll
+        for (int q = 0; q < DY; ++q) res[q] = a.y_cur[q] - hx[q];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) {
+          T v = T(0);
+#pragma unroll
+          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+          cw[m * DY + q] = SQ * v;
+        }
+      }
+    }
+    __syncwarp();
+    // ---- the L x M weights (eq. weightsMC with alpha of eq. qnobar), log2 units ----
+    T B[PPL];  // beta_k up to normalisation
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) B[p] = T(0);
+    bool general = XZ;
+    if (!XZ) {
+      // one pass: e(m,k) = 2^(a_k - |c'_m - g'_k|^2), S_m = sum_k e, B_k = sum_m e
+      for (int m = 0; m < L; ++m) {
+        T v[PPL];
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) v[p] = ak[p];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) sub_sq<T, PPL>(cw[m * DY + q], ngk[q], v);
+        T sp = T(0);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          const T e = exp2_t(v[p]);
+          B[p] += e;
+          sp += e;
+        }
+        part[m * 33 + lane] = sp;
+      }
+      __syncwarp();
+      // row sums (lane m adds the 32 lane partials of row m)
+      for (int m = lane; m < L; m += 32) {
+        T s = T(0);
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) s += part[m * 33 + l];
+        rowS[m] = s;
+        rowA[m] = SA0;
+        shS[m] = T(0);
+        shA[m] = T(0);
+      }
+      __syncwarp();
+      const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-290);
+      bool bad = false;
+      for (int m = lane; m < L; m += 32) bad |= rowS[m] < tiny;
+      general = __any_sync(FULL, bad);
+    }
+    if (general) {
+      // robust path (x transition depends on z, or a row underflowed): row maxima,
+      // row sums relative to them, then beta with the coefficients pi_m / S_m
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int m = 0; m < L; ++m) {
+          const T ha = pass ? shA[m] : T(0), hs = pass ? shS[m] : T(0);
+          T v[PPL];
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) v[p] = ak[p];
+          if (XZ) {
+#pragma unroll
+            for (int c = 0; c < D1; ++c) sub_sq<T, PPL>(xw[m * D1 + c], nfk[c], v);
+          }
+          T vl[PPL];
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) vl[p] = v[p];
+#pragma unroll
+          for (int q = 0; q < DY; ++q) sub_sq<T, PPL>(cw[m * DY + q], ngk[q], vl);
+          T pa = pass ? T(0) : NEG, ps = pass ? T(0) : NEG;
+          if (act) {
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) {
+              if (pass == 0) {
+                pa = fmax(pa, v[p]);
+                ps = fmax(ps, vl[p]);
+              } else {
+                pa += exp2_t(v[p] - ha);
+                ps += exp2_t(vl[p] - hs);
+              }
+            }
+          }
+          part[m * 33 + lane] = pa;
+          part[(L + m) * 33 + lane] = ps;
+        }
+        __syncwarp();
+        for (int m = lane; m < L; m += 32) {
+          T ra = pass ? T(0) : NEG, rs = pass ? T(0) : NEG;
+          for (int l = 0; l < 32; ++l) {
+            if (pass == 0) {
+              ra = fmax(ra, part[m * 33 + l]);
+              rs = fmax(rs, part[(L + m) * 33 + l]);
+            } else {
+              ra += part[m * 33 + l];
+              rs += part[(L + m) * 33 + l];
+            }
+          }
+          if (pass == 0) {
+            shA[m] = ra;
+            shS[m] = rs;
+          } else {
+            rowA[m] = ra;
+            rowS[m] = rs;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // ---- per-draw weights, the outer weight and the x part of the filtered mean ----
+    T lw0 = NEG, lw1 = NEG;
+    if (lane < L)
+      lw0 = mc.lognorm_y + LN2 * ((log2_t(rowS[lane]) + shS[lane]) - (log2_t(rowA[lane]) + shA[lane]));
+    if (lane + 32 < L)
+      lw1 = mc.lognorm_y + LN2 * ((log2_t(rowS[lane + 32]) + shS[lane + 32]) -
+                                  (log2_t(rowA[lane + 32]) + shA[lane + 32]));
+    if (lane < L) a.lwh_new[i * L + lane] = lw0;
+    if (lane + 32 < L) a.lwh_new[i * L + lane + 32] = lw1;
+    const T mx = warp_max(fmax(lw0, lw1));
+    const T p0 = lane < L ? exp_t<T>(lw0 - mx) : T(0);
+    const T p1 = lane + 32 < L ? exp_t<T>(lw1 - mx) : T(0);
+    const T psum = warp_sum(p0 + p1);
+    const T lwi = mx + log_t(psum) - log_t((T)L);
+#pragma unroll
+    for (int c = 0; c < D1; ++c) {
+      T v = (lane < L ? p0 * xbs[lane * D1 + c] : T(0)) +
+            (lane + 32 < L ? p1 * xbs[(lane + 32) * D1 + c] : T(0));
+      v = warp_sum(v) / psum;
+      if (lane == 0) a.xm[(long long)c * N + i] = v;
+    }
+    if (lane == 0) {
+      a.lw[i] = lwi;
+      if (lwi != lwi) atomicOr(a.err, ERR_NUMERIC);
+      const unsigned long long key = order_key(lwi);
+      if (lwi == lwi && key > *(volatile unsigned long long*)a.lwmax_key)
+        atomicMax(a.lwmax_key, key);
+    }
+    // ---- z part of the filtered mean: beta_k = sum_m pi_m e(m,k) / S_m ----
+    if (general) {
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) B[p] = T(0);
+      if (lane < L) coef[lane] = p0 / psum / rowS[lane];
+      if (lane + 32 < L) coef[lane + 32] = p1 / psum / rowS[lane + 32];
+      __syncwarp();
+      for (int m = 0; m < L; ++m) {
+        const T cf = coef[m], hs = shS[m];
+        T v[PPL];
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) v[p] = ak[p];
+        if (XZ) {
+#pragma unroll
+          for (int c = 0; c < D1; ++c) sub_sq<T, PPL>(xw[m * D1 + c], nfk[c], v);
+        }
+#pragma unroll
+        for (int q = 0; q < DY; ++q) sub_sq<T, PPL>(cw[m * DY + q], ngk[q], v);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) B[p] += act ? cf * exp2_t(v[p] - hs) : T(0);
+      }
+    } else {
+      T tot = T(0);
+      for (int m = lane; m < L; m += 32) tot += rowS[m];
+      tot = warp_sum(tot);
+      const T inv = T(1) / tot;
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) B[p] *= inv;
+    }
+    T acc[D2 + DY];
+#pragma unroll
+    for (int c = 0; c < D2; ++c) {
+      T v = T(0);
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) v = fma(B[p], zr[c][p], v);
+      acc[c] = act ? v : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < DY; ++q) {
+      T v = T(0);
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) v = fma(B[p], ep[q][p], v);
+      acc[D2 + q] = act ? v : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < D2 + DY; ++c) acc[c] = warp_sum(acc[c]);
+    if (lane < D2) {
+      const int r = lane;
+      T v = T(0);
+#pragma unroll
+      for (int c = 0; c < D1; ++c) v += mc.Azx[r < D2 ? r : 0][c] * x[c];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) v += mc.Azz[r < D2 ? r : 0][c] * acc[c];
+#pragma unroll
+      for (int q = 0; q < DY; ++q) v += mc.K[r < D2 ? r : 0][q] * acc[D2 + q];
+      a.zm[(long long)r * N + i] = v;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace dpf

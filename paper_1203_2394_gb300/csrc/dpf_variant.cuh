@@ -4,7 +4,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "dpf_step.cuh"
+#include "dpf_step_warp.cuh"
 
 namespace dpf {
 
@@ -30,6 +30,7 @@ struct VariantImpl {
     cp(h.Hx, &c.Hx[0][0], DY * D1);
     cp(h.Hz, &c.Hz[0][0], DY * D2);
     cp(h.LrInv, &c.LrInv[0][0], DY * DY);
+    cp(h.LrHz, &c.LrHz[0][0], DY * D2);
     cp(h.HzAzz, &c.HzAzz[0][0], DY * D2);
     cp(h.HzAzx, &c.HzAzx[0][0], DY * D1);
     cp(h.Ls, &c.Ls[0][0], DY * DY);
@@ -45,6 +46,9 @@ struct VariantImpl {
     c.lognorm_y = (T)h.lognorm_y;
     c.growth = h.growth;
     c.quad = h.quad;
+    c.diag_qz = 1;
+    for (int r = 0; r < D2; ++r)
+      for (int q = 0; q < r; ++q) c.diag_qz &= (h.Lqz[r * D2 + q] == 0.0);
     out.resize(sizeof(c));
     memcpy(out.data(), &c, sizeof(c));
     return DPF_OK;
@@ -52,28 +56,84 @@ struct VariantImpl {
 
   static const Const& cst(const Ctx& x) { return *reinterpret_cast<const Const*>(x.mconst.data()); }
 
-  static size_t smem(int M, int L) {
-    return step_smem<T, D1, D2, DY>(M, L, threads_for(M)).total;
+  // The warp-per-group kernel serves M <= 256 when every staged row is a
+  // multiple of 16 bytes (bulk copies); the block kernel serves the rest.
+  static bool warp_path(int M, int L) {
+    const size_t s = sizeof(T);
+    const int ppl = M <= 32 ? 1 : M <= 64 ? 2 : M <= 128 ? 4 : 8;
+    return M <= 256 && M % ppl == 0 && (M * s) % 16 == 0 && (L * s) % 16 == 0 &&
+           (L * D1 * s) % 16 == 0;
   }
+  static size_t smem(int M, int L, bool xz, int nt) {
+    if (warp_path(M, L))
+      return xz ? warp_geometry<T, D1, D2, DY, true>(M, L, nullptr)
+                : warp_geometry<T, D1, D2, DY, false>(M, L, nullptr);
+    return xz ? step_geometry<T, D1, D2, DY, true>(M, L, nt, nullptr)
+              : step_geometry<T, D1, D2, DY, false>(M, L, nt, nullptr);
+  }
+  static int xpad() { return (int)((D1 * sizeof(T) + 15) / 16 * 16 / sizeof(T)); }
 
   static dpf_status init(Ctx& x) {
     const Key key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
     init_kernel<T, D1, D2, DY><<<(unsigned)x.N, threads_for(x.M), 0, x.stream>>>(
-        cst(x), (T*)x.z[0], (T*)x.lq[0], (T*)x.x[0], x.N, x.M, key);
+        cst(x), (T*)x.z[0], (T*)x.lq[0], (T*)x.x[0], x.N, x.M, x.xp, key);
     return cuda_error(cudaGetLastError(), "init kernel launch");
   }
 
-  template <bool XZ, int MAXNT>
-  static dpf_status launch_step(Ctx& x, const StepArgs<T>& a, size_t sm) {
-    auto k = step_kernel<T, D1, D2, DY, XZ, MAXNT>;
+  template <bool XZ, int PPT, int MAXNT, bool BULK>
+  static dpf_status launch_step(Ctx& x, StepArgs<T>& a) {
+    auto k = step_kernel<T, D1, D2, DY, XZ, PPT, MAXNT, BULK>;
     static bool attr_done = false;
     if (!attr_done) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
       attr_done = true;
     }
-    k<<<(unsigned)x.N, threads_for(x.M), sm, x.stream>>>(cst(x), a);
+    const int nt = threads_for((x.M + PPT - 1) / PPT);
+    const size_t sm = step_geometry<T, D1, D2, DY, XZ>(x.M, x.L, nt, &a, a.first != 0);
+    if (x.grid_step == 0) {  // persistent grid: as many CTAs as fit on the device at once
+      int nb = 0, dev = 0, nsm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nt, sm);
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return cuda_error(e, "step kernel occupancy");
+      x.grid_step = (nb > 0 ? nb : 1) * nsm;
+    }
+    const long long grid = std::min<long long>(x.N, x.grid_step);
+    k<<<(unsigned)grid, nt, sm, x.stream>>>(cst(x), a);
     return cuda_error(cudaGetLastError(), "step kernel launch");
+  }
+
+  template <bool XZ, int PPL>
+  static dpf_status launch_warp(Ctx& x, StepArgs<T>& a) {
+    auto k = step_warp_kernel<T, D1, D2, DY, XZ, PPL>;
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+      attr_done = true;
+    }
+    const size_t sm = warp_geometry<T, D1, D2, DY, XZ>(x.M, x.L, &a, a.first != 0);
+    if (x.grid_step == 0) {  // persistent grid: as many CTAs as fit on the device at once
+      int nb = 0, dev = 0, nsm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, WARPS_PER_CTA * 32, sm);
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return cuda_error(e, "step kernel occupancy");
+      x.grid_step = (nb > 0 ? nb : 1) * nsm;
+    }
+    const long long grid = std::min<long long>((x.N + WARPS_PER_CTA - 1) / WARPS_PER_CTA, x.grid_step);
+    k<<<(unsigned)grid, WARPS_PER_CTA * 32, sm, x.stream>>>(cst(x), a);
+    return cuda_error(cudaGetLastError(), "step kernel launch");
+  }
+
+  template <bool XZ>
+  static dpf_status launch_xz(Ctx& x, StepArgs<T>& a) {
+    if (!warp_path(x.M, x.L)) return launch_step<XZ, 1, 1024, false>(x, a);
+    if (x.M <= 32) return launch_warp<XZ, 1>(x, a);
+    if (x.M <= 64) return launch_warp<XZ, 2>(x, a);
+    if (x.M <= 128) return launch_warp<XZ, 4>(x, a);
+    return launch_warp<XZ, 8>(x, a);
   }
 
   static dpf_status step(Ctx& x, int) {
@@ -111,10 +171,9 @@ struct VariantImpl {
     a.gcos_prev = h.growth ? (T)(h.gc * std::cos(h.gw * (double)(t - 2))) : T(0);
     a.gcos_cur = h.growth ? (T)(h.gc * std::cos(h.gw * (double)(t - 1))) : T(0);
     a.first = first ? 1 : 0;
-    const size_t sm = smem(x.M, x.L);
-    const int nt = threads_for(x.M);
-    if (h.xz) return nt <= 256 ? launch_step<true, 256>(x, a, sm) : launch_step<true, 1024>(x, a, sm);
-    return nt <= 256 ? launch_step<false, 256>(x, a, sm) : launch_step<false, 1024>(x, a, sm);
+    a.scaleM = (T)std::ldexp(1.0, 31 - ceil_log2_i(x.M));
+    a.scaleL = (T)std::ldexp(1.0, 31 - ceil_log2_i(x.L));
+    return h.xz ? launch_xz<true>(x, a) : launch_xz<false>(x, a);
   }
 
   static dpf_status outer(Ctx& x, double* mean_out, double* logz_out) {
@@ -135,7 +194,7 @@ struct VariantImpl {
     o.mean_out = mean_out;
     o.logz_out = logz_out;
     o.err = x.err;
-    outer_reduce_kernel<T><<<x.n_red_blocks, RED_NT, 0, x.stream>>>(o);
+    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, x.stream>>>(o);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
     const long long t = x.t + 1;
@@ -163,6 +222,7 @@ struct VariantImpl {
 
   static Variant make(int prec) {
     Variant v;
+    v.xpad = &xpad;
     v.prec = prec;
     v.d1 = D1;
     v.d2 = D2;

@@ -53,6 +53,7 @@ SIGNATURES = [
     ("dpf_step_async", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_sync", ctypes.c_int, [_P]),
     ("dpf_resample", ctypes.c_int, [_P, _I32, _I64, _I64, _I32, _P, _P, _P]),
+    ("dpf_box_muller", ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_set_debug", ctypes.c_int, [_P, _I32]),
@@ -166,7 +167,7 @@ class Filter:
     _SHAPES = {
         "lw": lambda s: (s.N,), "lwhat": lambda s: (s.N, s.L), "xbb": lambda s: (s.N, s.L, s.d1),
         "anc": lambda s: (s.N,), "sel": lambda s: (s.N,), "wout": lambda s: (s.N,),
-        "x": lambda s: (s.d1, s.N), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
+        "x": lambda s: (s.N, s.d1), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
         "bidx": lambda s: (s.N, s.M),
     }
 
@@ -205,4 +206,18 @@ def resample(w, u, rule=DPF_SYS_GLOBAL, n_seg=1, out=None, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream(w.device)
     check(lib().dpf_resample(w.data_ptr(), dtype, w.numel(), int(n_seg), int(rule), u.data_ptr(),
                              out.data_ptr(), _stream_ptr(s)))
+    return out
+
+
+def box_muller(words, dtype="float32", stream=None):
+    """The library's normal transform on device words (torch int32 tensor holding the
+    uint32 bit patterns, 2 per pair); returns a device tensor of 2 n_pairs normals."""
+    import torch
+    assert words.is_cuda and words.dtype == torch.int32 and words.numel() % 2 == 0
+    tdt = {"float32": torch.float32, "float64": torch.float64}[dtype]
+    out = torch.empty(words.numel(), dtype=tdt, device=words.device)
+    s = stream if stream is not None else torch.cuda.current_stream(words.device)
+    check(lib().dpf_box_muller(words.data_ptr(), words.numel() // 2,
+                               DPF_F32 if dtype == "float32" else DPF_F64, out.data_ptr(),
+                               _stream_ptr(s)))
     return out

@@ -6,7 +6,7 @@ from oracle import oracle
 
 def state_from_gpu(f):
     """The filter's newest materialised state in the oracle's layout (float64)."""
-    x = f.read("x").T.astype(np.float64)
+    x = f.read("x").astype(np.float64)
     z = f.read("z").transpose(1, 2, 0).astype(np.float64)
     lq = f.read("lq").astype(np.float64)
     return np.ascontiguousarray(x), np.ascontiguousarray(z), np.ascontiguousarray(lq)
