@@ -147,6 +147,29 @@ dpf_status dpf_resample(const void* w, int32_t dtype, int64_t n_total, int64_t n
                         const uint32_t* u, int32_t* out_idx, void* stream);
 
 /*
+ * dpf_resample with DPF_SYS_GLOBAL (one segment), for callers that cannot
+ * allocate device memory while they resample - for example a control loop that
+ * must not allocate after start-up, or an application whose framework allocator
+ * already holds the whole device. The paper has no counterpart; this is a
+ * property of the library, not of the method.
+ * It makes no cudaMalloc, cudaFree or other allocating call: its scratch (the
+ * largest weight, the quantised total and the look-back state of the scan) is
+ * a fixed device array of about 40 KB, one per device, held from the first
+ * call until the process exits. Consequences:
+ *  - n may be at most 4,194,304; larger n gives DPF_E_INVALID (use dpf_resample).
+ *  - Every call on a device shares that array and leaves its contents behind;
+ *    each call clears the part it uses first. Calls whose work overlaps on the
+ *    GPU (different streams, or several host threads) race on it and give
+ *    wrong indices: serialise them.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Arguments, results and errors are those of dpf_resample with n_total = n,
+ * n_seg = 1 and rule = DPF_SYS_GLOBAL; it synchronises `stream`.
+ */
+dpf_status dpf_resample_noalloc(const void* w, int32_t dtype, int64_t n, const uint32_t* u,
+                                int32_t* out_idx, void* stream);
+
+/*
  * The library's Box-Muller transform (the normal draws of every step) applied
  * to given 32-bit words, for verifying its accuracy against the exact formula
  * n0 = sqrt(-2 ln u_a) cos(2 pi u_b), n1 = sqrt(-2 ln u_a) sin(2 pi u_b) with

@@ -39,6 +39,11 @@ void scratch_free(Scratch& sc, cudaStream_t s);
 // Synchronise, read the device error word, free, and map it to a status.
 dpf_status scratch_finish(Scratch& sc, cudaStream_t s, const char* what);
 
+// Launch the global systematic-resampling kernels on caller-provided scratch
+// (laid out as by scratch_alloc and zeroed); no allocation, no synchronisation.
+void launch_global_on(const void* w, int32_t dtype, long long n, const uint32_t* u, int32_t* out,
+                      Scratch& sc, cudaStream_t s);
+
 // Model constants prepared on the host in double precision, in the internal
 // (x-first) coordinate order. Matrices are row-major.
 struct HostModel {

@@ -124,6 +124,15 @@ static void launch_global(const T* w, long long n, const uint32_t* u, int32_t* o
   global_scan_scatter<T, false><<<(unsigned)tiles, SCAN_NT, 0, s>>>(a);
 }
 
+// Launch the global-rule pipeline on scratch the caller has laid out (and zeroed).
+void launch_global_on(const void* w, int32_t dtype, long long n, const uint32_t* u, int32_t* out,
+                      Scratch& sc, cudaStream_t s) {
+  if (dtype == DPF_F32)
+    launch_global<float>((const float*)w, n, u, out, sc, s);
+  else
+    launch_global<double>((const double*)w, n, u, out, sc, s);
+}
+
 template <typename T>
 __global__ void box_muller_kernel(const uint32_t* words, long long n_pairs, T* out) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pairs;

@@ -53,6 +53,7 @@ SIGNATURES = [
     ("dpf_step_async", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_sync", ctypes.c_int, [_P]),
     ("dpf_resample", ctypes.c_int, [_P, _I32, _I64, _I64, _I32, _P, _P, _P]),
+    ("dpf_resample_noalloc", ctypes.c_int, [_P, _I32, _I64, _P, _P, _P]),
     ("dpf_box_muller", ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
@@ -206,6 +207,20 @@ def resample(w, u, rule=DPF_SYS_GLOBAL, n_seg=1, out=None, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream(w.device)
     check(lib().dpf_resample(w.data_ptr(), dtype, w.numel(), int(n_seg), int(rule), u.data_ptr(),
                              out.data_ptr(), _stream_ptr(s)))
+    return out
+
+
+def resample_noalloc(w, u, out=None, stream=None):
+    """Global systematic resampling through the allocation-free entry point (scratch in a
+    fixed per-device array; at most 4,194,304 weights; calls must not overlap on the GPU)."""
+    import torch
+    assert w.is_cuda and u.is_cuda and w.is_contiguous() and u.is_contiguous()
+    dtype = {torch.float32: DPF_F32, torch.float64: DPF_F64}[w.dtype]
+    if out is None:
+        out = torch.empty(w.numel(), dtype=torch.int32, device=w.device)
+    s = stream if stream is not None else torch.cuda.current_stream(w.device)
+    check(lib().dpf_resample_noalloc(w.data_ptr(), dtype, w.numel(), u.data_ptr(), out.data_ptr(),
+                                     _stream_ptr(s)))
     return out
 
 
