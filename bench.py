@@ -33,9 +33,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "growth_clg10"
 METRIC = "particle-updates/s (N*M per step)"
 UNIT = "particle-updates/s"
-KERNEL_SOURCES = ["paper_1203_2394_gb300/csrc/dpf_step.cuh", "paper_1203_2394_gb300/csrc/dpf_common.cuh",
-                  "paper_1203_2394_gb300/csrc/dpf_variant.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_growth_clg10_traffic.json")
+KERNEL_SOURCES = ["paper_1203_2394_gb300/csrc/dpf_step_warp.cuh", "paper_1203_2394_gb300/csrc/dpf_step.cuh",
+                  "paper_1203_2394_gb300/csrc/dpf_common.cuh", "paper_1203_2394_gb300/csrc/dpf_variant.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_warp_kernel_growth_clg10_traffic.json")
 
 
 def b_alg(d1, d2, M, s):
@@ -138,7 +138,7 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(spec, N, M, L, budget_s=12.0, n_sample=2048, seed=0):
+def cpu_oracle_rate(spec, N, M, L, budget_s=15.0, n_sample=8192, seed=0):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload: the
     first steps of a filter with n_sample outer particles (same M, L and model),
     all host cores. Returns (particle-updates/s, threads, sample description)."""
@@ -307,7 +307,7 @@ def run(args):
                    "l2": "state (2 x 302 MB) larger than L2; no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "step_kernel", "kernel_ms": kern_avg_s * 1e3,
+                     "kernel": "step_warp_kernel", "kernel_ms": kern_avg_s * 1e3,
                      "bytes_per_update": per, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spec.dy * 4,
                 "d2h_bytes_per_step": (4 + spec.d) * 8 + 4},

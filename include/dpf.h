@@ -190,12 +190,12 @@ dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ
  * `which` names the array; `bytes` must equal its size exactly:
  *   "lw" (N), "lwhat" (N*L), "xbb" (N*L*d1, [n][m][c]), "anc" (N int32),
  *   "sel" (N int32), "wout" (N, the outer weights fed to the resampler),
- *   "x" (d1*N, [c][n], the newest materialised x), "z" (d2*N*M, [c][n][j]),
- *   "lq" (N*M) - x/z/lq are the newest materialised state, which is step t-1
- *   after step t (the inner update of step t runs at the start of step t+1),
- *   "xsel" (d1*N, [c][n]: x_t after step t), "bidx" (N*M int32, only when
- *   debug recording is on). Element type: the context's precision (or int32).
- * Synchronises the context's stream.
+ *   "x" (N*d1, [n][c]), "z" (d2*N*M, [c][n][j]), "lq" (N*M) - x/z/lq are the
+ *   newest materialised state, which is that of step t-1 after step t (the
+ *   inner update of step t runs at the start of step t+1), and "sel" holds the
+ *   draws that chose it; "bidx" (N*M int32, the local-resampling ancestors of
+ *   that inner update; only when debug recording is on).
+ * Element type: the context's precision (or int32). Synchronises the stream.
  */
 dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t bytes);
 

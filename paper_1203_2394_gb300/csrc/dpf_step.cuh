@@ -76,6 +76,8 @@ struct StepArgs {
   int tpm, rows, stride;
   int xp;        // padded length of an x row (16-byte rows)
   T scaleM, scaleL;  // 2^(31 - ceil(log2 M)) and 2^(31 - ceil(log2 L)): the local-rule scalings
+  T logM, logL;      // log M, log L
+  int log2M;         // ceil(log2 M): halving steps of a search over M entries
   uint32_t stage_bytes, stage_tx;
   uint32_t off_stage, off_sz, off_slq, off_sx, off_slwh, off_sxbb;
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;

@@ -96,6 +96,23 @@ inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
   return warp_bytes * WARPS_PER_CTA;
 }
 
+// log2 for the per-group scalar math: the hardware approximation in FP32 (absolute
+// error about 2^-22, far inside the log-weight tolerance), the accurate one in FP64.
+__device__ __forceinline__ float log2_fast(float x) { return lg2_approx(x); }
+__device__ __forceinline__ double log2_fast(double x) { return log2(x); }
+
+// First index k in [0, n) with cum[k] * scale > rhs, as a fixed number of
+// branch-free halving steps (cum is non-decreasing and cum[n-1] * scale > rhs).
+__device__ __forceinline__ int search_cum_fixed(const uint32_t* cum, int n, uint64_t scale,
+                                                uint64_t rhs, int steps) {
+  int b = 0;  // invariant: every index below b has cum * scale <= rhs
+  for (int s = steps - 1; s >= 0; --s) {
+    const int nb = b + (1 << s);
+    if (nb <= n && (uint64_t)cum[nb - 1] * scale <= rhs) b = nb;
+  }
+  return b;
+}
+
 // Vector moves of P consecutive elements (16-byte chunks where possible).
 template <typename T, int P>
 __device__ __forceinline__ void vld(const T* src, T (&out)[P]) {
@@ -266,7 +283,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
         for (int c = 0; c < D2; ++c) vld<T, PPL>(sz + c * M + k0, zr[c]);
         vld<T, PPL>(slq + k0, lqr);
       }
-      sigma = -log_t((T)M);
+      sigma = -a.logM;
       SA0 = (T)M;
     } else {
       // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws ----
@@ -398,7 +415,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
       {
         const uint64_t scale = (uint64_t)M << 16;
         const uint64_t u16 = uin >> 16;
-        int b = act ? search_cum(cum, M, scale, (((uint64_t)k0 << 16) + u16) * C) : 0;
+        int b = act ? search_cum_fixed(cum, M, scale, (((uint64_t)k0 << 16) + u16) * C, a.log2M) : 0;
 #pragma unroll
         for (int p = 0; p < PPL; ++p) {
           if (p > 0 && act) {
@@ -459,7 +476,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
 #pragma unroll
       for (int p = 0; p < PPL; ++p) ls += act ? exp2_t((ell[p] - lmax) * LOG2E) : T(0);
       const T lsum = warp_sum(ls);
-      const T llsum = log_t(lsum);
+      const T llsum = LN2 * log2_fast(lsum);
 #pragma unroll
       for (int p = 0; p < PPL; ++p) lqr[p] = ell[p] - lmax - llsum;
       if (act) {
@@ -688,17 +705,17 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
     // ---- per-draw weights, the outer weight and the x part of the filtered mean ----
     T lw0 = NEG, lw1 = NEG;
     if (lane < L)
-      lw0 = mc.lognorm_y + LN2 * ((log2_t(rowS[lane]) + shS[lane]) - (log2_t(rowA[lane]) + shA[lane]));
+      lw0 = mc.lognorm_y + LN2 * ((log2_fast(rowS[lane]) + shS[lane]) - (log2_fast(rowA[lane]) + shA[lane]));
     if (lane + 32 < L)
-      lw1 = mc.lognorm_y + LN2 * ((log2_t(rowS[lane + 32]) + shS[lane + 32]) -
-                                  (log2_t(rowA[lane + 32]) + shA[lane + 32]));
+      lw1 = mc.lognorm_y + LN2 * ((log2_fast(rowS[lane + 32]) + shS[lane + 32]) -
+                                  (log2_fast(rowA[lane + 32]) + shA[lane + 32]));
     if (lane < L) a.lwh_new[i * L + lane] = lw0;
     if (lane + 32 < L) a.lwh_new[i * L + lane + 32] = lw1;
     const T mx = warp_max(fmax(lw0, lw1));
-    const T p0 = lane < L ? exp_t<T>(lw0 - mx) : T(0);
-    const T p1 = lane + 32 < L ? exp_t<T>(lw1 - mx) : T(0);
+    const T p0 = lane < L ? exp2_t((lw0 - mx) * LOG2E) : T(0);
+    const T p1 = lane + 32 < L ? exp2_t((lw1 - mx) * LOG2E) : T(0);
     const T psum = warp_sum(p0 + p1);
-    const T lwi = mx + log_t(psum) - log_t((T)L);
+    const T lwi = mx + LN2 * log2_fast(psum) - a.logL;
 #pragma unroll
     for (int c = 0; c < D1; ++c) {
       T v = (lane < L ? p0 * xbs[lane * D1 + c] : T(0)) +

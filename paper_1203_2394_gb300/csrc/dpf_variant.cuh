@@ -173,6 +173,9 @@ struct VariantImpl {
     a.first = first ? 1 : 0;
     a.scaleM = (T)std::ldexp(1.0, 31 - ceil_log2_i(x.M));
     a.scaleL = (T)std::ldexp(1.0, 31 - ceil_log2_i(x.L));
+    a.logM = (T)std::log((double)x.M);
+    a.logL = (T)std::log((double)x.L);
+    a.log2M = ceil_log2_i(x.M);
     return h.xz ? launch_xz<true>(x, a) : launch_xz<false>(x, a);
   }
 
