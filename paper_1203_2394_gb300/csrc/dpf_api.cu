@@ -296,7 +296,7 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   const size_t s = x->prec == DPF_F64 ? 8 : 4;
   const size_t NM = (size_t)N * M;
   const int d = x->d;
-  x->n_red_blocks = (int)std::min<long long>((N + 1023) / 1024, 304);
+  x->n_red_blocks = (int)std::min<long long>((N + 255) / 256, 2 * 152);
   const long long tiles = (N + 2047) / 2048;
   const size_t ssz = sizeof(double) * (4 + 2 * d);
   bool ok = true;

@@ -26,9 +26,17 @@ __device__ __forceinline__ long long points_below(unsigned long long c, long lon
   const u128 X = ((u128)c * (u128)(unsigned long long)n) << 32;
   const u128 uC = (u128)u * (u128)C;
   if (X <= uC) return 0;
-  const u128 Y = (X - uC - 1) >> 32;  // ceil((X - uC) / (C 2^32)) = floor(Y / C) + 1
-  const u128 q = Y / (u128)C + 1;
-  return q >= (u128)n ? n : (long long)q;
+  // K = ceil((X - uC) / (C 2^32)) = floor(Y / C) + 1 with Y = (X - uC - 1) >> 32 < 2^94:
+  // a double estimate of the quotient (<= n < 2^31), corrected exactly in 128 bits
+  const u128 Y = (X - uC - 1) >> 32;
+  const double yd = (double)(unsigned long long)(Y >> 64) * 18446744073709551616.0 +
+                    (double)(unsigned long long)Y;
+  long long q = (long long)(yd / (double)C);
+  if (q < 0) q = 0;
+  while (q > 0 && (u128)(unsigned long long)q * C > Y) --q;
+  while ((u128)(unsigned long long)(q + 1) * C <= Y) ++q;
+  const long long k = q + 1;
+  return k >= n ? n : k;
 }
 
 // Inputs of the scan-and-scatter pass. With from_log the weights are

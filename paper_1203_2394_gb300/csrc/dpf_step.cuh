@@ -970,20 +970,21 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
   T lwmax;
   order_decode(*a.lwmax_key, lwmax);
   const T sS = (T)ldexp(1.0, 62 - ceil_log2_i(a.N));
-  double v[NV];
+  // per-thread and per-warp sums in the working precision (a few hundred terms
+  // of W in [0, 1]), the cross-block combine in double
+  T v[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int q = 0; q < NV; ++q) v[q] = T(0);
   unsigned long long cc = 0;
   for (long long i = blockIdx.x * (long long)RED_NT + tid; i < a.N; i += (long long)gridDim.x * RED_NT) {
     const T W = exp_t<T>(a.lw[i] - lwmax);
     cc += (unsigned long long)floor(W * sS);  // exact: a power-of-two scaling, then a floor
-    const double Wd = (double)W;
-    v[0] += Wd;
-    v[1] += Wd * Wd;
+    v[0] += W;
+    v[1] += W * W;
 #pragma unroll
-    for (int c = 0; c < D1; ++c) v[2 + c] += Wd * (double)a.xm[(long long)c * a.N + i];
+    for (int c = 0; c < D1; ++c) v[2 + c] += W * a.xm[(long long)c * a.N + i];
 #pragma unroll
-    for (int c = 0; c < D2; ++c) v[2 + D1 + c] += Wd * (double)a.zm[(long long)c * a.N + i];
+    for (int c = 0; c < D2; ++c) v[2 + D1 + c] += W * a.zm[(long long)c * a.N + i];
   }
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
@@ -991,7 +992,7 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
   for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(FULL, cc, o);
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+    for (int q = 0; q < NV; ++q) sh[q][w] = (double)v[q];
     if (cc) atomicAdd(a.Csum, cc);
   }
   __syncthreads();
@@ -1008,18 +1009,19 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
   if (!last) return;
   __threadfence();
   // the last block combines the per-block partials in parallel (fixed order)
+  double vd[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int q = 0; q < NV; ++q) vd[q] = 0.0;
   for (int b = tid; b < (int)gridDim.x; b += RED_NT) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += a.partials[(long long)b * NV + q];
+    for (int q = 0; q < NV; ++q) vd[q] += a.partials[(long long)b * NV + q];
   }
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  for (int q = 0; q < NV; ++q) vd[q] = warp_sum(vd[q]);
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+    for (int q = 0; q < NV; ++q) sh[q][w] = vd[q];
   }
   __syncthreads();
   if (tid == 0) {
