@@ -216,6 +216,49 @@ dpf_status dpf_memory(dpf_ctx* ctx, size_t* bytes);
 /* Free everything the context owns (NULL is a no-op). */
 void dpf_destroy(dpf_ctx* ctx);
 
+/*
+ * Batched form: F independent filters stepped together (the many-filter
+ * workload; each filter may have its own model, x/z split d1, N and M, but all
+ * share d, dy, precision and L). Filter f uses seeds[f] (it reproduces a
+ * single filter created with that seed). The filters of one compiled
+ * (precision, d1, d2, dy) variant and inner-particles-per-lane class share one
+ * persistent launch of the step kernel; the outer stages of the filters run
+ * concurrently. Each M must be at most 256 with M, L and L*d1 rows of whole
+ * 16-byte units. models, d1, N, M, seeds: host arrays of F entries.
+ */
+typedef struct dpf_batch dpf_batch;
+dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* d1,
+                            const int64_t* N, const int32_t* M, int32_t L, const uint64_t* seeds,
+                            int32_t F, void* stream, dpf_batch** out);
+
+/* One step of every filter: y_dev is device memory, F x dy (filter-major) of the
+ * batch's precision; means_dev (F x d doubles) and logz_dev (F doubles, the
+ * running log-evidence) are device outputs or NULL. Stream-ordered. */
+dpf_status dpf_batch_step(dpf_batch* b, const void* y_dev, double* means_dev, double* logz_dev);
+
+/* T steps from device observations ys_dev (T x F x dy); means_dev (T x F x d) and
+ * logz_dev (T x F) are device outputs or NULL. With use_graph != 0 the whole run
+ * is captured into one CUDA graph and launched once. Synchronises. */
+dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* means_dev,
+                         double* logz_dev, int32_t use_graph);
+
+/* Time the launch-shape candidates of every class on the live state (reps
+ * launches each, without advancing the filters) and keep the fastest; a JSON
+ * report of the choices is written to report (report_bytes, may be NULL). */
+dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t report_bytes);
+
+/* Borrow filter f's context (for dpf_read, dpf_diag); owned by the batch. */
+dpf_status dpf_batch_filter(dpf_batch* b, int32_t f, dpf_ctx** out);
+
+/* Wait for the batch and report latched device-side errors of any filter. */
+dpf_status dpf_batch_sync(dpf_batch* b);
+
+/* Time the batched step kernels with CUDA events (as dpf_profile). */
+dpf_status dpf_batch_profile(dpf_batch* b, int32_t enable);
+dpf_status dpf_batch_profile_read(dpf_batch* b, double* kernel_ms, int64_t* launches);
+
+void dpf_batch_destroy(dpf_batch* b);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dpf_last_error(void);
 

@@ -21,6 +21,7 @@ dpf_status set_error(dpf_status st, const std::string& msg) {
 void clear_error() { g_err.clear(); }
 dpf_status cuda_error(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return DPF_OK;
+  cudaGetLastError();  // clear the runtime's last-error state so later calls start clean
   if (e == cudaErrorMemoryAllocation)
     return set_error(DPF_E_NOMEM, std::string(what) + ": " + cudaGetErrorString(e));
   return set_error(DPF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -362,7 +363,7 @@ static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
     cudaEventRecord(x->pev[x->pev_used + 1], x->stream);
     x->pev_used += 2;
   }
-  st = x->var->outer(*x, mean_out, logz_out);
+  st = x->var->outer(*x, mean_out, logz_out, x->stream);
   if (st) return st;
   x->t = t;
   return DPF_OK;

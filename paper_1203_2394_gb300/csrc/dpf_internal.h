@@ -61,15 +61,35 @@ struct HostModel {
 // Device buffers and state of one filter (defined below).
 using Ctx = ::dpf_ctx;
 
+// One batched launch: the filters of one (variant, PPL, x-kind) class.
+struct BatchLaunch {
+  const void* mcs;          // device: the class's model constants, one block per filter
+  const void* descs;        // device: the class's per-filter launch arguments
+  const long long* fstart;  // device: F + 1 cumulative group counts
+  int F;
+  long long chunk;          // groups per warp
+  uint32_t region;          // bytes of shared memory per warp
+  size_t smem;              // bytes per CTA
+  int ppl;
+  bool xz;
+  int grid;
+};
+
 // Per-variant launchers, one set per compiled (precision, d1, d2, dy).
 struct Variant {
   int prec, d1, d2, dy;
   dpf_status (*make_const)(const HostModel&, std::vector<unsigned char>&);
   dpf_status (*init)(Ctx&);
   dpf_status (*step)(Ctx&, int profile_slot);
-  dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out);
+  dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out, cudaStream_t s);
   size_t (*step_smem)(int M, int L, bool xz, int nt);
   int (*xpad)();
+  void (*batch_args)(Ctx&, const void* y_prev, const void* y_cur, bool xz, void* out);
+  size_t (*region_bytes)(int M, int L, bool xz);
+  dpf_status (*batch_launch)(const BatchLaunch&, cudaStream_t, int* occ);
+  bool (*use_xz)(const Ctx&);
+  int (*ppl_for)(int M);
+  size_t args_size, const_size;
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
 

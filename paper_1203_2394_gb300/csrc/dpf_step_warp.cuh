@@ -208,17 +208,17 @@ __device__ __forceinline__ void warp_stage(const StepArgs<T>& a, unsigned char* 
   }
 }
 
+// Steps groups gfirst, gfirst + W, ... (< gend) of one filter with one warp:
+// `mc` and `a` may live in kernel parameters or in global memory; `ws` is the
+// warp's shared-memory region, `bar` its stage barrier, `phase` its parity.
 template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
-    step_warp_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc,
-                     const __grid_constant__ StepArgs<T> a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[WARPS_PER_CTA];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+__device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const StepArgs<T>& a,
+                                         long long gfirst, long long gend, long long W,
+                                         unsigned char* ws, uint64_t* bar, uint32_t& phase) {
+  const int lane = threadIdx.x & 31;
   const int M = a.M, L = a.L;
   const long long N = a.N;
   const long long NM = N * (long long)M;
-  unsigned char* ws = smem_raw + (size_t)wib * a.stage_bytes;
   T* sz = (T*)(ws + a.off_sz);
   T* slq = (T*)(ws + a.off_slq);
   T* sx = (T*)(ws + a.off_sx);
@@ -235,29 +235,22 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
   T* shA = shS + L;
   T* coef = shA + L;
   T* part = (T*)(ws + a.off_part);  // [2L][33] lane partials (row stride 33: no bank conflicts)
-  uint64_t* bar = &bars[wib];
   const T NEG = neg_inf<T>();
   const T LOG2E = (T)LOG2E_D, SQ = (T)SQ_D, LN2 = (T)LN2_D;
   const RoundKeys rk = round_keys(a.key);
   // this lane's inner particles are k0 .. k0 + PPL - 1 (consecutive)
   const int k0 = PPL * lane;
   const bool act = k0 < M;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.Csum = 0ull;
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    mbar_fence_init();
+  if (gfirst == 0 && lane == 0) *a.Csum = 0ull;  // the outer reduction of this step sums into it
+
+  long long g = gfirst;
+  long long src_next = -1;
+  if (g < gend && lane == 0) {
+    warp_stage<T, D1, D2>(a, ws, bar, a.first ? g : (long long)a.anc[g]);
+    if (g + W < gend) src_next = a.first ? g + W : (long long)a.anc[g + W];
   }
   __syncwarp();
-
-  const long long W = (long long)gridDim.x * WARPS_PER_CTA;
-  long long g = (long long)blockIdx.x * WARPS_PER_CTA + wib;
-  long long src_next = -1;
-  if (g < N && lane == 0) {
-    warp_stage<T, D1, D2>(a, ws, bar, a.first ? g : (long long)a.anc[g]);
-    if (g + W < N) src_next = a.first ? g + W : (long long)a.anc[g + W];
-  }
-  uint32_t phase = 0;
-  for (; g < N; g += W, phase ^= 1u) {
+  for (; g < gend; g += W, phase ^= 1u) {
     const long long i = g;
     {  // wait for this group's rows (bounded)
       int spins = 0;
@@ -490,10 +483,10 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
     }
     // the stage is consumed: prefetch the next group's rows into it
     __syncwarp();
-    if (lane == 0 && g + W < N) {
+    if (lane == 0 && g + W < gend) {
       warp_stage<T, D1, D2>(a, ws, bar, src_next);
       const long long g2 = g + 2 * W;
-      if (g2 < N) src_next = a.first ? g2 : (long long)a.anc[g2];
+      if (g2 < gend) src_next = a.first ? g2 : (long long)a.anc[g2];
     }
 
     // ======== look-ahead of step t from (x, z, lq) with y_t ========
@@ -788,6 +781,61 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
       a.zm[(long long)r * N + i] = v;
     }
     __syncwarp();
+  }
+}
+
+
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
+    step_warp_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc,
+                     const __grid_constant__ StepArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (lane == 0) {
+    mbar_init(&bars[wib], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  warp_run<T, D1, D2, DY, XZ, PPL>(mc, a, (long long)blockIdx.x * WARPS_PER_CTA + wib, a.N,
+                                   (long long)gridDim.x * WARPS_PER_CTA,
+                                   smem_raw + (size_t)wib * a.stage_bytes, &bars[wib], phase);
+}
+
+// Many filters of one (precision, d1, d2, dy, PPL) class in one persistent
+// launch: the class's groups are numbered filter after filter (fstart[f] is the
+// first item of filter f) and each warp steps a contiguous chunk of them.
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
+    step_warp_batch_kernel(const MC<T, D1, D2, DY>* __restrict__ mcs,
+                           const StepArgs<T>* __restrict__ descs, const long long* __restrict__ fstart,
+                           int F, long long chunk, uint32_t region) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (lane == 0) {
+    mbar_init(&bars[wib], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  const long long total = fstart[F];
+  long long item = ((long long)blockIdx.x * WARPS_PER_CTA + wib) * chunk;
+  const long long iend = item + chunk < total ? item + chunk : total;
+  int lo = 0, hi = F;  // the filter holding `item`: last f with fstart[f] <= item
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (fstart[mid] <= item) lo = mid; else hi = mid;
+  }
+  int f = lo;
+  uint32_t phase = 0;
+  unsigned char* ws = smem_raw + (size_t)wib * region;
+  while (item < iend) {
+    while (fstart[f + 1] <= item) ++f;
+    const long long seg_end = iend < fstart[f + 1] ? iend : fstart[f + 1];
+    warp_run<T, D1, D2, DY, XZ, PPL>(mcs[f], descs[f], item - fstart[f], seg_end - fstart[f], 1,
+                                     ws, &bars[wib], phase);
+    item = seg_end;
   }
 }
 

@@ -10,7 +10,8 @@ namespace dpf {
 
 inline int threads_for(int M) { return ((M + 31) / 32) * 32; }
 
-template <typename T, int D1, int D2, int DY>
+// XZM: 0 = kernels for both x-transition kinds, 1 = only the general (x depends on z) kernels.
+template <typename T, int D1, int D2, int DY, int XZM = 0>
 struct VariantImpl {
   typedef MC<T, D1, D2, DY> Const;
 
@@ -65,6 +66,7 @@ struct VariantImpl {
            (L * D1 * s) % 16 == 0;
   }
   static size_t smem(int M, int L, bool xz, int nt) {
+    if (XZM == 1) xz = true;
     if (warp_path(M, L))
       return xz ? warp_geometry<T, D1, D2, DY, true>(M, L, nullptr)
                 : warp_geometry<T, D1, D2, DY, false>(M, L, nullptr);
@@ -136,10 +138,9 @@ struct VariantImpl {
     return launch_warp<XZ, 8>(x, a);
   }
 
-  static dpf_status step(Ctx& x, int) {
+  static void fill_args(Ctx& x, StepArgs<T>& a) {
     const long long t = x.t + 1;  // the step being taken
     const int so = (int)((t + 2) % 2), sn = (int)((t + 1) % 2);  // slots of t-2 and t-1
-    StepArgs<T> a{};
     const bool first = (t == 1);
     a.z_old = (const T*)x.z[first ? 0 : so];
     a.lq_old = (const T*)x.lq[first ? 0 : so];
@@ -176,10 +177,70 @@ struct VariantImpl {
     a.logM = (T)std::log((double)x.M);
     a.logL = (T)std::log((double)x.L);
     a.log2M = ceil_log2_i(x.M);
-    return h.xz ? launch_xz<true>(x, a) : launch_xz<false>(x, a);
   }
 
-  static dpf_status outer(Ctx& x, double* mean_out, double* logz_out) {
+  static bool use_xz(const Ctx& x) { return XZM == 1 || x.hm.xz; }
+
+  static dpf_status step(Ctx& x, int) {
+    StepArgs<T> a{};
+    fill_args(x, a);
+    if constexpr (XZM == 1) return launch_xz<true>(x, a);
+    else return use_xz(x) ? launch_xz<true>(x, a) : launch_xz<false>(x, a);
+  }
+
+  // ---- many filters of this variant in one launch per PPL class ----
+  static int ppl_for(int M) { return M <= 32 ? 1 : M <= 64 ? 2 : M <= 128 ? 4 : 8; }
+
+  // Per-filter launch arguments for a batched step (y rows given by the batch).
+  static void batch_args(Ctx& x, const void* y_prev, const void* y_cur, bool xz, void* out) {
+    StepArgs<T> a{};
+    fill_args(x, a);
+    a.y_prev = (const T*)y_prev;
+    a.y_cur = (const T*)y_cur;
+    if (xz)
+      warp_geometry<T, D1, D2, DY, true>(x.M, x.L, &a, a.first != 0);
+    else
+      warp_geometry<T, D1, D2, DY, false>(x.M, x.L, &a, a.first != 0);
+    memcpy(out, &a, sizeof(a));
+  }
+  static size_t region_bytes(int M, int L, bool xz) {
+    return (xz ? warp_geometry<T, D1, D2, DY, true>(M, L, nullptr)
+               : warp_geometry<T, D1, D2, DY, false>(M, L, nullptr)) / WARPS_PER_CTA;
+  }
+
+  template <bool XZ, int PPL>
+  static dpf_status batch_kernel(const BatchLaunch& b, cudaStream_t s, int* occ) {
+    auto k = step_warp_batch_kernel<T, D1, D2, DY, XZ, PPL>;
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+      attr_done = true;
+    }
+    if (occ) {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, WARPS_PER_CTA * 32, b.smem);
+      return cuda_error(e, "batch kernel occupancy");
+    }
+    k<<<b.grid, WARPS_PER_CTA * 32, b.smem, s>>>((const Const*)b.mcs, (const StepArgs<T>*)b.descs,
+                                                b.fstart, b.F, b.chunk, b.region);
+    return cuda_error(cudaGetLastError(), "batch step kernel launch");
+  }
+  template <bool XZ>
+  static dpf_status batch_ppl(const BatchLaunch& b, cudaStream_t s, int* occ) {
+    switch (b.ppl) {
+      case 1: return batch_kernel<XZ, 1>(b, s, occ);
+      case 2: return batch_kernel<XZ, 2>(b, s, occ);
+      case 4: return batch_kernel<XZ, 4>(b, s, occ);
+      default: return batch_kernel<XZ, 8>(b, s, occ);
+    }
+  }
+  // Launch (occ == nullptr) or query the blocks per SM (occ != nullptr).
+  static dpf_status batch_launch(const BatchLaunch& b, cudaStream_t s, int* occ) {
+    if constexpr (XZM == 1) return batch_ppl<true>(b, s, occ);
+    else return b.xz ? batch_ppl<true>(b, s, occ) : batch_ppl<false>(b, s, occ);
+  }
+
+  static dpf_status outer(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
     OuterArgs<T> o{};
     o.lw = (const T*)x.lw;
     o.xm = (const T*)x.xm;
@@ -197,7 +258,7 @@ struct VariantImpl {
     o.mean_out = mean_out;
     o.logz_out = logz_out;
     o.err = x.err;
-    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, x.stream>>>(o);
+    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, st>>>(o);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
     const long long t = x.t + 1;
@@ -219,7 +280,7 @@ struct VariantImpl {
     g.epoch = ++x.epoch;
     g.err = x.err;
     x.ticket_next += (unsigned long long)tiles;
-    global_scan_scatter<T, true><<<(unsigned)tiles, SCAN_NT, 0, x.stream>>>(g);
+    global_scan_scatter<T, true><<<(unsigned)tiles, SCAN_NT, 0, st>>>(g);
     return cuda_error(cudaGetLastError(), "outer resample launch");
   }
 
@@ -235,6 +296,13 @@ struct VariantImpl {
     v.step = &step;
     v.outer = &outer;
     v.step_smem = &smem;
+    v.batch_args = &batch_args;
+    v.region_bytes = &region_bytes;
+    v.batch_launch = &batch_launch;
+    v.use_xz = &use_xz;
+    v.ppl_for = &ppl_for;
+    v.args_size = sizeof(StepArgs<T>);
+    v.const_size = sizeof(Const);
     return v;
   }
 };

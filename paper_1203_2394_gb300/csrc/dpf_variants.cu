@@ -6,9 +6,15 @@ namespace dpf {
 Variant make_v_f32_2_8_2();
 Variant make_v_f64_2_2_2();
 Variant make_v_f32_2_2_2();
+Variant make_v_f32_1_15_4();
+Variant make_v_f32_2_14_4();
+Variant make_v_f32_4_12_4();
+Variant make_v_f32_8_8_4();
 
 const Variant* find_variant(int prec, int d1, int d2, int dy) {
-  static const Variant table[] = {make_v_f32_2_8_2(), make_v_f64_2_2_2(), make_v_f32_2_2_2()};
+  static const Variant table[] = {make_v_f32_2_8_2(), make_v_f64_2_2_2(), make_v_f32_2_2_2(),
+                                  make_v_f32_1_15_4(), make_v_f32_2_14_4(), make_v_f32_4_12_4(),
+                                  make_v_f32_8_8_4()};
   for (const Variant& v : table)
     if (v.prec == prec && v.d1 == d1 && v.d2 == d2 && v.dy == dy) return &v;
   return nullptr;

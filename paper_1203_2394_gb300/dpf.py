@@ -61,6 +61,15 @@ SIGNATURES = [
     ("dpf_profile", ctypes.c_int, [_P, _I32]),
     ("dpf_profile_read", ctypes.c_int, [_P, _P, _P]),
     ("dpf_memory", ctypes.c_int, [_P, _P]),
+    ("dpf_batch_create", ctypes.c_int, [_P, _P, _P, _P, _I32, _P, _I32, _P, _P]),
+    ("dpf_batch_step", ctypes.c_int, [_P, _P, _P, _P]),
+    ("dpf_batch_run", ctypes.c_int, [_P, _P, _I64, _P, _P, _I32]),
+    ("dpf_batch_autotune", ctypes.c_int, [_P, _I32, ctypes.c_char_p, _SZ]),
+    ("dpf_batch_filter", ctypes.c_int, [_P, _I32, _P]),
+    ("dpf_batch_sync", ctypes.c_int, [_P]),
+    ("dpf_batch_profile", ctypes.c_int, [_P, _I32]),
+    ("dpf_batch_profile_read", ctypes.c_int, [_P, _P, _P]),
+    ("dpf_batch_destroy", None, [_P]),
     ("dpf_destroy", None, [_P]),
     ("dpf_last_error", ctypes.c_char_p, []),
 ]
@@ -194,6 +203,84 @@ class Filter:
         b = ctypes.c_size_t()
         check(self._lib.dpf_memory(self.h, ctypes.byref(b)))
         return b.value
+
+
+class _Borrowed(Filter):
+    """A batch member's context viewed as a Filter (owned by the batch)."""
+
+    def __init__(self, h, model, d1, d2, N, M, L):
+        self.model = model
+        self.d1, self.d2, self.N, self.M, self.L = d1, d2, N, M, L
+        self.d, self.dy = model.d, model.dy
+        self.dtype = np.float64 if model.precision == DPF_F64 else np.float32
+        self._lib = lib()
+        self.h = h
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Many filters stepped together (``dpf_batch_*``)."""
+
+    def __init__(self, models, d1s, Ns, Ms, L, seeds, stream=None):
+        self.models = list(models)
+        F = len(self.models)
+        self.F, self.L = F, int(L)
+        self.d, self.dy = self.models[0].d, self.models[0].dy
+        self.d1s = [int(v) for v in d1s]
+        self.Ns = [int(v) for v in Ns]
+        self.Ms = [int(v) for v in Ms]
+        descs = (ctypes.c_void_p * F)(*[ctypes.addressof(m.desc) for m in self.models])
+        d1a = (ctypes.c_int32 * F)(*self.d1s)
+        Na = (ctypes.c_int64 * F)(*self.Ns)
+        Ma = (ctypes.c_int32 * F)(*self.Ms)
+        Sa = (ctypes.c_uint64 * F)(*[int(s) for s in seeds])
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        check(self._lib.dpf_batch_create(descs, d1a, Na, Ma, self.L, Sa, F, _stream_ptr(stream),
+                                         ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dpf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step_device(self, y_ptr, means_ptr=None, logz_ptr=None):
+        check(self._lib.dpf_batch_step(self.h, y_ptr, means_ptr, logz_ptr))
+
+    def run_device(self, ys_ptr, T, means_ptr=None, logz_ptr=None, graph=True):
+        check(self._lib.dpf_batch_run(self.h, ys_ptr, int(T), means_ptr, logz_ptr, int(bool(graph))))
+
+    def sync(self):
+        check(self._lib.dpf_batch_sync(self.h))
+
+    def autotune(self, reps=3):
+        buf = ctypes.create_string_buffer(1 << 16)
+        check(self._lib.dpf_batch_autotune(self.h, int(reps), buf, len(buf)))
+        import json
+        return json.loads(buf.value.decode())
+
+    def profile(self, on=True):
+        check(self._lib.dpf_batch_profile(self.h, int(on)))
+
+    def profile_read(self):
+        ms = ctypes.c_double(); n = ctypes.c_int64()
+        check(self._lib.dpf_batch_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def filter(self, f) -> Filter:
+        h = ctypes.c_void_p()
+        check(self._lib.dpf_batch_filter(self.h, int(f), ctypes.byref(h)))
+        return _Borrowed(h, self.models[f], self.d1s[f], self.d - self.d1s[f], self.Ns[f],
+                         self.Ms[f], self.L)
 
 
 def resample(w, u, rule=DPF_SYS_GLOBAL, n_seg=1, out=None, stream=None):
