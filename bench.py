@@ -323,6 +323,113 @@ def run(args):
     return 0
 
 
+def run_batched(args):
+    """The many-filter workload: 512 independent linear-Gaussian filters (d = 16, dy = 4,
+    split d1 in {1, 2, 4, 8}, N ~ U[1024, 65536], M in {16, 32, 64, 128, 256}, L = 8, FP32),
+    T = args.steps steps in one graph-captured run after autotuning; then the batched
+    launch against the same filters stepped one at a time on a subset."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    F = args.filters
+    d1s = [int(v) for v in rng.choice([1, 2, 4, 8], F)]
+    Ns = [int(v) for v in rng.integers(1024, 65537, F)]
+    Ms = [int(v) for v in rng.choice([16, 32, 64, 128, 256], F)]
+    L, T = 8, args.steps
+    free, _ = torch.cuda.mem_get_info()
+    need = sum(n * m * (16 - d + 1) * 4 * 2 for n, m, d in zip(Ns, Ms, d1s)) * 1.15
+    scale = 1.0
+    if need > 0.9 * free:  # run a proportional share of the filters (stated in the output)
+        scale = 0.9 * free / need
+        F = max(1, int(F * scale))
+        d1s, Ns, Ms = d1s[:F], Ns[:F], Ms[:F]
+    specs = [workloads.make_model("lg16", 1000 + f, d1=d1s[f]) for f in range(F)]
+    models = [dpf.Model.from_spec(sp, dpf.DPF_F32) for sp in specs]
+    ys = np.stack([workloads.simulate(sp, T + args.warmup, 5 + f)[1] for f, sp in enumerate(specs)],
+                  axis=1).astype(np.float32)
+    yd = torch.tensor(ys, device="cuda")
+    stream = torch.cuda.Stream()
+    b = dpf.Batch(models, d1s, Ns, Ms, L, list(range(F)), stream=stream)
+    b.run_device(yd.data_ptr(), args.warmup, graph=True)
+    t0 = time.perf_counter()
+    report = b.autotune(reps=2)  # on the live state after the warm-up steps
+    tune_s = time.perf_counter() - t0
+    upd = sum(n * m for n, m in zip(Ns, Ms))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.run_device(yd[args.warmup:].data_ptr(), T, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = upd * T / (ms / 1e3)
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    # the batched launch against the same filters stepped one at a time (subset)
+    S = min(32, F)
+    sub = list(range(S))
+    bs = dpf.Batch([models[f] for f in sub], [d1s[f] for f in sub], [Ns[f] for f in sub],
+                   [Ms[f] for f in sub], L, sub, stream=stream)
+    singles = [dpf.Filter(models[f], d1s[f], 16 - d1s[f], Ns[f], Ms[f], L, f, stream=stream) for f in sub]
+    ysub = yd[:, :S].contiguous()
+    steps_sub, w_sub = 10, 2
+
+    def time_batch(bt):
+        bt.run_device(ysub.data_ptr(), w_sub, graph=True)
+        bt.autotune(reps=2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bt.run_device(ysub[w_sub:].data_ptr(), steps_sub, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms_b = time_batch(bs)
+    for k in range(w_sub):
+        for q, f in enumerate(sub):
+            singles[q].step_device(ysub[k, q].data_ptr())
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(w_sub, w_sub + steps_sub):
+        for q, f in enumerate(sub):
+            singles[q].step_device(ysub[k, q].data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    for s_ in singles:
+        s_.close()
+    bs.close()
+    # the same shapes when every filter is a decomposition of one system: the model
+    # constants are then shared by a class and reach the kernel as a launch parameter
+    same = [dpf.Model.from_spec(workloads.make_model("lg16", 0, d1=d1s[f]), dpf.DPF_F32) for f in sub]
+    bo = dpf.Batch(same, [d1s[f] for f in sub], [Ns[f] for f in sub], [Ms[f] for f in sub], L, sub,
+                   stream=stream)
+    ms_o = time_batch(bo)
+    bo.close()
+    upd_sub = sum(Ns[f] * Ms[f] for f in sub) * steps_sub
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": T,
+        "warmup": args.warmup, "ms_per_step": ms / T, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {F} linear-Gaussian filters (d=16, dy=4, d1 in {{1,2,4,8}}, "
+                               f"N~U[1024,65536], M in {{16..256}}, L={L}), one graph per run",
+                   "filters": F, "share_of_512": F / 512, "particles_per_step": upd,
+                   "l2": "state far larger than L2; no flush"},
+        "autotune": report, "autotune_s": tune_s,
+        "vs_one_by_one": {"filters": S, "steps": steps_sub, "batched_updates_per_s": upd_sub / (ms_b / 1e3),
+                          "one_by_one_updates_per_s": upd_sub / (ms_s / 1e3), "speedup": ms_s / ms_b,
+                          "one_system_batched_updates_per_s": upd_sub / (ms_o / 1e3)},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,11 +437,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched"],
+                    help="the headline single-filter workload, or the many-filter one")
+    ap.add_argument("--filters", type=int, default=512, help="filters of the batched workload")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run(args)
 
 

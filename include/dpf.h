@@ -244,7 +244,9 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
 
 /* Time the launch-shape candidates of every class on the live state (reps
  * launches each, without advancing the filters) and keep the fastest; a JSON
- * report of the choices is written to report (report_bytes, may be NULL). */
+ * report of the choices is written to report (report_bytes, may be NULL).
+ * DPF_E_INVALID before the first step: that step has no inner update, so its
+ * launches would not time the steady-state kernel. */
 dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t report_bytes);
 
 /* Borrow filter f's context (for dpf_read, dpf_diag); owned by the batch. */

@@ -1,9 +1,11 @@
 // Batched form: many independent filters (different N, M, models and x/z
 // splits) stepped together. Filters of one (precision, d1, d2, dy, PPL,
 // x-kind) class share one persistent launch of the warp-per-group kernel; the
-// per-filter outer stages run concurrently on side streams. A whole run of T
-// steps can be captured as one CUDA graph. The launch shape of each class is
-// chosen by a small autotuner that times the candidates on the live state.
+// outer reductions of all filters of one variant share one launch, and the
+// outer resamplings of all filters one more, so a step is a fixed, small
+// number of launches whatever the number of filters. A whole run of T steps
+// can be captured as one CUDA graph. The launch shape of each class is chosen
+// by a small autotuner that times the candidates on the live state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,8 +32,20 @@ struct BatchClass {
   size_t desc_bytes = 0;         // one set
   int ring = 0;                  // sets in the ring
   BatchLaunch launch{};
+  std::vector<unsigned char> shared_mc;  // the constants, when all members share them
   int occ = 0;                   // CTAs per SM at this launch shape
   double tuned_us = 0.0;
+};
+
+// The filters of one variant, whose outer reductions share a launch.
+struct OuterGroup {
+  const Variant* var = nullptr;
+  std::vector<int> members;      // filter indices
+  int nblocks = 0;               // blocks of the launch: the members' reduction blocks
+  int* d_bstart = nullptr;       // prefix of the members' block counts
+  void* d_oargs = nullptr;       // a ring of argument sets, one OuterArgs per member
+  size_t set_bytes = 0;
+  const void* cur = nullptr;     // the set the next launch reads
 };
 
 }  // namespace dpf
@@ -42,8 +56,13 @@ struct dpf_batch {
   cudaStream_t stream = nullptr;
   std::vector<dpf_ctx*> ctx;
   std::vector<dpf::BatchClass> cls;
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> ev;
+  std::vector<dpf::OuterGroup> og;
+  int* d_tstart = nullptr;      // prefix of the filters' resampling tile counts
+  int ntiles = 0;
+  void* d_gargs = nullptr;      // a ring of sets of F resampling arguments
+  size_t gset_bytes = 0;
+  const void* gcur = nullptr;
+  int oring = 0;                // sets in the outer-argument rings
   void* yhist = nullptr;  // [2][F][dy]: slot t % 2 holds y_t
   long long t = 0;
   int nsm = 0;
@@ -76,6 +95,7 @@ static dpf_status shape_class(dpf_batch& b, BatchClass& c) {
   c.launch.F = (int)c.members.size();
   c.launch.fstart = c.d_fstart;
   c.launch.mcs = c.d_mcs;
+  c.launch.mc_shared = c.shared_mc.empty() ? nullptr : c.shared_mc.data();
   int occ = 0;
   dpf_status st = c.var->batch_launch(c.launch, nullptr, &occ);
   if (st) return st;
@@ -109,8 +129,48 @@ static dpf_status upload_descs(dpf_batch& b, const void* y_prev_rows, const void
   return DPF_OK;
 }
 
+// Arguments of the outer stages that follow the coming step, one set per step
+// from `slot` on (counters advanced as the launches will consume them).
+static void fill_outer(dpf_batch& b, double* means_dev, double* logz_dev,
+                       std::vector<std::vector<unsigned char>>& oh, std::vector<unsigned char>& gh,
+                       size_t k) {
+  for (size_t gi = 0; gi < b.og.size(); ++gi) {
+    OuterGroup& g = b.og[gi];
+    for (size_t q = 0; q < g.members.size(); ++q) {
+      const int f = g.members[q];
+      g.var->outer_args(*b.ctx[f], means_dev ? means_dev + (size_t)f * b.d : nullptr,
+                        logz_dev ? logz_dev + f : nullptr,
+                        oh[gi].data() + k * g.set_bytes + q * g.var->oargs_size,
+                        gh.data() + k * b.gset_bytes + (size_t)f * g.var->gargs_size);
+    }
+  }
+}
+
+static dpf_status upload_outer(dpf_batch& b, std::vector<std::vector<unsigned char>>& oh,
+                               std::vector<unsigned char>& gh, int slot, size_t nsets, cudaStream_t s) {
+  for (size_t gi = 0; gi < b.og.size(); ++gi) {
+    OuterGroup& g = b.og[gi];
+    char* dst = (char*)g.d_oargs + (size_t)slot * g.set_bytes;
+    cudaError_t e = cudaMemcpyAsync(dst, oh[gi].data(), g.set_bytes * nsets, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "batch: outer argument upload");
+    g.cur = dst;
+  }
+  char* dst = (char*)b.d_gargs + (size_t)slot * b.gset_bytes;
+  cudaError_t e = cudaMemcpyAsync(dst, gh.data(), b.gset_bytes * nsets, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "batch: resampling argument upload");
+  b.gcur = dst;
+  return DPF_OK;
+}
+
+static void outer_host_sets(dpf_batch& b, size_t nsets, std::vector<std::vector<unsigned char>>& oh,
+                            std::vector<unsigned char>& gh) {
+  oh.resize(b.og.size());
+  for (size_t gi = 0; gi < b.og.size(); ++gi) oh[gi].assign(b.og[gi].set_bytes * nsets, 0);
+  gh.assign(b.gset_bytes * nsets, 0);
+}
+
 // One batched step whose descriptors are already in place.
-static dpf_status step_launch(dpf_batch& b, double* means_dev, double* logz_dev) {
+static dpf_status step_launch(dpf_batch& b) {
   if (b.profiling) {
     if (b.pev_used + 2 > b.pev.size())
       for (int q = 0; q < 64; ++q) {
@@ -128,21 +188,13 @@ static dpf_status step_launch(dpf_batch& b, double* means_dev, double* logz_dev)
     cudaEventRecord(b.pev[b.pev_used + 1], b.stream);
     b.pev_used += 2;
   }
-  // the outer stages of the filters are independent: spread them over side streams
-  const int S = (int)b.side.size();
-  cudaEventRecord(b.ev[0], b.stream);
-  for (int q = 0; q < S; ++q) cudaStreamWaitEvent(b.side[q], b.ev[0], 0);
-  for (int f = 0; f < b.F; ++f) {
-    dpf_ctx& x = *b.ctx[f];
-    dpf_status st = x.var->outer(x, means_dev ? means_dev + (size_t)f * b.d : nullptr,
-                                 logz_dev ? logz_dev + f : nullptr, b.side[f % S]);
+  for (OuterGroup& g : b.og) {
+    dpf_status st = g.var->outer_batch(g.cur, g.d_bstart, g.nblocks, (int)g.members.size(), b.stream);
     if (st) return st;
-    x.t += 1;
   }
-  for (int q = 0; q < S; ++q) {
-    cudaEventRecord(b.ev[1 + q], b.side[q]);
-    cudaStreamWaitEvent(b.stream, b.ev[1 + q], 0);
-  }
+  dpf_status st = b.og[0].var->scan_batch(b.gcur, b.d_tstart, b.ntiles, b.F, b.stream);
+  if (st) return st;
+  for (int f = 0; f < b.F; ++f) b.ctx[f]->t += 1;
   b.t += 1;
   return cuda_error(cudaGetLastError(), "batch step");
 }
@@ -219,25 +271,54 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
     std::vector<unsigned char> mcs(c.var->const_size * nf);
     for (size_t q = 0; q < nf; ++q)
       memcpy(mcs.data() + q * c.var->const_size, b->ctx[c.members[q]]->mconst.data(), c.var->const_size);
+    bool same = true;
+    for (size_t q = 1; q < nf; ++q)
+      same &= memcmp(mcs.data(), mcs.data() + q * c.var->const_size, c.var->const_size) == 0;
+    if (same) c.shared_mc.assign(mcs.begin(), mcs.begin() + c.var->const_size);
     cudaMemcpy(c.d_fstart, c.fstart.data(), sizeof(long long) * (nf + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(c.d_mcs, mcs.data(), mcs.size(), cudaMemcpyHostToDevice);
     dpf_status st = shape_class(*b, c);
     if (st) return fail(st);
   }
   if (balloc(*b, &b->yhist, 2 * (size_t)F * b->dy * b->s)) return fail(DPF_E_NOMEM);
-  const int S = std::min(8, F);
-  for (int q = 0; q < S; ++q) {
-    cudaStream_t sq;
-    if (cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking) != cudaSuccess)
-      return fail(cuda_error(cudaGetLastError(), "dpf_batch_create: stream"));
-    b->side.push_back(sq);
+  // outer groups: one per variant
+  std::map<const Variant*, int> var2g;
+  for (int f = 0; f < F; ++f) {
+    auto it = var2g.find(b->ctx[f]->var);
+    if (it == var2g.end()) {
+      OuterGroup g;
+      g.var = b->ctx[f]->var;
+      b->og.push_back(g);
+      it = var2g.emplace(b->ctx[f]->var, (int)b->og.size() - 1).first;
+    }
+    b->og[it->second].members.push_back(f);
   }
-  for (int q = 0; q < S + 1; ++q) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return fail(cuda_error(cudaGetLastError(), "dpf_batch_create: event"));
-    b->ev.push_back(e);
+  b->oring = 2;
+  for (OuterGroup& g : b->og) {
+    std::vector<int> bs(1, 0);
+    for (int f : g.members) bs.push_back(bs.back() + b->ctx[f]->n_red_blocks);
+    g.nblocks = bs.back();
+    g.set_bytes = g.var->oargs_size * g.members.size();
+    if (balloc(*b, (void**)&g.d_bstart, sizeof(int) * bs.size()) ||
+        balloc(*b, &g.d_oargs, g.set_bytes * b->oring))
+      return fail(DPF_E_NOMEM);
+    cudaMemcpy(g.d_bstart, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
+    g.cur = g.d_oargs;
   }
+  std::vector<int> ts(1, 0);
+  for (int f = 0; f < F; ++f) {
+    const long long tiles = (b->ctx[f]->N + SCAN_TILE - 1) / SCAN_TILE;
+    if (ts.back() + tiles > (long long)INT32_MAX)
+      return fail(set_error(DPF_E_UNSUPPORTED, "dpf_batch_create: too many outer particles in all"));
+    ts.push_back(ts.back() + (int)tiles);
+  }
+  b->ntiles = ts.back();
+  b->gset_bytes = b->og[0].var->gargs_size * (size_t)F;
+  if (balloc(*b, (void**)&b->d_tstart, sizeof(int) * ts.size()) ||
+      balloc(*b, &b->d_gargs, b->gset_bytes * b->oring))
+    return fail(DPF_E_NOMEM);
+  cudaMemcpy(b->d_tstart, ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice);
+  b->gcur = b->d_gargs;
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "dpf_batch_create"));
   *out = b;
@@ -255,7 +336,13 @@ dpf_status dpf_batch_step(dpf_batch* b, const void* y_dev, double* means_dev, do
   if (e != cudaSuccess) return cuda_error(e, "dpf_batch_step: y copy");
   dpf_status st = upload_descs(*b, prev, cur, (int)(t % 2), b->stream);
   if (st) return st;
-  return step_launch(*b, means_dev, logz_dev);
+  std::vector<std::vector<unsigned char>> oh;
+  std::vector<unsigned char> gh;
+  outer_host_sets(*b, 1, oh, gh);
+  fill_outer(*b, means_dev, logz_dev, oh, gh, 0);
+  st = upload_outer(*b, oh, gh, (int)(t % 2), 1, b->stream);
+  if (st) return st;
+  return step_launch(*b);
 }
 
 dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* means_dev,
@@ -273,12 +360,21 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
       c.ring = (int)T;
     }
   }
+  if (b->oring < T) {
+    for (OuterGroup& g : b->og)
+      if (balloc(*b, &g.d_oargs, g.set_bytes * (size_t)T)) return set_error(DPF_E_NOMEM, "dpf_batch_run");
+    if (balloc(*b, &b->d_gargs, b->gset_bytes * (size_t)T)) return set_error(DPF_E_NOMEM, "dpf_batch_run");
+    b->oring = (int)T;
+  }
   const long long t0 = b->t;
   std::vector<long long> ctx_t(b->F);
   for (int f = 0; f < b->F; ++f) ctx_t[f] = b->ctx[f]->t;
   // descriptors: build them step by step with the host-side counters advanced as the run will
   std::vector<std::vector<unsigned char>> sets(b->cls.size());
   for (size_t ci = 0; ci < b->cls.size(); ++ci) sets[ci].resize(b->cls[ci].desc_bytes * (size_t)T);
+  std::vector<std::vector<unsigned char>> oh;
+  std::vector<unsigned char> gh;
+  outer_host_sets(*b, (size_t)T, oh, gh);
   for (long long k = 0; k < T; ++k) {
     const long long t = t0 + k + 1;
     const char* cur = (const char*)ys_dev + (size_t)k * rows;
@@ -292,9 +388,15 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
                           c.xz, sets[ci].data() + (size_t)k * c.desc_bytes + q * c.var->args_size);
       }
     }
+    fill_outer(*b, means_dev ? means_dev + (size_t)k * b->F * b->d : nullptr,
+               logz_dev ? logz_dev + (size_t)k * b->F : nullptr, oh, gh, (size_t)k);
     for (int f = 0; f < b->F; ++f) b->ctx[f]->t += 1;
   }
   for (int f = 0; f < b->F; ++f) b->ctx[f]->t = ctx_t[f];
+  {
+    dpf_status so = upload_outer(*b, oh, gh, 0, (size_t)T, b->stream);
+    if (so) return so;
+  }
   for (size_t ci = 0; ci < b->cls.size(); ++ci) {
     cudaError_t e = cudaMemcpyAsync(b->cls[ci].d_descs, sets[ci].data(), sets[ci].size(),
                                     cudaMemcpyHostToDevice, b->stream);
@@ -317,8 +419,9 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
   dpf_status st = DPF_OK;
   for (long long k = 0; k < T && !st; ++k) {
     for (BatchClass& c : b->cls) c.launch.descs = (char*)c.d_descs + (size_t)k * c.desc_bytes;
-    st = step_launch(*b, means_dev ? means_dev + (size_t)k * b->F * b->d : nullptr,
-                     logz_dev ? logz_dev + (size_t)k * b->F : nullptr);
+    for (OuterGroup& g : b->og) g.cur = (const char*)g.d_oargs + (size_t)k * g.set_bytes;
+    b->gcur = (const char*)b->d_gargs + (size_t)k * b->gset_bytes;
+    st = step_launch(*b);
   }
   // the last observation becomes y_{t-1} of a later dpf_batch_step
   if (!st) {
@@ -365,6 +468,9 @@ dpf_status dpf_batch_sync(dpf_batch* b) {
 dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t report_bytes) {
   clear_error();
   if (!b || reps < 1) return set_error(DPF_E_INVALID, "dpf_batch_autotune: bad arguments");
+  if (b->t < 1)
+    return set_error(DPF_E_INVALID,
+                     "dpf_batch_autotune: step the batch once first (the first step has no inner update)");
   // candidates per class: the smallest inner-particles-per-lane that fits M, and twice
   // that (more instruction-level parallelism per lane, fewer lanes busy); each is timed
   // on the live state with the next step's arguments, which only rewrites the outputs
@@ -474,11 +580,6 @@ dpf_status dpf_batch_profile_read(dpf_batch* b, double* ms, int64_t* launches) {
 void dpf_batch_destroy(dpf_batch* b) {
   if (!b) return;
   if (b->stream || !b->ctx.empty()) cudaStreamSynchronize(b->stream);
-  for (cudaStream_t s : b->side) {
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-  }
-  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   for (cudaEvent_t e : b->pev) cudaEventDestroy(e);
   for (dpf_ctx* x : b->ctx) dpf_destroy(x);
   for (void* p : b->allocs) cudaFree(p);

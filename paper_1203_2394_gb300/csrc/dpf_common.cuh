@@ -222,6 +222,20 @@ __device__ __forceinline__ uint32_t block_incl_scan_u32(uint32_t v, uint32_t* re
 //   out[k] = min{ i : cum_i * n_out * 2^b > (k 2^b + u_b) C },
 // with b = 16, u_b = u >> 16 for n_out > 1 and b = 32, u_b = u for one draw.
 // ---------------------------------------------------------------------------
+// Segment of item b under the prefix table start[0..F] (start[0] = 0, start[F] =
+// total): the largest f with start[f] <= b, which skips empty segments.
+__device__ __forceinline__ int find_segment(const int* __restrict__ start, int F, int b) {
+  int lo = 0, hi = F - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 __host__ __device__ __forceinline__ int ceil_log2_i(long long n) {
   int b = 0;
   while ((1ll << b) < n) ++b;

@@ -64,6 +64,7 @@ using Ctx = ::dpf_ctx;
 // One batched launch: the filters of one (variant, PPL, x-kind) class.
 struct BatchLaunch {
   const void* mcs;          // device: the class's model constants, one block per filter
+  const void* mc_shared;    // host: the constants when every filter of the class shares them, else null
   const void* descs;        // device: the class's per-filter launch arguments
   const long long* fstart;  // device: F + 1 cumulative group counts
   int F;
@@ -76,12 +77,21 @@ struct BatchLaunch {
 };
 
 // Per-variant launchers, one set per compiled (precision, d1, d2, dy).
+// Tiles of the decoupled look-back scan of the global resampling.
+constexpr int SCAN_NT = 256;   // threads per scan tile
+constexpr int SCAN_IPT = 8;    // items per thread
+constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
+
 struct Variant {
   int prec, d1, d2, dy;
   dpf_status (*make_const)(const HostModel&, std::vector<unsigned char>&);
   dpf_status (*init)(Ctx&);
   dpf_status (*step)(Ctx&, int profile_slot);
   dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out, cudaStream_t s);
+  // the outer stage in parts, for many filters at once
+  void (*outer_args)(Ctx&, double* mean_out, double* logz_out, void* oargs, void* gargs);
+  dpf_status (*outer_batch)(const void* oargs, const int* bstart, int nblocks, int F, cudaStream_t s);
+  dpf_status (*scan_batch)(const void* gargs, const int* tstart, int ntiles, int F, cudaStream_t s);
   size_t (*step_smem)(int M, int L, bool xz, int nt);
   int (*xpad)();
   void (*batch_args)(Ctx&, const void* y_prev, const void* y_cur, bool xz, void* out);
@@ -89,7 +99,7 @@ struct Variant {
   dpf_status (*batch_launch)(const BatchLaunch&, cudaStream_t, int* occ);
   bool (*use_xz)(const Ctx&);
   int (*ppl_for)(int M);
-  size_t args_size, const_size;
+  size_t args_size, const_size, oargs_size, gargs_size;
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
 

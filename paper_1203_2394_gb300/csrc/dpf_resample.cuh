@@ -11,9 +11,6 @@
 
 namespace dpf {
 
-constexpr int SCAN_NT = 256;   // threads per scan tile
-constexpr int SCAN_IPT = 8;    // items per thread
-constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 constexpr int SPIN_LIMIT = 1 << 22;  // bounded look-back wait (~0.3 s with the back-off)
 
 typedef unsigned __int128 u128;
@@ -76,8 +73,9 @@ __device__ __forceinline__ unsigned long long quantize_u64(double W, int shift) 
   return (unsigned long long)floor(ldexp(W, shift));
 }
 
+// One tile of the `ntiles` tiles of one resampling, the tile taken by ticket.
 template <typename T, bool FROM_LOG>
-__global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) {
+__device__ __forceinline__ void global_scan_scatter_body(const GlobalArgs<T>& a, long long ntiles) {
   __shared__ unsigned long long cum[SCAN_TILE];
   __shared__ unsigned long long wsum[SCAN_NT / 32];
   __shared__ unsigned long long s_prefix;
@@ -87,7 +85,7 @@ __global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) 
 
   if (tid == 0) {
     const unsigned long long tk = atomicAdd(a.st.ticket, 1ull) - a.ticket_base;
-    s_tile = tk < (unsigned long long)gridDim.x ? (long long)tk : -1;
+    s_tile = tk < (unsigned long long)ntiles ? (long long)tk : -1;
     if (s_tile < 0) atomicOr(a.err, ERR_BOUNDS);
   }
   __syncthreads();
@@ -220,6 +218,25 @@ __global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) 
     }
     a.out[k] = (int32_t)(base + lo);
   }
+}
+
+template <typename T, bool FROM_LOG>
+__global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) {
+  global_scan_scatter_body<T, FROM_LOG>(a, gridDim.x);
+}
+
+// The outer resamplings of many filters in one launch: blocks tstart[f] ..
+// tstart[f+1]-1 serve filter f, each taking its tile from that filter's ticket
+// counter (so a tile's predecessor is always held by a block already running).
+template <typename T>
+__global__ void __launch_bounds__(SCAN_NT)
+    global_scan_scatter_batch(const GlobalArgs<T>* __restrict__ args, const int* __restrict__ tstart, int F) {
+  __shared__ int s_f;
+  if (threadIdx.x == 0) s_f = find_segment(tstart, F, (int)blockIdx.x);
+  __syncthreads();
+  const int f = s_f;
+  const GlobalArgs<T> a = args[f];
+  global_scan_scatter_body<T, true>(a, tstart[f + 1] - tstart[f]);
 }
 
 }  // namespace dpf

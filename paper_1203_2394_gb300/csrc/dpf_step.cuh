@@ -951,7 +951,7 @@ struct OuterArgs {
   T* lwmax_t;
   unsigned long long* Csum;
   unsigned int* done;
-  double* partials;  // gridDim.x x (4 + d)
+  double* partials;  // one row of 2 + d sums per reducing block
   double* stats;     // [logZ_total, logZ_step, ess, s1, mean[d]]
   const int* perm;   // device, d
   double* mean_out;  // optional device outputs
@@ -961,8 +961,9 @@ struct OuterArgs {
 
 constexpr int RED_NT = 256;
 
+// Block `bid` of the `nb` blocks that reduce one filter.
 template <typename T, int D1, int D2>
-__global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
+__device__ __forceinline__ void outer_reduce_body(const OuterArgs<T>& a, int bid, int nb) {
   constexpr int D = D1 + D2, NV = 2 + D;  // sum W, sum W^2, sum W * mean pieces
   __shared__ double sh[NV][RED_NT / 32];
   __shared__ bool last;
@@ -976,7 +977,7 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = T(0);
   unsigned long long cc = 0;
-  for (long long i = blockIdx.x * (long long)RED_NT + tid; i < a.N; i += (long long)gridDim.x * RED_NT) {
+  for (long long i = bid * (long long)RED_NT + tid; i < a.N; i += (long long)nb * RED_NT) {
     const T W = exp_t<T>(a.lw[i] - lwmax);
     cc += (unsigned long long)floor(W * sS);  // exact: a power-of-two scaling, then a floor
     v[0] += W;
@@ -1000,11 +1001,11 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < RED_NT / 32; ++q) s += sh[tid][q];
-    a.partials[(long long)blockIdx.x * NV + tid] = s;
+    a.partials[(long long)bid * NV + tid] = s;
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) last = (atomicAdd(a.done, 1u) == gridDim.x - 1);
+  if (tid == 0) last = (atomicAdd(a.done, 1u) == (unsigned)nb - 1u);
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -1012,7 +1013,7 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
   double vd[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) vd[q] = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += RED_NT) {
+  for (int b = tid; b < nb; b += RED_NT) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) vd[q] += a.partials[(long long)b * NV + q];
   }
@@ -1048,6 +1049,24 @@ __global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
     *a.lwmax_key = 0ull;
     *a.done = 0u;
   }
+}
+
+template <typename T, int D1, int D2>
+__global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
+  outer_reduce_body<T, D1, D2>(a, blockIdx.x, gridDim.x);
+}
+
+// The outer reductions of many filters in one launch: blocks bstart[f] ..
+// bstart[f+1]-1 reduce filter f, exactly as the single launch above would.
+template <typename T, int D1, int D2>
+__global__ void __launch_bounds__(RED_NT)
+    outer_reduce_batch_kernel(const OuterArgs<T>* __restrict__ args, const int* __restrict__ bstart, int F) {
+  __shared__ int s_f;
+  if (threadIdx.x == 0) s_f = find_segment(bstart, F, (int)blockIdx.x);
+  __syncthreads();
+  const int f = s_f;
+  const OuterArgs<T> a = args[f];
+  outer_reduce_body<T, D1, D2>(a, (int)blockIdx.x - bstart[f], bstart[f + 1] - bstart[f]);
 }
 
 }  // namespace dpf

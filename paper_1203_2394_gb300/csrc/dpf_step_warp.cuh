@@ -21,6 +21,12 @@ namespace dpf {
 
 constexpr int WARPS_PER_CTA = 4;
 
+// CTAs per SM the register allocation aims for: 4 (128 registers a thread)
+// unless a lane holds many coordinates of many particles, where 2 (255) avoids
+// spilling them.
+template <int PPL, int D2>
+constexpr int warp_min_blocks() { return PPL * D2 >= 48 ? 2 : 4; }
+
 // Philox4x32-10 with the round keys precomputed (they are kernel-uniform).
 struct RoundKeys {
   uint32_t k0[10], k1[10];
@@ -44,21 +50,25 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys& rk) {
   }
   return c;
 }
+// Normals 4b .. 4b+n-1 (n <= 4) of the draw (t, i, purpose, sub): one Philox
+// block, Box-Muller on its first pair and, when needed, its second.
+template <typename T>
+__device__ __forceinline__ void normal_block_rk(const RoundKeys& rk, uint32_t t, uint32_t i,
+                                                uint32_t purpose, uint32_t sub, int b, int n, T (&out)[4]) {
+  const uint4 w = philox_rk(ctr(t, i, purpose, sub, (uint32_t)b), rk);
+  box_muller(w.x, w.y, out[0], out[1]);
+  if (n > 2) box_muller(w.z, w.w, out[2], out[3]);
+}
 template <int N, typename T>
 __device__ __forceinline__ void normals_rk(const RoundKeys& rk, uint32_t t, uint32_t i,
                                            uint32_t purpose, uint32_t sub, T (&out)[N]) {
 #pragma unroll
   for (int b = 0; b < (N + 3) / 4; ++b) {
-    const uint4 w = philox_rk(ctr(t, i, purpose, sub, (uint32_t)b), rk);
-    T a0, a1, a2, a3;
-    box_muller(w.x, w.y, a0, a1);
-    if (4 * b + 0 < N) out[4 * b + 0] = a0;
-    if (4 * b + 1 < N) out[4 * b + 1] = a1;
-    if (4 * b + 2 < N) {
-      box_muller(w.z, w.w, a2, a3);
-      out[4 * b + 2] = a2;
-      if (4 * b + 3 < N) out[4 * b + 3] = a3;
-    }
+    T e[4];
+    normal_block_rk(rk, t, i, purpose, sub, b, N - 4 * b, e);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * b + j < N) out[4 * b + j] = e[j];
   }
 }
 
@@ -419,30 +429,42 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         }
       }
       if (a.dbg_b && act) vst<int, PPL>(a.dbg_b + i * M + k0, bidx);
-      T eps[D2][PPL];
+      // z_t = A_zz z_anc + (A_zx x + ...) + L_qz eps, column by column so that only
+      // one column of the ancestors' z, or one block of four normals a particle,
+      // is live beside the result; each row keeps its order of accumulation
 #pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        T e[D2];
-        normals_rk<D2>(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)(k0 + p), e);
-#pragma unroll
-        for (int c = 0; c < D2; ++c) eps[c][p] = e[c];
-      }
-      T zb[D2][PPL];
-#pragma unroll
-      for (int c = 0; c < D2; ++c)
-#pragma unroll
-        for (int p = 0; p < PPL; ++p) zb[c][p] = sz[c * M + bidx[p]];
-#pragma unroll
-      for (int r = 0; r < D2; ++r) {
+      for (int r = 0; r < D2; ++r)
 #pragma unroll
         for (int p = 0; p < PPL; ++p) zr[r][p] = azx[r];
 #pragma unroll
-        for (int c = 0; c < D2; ++c) axpy<T, PPL>(mc.Azz[r][c], zb[c], zr[r]);
-        if (mc.diag_qz) {
-          axpy<T, PPL>(mc.Lqz[r][r], eps[r], zr[r]);
-        } else {
+      for (int c = 0; c < D2; ++c) {
+        T zc[PPL];
 #pragma unroll
-          for (int c = 0; c <= r; ++c) axpy<T, PPL>(mc.Lqz[r][c], eps[c], zr[r]);
+        for (int p = 0; p < PPL; ++p) zc[p] = sz[c * M + bidx[p]];
+#pragma unroll
+        for (int r = 0; r < D2; ++r) axpy<T, PPL>(mc.Azz[r][c], zc, zr[r]);
+      }
+#pragma unroll
+      for (int b = 0; b < (D2 + 3) / 4; ++b) {
+        T e4[4][PPL];
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          T e[4];
+          normal_block_rk(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)(k0 + p), b, D2 - 4 * b, e);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) e4[j][p] = e[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = 4 * b + j;
+          if (c < D2) {
+            if (mc.diag_qz) {
+              axpy<T, PPL>(mc.Lqz[c][c], e4[j], zr[c]);
+            } else {
+#pragma unroll
+              for (int r = c; r < D2; ++r) axpy<T, PPL>(mc.Lqz[r][c], e4[j], zr[r]);
+            }
+          }
         }
       }
       T ell[PPL];
@@ -786,7 +808,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 
 
 template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>())
     step_warp_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc,
                      const __grid_constant__ StepArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -806,9 +828,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
 // Many filters of one (precision, d1, d2, dy, PPL) class in one persistent
 // launch: the class's groups are numbered filter after filter (fstart[f] is the
 // first item of filter f) and each warp steps a contiguous chunk of them.
-template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
-    step_warp_batch_kernel(const MC<T, D1, D2, DY>* __restrict__ mcs,
+// With SHARED every filter of the launch has the same model constants, passed
+// by value (read through the constant cache); otherwise they come from mcs[f].
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL, bool SHARED>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>())
+    step_warp_batch_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc1,
+                           const MC<T, D1, D2, DY>* __restrict__ mcs,
                            const StepArgs<T>* __restrict__ descs, const long long* __restrict__ fstart,
                            int F, long long chunk, uint32_t region) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -833,8 +858,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, 4)
   while (item < iend) {
     while (fstart[f + 1] <= item) ++f;
     const long long seg_end = iend < fstart[f + 1] ? iend : fstart[f + 1];
-    warp_run<T, D1, D2, DY, XZ, PPL>(mcs[f], descs[f], item - fstart[f], seg_end - fstart[f], 1,
-                                     ws, &bars[wib], phase);
+    warp_run<T, D1, D2, DY, XZ, PPL>(SHARED ? mc1 : mcs[f], descs[f], item - fstart[f],
+                                     seg_end - fstart[f], 1, ws, &bars[wib], phase);
     item = seg_end;
   }
 }

@@ -208,9 +208,9 @@ struct VariantImpl {
                : warp_geometry<T, D1, D2, DY, false>(M, L, nullptr)) / WARPS_PER_CTA;
   }
 
-  template <bool XZ, int PPL>
+  template <bool XZ, int PPL, bool SHARED>
   static dpf_status batch_kernel(const BatchLaunch& b, cudaStream_t s, int* occ) {
-    auto k = step_warp_batch_kernel<T, D1, D2, DY, XZ, PPL>;
+    auto k = step_warp_batch_kernel<T, D1, D2, DY, XZ, PPL, SHARED>;
     static bool attr_done = false;
     if (!attr_done) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -221,18 +221,25 @@ struct VariantImpl {
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, WARPS_PER_CTA * 32, b.smem);
       return cuda_error(e, "batch kernel occupancy");
     }
-    k<<<b.grid, WARPS_PER_CTA * 32, b.smem, s>>>((const Const*)b.mcs, (const StepArgs<T>*)b.descs,
+    Const mc1;
+    if (SHARED) memcpy(&mc1, b.mc_shared, sizeof(Const));
+    else memset(&mc1, 0, sizeof(Const));
+    k<<<b.grid, WARPS_PER_CTA * 32, b.smem, s>>>(mc1, (const Const*)b.mcs, (const StepArgs<T>*)b.descs,
                                                 b.fstart, b.F, b.chunk, b.region);
     return cuda_error(cudaGetLastError(), "batch step kernel launch");
   }
+  template <bool XZ, bool SHARED>
+  static dpf_status batch_ppl2(const BatchLaunch& b, cudaStream_t s, int* occ) {
+    switch (b.ppl) {
+      case 1: return batch_kernel<XZ, 1, SHARED>(b, s, occ);
+      case 2: return batch_kernel<XZ, 2, SHARED>(b, s, occ);
+      case 4: return batch_kernel<XZ, 4, SHARED>(b, s, occ);
+      default: return batch_kernel<XZ, 8, SHARED>(b, s, occ);
+    }
+  }
   template <bool XZ>
   static dpf_status batch_ppl(const BatchLaunch& b, cudaStream_t s, int* occ) {
-    switch (b.ppl) {
-      case 1: return batch_kernel<XZ, 1>(b, s, occ);
-      case 2: return batch_kernel<XZ, 2>(b, s, occ);
-      case 4: return batch_kernel<XZ, 4>(b, s, occ);
-      default: return batch_kernel<XZ, 8>(b, s, occ);
-    }
+    return b.mc_shared ? batch_ppl2<XZ, true>(b, s, occ) : batch_ppl2<XZ, false>(b, s, occ);
   }
   // Launch (occ == nullptr) or query the blocks per SM (occ != nullptr).
   static dpf_status batch_launch(const BatchLaunch& b, cudaStream_t s, int* occ) {
@@ -240,8 +247,12 @@ struct VariantImpl {
     else return b.xz ? batch_ppl<true>(b, s, occ) : batch_ppl<false>(b, s, occ);
   }
 
-  static dpf_status outer(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
-    OuterArgs<T> o{};
+  // Arguments of the outer stage that follows the coming step: the reduction (o)
+  // and the global resampling (g). Advances the context's scan epoch and ticket
+  // base, as the launches that use these arguments will consume them.
+  static void outer_args(Ctx& x, double* mean_out, double* logz_out, void* ov, void* gv) {
+    OuterArgs<T>& o = *(OuterArgs<T>*)ov;
+    o = OuterArgs<T>{};
     o.lw = (const T*)x.lw;
     o.xm = (const T*)x.xm;
     o.zm = (const T*)x.zm;
@@ -258,12 +269,10 @@ struct VariantImpl {
     o.mean_out = mean_out;
     o.logz_out = logz_out;
     o.err = x.err;
-    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, st>>>(o);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
     const long long t = x.t + 1;
     const long long tiles = (x.N + SCAN_TILE - 1) / SCAN_TILE;
-    GlobalArgs<T> g{};
+    GlobalArgs<T>& g = *(GlobalArgs<T>*)gv;
+    g = GlobalArgs<T>{};
     g.w = (const T*)x.lw;
     g.lwmax = (const T*)x.lwmax_t;
     g.w_out = (T*)x.wout;
@@ -280,8 +289,30 @@ struct VariantImpl {
     g.epoch = ++x.epoch;
     g.err = x.err;
     x.ticket_next += (unsigned long long)tiles;
-    global_scan_scatter<T, true><<<(unsigned)tiles, SCAN_NT, 0, st>>>(g);
+  }
+
+  static dpf_status outer(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
+    OuterArgs<T> o;
+    GlobalArgs<T> g;
+    outer_args(x, mean_out, logz_out, &o, &g);
+    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, st>>>(o);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
+    global_scan_scatter<T, true><<<(unsigned)((x.N + SCAN_TILE - 1) / SCAN_TILE), SCAN_NT, 0, st>>>(g);
     return cuda_error(cudaGetLastError(), "outer resample launch");
+  }
+
+  // The outer reductions of F filters of this variant in one launch (device
+  // arguments, bstart[F] blocks in all).
+  static dpf_status outer_batch(const void* oargs, const int* bstart, int nblocks, int F, cudaStream_t st) {
+    outer_reduce_batch_kernel<T, D1, D2><<<nblocks, RED_NT, 0, st>>>((const OuterArgs<T>*)oargs, bstart, F);
+    return cuda_error(cudaGetLastError(), "batched outer reduce launch");
+  }
+
+  // The outer resamplings of F filters of this precision in one launch.
+  static dpf_status scan_batch(const void* gargs, const int* tstart, int ntiles, int F, cudaStream_t st) {
+    global_scan_scatter_batch<T><<<ntiles, SCAN_NT, 0, st>>>((const GlobalArgs<T>*)gargs, tstart, F);
+    return cuda_error(cudaGetLastError(), "batched outer resample launch");
   }
 
   static Variant make(int prec) {
@@ -295,6 +326,11 @@ struct VariantImpl {
     v.init = &init;
     v.step = &step;
     v.outer = &outer;
+    v.outer_args = &outer_args;
+    v.outer_batch = &outer_batch;
+    v.scan_batch = &scan_batch;
+    v.oargs_size = sizeof(OuterArgs<T>);
+    v.gargs_size = sizeof(GlobalArgs<T>);
     v.step_smem = &smem;
     v.batch_args = &batch_args;
     v.region_bytes = &region_bytes;

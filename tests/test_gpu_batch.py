@@ -1,7 +1,8 @@
 """The batched form: many filters of mixed N, M and x/z split stepped together.
 
 * Every member reproduces, bit for bit, the single filter created with its seed
-  (same kernels, same random-number keys).
+  (same kernels, same random-number keys), whether the members of a launch read
+  their own model constants or share one set.
 * A graph-captured run equals step-by-step stepping.
 * Members of the d = 16 variants (splits 1/15 and 8/8, dy = 4) agree with the
   FP64 oracle, teacher-forced, within the FP32 tolerances.
@@ -25,9 +26,12 @@ MEMBERS = [  # (d1, N, M)
 L, T, SEED0 = 8, 5, 100
 
 
-def _models():
+def _models(one_system=False):
+    # one_system: every filter decomposes the same system, so the members of a class
+    # share their model constants (the launch-parameter path of the batched kernel)
     from paper_1203_2394_gb300 import dpf
-    specs = [workloads.make_model("lg16", 10 + f, d1=d1) for f, (d1, _, _) in enumerate(MEMBERS)]
+    specs = [workloads.make_model("lg16", 10 if one_system else 10 + f, d1=d1)
+             for f, (d1, _, _) in enumerate(MEMBERS)]
     return specs, [dpf.Model.from_spec(s, dpf.DPF_F32) for s in specs]
 
 
@@ -42,9 +46,10 @@ def _batch(models):
                      [m[2] for m in MEMBERS], L, [SEED0 + f for f in range(len(MEMBERS))])
 
 
-def test_members_equal_single_filters_bitwise():
+@pytest.mark.parametrize("one_system", [False, True])
+def test_members_equal_single_filters_bitwise(one_system):
     from paper_1203_2394_gb300 import dpf
-    specs, models = _models()
+    specs, models = _models(one_system)
     ys = _ys(specs).astype(np.float32)
     b = _batch(models)
     singles = [dpf.Filter(models[f], d1, 16 - d1, N, M, L, SEED0 + f)
@@ -117,13 +122,19 @@ def test_autotune_keeps_results_within_tolerance():
     ys = _ys(specs).astype(np.float32)
     yd = torch.tensor(ys, device="cuda")
     b = _batch(models)
+    with pytest.raises(dpf.DpfError):  # nothing to time before the first step
+        b.autotune(reps=1)
+    single = [dpf.Filter(models[f], d1, 16 - d1, N, M, L, SEED0 + f) for f, (d1, N, M) in enumerate(MEMBERS)]
+    b.step_device(yd[0].data_ptr())
+    for s, f in zip(single, range(len(MEMBERS))):
+        s.step(ys[0, f])
     report = b.autotune(reps=2)
     assert len(report["classes"]) >= 4
     for c in report["classes"]:
         assert c["chosen_ppl"] in [t["ppl"] for t in c["tried"]]
-    single = [dpf.Filter(models[f], d1, 16 - d1, N, M, L, SEED0 + f) for f, (d1, N, M) in enumerate(MEMBERS)]
-    b.step_device(yd[0].data_ptr())
+    b.step_device(yd[1].data_ptr())
     b.sync()
     for f, s in enumerate(single):
-        s.step(ys[0, f])
-        assert np.max(rel(b.filter(f).read("lw"), s.read("lw"))) <= 1e-5
+        s.step(ys[1, f])
+        for name in ("lw", "lwhat"):
+            assert np.max(rel(b.filter(f).read(name), s.read(name))) <= 1e-5, (name, f)
