@@ -40,6 +40,7 @@ typedef enum {
 enum { DPF_F32 = 0, DPF_F64 = 1 };          /* precision / dtype codes */
 enum { DPF_MODEL_CLG = 1 };                 /* conditionally linear-Gaussian family */
 enum { DPF_SYS_GLOBAL = 0, DPF_SYS_LOCAL = 1 }; /* resampling rules, see dpf_resample */
+enum { DPF_TC_TF32 = 0, DPF_TC_TF32X3 = 1, DPF_TC_BF16 = 2 }; /* tensor-core operand modes */
 
 typedef struct dpf_ctx dpf_ctx; /* opaque; created by dpf_create, freed by dpf_destroy */
 
@@ -180,6 +181,25 @@ dpf_status dpf_resample_noalloc(const void* w, int32_t dtype, int64_t n, const u
  */
 dpf_status dpf_box_muller(const uint32_t* words, int64_t n_pairs, int32_t dtype, void* out,
                           void* stream);
+
+/*
+ * The fifth-generation tensor-core product that the high-dimensional step
+ * (A z for a 56-dimensional z block) and the learned proposal build on, run
+ * alone: D = A B^T with FP32 accumulation. The paper has no counterpart; this
+ * exposes the building block so that it can be checked against a plain product.
+ *   mode DPF_TC_TF32:   A, B float; each operand rounded to TF32 once.
+ *   mode DPF_TC_TF32X3: A, B float; each operand split as hi = tf32(v),
+ *                       lo = tf32(v - hi) and D = A_lo B_hi + A_hi B_lo + A_hi B_hi
+ *                       (close to an FP32 product).
+ *   mode DPF_TC_BF16:   A, B bfloat16.
+ * A: M x K, B: N x K, D: M x N float, all row-major device buffers owned by the
+ * caller. M a multiple of 128; N a multiple of 16 in [16, 128]; K a multiple of
+ * 8 up to 64 (TF32 modes) or of 16 up to 128 (BF16). Other shapes:
+ * DPF_E_INVALID. Synchronises the stream; DPF_E_TIMEOUT if the MMAs did not
+ * complete within the kernel's bounded wait.
+ */
+dpf_status dpf_tc_matmul(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K,
+                         int32_t mode, void* stream);
 
 /* Diagnostics of the last step: outer effective sample size 1/sum W^2 (with
  * normalised W), the step counter t, and the last step's log p(y_t | y_1..t-1). */

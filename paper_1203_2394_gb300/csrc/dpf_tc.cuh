@@ -1,0 +1,151 @@
+// Fifth-generation tensor-core building blocks (tcgen05, sm_103a): shared-memory
+// matrix descriptors for the canonical K-major layout without swizzle, the
+// instruction descriptor, tensor-memory (TMEM) allocation, MMA issue, completion
+// on an mbarrier and TMEM loads. Everything is inline PTX.
+//
+// Operand layout used throughout (K-major, no swizzle): a tile of R rows and
+// K bytes per row is cut into core matrices of 8 rows x 16 bytes, each stored
+// as 128 contiguous bytes (row-major inside). Core matrices adjacent in K are
+// 128 bytes apart (the leading-dimension offset), 8-row groups are
+// (K / 16) * 128 bytes apart (the stride-dimension offset). One MMA consumes
+// 32 bytes of K (8 TF32 or 16 BF16 values): the next K step starts 256 bytes on.
+#pragma once
+
+#include "dpf_common.cuh"
+
+namespace dpf {
+namespace tc {
+
+// Operand element formats of the instruction descriptor.
+constexpr uint32_t FMT_F16 = 0, FMT_BF16 = 1, FMT_TF32 = 2;
+
+// Instruction descriptor: FP32 accumulator, A and B both of format `fmt` and
+// K-major, no negation, dense, tile M x N (M = 128 here: one TMEM lane a row).
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int m, int n) {
+  return (1u << 4)                          // accumulator FP32
+         | (fmt << 7) | (fmt << 10)         // A and B formats
+         | ((uint32_t)(n >> 3) << 17)       // N / 8
+         | ((uint32_t)(m >> 4) << 24);      // M / 16
+}
+
+// Byte offset of byte `kb` of row r in a K-major tile whose rows hold kc16
+// 16-byte chunks.
+__host__ __device__ constexpr uint32_t kmajor_offset(int r, int kb, int kc16) {
+  return (uint32_t)((r >> 3) * kc16 * 128 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
+// Shared-memory matrix descriptor of such a tile starting at shared address
+// `saddr` (16-byte aligned), for rows of kc16 chunks; no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int kc16) {
+  const uint32_t lbo = 128, sbo = (uint32_t)kc16 * 128;
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the fifth-generation tensor cores
+  return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// ---- tensor memory ----
+// Allocation and release are warp-wide (every lane of one warp calls them).
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Make this thread's generic-proxy shared-memory writes visible to the tensor
+// cores (async proxy); a barrier must follow before the MMA is issued.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---- MMA issue (one thread) ----
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// The mbarrier at `bar` receives one arrival when every MMA this thread issued
+// before has completed.
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`; false if it gave up.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  for (int s = 0; s < limit; ++s)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+// ---- TMEM loads: warp w reads lanes 32 (w % 4) .. +31, 16 consecutive
+// columns from `taddr` (lane in the high half-word, column in the low), one
+// row a thread; the load and its completion wait are one statement ----
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// ---- operand rounding ----
+// x rounded to TF32 (nearest, ties away from zero), as an FP32 bit pattern.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+// x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (the subtraction is exact).
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - hi);
+}
+
+}  // namespace tc
+}  // namespace dpf

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("dpf_resample", ctypes.c_int, [_P, _I32, _I64, _I64, _I32, _P, _P, _P]),
     ("dpf_resample_noalloc", ctypes.c_int, [_P, _I32, _I64, _P, _P, _P]),
     ("dpf_box_muller", ctypes.c_int, [_P, _I64, _I32, _P, _P]),
+    ("dpf_tc_matmul", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_set_debug", ctypes.c_int, [_P, _I32]),
@@ -323,3 +324,18 @@ def box_muller(words, dtype="float32", stream=None):
                                DPF_F32 if dtype == "float32" else DPF_F64, out.data_ptr(),
                                _stream_ptr(s)))
     return out
+
+
+DPF_TC_TF32, DPF_TC_TF32X3, DPF_TC_BF16 = 0, 1, 2
+
+
+def tc_matmul(A, B, mode=DPF_TC_TF32X3, stream=None):
+    """D = A B^T on the tensor cores (see ``dpf_tc_matmul``). A: (M, K), B: (N, K)
+    CUDA tensors, float32 (TF32 modes) or bfloat16 (DPF_TC_BF16); returns D (M, N) float32."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    check(lib().dpf_tc_matmul(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, int(mode), s))
+    return D
