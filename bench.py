@@ -430,6 +430,110 @@ def run_batched(args):
     return 0
 
 
+def run_highdim(args):
+    """The high-dimensional workload: growth_clg64 (x of dim 8 with the growth map, z of
+    dim 56 with a dense A_zz, dy = 8), F filters of N = 32768, M = 256, L = 16, FP32,
+    every filter's state resident; a step steps all F filters one after another on one
+    stream. Then the tensor-core propagation against the CUDA-core one on one filter."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    spec = workloads.make_model("growth_clg64", 0)
+    sz = spec.sizes
+    N, M, L = sz["N"], sz["M"], sz["L"]
+    K, W = args.steps, args.warmup
+    F = args.filters if args.filters else 64
+    free, _ = torch.cuda.mem_get_info()
+    per_filter = 2 * N * M * (spec.d2 + 1) * 4 + N * (16 * 64 + 2 * L * 40)
+    share = 1.0
+    if F * per_filter > 0.9 * free:  # a proportional share of the filters (stated in the output)
+        F2 = max(1, int(0.9 * free // per_filter))
+        share = F2 / F
+        F = F2
+    stream = torch.cuda.Stream()
+    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    filt = [dpf.Filter(model, spec.d1, spec.d2, N, M, L, seed=f, stream=stream) for f in range(F)]
+    ys = np.stack([workloads.simulate(spec, W + K + 1, 5 + f)[1] for f in range(F)], axis=1)
+    yd = torch.tensor(ys.astype(np.float32), device="cuda")  # (T, F, dy)
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            for f in range(F):
+                filt[f].step_device(yd[k, f].data_ptr())
+        for fl in filt:
+            fl.sync()
+            fl.profile(True)
+            fl.profile_read()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.monotonic()
+        e0.record(stream)
+        for k in range(W, W + K):
+            for f in range(F):
+                filt[f].step_device(yd[k, f].data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        w1 = time.monotonic()
+        ms = e0.elapsed_time(e1)
+        kms, kn = 0.0, 0
+        for fl in filt:
+            fl.sync()
+            a, b = fl.profile_read()
+            fl.profile(False)
+            kms, kn = kms + a, kn + b
+        clk = clocks.stop(window=(w0, w1))
+    value = F * N * M * K / (ms / 1e3)
+    # tensor cores against CUDA cores on filter 0 (same state, next steps)
+    cmp = {}
+    with torch.cuda.stream(stream):
+        for tc in (True, False):
+            f0 = filt[0]
+            f0.set_tensor_cores(tc)
+            f0.step_device(yd[W + K - 1, 0].data_ptr())  # settle the launch shape
+            f0.sync()
+            f0.profile(True)
+            f0.profile_read()
+            for r in range(3):
+                f0.step_device(yd[W + K - 1, 0].data_ptr())
+            f0.sync()
+            a, b = f0.profile_read()
+            f0.profile(False)
+            cmp["tensor_cores" if tc else "cuda_cores"] = a / max(1, b)
+        filt[0].set_tensor_cores(True)
+    for fl in filt:
+        fl.close()
+    peak, peak_kind = measured_peaks()
+    per = b_alg(spec.d1, spec.d2, M, 4)
+    kern_s = kms / 1e3 / max(1, kn)
+    achieved = per * N * M / kern_s / 1e9
+    mma_flop = 3 * 2 * N * M * 64 * spec.d2  # 3xTF32, A_zz padded to 64 rows
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"growth_clg64: growth-map x (d1=8), linear-Gaussian z (d2=56, dense A_zz), "
+                               f"dy=8, {F} filters of N={N}, M={M}, L={L}, FP32",
+                   "filters": F, "share_of_64": F / 64 if share == 1.0 else share,
+                   "l2": "state far larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "step_kernel_g (tensor-core)",
+                     "kernel_ms": kern_s * 1e3, "bytes_per_update": per,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "tensor": {"mma_tflops": mma_flop / kern_s / 1e12, "mma_flop_per_launch": mma_flop},
+        "propagation_kernel_ms": cmp,
+        "gpu_launches": 3 * K * F,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,16 +541,21 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched"],
-                    help="the headline single-filter workload, or the many-filter one")
-    ap.add_argument("--filters", type=int, default=512, help="filters of the batched workload")
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim"],
+                    help="the headline single-filter workload, the many-filter one, or the d2 = 56 one")
+    ap.add_argument("--filters", type=int, default=None,
+                    help="filters of the batched (default 512) or high-dimensional (default 64) workload")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
+        if args.filters is None:
+            args.filters = 512
         return run_batched(args)
+    if args.workload == "highdim":
+        return run_highdim(args)
     return run(args)
 
 

@@ -222,6 +222,12 @@ dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t byte
 /* Record per-step debug arrays ("bidx") when enable != 0. */
 dpf_status dpf_set_debug(dpf_ctx* ctx, int32_t enable);
 
+/* Choose the tensor-core propagation z_new = A_zz z (3xTF32 on tcgen05, the
+ * default) or the CUDA-core one, for variants that have both (FP32, d2 a
+ * multiple of 8 with constants too large for a launch parameter, M = 128 or
+ * 256; elsewhere the flag has no effect). Takes effect at the next step. */
+dpf_status dpf_set_tensor_cores(dpf_ctx* ctx, int32_t enable);
+
 /*
  * Time the main step kernel: when enable != 0, every later step brackets that
  * kernel with CUDA events on the context's stream; dpf_profile_read returns the

@@ -285,6 +285,17 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
                          std::to_string(model->precision) + ", " + std::to_string(d1) + ", " +
                          std::to_string(d2) + ", " + std::to_string(model->dy) + ")");
   }
+  if (x->hm.xz && !x->var->xz_supported) {
+    delete x;
+    return set_error(DPF_E_UNSUPPORTED,
+                     "dpf_create: this (d1, d2, dy) variant serves only models whose x transition is free of z");
+  }
+  if (M > x->var->max_m) {
+    const int mm = x->var->max_m;
+    delete x;
+    return set_error(DPF_E_UNSUPPORTED, "dpf_create: this (d1, d2, dy) variant accepts M <= " +
+                                            std::to_string(mm));
+  }
   x->ppt = M >= 64 ? 2 : 1;
   if (const char* e = getenv("DPF_PPT")) x->ppt = atoi(e) == 2 ? 2 : 1;
   const size_t sm = x->var->step_smem(M, L, x->hm.xz, ((M + x->ppt - 1) / x->ppt + 31) / 32 * 32);
@@ -460,6 +471,14 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, x->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
   return cuda_error(e, "dpf_read");
+}
+
+dpf_status dpf_set_tensor_cores(dpf_ctx* x, int32_t enable) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_set_tensor_cores: null context");
+  if (x->tensor_cores != (enable != 0)) x->grid_step = 0;  // the other kernel sizes its own grid
+  x->tensor_cores = enable != 0;
+  return DPF_OK;
 }
 
 dpf_status dpf_set_debug(dpf_ctx* x, int32_t enable) {

@@ -234,6 +234,8 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
     dpf_status st = dpf_create(models[f], d1[f], models[f]->d - d1[f], N[f], M[f], L, seeds[f], stream, &x);
     if (st) return fail(st);
     b->ctx.push_back(x);
+    if (!x->var->batch_launch)
+      return fail(set_error(DPF_E_UNSUPPORTED, "dpf_batch_create: this (d1, d2, dy) variant has no batched form"));
     const size_t sz = b->s;
     const int ppl = x->var->ppl_for(M[f]);
     if (!(M[f] <= 256 && M[f] % ppl == 0 && (M[f] * sz) % 16 == 0 && (L * sz) % 16 == 0 &&

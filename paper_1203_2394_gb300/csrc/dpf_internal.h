@@ -100,6 +100,9 @@ struct Variant {
   bool (*use_xz)(const Ctx&);
   int (*ppl_for)(int M);
   size_t args_size, const_size, oargs_size, gargs_size;
+  int max_m = 1024;       // largest M the variant's kernels accept
+  bool has_tc = false;    // has a tensor-core propagation (see dpf_set_tensor_cores)
+  bool xz_supported = true;  // serves models whose x transition depends on z
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
 
@@ -153,6 +156,8 @@ struct dpf_ctx {
   int ppt = 1;        // inner particles per thread of the step kernel
   int xp = 4;         // padded x row length (elements; 16-byte rows)
   int grid_step = 0;  // persistent grid of the step kernel (0 = not yet sized)
+  void* d_mconst = nullptr;  // the model constants in device memory (variants that read them there)
+  bool tensor_cores = true;  // tensor-core propagation where the variant has one
   // profiling of the main kernel
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // pairs bracketing the step kernel

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "dpf_common.cuh"
+#include "dpf_tc.cuh"
 #include "dpf_internal.h"
 #include "dpf_resample.cuh"
 
@@ -81,6 +82,7 @@ struct StepArgs {
   uint32_t stage_bytes, stage_tx;
   uint32_t off_stage, off_sz, off_slq, off_sx, off_slwh, off_sxbb;
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
+  uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
 };
 
 // Order-preserving unsigned keys of floating-point values (for atomicMax).
@@ -121,7 +123,8 @@ constexpr int rec_len() {
 // Shared-memory carve-up and row mapping of step_kernel, on the host: two
 // input stages (the source rows of a group), then the work buffers.
 template <typename T, int D1, int D2, int DY, bool XZ>
-inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = false) {
+inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = false,
+                            int nstages = 2, bool tc = false) {
   const int tpm = rows_tpm(nt, L);
   int stride = M;
   while (stride % 32 != tpm % 32) ++stride;
@@ -141,12 +144,18 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
     o += r16(bytes);
     return (uint32_t)at;
   };
-  const uint32_t st0 = take(2 * stage), cum = take(sizeof(uint32_t) * M),
+  const uint32_t st0 = take(nstages * stage), cum = take(sizeof(uint32_t) * M),
                  kd = take(sizeof(T) * rec_len<T, D1, DY, XZ>() * M),
                  E = take(sizeof(T) * (size_t)L * stride), xw = take(sizeof(T) * L * D1),
                  cw = take(sizeof(T) * L * DY), xbs = take(sizeof(T) * L * D1),
                  row = take(sizeof(T) * L * 5), red = take(sizeof(T) * 32 + sizeof(uint32_t) * 64),
                  part = take(sizeof(T) * 32 * (D2 + DY));
+  // tensor-core propagation: the ancestors' z as TF32 low parts (the high parts
+  // reuse the stage's z rows), and A_zz split in two, padded to 16-row multiples
+  const int np = (D2 + 15) / 16 * 16;
+  const uint32_t zlo = tc ? take(sizeof(float) * (size_t)M * D2) : 0u,
+                 ahi = tc ? take(sizeof(float) * (size_t)np * D2) : 0u,
+                 alo = tc ? take(sizeof(float) * (size_t)np * D2) : 0u;
   if (a) {
     a->tpm = tpm;
     a->rows = nt / tpm;
@@ -158,6 +167,7 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
     a->off_sxbb = sxbb;
     a->off_cum = cum; a->off_kd = kd; a->off_E = E; a->off_xw = xw;
     a->off_cw = cw; a->off_xbs = xbs; a->off_row = row; a->off_red = red; a->off_part = part;
+    a->off_zlo = zlo; a->off_ahi = ahi; a->off_alo = alo;
   }
   return o;
 }
@@ -229,8 +239,8 @@ __device__ __forceinline__ void h_x(const MC<T, D1, D2, DY>& mc, const T (&x)[D1
 // Initialisation (Fig. 4, "Initialize"): x_0 ~ N(m0x, P0xx), z_0 | x_0 from the
 // conditional Gaussian, lq = -log M. One CTA per outer particle.
 template <typename T, int D1, int D2, int DY>
-__global__ void init_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, T* z, T* lq, T* x,
-                            long long N, int M, int xp, Key key) {
+__device__ __forceinline__ void init_body(const MC<T, D1, D2, DY>& mc, T* z, T* lq, T* x, long long N,
+                                          int M, int xp, Key key) {
   const long long i = blockIdx.x;
   const int j = threadIdx.x;
   if (j >= M) return;
@@ -259,6 +269,19 @@ __global__ void init_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, T* z, 
 #pragma unroll
     for (int r = 0; r < xp; ++r) x[i * xp + r] = r < D1 ? xi[r < D1 ? r : 0] : T(0);
   }
+}
+
+template <typename T, int D1, int D2, int DY>
+__global__ void init_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, T* z, T* lq, T* x,
+                            long long N, int M, int xp, Key key) {
+  init_body<T, D1, D2, DY>(mc, z, lq, x, N, M, xp, key);
+}
+
+// The same with the model constants in global memory.
+template <typename T, int D1, int D2, int DY>
+__global__ void init_kernel_g(const MC<T, D1, D2, DY>* __restrict__ mcp, T* z, T* lq, T* x,
+                              long long N, int M, int xp, Key key) {
+  init_body<T, D1, D2, DY>(*mcp, z, lq, x, N, M, xp, key);
 }
 
 __device__ __forceinline__ float exp2_t(float x) { return ex2_approx(x); }
@@ -350,9 +373,15 @@ __device__ __forceinline__ void stage_group(const StepArgs<T>& a, unsigned char*
   }
 }
 
-template <typename T, int D1, int D2, int DY, bool XZ, int PPT, int MAXNT, bool BULK>
-__global__ void __launch_bounds__(MAXNT)
-    step_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, const __grid_constant__ StepArgs<T> a) {
+constexpr int TC_SPIN = 1 << 22;  // bounded wait for the tensor-core MMAs of one group
+
+// The block step. TC: the propagation A_zz z runs on the tensor cores (3xTF32,
+// FP32 only, one thread per inner particle, M a multiple of 128, one stage).
+template <typename T, int D1, int D2, int DY, bool XZ, int PPT, bool BULK, bool TC>
+__device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const StepArgs<T>& a) {
+  static_assert(!TC || (sizeof(T) == 4 && PPT == 1 && !BULK && D2 % 8 == 0), "tensor-core step");
+  constexpr int NP = (D2 + 15) / 16 * 16;  // MMA N: A_zz rows padded to 16
+  constexpr int KC16 = D2 * 4 / 16;        // 16-byte chunks per operand row
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int REC = rec_len<T, D1, DY, XZ>();
   const int NT = blockDim.x;
@@ -375,6 +404,8 @@ __global__ void __launch_bounds__(MAXNT)
   uint32_t* redU = (uint32_t*)(red + 32);
   T* part = (T*)(smem_raw + a.off_part);
   __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t tcbar;
+  __shared__ uint32_t s_taddr;
   __shared__ int s_m, s_fallback;
   __shared__ uint32_t s_uin;
 
@@ -387,7 +418,35 @@ __global__ void __launch_bounds__(MAXNT)
     mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
+  uint32_t taddr = 0, tc_phase = 0;
+  constexpr uint32_t TC_COLS = TC ? (NP * 2 <= 32 ? 32 : NP * 2 <= 64 ? 64 : NP * 2 <= 128 ? 128 : 256) : 32;
+  if constexpr (TC) {
+    // B operand: A_zz (row n = output coordinate n) split hi/lo, K-major; rows >= D2 zero
+    unsigned char* ahi = smem_raw + a.off_ahi;
+    unsigned char* alo = smem_raw + a.off_alo;
+    for (int e = tid; e < NP * D2; e += NT) {
+      const int n = e / D2, k = e % D2;
+      float hi = 0.f, lo = 0.f;
+      if (n < D2) tc::split_tf32((float)mc.Azz[n][k], hi, lo);
+      *(float*)(ahi + tc::kmajor_offset(n, 4 * k, KC16)) = hi;
+      *(float*)(alo + tc::kmajor_offset(n, 4 * k, KC16)) = lo;
+    }
+    tc::fence_proxy_async();
+    if (tid < 32) {
+      tc::tmem_alloc(&s_taddr, TC_COLS);
+      tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+      mbar_init(&tcbar, 1);
+      mbar_fence_init();
+    }
+    tc::fence_before();
+  }
   __syncthreads();
+  if constexpr (TC) {
+    tc::fence_after();
+    taddr = s_taddr;
+  }
 
   // prologue (bulk path): stage the first group; thread 0 keeps the next group's
   // source index in flight
@@ -401,7 +460,7 @@ __global__ void __launch_bounds__(MAXNT)
   for (int k = 0; g < N; g += gridDim.x, ++k) {
     const long long i = g;
     const int sidx = k & 1;
-    unsigned char* st = stage0 + sidx * a.stage_bytes;
+    unsigned char* st = stage0 + (BULK ? sidx * a.stage_bytes : 0);
     if (BULK) {
       // prefetch the next group into the other stage (released at the end of the last group)
       if (tid == 0 && g + gridDim.x < N) {
@@ -566,42 +625,150 @@ __global__ void __launch_bounds__(MAXNT)
       }
       T ell[PPT];
       T lmax = NEG;
+      if constexpr (!TC) {
 #pragma unroll
-      for (int p = 0; p < PPT; ++p) {
-        const int j = tid + p * NT;
-        ell[p] = NEG;
-        if (j < M) {
-          const int b = sys_local_pick(cum, M, C, M, j, uin);
-          if (a.dbg_b) a.dbg_b[i * M + j] = b;
-          T eps[D2];
-          normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
-          T zb2[D2];
+        for (int p = 0; p < PPT; ++p) {
+          const int j = tid + p * NT;
+          ell[p] = NEG;
+          if (j < M) {
+            const int b = sys_local_pick(cum, M, C, M, j, uin);
+            if (a.dbg_b) a.dbg_b[i * M + j] = b;
+            T eps[D2];
+            normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
+            if constexpr (D2 > 32) {
+              // wide z: column by column from the staged rows (same order per row)
 #pragma unroll
-          for (int c = 0; c < D2; ++c) zb2[c] = sz[c * M + b];
+              for (int r = 0; r < D2; ++r) zr[p][r] = azx[r];
+#pragma unroll 1
+              for (int c = 0; c < D2; ++c) {
+                const T zc = sz[c * M + b];
 #pragma unroll
-          for (int r = 0; r < D2; ++r) {
-            T v = azx[r];
+                for (int r = 0; r < D2; ++r) zr[p][r] += mc.Azz[r][c] * zc;
+              }
 #pragma unroll
-            for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * zb2[c];
-            if (mc.diag_qz) {
-              v += mc.Lqz[r][r] * eps[r];
+              for (int r = 0; r < D2; ++r) {
+                if (mc.diag_qz) {
+                  zr[p][r] += mc.Lqz[r][r] * eps[r];
+                } else {
+#pragma unroll
+                  for (int c = 0; c <= r; ++c) zr[p][r] += mc.Lqz[r][c] * eps[c];
+                }
+              }
             } else {
+              T zb2[D2];
 #pragma unroll
-              for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+              for (int c = 0; c < D2; ++c) zb2[c] = sz[c * M + b];
+#pragma unroll
+              for (int r = 0; r < D2; ++r) {
+                T v = azx[r];
+#pragma unroll
+                for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * zb2[c];
+                if (mc.diag_qz) {
+                  v += mc.Lqz[r][r] * eps[r];
+                } else {
+#pragma unroll
+                  for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+                }
+                zr[p][r] = v;
+              }
             }
-            zr[p][r] = v;
-          }
-          T qf = T(0);
+            T qf = T(0);
 #pragma unroll
-          for (int q = 0; q < DY; ++q) {
-            T v = yh[q];
+            for (int q = 0; q < DY; ++q) {
+              T v = yh[q];
 #pragma unroll
-            for (int c = 0; c < D2; ++c) v -= mc.LrHz[q][c] * zr[p][c];
-            qf += v * v;
+              for (int c = 0; c < D2; ++c) v -= mc.LrHz[q][c] * zr[p][c];
+              qf += v * v;
+            }
+            ell[p] = T(-0.5) * qf;
+            lmax = fmax(lmax, ell[p]);
           }
-          ell[p] = T(-0.5) * qf;
-          lmax = fmax(lmax, ell[p]);
         }
+      } else {
+        // ---- z_new = A_zz z_b on the tensor cores, then + A_zx x_a + L_qz eps ----
+        const int j = tid;  // one inner particle a thread, NT == M
+        const int b = sys_local_pick(cum, M, C, M, j, uin);
+        if (a.dbg_b) a.dbg_b[i * M + j] = b;
+        float zb2[D2];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) zb2[c] = (float)sz[c * M + b];
+        __syncthreads();  // every gather is done: the staged z rows become the A operand
+        unsigned char* zhi = (unsigned char*)sz;
+        unsigned char* zlo = smem_raw + a.off_zlo;
+        const uint32_t tb = (uint32_t)(j >> 7) * 128u * (uint32_t)(D2 * 4);
+        const int rr = j & 127;
+#pragma unroll
+        for (int c = 0; c < D2; ++c) {
+          float hi, lo;
+          tc::split_tf32(zb2[c], hi, lo);
+          *(float*)(zhi + tb + tc::kmajor_offset(rr, 4 * c, KC16)) = hi;
+          *(float*)(zlo + tb + tc::kmajor_offset(rr, 4 * c, KC16)) = lo;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after();
+          const uint32_t idesc = tc::instr_desc(tc::FMT_TF32, 128, NP);
+          const uint32_t s_zhi = smem_addr(zhi), s_zlo = smem_addr(zlo);
+          const uint32_t s_ahi = smem_addr(smem_raw + a.off_ahi), s_alo = smem_addr(smem_raw + a.off_alo);
+          for (int tt = 0; tt < M / 128; ++tt) {
+            const uint32_t d = taddr + (uint32_t)(tt * NP), ob = (uint32_t)tt * 128u * (uint32_t)(D2 * 4);
+#pragma unroll
+            for (int ks = 0; ks < D2 / 8; ++ks) {
+              const uint32_t o = (uint32_t)ks * 256u;
+              tc::mma_tf32(d, tc::smem_desc(s_zlo + ob + o, KC16), tc::smem_desc(s_ahi + o, KC16), idesc, ks > 0);
+              tc::mma_tf32(d, tc::smem_desc(s_zhi + ob + o, KC16), tc::smem_desc(s_alo + o, KC16), idesc, 1);
+              tc::mma_tf32(d, tc::smem_desc(s_zhi + ob + o, KC16), tc::smem_desc(s_ahi + o, KC16), idesc, 1);
+            }
+          }
+          tc::commit(&tcbar);
+        }
+        const bool ok = tc::bar_wait(&tcbar, tc_phase, TC_SPIN);
+        tc_phase ^= 1u;
+        if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+        tc::fence_after();
+        float azz[D2];
+        {
+          const uint32_t ta = taddr + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((j >> 7) * NP);
+#pragma unroll
+          for (int c0 = 0; c0 + 16 <= D2; c0 += 16) {
+            float v[16];
+            tc::ld16(ta + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) azz[c0 + q] = ok ? v[q] : 0.f;
+          }
+          if (D2 % 16) {
+            float v[8];
+            tc::ld8(ta + (uint32_t)(D2 / 16 * 16), v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (D2 / 16 * 16 + q < D2) azz[D2 / 16 * 16 + q] = ok ? v[q] : 0.f;
+          }
+        }
+        tc::fence_before();
+        T eps[D2];
+        normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
+#pragma unroll
+        for (int r = 0; r < D2; ++r) {
+          T v = azx[r] + (T)azz[r];
+          if (mc.diag_qz) {
+            v += mc.Lqz[r][r] * eps[r];
+          } else {
+            for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+          }
+          zr[0][r] = v;
+        }
+        T qf = T(0);
+#pragma unroll
+        for (int q = 0; q < DY; ++q) {
+          T v = yh[q];
+#pragma unroll
+          for (int c = 0; c < D2; ++c) v -= mc.LrHz[q][c] * zr[0][c];
+          qf += v * v;
+        }
+        ell[0] = T(-0.5) * qf;
+        lmax = ell[0];
       }
       lmax = bmax(lmax, red);
       T ls = T(0);
@@ -906,6 +1073,26 @@ __global__ void __launch_bounds__(MAXNT)
     }
     __syncthreads();  // the stage and the work buffers are free for the next group
   }
+  if constexpr (TC) {
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(taddr, TC_COLS);
+  }
+}
+
+// The block step with the model constants as a launch parameter.
+template <typename T, int D1, int D2, int DY, bool XZ, int PPT, int MAXNT, bool BULK>
+__global__ void __launch_bounds__(MAXNT)
+    step_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, const __grid_constant__ StepArgs<T> a) {
+  step_body<T, D1, D2, DY, XZ, PPT, BULK, false>(mc, a);
+}
+
+// The block step with the model constants in global memory (models too large
+// for a launch parameter), optionally with the tensor-core propagation.
+template <typename T, int D1, int D2, int DY, bool XZ, int PPT, int MAXNT, bool BULK, bool TC>
+__global__ void __launch_bounds__(MAXNT)
+    step_kernel_g(const MC<T, D1, D2, DY>* __restrict__ mcp, const __grid_constant__ StepArgs<T> a) {
+  step_body<T, D1, D2, DY, XZ, PPT, BULK, TC>(*mcp, a);
 }
 
 // ---- outer reduction: evidence, ESS, filtered mean, quantised total ----

@@ -10,11 +10,12 @@ Variant make_v_f32_1_15_4();
 Variant make_v_f32_2_14_4();
 Variant make_v_f32_4_12_4();
 Variant make_v_f32_8_8_4();
+Variant make_v_f32_8_56_8();
 
 const Variant* find_variant(int prec, int d1, int d2, int dy) {
   static const Variant table[] = {make_v_f32_2_8_2(), make_v_f64_2_2_2(), make_v_f32_2_2_2(),
                                   make_v_f32_1_15_4(), make_v_f32_2_14_4(), make_v_f32_4_12_4(),
-                                  make_v_f32_8_8_4()};
+                                  make_v_f32_8_8_4(), make_v_f32_8_56_8()};
   for (const Variant& v : table)
     if (v.prec == prec && v.d1 == d1 && v.d2 == d2 && v.dy == dy) return &v;
   return nullptr;

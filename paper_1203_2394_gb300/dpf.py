@@ -58,6 +58,7 @@ SIGNATURES = [
     ("dpf_tc_matmul", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
+    ("dpf_set_tensor_cores", ctypes.c_int, [_P, _I32]),
     ("dpf_set_debug", ctypes.c_int, [_P, _I32]),
     ("dpf_profile", ctypes.c_int, [_P, _I32]),
     ("dpf_profile_read", ctypes.c_int, [_P, _P, _P]),
@@ -191,6 +192,9 @@ class Filter:
 
     def set_debug(self, on=True):
         check(self._lib.dpf_set_debug(self.h, int(on)))
+
+    def set_tensor_cores(self, on=True):
+        check(self._lib.dpf_set_tensor_cores(self.h, int(on)))
 
     def profile(self, on=True):
         check(self._lib.dpf_profile(self.h, int(on)))

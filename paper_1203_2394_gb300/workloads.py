@@ -19,6 +19,10 @@ Named workloads (sizes are the filter's, model sizes in the spec):
   N(0, I) with C 2x8 of N(0, 1/8) entries; T = 200, N = 65536, M = 128, L = 16, FP32.
 * ``lg16``: linear-Gaussian, d = 16, A spectral radius 0.9, Q = 0.1 I, dy = 4,
   H of N(0, 1/16) entries, R = 0.5 I; the x/z split d1 is chosen per filter.
+* ``growth_clg64``: the growth_clg10 recipe widened: x of dim 8 (the growth map per
+  coordinate, Q_x = I), z of dim 56 with a dense A_zz of spectral radius 0.95 and
+  Q_z = 0.1 I, y = x.^2/20 + C z + N(0, I) with C 8x56 of N(0, 1/56) entries;
+  T = 500, N = 32768, M = 256, L = 16, FP32.
 """
 from __future__ import annotations
 
@@ -96,6 +100,19 @@ def make_model(name: str, seed: int = 0, d1: int | None = None) -> ModelSpec:
         return ModelSpec(name, d, dd1, dy, A, Q, H, np.eye(dy), np.zeros(d), np.eye(d),
                          growth=(0.5, 25.0, 8.0, 1.2), qc=1.0 / 20.0,
                          sizes=dict(T=200, N=65536, M=128, L=16, dtype="f32"))
+    if name == "growth_clg64":
+        dd1, d2, dy = 8, 56, 8
+        d = dd1 + d2
+        A = np.zeros((d, d))
+        A[dd1:, dd1:] = random_spectral(rng, d2, 0.95)
+        Q = np.zeros((d, d))
+        Q[:dd1, :dd1] = np.eye(dd1)
+        Q[dd1:, dd1:] = 0.1 * np.eye(d2)
+        H = np.zeros((dy, d))
+        H[:, dd1:] = rng.standard_normal((dy, d2)) / np.sqrt(d2)
+        return ModelSpec(name, d, dd1, dy, A, Q, H, np.eye(dy), np.zeros(d), np.eye(d),
+                         growth=(0.5, 25.0, 8.0, 1.2), qc=1.0 / 20.0,
+                         sizes=dict(T=500, N=32768, M=256, L=16, dtype="f32"))
     if name == "lg16":
         d, dy = 16, 4
         A = random_spectral(rng, d, 0.9)
