@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 P_INIT_X, P_INIT_Z, P_LA_J, P_LA_X, P_LA_Z, P_OUTER, P_SEL, P_INNER, P_PROP = range(1, 10)
+P_LCOMP = 10  # mixture-component draw of the learned inner proposal
 
 
 def build(force: bool = False, extra_flags: tuple = ()) -> str:
@@ -105,6 +106,7 @@ class OracleModel:
         self.d1, self.d2, self.dy = int(d1), int(d2), int(dy)
         self.A, self.Q, self.H, self.R = _f64(A), _f64(Q), _f64(H), _f64(R)
         self.m0, self.P0 = _f64(m0), _f64(P0)
+        self.growth, self.qc = growth, qc
         g = growth if growth is not None else (0.0, 0.0, 0.0, 0.0)
         self.s = ModelIn(self.d1, self.d2, self.dy, int(growth is not None), int(qc is not None), 0,
                          float(g[0]), float(g[1]), float(g[2]), float(g[3]),

@@ -136,3 +136,27 @@ def simulate(spec: ModelSpec, T: int, seed: int = 0):
         s[t] = spec.mean_fn(s[t - 1], t - 1) + Lq @ rng.standard_normal(d)
         ys[t - 1] = spec.obs_fn(s[t]) + Lr @ rng.standard_normal(dy)
     return s, ys
+
+
+def proposal_dims(spec, d1: int | None = None, components: int = 4, hidden: int = 256):
+    """Sizes of the learned inner proposal for a model: inputs (x_{t-1}, x_t, z_{t-1}, y_t),
+    hidden width, and the mixture head (logits, means, log standard deviations)."""
+    d1 = spec.d1 if d1 is None else d1
+    d2 = spec.d - d1
+    return dict(din=2 * d1 + d2 + spec.dy, hidden=hidden, components=components,
+                dout=components * (1 + 2 * d2), d2=d2)
+
+
+def init_mlp_weights(din: int, hidden: int, dout: int, seed: int = 0, layers: int = 3):
+    """Seeded initial weights of an MLP with `layers` hidden ReLU layers of width `hidden`:
+    He-normal weights, zero biases; the head starts at a tenth of that scale. Returns a
+    dict of float64 arrays W1, b1, ..., W{layers+1}, b{layers+1} (W_l is out x in)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = [din] + [hidden] * layers + [dout]
+    w = {}
+    for l in range(1, len(sizes)):
+        fan_in = sizes[l - 1]
+        scale = np.sqrt(2.0 / fan_in) * (0.1 if l == len(sizes) - 1 else 1.0)
+        w[f"W{l}"] = rng.standard_normal((sizes[l], fan_in)) * scale
+        w[f"b{l}"] = np.zeros(sizes[l])
+    return w

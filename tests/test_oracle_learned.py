@@ -1,0 +1,169 @@
+"""Pins of the learned-proposal oracle (``oracle/learned.py``), none of which reuses its
+own formulas:
+
+* gradients of the weighted NLL against central finite differences (FP64), with some
+  log-sigmas outside the clamp (zero gradient there);
+* one component: log q equals scipy's multivariate normal log-density;
+* the mixture density integrates to one on a grid; identical components give the
+  single-component density whatever the logits;
+* Adam's first step equals -lr g / (|g| + eps) (bias correction cancels), and Adam
+  minimises a convex quadratic;
+* bfloat16 rounding agrees with torch's float32 -> bfloat16 conversion;
+* a network that outputs exactly the prior (a ReLU pair per input, identity hidden
+  layers, four equal components with sigma^2 = Q_z) makes the learned inner update
+  reproduce the plain one of the C oracle (which the Kalman pins hold), z and lq.
+"""
+import numpy as np
+import pytest
+
+from oracle import learned, oracle
+from paper_1203_2394_gb300 import workloads
+
+
+def _small(seed=0, din=8, hidden=12, d2=2, C=3, n=40):
+    rng = np.random.default_rng(seed)
+    W = workloads.init_mlp_weights(din, hidden, C * (1 + 2 * d2), seed=seed)
+    for k in W:
+        W[k] = W[k] + 0.05 * rng.standard_normal(W[k].shape)
+    F = rng.standard_normal((n, din))
+    Z = rng.standard_normal((n, d2))
+    w = rng.uniform(0.1, 1.0, n)
+    return W, F, Z, w
+
+
+def test_gradients_match_finite_differences():
+    W, F, Z, w = _small()
+    d2, C = 2, 3
+    # push a few raw log-sigmas outside the clamp
+    W["b4"][C + C * d2 + 0] = 9.0
+    W["b4"][C + C * d2 + 3] = -11.0
+    loss, G = learned.nll_and_grad(W, F, Z, w, d2, C)
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    for k in W:
+        flat = W[k].reshape(-1)
+        picks = rng.choice(flat.size, min(flat.size, 25), replace=False)
+        for p in picks:
+            old = flat[p]
+            flat[p] = old + h
+            lp, _ = learned.nll_and_grad(W, F, Z, w, d2, C)
+            flat[p] = old - h
+            lm, _ = learned.nll_and_grad(W, F, Z, w, d2, C)
+            flat[p] = old
+            fd = (lp - lm) / (2 * h)
+            g = G[k].reshape(-1)[p]
+            assert abs(fd - g) <= 1e-6 * max(1.0, abs(fd)), (k, p, fd, g)
+    assert G["b4"][C + C * d2 + 0] == 0.0 and G["b4"][C + C * d2 + 3] == 0.0
+
+
+def test_one_component_is_the_gaussian_density():
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(2)
+    n, d2 = 30, 3
+    z = rng.standard_normal((n, d2))
+    mu = rng.standard_normal((n, 1, d2))
+    ls = rng.uniform(-1, 1, (n, 1, d2))
+    lq = learned.logq(z, rng.standard_normal((n, 1)), mu, ls)
+    for b in range(n):
+        ref = stats.multivariate_normal.logpdf(z[b], mu[b, 0], np.diag(np.exp(2 * ls[b, 0])))
+        assert lq[b] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_mixture_integrates_to_one_and_equal_components_collapse():
+    rng = np.random.default_rng(3)
+    C = 4
+    logits = rng.standard_normal((1, C))
+    mu = rng.uniform(-1, 1, (1, C, 2))
+    ls = rng.uniform(-0.7, 0.2, (1, C, 2))
+    g = np.linspace(-9, 9, 721)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel()], 1)
+    lq = learned.logq(pts, np.repeat(logits, len(pts), 0), np.repeat(mu, len(pts), 0),
+                      np.repeat(ls, len(pts), 0))
+    mass = np.exp(lq).sum() * (g[1] - g[0]) ** 2
+    assert mass == pytest.approx(1.0, abs=1e-6)
+    same_mu = np.repeat(mu[:, :1], C, 1)
+    same_ls = np.repeat(ls[:, :1], C, 1)
+    z = rng.standard_normal((1, 2))
+    a = learned.logq(z, logits, same_mu, same_ls)
+    b = learned.logq(z, np.zeros((1, 1)), mu[:, :1], ls[:, :1])
+    assert a[0] == pytest.approx(b[0], rel=1e-13, abs=1e-13)
+
+
+def test_adam_first_step_and_convergence():
+    rng = np.random.default_rng(4)
+    W = {"a": rng.standard_normal(7)}
+    G = {"a": rng.standard_normal(7)}
+    st = learned.adam_init(W)
+    lr, eps = 3e-3, 1e-8
+    W1 = learned.adam_step(W, G, st, lr=lr, eps=eps)
+    np.testing.assert_allclose(W1["a"] - W["a"], -lr * G["a"] / (np.abs(G["a"]) + eps), rtol=1e-9)
+    # minimise 0.5 (w - c)^T D (w - c)
+    c = rng.standard_normal(5)
+    D = rng.uniform(0.5, 3.0, 5)
+    W = {"a": np.zeros(5)}
+    st = learned.adam_init(W)
+    for _ in range(3000):
+        W = learned.adam_step(W, {"a": D * (W["a"] - c)}, st, lr=1e-2)
+    np.testing.assert_allclose(W["a"], c, atol=1e-3)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.standard_normal(4000) * 10 ** rng.uniform(-6, 6, 4000),
+                        [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -1.0 - 2.0 ** -8, 0.0, -0.0]])
+    ref = torch.tensor(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(learned.bf16(v), ref)
+
+
+def _prior_net(model, hidden=16, C=4):
+    """An MLP whose mixture is exactly the prior N(A_zx x_a + A_zz z_b, Q_z)."""
+    d1, d2, dy = model.d1, model.d2, model.dy
+    din = 2 * d1 + d2 + dy
+    A = model.A
+    P = np.zeros((d2, din))
+    P[:, :d1] = A[d1:, :d1]             # A_zx x_{t-1}
+    P[:, 2 * d1:2 * d1 + d2] = A[d1:, d1:]  # A_zz z_b
+    W = {}
+    W1 = np.zeros((hidden, din))
+    W1[:din] = np.eye(din)
+    W1[din:2 * din] = -np.eye(din)
+    W["W1"], W["b1"] = W1, np.zeros(hidden)
+    for l in (2, 3):
+        W[f"W{l}"], W[f"b{l}"] = np.eye(hidden), np.zeros(hidden)
+    dout = C * (1 + 2 * d2)
+    W4 = np.zeros((dout, hidden))
+    b4 = np.zeros(dout)
+    sig = np.sqrt(np.diag(model.Q[d1:, d1:]))
+    for c in range(C):
+        rows = slice(C + c * d2, C + (c + 1) * d2)
+        W4[rows, :din] = P
+        W4[rows, din:2 * din] = -P
+        b4[C + C * d2 + c * d2:C + C * d2 + (c + 1) * d2] = np.log(sig)
+    W["W4"], W["b4"] = W4, b4
+    return W
+
+
+def test_prior_network_reproduces_the_plain_inner_update():
+    spec = workloads.make_model("lg4", 0)
+    om = oracle.OracleModel.from_spec(spec)
+    N, M, L, seed = 12, 16, 4, 3
+    o = oracle.Oracle(om, N, M, L, seed)
+    _, ys = workloads.simulate(spec, 3, 0)
+    x, z, lq = o.init()
+    r1 = o.step(1, ys[0], x, z, lq)
+    x1, z1, lq1 = r1["x"], r1["z"], r1["lq"]
+    r2 = o.step(2, ys[1], x1, z1, lq1)
+    anc, xn = r2["anc"], r2["x"]
+    fin = o.finalize(2, ys[1], np.arange(N), anc, x1, z1, lq1, xn)
+    W = _prior_net(om)
+    lib = oracle.load()
+    got = learned.learned_finalize(
+        om, W, 4, seed, 2, ys[1], anc, x1, z1, xn, fin["bidx"],
+        normals=lambda t, i, p, j, n: oracle.normals(seed, 0, t, i, p, j, n, lib),
+        sys_local=lambda w, k, u: oracle.sys_local(w, k, u, lib),
+        word=lambda t, i, p, j: int(oracle.philox((t, i, (p << 24) | j, 0), (seed, 0), lib)[0]))
+    np.testing.assert_allclose(got["z"], fin["z"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got["lq"], fin["lq"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(fin["z"], r2["z"], rtol=0, atol=0)
