@@ -214,7 +214,9 @@ dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ
  *   newest materialised state, which is that of step t-1 after step t (the
  *   inner update of step t runs at the start of step t+1), and "sel" holds the
  *   draws that chose it; "bidx" (N*M int32, the local-resampling ancestors of
- *   that inner update; only when debug recording is on).
+ *   that inner update; only when debug recording is on);
+ * "head": N x M x dout float, the learned proposal's head outputs of that
+ *   inner update (with a proposal set and debug recording on).
  * Element type: the context's precision (or int32). Synchronises the stream.
  */
 dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t bytes);
@@ -286,6 +288,77 @@ dpf_status dpf_batch_profile(dpf_batch* b, int32_t enable);
 dpf_status dpf_batch_profile_read(dpf_batch* b, double* kernel_ms, int64_t* launches);
 
 void dpf_batch_destroy(dpf_batch* b);
+
+/*
+ * ---- Learned inner proposal ----
+ * Not in the paper: a learned replacement of the prior proposal of the inner
+ * particles (Fig. 4, step 4; the r-tilde weight of eq. qbar):
+ *   q_phi(z_t | f) = sum_c pi_c N(z_t; mu_c, diag sigma_c^2),
+ *   f = (x_{t-1} of the ancestor, x_t, z_{t-1} of the resampled parent, y_t),
+ * an MLP of three hidden ReLU layers (width `hidden`) with a head of
+ * components (1 + 2 d2) outputs: logits, the means (component-major), then the
+ * raw log standard deviations, clamped to [-7, 5] where used. Weights are FP32
+ * master copies; the forward pass uses bfloat16 weights and activations with
+ * FP32 accumulation (dpf_proposal_set_bf16(p, 0) makes training plain FP32).
+ *
+ * Parameters (dpf_proposal_get/set_weights, host float arrays of num_params):
+ *   W1 (hidden x din), b1, W2 (hidden x hidden), b2, W3, b3, W4 (dout x hidden), b4,
+ * row-major, din = 2 d1 + d2 + dy <= 16, d2 <= 8, hidden a multiple of 16 up to
+ * 256, 1..8 components, dout <= 128. The proposal is owned by the caller and
+ * must outlive every filter that uses it.
+ */
+typedef struct dpf_proposal dpf_proposal;
+
+dpf_status dpf_proposal_create(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, int32_t components,
+                               void* stream, dpf_proposal** out);
+dpf_status dpf_proposal_num_params(const dpf_proposal* p, int64_t* n);
+/* Load parameters (and reset Adam); n must equal num_params. Synchronises. */
+dpf_status dpf_proposal_set_weights(dpf_proposal* p, const float* params, int64_t n);
+dpf_status dpf_proposal_get_weights(const dpf_proposal* p, float* params, int64_t n);
+/* Round the forward pass to bfloat16 (default, as the filter's tensor-core pass) or not. */
+dpf_status dpf_proposal_set_bf16(dpf_proposal* p, int32_t enable);
+/*
+ * Weighted negative log-likelihood of n rows and its gradient: loss =
+ * sum_b w_b (-log q(Z_b | F_b)) / sum_b w_b. F (n x din), Z (n x d2), w (n):
+ * device float arrays; loss: host (may be NULL); grad_dev: device, num_params
+ * floats in the parameter order, or NULL. Synchronises.
+ */
+dpf_status dpf_proposal_loss_grad(dpf_proposal* p, const float* F, const float* Z, const float* w, int64_t n,
+                                  double* loss, float* grad_dev);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the given device gradient. Synchronises. */
+dpf_status dpf_proposal_adam_step(dpf_proposal* p, const float* grad_dev, float lr);
+/*
+ * Train on n device rows (as dpf_proposal_loss_grad): `epochs` passes in
+ * minibatches of `batch` rows, a fresh order each epoch (Fisher-Yates driven by
+ * splitmix64 from `seed`), one Adam step per minibatch. losses: host, epochs
+ * doubles (mean minibatch loss of each epoch), or NULL. Synchronises.
+ */
+dpf_status dpf_proposal_train(dpf_proposal* p, const float* F, const float* Z, const float* w, int64_t n,
+                              int32_t batch, int32_t epochs, float lr, uint64_t seed, double* losses);
+/* The head outputs (n x dout floats, device) of n device feature rows by the
+ * tensor-core forward pass the filter step uses. Synchronises. */
+dpf_status dpf_proposal_forward(dpf_proposal* p, const float* F, int64_t n, float* out);
+void dpf_proposal_destroy(dpf_proposal* p);
+
+/*
+ * Use `p` as the inner proposal of ctx from the next step on (NULL: the prior
+ * again). Needs an FP32 context with d1, d2, dy equal to the proposal's and M
+ * in {32, 64, 128}; the look-ahead is unchanged. The inner update then draws
+ * z_t^(i,j) ~ q_phi(. | f) (component by the one-draw local systematic rule,
+ * Philox purpose 10 = LCOMP, the normal noise from the PROP stream) and weights
+ * it by log r = log p(z_t | z_{t-1}, x_{t-1}) - log q_phi(z_t | f) + log p(y_t | x_t, z_t).
+ */
+dpf_status dpf_set_proposal(dpf_ctx* ctx, dpf_proposal* p);
+
+/*
+ * Training rows from the inner update the last dpf_step ran (it must have run
+ * one, with debug recording on: dpf_set_debug(ctx, 1)): for every inner
+ * particle of the outer particles i0 .. i0 + n_outer - 1, F = (x_{t-1} of the
+ * ancestor, x_t, z_{t-1} of the parent, y_t), Z = z_t and w = exp(lq_t) / N
+ * (the normalised inner weight times the equal outer weight after resampling).
+ * F: n_outer M x din, Z: n_outer M x d2, w: n_outer M; device floats. Synchronises.
+ */
+dpf_status dpf_record_tuples(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* F, float* Z, float* w);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* dpf_last_error(void);

@@ -368,7 +368,20 @@ static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
     }
     cudaEventRecord(x->pev[x->pev_used], x->stream);
   }
-  dpf_status st = x->var->step(*x, 0);
+  dpf_status st = DPF_OK;
+  if (x->debug && x->anc_prev && t >= 2)  // the ancestors this call's inner update reads
+    cudaMemcpyAsync(x->anc_prev, x->anc, sizeof(int32_t) * x->N, cudaMemcpyDeviceToDevice, x->stream);
+  if (x->proposal && t >= 2) {
+    // learned proposal: its inner update, then the look-ahead alone
+    st = learned_inner_step(*x);
+    if (!st) {
+      x->la_only = true;
+      st = x->var->step(*x, 0);
+      x->la_only = false;
+    }
+  } else {
+    st = x->var->step(*x, 0);
+  }
   if (st) return st;
   if (x->profiling) {
     cudaEventRecord(x->pev[x->pev_used + 1], x->stream);
@@ -465,6 +478,10 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   else if (w == "bidx") {
     if (!x->dbg_b) return set_error(DPF_E_INVALID, "dpf_read: bidx needs dpf_set_debug(ctx, 1)");
     src = x->dbg_b; need = 4 * N * M;
+  } else if (w == "head") {
+    if (!x->dbg_head || !x->proposal)
+      return set_error(DPF_E_INVALID, "dpf_read: head needs a learned proposal and dpf_set_debug(ctx, 1)");
+    src = x->dbg_head; need = 4 * N * M * (size_t)dpf_proposal_dout(x->proposal);
   } else return set_error(DPF_E_INVALID, "dpf_read: unknown array '" + w + "'");
   if (bytes != need)
     return set_error(DPF_E_INVALID, "dpf_read: '" + w + "' needs " + std::to_string(need) + " bytes");
@@ -486,6 +503,8 @@ dpf_status dpf_set_debug(dpf_ctx* x, int32_t enable) {
   if (!x) return set_error(DPF_E_INVALID, "dpf_set_debug: null context");
   if (enable && !x->dbg_b) {
     dpf_status st = dalloc(*x, x->dbg_b, (size_t)4 * x->N * x->M);
+    if (!st) st = dalloc(*x, x->anc_prev, (size_t)4 * x->N);
+    if (!st && x->prec == DPF_F32) st = dalloc(*x, x->dbg_head, (size_t)4 * x->N * x->M * 32);
     if (st) return st;
   }
   x->debug = enable != 0;

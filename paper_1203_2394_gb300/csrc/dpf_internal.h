@@ -105,6 +105,8 @@ struct Variant {
   bool xz_supported = true;  // serves models whose x transition depends on z
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
+dpf_status learned_inner_step(Ctx& x);  // dpf_learned_step.cu
+int dpf_proposal_dout(const dpf_proposal* p);  // head outputs of a proposal
 
 }  // namespace dpf
 
@@ -133,6 +135,8 @@ struct dpf_ctx {
   int32_t* anc = nullptr;
   int32_t* sel = nullptr;
   int32_t* dbg_b = nullptr;
+  int32_t* anc_prev = nullptr;  // debug: the ancestors the last inner update used
+  void* dbg_head = nullptr;     // debug: the learned proposal's head outputs of the last inner update
   // small device block: reduction partials, statistics, counters, error word
   void* small = nullptr;
   double* stats = nullptr;          // [logZ_total, logZ_step, ess, s1, mean[d]]
@@ -158,6 +162,8 @@ struct dpf_ctx {
   int grid_step = 0;  // persistent grid of the step kernel (0 = not yet sized)
   void* d_mconst = nullptr;  // the model constants in device memory (variants that read them there)
   bool tensor_cores = true;  // tensor-core propagation where the variant has one
+  dpf_proposal* proposal = nullptr;  // learned inner proposal (null: the prior)
+  bool la_only = false;      // the next step kernel runs the look-ahead only
   // profiling of the main kernel
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // pairs bracketing the step kernel

@@ -1,0 +1,551 @@
+// The learned inner proposal: an MLP (3 hidden ReLU layers) with a Gaussian-mixture
+// head, its training on the GPU (forward, backward and Adam kernels written here) and
+// the packing of its weights for the tensor-core forward pass of the filter step.
+//
+// Parameters, one FP32 buffer in this order (row-major, W_l is out x in):
+//   W1 (H x din), b1 (H), W2 (H x H), b2, W3 (H x H), b3, W4 (dout x H), b4 (dout),
+// with dout = C (1 + 2 d2): logits, then the C x d2 means, then the C x d2 raw log
+// standard deviations (clamped to [-7, 5] where used).
+//
+// Training minimises the weighted negative log-likelihood of the recorded
+// (features, z) rows, sum_b w_b (-log q(z_b | f_b)) / sum_b w_b, per minibatch, with
+// Adam (Kingma and Ba 2015). With bf16 on, the forward pass rounds the inputs, the
+// weights and every hidden activation to bfloat16 as the tensor-core pass does
+// (gradients pass the rounding straight through); off, it is plain FP32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dpf_learned.h"
+
+namespace dpf {
+
+// ---- tiled FP32 GEMM: C[M x N] = op(A) op(B) with an epilogue ----
+// A(m, k) = TA ? A[k lda + m] : A[m lda + k];  B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].
+// EPI: 0 store; 1 bias, ReLU and optional bfloat16 rounding; 2 bias; 3 multiply by
+// (mask(m, n) > 0), mask with leading dimension ldc.
+constexpr int GT = 64, GK = 16;
+
+__device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(256)
+    sgemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
+                 int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias,
+                 const float* __restrict__ mask, int round) {
+  __shared__ float As[GK][GT + 4];
+  __shared__ float Bs[GK][GT + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    // 64 x 16 of A and 16 x 64 of B, 4 elements a thread each
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int r = e / GK, c = e % GK;  // A tile: row r (m), column c (k)
+      const int m = m0 + r, k = k0 + c;
+      float v = 0.f;
+      if (m < M && k < K) v = TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k];
+      As[c][r] = v;
+      const int kb = e / GT, nb = e % GT;  // B tile: row kb (k), column nb (n)
+      const int k2 = k0 + kb, n = n0 + nb;
+      float w = 0.f;
+      if (k2 < K && n < N) w = TB ? B[(long long)n * ldb + k2] : B[(long long)k2 * ldb + n];
+      Bs[kb][nb] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == 1) {
+        v = fmaxf(v + bias[n], 0.f);
+        if (round) v = round_bf16(v);
+      } else if (EPI == 2) {
+        v += bias[n];
+      } else if (EPI == 3) {
+        v = mask[(long long)m * ldc + n] > 0.f ? v : 0.f;
+      }
+      C[(long long)m * ldc + n] = v;
+    }
+  }
+}
+
+template <bool TA, bool TB, int EPI>
+static void sgemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                  float* C, int ldc, const float* bias = nullptr, const float* mask = nullptr, int round = 0) {
+  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
+  sgemm_kernel<TA, TB, EPI><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round);
+}
+
+// ---- the mixture head: loss and d(loss)/d(out) per row ----
+struct HeadArgs {
+  const float* out;  // n x dout
+  const float* Z;    // n x d2
+  const float* w;    // n
+  const double* wsum;
+  float* dout;       // n x dout
+  double* loss;      // accumulated: sum_b w_b (-log q_b) / wsum
+  int n, d2, C, dout_n;
+};
+
+__global__ void head_loss_kernel(HeadArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.n) return;
+  const int C = a.C, d2 = a.d2, D = a.dout_n;
+  const float* o = a.out + (long long)b * D;
+  const float* z = a.Z + (long long)b * d2;
+  float* g = a.dout + (long long)b * D;
+  // log softmax of the logits
+  float lmax = -INFINITY;
+  for (int c = 0; c < C; ++c) lmax = fmaxf(lmax, o[c]);
+  float se = 0.f;
+  for (int c = 0; c < C; ++c) se += expf(o[c] - lmax);
+  const float lse_a = lmax + logf(se);
+  float lc[kMaxComponents];
+  float cmax = -INFINITY;
+  const float HL2PI = 0.91893853320467274f;
+  for (int c = 0; c < C; ++c) {
+    float s = o[c] - lse_a;
+    for (int d = 0; d < d2; ++d) {
+      const float mu = o[C + c * d2 + d];
+      const float ls = fminf(fmaxf(o[C + C * d2 + c * d2 + d], kLogSigMin), kLogSigMax);
+      const float u = (z[d] - mu) * expf(-ls);
+      s += -0.5f * u * u - ls - HL2PI;
+    }
+    lc[c] = s;
+    cmax = fmaxf(cmax, s);
+  }
+  float sc = 0.f;
+  for (int c = 0; c < C; ++c) sc += expf(lc[c] - cmax);
+  const float lq = cmax + logf(sc);
+  const float wn = (float)((double)a.w[b] / *a.wsum);
+  atomicAdd(a.loss, -(double)wn * (double)lq);
+  for (int c = 0; c < C; ++c) {
+    const float gam = expf(lc[c] - lq);
+    const float pi = expf(o[c] - lse_a);
+    g[c] = wn * (pi - gam);
+    for (int d = 0; d < d2; ++d) {
+      const float mu = o[C + c * d2 + d];
+      const float raw = o[C + C * d2 + c * d2 + d];
+      const float ls = fminf(fmaxf(raw, kLogSigMin), kLogSigMax);
+      const float is = expf(-ls);
+      const float u = (z[d] - mu) * is;
+      g[C + c * d2 + d] = -wn * gam * u * is;
+      const bool inside = raw > kLogSigMin && raw < kLogSigMax;
+      g[C + C * d2 + c * d2 + d] = inside ? -wn * gam * (u * u - 1.f) : 0.f;
+    }
+  }
+}
+
+__global__ void wsum_kernel(const float* w, int n, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < n; b += 256) s += (double)w[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// db[n] = sum_b d[b][n] (rows in order)
+__global__ void colsum_kernel(const float* d, int rows, int cols, float* db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= cols) return;
+  float s = 0.f;
+  for (int b = 0; b < rows; ++b) s += d[(long long)b * cols + n];
+  db[n] = s;
+}
+
+__global__ void round_rows_kernel(const float* src, float* dst, long long n, int round) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = round ? round_bf16(src[e]) : src[e];
+}
+
+// minibatch gather: rows perm[b] of F, Z, w
+__global__ void gather_rows_kernel(const float* F, const float* Z, const float* w, const int64_t* perm,
+                                   int nb, int din, int d2, float* Fb, float* Zb, float* wb, int round) {
+  const int b = blockIdx.x;
+  if (b >= nb) return;
+  const long long r = perm[b];
+  for (int c = threadIdx.x; c < din; c += blockDim.x) {
+    const float v = F[r * din + c];
+    Fb[(long long)b * din + c] = round ? round_bf16(v) : v;
+  }
+  for (int c = threadIdx.x; c < d2; c += blockDim.x) Zb[(long long)b * d2 + c] = Z[r * d2 + c];
+  if (threadIdx.x == 0) wb[b] = w[r];
+}
+
+struct AdamArgs {
+  float* W;
+  float* Wq;  // the weights the forward pass uses (bfloat16-rounded weight matrices)
+  float* m;
+  float* v;
+  const float* g;
+  long long n;
+  long long wend[kLayers];  // [wbeg[l], wend[l]) is weight matrix l
+  long long wbeg[kLayers];
+  float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+  int round;
+};
+
+__global__ void adam_kernel(AdamArgs a) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= a.n) return;
+  const float g = a.g[e];
+  const float m = a.b1 * a.m[e] + (1.f - a.b1) * g;
+  const float v = a.b2 * a.v[e] + (1.f - a.b2) * g * g;
+  a.m[e] = m;
+  a.v[e] = v;
+  const float mh = m / a.c1, vh = v / a.c2;
+  const float w = a.W[e] - a.lr * mh / (sqrtf(vh) + a.eps);
+  a.W[e] = w;
+  bool is_w = false;
+  for (int l = 0; l < kLayers; ++l) is_w |= (e >= a.wbeg[l] && e < a.wend[l]);
+  a.Wq[e] = (is_w && a.round) ? round_bf16(w) : w;
+}
+
+__global__ void quantize_params_kernel(const float* W, float* Wq, long long n, AdamArgs seg) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  bool is_w = false;
+  for (int l = 0; l < kLayers; ++l) is_w |= (e >= seg.wbeg[l] && e < seg.wend[l]);
+  Wq[e] = (is_w && seg.round) ? round_bf16(W[e]) : W[e];
+}
+
+// ---- host side ----
+static dpf_status palloc(dpf_proposal& p, void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return set_error(DPF_E_NOMEM, "proposal: device allocation failed");
+  }
+  p.allocs.push_back(*ptr);
+  return DPF_OK;
+}
+
+int dpf_proposal_dout(const dpf_proposal* p) { return p->dout; }
+
+static AdamArgs segments(const dpf_proposal& p) {
+  AdamArgs a{};
+  for (int l = 0; l < kLayers; ++l) {
+    a.wbeg[l] = p.offW[l];
+    a.wend[l] = p.offW[l] + (long long)p.rows[l] * p.cols[l];
+  }
+  a.round = p.bf16 ? 1 : 0;
+  return a;
+}
+
+dpf_status proposal_requantize(dpf_proposal& p) {
+  AdamArgs seg = segments(p);
+  quantize_params_kernel<<<(unsigned)((p.nparams + 255) / 256), 256, 0, p.stream>>>(p.W, p.Wq, p.nparams, seg);
+  p.packed_valid = false;
+  return cuda_error(cudaGetLastError(), "proposal quantize");
+}
+
+// Ensure the per-minibatch workspace holds nb rows.
+static dpf_status workspace(dpf_proposal& p, int nb) {
+  if (nb <= p.ws_rows) return DPF_OK;
+  const size_t H = p.hidden;
+  auto take = [&](float** q, size_t n) { return palloc(p, (void**)q, sizeof(float) * n); };
+  if (take(&p.Fb, (size_t)nb * p.din) || take(&p.Zb, (size_t)nb * p.d2) || take(&p.wb, nb) ||
+      take(&p.h1, nb * H) || take(&p.h2, nb * H) || take(&p.h3, nb * H) || take(&p.ob, (size_t)nb * p.dout) ||
+      take(&p.dA, nb * H) || take(&p.dB, nb * H) || take(&p.dO, (size_t)nb * p.dout) ||
+      palloc(p, (void**)&p.perm_d, sizeof(int64_t) * nb))
+    return DPF_E_NOMEM;
+  p.ws_rows = nb;
+  return DPF_OK;
+}
+
+// Forward and backward over the nb rows already in Fb/Zb/wb: loss into *loss_dev
+// (accumulated), gradients into grad (nparams floats).
+static dpf_status fwd_bwd(dpf_proposal& p, int nb, double* loss_dev, float* grad) {
+  cudaStream_t s = p.stream;
+  const int H = p.hidden, din = p.din, dO = p.dout;
+  const float* Wq = p.Wq;
+  const int rd = p.bf16 ? 1 : 0;
+  const float *W1 = Wq + p.offW[0], *W2 = Wq + p.offW[1], *W3 = Wq + p.offW[2], *W4 = Wq + p.offW[3];
+  const float *b1 = Wq + p.offB[0], *b2 = Wq + p.offB[1], *b3 = Wq + p.offB[2], *b4 = Wq + p.offB[3];
+  // forward: h_l = round(relu(h_{l-1} W_l^T + b_l)), out = h3 W4^T + b4
+  sgemm<false, true, 1>(s, nb, H, din, p.Fb, din, W1, din, p.h1, H, b1, nullptr, rd);
+  sgemm<false, true, 1>(s, nb, H, H, p.h1, H, W2, H, p.h2, H, b2, nullptr, rd);
+  sgemm<false, true, 1>(s, nb, H, H, p.h2, H, W3, H, p.h3, H, b3, nullptr, rd);
+  sgemm<false, true, 2>(s, nb, dO, H, p.h3, H, W4, H, p.ob, dO, b4);
+  wsum_kernel<<<1, 256, 0, s>>>(p.wb, nb, p.wsum_d);
+  HeadArgs ha{p.ob, p.Zb, p.wb, p.wsum_d, p.dO, loss_dev, nb, p.d2, p.C, dO};
+  head_loss_kernel<<<(nb + 127) / 128, 128, 0, s>>>(ha);
+  if (!grad) return cuda_error(cudaGetLastError(), "proposal forward");
+  float *gW1 = grad + p.offW[0], *gW2 = grad + p.offW[1], *gW3 = grad + p.offW[2], *gW4 = grad + p.offW[3];
+  float *gb1 = grad + p.offB[0], *gb2 = grad + p.offB[1], *gb3 = grad + p.offB[2], *gb4 = grad + p.offB[3];
+  // layer 4: dW4 = dO^T h3, db4 = colsum dO, d3 = (dO W4) * (h3 > 0)
+  sgemm<true, false, 0>(s, dO, H, nb, p.dO, dO, p.h3, H, gW4, H);
+  colsum_kernel<<<(dO + 127) / 128, 128, 0, s>>>(p.dO, nb, dO, gb4);
+  sgemm<false, false, 3>(s, nb, H, dO, p.dO, dO, W4, H, p.dA, H, nullptr, p.h3);
+  // layer 3
+  sgemm<true, false, 0>(s, H, H, nb, p.dA, H, p.h2, H, gW3, H);
+  colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dA, nb, H, gb3);
+  sgemm<false, false, 3>(s, nb, H, H, p.dA, H, W3, H, p.dB, H, nullptr, p.h2);
+  // layer 2
+  sgemm<true, false, 0>(s, H, H, nb, p.dB, H, p.h1, H, gW2, H);
+  colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dB, nb, H, gb2);
+  sgemm<false, false, 3>(s, nb, H, H, p.dB, H, W2, H, p.dA, H, nullptr, p.h1);
+  // layer 1
+  sgemm<true, false, 0>(s, H, din, nb, p.dA, H, p.Fb, din, gW1, din);
+  colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dA, nb, H, gb1);
+  return cuda_error(cudaGetLastError(), "proposal backward");
+}
+
+static dpf_status adam(dpf_proposal& p, const float* grad, float lr) {
+  p.adam_t += 1;
+  AdamArgs a = segments(p);
+  a.W = p.W;
+  a.Wq = p.Wq;
+  a.m = p.am;
+  a.v = p.av;
+  a.g = grad;
+  a.n = p.nparams;
+  a.lr = lr;
+  a.b1 = 0.9f;
+  a.b2 = 0.999f;
+  a.eps = 1e-8f;
+  a.c1 = (float)(1.0 - std::pow(0.9, (double)p.adam_t));
+  a.c2 = (float)(1.0 - std::pow(0.999, (double)p.adam_t));
+  adam_kernel<<<(unsigned)((p.nparams + 255) / 256), 256, 0, p.stream>>>(a);
+  p.packed_valid = false;
+  return cuda_error(cudaGetLastError(), "adam");
+}
+
+// splitmix64 (Steele, Lea and Flood 2014): the minibatch order of training.
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace dpf
+
+using namespace dpf;
+
+extern "C" {
+
+dpf_status dpf_proposal_create(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, int32_t components,
+                               void* stream, dpf_proposal** out) {
+  clear_error();
+  if (!out) return set_error(DPF_E_INVALID, "dpf_proposal_create: null output");
+  *out = nullptr;
+  const int din = 2 * d1 + d2 + dy;
+  if (d1 < 1 || d2 < 1 || dy < 1 || din > kMaxDin || d2 > kMaxD2 || hidden < 16 || hidden > kMaxHidden ||
+      hidden % 16 || components < 1 || components > kMaxComponents ||
+      components * (1 + 2 * d2) > kMaxDout)
+    return set_error(DPF_E_INVALID, "dpf_proposal_create: unsupported sizes (din <= 16, d2 <= 8, hidden a "
+                                    "multiple of 16 up to 256, components 1..8, head <= 128)");
+  dpf_proposal* p = new dpf_proposal();
+  p->d1 = d1;
+  p->d2 = d2;
+  p->dy = dy;
+  p->din = din;
+  p->hidden = hidden;
+  p->C = components;
+  p->dout = components * (1 + 2 * d2);
+  p->stream = (cudaStream_t)stream;
+  const int H = hidden;
+  p->rows[0] = H; p->cols[0] = din;
+  p->rows[1] = H; p->cols[1] = H;
+  p->rows[2] = H; p->cols[2] = H;
+  p->rows[3] = p->dout; p->cols[3] = H;
+  long long o = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    p->offW[l] = o;
+    o += (long long)p->rows[l] * p->cols[l];
+    p->offB[l] = o;
+    o += p->rows[l];
+  }
+  p->nparams = o;
+  const size_t bytes = sizeof(float) * (size_t)o;
+  if (palloc(*p, (void**)&p->W, bytes) || palloc(*p, (void**)&p->Wq, bytes) ||
+      palloc(*p, (void**)&p->am, bytes) || palloc(*p, (void**)&p->av, bytes) ||
+      palloc(*p, (void**)&p->grad, bytes) || palloc(*p, (void**)&p->loss_d, sizeof(double)) ||
+      palloc(*p, (void**)&p->wsum_d, sizeof(double))) {
+    dpf_proposal_destroy(p);
+    return DPF_E_NOMEM;
+  }
+  cudaMemsetAsync(p->W, 0, bytes, p->stream);
+  cudaMemsetAsync(p->Wq, 0, bytes, p->stream);
+  cudaMemsetAsync(p->am, 0, bytes, p->stream);
+  cudaMemsetAsync(p->av, 0, bytes, p->stream);
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    dpf_proposal_destroy(p);
+    return cuda_error(e, "dpf_proposal_create");
+  }
+  *out = p;
+  return DPF_OK;
+}
+
+dpf_status dpf_proposal_num_params(const dpf_proposal* p, int64_t* n) {
+  clear_error();
+  if (!p || !n) return set_error(DPF_E_INVALID, "dpf_proposal_num_params: null argument");
+  *n = p->nparams;
+  return DPF_OK;
+}
+
+dpf_status dpf_proposal_set_bf16(dpf_proposal* p, int32_t enable) {
+  clear_error();
+  if (!p) return set_error(DPF_E_INVALID, "dpf_proposal_set_bf16: null proposal");
+  p->bf16 = enable != 0;
+  dpf_status st = proposal_requantize(*p);
+  if (st) return st;
+  return cuda_error(cudaStreamSynchronize(p->stream), "dpf_proposal_set_bf16");
+}
+
+dpf_status dpf_proposal_set_weights(dpf_proposal* p, const float* params, int64_t n) {
+  clear_error();
+  if (!p || !params || n != p->nparams)
+    return set_error(DPF_E_INVALID, "dpf_proposal_set_weights: need exactly num_params floats");
+  cudaError_t e = cudaMemcpyAsync(p->W, params, sizeof(float) * n, cudaMemcpyHostToDevice, p->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_proposal_set_weights");
+  cudaMemsetAsync(p->am, 0, sizeof(float) * n, p->stream);
+  cudaMemsetAsync(p->av, 0, sizeof(float) * n, p->stream);
+  p->adam_t = 0;
+  dpf_status st = proposal_requantize(*p);
+  if (st) return st;
+  return cuda_error(cudaStreamSynchronize(p->stream), "dpf_proposal_set_weights");
+}
+
+dpf_status dpf_proposal_get_weights(const dpf_proposal* p, float* params, int64_t n) {
+  clear_error();
+  if (!p || !params || n != p->nparams)
+    return set_error(DPF_E_INVALID, "dpf_proposal_get_weights: need exactly num_params floats");
+  cudaError_t e = cudaMemcpyAsync(params, p->W, sizeof(float) * n, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  return cuda_error(e, "dpf_proposal_get_weights");
+}
+
+dpf_status dpf_proposal_loss_grad(dpf_proposal* p, const float* F, const float* Z, const float* w, int64_t n,
+                                  double* loss, float* grad_dev) {
+  clear_error();
+  if (!p || !F || !Z || !w || n < 1 || n > (1 << 24))
+    return set_error(DPF_E_INVALID, "dpf_proposal_loss_grad: bad arguments");
+  dpf_status st = workspace(*p, (int)n);
+  if (st) return st;
+  cudaStream_t s = p->stream;
+  const int rd = p->bf16 ? 1 : 0;
+  round_rows_kernel<<<(unsigned)((n * p->din + 255) / 256), 256, 0, s>>>(F, p->Fb, n * p->din, rd);
+  cudaMemcpyAsync(p->Zb, Z, sizeof(float) * n * p->d2, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->wb, w, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(p->loss_d, 0, sizeof(double), s);
+  st = fwd_bwd(*p, (int)n, p->loss_d, grad_dev);
+  if (st) return st;
+  double h = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&h, p->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_proposal_loss_grad");
+  if (loss) *loss = h;
+  return DPF_OK;
+}
+
+dpf_status dpf_proposal_adam_step(dpf_proposal* p, const float* grad_dev, float lr) {
+  clear_error();
+  if (!p || !grad_dev || !(lr > 0.f)) return set_error(DPF_E_INVALID, "dpf_proposal_adam_step: bad arguments");
+  dpf_status st = adam(*p, grad_dev, lr);
+  if (st) return st;
+  return cuda_error(cudaStreamSynchronize(p->stream), "dpf_proposal_adam_step");
+}
+
+dpf_status dpf_proposal_train(dpf_proposal* p, const float* F, const float* Z, const float* w, int64_t n,
+                              int32_t batch, int32_t epochs, float lr, uint64_t seed, double* losses) {
+  clear_error();
+  if (!p || !F || !Z || !w || n < 1 || batch < 1 || batch > (1 << 16) || epochs < 1 || !(lr > 0.f))
+    return set_error(DPF_E_INVALID, "dpf_proposal_train: bad arguments");
+  const int nb_max = (int)std::min<int64_t>(batch, n);
+  dpf_status st = workspace(*p, nb_max);
+  if (st) return st;
+  cudaStream_t s = p->stream;
+  const int rd = p->bf16 ? 1 : 0;
+  std::vector<int64_t> perm(n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = i;
+  uint64_t rs = seed;
+  int64_t* perm_dev = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&perm_dev, sizeof(int64_t) * n, s);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_proposal_train: allocation");
+  std::vector<double> ep_loss(epochs, 0.0);
+  double* eloss_d = nullptr;
+  e = cudaMallocAsync((void**)&eloss_d, sizeof(double) * epochs, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(perm_dev, s);
+    return cuda_error(e, "dpf_proposal_train: allocation");
+  }
+  cudaMemsetAsync(eloss_d, 0, sizeof(double) * epochs, s);
+  const int64_t nbatches = (n + nb_max - 1) / nb_max;
+  for (int ep = 0; ep < epochs && !st; ++ep) {
+    for (int64_t i = n - 1; i > 0; --i) {  // Fisher-Yates with splitmix64
+      const int64_t j = (int64_t)(splitmix64(rs) % (uint64_t)(i + 1));
+      std::swap(perm[i], perm[j]);
+    }
+    e = cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // perm is rewritten next epoch
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "dpf_proposal_train: permutation");
+      break;
+    }
+    for (int64_t bi = 0; bi < nbatches && !st; ++bi) {
+      const int64_t b0 = bi * nb_max;
+      const int nb = (int)std::min<int64_t>(nb_max, n - b0);
+      gather_rows_kernel<<<nb, 32, 0, s>>>(F, Z, w, perm_dev + b0, nb, p->din, p->d2, p->Fb, p->Zb, p->wb, rd);
+      st = fwd_bwd(*p, nb, eloss_d + ep, p->grad);
+      if (!st) st = adam(*p, p->grad, lr);
+    }
+  }
+  if (!st) {
+    e = cudaMemcpyAsync(ep_loss.data(), eloss_d, sizeof(double) * epochs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "dpf_proposal_train");
+  }
+  cudaFreeAsync(perm_dev, s);
+  cudaFreeAsync(eloss_d, s);
+  if (!st && losses)
+    for (int ep = 0; ep < epochs; ++ep) losses[ep] = ep_loss[ep] / (double)nbatches;
+  return st;
+}
+
+void dpf_proposal_destroy(dpf_proposal* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (void* q : p->allocs) cudaFree(q);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// The learned inner proposal object (see dpf_learned.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "dpf_internal.h"
+
+namespace dpf {
+
+constexpr int kLayers = 4;           // three hidden layers and the head
+constexpr int kMaxComponents = 8;
+constexpr int kMaxDin = 16;          // inputs, padded to one BF16 MMA K step
+constexpr int kMaxD2 = 8;
+constexpr int kMaxHidden = 256;
+constexpr int kMaxDout = 128;
+constexpr float kLogSigMin = -7.f, kLogSigMax = 5.f;
+
+dpf_status proposal_requantize(dpf_proposal& p);
+
+}  // namespace dpf
+
+struct dpf_proposal {
+  int d1 = 0, d2 = 0, dy = 0, din = 0, hidden = 0, C = 0, dout = 0;
+  long long nparams = 0;
+  long long offW[dpf::kLayers] = {}, offB[dpf::kLayers] = {};
+  int rows[dpf::kLayers] = {}, cols[dpf::kLayers] = {};
+  cudaStream_t stream = nullptr;
+  bool bf16 = true;  // the forward pass rounds as the tensor-core pass does
+  float* W = nullptr;      // FP32 master parameters
+  float* Wq = nullptr;     // what the forward pass uses (bfloat16-rounded matrices when bf16)
+  float* am = nullptr;     // Adam moments
+  float* av = nullptr;
+  float* grad = nullptr;
+  double* loss_d = nullptr;
+  double* wsum_d = nullptr;
+  int adam_t = 0;
+  // minibatch workspace
+  int ws_rows = 0;
+  float *Fb = nullptr, *Zb = nullptr, *wb = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+  float *ob = nullptr, *dA = nullptr, *dB = nullptr, *dO = nullptr;
+  int64_t* perm_d = nullptr;
+  // weights packed for the tensor-core forward pass (rebuilt when stale)
+  bool packed_valid = false;
+  void* packed = nullptr;
+  size_t packed_bytes = 0;
+  std::vector<void*> allocs;
+};

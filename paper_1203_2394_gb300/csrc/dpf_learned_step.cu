@@ -1,0 +1,723 @@
+// The learned proposal on the tensor cores: the MLP forward pass of 128-row tiles
+// (tcgen05 kind::f16 with BF16 operands, FP32 accumulators in TMEM), used alone
+// (dpf_proposal_forward) and as the inner update of the filter step (selection,
+// local resampling and feature rows before it; the mixture draw and the importance
+// weights after it), plus the recording of training rows.
+//
+// Per tile, one thread per row: layer 1 (K = 16 padded inputs) and the head
+// (N = 32 padded outputs) have their weights resident in shared memory; the two
+// 256 x 256 layers stream their weights through a three-stage ring of 32 KB
+// chunks (64 K-columns each) copied by cp.async.bulk from a packed copy in global
+// memory, so the copy of the next chunks overlaps the MMAs of the current ones.
+// Every hidden layer's accumulator (128 x 256 FP32, TMEM columns 0..255) is read
+// back row by row, biased, passed through ReLU, rounded to BF16 and written as
+// the next layer's A operand (K-major, no swizzle). All waits are bounded.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "dpf_learned.h"
+#include "dpf_tc.cuh"
+#include "dpf_variant.cuh"
+
+namespace dpf {
+
+constexpr int LH = 256;                // hidden width of the tensor-core pass
+constexpr int LDIN = 16;               // inputs padded to one K step
+constexpr int LNP = 32;                // head outputs padded to an MMA N
+constexpr int LKCH = 64;               // K columns per streamed chunk
+constexpr int LNCH = LH / LKCH;        // chunks per hidden layer
+constexpr int LSTAGES = 3;
+constexpr uint32_t LCHUNK = LH * LKCH * 2;  // bytes of one chunk
+constexpr int L_SPIN = 1 << 22;
+constexpr uint32_t LTMEM_COLS = 512;
+
+// packed global layout (bytes)
+constexpr size_t PK_W1 = 0;
+constexpr size_t PK_W2 = PK_W1 + (size_t)LH * LDIN * 2;
+constexpr size_t PK_W3 = PK_W2 + (size_t)LNCH * LCHUNK;
+constexpr size_t PK_W4 = PK_W3 + (size_t)LNCH * LCHUNK;
+constexpr size_t PK_B = PK_W4 + (size_t)LNP * LH * 2;
+constexpr size_t PK_BYTES = PK_B + sizeof(float) * (3 * LH + LNP);
+
+// shared-memory layout (bytes)
+constexpr uint32_t SM_ACT = 0;                              // 128 x 256 bf16, kc16 = 32
+constexpr uint32_t SM_IN = SM_ACT + 128 * LH * 2;           // 128 x 16 bf16, kc16 = 2
+constexpr uint32_t SM_W1 = SM_IN + 128 * LDIN * 2;          // 256 x 16, kc16 = 2
+constexpr uint32_t SM_W4 = SM_W1 + LH * LDIN * 2;           // 32 x 256, kc16 = 32
+constexpr uint32_t SM_RING = SM_W4 + LNP * LH * 2;          // 3 x (256 x 64), kc16 = 8
+constexpr uint32_t SM_BIAS = SM_RING + LSTAGES * LCHUNK;    // b1 b2 b3 (256 each), b4 (32)
+constexpr uint32_t SM_CUM = SM_BIAS + sizeof(float) * (3 * LH + LNP);  // 128 uint32
+constexpr uint32_t SM_RED = SM_CUM + 128 * 4;               // 8 floats / words
+constexpr uint32_t SM_BYTES = SM_RED + 64;
+
+// Pack one FP32 matrix (rows x cols, row-major) into BF16 K-major chunks of kch
+// columns, rows padded to rows_pad and columns to a multiple of kch with zeros.
+__global__ void pack_matrix_kernel(const float* __restrict__ W, int rows, int cols, int rows_pad, int kch,
+                                   int nchunks, unsigned char* __restrict__ dst) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)rows_pad * kch * nchunks;
+  if (e >= total) return;
+  const int n = (int)(e / ((long long)kch * nchunks));
+  const int k = (int)(e % ((long long)kch * nchunks));
+  const int ch = k / kch, kl = k % kch;
+  const float v = (n < rows && k < cols) ? W[(long long)n * cols + k] : 0.f;
+  const size_t off = (size_t)ch * rows_pad * kch * 2 + tc::kmajor_offset(n, 2 * kl, kch * 2 / 16);
+  *(__nv_bfloat16*)(dst + off) = __float2bfloat16_rn(v);
+}
+
+__global__ void pack_bias_kernel(const float* __restrict__ b1, const float* __restrict__ b2,
+                                 const float* __restrict__ b3, const float* __restrict__ b4, int dout,
+                                 float* __restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 3 * LH) dst[e] = e < LH ? b1[e] : e < 2 * LH ? b2[e - LH] : b3[e - 2 * LH];
+  else if (e < 3 * LH + LNP) dst[e] = (e - 3 * LH) < dout ? b4[e - 3 * LH] : 0.f;
+}
+
+static dpf_status pack(dpf_proposal& p) {
+  if (p.packed_valid) return DPF_OK;
+  if (!p.packed) {
+    cudaError_t e = cudaMalloc(&p.packed, PK_BYTES);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p.packed = nullptr;
+      return set_error(DPF_E_NOMEM, "proposal: packed weights");
+    }
+    p.allocs.push_back(p.packed);
+    p.packed_bytes = PK_BYTES;
+  }
+  cudaStream_t s = p.stream;
+  unsigned char* d = (unsigned char*)p.packed;
+  const float* Wq = p.Wq;
+  auto launch = [&](const float* W, int rows, int cols, int rows_pad, int kch, int nch, size_t off) {
+    const long long total = (long long)rows_pad * kch * nch;
+    pack_matrix_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(W, rows, cols, rows_pad, kch, nch, d + off);
+  };
+  launch(Wq + p.offW[0], LH, p.din, LH, LDIN, 1, PK_W1);
+  launch(Wq + p.offW[1], LH, LH, LH, LKCH, LNCH, PK_W2);
+  launch(Wq + p.offW[2], LH, LH, LH, LKCH, LNCH, PK_W3);
+  launch(Wq + p.offW[3], p.dout, LH, LNP, LH, 1, PK_W4);
+  pack_bias_kernel<<<(3 * LH + LNP + 255) / 256, 256, 0, s>>>(Wq + p.offB[0], Wq + p.offB[1], Wq + p.offB[2],
+                                                               Wq + p.offB[3], p.dout, (float*)(d + PK_B));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "proposal pack");
+  p.packed_valid = true;
+  return DPF_OK;
+}
+
+struct LearnArgs {
+  const unsigned char* wp;  // packed weights (PK_* layout)
+  int din, dout, C;
+  // forward-only mode
+  const float* F;
+  float* out;
+  long long nrows;
+  // filter mode
+  float* dbg_head;  // N M x dout head outputs, or null
+  uint32_t scaleC;  // 2^(31 - ceil log2 C)
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+
+// Read one hidden accumulator row (256 FP32 columns of TMEM), add the bias, ReLU,
+// round to BF16 and store it as row r of the activation tile.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr_row, const float* bias, unsigned char* act, int r) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < LH; c0 += 16) {
+    float v[16];
+    tc::ld16(taddr_row + (uint32_t)c0, v);
+    uint4 q0, q1;
+    q0.x = pack_bf16x2(fmaxf(v[0] + bias[c0 + 0], 0.f), fmaxf(v[1] + bias[c0 + 1], 0.f));
+    q0.y = pack_bf16x2(fmaxf(v[2] + bias[c0 + 2], 0.f), fmaxf(v[3] + bias[c0 + 3], 0.f));
+    q0.z = pack_bf16x2(fmaxf(v[4] + bias[c0 + 4], 0.f), fmaxf(v[5] + bias[c0 + 5], 0.f));
+    q0.w = pack_bf16x2(fmaxf(v[6] + bias[c0 + 6], 0.f), fmaxf(v[7] + bias[c0 + 7], 0.f));
+    q1.x = pack_bf16x2(fmaxf(v[8] + bias[c0 + 8], 0.f), fmaxf(v[9] + bias[c0 + 9], 0.f));
+    q1.y = pack_bf16x2(fmaxf(v[10] + bias[c0 + 10], 0.f), fmaxf(v[11] + bias[c0 + 11], 0.f));
+    q1.z = pack_bf16x2(fmaxf(v[12] + bias[c0 + 12], 0.f), fmaxf(v[13] + bias[c0 + 13], 0.f));
+    q1.w = pack_bf16x2(fmaxf(v[14] + bias[c0 + 14], 0.f), fmaxf(v[15] + bias[c0 + 15], 0.f));
+    *(uint4*)(act + tc::kmajor_offset(r, 2 * c0, 32)) = q0;
+    *(uint4*)(act + tc::kmajor_offset(r, 2 * c0 + 16, 32)) = q1;
+  }
+}
+
+// Group reductions over the M consecutive rows of a tile (M in {32, 64, 128}).
+__device__ __forceinline__ float group_max(float v, int M, float* red) {
+  v = warp_max(v);
+  if (M <= 32) return v;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  const int g0 = (w * 32 / M) * (M / 32);
+  float m = red[g0];
+  for (int q = 1; q < M / 32; ++q) m = fmaxf(m, red[g0 + q]);
+  return m;
+}
+__device__ __forceinline__ float group_sum(float v, int M, float* red) {
+  v = warp_sum(v);
+  if (M <= 32) return v;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  const int g0 = (w * 32 / M) * (M / 32);
+  float s = 0.f;
+  for (int q = 0; q < M / 32; ++q) s += red[g0 + q];
+  return s;
+}
+
+// MODE 0: head outputs of feature rows; MODE 1: the filter's inner update.
+template <int MODE, int D1, int D2, int DY, bool XZ>
+__global__ void __launch_bounds__(128, 1)
+    learned_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const __grid_constant__ StepArgs<float> a,
+                   const __grid_constant__ LearnArgs la) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t full[LSTAGES], empty[LSTAGES], mbar;
+  __shared__ uint32_t s_taddr;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  unsigned char* act = sm + SM_ACT;
+  unsigned char* in = sm + SM_IN;
+  float* bias = (float*)(sm + SM_BIAS);
+  uint32_t* cum = (uint32_t*)(sm + SM_CUM);
+  float* red = (float*)(sm + SM_RED);
+  const float NEG = -INFINITY;
+
+  const int M = MODE == 1 ? a.M : 128;
+  const long long rows_total = MODE == 1 ? a.N * (long long)a.M : la.nrows;
+  const long long ntiles = (rows_total + 127) / 128;
+  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total_chunks = my_tiles * 2 * LNCH;
+
+  // ---- set-up: barriers, TMEM, resident weights and biases ----
+  if (tid == 0) {
+    for (int s = 0; s < LSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&mbar, 1);
+    mbar_fence_init();
+  }
+  if (w == 0) {
+    tc::tmem_alloc(&s_taddr, LTMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  for (int e = tid; e < (int)(LH * LDIN * 2 / 16); e += 128)
+    ((uint4*)(sm + SM_W1))[e] = ((const uint4*)(la.wp + PK_W1))[e];
+  for (int e = tid; e < (int)(LNP * LH * 2 / 16); e += 128)
+    ((uint4*)(sm + SM_W4))[e] = ((const uint4*)(la.wp + PK_W4))[e];
+  for (int e = tid; e < 3 * LH + LNP; e += 128) bias[e] = ((const float*)(la.wp + PK_B))[e];
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = s_taddr;
+  const uint32_t trow = taddr + ((uint32_t)(32 * w) << 16);  // this warp's TMEM lanes
+  bool ok = true;
+
+  auto chunk_src = [&](long long c) -> const unsigned char* {
+    const int q = (int)(c % (2 * LNCH));
+    return la.wp + (q < LNCH ? PK_W2 + (size_t)q * LCHUNK : PK_W3 + (size_t)(q - LNCH) * LCHUNK);
+  };
+  auto load_chunk = [&](long long c) {  // thread 0 only
+    const int s = (int)(c % LSTAGES);
+    mbar_arrive_tx(&full[s], LCHUNK);
+    bulk_load(sm + SM_RING + s * LCHUNK, chunk_src(c), LCHUNK, &full[s]);
+  };
+  if (tid == 0)
+    for (long long c = 0; c < std::min<long long>(LSTAGES, total_chunks); ++c) load_chunk(c);
+  long long c_use = 0;      // next chunk to consume (thread 0)
+  uint32_t mph = 0;         // phase of mbar (all threads)
+
+  const uint32_t id_h = tc::instr_desc(tc::FMT_BF16, 128, LH);
+  const uint32_t id_o = tc::instr_desc(tc::FMT_BF16, 128, LNP);
+
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row = tile * 128 + tid;
+    const bool live = row < rows_total;
+    // ---- prologue: this row's input features ----
+    float feat[LDIN];
+#pragma unroll
+    for (int k = 0; k < LDIN; ++k) feat[k] = 0.f;
+    // filter-mode registers
+    long long g = 0;
+    int j = 0, anc_g = 0;
+    float xa[D1], xt[D1], zb[D2];
+    if (MODE == 0) {
+      if (live)
+        for (int k = 0; k < la.din; ++k) feat[k] = la.F[row * la.din + k];
+    } else {
+      g = row / M;
+      j = (int)(row % M);
+      const long long gg = live ? g : 0;
+      anc_g = a.anc[gg];
+      const long long NM = a.N * (long long)M;
+      // selection of x_{t-1} among the ancestor's look-ahead draws (one SIR draw)
+      const int L = a.L;
+      int msel = 0;
+      {
+        const float l0 = lane < L ? a.lwh_old[(long long)anc_g * L + lane] : NEG;
+        const float l1 = lane + 32 < L ? a.lwh_old[(long long)anc_g * L + lane + 32] : NEG;
+        // every lane of a warp holds one group (M >= 32): the warp's lanes read that group
+        const float mx = warp_max(fmaxf(l0, l1));
+        const uint32_t c0 = lane < L ? (uint32_t)floorf(exp2f((l0 - mx) * 1.4426950408889634f) * a.scaleL) : 0u;
+        const uint32_t c1 = lane + 32 < L ? (uint32_t)floorf(exp2f((l1 - mx) * 1.4426950408889634f) * a.scaleL) : 0u;
+        uint32_t s0 = c0, s1 = c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
+          if (lane >= o) {
+            s0 += n0;
+            s1 += n1;
+          }
+        }
+        const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
+        const uint64_t Cs = (uint64_t)tot0 + tot1;
+        const uint32_t usel = philox(ctr(a.t - 1, (uint32_t)gg, P_SEL, 0u, 0u), a.key).x;
+        const uint64_t rhs = (uint64_t)usel * Cs;
+        const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
+        const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
+        msel = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
+        if ((Cs == 0 || msel >= L) && live && j == 0) atomicOr(a.err, ERR_NUMERIC);
+        if (msel >= L) msel = L - 1;
+      }
+#pragma unroll
+      for (int c = 0; c < D1; ++c) {
+        xt[c] = a.xbb_old[((long long)anc_g * L + msel) * D1 + c];
+        xa[c] = a.x_old[(long long)anc_g * a.xp + c];
+      }
+      if (live && j == 0) {
+        a.sel[g] = msel;
+        for (int c = 0; c < a.xp; ++c) a.x_new[g * a.xp + c] = c < D1 ? xt[c < D1 ? c : 0] : 0.f;
+      }
+      // local resampling of the ancestor's inner set by alpha = lq + log p(x_t | x_a, z)
+      float al = a.lq_old[(long long)anc_g * M + j];
+      if (XZ) {
+        float mxa[D1], wres[D1];
+        mu_x(mc, xa, a.gcos_prev, mxa);
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          float v = 0.f;
+#pragma unroll
+          for (int c = 0; c <= r; ++c) v += mc.LqxInv[r][c] * (xt[c] - mxa[c]);
+          wres[r] = v;
+        }
+        float q = 0.f;
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          float v = wres[r];
+#pragma unroll
+          for (int c = 0; c < D2; ++c) v -= mc.WAxz[r][c] * a.z_old[c * NM + (long long)anc_g * M + j];
+          q += v * v;
+        }
+        al -= 0.5f * q;
+      }
+      const float amax = group_max(al, M, red);
+      const uint32_t cq = (uint32_t)floorf(exp2f((al - amax) * 1.4426950408889634f) * a.scaleM);
+      uint32_t inc = cq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += n;
+      }
+      __syncthreads();
+      if (lane == 31) ((uint32_t*)red)[8 + w] = inc;  // warp totals after the float slots
+      __syncthreads();
+      const int gw0 = (w * 32 / M) * (M / 32);  // first warp of this group
+      for (int q = gw0; q < w; ++q) inc += ((uint32_t*)red)[8 + q];
+      cum[tid] = inc;
+      __syncthreads();
+      const int gbase = (tid / M) * M;
+      const uint32_t Cg = cum[gbase + M - 1];
+      if (Cg == 0 && live && j == 0) atomicOr(a.err, ERR_NUMERIC);
+      const uint32_t uin = philox(ctr(a.t - 1, (uint32_t)gg, P_INNER, 0u, 0u), a.key).x;
+      const int b = sys_local_pick(cum + gbase, M, Cg, M, j, uin);
+      if (a.dbg_b && live) a.dbg_b[g * M + j] = b;
+#pragma unroll
+      for (int c = 0; c < D2; ++c) zb[c] = a.z_old[c * NM + (long long)anc_g * M + b];
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < D1; ++c) {
+          feat[c] = xa[c];
+          feat[D1 + c] = xt[c];
+        }
+#pragma unroll
+        for (int c = 0; c < D2; ++c) feat[2 * D1 + c] = zb[c];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) feat[2 * D1 + D2 + q] = a.y_prev[q];
+      }
+    }
+    {
+      uint4 q0, q1;
+      q0.x = pack_bf16x2(feat[0], feat[1]);
+      q0.y = pack_bf16x2(feat[2], feat[3]);
+      q0.z = pack_bf16x2(feat[4], feat[5]);
+      q0.w = pack_bf16x2(feat[6], feat[7]);
+      q1.x = pack_bf16x2(feat[8], feat[9]);
+      q1.y = pack_bf16x2(feat[10], feat[11]);
+      q1.z = pack_bf16x2(feat[12], feat[13]);
+      q1.w = pack_bf16x2(feat[14], feat[15]);
+      *(uint4*)(in + tc::kmajor_offset(tid, 0, 2)) = q0;
+      *(uint4*)(in + tc::kmajor_offset(tid, 16, 2)) = q1;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+
+    // ---- layer 1 ----
+    if (tid == 0) {
+      tc::fence_after();
+      tc::mma_f16(taddr, tc::smem_desc(smem_addr(in), 2), tc::smem_desc(smem_addr(sm + SM_W1), 2), id_h, 0u);
+      tc::commit(&mbar);
+    }
+    ok &= tc::bar_wait(&mbar, mph, L_SPIN);
+    mph ^= 1u;
+    tc::fence_after();
+    hidden_epilogue(trow, bias, act, tid);
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+
+    // ---- layers 2 and 3 (streamed weights) ----
+#pragma unroll 1
+    for (int layer = 0; layer < 2; ++layer) {
+      if (tid == 0) {
+        tc::fence_after();
+        for (int k = 0; k < LNCH; ++k) {
+          const long long c = c_use++;
+          const int s = (int)(c % LSTAGES);
+          if (!tc::bar_wait(&full[s], (uint32_t)((c / LSTAGES) & 1), L_SPIN)) ok = false;
+          const uint32_t sa = smem_addr(act), sb = smem_addr(sm + SM_RING + s * LCHUNK);
+#pragma unroll
+          for (int ks = 0; ks < LKCH / 16; ++ks)
+            tc::mma_f16(taddr, tc::smem_desc(sa + (uint32_t)(k * 8 + ks * 2) * 128u, 32),
+                        tc::smem_desc(sb + (uint32_t)ks * 256u, 8), id_h, (k > 0 || ks > 0) ? 1u : 0u);
+          tc::commit(&empty[s]);
+          // refill the stage of the previous chunk (likely free by now) with chunk c + 2
+          if (c >= 1 && c + LSTAGES - 1 < total_chunks) {
+            const long long cp = c - 1;
+            if (!tc::bar_wait(&empty[cp % LSTAGES], (uint32_t)((cp / LSTAGES) & 1), L_SPIN)) ok = false;
+            load_chunk(c + LSTAGES - 1);
+          }
+        }
+        tc::commit(&mbar);
+      }
+      ok &= tc::bar_wait(&mbar, mph, L_SPIN);
+      mph ^= 1u;
+      tc::fence_after();
+      hidden_epilogue(trow, bias + (layer + 1) * LH, act, tid);
+      tc::fence_proxy_async();
+      tc::fence_before();
+      __syncthreads();
+    }
+
+    // ---- head ----
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t sa = smem_addr(act), sb = smem_addr(sm + SM_W4);
+#pragma unroll
+      for (int ks = 0; ks < LH / 16; ++ks)
+        tc::mma_f16(taddr + LH, tc::smem_desc(sa + (uint32_t)ks * 256u, 32), tc::smem_desc(sb + (uint32_t)ks * 256u, 32),
+                    id_o, ks > 0 ? 1u : 0u);
+      tc::commit(&mbar);
+    }
+    ok &= tc::bar_wait(&mbar, mph, L_SPIN);
+    mph ^= 1u;
+    tc::fence_after();
+    float o[LNP];
+    {
+      float v[16];
+      tc::ld16(trow + LH, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = v[q] + bias[3 * LH + q];
+      tc::ld16(trow + LH + 16, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[16 + q] = v[q] + bias[3 * LH + 16 + q];
+    }
+    tc::fence_before();
+
+    if (MODE == 0) {
+      if (live)
+        for (int q = 0; q < la.dout; ++q) la.out[row * la.dout + q] = o[q];
+    } else {
+      // ---- the mixture draw and the importance weight ----
+      const int C = la.C;
+      if (la.dbg_head && live)
+        for (int q = 0; q < la.dout; ++q) la.dbg_head[row * la.dout + q] = o[q];
+      float lmax = NEG;
+      for (int c = 0; c < C; ++c) lmax = fmaxf(lmax, o[c]);
+      float se = 0.f;
+      for (int c = 0; c < C; ++c) se += expf(o[c] - lmax);
+      const float lse_a = lmax + logf(se);
+      // component: one-draw systematic pick over exp(logit - max), quantised
+      uint32_t cumc[kMaxComponents];
+      uint32_t run = 0;
+      for (int c = 0; c < C; ++c) {
+        run += (uint32_t)floorf(exp2f((o[c] - lmax) * 1.4426950408889634f) * (float)la.scaleC);
+        cumc[c] = run;
+      }
+      const uint32_t uc = philox(ctr(a.t - 1, (uint32_t)g, P_LCOMP, (uint32_t)j, 0u), a.key).x;
+      const uint64_t rhs = (uint64_t)uc * run;
+      int comp = C - 1;
+      for (int c = C - 1; c >= 0; --c)
+        if (((uint64_t)cumc[c] << 32) > rhs) comp = c;
+      float eps[D2];
+      normals<D2>(a.key, a.t - 1, (uint32_t)g, P_PROP, (uint32_t)j, eps);
+      float z[D2];
+      for (int d = 0; d < D2; ++d) {
+        const float mu = o[C + comp * D2 + d];
+        const float ls = fminf(fmaxf(o[C + C * D2 + comp * D2 + d], kLogSigMin), kLogSigMax);
+        z[d] = mu + expf(ls) * eps[d];
+      }
+      // log q(z): LSE over components (the -d2/2 log 2 pi constant cancels in lq)
+      float lc[kMaxComponents];
+      float cmax = NEG;
+      for (int c = 0; c < C; ++c) {
+        float s = o[c] - lse_a;
+        for (int d = 0; d < D2; ++d) {
+          const float mu = o[C + c * D2 + d];
+          const float ls = fminf(fmaxf(o[C + C * D2 + c * D2 + d], kLogSigMin), kLogSigMax);
+          const float u = (z[d] - mu) * expf(-ls);
+          s += -0.5f * u * u - ls;
+        }
+        lc[c] = s;
+        cmax = fmaxf(cmax, s);
+      }
+      float sc = 0.f;
+      for (int c = 0; c < C; ++c) sc += expf(lc[c] - cmax);
+      const float lqz = cmax + logf(sc);
+      // log N(z; A_zx x_a + A_zz z_b, Q_z) up to its constant
+      float rp[D2];
+#pragma unroll
+      for (int r = 0; r < D2; ++r) {
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < D1; ++c) m += mc.Azx[r][c] * xa[c];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) m += mc.Azz[r][c] * zb[c];
+        float v = z[r] - m;
+#pragma unroll
+        for (int c = 0; c < r; ++c) v -= mc.Lqz[r][c] * rp[c];
+        rp[r] = v / mc.Lqz[r][r];
+      }
+      float lpz = 0.f;
+#pragma unroll
+      for (int r = 0; r < D2; ++r) lpz -= 0.5f * rp[r] * rp[r];
+      // log p(y | x_t, z) up to its constant
+      float hx[DY];
+      h_x(mc, xt, hx);
+      float res[DY];
+#pragma unroll
+      for (int q = 0; q < DY; ++q) {
+        float v = a.y_prev[q] - hx[q];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) v -= mc.Hz[q][c] * z[c];
+        res[q] = v;
+      }
+      float lpy = 0.f;
+#pragma unroll
+      for (int q = 0; q < DY; ++q) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+        lpy -= 0.5f * v * v;
+      }
+      float lr = lpz - lqz + lpy;
+      if (!live) lr = NEG;
+      const float gm = group_max(lr, M, red);
+      const float gs = group_sum(live ? expf(lr - gm) : 0.f, M, red);
+      const float lqn = lr - gm - logf(gs);
+      if (live) {
+        const long long NM = a.N * (long long)M;
+#pragma unroll
+        for (int d = 0; d < D2; ++d) a.z_new[d * NM + row] = z[d];
+        a.lq_new[row] = lqn;
+        if (!(lqn == lqn)) atomicOr(a.err, ERR_NUMERIC);
+      }
+    }
+    __syncthreads();  // TMEM and the tiles are free for the next tile
+  }
+  if (!ok && lane == 0) atomicOr(MODE == 1 ? a.err : la.err, ERR_TIMEOUT);
+  tc::fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(taddr, LTMEM_COLS);
+}
+
+template <int MODE, int D1, int D2, int DY, bool XZ>
+static dpf_status launch_learned(const MC<float, D1, D2, DY>& mc, const StepArgs<float>& a, const LearnArgs& la,
+                                 long long rows, cudaStream_t s) {
+  auto k = learned_kernel<MODE, D1, D2, DY, XZ>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+    if (e != cudaSuccess) return cuda_error(e, "learned kernel attribute");
+    attr = true;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (rows + 127) / 128;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, nsm));
+  k<<<grid, 128, SM_BYTES, s>>>(mc, a, la);
+  return cuda_error(cudaGetLastError(), "learned kernel launch");
+}
+
+static uint32_t scale_for(int n) {
+  return 1u << (31 - ceil_log2_i(n));
+}
+
+// The inner update of the coming step with the learned proposal (the variant
+// (FP32, 2, 2, 2)); then the look-ahead runs alone from the materialised state.
+dpf_status learned_inner_step(Ctx& x) {
+  dpf_proposal& p = *x.proposal;
+  dpf_status st = pack(p);
+  if (st) return st;
+  typedef VariantImpl<float, 2, 2, 2, 0> V;
+  StepArgs<float> a{};
+  V::fill_args(x, a);
+  a.xp = x.xp;  // the padded x row (set by the step geometry for the other kernels)
+  LearnArgs la{};
+  la.wp = (const unsigned char*)p.packed;
+  la.din = p.din;
+  la.dout = p.dout;
+  la.C = p.C;
+  la.dbg_head = x.debug ? (float*)x.dbg_head : nullptr;
+  la.scaleC = scale_for(p.C);
+  la.err = x.err;
+  const MC<float, 2, 2, 2>& mc = *reinterpret_cast<const MC<float, 2, 2, 2>*>(x.mconst.data());
+  const long long rows = x.N * (long long)x.M;
+  return x.hm.xz ? launch_learned<1, 2, 2, 2, true>(mc, a, la, rows, x.stream)
+                 : launch_learned<1, 2, 2, 2, false>(mc, a, la, rows, x.stream);
+}
+
+// ---- training rows from the last inner update ----
+struct RecordArgs {
+  const float *x_old, *x_new, *z_old, *z_new, *lq_new, *y_prev;
+  const int32_t *anc_prev, *bidx;
+  long long N, i0, n_outer;
+  int M, d1, d2, dy, xp, din;
+  float* F;
+  float* Z;
+  float* w;
+};
+
+__global__ void record_kernel(RecordArgs r) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= r.n_outer * r.M) return;
+  const long long g = r.i0 + e / r.M;
+  const int j = (int)(e % r.M);
+  const long long NM = r.N * (long long)r.M;
+  const long long a = r.anc_prev[g];
+  const int b = r.bidx[g * r.M + j];
+  float* f = r.F + e * r.din;
+  int k = 0;
+  for (int c = 0; c < r.d1; ++c) f[k++] = r.x_old[a * r.xp + c];
+  for (int c = 0; c < r.d1; ++c) f[k++] = r.x_new[g * r.xp + c];
+  for (int c = 0; c < r.d2; ++c) f[k++] = r.z_old[c * NM + a * r.M + b];
+  for (int q = 0; q < r.dy; ++q) f[k++] = r.y_prev[q];
+  for (int c = 0; c < r.d2; ++c) r.Z[e * r.d2 + c] = r.z_new[c * NM + g * r.M + j];
+  r.w[e] = expf(r.lq_new[g * r.M + j]) / (float)r.N;
+}
+
+}  // namespace dpf
+
+using namespace dpf;
+
+extern "C" {
+
+dpf_status dpf_proposal_forward(dpf_proposal* p, const float* F, int64_t n, float* out) {
+  clear_error();
+  if (!p || !F || !out || n < 1) return set_error(DPF_E_INVALID, "dpf_proposal_forward: bad arguments");
+  if (p->hidden != LH || p->dout > LNP || p->din > LDIN)
+    return set_error(DPF_E_UNSUPPORTED, "dpf_proposal_forward: the tensor-core pass needs hidden = 256, "
+                                        "din <= 16 and dout <= 32");
+  dpf_status st = pack(*p);
+  if (st) return st;
+  int* err = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&err, sizeof(int), p->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_proposal_forward: allocation");
+  cudaMemsetAsync(err, 0, sizeof(int), p->stream);
+  LearnArgs la{};
+  la.wp = (const unsigned char*)p->packed;
+  la.din = p->din;
+  la.dout = p->dout;
+  la.C = p->C;
+  la.F = F;
+  la.out = out;
+  la.nrows = n;
+  la.err = err;
+  MC<float, 2, 2, 2> mc;
+  memset(&mc, 0, sizeof(mc));
+  StepArgs<float> a{};
+  st = launch_learned<0, 2, 2, 2, false>(mc, a, la, n, p->stream);
+  int h = 0;
+  e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  cudaFreeAsync(err, p->stream);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_error(e, "dpf_proposal_forward");
+  if (h) return set_error(DPF_E_TIMEOUT, "dpf_proposal_forward: a bounded wait gave up");
+  return DPF_OK;
+}
+
+dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
+  clear_error();
+  if (!x) return set_error(DPF_E_INVALID, "dpf_set_proposal: null context");
+  if (!p) {
+    x->proposal = nullptr;
+    return DPF_OK;
+  }
+  if (x->prec != DPF_F32 || p->d1 != x->d1 || p->d2 != x->d2 || p->dy != x->dy)
+    return set_error(DPF_E_INVALID, "dpf_set_proposal: the proposal's (d1, d2, dy) and FP32 must match the filter");
+  if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH || p->dout > LNP ||
+      !(x->M == 32 || x->M == 64 || x->M == 128))
+    return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: compiled for (d1, d2, dy) = (2, 2, 2), hidden 256, "
+                                        "head <= 32 outputs and M in {32, 64, 128}");
+  x->proposal = p;
+  return DPF_OK;
+}
+
+dpf_status dpf_record_tuples(dpf_ctx* x, int64_t i0, int64_t n_outer, float* F, float* Z, float* w) {
+  clear_error();
+  if (!x || !F || !Z || !w || i0 < 0 || n_outer < 1 || i0 + n_outer > x->N)
+    return set_error(DPF_E_INVALID, "dpf_record_tuples: bad arguments");
+  if (x->t < 2 || !x->dbg_b || !x->anc_prev || x->prec != DPF_F32)
+    return set_error(DPF_E_INVALID, "dpf_record_tuples: needs an FP32 filter stepped at least twice with "
+                                    "debug recording on");
+  const long long t = x->t;  // the last call materialised step t - 1 from step t - 2
+  RecordArgs r{};
+  r.x_old = (const float*)x->x[t % 2];
+  r.z_old = (const float*)x->z[t % 2];
+  r.x_new = (const float*)x->x[(t + 1) % 2];
+  r.z_new = (const float*)x->z[(t + 1) % 2];
+  r.lq_new = (const float*)x->lq[(t + 1) % 2];
+  r.y_prev = (const float*)x->yb + ((t + 1) % 2) * x->dy;
+  r.anc_prev = x->anc_prev;
+  r.bidx = x->dbg_b;
+  r.N = x->N;
+  r.i0 = i0;
+  r.n_outer = n_outer;
+  r.M = x->M;
+  r.d1 = x->d1;
+  r.d2 = x->d2;
+  r.dy = x->dy;
+  r.xp = x->xp;
+  r.din = 2 * x->d1 + x->d2 + x->dy;
+  r.F = F;
+  r.Z = Z;
+  r.w = w;
+  const long long n = n_outer * x->M;
+  record_kernel<<<(unsigned)((n + 255) / 256), 256, 0, x->stream>>>(r);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return cuda_error(e, "dpf_record_tuples");
+}
+
+}  // extern "C"

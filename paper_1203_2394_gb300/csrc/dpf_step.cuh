@@ -83,6 +83,7 @@ struct StepArgs {
   uint32_t off_stage, off_sz, off_slq, off_sx, off_slwh, off_sxbb;
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
   uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
+  int la_only;  // the inner update already ran (learned proposal): look-ahead from the materialised state
 };
 
 // Order-preserving unsigned keys of floating-point values (for atomicMax).
@@ -505,8 +506,20 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           lqr[p] = slq[j];
         }
       }
-      sigma = -log_t((T)M);
-      SA0 = (T)M;
+      if (a.la_only) {  // the state's own weights: largest lq and sum exp(lq - largest)
+        T mx = NEG;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) mx = fmax(mx, lqr[p]);
+        sigma = bmax(mx, red);
+        T se = T(0);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p)
+          if (tid + p * NT < M) se += exp2_t((lqr[p] - sigma) * LOG2E);
+        SA0 = bsum(se, red);
+      } else {
+        sigma = -log_t((T)M);
+        SA0 = (T)M;
+      }
     } else {
       // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws ----
       if (tid < 32) {

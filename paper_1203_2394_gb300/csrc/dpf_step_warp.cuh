@@ -286,8 +286,19 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int c = 0; c < D2; ++c) vld<T, PPL>(sz + c * M + k0, zr[c]);
         vld<T, PPL>(slq + k0, lqr);
       }
-      sigma = -a.logM;
-      SA0 = (T)M;
+      if (a.la_only) {  // the state's own weights: largest lq and sum exp(lq - largest)
+        T mx = NEG;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) mx = fmax(mx, lqr[p]);
+        sigma = warp_max(mx);
+        T se = T(0);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) se += act ? exp2_t((lqr[p] - sigma) * LOG2E) : T(0);
+        SA0 = warp_sum(se);
+      } else {
+        sigma = -a.logM;
+        SA0 = (T)M;
+      }
     } else {
       // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws ----
       int msel;

@@ -141,10 +141,13 @@ struct VariantImpl {
   static void fill_args(Ctx& x, StepArgs<T>& a) {
     const long long t = x.t + 1;  // the step being taken
     const int so = (int)((t + 2) % 2), sn = (int)((t + 1) % 2);  // slots of t-2 and t-1
-    const bool first = (t == 1);
-    a.z_old = (const T*)x.z[first ? 0 : so];
-    a.lq_old = (const T*)x.lq[first ? 0 : so];
-    a.x_old = (const T*)x.x[first ? 0 : so];
+    // first step, or the inner update already done (learned proposal): the look-ahead
+    // starts from the materialised state of t-1 in slot sn (slot 0 at t = 1)
+    const bool first = (t == 1) || x.la_only;
+    a.la_only = (t > 1 && x.la_only) ? 1 : 0;
+    a.z_old = (const T*)x.z[first ? sn : so];
+    a.lq_old = (const T*)x.lq[first ? sn : so];
+    a.x_old = (const T*)x.x[first ? sn : so];
     a.z_new = (T*)x.z[sn];
     a.lq_new = (T*)x.lq[sn];
     a.x_new = (T*)x.x[sn];

@@ -58,6 +58,18 @@ SIGNATURES = [
     ("dpf_tc_matmul", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
+    ("dpf_proposal_create", ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _P, _P]),
+    ("dpf_proposal_num_params", ctypes.c_int, [_P, _P]),
+    ("dpf_proposal_set_weights", ctypes.c_int, [_P, _P, _I64]),
+    ("dpf_proposal_get_weights", ctypes.c_int, [_P, _P, _I64]),
+    ("dpf_proposal_set_bf16", ctypes.c_int, [_P, _I32]),
+    ("dpf_proposal_loss_grad", ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    ("dpf_proposal_adam_step", ctypes.c_int, [_P, _P, ctypes.c_float]),
+    ("dpf_proposal_train", ctypes.c_int, [_P, _P, _P, _P, _I64, _I32, _I32, ctypes.c_float, _U64, _P]),
+    ("dpf_proposal_forward", ctypes.c_int, [_P, _P, _I64, _P]),
+    ("dpf_proposal_destroy", None, [_P]),
+    ("dpf_set_proposal", ctypes.c_int, [_P, _P]),
+    ("dpf_record_tuples", ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
     ("dpf_set_tensor_cores", ctypes.c_int, [_P, _I32]),
     ("dpf_set_debug", ctypes.c_int, [_P, _I32]),
     ("dpf_profile", ctypes.c_int, [_P, _I32]),
@@ -181,6 +193,7 @@ class Filter:
         "anc": lambda s: (s.N,), "sel": lambda s: (s.N,), "wout": lambda s: (s.N,),
         "x": lambda s: (s.N, s.d1), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
         "bidx": lambda s: (s.N, s.M),
+        "head": lambda s: (s.N, s.M, s.proposal.dout),
     }
 
     def read(self, which: str) -> np.ndarray:
@@ -195,6 +208,25 @@ class Filter:
 
     def set_tensor_cores(self, on=True):
         check(self._lib.dpf_set_tensor_cores(self.h, int(on)))
+
+    def set_proposal(self, proposal):
+        """Use a learned inner proposal from the next step on (None: the prior)."""
+        check(self._lib.dpf_set_proposal(self.h, proposal.h if proposal is not None else None))
+        self.proposal = proposal
+
+    def record(self, i0=0, n_outer=None):
+        """Training rows of the last inner update (see ``dpf_record_tuples``): device
+        tensors F (n, din), Z (n, d2), w (n)."""
+        import torch
+        n_outer = self.N - i0 if n_outer is None else n_outer
+        din = 2 * self.d1 + self.d2 + self.dy
+        n = n_outer * self.M
+        F = torch.empty((n, din), dtype=torch.float32, device="cuda")
+        Z = torch.empty((n, self.d2), dtype=torch.float32, device="cuda")
+        w = torch.empty((n,), dtype=torch.float32, device="cuda")
+        check(self._lib.dpf_record_tuples(self.h, int(i0), int(n_outer), F.data_ptr(), Z.data_ptr(),
+                                          w.data_ptr()))
+        return F, Z, w
 
     def profile(self, on=True):
         check(self._lib.dpf_profile(self.h, int(on)))
@@ -343,3 +375,92 @@ def tc_matmul(A, B, mode=DPF_TC_TF32X3, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     check(lib().dpf_tc_matmul(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, int(mode), s))
     return D
+
+
+class Proposal:
+    """The learned inner proposal (``dpf_proposal_*``): an MLP of three hidden ReLU layers
+    with a Gaussian-mixture head, trained on the GPU by the library's kernels."""
+
+    def __init__(self, d1, d2, dy, hidden=256, components=4, stream=None):
+        self.d1, self.d2, self.dy = int(d1), int(d2), int(dy)
+        self.hidden, self.C = int(hidden), int(components)
+        self.din = 2 * self.d1 + self.d2 + self.dy
+        self.dout = self.C * (1 + 2 * self.d2)
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        check(self._lib.dpf_proposal_create(self.d1, self.d2, self.dy, self.hidden, self.C,
+                                            _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        n = ctypes.c_int64()
+        check(self._lib.dpf_proposal_num_params(self.h, ctypes.byref(n)))
+        self.nparams = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dpf_proposal_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        """(name, shape) of every parameter block in the library's order."""
+        H, out = [], []
+        sizes = [(self.hidden, self.din), (self.hidden, self.hidden), (self.hidden, self.hidden),
+                 (self.dout, self.hidden)]
+        for l, (r, c) in enumerate(sizes, 1):
+            out += [(f"W{l}", (r, c)), (f"b{l}", (r,))]
+        return out
+
+    def flatten(self, W):
+        return np.concatenate([np.asarray(W[k], np.float32).ravel() for k, _ in self.layout()])
+
+    def unflatten(self, flat):
+        W, o = {}, 0
+        for k, shp in self.layout():
+            n = int(np.prod(shp))
+            W[k] = flat[o:o + n].reshape(shp).astype(np.float64)
+            o += n
+        return W
+
+    def set_weights(self, W):
+        flat = np.ascontiguousarray(self.flatten(W))
+        check(self._lib.dpf_proposal_set_weights(self.h, flat.ctypes.data, flat.size))
+
+    def get_weights(self):
+        flat = np.zeros(self.nparams, np.float32)
+        check(self._lib.dpf_proposal_get_weights(self.h, flat.ctypes.data, flat.size))
+        return self.unflatten(flat)
+
+    def set_bf16(self, on=True):
+        check(self._lib.dpf_proposal_set_bf16(self.h, int(on)))
+
+    def loss_grad(self, F, Z, w, grad=True):
+        """Weighted NLL and (optionally) its gradient (device tensor of num_params)."""
+        import torch
+        loss = ctypes.c_double()
+        g = torch.empty(self.nparams, dtype=torch.float32, device=F.device) if grad else None
+        check(self._lib.dpf_proposal_loss_grad(self.h, F.data_ptr(), Z.data_ptr(), w.data_ptr(),
+                                               F.shape[0], ctypes.byref(loss),
+                                               g.data_ptr() if g is not None else None))
+        return loss.value, g
+
+    def adam_step(self, grad, lr):
+        check(self._lib.dpf_proposal_adam_step(self.h, grad.data_ptr(), ctypes.c_float(lr)))
+
+    def train(self, F, Z, w, batch=1024, epochs=1, lr=1e-3, seed=0):
+        losses = np.zeros(epochs)
+        check(self._lib.dpf_proposal_train(self.h, F.data_ptr(), Z.data_ptr(), w.data_ptr(),
+                                           F.shape[0], int(batch), int(epochs), ctypes.c_float(lr),
+                                           ctypes.c_uint64(seed), losses.ctypes.data))
+        return losses
+
+    def forward(self, F):
+        """Head outputs by the tensor-core pass (device tensor (n, dout))."""
+        import torch
+        out = torch.empty((F.shape[0], self.dout), dtype=torch.float32, device=F.device)
+        check(self._lib.dpf_proposal_forward(self.h, F.data_ptr(), F.shape[0], out.data_ptr()))
+        return out
