@@ -534,6 +534,131 @@ def run_highdim(args):
     return 0
 
 
+def run_learned(args):
+    """The learned-proposal workload: the lg4 model in FP32 with N = 262144 outer and
+    M = 64 inner particles. A proposal (MLP 3 x 256 ReLU, 4-component mixture head, BF16
+    weights, FP32 accumulation) is trained on the GPU on 10^6 rows the plain filter
+    records; then the filter with it (L = 1) and the plain filter (L = 8) are timed over
+    the same steps, and their accuracy (RMSE of the filtered mean against the Kalman
+    filter, inner ESS) is measured on a separate untimed run."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    spec = workloads.make_model("lg4", 0)
+    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    N, M = 262144, 64
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    # ---- training rows and training ----
+    t0 = time.perf_counter()
+    _, ys_tr = workloads.simulate(spec, 3, 100)
+    rec = dpf.Filter(model, 2, 2, 16384, M, 8, seed=1, stream=stream)
+    rec.set_debug(True)
+    for t in range(2):
+        rec.step(ys_tr[t].astype(np.float32))
+    F, Z, w = rec.record()
+    rec.close()
+    prop = dpf.Proposal(2, 2, 2, hidden=256, components=4, stream=stream)
+    W0 = workloads.init_mlp_weights(8, 256, 20, seed=0)
+    W0["b4"][12:] = np.log(np.sqrt(0.1))
+    prop.set_weights(W0)
+    losses = prop.train(F, Z, w, batch=1024, epochs=3, lr=1e-3, seed=2)
+    train_s = time.perf_counter() - t0
+    del F, Z, w
+    # ---- timing ----
+    _, ys = workloads.simulate(spec, W + K + 1, 0)
+    yd = torch.tensor(ys.astype(np.float32), device="cuda")
+
+    def timed(L, use_prop):
+        f = dpf.Filter(model, 2, 2, N, M, L, seed=3, stream=stream)
+        if use_prop:
+            f.set_proposal(prop)
+        with torch.cuda.stream(stream):
+            for k in range(W):
+                f.step_device(yd[k].data_ptr())
+            f.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(W, W + K):
+                f.step_device(yd[k].data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f.sync()
+        f.close()
+        return e0.elapsed_time(e1)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    w0 = time.monotonic()
+    ms_l = timed(1, True)
+    w1 = time.monotonic()
+    clk = clocks.stop(window=(w0, w1))
+    ms_p = timed(8, False)
+    # ---- accuracy on an untimed run ----
+    T = 25
+    _, ya = workloads.simulate(spec, T, 200)
+    import numpy.linalg as la_
+
+    def kalman_means(ys_):
+        m, P = spec.m0.copy(), spec.P0.copy()
+        out = []
+        for y in ys_:
+            m = spec.A @ m
+            P = spec.A @ P @ spec.A.T + spec.Q
+            S = spec.H @ P @ spec.H.T + spec.R
+            Kg = P @ spec.H.T @ la_.inv(S)
+            m = m + Kg @ (y - spec.H @ m)
+            P = P - Kg @ S @ Kg.T
+            out.append(m.copy())
+        return np.array(out)
+    km = kalman_means(ya)
+
+    def accuracy(L, use_prop):
+        f = dpf.Filter(model, 2, 2, N, M, L, seed=5, stream=stream)
+        if use_prop:
+            f.set_proposal(prop)
+        err, ess = [], []
+        for t in range(T):
+            m, _ = f.step(ya[t].astype(np.float32))
+            err.append(m - km[t])
+            if t >= 1:
+                lq = f.read("lq").astype(np.float64)
+                Wt = np.exp(lq - lq.max(axis=1, keepdims=True))
+                ess.append(float(np.mean(Wt.sum(1) ** 2 / (Wt * Wt).sum(1)) / M))
+        f.close()
+        return float(np.sqrt(np.mean(np.square(err)))), float(np.mean(ess))
+
+    rmse_l, ess_l = accuracy(1, True)
+    rmse_p, ess_p = accuracy(8, False)
+    value = N * M * K / (ms_l / 1e3)
+    mlp_flop = 2 * (8 * 256 + 2 * 256 * 256 + 256 * 20)  # per inner particle
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms_l / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 filter, bf16 MLP", "data": "synthetic",
+        "config": {"workload": f"learned proposal: lg4 model (d=4, x 2 / z 2), FP32, N={N}, M={M}, L=1; "
+                               "MLP 3x256 ReLU, 4-component mixture head, BF16 weights, FP32 accumulate",
+                   "training_rows": 16384 * M, "training_epochs": 3, "training_s": train_s,
+                   "training_losses": list(losses),
+                   "l2": "state larger than L2; no flush"},
+        "tensor": {"mlp_tflops": mlp_flop * N * M * K / (ms_l / 1e3) / 1e12,
+                   "mlp_flop_per_update": mlp_flop},
+        "plain": {"L": 8, "value": N * M * K / (ms_p / 1e3), "ms_per_step": ms_p / K},
+        "accuracy": {"steps": T, "rmse_vs_kalman_learned": rmse_l, "rmse_vs_kalman_plain": rmse_p,
+                     "inner_ess_learned": ess_l, "inner_ess_plain": ess_p},
+        "gpu_launches": 4 * K,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    prop.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,8 +666,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim"],
-                    help="the headline single-filter workload, the many-filter one, or the d2 = 56 one")
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned"],
+                    help="the headline single-filter workload, the many-filter one, the d2 = 56 one, "
+                         "or the learned-proposal one")
     ap.add_argument("--filters", type=int, default=None,
                     help="filters of the batched (default 512) or high-dimensional (default 64) workload")
     args = ap.parse_args(argv)
@@ -556,6 +682,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "highdim":
         return run_highdim(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run(args)
 
 
