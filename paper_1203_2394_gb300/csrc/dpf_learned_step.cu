@@ -34,6 +34,7 @@ constexpr int LSTAGES = 3;
 constexpr uint32_t LCHUNK = LH * LKCH * 2;  // bytes of one chunk
 constexpr int L_SPIN = 1 << 22;
 constexpr uint32_t LTMEM_COLS = 512;
+constexpr int kFilterComponents = 4;  // mixture components of the filter's compiled pass
 
 // packed global layout (bytes)
 constexpr size_t PK_W1 = 0;
@@ -127,24 +128,22 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return lo | (hi << 16);
 }
 
-// Read one hidden accumulator row (256 FP32 columns of TMEM), add the bias, ReLU,
-// round to BF16 and store it as row r of the activation tile.
+// Read one hidden accumulator row (256 FP32 columns of TMEM, 64 per load), add the
+// bias, ReLU, round to BF16 and store it as row r of the activation tile.
 __device__ __forceinline__ void hidden_epilogue(uint32_t taddr_row, const float* bias, unsigned char* act, int r) {
 #pragma unroll 1
-  for (int c0 = 0; c0 < LH; c0 += 16) {
-    float v[16];
-    tc::ld16(taddr_row + (uint32_t)c0, v);
-    uint4 q0, q1;
-    q0.x = pack_bf16x2(fmaxf(v[0] + bias[c0 + 0], 0.f), fmaxf(v[1] + bias[c0 + 1], 0.f));
-    q0.y = pack_bf16x2(fmaxf(v[2] + bias[c0 + 2], 0.f), fmaxf(v[3] + bias[c0 + 3], 0.f));
-    q0.z = pack_bf16x2(fmaxf(v[4] + bias[c0 + 4], 0.f), fmaxf(v[5] + bias[c0 + 5], 0.f));
-    q0.w = pack_bf16x2(fmaxf(v[6] + bias[c0 + 6], 0.f), fmaxf(v[7] + bias[c0 + 7], 0.f));
-    q1.x = pack_bf16x2(fmaxf(v[8] + bias[c0 + 8], 0.f), fmaxf(v[9] + bias[c0 + 9], 0.f));
-    q1.y = pack_bf16x2(fmaxf(v[10] + bias[c0 + 10], 0.f), fmaxf(v[11] + bias[c0 + 11], 0.f));
-    q1.z = pack_bf16x2(fmaxf(v[12] + bias[c0 + 12], 0.f), fmaxf(v[13] + bias[c0 + 13], 0.f));
-    q1.w = pack_bf16x2(fmaxf(v[14] + bias[c0 + 14], 0.f), fmaxf(v[15] + bias[c0 + 15], 0.f));
-    *(uint4*)(act + tc::kmajor_offset(r, 2 * c0, 32)) = q0;
-    *(uint4*)(act + tc::kmajor_offset(r, 2 * c0 + 16, 32)) = q1;
+  for (int c0 = 0; c0 < LH; c0 += 64) {
+    float v[64];
+    tc::ld64(taddr_row + (uint32_t)c0, v);
+#pragma unroll
+    for (int h = 0; h < 64; h += 8) {
+      uint4 q;
+      q.x = pack_bf16x2(fmaxf(v[h + 0] + bias[c0 + h + 0], 0.f), fmaxf(v[h + 1] + bias[c0 + h + 1], 0.f));
+      q.y = pack_bf16x2(fmaxf(v[h + 2] + bias[c0 + h + 2], 0.f), fmaxf(v[h + 3] + bias[c0 + h + 3], 0.f));
+      q.z = pack_bf16x2(fmaxf(v[h + 4] + bias[c0 + h + 4], 0.f), fmaxf(v[h + 5] + bias[c0 + h + 5], 0.f));
+      q.w = pack_bf16x2(fmaxf(v[h + 6] + bias[c0 + h + 6], 0.f), fmaxf(v[h + 7] + bias[c0 + h + 7], 0.f));
+      *(uint4*)(act + tc::kmajor_offset(r, 2 * (c0 + h), 32)) = q;
+    }
   }
 }
 
@@ -174,8 +173,9 @@ __device__ __forceinline__ float group_sum(float v, int M, float* red) {
   return s;
 }
 
-// MODE 0: head outputs of feature rows; MODE 1: the filter's inner update.
-template <int MODE, int D1, int D2, int DY, bool XZ>
+// MODE 0: head outputs of feature rows; MODE 1: the filter's inner update with NC
+// mixture components (compile-time, so that the head's arrays stay in registers).
+template <int MODE, int D1, int D2, int DY, bool XZ, int NC>
 __global__ void __launch_bounds__(128, 1)
     learned_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const __grid_constant__ StepArgs<float> a,
                    const __grid_constant__ LearnArgs la) {
@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(128, 1)
     int j = 0, anc_g = 0;
     float xa[D1], xt[D1], zb[D2];
     if (MODE == 0) {
-      if (live)
-        for (int k = 0; k < la.din; ++k) feat[k] = la.F[row * la.din + k];
+#pragma unroll
+      for (int k = 0; k < LDIN; ++k)
+        if (live && k < la.din) feat[k] = la.F[row * la.din + k];
     } else {
       g = row / M;
       j = (int)(row % M);
@@ -444,43 +445,61 @@ __global__ void __launch_bounds__(128, 1)
     tc::fence_before();
 
     if (MODE == 0) {
-      if (live)
-        for (int q = 0; q < la.dout; ++q) la.out[row * la.dout + q] = o[q];
+#pragma unroll
+      for (int q = 0; q < LNP; ++q)
+        if (live && q < la.dout) la.out[row * la.dout + q] = o[q];
     } else {
       // ---- the mixture draw and the importance weight ----
-      const int C = la.C;
-      if (la.dbg_head && live)
-        for (int q = 0; q < la.dout; ++q) la.dbg_head[row * la.dout + q] = o[q];
+      constexpr int C = NC;
+      constexpr int DO = NC * (1 + 2 * D2);
+      if (la.dbg_head && live) {
+#pragma unroll
+        for (int q = 0; q < DO; ++q) la.dbg_head[row * DO + q] = o[q];
+      }
       float lmax = NEG;
+#pragma unroll
       for (int c = 0; c < C; ++c) lmax = fmaxf(lmax, o[c]);
       float se = 0.f;
+#pragma unroll
       for (int c = 0; c < C; ++c) se += expf(o[c] - lmax);
       const float lse_a = lmax + logf(se);
       // component: one-draw systematic pick over exp(logit - max), quantised
-      uint32_t cumc[kMaxComponents];
+      uint32_t cumc[C];
       uint32_t run = 0;
+#pragma unroll
       for (int c = 0; c < C; ++c) {
         run += (uint32_t)floorf(exp2f((o[c] - lmax) * 1.4426950408889634f) * (float)la.scaleC);
         cumc[c] = run;
       }
       const uint32_t uc = philox(ctr(a.t - 1, (uint32_t)g, P_LCOMP, (uint32_t)j, 0u), a.key).x;
       const uint64_t rhs = (uint64_t)uc * run;
+      // the first component whose cumulative count passes the draw (unrolled select)
       int comp = C - 1;
+#pragma unroll
       for (int c = C - 1; c >= 0; --c)
         if (((uint64_t)cumc[c] << 32) > rhs) comp = c;
       float eps[D2];
       normals<D2>(a.key, a.t - 1, (uint32_t)g, P_PROP, (uint32_t)j, eps);
       float z[D2];
+#pragma unroll
       for (int d = 0; d < D2; ++d) {
-        const float mu = o[C + comp * D2 + d];
-        const float ls = fminf(fmaxf(o[C + C * D2 + comp * D2 + d], kLogSigMin), kLogSigMax);
+        float mu = 0.f, lsr = 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          if (c == comp) {
+            mu = o[C + c * D2 + d];
+            lsr = o[C + C * D2 + c * D2 + d];
+          }
+        const float ls = fminf(fmaxf(lsr, kLogSigMin), kLogSigMax);
         z[d] = mu + expf(ls) * eps[d];
       }
       // log q(z): LSE over components (the -d2/2 log 2 pi constant cancels in lq)
-      float lc[kMaxComponents];
+      float lc[C];
       float cmax = NEG;
+#pragma unroll
       for (int c = 0; c < C; ++c) {
         float s = o[c] - lse_a;
+#pragma unroll
         for (int d = 0; d < D2; ++d) {
           const float mu = o[C + c * D2 + d];
           const float ls = fminf(fmaxf(o[C + C * D2 + c * D2 + d], kLogSigMin), kLogSigMax);
@@ -491,6 +510,7 @@ __global__ void __launch_bounds__(128, 1)
         cmax = fmaxf(cmax, s);
       }
       float sc = 0.f;
+#pragma unroll
       for (int c = 0; c < C; ++c) sc += expf(lc[c] - cmax);
       const float lqz = cmax + logf(sc);
       // log N(z; A_zx x_a + A_zz z_b, Q_z) up to its constant
@@ -550,10 +570,10 @@ __global__ void __launch_bounds__(128, 1)
   if (w == 0) tc::tmem_dealloc(taddr, LTMEM_COLS);
 }
 
-template <int MODE, int D1, int D2, int DY, bool XZ>
+template <int MODE, int D1, int D2, int DY, bool XZ, int NC>
 static dpf_status launch_learned(const MC<float, D1, D2, DY>& mc, const StepArgs<float>& a, const LearnArgs& la,
                                  long long rows, cudaStream_t s) {
-  auto k = learned_kernel<MODE, D1, D2, DY, XZ>;
+  auto k = learned_kernel<MODE, D1, D2, DY, XZ, NC>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
@@ -593,8 +613,8 @@ dpf_status learned_inner_step(Ctx& x) {
   la.err = x.err;
   const MC<float, 2, 2, 2>& mc = *reinterpret_cast<const MC<float, 2, 2, 2>*>(x.mconst.data());
   const long long rows = x.N * (long long)x.M;
-  return x.hm.xz ? launch_learned<1, 2, 2, 2, true>(mc, a, la, rows, x.stream)
-                 : launch_learned<1, 2, 2, 2, false>(mc, a, la, rows, x.stream);
+  return x.hm.xz ? launch_learned<1, 2, 2, 2, true, kFilterComponents>(mc, a, la, rows, x.stream)
+                 : launch_learned<1, 2, 2, 2, false, kFilterComponents>(mc, a, la, rows, x.stream);
 }
 
 // ---- training rows from the last inner update ----
@@ -656,7 +676,7 @@ dpf_status dpf_proposal_forward(dpf_proposal* p, const float* F, int64_t n, floa
   MC<float, 2, 2, 2> mc;
   memset(&mc, 0, sizeof(mc));
   StepArgs<float> a{};
-  st = launch_learned<0, 2, 2, 2, false>(mc, a, la, n, p->stream);
+  st = launch_learned<0, 2, 2, 2, false, kFilterComponents>(mc, a, la, n, p->stream);
   int h = 0;
   e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -676,10 +696,10 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
   }
   if (x->prec != DPF_F32 || p->d1 != x->d1 || p->d2 != x->d2 || p->dy != x->dy)
     return set_error(DPF_E_INVALID, "dpf_set_proposal: the proposal's (d1, d2, dy) and FP32 must match the filter");
-  if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH || p->dout > LNP ||
+  if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH || p->C != kFilterComponents ||
       !(x->M == 32 || x->M == 64 || x->M == 128))
     return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: compiled for (d1, d2, dy) = (2, 2, 2), hidden 256, "
-                                        "head <= 32 outputs and M in {32, 64, 128}");
+                                        "4 components and M in {32, 64, 128}");
   x->proposal = p;
   return DPF_OK;
 }
