@@ -221,6 +221,21 @@ dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ
  */
 dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t bytes);
 
+/*
+ * Checkpoints. A state holds everything the next step reads: the newest
+ * materialised particles (x, z, lq), the look-ahead products and the ancestors
+ * of the last step, the last observation, the running evidence and the step
+ * counter, with a header of the sizes. dpf_state_bytes gives its size;
+ * dpf_get_state copies it into dst_device (device memory, caller-owned, at
+ * least that many bytes); dpf_set_state loads one taken from a filter of the
+ * same precision and sizes (d1, d2, dy, N, M, L; else DPF_E_INVALID). The steps
+ * after a restore equal those of the original filter when both have the same
+ * seed. Both synchronise the stream.
+ */
+dpf_status dpf_state_bytes(dpf_ctx* ctx, size_t* bytes);
+dpf_status dpf_get_state(dpf_ctx* ctx, void* dst_device, size_t bytes);
+dpf_status dpf_set_state(dpf_ctx* ctx, const void* src_device, size_t bytes);
+
 /* Record per-step debug arrays ("bidx") when enable != 0. */
 dpf_status dpf_set_debug(dpf_ctx* ctx, int32_t enable);
 

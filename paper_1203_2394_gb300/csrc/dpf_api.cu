@@ -448,6 +448,95 @@ dpf_status dpf_diag(dpf_ctx* x, double* ess, int64_t* step, double* logz_step) {
   return DPF_OK;
 }
 
+// ---- checkpoints: everything the next step reads ----
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  int32_t version, prec, d1, d2, dy, M, L, xp;
+  int64_t N, t;
+  uint64_t seed;
+};
+constexpr uint64_t kStateMagic = 0x4450465354415445ull;  // "DPFSTATE"
+struct StateLayout {
+  size_t off[10];
+  size_t len[10];
+  size_t total;
+};
+StateLayout state_layout(const dpf_ctx& x) {
+  const size_t s = x.prec == DPF_F64 ? 8 : 4;
+  const size_t N = (size_t)x.N, M = (size_t)x.M, L = (size_t)x.L;
+  const size_t len[10] = {sizeof(StateHeader), s * N * x.xp, s * N * M * x.d2, s * N * M, s * N * L,
+                          s * N * L * x.d1, 4 * N, s * 2 * x.dy, sizeof(double) * (4 + x.d), 4 * N};
+  StateLayout l{};
+  size_t o = 0;
+  for (int q = 0; q < 10; ++q) {
+    l.off[q] = o;
+    l.len[q] = len[q];
+    o += (len[q] + 255) / 256 * 256;
+  }
+  l.total = o;
+  return l;
+}
+// the device arrays of the sections (header excluded), in layout order
+void state_arrays(dpf_ctx& x, void* a[10]) {
+  const long long t = x.t;
+  const int mat = t >= 2 ? (int)((t - 1) % 2) : 0, cur = (int)(t % 2);
+  a[0] = nullptr;
+  a[1] = x.x[mat];
+  a[2] = x.z[mat];
+  a[3] = x.lq[mat];
+  a[4] = x.lwh[cur];
+  a[5] = x.xbb[cur];
+  a[6] = x.anc;
+  a[7] = x.yb;
+  a[8] = x.stats;
+  a[9] = x.sel;
+}
+}  // namespace
+
+dpf_status dpf_state_bytes(dpf_ctx* x, size_t* bytes) {
+  clear_error();
+  if (!x || !bytes) return set_error(DPF_E_INVALID, "dpf_state_bytes: null argument");
+  *bytes = state_layout(*x).total;
+  return DPF_OK;
+}
+
+dpf_status dpf_get_state(dpf_ctx* x, void* dst, size_t bytes) {
+  clear_error();
+  if (!x || !dst) return set_error(DPF_E_INVALID, "dpf_get_state: null argument");
+  const StateLayout l = state_layout(*x);
+  if (bytes < l.total) return set_error(DPF_E_INVALID, "dpf_get_state: buffer smaller than dpf_state_bytes");
+  StateHeader h{kStateMagic, 1, x->prec, x->d1, x->d2, x->dy, x->M, x->L, x->xp, x->N, x->t, x->seed};
+  void* a[10];
+  state_arrays(*x, a);
+  cudaError_t e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, x->stream);
+  for (int q = 1; q < 10 && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync((char*)dst + l.off[q], a[q], l.len[q], cudaMemcpyDeviceToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);  // h lives on this stack frame
+  return cuda_error(e, "dpf_get_state");
+}
+
+dpf_status dpf_set_state(dpf_ctx* x, const void* src, size_t bytes) {
+  clear_error();
+  if (!x || !src) return set_error(DPF_E_INVALID, "dpf_set_state: null argument");
+  const StateLayout l = state_layout(*x);
+  if (bytes < l.total) return set_error(DPF_E_INVALID, "dpf_set_state: buffer smaller than dpf_state_bytes");
+  StateHeader h{};
+  cudaError_t e = cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_set_state");
+  if (h.magic != kStateMagic || h.version != 1 || h.prec != x->prec || h.d1 != x->d1 || h.d2 != x->d2 ||
+      h.dy != x->dy || h.M != x->M || h.L != x->L || h.xp != x->xp || h.N != x->N || h.t < 0)
+    return set_error(DPF_E_INVALID, "dpf_set_state: not a state of a filter of this precision and these sizes");
+  x->t = h.t;
+  void* a[10];
+  state_arrays(*x, a);
+  for (int q = 1; q < 10 && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(a[q], (const char*)src + l.off[q], l.len[q], cudaMemcpyDeviceToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return cuda_error(e, "dpf_set_state");
+}
+
 dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   clear_error();
   if (!x || !which || !dst) return set_error(DPF_E_INVALID, "dpf_read: null argument");

@@ -70,6 +70,9 @@ SIGNATURES = [
     ("dpf_proposal_destroy", None, [_P]),
     ("dpf_set_proposal", ctypes.c_int, [_P, _P]),
     ("dpf_record_tuples", ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
+    ("dpf_state_bytes", ctypes.c_int, [_P, _P]),
+    ("dpf_get_state", ctypes.c_int, [_P, _P, _SZ]),
+    ("dpf_set_state", ctypes.c_int, [_P, _P, _SZ]),
     ("dpf_set_tensor_cores", ctypes.c_int, [_P, _I32]),
     ("dpf_set_debug", ctypes.c_int, [_P, _I32]),
     ("dpf_profile", ctypes.c_int, [_P, _I32]),
@@ -208,6 +211,21 @@ class Filter:
 
     def set_tensor_cores(self, on=True):
         check(self._lib.dpf_set_tensor_cores(self.h, int(on)))
+
+    def state_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        check(self._lib.dpf_state_bytes(self.h, ctypes.byref(n)))
+        return n.value
+
+    def get_state(self):
+        """A checkpoint of the filter (a device uint8 tensor)."""
+        import torch
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device="cuda")
+        check(self._lib.dpf_get_state(self.h, buf.data_ptr(), buf.numel()))
+        return buf
+
+    def set_state(self, buf):
+        check(self._lib.dpf_set_state(self.h, buf.data_ptr(), buf.numel()))
 
     def set_proposal(self, proposal):
         """Use a learned inner proposal from the next step on (None: the prior)."""
