@@ -205,3 +205,100 @@ def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, 
         lqs[i] = lr_ - _lse(lr_[None, :], 1)[0]
         outs[i] = out
     return dict(z=zs, lq=lqs, comp=comps, out=outs, logr=logrs)
+
+
+# ---------------------------------------------------------------------------
+# The outer-amortised proposal: one network evaluation per outer particle gives
+# a diagonal affine map of that group's prior draws.
+#   group features g_i = (x_{t-1}^(a), x_t, y_t, m_i, v_i), with mu_ij the prior means
+#   A_zx x_{t-1}^(a) + A_zz z_{t-1}^(a, b_ij), m_i their mean and v_i their variance
+#   (per coordinate, over j); head (log s_i, c_i) (d2 each, log s clamped to [-7, 5]);
+#   zhat_ij = mu_ij + L_qz eps_ij (the prior draw, PROP noise), and
+#   z_ij = m_i + c_i + s_i * (zhat_ij - m_i),
+#   log q(z_ij) = log N(zhat_ij; mu_ij, Q_z) - sum log s_i.
+# ---------------------------------------------------------------------------
+def affine_head(out, d2):
+    raw = out[:, :d2]
+    ls = np.clip(raw, LOGSIG_MIN, LOGSIG_MAX)
+    inside = (raw > LOGSIG_MIN) & (raw < LOGSIG_MAX)
+    return ls, out[:, d2:2 * d2], inside
+
+
+def affine_nll_and_grad(W, G, Z, MU, MG, Qz, w, bf16_mode=False):
+    """Weighted mean of -log q(z_b) for rows (group features G_b, target Z_b, prior
+    mean MU_b, group centre MG_b) under the affine proposal, and dL/dW."""
+    d2 = Z.shape[1]
+    out, cache = forward(W, G, bf16_mode)
+    ls, c, inside = affine_head(out, d2)
+    s = np.exp(ls)
+    zhat = MG + (Z - MG - c) / s
+    Qinv = np.linalg.inv(Qz)
+    r = zhat - MU
+    gz = r @ Qinv.T                                            # d(1/2 r^T Q^-1 r)/d zhat
+    nll = 0.5 * np.sum(r * gz, 1) + np.sum(ls, 1) + 0.5 * np.linalg.slogdet(2 * np.pi * Qz)[1]
+    wn = np.asarray(w, dtype=np.float64) / np.sum(w)
+    loss = float(np.sum(wn * nll))
+    g_c = -gz / s                                              # dzhat/dc = -1/s
+    g_ls = (-gz * (Z - MG - c) / s + 1.0) * inside             # dzhat/dls = -(z - m - c)/s
+    dout = np.concatenate([g_ls, g_c], axis=1) * wn[:, None]
+    grads = {}
+    L = n_layers(W)
+    d = dout
+    for l in range(L, 0, -1):
+        grads[f"W{l}"] = d.T @ cache[f"h{l - 1}"]
+        grads[f"b{l}"] = d.sum(axis=0)
+        if l > 1:
+            d = (d @ _q(W[f"W{l}"], bf16_mode)) * (cache[f"pre{l - 1}"] > 0)
+    return loss, grads
+
+
+def amortised_features(model, x_prev_a, x_new, y, zb):
+    """Group features and the per-particle prior means of one group (zb: M x d2 parents)."""
+    d1 = model.d1
+    A = model.A
+    mu = x_prev_a @ A[d1:, :d1].T + zb @ A[d1:, d1:].T
+    m = mu.mean(0)
+    v = ((mu - m) ** 2).mean(0)
+    return np.concatenate([x_prev_a, x_new, y, m, v]), mu, m
+
+
+def amortised_finalize(model, W, seed, t, y, anc, x_prev, z_prev, x_new, bidx, normals, bf16_mode=False,
+                       head_out=None):
+    """The inner update of step t with the outer-amortised proposal (see above) for
+    destinations 0..n-1, bidx from the plain local resampling. head_out: (n, >= 2 d2)
+    network outputs to use instead of evaluating it. Returns z, lq, feats, out."""
+    d1, d2, dy = model.d1, model.d2, model.dy
+    Q, H, R = model.Q, model.H, model.R
+    Qz = Q[d1:, d1:]
+    Lqz = np.linalg.cholesky(Qz)
+    Hx, Hz = H[:, :d1], H[:, d1:]
+    Lr = np.linalg.cholesky(R)
+    n, M = len(anc), bidx.shape[1]
+    feats = np.zeros((n, 2 * d1 + dy + 2 * d2))
+    mus, ms = [], []
+    for i in range(n):
+        a = anc[i]
+        feats[i], mu, m = amortised_features(model, x_prev[a], x_new[i], y, z_prev[a][bidx[i]])
+        mus.append(mu)
+        ms.append(m)
+    out = head_out if head_out is not None else forward(W, feats, bf16_mode)[0]
+    ls, c, _ = affine_head(out, d2)
+    zs = np.zeros((n, M, d2)); lqs = np.zeros((n, M))
+    for i in range(n):
+        eps = np.stack([normals(t, i, 9, j, d2) for j in range(M)])  # P_PROP
+        zhat = mus[i] + eps @ Lqz.T
+        s = np.exp(ls[i])
+        z = ms[i] + c[i] + s * (zhat - ms[i])
+        def lgauss(v, L):
+            u = np.linalg.solve(L, v.T).T
+            return -0.5 * np.sum(u * u, 1) - np.sum(np.log(np.diag(L))) - 0.5 * L.shape[0] * LOG2PI
+        lprior = lgauss(z - mus[i], Lqz)
+        lq_prop = lgauss(zhat - mus[i], Lqz) - np.sum(ls[i])
+        hx = Hx @ x_new[i]
+        if model.qc is not None:
+            hx = hx + model.qc * x_new[i][:dy] ** 2
+        lpy = lgauss(y - hx - z @ Hz.T, Lr)
+        lr_ = lprior - lq_prop + lpy
+        zs[i] = z
+        lqs[i] = lr_ - _lse(lr_[None, :], 1)[0]
+    return dict(z=zs, lq=lqs, feats=feats, out=out)

@@ -167,3 +167,70 @@ def test_prior_network_reproduces_the_plain_inner_update():
     np.testing.assert_allclose(got["z"], fin["z"], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(got["lq"], fin["lq"], rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(fin["z"], r2["z"], rtol=0, atol=0)
+
+
+def test_affine_gradients_match_finite_differences():
+    rng = np.random.default_rng(20)
+    din, d2, n = 10, 2, 30
+    W = workloads.init_mlp_weights(din, 12, 2 * d2, seed=21)
+    for k in W:
+        W[k] = W[k] + 0.05 * rng.standard_normal(W[k].shape)
+    W["b4"][0] = 8.0  # one log-scale outside the clamp
+    G = rng.standard_normal((n, din))
+    Z = rng.standard_normal((n, d2)); MU = rng.standard_normal((n, d2)); MG = rng.standard_normal((n, d2))
+    Qz = np.array([[0.2, 0.05], [0.05, 0.1]])
+    w = rng.uniform(0.1, 1, n)
+    loss, Gr = learned.affine_nll_and_grad(W, G, Z, MU, MG, Qz, w)
+    h = 1e-6
+    for k in W:
+        flat = W[k].reshape(-1)
+        for p in rng.choice(flat.size, min(flat.size, 20), replace=False):
+            old = flat[p]
+            flat[p] = old + h
+            lp, _ = learned.affine_nll_and_grad(W, G, Z, MU, MG, Qz, w)
+            flat[p] = old - h
+            lm, _ = learned.affine_nll_and_grad(W, G, Z, MU, MG, Qz, w)
+            flat[p] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - Gr[k].reshape(-1)[p]) <= 1e-6 * max(1.0, abs(fd)), (k, p)
+    assert Gr["b4"][0] == 0.0
+
+
+def test_affine_density_is_the_change_of_variables():
+    # q(z) of the affine map equals N(z; m + c + s (mu - m), S Qz S), by scipy
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(22)
+    d2 = 2
+    Qz = np.array([[0.2, 0.05], [0.05, 0.1]])
+    mu, m = rng.standard_normal(d2), rng.standard_normal(d2)
+    ls, c = rng.uniform(-0.5, 0.5, d2), rng.standard_normal(d2)
+    s = np.exp(ls)
+    W = {"W1": np.zeros((4, 1)), "b1": np.zeros(4), "W2": np.zeros((2 * d2, 4)),
+         "b2": np.concatenate([ls, c])}
+    for _ in range(5):
+        z = rng.standard_normal(d2)
+        loss, _ = learned.affine_nll_and_grad(W, np.zeros((1, 1)), z[None], mu[None], m[None], Qz, [1.0])
+        S = np.diag(s)
+        ref = stats.multivariate_normal.logpdf(z, m + c + s * (mu - m), S @ Qz @ S)
+        assert -loss == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_identity_affine_map_reproduces_the_plain_inner_update():
+    spec = workloads.make_model("lg4", 0)
+    om = oracle.OracleModel.from_spec(spec)
+    N, M, L, seed = 10, 16, 4, 3
+    o = oracle.Oracle(om, N, M, L, seed)
+    _, ys = workloads.simulate(spec, 3, 0)
+    x, z, lq = o.init()
+    r1 = o.step(1, ys[0], x, z, lq)
+    r2 = o.step(2, ys[1], r1["x"], r1["z"], r1["lq"])
+    fin = o.finalize(2, ys[1], np.arange(N), r2["anc"], r1["x"], r1["z"], r1["lq"], r2["x"])
+    din = 2 * om.d1 + om.dy + 2 * om.d2
+    W = workloads.init_mlp_weights(din, 16, 2 * om.d2, seed=1)
+    W["W4"][:] = 0.0
+    W["b4"][:] = 0.0  # s = 1, c = 0
+    lib = oracle.load()
+    got = learned.amortised_finalize(om, W, seed, 2, ys[1], r2["anc"], r1["x"], r1["z"], r2["x"], fin["bidx"],
+                                     normals=lambda t, i, p, j, n: oracle.normals(seed, 0, t, i, p, j, n, lib))
+    np.testing.assert_allclose(got["z"], fin["z"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got["lq"], fin["lq"], rtol=1e-10, atol=1e-10)
