@@ -538,9 +538,11 @@ def run_learned(args):
     """The learned-proposal workload: the lg4 model in FP32 with N = 262144 outer and
     M = 64 inner particles. A proposal (MLP 3 x 256 ReLU, 4-component mixture head, BF16
     weights, FP32 accumulation) is trained on the GPU on 10^6 rows the plain filter
-    records; then the filter with it (L = 1) and the plain filter (L = 8) are timed over
-    the same steps, and their accuracy (RMSE of the filtered mean against the Kalman
-    filter, inner ESS) is measured on a separate untimed run."""
+    records, and so is the outer-amortised form (one network row per group); then the
+    filter with the mixture (L = 1), the plain filter (L = 8) and the filter with the
+    amortised form (L = 8) are timed over the same steps, and their accuracy (RMSE of the
+    filtered mean against the Kalman filter, inner ESS) is measured on a separate
+    untimed run."""
     import numpy as np
     import torch
 
@@ -568,6 +570,21 @@ def run_learned(args):
     losses = prop.train(F, Z, w, batch=1024, epochs=3, lr=1e-3, seed=2)
     train_s = time.perf_counter() - t0
     del F, Z, w
+    # the outer-amortised form: rows of the same recorder, one network row per group
+    rec = dpf.Filter(model, 2, 2, 16384, M, 8, seed=1, stream=stream)
+    rec.set_debug(True)
+    for t in range(2):
+        rec.step(ys_tr[t].astype(np.float32))
+    G, Zm, wm = rec.record_amortised()
+    rec.close()
+    Qz = spec.Q[2:, 2:]
+    aprop = dpf.Proposal(2, 2, 2, hidden=256, stream=stream, amortised_Qz=Qz)
+    A0 = workloads.init_mlp_weights(10, 256, 4, seed=0)
+    A0["W4"][:] = 0.0
+    A0["b4"][:] = 0.0
+    aprop.set_weights(A0)
+    alosses = aprop.train(G, Zm, wm, batch=1024, epochs=3, lr=1e-3, seed=2)
+    del G, Zm, wm
     # ---- timing ----
     _, ys = workloads.simulate(spec, W + K + 1, 0)
     yd = torch.tensor(ys.astype(np.float32), device="cuda")
@@ -575,7 +592,7 @@ def run_learned(args):
     def timed(L, use_prop):
         f = dpf.Filter(model, 2, 2, N, M, L, seed=3, stream=stream)
         if use_prop:
-            f.set_proposal(prop)
+            f.set_proposal(use_prop)
         with torch.cuda.stream(stream):
             for k in range(W):
                 f.step_device(yd[k].data_ptr())
@@ -595,10 +612,11 @@ def run_learned(args):
     clocks.start()
     time.sleep(0.3)
     w0 = time.monotonic()
-    ms_l = timed(1, True)
+    ms_l = timed(1, prop)
     w1 = time.monotonic()
     clk = clocks.stop(window=(w0, w1))
-    ms_p = timed(8, False)
+    ms_p = timed(8, None)
+    ms_a = timed(8, aprop)
     # ---- accuracy on an untimed run ----
     T = 25
     _, ya = workloads.simulate(spec, T, 200)
@@ -621,7 +639,7 @@ def run_learned(args):
     def accuracy(L, use_prop):
         f = dpf.Filter(model, 2, 2, N, M, L, seed=5, stream=stream)
         if use_prop:
-            f.set_proposal(prop)
+            f.set_proposal(use_prop)
         err, ess = [], []
         for t in range(T):
             m, _ = f.step(ya[t].astype(np.float32))
@@ -633,8 +651,9 @@ def run_learned(args):
         f.close()
         return float(np.sqrt(np.mean(np.square(err)))), float(np.mean(ess))
 
-    rmse_l, ess_l = accuracy(1, True)
-    rmse_p, ess_p = accuracy(8, False)
+    rmse_l, ess_l = accuracy(1, prop)
+    rmse_p, ess_p = accuracy(8, None)
+    rmse_a, ess_a = accuracy(8, aprop)
     value = N * M * K / (ms_l / 1e3)
     mlp_flop = 2 * (8 * 256 + 2 * 256 * 256 + 256 * 20)  # per inner particle
     line = {
@@ -649,13 +668,17 @@ def run_learned(args):
         "tensor": {"mlp_tflops": mlp_flop * N * M * K / (ms_l / 1e3) / 1e12,
                    "mlp_flop_per_update": mlp_flop},
         "plain": {"L": 8, "value": N * M * K / (ms_p / 1e3), "ms_per_step": ms_p / K},
+        "amortised": {"L": 8, "value": N * M * K / (ms_a / 1e3), "ms_per_step": ms_a / K,
+                      "training_losses": list(alosses), "network_rows_per_step": N},
         "accuracy": {"steps": T, "rmse_vs_kalman_learned": rmse_l, "rmse_vs_kalman_plain": rmse_p,
-                     "inner_ess_learned": ess_l, "inner_ess_plain": ess_p},
+                     "rmse_vs_kalman_amortised": rmse_a, "inner_ess_learned": ess_l,
+                     "inner_ess_plain": ess_p, "inner_ess_amortised": ess_a},
         "gpu_launches": 4 * K,
         "clocks": clk,
     }
     print(json.dumps(line))
     prop.close()
+    aprop.close()
     return 0
 
 

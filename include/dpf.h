@@ -216,7 +216,9 @@ dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ
  *   draws that chose it; "bidx" (N*M int32, the local-resampling ancestors of
  *   that inner update; only when debug recording is on);
  * "head": N x M x dout float, the learned proposal's head outputs of that
- *   inner update (with a proposal set and debug recording on).
+ *   inner update (with a proposal set and debug recording on);
+ * "afeat" (N x (2 d1 + dy + 2 d2) float) and "ahead" (N x 2 d2 float): the
+ *   outer-amortised proposal's group features and network outputs of that update.
  * Element type: the context's precision (or int32). Synchronises the stream.
  */
 dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t bytes);
@@ -350,6 +352,20 @@ dpf_status dpf_proposal_adam_step(dpf_proposal* p, const float* grad_dev, float 
  */
 dpf_status dpf_proposal_train(dpf_proposal* p, const float* F, const float* Z, const float* w, int64_t n,
                               int32_t batch, int32_t epochs, float lr, uint64_t seed, double* losses);
+/*
+ * The outer-amortised form: one network row per outer particle, whose head
+ * gives a diagonal affine map (log s, c; 2 d2 outputs, log s clamped to
+ * [-7, 5]) of that group's prior draws. Inputs (din = 2 d1 + dy + 2 d2): x_{t-1}
+ * of the ancestor, x_t, y_t, and the mean m and per-coordinate variance v of the
+ * group's prior means mu_j = A_zx x_{t-1} + A_zz z_{t-1}^(a, b_j); a particle's
+ * prior draw zhat = mu_j + chol(Q_z) eps (PROP noise) becomes
+ * z = m + c + s (zhat - m), weighted by log N(z; mu_j, Q_z) - log N(zhat; mu_j, Q_z)
+ * + sum log s + log p(y_t | x_t, z). Qz: host, d2 x d2 (row-major), for the
+ * training loss. Training rows (dpf_proposal_train, dpf_proposal_loss_grad):
+ * F = the group features, Z = (z_t, mu_j, m) (3 d2 floats a row).
+ */
+dpf_status dpf_proposal_create_amortised(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, const double* Qz,
+                                         void* stream, dpf_proposal** out);
 /* The head outputs (n x dout floats, device) of n device feature rows by the
  * tensor-core forward pass the filter step uses. Synchronises. */
 dpf_status dpf_proposal_forward(dpf_proposal* p, const float* F, int64_t n, float* out);
@@ -374,6 +390,10 @@ dpf_status dpf_set_proposal(dpf_ctx* ctx, dpf_proposal* p);
  * F: n_outer M x din, Z: n_outer M x d2, w: n_outer M; device floats. Synchronises.
  */
 dpf_status dpf_record_tuples(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* F, float* Z, float* w);
+/* The same rows for the outer-amortised form: G (n_outer M x (2 d1 + dy + 2 d2)),
+ * Z (n_outer M x 3 d2: z_t, mu_j, m), w (n_outer M). Compiled for (d1, d2, dy) =
+ * (2, 2, 2) and M a multiple of 32 up to 256. */
+dpf_status dpf_record_tuples_amortised(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* G, float* Z, float* w);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* dpf_last_error(void);

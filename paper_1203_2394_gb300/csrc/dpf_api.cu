@@ -567,6 +567,11 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   else if (w == "bidx") {
     if (!x->dbg_b) return set_error(DPF_E_INVALID, "dpf_read: bidx needs dpf_set_debug(ctx, 1)");
     src = x->dbg_b; need = 4 * N * M;
+  } else if (w == "afeat" || w == "ahead") {
+    if (!x->proposal || !x->oa_feat || dpf_proposal_kind(x->proposal) != 1)
+      return set_error(DPF_E_INVALID, "dpf_read: afeat/ahead need an outer-amortised proposal");
+    const int d = w == "afeat" ? 2 * x->d1 + x->dy + 2 * x->d2 : 2 * x->d2;
+    src = w == "afeat" ? x->oa_feat : x->oa_out; need = 4 * N * (size_t)d;
   } else if (w == "head") {
     if (!x->dbg_head || !x->proposal)
       return set_error(DPF_E_INVALID, "dpf_read: head needs a learned proposal and dpf_set_debug(ctx, 1)");

@@ -107,6 +107,7 @@ struct Variant {
 const Variant* find_variant(int prec, int d1, int d2, int dy);
 dpf_status learned_inner_step(Ctx& x);  // dpf_learned_step.cu
 int dpf_proposal_dout(const dpf_proposal* p);  // head outputs of a proposal
+int dpf_proposal_kind(const dpf_proposal* p);  // 0 mixture, 1 outer-amortised
 
 }  // namespace dpf
 
@@ -137,6 +138,9 @@ struct dpf_ctx {
   int32_t* dbg_b = nullptr;
   int32_t* anc_prev = nullptr;  // debug: the ancestors the last inner update used
   void* dbg_head = nullptr;     // debug: the learned proposal's head outputs of the last inner update
+  void* oa_bidx = nullptr;      // amortised proposal: local resampling indices, group features, head outputs
+  void* oa_feat = nullptr;
+  void* oa_out = nullptr;
   // small device block: reduction partials, statistics, counters, error word
   void* small = nullptr;
   double* stats = nullptr;          // [logZ_total, logZ_step, ess, s1, mean[d]]

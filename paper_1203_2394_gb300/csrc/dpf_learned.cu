@@ -166,6 +166,54 @@ __global__ void head_loss_kernel(HeadArgs a) {
   }
 }
 
+// Affine (outer-amortised) head: out = (raw log s, c); Z row = (z, mu, m) (3 d2);
+// zhat = m + (z - m - c) / s; -log q = 1/2 (zhat - mu)^T Q^-1 (zhat - mu) + sum log s + const.
+struct AffineArgs {
+  const float* out;
+  const float* Z;
+  const float* w;
+  const double* wsum;
+  float* dout;
+  double* loss;
+  int n, d2;
+  float qinv[kMaxD2 * kMaxD2];
+  float half_logdet;
+};
+
+__global__ void head_affine_kernel(AffineArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.n) return;
+  const int d2 = a.d2;
+  const float* o = a.out + (long long)b * 2 * d2;
+  const float* zr = a.Z + (long long)b * 3 * d2;
+  float* g = a.dout + (long long)b * 2 * d2;
+  float r[kMaxD2], u[kMaxD2], ls[kMaxD2];
+  float sum_ls = 0.f;
+  for (int d = 0; d < d2; ++d) {
+    ls[d] = fminf(fmaxf(o[d], kLogSigMin), kLogSigMax);
+    u[d] = zr[d] - zr[2 * d2 + d] - o[d2 + d];  // z - m - c
+    const float zhat = zr[2 * d2 + d] + u[d] * expf(-ls[d]);
+    r[d] = zhat - zr[d2 + d];
+    sum_ls += ls[d];
+  }
+  float quad = 0.f;
+  float gz[kMaxD2];
+  for (int d = 0; d < d2; ++d) {
+    float v = 0.f;
+    for (int e = 0; e < d2; ++e) v += a.qinv[d * d2 + e] * r[e];
+    gz[d] = v;
+    quad += r[d] * v;
+  }
+  const float wn = (float)((double)a.w[b] / *a.wsum);
+  atomicAdd(a.loss, (double)wn * (0.5 * (double)quad + (double)sum_ls + (double)a.half_logdet));
+  for (int d = 0; d < d2; ++d) {
+    const float is = expf(-ls[d]);
+    const bool inside = o[d] > kLogSigMin && o[d] < kLogSigMax;
+    g[d] = inside ? wn * (-gz[d] * u[d] * is + 1.f) : 0.f;
+    g[d2 + d] = -wn * gz[d] * is;
+  }
+}
+
 __global__ void wsum_kernel(const float* w, int n, double* out) {
   __shared__ double sh[256];
   double s = 0.0;
@@ -203,7 +251,7 @@ __global__ void gather_rows_kernel(const float* F, const float* Z, const float* 
     const float v = F[r * din + c];
     Fb[(long long)b * din + c] = round ? round_bf16(v) : v;
   }
-  for (int c = threadIdx.x; c < d2; c += blockDim.x) Zb[(long long)b * d2 + c] = Z[r * d2 + c];
+  for (int c = threadIdx.x; c < d2; c += blockDim.x) Zb[(long long)b * d2 + c] = Z[r * d2 + c];  // d2: row width
   if (threadIdx.x == 0) wb[b] = w[r];
 }
 
@@ -257,6 +305,7 @@ static dpf_status palloc(dpf_proposal& p, void** ptr, size_t bytes) {
 }
 
 int dpf_proposal_dout(const dpf_proposal* p) { return p->dout; }
+int dpf_proposal_kind(const dpf_proposal* p) { return p->kind; }
 
 static AdamArgs segments(const dpf_proposal& p) {
   AdamArgs a{};
@@ -280,7 +329,7 @@ static dpf_status workspace(dpf_proposal& p, int nb) {
   if (nb <= p.ws_rows) return DPF_OK;
   const size_t H = p.hidden;
   auto take = [&](float** q, size_t n) { return palloc(p, (void**)q, sizeof(float) * n); };
-  if (take(&p.Fb, (size_t)nb * p.din) || take(&p.Zb, (size_t)nb * p.d2) || take(&p.wb, nb) ||
+  if (take(&p.Fb, (size_t)nb * p.din) || take(&p.Zb, (size_t)nb * p.zw) || take(&p.wb, nb) ||
       take(&p.h1, nb * H) || take(&p.h2, nb * H) || take(&p.h3, nb * H) || take(&p.ob, (size_t)nb * p.dout) ||
       take(&p.dA, nb * H) || take(&p.dB, nb * H) || take(&p.dO, (size_t)nb * p.dout) ||
       palloc(p, (void**)&p.perm_d, sizeof(int64_t) * nb))
@@ -304,8 +353,17 @@ static dpf_status fwd_bwd(dpf_proposal& p, int nb, double* loss_dev, float* grad
   sgemm<false, true, 1>(s, nb, H, H, p.h2, H, W3, H, p.h3, H, b3, nullptr, rd);
   sgemm<false, true, 2>(s, nb, dO, H, p.h3, H, W4, H, p.ob, dO, b4);
   wsum_kernel<<<1, 256, 0, s>>>(p.wb, nb, p.wsum_d);
-  HeadArgs ha{p.ob, p.Zb, p.wb, p.wsum_d, p.dO, loss_dev, nb, p.d2, p.C, dO};
-  head_loss_kernel<<<(nb + 127) / 128, 128, 0, s>>>(ha);
+  if (p.kind == 0) {
+    HeadArgs ha{p.ob, p.Zb, p.wb, p.wsum_d, p.dO, loss_dev, nb, p.d2, p.C, dO};
+    head_loss_kernel<<<(nb + 127) / 128, 128, 0, s>>>(ha);
+  } else {
+    AffineArgs aa{};
+    aa.out = p.ob; aa.Z = p.Zb; aa.w = p.wb; aa.wsum = p.wsum_d; aa.dout = p.dO; aa.loss = loss_dev;
+    aa.n = nb; aa.d2 = p.d2;
+    memcpy(aa.qinv, p.qinv, sizeof(aa.qinv));
+    aa.half_logdet = p.half_logdet;
+    head_affine_kernel<<<(nb + 127) / 128, 128, 0, s>>>(aa);
+  }
   if (!grad) return cuda_error(cudaGetLastError(), "proposal forward");
   float *gW1 = grad + p.offW[0], *gW2 = grad + p.offW[1], *gW3 = grad + p.offW[2], *gW4 = grad + p.offW[3];
   float *gb1 = grad + p.offB[0], *gb2 = grad + p.offB[1], *gb3 = grad + p.offB[2], *gb4 = grad + p.offB[3];
@@ -355,31 +413,22 @@ static uint64_t splitmix64(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
-}  // namespace dpf
-
-using namespace dpf;
-
-extern "C" {
-
-dpf_status dpf_proposal_create(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, int32_t components,
-                               void* stream, dpf_proposal** out) {
-  clear_error();
-  if (!out) return set_error(DPF_E_INVALID, "dpf_proposal_create: null output");
-  *out = nullptr;
-  const int din = 2 * d1 + d2 + dy;
+static dpf_status proposal_make(int kind, int32_t d1, int32_t d2, int32_t dy, int32_t hidden, int32_t components,
+                                int din, int dout, int zw, void* stream, dpf_proposal** out) {
   if (d1 < 1 || d2 < 1 || dy < 1 || din > kMaxDin || d2 > kMaxD2 || hidden < 16 || hidden > kMaxHidden ||
-      hidden % 16 || components < 1 || components > kMaxComponents ||
-      components * (1 + 2 * d2) > kMaxDout)
+      hidden % 16 || components < 1 || components > kMaxComponents || dout > kMaxDout)
     return set_error(DPF_E_INVALID, "dpf_proposal_create: unsupported sizes (din <= 16, d2 <= 8, hidden a "
                                     "multiple of 16 up to 256, components 1..8, head <= 128)");
   dpf_proposal* p = new dpf_proposal();
+  p->kind = kind;
   p->d1 = d1;
   p->d2 = d2;
   p->dy = dy;
   p->din = din;
   p->hidden = hidden;
   p->C = components;
-  p->dout = components * (1 + 2 * d2);
+  p->dout = dout;
+  p->zw = zw;
   p->stream = (cudaStream_t)stream;
   const int H = hidden;
   p->rows[0] = H; p->cols[0] = din;
@@ -412,6 +461,63 @@ dpf_status dpf_proposal_create(int32_t d1, int32_t d2, int32_t dy, int32_t hidde
     return cuda_error(e, "dpf_proposal_create");
   }
   *out = p;
+  return DPF_OK;
+}
+
+}  // namespace dpf
+
+using namespace dpf;
+
+extern "C" {
+
+dpf_status dpf_proposal_create(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, int32_t components,
+                               void* stream, dpf_proposal** out) {
+  clear_error();
+  if (!out) return set_error(DPF_E_INVALID, "dpf_proposal_create: null output");
+  *out = nullptr;
+  return dpf::proposal_make(0, d1, d2, dy, hidden, components, 2 * d1 + d2 + dy, components * (1 + 2 * d2), d2,
+                            stream, out);
+}
+
+dpf_status dpf_proposal_create_amortised(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, const double* Qz,
+                                         void* stream, dpf_proposal** out) {
+  clear_error();
+  if (!out || !Qz) return set_error(DPF_E_INVALID, "dpf_proposal_create_amortised: null argument");
+  *out = nullptr;
+  if (d2 < 1 || d2 > kMaxD2) return set_error(DPF_E_INVALID, "dpf_proposal_create_amortised: d2 in 1..8");
+  // Q_z^-1 and log det(2 pi Q_z) by a Cholesky factorisation on the host
+  std::vector<double> Lc(d2 * d2, 0.0), inv(d2 * d2, 0.0);
+  for (int r = 0; r < d2; ++r)
+    for (int c = 0; c <= r; ++c) {
+      double v = Qz[r * d2 + c];
+      for (int k = 0; k < c; ++k) v -= Lc[r * d2 + k] * Lc[c * d2 + k];
+      if (r == c) {
+        if (!(v > 0)) return set_error(DPF_E_INVALID, "dpf_proposal_create_amortised: Q_z not positive definite");
+        Lc[r * d2 + r] = std::sqrt(v);
+      } else {
+        Lc[r * d2 + c] = v / Lc[c * d2 + c];
+      }
+    }
+  double logdet = 0.0;
+  for (int r = 0; r < d2; ++r) logdet += 2.0 * std::log(Lc[r * d2 + r]);
+  for (int col = 0; col < d2; ++col) {  // solve Q x = e_col
+    std::vector<double> yv(d2), xv(d2);
+    for (int r = 0; r < d2; ++r) {
+      double v = (r == col) ? 1.0 : 0.0;
+      for (int k = 0; k < r; ++k) v -= Lc[r * d2 + k] * yv[k];
+      yv[r] = v / Lc[r * d2 + r];
+    }
+    for (int r = d2 - 1; r >= 0; --r) {
+      double v = yv[r];
+      for (int k = r + 1; k < d2; ++k) v -= Lc[k * d2 + r] * xv[k];
+      xv[r] = v / Lc[r * d2 + r];
+    }
+    for (int r = 0; r < d2; ++r) inv[r * d2 + col] = xv[r];
+  }
+  dpf_status st = dpf::proposal_make(1, d1, d2, dy, hidden, 1, 2 * d1 + dy + 2 * d2, 2 * d2, 3 * d2, stream, out);
+  if (st) return st;
+  for (int q = 0; q < d2 * d2; ++q) (*out)->qinv[q] = (float)inv[q];
+  (*out)->half_logdet = (float)(0.5 * (logdet + d2 * std::log(2.0 * M_PI)));
   return DPF_OK;
 }
 
@@ -464,7 +570,7 @@ dpf_status dpf_proposal_loss_grad(dpf_proposal* p, const float* F, const float* 
   cudaStream_t s = p->stream;
   const int rd = p->bf16 ? 1 : 0;
   round_rows_kernel<<<(unsigned)((n * p->din + 255) / 256), 256, 0, s>>>(F, p->Fb, n * p->din, rd);
-  cudaMemcpyAsync(p->Zb, Z, sizeof(float) * n * p->d2, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->Zb, Z, sizeof(float) * n * p->zw, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(p->wb, w, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(p->loss_d, 0, sizeof(double), s);
   st = fwd_bwd(*p, (int)n, p->loss_d, grad_dev);
@@ -524,7 +630,7 @@ dpf_status dpf_proposal_train(dpf_proposal* p, const float* F, const float* Z, c
     for (int64_t bi = 0; bi < nbatches && !st; ++bi) {
       const int64_t b0 = bi * nb_max;
       const int nb = (int)std::min<int64_t>(nb_max, n - b0);
-      gather_rows_kernel<<<nb, 32, 0, s>>>(F, Z, w, perm_dev + b0, nb, p->din, p->d2, p->Fb, p->Zb, p->wb, rd);
+      gather_rows_kernel<<<nb, 32, 0, s>>>(F, Z, w, perm_dev + b0, nb, p->din, p->zw, p->Fb, p->Zb, p->wb, rd);
       st = fwd_bwd(*p, nb, eloss_d + ep, p->grad);
       if (!st) st = adam(*p, p->grad, lr);
     }

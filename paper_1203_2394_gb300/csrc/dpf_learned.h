@@ -23,7 +23,11 @@ dpf_status proposal_requantize(dpf_proposal& p);
 }  // namespace dpf
 
 struct dpf_proposal {
+  int kind = 0;  // 0: mixture of Gaussians per inner particle; 1: per-group affine map of the prior draws
   int d1 = 0, d2 = 0, dy = 0, din = 0, hidden = 0, C = 0, dout = 0;
+  int zw = 0;    // floats per training target row: d2 (kind 0) or 3 d2 (z, prior mean, group centre)
+  float qinv[dpf::kMaxD2 * dpf::kMaxD2] = {};  // kind 1: Q_z^-1 (row-major) for the training loss
+  float half_logdet = 0.f;                      // kind 1: 1/2 log det(2 pi Q_z)
   long long nparams = 0;
   long long offW[dpf::kLayers] = {}, offB[dpf::kLayers] = {};
   int rows[dpf::kLayers] = {}, cols[dpf::kLayers] = {};

@@ -593,6 +593,380 @@ static uint32_t scale_for(int n) {
   return 1u << (31 - ceil_log2_i(n));
 }
 
+// ---- the outer-amortised proposal: one network row per outer particle ----
+// Group features (x_{t-1} of the ancestor, x_t, y_t, m, v) with mu_ij = A_zx x_{t-1} +
+// A_zz z_{t-1}^(a, b_ij), m and v their mean and variance over j; the head gives the
+// group's (raw log s, c); the particle draws zhat = mu + L_qz eps (PROP noise) and
+// takes z = m + c + s (zhat - m), weighted by log N(z; mu, Q_z) - log N(zhat; mu, Q_z)
+// + sum log s + log p(y_t | x_t, z).
+
+// Selection, local resampling and the group features; one warp per outer particle,
+// PP = M / 32 consecutive inner particles a lane.
+template <int D1, int D2, int DY, bool XZ, int PP>
+__global__ void __launch_bounds__(128)
+    oa_prepare_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const __grid_constant__ StepArgs<float> a,
+                      int32_t* __restrict__ bidx_out, float* __restrict__ feat, int din) {
+  constexpr int M = 32 * PP;
+  __shared__ uint32_t cum_s[4][M];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long g = blockIdx.x * 4LL + w;
+  if (g >= a.N) return;  // whole warps only
+  uint32_t* cum = cum_s[w];
+  const float NEG = -INFINITY;
+  const long long NM = a.N * (long long)M;
+  const int anc_g = a.anc[g];
+  const int L = a.L;
+  int msel;
+  {
+    const float l0 = lane < L ? a.lwh_old[(long long)anc_g * L + lane] : NEG;
+    const float l1 = lane + 32 < L ? a.lwh_old[(long long)anc_g * L + lane + 32] : NEG;
+    const float mx = warp_max(fmaxf(l0, l1));
+    const uint32_t c0 = lane < L ? (uint32_t)floorf(exp2f((l0 - mx) * 1.4426950408889634f) * a.scaleL) : 0u;
+    const uint32_t c1 = lane + 32 < L ? (uint32_t)floorf(exp2f((l1 - mx) * 1.4426950408889634f) * a.scaleL) : 0u;
+    uint32_t s0 = c0, s1 = c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
+      if (lane >= o) {
+        s0 += n0;
+        s1 += n1;
+      }
+    }
+    const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
+    const uint64_t Cs = (uint64_t)tot0 + tot1;
+    const uint32_t usel = philox(ctr(a.t - 1, (uint32_t)g, P_SEL, 0u, 0u), a.key).x;
+    const uint64_t rhs = (uint64_t)usel * Cs;
+    const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
+    const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
+    msel = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
+    if ((Cs == 0 || msel >= L) && lane == 0) atomicOr(a.err, ERR_NUMERIC);
+    if (msel >= L) msel = L - 1;
+  }
+  float xt[D1], xa[D1];
+#pragma unroll
+  for (int c = 0; c < D1; ++c) {
+    xt[c] = a.xbb_old[((long long)anc_g * L + msel) * D1 + c];
+    xa[c] = a.x_old[(long long)anc_g * a.xp + c];
+  }
+  if (lane == 0) {
+    a.sel[g] = msel;
+    for (int c = 0; c < a.xp; ++c) a.x_new[g * a.xp + c] = c < D1 ? xt[c < D1 ? c : 0] : 0.f;
+  }
+  float wres[D1];
+  if (XZ) {
+    float mxa[D1];
+    mu_x(mc, xa, a.gcos_prev, mxa);
+#pragma unroll
+    for (int r = 0; r < D1; ++r) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c <= r; ++c) v += mc.LqxInv[r][c] * (xt[c] - mxa[c]);
+      wres[r] = v;
+    }
+  }
+  float al[PP];
+  float amax = NEG;
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    const int k = lane * PP + p;
+    float v0 = a.lq_old[(long long)anc_g * M + k];
+    if (XZ) {
+      float q = 0.f;
+#pragma unroll
+      for (int r = 0; r < D1; ++r) {
+        float v = wres[r];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) v -= mc.WAxz[r][c] * a.z_old[c * NM + (long long)anc_g * M + k];
+        q += v * v;
+      }
+      v0 -= 0.5f * q;
+    }
+    al[p] = v0;
+    amax = fmaxf(amax, v0);
+  }
+  amax = warp_max(amax);
+  uint32_t loc[PP];
+  uint32_t run = 0;
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    run += (uint32_t)floorf(exp2f((al[p] - amax) * 1.4426950408889634f) * a.scaleM);
+    loc[p] = run;
+  }
+  uint32_t inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += n;
+  }
+#pragma unroll
+  for (int p = 0; p < PP; ++p) cum[lane * PP + p] = loc[p] + inc - run;
+  __syncwarp();
+  const uint32_t C = cum[M - 1];
+  if (C == 0 && lane == 0) atomicOr(a.err, ERR_NUMERIC);
+  const uint32_t uin = philox(ctr(a.t - 1, (uint32_t)g, P_INNER, 0u, 0u), a.key).x;
+  float mu[PP][D2];
+  float msum[D2];
+#pragma unroll
+  for (int d = 0; d < D2; ++d) msum[d] = 0.f;
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    const int k = lane * PP + p;
+    const int b = sys_local_pick(cum, M, C, M, k, uin);
+    bidx_out[g * M + k] = b;
+    if (a.dbg_b) a.dbg_b[g * M + k] = b;
+    float zb[D2];
+#pragma unroll
+    for (int c = 0; c < D2; ++c) zb[c] = a.z_old[c * NM + (long long)anc_g * M + b];
+#pragma unroll
+    for (int r = 0; r < D2; ++r) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * zb[c];
+      mu[p][r] = v;
+      msum[r] += v;
+    }
+  }
+  float m[D2], vs[D2];
+#pragma unroll
+  for (int d = 0; d < D2; ++d) m[d] = warp_sum(msum[d]) / (float)M;
+#pragma unroll
+  for (int d = 0; d < D2; ++d) {
+    float q = 0.f;
+#pragma unroll
+    for (int p = 0; p < PP; ++p) q += (mu[p][d] - m[d]) * (mu[p][d] - m[d]);
+    vs[d] = warp_sum(q) / (float)M;
+  }
+  if (lane == 0) {
+    float* f = feat + g * din;
+    int k = 0;
+#pragma unroll
+    for (int c = 0; c < D1; ++c) f[k++] = xa[c];
+#pragma unroll
+    for (int c = 0; c < D1; ++c) f[k++] = xt[c];
+#pragma unroll
+    for (int q = 0; q < DY; ++q) f[k++] = a.y_prev[q];
+#pragma unroll
+    for (int d = 0; d < D2; ++d) f[k++] = m[d];
+#pragma unroll
+    for (int d = 0; d < D2; ++d) f[k++] = vs[d];
+  }
+}
+
+// The draws and weights of the amortised proposal; one warp per outer particle.
+template <int D1, int D2, int DY, int PP>
+__global__ void __launch_bounds__(128)
+    oa_update_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const __grid_constant__ StepArgs<float> a,
+                     const int32_t* __restrict__ bidx, const float* __restrict__ feat, const float* __restrict__ out,
+                     int din, int dout) {
+  constexpr int M = 32 * PP;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long g = blockIdx.x * 4LL + w;
+  if (g >= a.N) return;
+  const float NEG = -INFINITY;
+  const long long NM = a.N * (long long)M;
+  const int anc_g = a.anc[g];
+  float xa[D1], xt[D1];
+#pragma unroll
+  for (int c = 0; c < D1; ++c) {
+    xa[c] = a.x_old[(long long)anc_g * a.xp + c];
+    xt[c] = a.x_new[g * a.xp + c];
+  }
+  float ls[D2], sc[D2], cc[D2], m[D2];
+  float sum_ls = 0.f;
+#pragma unroll
+  for (int d = 0; d < D2; ++d) {
+    ls[d] = fminf(fmaxf(out[g * dout + d], kLogSigMin), kLogSigMax);
+    sc[d] = expf(ls[d]);
+    cc[d] = out[g * dout + D2 + d];
+    m[d] = feat[g * din + 2 * D1 + DY + d];
+    sum_ls += ls[d];
+  }
+  float hx[DY];
+  h_x(mc, xt, hx);
+  float z[PP][D2], lr[PP];
+  float lmax = NEG;
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    const int k = lane * PP + p;
+    const int b = bidx[g * M + k];
+    float zb[D2], mu[D2];
+#pragma unroll
+    for (int c = 0; c < D2; ++c) zb[c] = a.z_old[c * NM + (long long)anc_g * M + b];
+#pragma unroll
+    for (int r = 0; r < D2; ++r) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * zb[c];
+      mu[r] = v;
+    }
+    float eps[D2];
+    normals<D2>(a.key, a.t - 1, (uint32_t)g, P_PROP, (uint32_t)k, eps);
+    float e2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < D2; ++r) {
+      float zh = mu[r];
+#pragma unroll
+      for (int c = 0; c <= r; ++c) zh += mc.Lqz[r][c] * eps[c];
+      z[p][r] = m[r] + cc[r] + sc[r] * (zh - m[r]);
+      e2 += eps[r] * eps[r];
+    }
+    // log N(z; mu, Q_z) by forward substitution with L_qz
+    float rp[D2];
+    float lpz = 0.f;
+#pragma unroll
+    for (int r = 0; r < D2; ++r) {
+      float v = z[p][r] - mu[r];
+#pragma unroll
+      for (int c = 0; c < r; ++c) v -= mc.Lqz[r][c] * rp[c];
+      rp[r] = v / mc.Lqz[r][r];
+      lpz -= 0.5f * rp[r] * rp[r];
+    }
+    float lpy = 0.f;
+#pragma unroll
+    for (int q = 0; q < DY; ++q) {
+      float res[DY];
+      (void)res;
+      float v = 0.f;
+#pragma unroll
+      for (int c2 = 0; c2 <= q; ++c2) {
+        float rr = a.y_prev[c2] - hx[c2];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) rr -= mc.Hz[c2][c] * z[p][c];
+        v += mc.LrInv[q][c2] * rr;
+      }
+      lpy -= 0.5f * v * v;
+    }
+    lr[p] = lpz - (-0.5f * e2 - sum_ls) + lpy;
+    lmax = fmaxf(lmax, lr[p]);
+  }
+  lmax = warp_max(lmax);
+  float se = 0.f;
+#pragma unroll
+  for (int p = 0; p < PP; ++p) se += expf(lr[p] - lmax);
+  const float lse = lmax + logf(warp_sum(se));
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    const int k = lane * PP + p;
+#pragma unroll
+    for (int d = 0; d < D2; ++d) a.z_new[d * NM + g * M + k] = z[p][d];
+    const float lq = lr[p] - lse;
+    a.lq_new[g * M + k] = lq;
+    if (!(lq == lq)) atomicOr(a.err, ERR_NUMERIC);
+  }
+}
+
+// Training rows of the amortised proposal from the last inner update: one warp per
+// outer particle writes, for each of its inner particles, the group features and
+// (z_t, mu, m), and w = exp(lq_t) / N.
+template <int D1, int D2, int DY, int PP>
+__global__ void __launch_bounds__(128)
+    oa_record_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const float* x_old, const float* x_new,
+                     const float* z_old, const float* z_new, const float* lq_new, const float* y_prev,
+                     const int32_t* anc_prev, const int32_t* bidx, long long N, int xp, long long i0,
+                     long long n_outer, float* G, float* Zr, float* wr) {
+  constexpr int M = 32 * PP;
+  constexpr int DIN = 2 * D1 + DY + 2 * D2;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long q = blockIdx.x * 4LL + w;
+  if (q >= n_outer) return;
+  const long long g = i0 + q;
+  const long long NM = N * (long long)M;
+  const int a = anc_prev[g];
+  float xa[D1], xt[D1];
+#pragma unroll
+  for (int c = 0; c < D1; ++c) {
+    xa[c] = x_old[(long long)a * xp + c];
+    xt[c] = x_new[g * xp + c];
+  }
+  float mu[PP][D2], msum[D2];
+#pragma unroll
+  for (int d = 0; d < D2; ++d) msum[d] = 0.f;
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    const int k = lane * PP + p;
+    const int b = bidx[g * M + k];
+#pragma unroll
+    for (int r = 0; r < D2; ++r) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * z_old[c * NM + (long long)a * M + b];
+      mu[p][r] = v;
+      msum[r] += v;
+    }
+  }
+  float m[D2], vs[D2];
+#pragma unroll
+  for (int d = 0; d < D2; ++d) m[d] = warp_sum(msum[d]) / (float)M;
+#pragma unroll
+  for (int d = 0; d < D2; ++d) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int p = 0; p < PP; ++p) s2 += (mu[p][d] - m[d]) * (mu[p][d] - m[d]);
+    vs[d] = warp_sum(s2) / (float)M;
+  }
+#pragma unroll
+  for (int p = 0; p < PP; ++p) {
+    const int k = lane * PP + p;
+    const long long e = q * M + k;
+    float* f = G + e * DIN;
+    int o = 0;
+#pragma unroll
+    for (int c = 0; c < D1; ++c) f[o++] = xa[c];
+#pragma unroll
+    for (int c = 0; c < D1; ++c) f[o++] = xt[c];
+#pragma unroll
+    for (int c = 0; c < DY; ++c) f[o++] = y_prev[c];
+#pragma unroll
+    for (int d = 0; d < D2; ++d) f[o++] = m[d];
+#pragma unroll
+    for (int d = 0; d < D2; ++d) f[o++] = vs[d];
+    float* zr = Zr + e * 3 * D2;
+#pragma unroll
+    for (int d = 0; d < D2; ++d) {
+      zr[d] = z_new[d * NM + g * M + k];
+      zr[D2 + d] = mu[p][d];
+      zr[2 * D2 + d] = m[d];
+    }
+    wr[e] = expf(lq_new[g * M + k]) / (float)N;
+  }
+}
+
+template <int PP>
+static dpf_status oa_step_pp(Ctx& x, const MC<float, 2, 2, 2>& mc, StepArgs<float>& a, dpf_proposal& p) {
+  const unsigned blocks = (unsigned)((x.N + 3) / 4);
+  if (x.hm.xz)
+    oa_prepare_kernel<2, 2, 2, true, PP><<<blocks, 128, 0, x.stream>>>(mc, a, (int32_t*)x.oa_bidx, (float*)x.oa_feat, p.din);
+  else
+    oa_prepare_kernel<2, 2, 2, false, PP><<<blocks, 128, 0, x.stream>>>(mc, a, (int32_t*)x.oa_bidx, (float*)x.oa_feat, p.din);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "amortised prepare launch");
+  LearnArgs la{};
+  la.wp = (const unsigned char*)p.packed;
+  la.din = p.din;
+  la.dout = p.dout;
+  la.C = 1;
+  la.F = (const float*)x.oa_feat;
+  la.out = (float*)x.oa_out;
+  la.nrows = x.N;
+  la.err = x.err;
+  MC<float, 2, 2, 2> mc0;
+  memset(&mc0, 0, sizeof(mc0));
+  StepArgs<float> a0{};
+  a0.err = x.err;
+  dpf_status st = launch_learned<0, 2, 2, 2, false, kFilterComponents>(mc0, a0, la, x.N, x.stream);
+  if (st) return st;
+  oa_update_kernel<2, 2, 2, PP><<<blocks, 128, 0, x.stream>>>(mc, a, (const int32_t*)x.oa_bidx,
+                                                               (const float*)x.oa_feat, (const float*)x.oa_out,
+                                                               p.din, p.dout);
+  return cuda_error(cudaGetLastError(), "amortised update launch");
+}
+
 // The inner update of the coming step with the learned proposal (the variant
 // (FP32, 2, 2, 2)); then the look-ahead runs alone from the materialised state.
 dpf_status learned_inner_step(Ctx& x) {
@@ -612,6 +986,14 @@ dpf_status learned_inner_step(Ctx& x) {
   la.scaleC = scale_for(p.C);
   la.err = x.err;
   const MC<float, 2, 2, 2>& mc = *reinterpret_cast<const MC<float, 2, 2, 2>*>(x.mconst.data());
+  if (p.kind == 1) {
+    switch (x.M) {
+      case 32: return oa_step_pp<1>(x, mc, a, p);
+      case 64: return oa_step_pp<2>(x, mc, a, p);
+      case 128: return oa_step_pp<4>(x, mc, a, p);
+      default: return oa_step_pp<8>(x, mc, a, p);
+    }
+  }
   const long long rows = x.N * (long long)x.M;
   return x.hm.xz ? launch_learned<1, 2, 2, 2, true, kFilterComponents>(mc, a, la, rows, x.stream)
                  : launch_learned<1, 2, 2, 2, false, kFilterComponents>(mc, a, la, rows, x.stream);
@@ -696,12 +1078,58 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
   }
   if (x->prec != DPF_F32 || p->d1 != x->d1 || p->d2 != x->d2 || p->dy != x->dy)
     return set_error(DPF_E_INVALID, "dpf_set_proposal: the proposal's (d1, d2, dy) and FP32 must match the filter");
-  if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH || p->C != kFilterComponents ||
-      !(x->M == 32 || x->M == 64 || x->M == 128))
+  if (p->kind == 0 && (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH || p->C != kFilterComponents ||
+                       !(x->M == 32 || x->M == 64 || x->M == 128)))
     return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: compiled for (d1, d2, dy) = (2, 2, 2), hidden 256, "
                                         "4 components and M in {32, 64, 128}");
+  if (p->kind == 1) {
+    if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH ||
+        !(x->M == 32 || x->M == 64 || x->M == 128 || x->M == 256))
+      return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: the amortised pass is compiled for (d1, d2, dy) = "
+                                          "(2, 2, 2), hidden 256 and M in {32, 64, 128, 256}");
+    auto grow = [&](void** q, size_t bytes) -> cudaError_t {
+      if (*q) return cudaSuccess;
+      cudaError_t e = cudaMalloc(q, bytes);
+      if (e == cudaSuccess) x->allocs.push_back(*q);
+      return e;
+    };
+    cudaError_t e = grow(&x->oa_bidx, sizeof(int32_t) * (size_t)x->N * x->M);
+    if (e == cudaSuccess) e = grow(&x->oa_feat, sizeof(float) * (size_t)x->N * LDIN);
+    if (e == cudaSuccess) e = grow(&x->oa_out, sizeof(float) * (size_t)x->N * LNP);
+    if (e != cudaSuccess) return cuda_error(e, "dpf_set_proposal: amortised buffers");
+  }
   x->proposal = p;
   return DPF_OK;
+}
+
+dpf_status dpf_record_tuples_amortised(dpf_ctx* x, int64_t i0, int64_t n_outer, float* G, float* Z, float* w) {
+  clear_error();
+  if (!x || !G || !Z || !w || i0 < 0 || n_outer < 1 || i0 + n_outer > x->N)
+    return set_error(DPF_E_INVALID, "dpf_record_tuples_amortised: bad arguments");
+  if (x->t < 2 || !x->dbg_b || !x->anc_prev || x->prec != DPF_F32)
+    return set_error(DPF_E_INVALID, "dpf_record_tuples_amortised: needs an FP32 filter stepped at least twice "
+                                    "with debug recording on");
+  if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || x->M % 32 || x->M > 256)
+    return set_error(DPF_E_UNSUPPORTED, "dpf_record_tuples_amortised: compiled for (2, 2, 2), M in {32, ..., 256}");
+  const long long t = x->t;
+  const MC<float, 2, 2, 2>& mc = *reinterpret_cast<const MC<float, 2, 2, 2>*>(x->mconst.data());
+  const unsigned blocks = (unsigned)((n_outer + 3) / 4);
+  auto go = [&](auto kern) {
+    kern<<<blocks, 128, 0, x->stream>>>(mc, (const float*)x->x[t % 2], (const float*)x->x[(t + 1) % 2],
+                                        (const float*)x->z[t % 2], (const float*)x->z[(t + 1) % 2],
+                                        (const float*)x->lq[(t + 1) % 2],
+                                        (const float*)x->yb + ((t + 1) % 2) * x->dy, x->anc_prev, x->dbg_b, x->N,
+                                        x->xp, i0, n_outer, G, Z, w);
+  };
+  switch (x->M) {
+    case 32: go(oa_record_kernel<2, 2, 2, 1>); break;
+    case 64: go(oa_record_kernel<2, 2, 2, 2>); break;
+    case 128: go(oa_record_kernel<2, 2, 2, 4>); break;
+    default: go(oa_record_kernel<2, 2, 2, 8>); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return cuda_error(e, "dpf_record_tuples_amortised");
 }
 
 dpf_status dpf_record_tuples(dpf_ctx* x, int64_t i0, int64_t n_outer, float* F, float* Z, float* w) {

@@ -59,6 +59,7 @@ SIGNATURES = [
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_proposal_create", ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _P, _P]),
+    ("dpf_proposal_create_amortised", ctypes.c_int, [_I32, _I32, _I32, _I32, _P, _P, _P]),
     ("dpf_proposal_num_params", ctypes.c_int, [_P, _P]),
     ("dpf_proposal_set_weights", ctypes.c_int, [_P, _P, _I64]),
     ("dpf_proposal_get_weights", ctypes.c_int, [_P, _P, _I64]),
@@ -70,6 +71,7 @@ SIGNATURES = [
     ("dpf_proposal_destroy", None, [_P]),
     ("dpf_set_proposal", ctypes.c_int, [_P, _P]),
     ("dpf_record_tuples", ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
+    ("dpf_record_tuples_amortised", ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
     ("dpf_state_bytes", ctypes.c_int, [_P, _P]),
     ("dpf_get_state", ctypes.c_int, [_P, _P, _SZ]),
     ("dpf_set_state", ctypes.c_int, [_P, _P, _SZ]),
@@ -197,6 +199,8 @@ class Filter:
         "x": lambda s: (s.N, s.d1), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
         "bidx": lambda s: (s.N, s.M),
         "head": lambda s: (s.N, s.M, s.proposal.dout),
+        "afeat": lambda s: (s.N, 2 * s.d1 + s.dy + 2 * s.d2),
+        "ahead": lambda s: (s.N, 2 * s.d2),
     }
 
     def read(self, which: str) -> np.ndarray:
@@ -231,6 +235,20 @@ class Filter:
         """Use a learned inner proposal from the next step on (None: the prior)."""
         check(self._lib.dpf_set_proposal(self.h, proposal.h if proposal is not None else None))
         self.proposal = proposal
+
+    def record_amortised(self, i0=0, n_outer=None):
+        """Training rows of the last inner update for the outer-amortised proposal: device
+        tensors G (n, 2 d1 + dy + 2 d2), Z (n, 3 d2), w (n)."""
+        import torch
+        n_outer = self.N - i0 if n_outer is None else n_outer
+        din = 2 * self.d1 + self.dy + 2 * self.d2
+        n = n_outer * self.M
+        G = torch.empty((n, din), dtype=torch.float32, device="cuda")
+        Z = torch.empty((n, 3 * self.d2), dtype=torch.float32, device="cuda")
+        w = torch.empty((n,), dtype=torch.float32, device="cuda")
+        check(self._lib.dpf_record_tuples_amortised(self.h, int(i0), int(n_outer), G.data_ptr(), Z.data_ptr(),
+                                                    w.data_ptr()))
+        return G, Z, w
 
     def record(self, i0=0, n_outer=None):
         """Training rows of the last inner update (see ``dpf_record_tuples``): device
@@ -397,17 +415,29 @@ def tc_matmul(A, B, mode=DPF_TC_TF32X3, stream=None):
 
 class Proposal:
     """The learned inner proposal (``dpf_proposal_*``): an MLP of three hidden ReLU layers
-    with a Gaussian-mixture head, trained on the GPU by the library's kernels."""
+    with a Gaussian-mixture head (per inner particle), or with the Qz given, the
+    outer-amortised form (one row per outer particle, a diagonal affine map of the
+    group's prior draws); trained on the GPU by the library's kernels."""
 
-    def __init__(self, d1, d2, dy, hidden=256, components=4, stream=None):
+    def __init__(self, d1, d2, dy, hidden=256, components=4, stream=None, amortised_Qz=None):
         self.d1, self.d2, self.dy = int(d1), int(d2), int(dy)
-        self.hidden, self.C = int(hidden), int(components)
-        self.din = 2 * self.d1 + self.d2 + self.dy
-        self.dout = self.C * (1 + 2 * self.d2)
+        self.hidden = int(hidden)
         self._lib = lib()
         h = ctypes.c_void_p()
-        check(self._lib.dpf_proposal_create(self.d1, self.d2, self.dy, self.hidden, self.C,
-                                            _stream_ptr(stream), ctypes.byref(h)))
+        if amortised_Qz is None:
+            self.kind, self.C = 0, int(components)
+            self.din = 2 * self.d1 + self.d2 + self.dy
+            self.dout = self.C * (1 + 2 * self.d2)
+            check(self._lib.dpf_proposal_create(self.d1, self.d2, self.dy, self.hidden, self.C,
+                                                _stream_ptr(stream), ctypes.byref(h)))
+        else:
+            self.kind, self.C = 1, 1
+            self.din = 2 * self.d1 + self.dy + 2 * self.d2
+            self.dout = 2 * self.d2
+            q = np.ascontiguousarray(amortised_Qz, dtype=np.float64)
+            check(self._lib.dpf_proposal_create_amortised(self.d1, self.d2, self.dy, self.hidden,
+                                                          q.ctypes.data, _stream_ptr(stream),
+                                                          ctypes.byref(h)))
         self.h = h
         n = ctypes.c_int64()
         check(self._lib.dpf_proposal_num_params(self.h, ctypes.byref(n)))
