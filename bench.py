@@ -556,13 +556,19 @@ def run_learned(args):
     stream = torch.cuda.Stream()
     # ---- training rows and training ----
     t0 = time.perf_counter()
-    _, ys_tr = workloads.simulate(spec, 3, 100)
-    rec = dpf.Filter(model, 2, 2, 16384, M, 8, seed=1, stream=stream)
+    # 8 steps x 2048 outer x 64 inner = 1,048,576 rows of the plain filter (L = 8)
+    _, ys_tr = workloads.simulate(spec, 10, 100)
+    rec = dpf.Filter(model, 2, 2, 2048, M, 8, seed=1, stream=stream)
     rec.set_debug(True)
-    for t in range(2):
+    rows, arows = [], []
+    for t in range(9):
         rec.step(ys_tr[t].astype(np.float32))
-    F, Z, w = rec.record()
+        if t >= 1:
+            rows.append(rec.record())
+            arows.append(rec.record_amortised())
     rec.close()
+    F = torch.cat([r[0] for r in rows]); Z = torch.cat([r[1] for r in rows]); w = torch.cat([r[2] for r in rows])
+    del rows
     prop = dpf.Proposal(2, 2, 2, hidden=256, components=4, stream=stream)
     W0 = workloads.init_mlp_weights(8, 256, 20, seed=0)
     W0["b4"][12:] = np.log(np.sqrt(0.1))
@@ -571,12 +577,8 @@ def run_learned(args):
     train_s = time.perf_counter() - t0
     del F, Z, w
     # the outer-amortised form: rows of the same recorder, one network row per group
-    rec = dpf.Filter(model, 2, 2, 16384, M, 8, seed=1, stream=stream)
-    rec.set_debug(True)
-    for t in range(2):
-        rec.step(ys_tr[t].astype(np.float32))
-    G, Zm, wm = rec.record_amortised()
-    rec.close()
+    G = torch.cat([r[0] for r in arows]); Zm = torch.cat([r[1] for r in arows]); wm = torch.cat([r[2] for r in arows])
+    del arows
     Qz = spec.Q[2:, 2:]
     aprop = dpf.Proposal(2, 2, 2, hidden=256, stream=stream, amortised_Qz=Qz)
     A0 = workloads.init_mlp_weights(10, 256, 4, seed=0)
@@ -589,8 +591,8 @@ def run_learned(args):
     _, ys = workloads.simulate(spec, W + K + 1, 0)
     yd = torch.tensor(ys.astype(np.float32), device="cuda")
 
-    def timed(L, use_prop):
-        f = dpf.Filter(model, 2, 2, N, M, L, seed=3, stream=stream)
+    def timed(L, use_prop, n_outer=N, m_inner=M):
+        f = dpf.Filter(model, 2, 2, n_outer, m_inner, L, seed=3, stream=stream)
         if use_prop:
             f.set_proposal(use_prop)
         with torch.cuda.stream(stream):
@@ -617,6 +619,7 @@ def run_learned(args):
     clk = clocks.stop(window=(w0, w1))
     ms_p = timed(8, None)
     ms_a = timed(8, aprop)
+    ms_p4 = timed(8, None, N, 4 * M)  # the plain filter with four times the inner particles
     # ---- accuracy on an untimed run ----
     T = 25
     _, ya = workloads.simulate(spec, T, 200)
@@ -636,8 +639,8 @@ def run_learned(args):
         return np.array(out)
     km = kalman_means(ya)
 
-    def accuracy(L, use_prop):
-        f = dpf.Filter(model, 2, 2, N, M, L, seed=5, stream=stream)
+    def accuracy(L, use_prop, n_outer=N, m_inner=M):
+        f = dpf.Filter(model, 2, 2, n_outer, m_inner, L, seed=5, stream=stream)
         if use_prop:
             f.set_proposal(use_prop)
         err, ess = [], []
@@ -647,13 +650,14 @@ def run_learned(args):
             if t >= 1:
                 lq = f.read("lq").astype(np.float64)
                 Wt = np.exp(lq - lq.max(axis=1, keepdims=True))
-                ess.append(float(np.mean(Wt.sum(1) ** 2 / (Wt * Wt).sum(1)) / M))
+                ess.append(float(np.mean(Wt.sum(1) ** 2 / (Wt * Wt).sum(1)) / m_inner))
         f.close()
         return float(np.sqrt(np.mean(np.square(err)))), float(np.mean(ess))
 
     rmse_l, ess_l = accuracy(1, prop)
     rmse_p, ess_p = accuracy(8, None)
     rmse_a, ess_a = accuracy(8, aprop)
+    rmse_p4, ess_p4 = accuracy(8, None, N, 4 * M)
     value = N * M * K / (ms_l / 1e3)
     mlp_flop = 2 * (8 * 256 + 2 * 256 * 256 + 256 * 20)  # per inner particle
     line = {
@@ -662,12 +666,14 @@ def run_learned(args):
         "dtype": "f32 filter, bf16 MLP", "data": "synthetic",
         "config": {"workload": f"learned proposal: lg4 model (d=4, x 2 / z 2), FP32, N={N}, M={M}, L=1; "
                                "MLP 3x256 ReLU, 4-component mixture head, BF16 weights, FP32 accumulate",
-                   "training_rows": 16384 * M, "training_epochs": 3, "training_s": train_s,
+                   "training_rows": 8 * 2048 * M, "training_epochs": 3, "training_s": train_s,
                    "training_losses": list(losses),
                    "l2": "state larger than L2; no flush"},
         "tensor": {"mlp_tflops": mlp_flop * N * M * K / (ms_l / 1e3) / 1e12,
                    "mlp_flop_per_update": mlp_flop},
         "plain": {"L": 8, "value": N * M * K / (ms_p / 1e3), "ms_per_step": ms_p / K},
+        "plain_4M": {"L": 8, "M": 4 * M, "ms_per_step": ms_p4 / K, "rmse_vs_kalman": rmse_p4,
+                     "inner_ess": ess_p4, "value": N * 4 * M * K / (ms_p4 / 1e3)},
         "amortised": {"L": 8, "value": N * M * K / (ms_a / 1e3), "ms_per_step": ms_a / K,
                       "training_losses": list(alosses), "network_rows_per_step": N},
         "accuracy": {"steps": T, "rmse_vs_kalman_learned": rmse_l, "rmse_vs_kalman_plain": rmse_p,
