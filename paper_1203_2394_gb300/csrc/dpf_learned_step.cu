@@ -28,7 +28,7 @@ namespace dpf {
 constexpr int LH = 256;                // hidden width of the tensor-core pass
 constexpr int LDIN = 16;               // inputs padded to one K step
 constexpr int LNP = 32;                // head outputs padded to an MMA N
-constexpr int LKCH = 64;               // K columns per streamed chunk
+constexpr int LKCH = 32;               // K columns per streamed chunk
 constexpr int LNCH = LH / LKCH;        // chunks per hidden layer
 constexpr int LSTAGES = 3;
 constexpr uint32_t LCHUNK = LH * LKCH * 2;  // bytes of one chunk
@@ -44,16 +44,25 @@ constexpr size_t PK_W4 = PK_W3 + (size_t)LNCH * LCHUNK;
 constexpr size_t PK_B = PK_W4 + (size_t)LNP * LH * 2;
 constexpr size_t PK_BYTES = PK_B + sizeof(float) * (3 * LH + LNP);
 
+// One iteration of the kernel takes 2 x 128 rows (tiles A and B, TMEM columns 0..255 and
+// 256..511); 8 compute warps hold one row a thread, a ninth warp feeds the weight ring.
+constexpr int LROWS = 256;
+constexpr int LCOMPUTE = 256;                               // compute threads
+constexpr int LTHREADS = LCOMPUTE + 32;                     // + the producer warp
 // shared-memory layout (bytes)
-constexpr uint32_t SM_ACT = 0;                              // 128 x 256 bf16, kc16 = 32
-constexpr uint32_t SM_IN = SM_ACT + 128 * LH * 2;           // 128 x 16 bf16, kc16 = 2
-constexpr uint32_t SM_W1 = SM_IN + 128 * LDIN * 2;          // 256 x 16, kc16 = 2
+constexpr uint32_t SM_ACT = 0;                              // 2 x (128 x 256 bf16), kc16 = 32
+constexpr uint32_t SM_IN = SM_ACT + 2 * 128 * LH * 2;       // 2 x (128 x 16 bf16), kc16 = 2
+constexpr uint32_t SM_W1 = SM_IN + 2 * 128 * LDIN * 2;      // 256 x 16, kc16 = 2
 constexpr uint32_t SM_W4 = SM_W1 + LH * LDIN * 2;           // 32 x 256, kc16 = 32
-constexpr uint32_t SM_RING = SM_W4 + LNP * LH * 2;          // 3 x (256 x 64), kc16 = 8
+constexpr uint32_t SM_RING = SM_W4 + LNP * LH * 2;          // 3 x (256 x 32), kc16 = 4
 constexpr uint32_t SM_BIAS = SM_RING + LSTAGES * LCHUNK;    // b1 b2 b3 (256 each), b4 (32)
-constexpr uint32_t SM_CUM = SM_BIAS + sizeof(float) * (3 * LH + LNP);  // 128 uint32
-constexpr uint32_t SM_RED = SM_CUM + 128 * 4;               // 8 floats / words
+constexpr uint32_t SM_CUM = SM_BIAS + sizeof(float) * (3 * LH + LNP);  // 256 uint32
+constexpr uint32_t SM_RED = SM_CUM + LROWS * 4;             // 8 floats, 8 words
 constexpr uint32_t SM_BYTES = SM_RED + 64;
+static_assert(SM_BYTES <= 227 * 1024, "shared memory of the learned kernel");
+
+// Barrier of the 256 compute threads only (the producer warp runs its own loop).
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Pack one FP32 matrix (rows x cols, row-major) into BF16 K-major chunks of kch
 // columns, rows padded to rows_pad and columns to a multiple of kch with zeros.
@@ -152,9 +161,9 @@ __device__ __forceinline__ float group_max(float v, int M, float* red) {
   v = warp_max(v);
   if (M <= 32) return v;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
+  compute_sync();
   if (lane == 0) red[w] = v;
-  __syncthreads();
+  compute_sync();
   const int g0 = (w * 32 / M) * (M / 32);
   float m = red[g0];
   for (int q = 1; q < M / 32; ++q) m = fmaxf(m, red[g0 + q]);
@@ -164,9 +173,9 @@ __device__ __forceinline__ float group_sum(float v, int M, float* red) {
   v = warp_sum(v);
   if (M <= 32) return v;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
+  compute_sync();
   if (lane == 0) red[w] = v;
-  __syncthreads();
+  compute_sync();
   const int g0 = (w * 32 / M) * (M / 32);
   float s = 0.f;
   for (int q = 0; q < M / 32; ++q) s += red[g0 + q];
@@ -176,15 +185,17 @@ __device__ __forceinline__ float group_sum(float v, int M, float* red) {
 // MODE 0: head outputs of feature rows; MODE 1: the filter's inner update with NC
 // mixture components (compile-time, so that the head's arrays stay in registers).
 template <int MODE, int D1, int D2, int DY, bool XZ, int NC>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(LTHREADS, 1)
     learned_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const __grid_constant__ StepArgs<float> a,
                    const __grid_constant__ LearnArgs la) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t full[LSTAGES], empty[LSTAGES], mbar;
   __shared__ uint32_t s_taddr;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  unsigned char* act = sm + SM_ACT;
-  unsigned char* in = sm + SM_IN;
+  const int half = tid >> 7;  // tile A (0) or B (1) of this thread's row
+  const int r128 = tid & 127;
+  unsigned char* act = sm + SM_ACT + half * (128 * LH * 2);
+  unsigned char* in = sm + SM_IN + half * (128 * LDIN * 2);
   float* bias = (float*)(sm + SM_BIAS);
   uint32_t* cum = (uint32_t*)(sm + SM_CUM);
   float* red = (float*)(sm + SM_RED);
@@ -192,9 +203,9 @@ __global__ void __launch_bounds__(128, 1)
 
   const int M = MODE == 1 ? a.M : 128;
   const long long rows_total = MODE == 1 ? a.N * (long long)a.M : la.nrows;
-  const long long ntiles = (rows_total + 127) / 128;
-  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long total_chunks = my_tiles * 2 * LNCH;
+  const long long niters = (rows_total + LROWS - 1) / LROWS;
+  const long long my_iters = niters > blockIdx.x ? (niters - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total_chunks = my_iters * 2 * LNCH;
 
   // ---- set-up: barriers, TMEM, resident weights and biases ----
   if (tid == 0) {
@@ -209,38 +220,49 @@ __global__ void __launch_bounds__(128, 1)
     tc::tmem_alloc(&s_taddr, LTMEM_COLS);
     tc::tmem_relinquish();
   }
-  for (int e = tid; e < (int)(LH * LDIN * 2 / 16); e += 128)
+  for (int e = tid; e < (int)(LH * LDIN * 2 / 16); e += LTHREADS)
     ((uint4*)(sm + SM_W1))[e] = ((const uint4*)(la.wp + PK_W1))[e];
-  for (int e = tid; e < (int)(LNP * LH * 2 / 16); e += 128)
+  for (int e = tid; e < (int)(LNP * LH * 2 / 16); e += LTHREADS)
     ((uint4*)(sm + SM_W4))[e] = ((const uint4*)(la.wp + PK_W4))[e];
-  for (int e = tid; e < 3 * LH + LNP; e += 128) bias[e] = ((const float*)(la.wp + PK_B))[e];
+  for (int e = tid; e < 3 * LH + LNP; e += LTHREADS) bias[e] = ((const float*)(la.wp + PK_B))[e];
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t taddr = s_taddr;
-  const uint32_t trow = taddr + ((uint32_t)(32 * w) << 16);  // this warp's TMEM lanes
+  // this thread's accumulator row: lanes 32 (w % 4) .., columns 256 half ..
+  const uint32_t trow = taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(half * LH);
   bool ok = true;
 
-  auto chunk_src = [&](long long c) -> const unsigned char* {
-    const int q = (int)(c % (2 * LNCH));
-    return la.wp + (q < LNCH ? PK_W2 + (size_t)q * LCHUNK : PK_W3 + (size_t)(q - LNCH) * LCHUNK);
-  };
-  auto load_chunk = [&](long long c) {  // thread 0 only
-    const int s = (int)(c % LSTAGES);
-    mbar_arrive_tx(&full[s], LCHUNK);
-    bulk_load(sm + SM_RING + s * LCHUNK, chunk_src(c), LCHUNK, &full[s]);
-  };
-  if (tid == 0)
-    for (long long c = 0; c < std::min<long long>(LSTAGES, total_chunks); ++c) load_chunk(c);
+  if (w == LCOMPUTE / 32) {
+    // ---- producer warp: refill each ring stage as soon as its MMAs are done ----
+    if (lane == 0) {
+      for (long long c = 0; c < total_chunks; ++c) {
+        const int s = (int)(c % LSTAGES);
+        if (c >= LSTAGES && !tc::bar_wait(&empty[s], (uint32_t)(((c / LSTAGES) - 1) & 1), L_SPIN)) {
+          ok = false;
+          break;
+        }
+        const int q = (int)(c % (2 * LNCH));
+        const unsigned char* src =
+            la.wp + (q < LNCH ? PK_W2 + (size_t)q * LCHUNK : PK_W3 + (size_t)(q - LNCH) * LCHUNK);
+        mbar_arrive_tx(&full[s], LCHUNK);
+        bulk_load(sm + SM_RING + s * LCHUNK, src, LCHUNK, &full[s]);
+      }
+      // wait until the last chunks' MMAs have released their stages, so that no
+      // copy is in flight when the kernel ends
+      for (long long c = std::max<long long>(0, total_chunks - LSTAGES); c < total_chunks && ok; ++c)
+        if (!tc::bar_wait(&empty[c % LSTAGES], (uint32_t)((c / LSTAGES) & 1), L_SPIN)) ok = false;
+    }
+  } else {
   long long c_use = 0;      // next chunk to consume (thread 0)
-  uint32_t mph = 0;         // phase of mbar (all threads)
+  uint32_t mph = 0;         // phase of mbar (compute threads)
 
   const uint32_t id_h = tc::instr_desc(tc::FMT_BF16, 128, LH);
   const uint32_t id_o = tc::instr_desc(tc::FMT_BF16, 128, LNP);
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long row = tile * 128 + tid;
+  for (long long it = blockIdx.x; it < niters; it += gridDim.x) {
+    const long long row = it * LROWS + tid;
     const bool live = row < rows_total;
     // ---- prologue: this row's input features ----
     float feat[LDIN];
@@ -328,13 +350,13 @@ __global__ void __launch_bounds__(128, 1)
         const uint32_t n = __shfl_up_sync(FULL, inc, o);
         if (lane >= o) inc += n;
       }
-      __syncthreads();
+      compute_sync();
       if (lane == 31) ((uint32_t*)red)[8 + w] = inc;  // warp totals after the float slots
-      __syncthreads();
+      compute_sync();
       const int gw0 = (w * 32 / M) * (M / 32);  // first warp of this group
       for (int q = gw0; q < w; ++q) inc += ((uint32_t*)red)[8 + q];
       cum[tid] = inc;
-      __syncthreads();
+      compute_sync();
       const int gbase = (tid / M) * M;
       const uint32_t Cg = cum[gbase + M - 1];
       if (Cg == 0 && live && j == 0) atomicOr(a.err, ERR_NUMERIC);
@@ -365,26 +387,29 @@ __global__ void __launch_bounds__(128, 1)
       q1.y = pack_bf16x2(feat[10], feat[11]);
       q1.z = pack_bf16x2(feat[12], feat[13]);
       q1.w = pack_bf16x2(feat[14], feat[15]);
-      *(uint4*)(in + tc::kmajor_offset(tid, 0, 2)) = q0;
-      *(uint4*)(in + tc::kmajor_offset(tid, 16, 2)) = q1;
+      *(uint4*)(in + tc::kmajor_offset(r128, 0, 2)) = q0;
+      *(uint4*)(in + tc::kmajor_offset(r128, 16, 2)) = q1;
     }
     tc::fence_proxy_async();
     tc::fence_before();
-    __syncthreads();
+    compute_sync();
 
-    // ---- layer 1 ----
+    const uint32_t s_act0 = smem_addr(sm + SM_ACT), s_in0 = smem_addr(sm + SM_IN);
+    // ---- layer 1 (both tiles) ----
     if (tid == 0) {
       tc::fence_after();
-      tc::mma_f16(taddr, tc::smem_desc(smem_addr(in), 2), tc::smem_desc(smem_addr(sm + SM_W1), 2), id_h, 0u);
+      for (int h = 0; h < 2; ++h)
+        tc::mma_f16(taddr + h * LH, tc::smem_desc(s_in0 + h * (128 * LDIN * 2), 2),
+                    tc::smem_desc(smem_addr(sm + SM_W1), 2), id_h, 0u);
       tc::commit(&mbar);
     }
     ok &= tc::bar_wait(&mbar, mph, L_SPIN);
     mph ^= 1u;
     tc::fence_after();
-    hidden_epilogue(trow, bias, act, tid);
+    hidden_epilogue(trow, bias, act, r128);
     tc::fence_proxy_async();
     tc::fence_before();
-    __syncthreads();
+    compute_sync();
 
     // ---- layers 2 and 3 (streamed weights) ----
 #pragma unroll 1
@@ -395,38 +420,38 @@ __global__ void __launch_bounds__(128, 1)
           const long long c = c_use++;
           const int s = (int)(c % LSTAGES);
           if (!tc::bar_wait(&full[s], (uint32_t)((c / LSTAGES) & 1), L_SPIN)) ok = false;
-          const uint32_t sa = smem_addr(act), sb = smem_addr(sm + SM_RING + s * LCHUNK);
+          const uint32_t sb = smem_addr(sm + SM_RING + s * LCHUNK);
 #pragma unroll
           for (int ks = 0; ks < LKCH / 16; ++ks)
-            tc::mma_f16(taddr, tc::smem_desc(sa + (uint32_t)(k * 8 + ks * 2) * 128u, 32),
-                        tc::smem_desc(sb + (uint32_t)ks * 256u, 8), id_h, (k > 0 || ks > 0) ? 1u : 0u);
-          tc::commit(&empty[s]);
-          // refill the stage of the previous chunk (likely free by now) with chunk c + 2
-          if (c >= 1 && c + LSTAGES - 1 < total_chunks) {
-            const long long cp = c - 1;
-            if (!tc::bar_wait(&empty[cp % LSTAGES], (uint32_t)((cp / LSTAGES) & 1), L_SPIN)) ok = false;
-            load_chunk(c + LSTAGES - 1);
-          }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              tc::mma_f16(taddr + h * LH,
+                          tc::smem_desc(s_act0 + h * (128 * LH * 2) + (uint32_t)(k * (LKCH / 8) + ks * 2) * 128u, 32),
+                          tc::smem_desc(sb + (uint32_t)ks * 256u, LKCH / 8), id_h, (k > 0 || ks > 0) ? 1u : 0u);
+          tc::commit(&empty[s]);  // the producer refills the stage once these MMAs are done
         }
         tc::commit(&mbar);
       }
       ok &= tc::bar_wait(&mbar, mph, L_SPIN);
       mph ^= 1u;
       tc::fence_after();
-      hidden_epilogue(trow, bias + (layer + 1) * LH, act, tid);
+      hidden_epilogue(trow, bias + (layer + 1) * LH, act, r128);
       tc::fence_proxy_async();
       tc::fence_before();
-      __syncthreads();
+      compute_sync();
     }
 
     // ---- head ----
     if (tid == 0) {
       tc::fence_after();
-      const uint32_t sa = smem_addr(act), sb = smem_addr(sm + SM_W4);
+      const uint32_t sb = smem_addr(sm + SM_W4);
+      // the head of tile h goes to its own columns 0..31 (read by its last hidden epilogue)
 #pragma unroll
       for (int ks = 0; ks < LH / 16; ++ks)
-        tc::mma_f16(taddr + LH, tc::smem_desc(sa + (uint32_t)ks * 256u, 32), tc::smem_desc(sb + (uint32_t)ks * 256u, 32),
-                    id_o, ks > 0 ? 1u : 0u);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          tc::mma_f16(taddr + h * LH, tc::smem_desc(s_act0 + h * (128 * LH * 2) + (uint32_t)ks * 256u, 32),
+                      tc::smem_desc(sb + (uint32_t)ks * 256u, 32), id_o, ks > 0 ? 1u : 0u);
       tc::commit(&mbar);
     }
     ok &= tc::bar_wait(&mbar, mph, L_SPIN);
@@ -435,10 +460,10 @@ __global__ void __launch_bounds__(128, 1)
     float o[LNP];
     {
       float v[16];
-      tc::ld16(trow + LH, v);
+      tc::ld16(trow, v);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = v[q] + bias[3 * LH + q];
-      tc::ld16(trow + LH + 16, v);
+      tc::ld16(trow + 16, v);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[16 + q] = v[q] + bias[3 * LH + 16 + q];
     }
@@ -562,8 +587,9 @@ __global__ void __launch_bounds__(128, 1)
         if (!(lqn == lqn)) atomicOr(a.err, ERR_NUMERIC);
       }
     }
-    __syncthreads();  // TMEM and the tiles are free for the next tile
+    compute_sync();  // TMEM and the tiles are free for the next iteration
   }
+  }  // compute warps
   if (!ok && lane == 0) atomicOr(MODE == 1 ? a.err : la.err, ERR_TIMEOUT);
   tc::fence_before();
   __syncthreads();
@@ -583,9 +609,9 @@ static dpf_status launch_learned(const MC<float, D1, D2, DY>& mc, const StepArgs
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long tiles = (rows + 127) / 128;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, nsm));
-  k<<<grid, 128, SM_BYTES, s>>>(mc, a, la);
+  const long long iters = (rows + LROWS - 1) / LROWS;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(iters, nsm));
+  k<<<grid, LTHREADS, SM_BYTES, s>>>(mc, a, la);
   return cuda_error(cudaGetLastError(), "learned kernel launch");
 }
 
