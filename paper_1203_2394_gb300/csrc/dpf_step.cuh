@@ -83,6 +83,7 @@ struct StepArgs {
   uint32_t off_stage, off_sz, off_slq, off_sx, off_slwh, off_sxbb;
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
   uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
+  uint32_t off_zmat, off_sb;           // wide z (d2 > 32): [A_zz K] rows and the combined sums
   int la_only;  // the inner update already ran (learned proposal): look-ahead from the materialised state
 };
 
@@ -157,6 +158,9 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
   const uint32_t zlo = tc ? take(sizeof(float) * (size_t)M * D2) : 0u,
                  ahi = tc ? take(sizeof(float) * (size_t)np * D2) : 0u,
                  alo = tc ? take(sizeof(float) * (size_t)np * D2) : 0u;
+  // wide z: the rows [A_zz(r, .) K(r, .)] for the z-mean combine, one warp a row
+  const uint32_t zmat = D2 > 32 ? take(sizeof(T) * (size_t)D2 * (D2 + DY)) : 0u,
+                 sbo = D2 > 32 ? take(sizeof(T) * (size_t)(D2 + DY)) : 0u;
   if (a) {
     a->tpm = tpm;
     a->rows = nt / tpm;
@@ -169,6 +173,7 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
     a->off_cum = cum; a->off_kd = kd; a->off_E = E; a->off_xw = xw;
     a->off_cw = cw; a->off_xbs = xbs; a->off_row = row; a->off_red = red; a->off_part = part;
     a->off_zlo = zlo; a->off_ahi = ahi; a->off_alo = alo;
+    a->off_zmat = zmat; a->off_sb = sbo;
   }
   return o;
 }
@@ -418,6 +423,13 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     mbar_fence_init();
+  }
+  if constexpr (D2 > 32) {
+    T* zmat = (T*)(smem_raw + a.off_zmat);
+    for (int e = tid; e < D2 * (D2 + DY); e += NT) {
+      const int r = e / (D2 + DY), c = e % (D2 + DY);
+      zmat[e] = c < D2 ? mc.Azz[r][c] : mc.K[r][c - D2];
+    }
   }
   uint32_t taddr = 0, tc_phase = 0;
   constexpr uint32_t TC_COLS = TC ? (NP * 2 <= 32 ? 32 : NP * 2 <= 64 ? 64 : NP * 2 <= 128 ? 128 : 256) : 32;
@@ -710,12 +722,16 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         unsigned char* zlo = smem_raw + a.off_zlo;
         const uint32_t tb = (uint32_t)(j >> 7) * 128u * (uint32_t)(D2 * 4);
         const int rr = j & 127;
+        // four coordinates (one 16-byte chunk of the row) per store
 #pragma unroll
-        for (int c = 0; c < D2; ++c) {
-          float hi, lo;
-          tc::split_tf32(zb2[c], hi, lo);
-          *(float*)(zhi + tb + tc::kmajor_offset(rr, 4 * c, KC16)) = hi;
-          *(float*)(zlo + tb + tc::kmajor_offset(rr, 4 * c, KC16)) = lo;
+        for (int c = 0; c < D2; c += 4) {
+          float4 hi, lo;
+          tc::split_tf32(zb2[c + 0], hi.x, lo.x);
+          tc::split_tf32(zb2[c + 1], hi.y, lo.y);
+          tc::split_tf32(zb2[c + 2], hi.z, lo.z);
+          tc::split_tf32(zb2[c + 3], hi.w, lo.w);
+          *(float4*)(zhi + tb + tc::kmajor_offset(rr, 4 * c, KC16)) = hi;
+          *(float4*)(zlo + tb + tc::kmajor_offset(rr, 4 * c, KC16)) = lo;
         }
         tc::fence_proxy_async();
         tc::fence_before();
@@ -737,40 +753,36 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           }
           tc::commit(&tcbar);
         }
+        // the propagation noise, drawn while the MMAs run
+        T eps[D2];
+        normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
         const bool ok = tc::bar_wait(&tcbar, tc_phase, TC_SPIN);
         tc_phase ^= 1u;
         if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
         tc::fence_after();
-        float azz[D2];
         {
           const uint32_t ta = taddr + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((j >> 7) * NP);
-#pragma unroll
-          for (int c0 = 0; c0 + 16 <= D2; c0 += 16) {
-            float v[16];
-            tc::ld16(ta + (uint32_t)c0, v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) azz[c0 + q] = ok ? v[q] : 0.f;
-          }
-          if (D2 % 16) {
-            float v[8];
-            tc::ld8(ta + (uint32_t)(D2 / 16 * 16), v);
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if (D2 / 16 * 16 + q < D2) azz[D2 / 16 * 16 + q] = ok ? v[q] : 0.f;
-          }
-        }
-        tc::fence_before();
-        T eps[D2];
-        normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
-#pragma unroll
-        for (int r = 0; r < D2; ++r) {
-          T v = azx[r] + (T)azz[r];
-          if (mc.diag_qz) {
-            v += mc.Lqz[r][r] * eps[r];
+          float azz[(D2 + 15) / 16 * 16];
+          if constexpr (NP == 64) {  // the whole padded row in one load
+            tc::ld64(ta, *reinterpret_cast<float(*)[64]>(azz));
           } else {
-            for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+#pragma unroll
+            for (int c0 = 0; c0 < D2; c0 += 16) tc::ld16(ta + (uint32_t)c0, *reinterpret_cast<float(*)[16]>(azz + c0));
           }
-          zr[0][r] = v;
+          tc::fence_before();
+          // z_new = A_zz z_b + A_zx x_a + L_qz eps, one coordinate at a time
+#pragma unroll
+          for (int r = 0; r < D2; ++r) {
+            T v = ok ? (T)azz[r] : T(0);
+#pragma unroll
+            for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+            if (mc.diag_qz) {
+              v += mc.Lqz[r][r] * eps[r];
+            } else {
+              for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+            }
+            zr[0][r] = v;
+          }
         }
         T qf = T(0);
 #pragma unroll
@@ -1066,7 +1078,27 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
       for (int c = 0; c < D2 + DY; ++c) part[c * 32 + w] = acc[c];
     }
     __syncthreads();
-    if (tid < D2) {
+    if constexpr (D2 > 32) {
+      // wide z: the D2 + DY sums over the warps, then one warp a row of [A_zz K] . sums
+      T* sbs = (T*)(smem_raw + a.off_sb);
+      const T* zmat = (const T*)(smem_raw + a.off_zmat);
+      if (tid < D2 + DY) {
+        T v = T(0);
+        for (int q = 0; q < nw; ++q) v += part[tid * 32 + q];
+        sbs[tid] = v;
+      }
+      __syncthreads();
+      for (int r = w; r < D2; r += nw) {
+        T v = T(0);
+        for (int c = lane; c < D2 + DY; c += 32) v += zmat[r * (D2 + DY) + c] * sbs[c];
+        v = warp_sum(v);
+        if (lane == 0) {
+#pragma unroll
+          for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * x[c];
+          a.zm[(long long)r * N + i] = v;
+        }
+      }
+    } else if (tid < D2) {
       const int r = tid;
       T sb[D2 + DY];
 #pragma unroll
