@@ -202,19 +202,25 @@ __device__ __forceinline__ void sub_sq(T c, const T (&g)[P], T (&acc)[P]) {
 // Issue the bulk copies of one group's source rows into a warp's stage (lane 0).
 template <typename T, int D1, int D2>
 __device__ __forceinline__ void warp_stage(const StepArgs<T>& a, unsigned char* st, uint64_t* bar,
-                                           long long src) {
+                                           long long src, int lane) {
+  // warp-wide: lane 0 arms the barrier with the stage's bytes, one lane a copy
   const int M = a.M, L = a.L;
   const long long NM = a.N * (long long)M;
-  mbar_arrive_tx(bar, a.stage_tx);
-#pragma unroll
-  for (int c = 0; c < D2; ++c)
-    bulk_load(st + a.off_sz + (size_t)c * M * sizeof(T), a.z_old + c * NM + src * M,
-              (uint32_t)(M * sizeof(T)), bar);
-  bulk_load(st + a.off_slq, a.lq_old + src * M, (uint32_t)(M * sizeof(T)), bar);
-  bulk_load(st + a.off_sx, a.x_old + src * a.xp, (uint32_t)(a.xp * sizeof(T)), bar);
-  if (!a.first) {
-    bulk_load(st + a.off_slwh, a.lwh_old + src * L, (uint32_t)(L * sizeof(T)), bar);
-    bulk_load(st + a.off_sxbb, a.xbb_old + src * L * D1, (uint32_t)(L * D1 * sizeof(T)), bar);
+  if (lane == 0) mbar_arrive_tx(bar, a.stage_tx);
+  for (int e = lane; e < D2 + 4; e += 32) {
+    if (e < D2) {
+      bulk_load(st + a.off_sz + (size_t)e * M * sizeof(T), a.z_old + e * NM + src * M,
+                (uint32_t)(M * sizeof(T)), bar);
+    } else if (e == D2) {
+      bulk_load(st + a.off_slq, a.lq_old + src * M, (uint32_t)(M * sizeof(T)), bar);
+    } else if (e == D2 + 1) {
+      bulk_load(st + a.off_sx, a.x_old + src * a.xp, (uint32_t)(a.xp * sizeof(T)), bar);
+    } else if (!a.first) {
+      if (e == D2 + 2)
+        bulk_load(st + a.off_slwh, a.lwh_old + src * L, (uint32_t)(L * sizeof(T)), bar);
+      else
+        bulk_load(st + a.off_sxbb, a.xbb_old + src * L * D1, (uint32_t)(L * D1 * sizeof(T)), bar);
+    }
   }
 }
 
@@ -254,9 +260,9 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
   if (gfirst == 0 && lane == 0) *a.Csum = 0ull;  // the outer reduction of this step sums into it
 
   long long g = gfirst;
-  long long src_next = -1;
-  if (g < gend && lane == 0) {
-    warp_stage<T, D1, D2>(a, ws, bar, a.first ? g : (long long)a.anc[g]);
+  long long src_next = -1;  // the same in every lane
+  if (g < gend) {
+    warp_stage<T, D1, D2>(a, ws, bar, a.first ? g : (long long)a.anc[g], lane);
     if (g + W < gend) src_next = a.first ? g + W : (long long)a.anc[g + W];
   }
   __syncwarp();
@@ -516,8 +522,8 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
     }
     // the stage is consumed: prefetch the next group's rows into it
     __syncwarp();
-    if (lane == 0 && g + W < gend) {
-      warp_stage<T, D1, D2>(a, ws, bar, src_next);
+    if (g + W < gend) {
+      warp_stage<T, D1, D2>(a, ws, bar, src_next, lane);
       const long long g2 = g + 2 * W;
       if (g2 < gend) src_next = a.first ? g2 : (long long)a.anc[g2];
     }
