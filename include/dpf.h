@@ -395,6 +395,16 @@ dpf_status dpf_record_tuples(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* F
  * (2, 2, 2) and M a multiple of 32 up to 256. */
 dpf_status dpf_record_tuples_amortised(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* G, float* Z, float* w);
 
+/*
+ * A check of the failure path of the bounded waits; the paper has no
+ * counterpart. Runs the global resampling's scan on 3 x 2048 unit weights with
+ * tile 0 publishing nothing, so that the look-back waits of the other tiles
+ * can never be satisfied: they give up after their bound (a few tenths of a
+ * second), the call returns DPF_E_TIMEOUT, and the context stays usable.
+ * Synchronises the stream.
+ */
+dpf_status dpf_check_bounded_wait(void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dpf_last_error(void);
 

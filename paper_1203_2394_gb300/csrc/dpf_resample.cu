@@ -104,7 +104,7 @@ static dpf_status launch_local(const T* w, int n, long long nseg, const uint32_t
 
 template <typename T>
 static void launch_global(const T* w, long long n, const uint32_t* u, int32_t* out, Scratch& sc,
-                          cudaStream_t s) {
+                          cudaStream_t s, long long withhold = -1) {
   const int S = 62 - ceil_log2_i(n);
   const int grid = (int)std::min<long long>((n + 1023) / 1024, 4 * 152);
   wmax_kernel<T><<<grid, 256, 0, s>>>(w, n, sc.maxkey, sc.err);
@@ -120,6 +120,7 @@ static void launch_global(const T* w, long long n, const uint32_t* u, int32_t* o
   a.ticket_base = 0;
   a.epoch = 1;
   a.err = sc.err;
+  a.withhold = withhold;
   const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   global_scan_scatter<T, false><<<(unsigned)tiles, SCAN_NT, 0, s>>>(a);
 }
@@ -161,6 +162,36 @@ extern "C" dpf_status dpf_box_muller(const uint32_t* words, int64_t n_pairs, int
   else
     box_muller_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(words, n_pairs, (double*)out);
   return cuda_error(cudaGetLastError(), "dpf_box_muller");
+}
+
+__global__ void fill_ones_kernel(float* w, long long n) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n) w[e] = 1.f;
+}
+
+extern "C" dpf_status dpf_check_bounded_wait(void* stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = 3 * SCAN_TILE;
+  float* w = nullptr;
+  int32_t* out = nullptr;
+  uint32_t* u = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&w, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&out, sizeof(int32_t) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&u, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_check_bounded_wait: allocation");
+  fill_ones_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, n);
+  cudaMemsetAsync(u, 0, sizeof(uint32_t), s);
+  Scratch sc;
+  dpf_status st = scratch_alloc(sc, 3, s);
+  if (!st) {
+    launch_global<float>(w, n, u, out, sc, s, 0);  // tile 0 withholds its prefix
+    st = scratch_finish(sc, s, "dpf_check_bounded_wait");
+  }
+  cudaFreeAsync(w, s);
+  cudaFreeAsync(out, s);
+  cudaFreeAsync(u, s);
+  return st;
 }
 
 extern "C" dpf_status dpf_resample(const void* w, int32_t dtype, int64_t n_total, int64_t n_seg,

@@ -56,6 +56,7 @@ struct GlobalArgs {
   unsigned long long ticket_base;
   uint32_t epoch;
   int* err;
+  long long withhold;  // a tile that publishes nothing (a check of the bounded waits); -1: none
 };
 
 template <typename T>
@@ -139,7 +140,9 @@ __device__ __forceinline__ void global_scan_scatter_body(const GlobalArgs<T>& a,
   if (wid == 0) {
     const uint32_t ep = a.epoch & 0x3FFFFFFFu;
     unsigned long long prefix = 0;
-    if (tile == 0) {
+    if (tile == a.withhold) {
+      // publishes nothing: its successors' waits must run out and report
+    } else if (tile == 0) {
       if (lane == 0) {
         a.st.incl[0] = agg;
         cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(a.st.flags[0])

@@ -291,6 +291,7 @@ struct VariantImpl {
     g.ticket_base = x.ticket_next;
     g.epoch = ++x.epoch;
     g.err = x.err;
+    g.withhold = -1;
     x.ticket_next += (unsigned long long)tiles;
   }
 

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("dpf_resample_noalloc", ctypes.c_int, [_P, _I32, _I64, _P, _P, _P]),
     ("dpf_box_muller", ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     ("dpf_tc_matmul", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _P]),
+    ("dpf_check_bounded_wait", ctypes.c_int, [_P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_proposal_create", ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _P, _P]),
@@ -512,3 +513,11 @@ class Proposal:
         out = torch.empty((F.shape[0], self.dout), dtype=torch.float32, device=F.device)
         check(self._lib.dpf_proposal_forward(self.h, F.data_ptr(), F.shape[0], out.data_ptr()))
         return out
+
+
+def check_bounded_wait(stream=None):
+    """Run the scan whose look-back can never finish (see ``dpf_check_bounded_wait``);
+    raises DpfError with status DPF_E_TIMEOUT when the waits give up as designed."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    check(lib().dpf_check_bounded_wait(s))
