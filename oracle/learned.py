@@ -148,7 +148,7 @@ def features(x_prev_a, x_new, z_b, y):
 
 
 def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, normals, sys_local,
-                     word, bf16_mode=False, head_out=None):
+                     word, bf16_mode=False, head_out=None, dest=None):
     """The inner update of step t with the learned proposal, for destinations 0..n-1.
 
     model: the model in x-first order (attributes d1, d2, dy, A, Q, H, R of an
@@ -156,7 +156,8 @@ def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, 
     selected x_t; bidx[i]: its local resampling indices (the plain rule, unchanged);
     normals(t, i, purpose, sub, n), sys_local(W, n_out, u) and word(t, i, purpose,
     sub): the shared random streams and the integer resampling rule. head_out: if
-    given (n, M, dout), the MLP outputs to use instead of evaluating the network.
+    given (n, M, dout), the MLP outputs to use instead of evaluating the network. dest:
+    the destinations' indices in the filter (their random-stream keys; default 0..n-1).
     For particle j of destination i:
       z_b  = z_{t-1}^(a, bidx_j),  f = (x_{t-1}^(a), x_t^(i), z_b, y_t);
       c    = the one-draw local systematic pick over exp(logits - max), word (t, i, LCOMP, j);
@@ -177,8 +178,10 @@ def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, 
     dout = C * (1 + 2 * d2)
     zs = np.zeros((n, M, d2)); lqs = np.zeros((n, M)); comps = np.zeros((n, M), np.int32)
     outs = np.zeros((n, M, dout)); logrs = np.zeros((n, M))
+    dest = np.arange(n) if dest is None else np.asarray(dest)
     for i in range(n):
         a = anc[i]
+        g = int(dest[i])
         zb = z_prev[a][bidx[i]]
         f = features(x_prev[a], x_new[i], zb, y)
         out = head_out[i] if head_out is not None else forward(W, f, bf16_mode)[0]
@@ -186,8 +189,8 @@ def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, 
         z = np.zeros((M, d2))
         for j in range(M):
             wts = np.exp(logits[j] - logits[j].max())
-            c = int(sys_local(wts, 1, word(t, i, P_LCOMP, j))[0])
-            eps = normals(t, i, 9, j, d2)  # P_PROP
+            c = int(sys_local(wts, 1, word(t, g, P_LCOMP, j))[0])
+            eps = normals(t, g, 9, j, d2)  # P_PROP
             z[j] = mu[j, c] + np.exp(logsig[j, c]) * eps
             comps[i, j] = c
         lq_prop = logq(z, logits, mu, logsig)

@@ -138,3 +138,44 @@ def test_autotune_keeps_results_within_tolerance():
         s.step(ys[1, f])
         for name in ("lw", "lwhat"):
             assert np.max(rel(b.filter(f).read(name), s.read(name))) <= 1e-5, (name, f)
+
+
+def test_full_size_batched_workload_sampled():
+    """The benchmark's batched workload (512 filters of d = 16, mixed N, M and d1) in its
+    graph-captured launch: sampled groups of a few members against the oracle's look-ahead
+    from the member's own state, and every member's outer ancestors bit-exact."""
+    from paper_1203_2394_gb300 import dpf
+    rng = np.random.default_rng(0)
+    F = 512
+    d1s = [int(v) for v in rng.choice([1, 2, 4, 8], F)]
+    Ns = [int(v) for v in rng.integers(1024, 65537, F)]
+    Ms = [int(v) for v in rng.choice([16, 32, 64, 128, 256], F)]
+    free, _ = torch.cuda.mem_get_info()
+    need = sum(n * m * (16 - d + 1) * 4 * 2 for n, m, d in zip(Ns, Ms, d1s)) * 1.15
+    if need > 0.9 * free:  # the bench runs the same proportional share
+        F = max(1, int(F * 0.9 * free / need))
+        d1s, Ns, Ms = d1s[:F], Ns[:F], Ms[:F]
+    specs = [workloads.make_model("lg16", 1000 + f, d1=d1s[f]) for f in range(F)]
+    models = [dpf.Model.from_spec(s, dpf.DPF_F32) for s in specs]
+    T = 3
+    ys = np.stack([workloads.simulate(s, T, 5 + f)[1] for f, s in enumerate(specs)], axis=1).astype(np.float32)
+    b = dpf.Batch(models, d1s, Ns, Ms, 8, list(range(F)))
+    yd = torch.tensor(ys, device="cuda")
+    b.run_device(yd.data_ptr(), T, graph=True)
+    # after call T the materialised state is that of step T-1: the look-ahead of step T
+    # starts from it
+    picks = sorted({0, int(np.argmax(Ns)), int(np.argmax(Ms)), d1s.index(8) if 8 in d1s else 1})
+    states = {f: state_from_gpu(b.filter(f)) for f in picks}
+    for f in picks:
+        m = b.filter(f)
+        x, z, lq = states[f]
+        o = oracle.Oracle(oracle.OracleModel.from_spec(specs[f], d1s[f]), Ns[f], Ms[f], 8, f, nthreads=16)
+        idx = np.sort(np.random.default_rng(f).choice(Ns[f], min(64, Ns[f]), replace=False))
+        ref = o.lookahead(T, ys[T - 1, f], idx, x, z, lq)
+        lw = m.read("lw").astype(np.float64)
+        assert np.max(rel(lw[idx], ref["lw"])) <= 1e-5, (f, np.max(rel(lw[idx], ref["lw"])))
+        check_lwhat(m.read("lwhat").astype(np.float64)[idx], ref["lwhat"], 1e-5)
+    for f in range(F):
+        m = b.filter(f)
+        wout = m.read("wout").astype(np.float64)
+        np.testing.assert_array_equal(m.read("anc"), oracle.sys_global(wout, word(f, T, 0, oracle.P_OUTER)))

@@ -239,3 +239,42 @@ def test_learned_inner_update_teacher_forced():
             np.testing.assert_allclose(z, got["z"], rtol=0, atol=1e-5)
             assert np.max(rel(lq, got["lq"])) <= 1e-5, np.max(rel(lq, got["lq"]))
         prev = (f.read("anc"), x, z, lq, f.read("lwhat").astype(np.float64), f.read("xbb").astype(np.float64))
+
+
+def test_learned_full_size_sampled():
+    """The learned workload's launch (N = 262144, M = 64, L = 1): on sampled groups the
+    head outputs within the bfloat16 bound and the draws and weights within 1e-5 of the
+    oracle fed the GPU's outputs."""
+    N, M, L, seed = 262144, 64, 1, 3
+    spec, f = _lg4_filter(N, M, L, seed)
+    f.set_debug(True)
+    om = oracle.OracleModel.from_spec(spec)
+    lib = oracle.load()
+    p = _prop()
+    W = workloads.init_mlp_weights(DIN, H, DOUT, seed=14)
+    W["b4"][C + C * D2:] = np.log(np.sqrt(0.1))
+    p.set_weights(W)
+    Wq = p.get_weights()
+    _, ys = workloads.simulate(spec, 3, 0)
+    f.step(ys[0].astype(np.float32))
+    px, pz, plq = state_from_gpu(f)
+    pa = f.read("anc")
+    f.set_proposal(p)
+    f.step(ys[1].astype(np.float32))
+    x, z, lq = state_from_gpu(f)
+    bidx = f.read("bidx")
+    head = f.read("head").astype(np.float64)
+    idx = np.sort(np.random.default_rng(5).choice(N, 48, replace=False))
+    feats = np.concatenate([np.repeat(px[pa[idx]], M, 0), np.repeat(x[idx], M, 0),
+                            pz[np.repeat(pa[idx], M), bidx[idx].ravel()],
+                            np.repeat(ys[0][None].astype(np.float32), len(idx) * M, 0)], 1)
+    href, cache = learned.forward(Wq, feats, bf16_mode=True)
+    scale = np.abs(cache["h3"]) @ np.abs(learned.bf16(Wq["W4"])).T + np.abs(Wq["b4"])
+    assert np.all(np.abs(head[idx].reshape(-1, DOUT) - href) <= 2.0 ** -6 * scale + 1e-5)
+    got = learned.learned_finalize(
+        om, Wq, C, seed, 1, ys[0].astype(np.float32), pa[idx], px, pz, x[idx], bidx[idx],
+        normals=lambda tt, i, pp, j, n: oracle.normals(seed, 0, tt, i, pp, j, n, lib),
+        sys_local=lambda wv, k, u: oracle.sys_local(wv, k, u, lib),
+        word=lambda tt, i, pp, j: word(seed, tt, i, pp, j), head_out=head[idx], dest=idx)
+    np.testing.assert_allclose(z[idx], got["z"], rtol=0, atol=1e-5)
+    assert np.max(rel(lq[idx], got["lq"])) <= 1e-5
