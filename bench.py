@@ -522,7 +522,7 @@ def run_highdim(args):
                    "filters": F, "share_of_64": F / 64 if share == 1.0 else share,
                    "l2": "state far larger than L2; no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "step_kernel_g (tensor-core)",
+                     "frac": achieved / peak, "traffic": None, "kernel": "step_kernel_wide (tensor-core)",
                      "kernel_ms": kern_s * 1e3, "bytes_per_update": per,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "tensor": {"mma_tflops": mma_flop / kern_s / 1e12, "mma_flop_per_launch": mma_flop},

@@ -1132,13 +1132,6 @@ __global__ void __launch_bounds__(MAXNT)
   step_body<T, D1, D2, DY, XZ, PPT, BULK, false>(mc, a);
 }
 
-// The block step with the model constants in global memory (models too large
-// for a launch parameter), optionally with the tensor-core propagation.
-template <typename T, int D1, int D2, int DY, bool XZ, int PPT, int MAXNT, bool BULK, bool TC>
-__global__ void __launch_bounds__(MAXNT)
-    step_kernel_g(const MC<T, D1, D2, DY>* __restrict__ mcp, const __grid_constant__ StepArgs<T> a) {
-  step_body<T, D1, D2, DY, XZ, PPT, BULK, TC>(*mcp, a);
-}
 
 // ---- outer reduction: evidence, ESS, filtered mean, quantised total ----
 template <typename T>
