@@ -405,6 +405,35 @@ dpf_status dpf_record_tuples_amortised(dpf_ctx* ctx, int64_t i0, int64_t n_outer
  */
 dpf_status dpf_check_bounded_wait(void* stream);
 
+/*
+ * ---- Automatic state decomposition (Section "Automatic State Decomposition",
+ * Fig. hedge) ----
+ * Online bandits over K candidate decompositions (arms). Host code; no device.
+ * DPF_HEDGE: full information. Round t draws from p_i(t) proportional to
+ *   exp(eta G_i(t-1)); dpf_bandit_update(b, r) then takes the whole reward
+ *   vector r(t) (K values in [0, 1]) and adds it to G.
+ * DPF_EXP3: one arm a round. The draw is from phat_j(t) = (1 - gamma) p_j(t) +
+ *   gamma / K; dpf_bandit_update(b, &r) takes the tried arm's reward r in [0, 1]
+ *   and adds r / phat_{i_t}(t) to that arm's G (the simulated reward vector is
+ *   zero elsewhere). dpf_bandit_choose must precede each update.
+ * dpf_bandit_choose draws i_t by the inverse CDF of that distribution at
+ * u = (w + 1/2) 2^-32, w the first word of Philox4x32-10 at counter
+ * (t, 0, 11 << 24, 0) with key (seed_lo, seed_hi). dpf_bandit_probs gives the
+ * current distribution (p for Hedge, phat for Exp3). Rewards outside [0, 1]:
+ * DPF_E_INVALID.
+ */
+typedef struct dpf_bandit dpf_bandit;
+enum { DPF_HEDGE = 0, DPF_EXP3 = 1 };
+dpf_status dpf_bandit_create(int32_t kind, int32_t K, double eta, double gamma, uint64_t seed, dpf_bandit** out);
+dpf_status dpf_bandit_probs(const dpf_bandit* b, double* p);
+dpf_status dpf_bandit_choose(dpf_bandit* b, int32_t* action);
+dpf_status dpf_bandit_update(dpf_bandit* b, const double* rewards);
+/* Reward of an arm (Section 4.3): r = alpha / (alpha + |y - yhat|^2) in (0, 1], with
+ * yhat the arm's one-step-ahead prediction of y (dy values each, host). For a
+ * linear-Gaussian model, yhat_t = H A m_{t-1} from the arm's filtered mean m_{t-1}. */
+dpf_status dpf_bandit_reward(const double* y, const double* yhat, int32_t dy, double alpha, double* r);
+void dpf_bandit_destroy(dpf_bandit* b);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dpf_last_error(void);
 

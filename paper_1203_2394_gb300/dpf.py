@@ -76,6 +76,12 @@ SIGNATURES = [
     ("dpf_state_bytes", ctypes.c_int, [_P, _P]),
     ("dpf_get_state", ctypes.c_int, [_P, _P, _SZ]),
     ("dpf_set_state", ctypes.c_int, [_P, _P, _SZ]),
+    ("dpf_bandit_create", ctypes.c_int, [_I32, _I32, ctypes.c_double, ctypes.c_double, _U64, _P]),
+    ("dpf_bandit_probs", ctypes.c_int, [_P, _P]),
+    ("dpf_bandit_choose", ctypes.c_int, [_P, _P]),
+    ("dpf_bandit_update", ctypes.c_int, [_P, _P]),
+    ("dpf_bandit_reward", ctypes.c_int, [_P, _P, _I32, ctypes.c_double, _P]),
+    ("dpf_bandit_destroy", None, [_P]),
     ("dpf_set_tensor_cores", ctypes.c_int, [_P, _I32]),
     ("dpf_set_debug", ctypes.c_int, [_P, _I32]),
     ("dpf_profile", ctypes.c_int, [_P, _I32]),
@@ -521,3 +527,52 @@ def check_bounded_wait(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     check(lib().dpf_check_bounded_wait(s))
+
+
+DPF_HEDGE, DPF_EXP3 = 0, 1
+
+
+class Bandit:
+    """Hedge or Exp3 over K decompositions (``dpf_bandit_*``)."""
+
+    def __init__(self, kind, K, eta, gamma=0.0, seed=0):
+        self.kind, self.K = int(kind), int(K)
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        check(self._lib.dpf_bandit_create(self.kind, self.K, float(eta), float(gamma),
+                                          ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dpf_bandit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def probs(self):
+        p = np.zeros(self.K)
+        check(self._lib.dpf_bandit_probs(self.h, p.ctypes.data))
+        return p
+
+    def choose(self):
+        a = ctypes.c_int32()
+        check(self._lib.dpf_bandit_choose(self.h, ctypes.byref(a)))
+        return a.value
+
+    def update(self, rewards):
+        r = np.ascontiguousarray(np.atleast_1d(rewards), dtype=np.float64)
+        check(self._lib.dpf_bandit_update(self.h, r.ctypes.data))
+
+
+def bandit_reward(y, yhat, alpha):
+    """``dpf_bandit_reward``: alpha / (alpha + |y - yhat|^2)."""
+    y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    yh = np.ascontiguousarray(yhat, dtype=np.float64).ravel()
+    r = ctypes.c_double()
+    check(lib().dpf_bandit_reward(y.ctypes.data, yh.ctypes.data, y.size, float(alpha), ctypes.byref(r)))
+    return r.value
