@@ -96,9 +96,17 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ts, ln in self.lines:
-            if window is not None and not (window[0] <= ts <= window[1] + 0.2):
-                continue
+        lines, span = self.lines, "timed region"
+        if window is not None:
+            inside = [x for x in lines if window[0] <= x[0] <= window[1] + 0.2]
+            if not inside:
+                # a timed region shorter than the sampling period: the samples just before
+                # and just after it (the GPU is loaded by the warm-up and the timed steps)
+                before = [x for x in lines if x[0] < window[0]][-1:]
+                after = [x for x in lines if x[0] > window[1]][:1]
+                inside, span = before + after, "adjacent to a timed region shorter than 200 ms"
+            lines = inside
+        for ts, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -111,7 +119,7 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "span": span}
 
 
 def dist_env():
