@@ -218,7 +218,8 @@ dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ
  * "head": N x M x dout float, the learned proposal's head outputs of that
  *   inner update (with a proposal set and debug recording on);
  * "afeat" (N x (2 d1 + dy + 2 d2) float) and "ahead" (N x 2 d2 float): the
- *   outer-amortised proposal's group features and network outputs of that update.
+ *   outer-amortised proposal's group features and network outputs of that update;
+ * "fallback" (N int32): 1 where that learned update fell back to the plain rule.
  * Element type: the context's precision (or int32). Synchronises the stream.
  */
 dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t bytes);
@@ -380,6 +381,18 @@ void dpf_proposal_destroy(dpf_proposal* p);
  * it by log r = log p(z_t | z_{t-1}, x_{t-1}) - log q_phi(z_t | f) + log p(y_t | x_t, z_t).
  */
 dpf_status dpf_set_proposal(dpf_ctx* ctx, dpf_proposal* p);
+
+/*
+ * Per-group fallback of the learned proposal to the plain inner update (the prior
+ * proposal after local resampling, Fig. 4 step 4): after the learned update of a
+ * step, a group whose inner effective sample size (sum_j W_j)^2 / sum_j W_j^2,
+ * W = exp(lq) in FP32, is below frac * M (or has no finite weight) redoes its
+ * inner update by the plain rule, with the same keys as a filter without a
+ * proposal. frac in [0, 1]; 0 turns the fallback off; 0.25 when never set.
+ * dpf_read(ctx, "fallback", ...) gives the last step's flags (N int32, 1 = fell
+ * back).
+ */
+dpf_status dpf_set_fallback(dpf_ctx* ctx, double frac);
 
 /*
  * Training rows from the inner update the last dpf_step ran (it must have run

@@ -220,6 +220,20 @@ def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, 
 #   z_ij = m_i + c_i + s_i * (zhat_ij - m_i),
 #   log q(z_ij) = log N(zhat_ij; mu_ij, Q_z) - sum log s_i.
 # ---------------------------------------------------------------------------
+def inner_ess(lq):
+    """Inner effective sample size of each group, (sum_j W_j)^2 / sum_j W_j^2 with
+    W = exp(lq) (rows of lq are groups)."""
+    lq = np.asarray(lq, dtype=np.float64)
+    W = np.exp(lq - lq.max(axis=1, keepdims=True))
+    return W.sum(1) ** 2 / (W * W).sum(1)
+
+
+def fallback_groups(lq, frac):
+    """The groups whose learned inner update falls back to the plain rule: inner ESS
+    below frac * M (M = the row length)."""
+    return inner_ess(lq) < frac * np.asarray(lq).shape[1]
+
+
 def affine_head(out, d2):
     raw = out[:, :d2]
     ls = np.clip(raw, LOGSIG_MIN, LOGSIG_MAX)

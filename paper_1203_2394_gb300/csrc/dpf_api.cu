@@ -372,13 +372,25 @@ static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
   if (x->debug && x->anc_prev && t >= 2)  // the ancestors this call's inner update reads
     cudaMemcpyAsync(x->anc_prev, x->anc, sizeof(int32_t) * x->N, cudaMemcpyDeviceToDevice, x->stream);
   if (x->proposal && t >= 2) {
-    // learned proposal: its inner update, then the look-ahead alone
+    // learned proposal: its inner update; groups whose inner ESS fell below
+    // fb_frac * M redo it with the plain rule (and their look-ahead); the look-ahead
+    // of the other groups then runs alone from the materialised state
     st = learned_inner_step(*x);
+    const bool fallback = x->fb_frac > 0.0;
+    if (!st) st = learned_fallback_lists(*x);
+    if (!st && fallback) {
+      x->glist_cur = x->fb_list;
+      x->gcount_cur = x->fb_count;
+      st = x->var->step(*x, 0);
+      x->glist_cur = x->gcount_cur = nullptr;
+      x->gskip_cur = x->fb_flag;
+    }
     if (!st) {
       x->la_only = true;
       st = x->var->step(*x, 0);
       x->la_only = false;
     }
+    x->glist_cur = x->gcount_cur = x->gskip_cur = nullptr;
   } else {
     st = x->var->step(*x, 0);
   }
@@ -572,6 +584,9 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
       return set_error(DPF_E_INVALID, "dpf_read: afeat/ahead need an outer-amortised proposal");
     const int d = w == "afeat" ? 2 * x->d1 + x->dy + 2 * x->d2 : 2 * x->d2;
     src = w == "afeat" ? x->oa_feat : x->oa_out; need = 4 * N * (size_t)d;
+  } else if (w == "fallback") {
+    if (!x->fb_flag) return set_error(DPF_E_INVALID, "dpf_read: fallback needs a learned proposal");
+    src = x->fb_flag; need = 4 * N;
   } else if (w == "head") {
     if (!x->dbg_head || !x->proposal)
       return set_error(DPF_E_INVALID, "dpf_read: head needs a learned proposal and dpf_set_debug(ctx, 1)");

@@ -105,7 +105,8 @@ struct Variant {
   bool xz_supported = true;  // serves models whose x transition depends on z
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
-dpf_status learned_inner_step(Ctx& x);  // dpf_learned_step.cu
+dpf_status learned_inner_step(Ctx& x);
+dpf_status learned_fallback_lists(Ctx& x);  // dpf_learned_step.cu
 int dpf_proposal_dout(const dpf_proposal* p);  // head outputs of a proposal
 int dpf_proposal_kind(const dpf_proposal* p);  // 0 mixture, 1 outer-amortised
 
@@ -168,6 +169,14 @@ struct dpf_ctx {
   bool tensor_cores = true;  // tensor-core propagation where the variant has one
   dpf_proposal* proposal = nullptr;  // learned inner proposal (null: the prior)
   bool la_only = false;      // the next step kernel runs the look-ahead only
+  // the learned proposal's per-group fallback to the plain inner update
+  double fb_frac = 0.25;          // a group falls back when its inner ESS < fb_frac * M (0: never)
+  int32_t* fb_flag = nullptr;     // [N] 1 where the last learned inner update fell back
+  int32_t* fb_list = nullptr;     // [N] the groups that fall back
+  int32_t* fb_count = nullptr;    // [1] their count
+  const int32_t* glist_cur = nullptr;   // the next step kernel's group subset (null: all)
+  const int32_t* gcount_cur = nullptr;
+  const int32_t* gskip_cur = nullptr;   // ... groups it leaves untouched (null: none)
   // profiling of the main kernel
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // pairs bracketing the step kernel

@@ -993,6 +993,43 @@ static dpf_status oa_step_pp(Ctx& x, const MC<float, 2, 2, 2>& mc, StepArgs<floa
   return cuda_error(cudaGetLastError(), "amortised update launch");
 }
 
+// The per-group fallback: the inner effective sample size of each group's learned
+// update, ESS = (sum_j W_j)^2 / sum_j W_j^2 with W = exp(lq), against thr = fb_frac M.
+// Groups below it (or with no finite weight) are flagged and listed (in no particular
+// order) for the plain inner update; one warp a group.
+__global__ void fallback_lists_kernel(const float* __restrict__ lq, long long N, int M, float thr,
+                                      int32_t* flag, int32_t* list, int32_t* count) {
+  const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;  // whole warps
+  float s1 = 0.f, s2 = 0.f;
+  for (int k = lane; k < M; k += 32) {
+    const float w = expf(lq[i * M + k]);
+    s1 += w;
+    s2 += w * w;
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    const bool fb = !(s1 * s1 >= thr * s2);
+    flag[i] = fb ? 1 : 0;
+    if (fb) list[atomicAdd(count, 1)] = (int32_t)i;
+  }
+}
+
+dpf_status learned_fallback_lists(Ctx& x) {
+  const long long t = x.t + 1;
+  if (x.fb_frac <= 0.0)  // no fallback: no group is flagged
+    return cuda_error(cudaMemsetAsync(x.fb_flag, 0, sizeof(int32_t) * x.N, x.stream), "fallback flags");
+  cudaError_t e = cudaMemsetAsync(x.fb_count, 0, sizeof(int32_t), x.stream);
+  if (e != cudaSuccess) return cuda_error(e, "fallback counts");
+  const unsigned blocks = (unsigned)((x.N + 3) / 4);
+  fallback_lists_kernel<<<blocks, 128, 0, x.stream>>>((const float*)x.lq[(t + 1) % 2], x.N, x.M,
+                                                      (float)(x.fb_frac * x.M), x.fb_flag, x.fb_list,
+                                                      x.fb_count);
+  return cuda_error(cudaGetLastError(), "fallback lists launch");
+}
+
 // The inner update of the coming step with the learned proposal (the variant
 // (FP32, 2, 2, 2)); then the look-ahead runs alone from the materialised state.
 dpf_status learned_inner_step(Ctx& x) {
@@ -1108,23 +1145,38 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
                        !(x->M == 32 || x->M == 64 || x->M == 128)))
     return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: compiled for (d1, d2, dy) = (2, 2, 2), hidden 256, "
                                         "4 components and M in {32, 64, 128}");
+  if (p->kind == 1 && (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH ||
+                       !(x->M == 32 || x->M == 64 || x->M == 128 || x->M == 256)))
+    return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: the amortised pass is compiled for (d1, d2, dy) = "
+                                        "(2, 2, 2), hidden 256 and M in {32, 64, 128, 256}");
+  auto grow = [&](void** q, size_t bytes) -> cudaError_t {
+    if (*q) return cudaSuccess;
+    cudaError_t e = cudaMalloc(q, bytes);
+    if (e == cudaSuccess) x->allocs.push_back(*q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*q, 0, bytes, x->stream);
+    return e;
+  };
+  {  // the per-group fallback's flags, group lists and counts
+    cudaError_t e = grow((void**)&x->fb_flag, sizeof(int32_t) * (size_t)x->N);
+    if (e == cudaSuccess) e = grow((void**)&x->fb_list, sizeof(int32_t) * (size_t)x->N);
+    if (e == cudaSuccess) e = grow((void**)&x->fb_count, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_error(e, "dpf_set_proposal: fallback buffers");
+  }
   if (p->kind == 1) {
-    if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH ||
-        !(x->M == 32 || x->M == 64 || x->M == 128 || x->M == 256))
-      return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: the amortised pass is compiled for (d1, d2, dy) = "
-                                          "(2, 2, 2), hidden 256 and M in {32, 64, 128, 256}");
-    auto grow = [&](void** q, size_t bytes) -> cudaError_t {
-      if (*q) return cudaSuccess;
-      cudaError_t e = cudaMalloc(q, bytes);
-      if (e == cudaSuccess) x->allocs.push_back(*q);
-      return e;
-    };
     cudaError_t e = grow(&x->oa_bidx, sizeof(int32_t) * (size_t)x->N * x->M);
     if (e == cudaSuccess) e = grow(&x->oa_feat, sizeof(float) * (size_t)x->N * LDIN);
     if (e == cudaSuccess) e = grow(&x->oa_out, sizeof(float) * (size_t)x->N * LNP);
     if (e != cudaSuccess) return cuda_error(e, "dpf_set_proposal: amortised buffers");
   }
   x->proposal = p;
+  return DPF_OK;
+}
+
+dpf_status dpf_set_fallback(dpf_ctx* x, double frac) {
+  clear_error();
+  if (!x || !(frac >= 0.0 && frac <= 1.0))
+    return set_error(DPF_E_INVALID, "dpf_set_fallback: null context or frac outside [0, 1]");
+  x->fb_frac = frac;
   return DPF_OK;
 }
 

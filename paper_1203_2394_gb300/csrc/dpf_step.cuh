@@ -85,7 +85,25 @@ struct StepArgs {
   uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
   uint32_t off_zmat, off_sb;           // wide z (d2 > 32): [A_zz K] rows and the combined sums
   int la_only;  // the inner update already ran (learned proposal): look-ahead from the materialised state
+  // optional subset of the groups: positions 0 .. *gcount - 1 of glist (device), in
+  // place of every group 0 .. N - 1 (the learned proposal's per-group fallback)
+  const int32_t* glist;
+  const int32_t* gcount;
+  const int32_t* gskip;  // optional [N]: groups with a nonzero entry are left untouched
 };
+
+// Group index at position g of the launch's group sequence.
+template <typename T>
+__device__ __forceinline__ long long group_at(const StepArgs<T>& a, long long g) {
+  return a.glist ? (long long)a.glist[g] : g;
+}
+// Number of positions in the launch's group sequence.
+template <typename T>
+__device__ __forceinline__ long long group_count(const StepArgs<T>& a) {
+  if (!a.glist) return a.N;
+  const long long c = (long long)*a.gcount;
+  return c < a.N ? c : a.N;
+}
 
 // Order-preserving unsigned keys of floating-point values (for atomicMax).
 __device__ __forceinline__ unsigned long long order_key(float v) {
@@ -465,21 +483,29 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
   // source index in flight
   long long g = blockIdx.x;
   long long src_next = -1;
-  if (BULK && g < N) {
-    const long long src0 = a.first ? g : (long long)a.anc[g];
+  const long long G = group_count(a);
+  if (BULK && g < G) {
+    const long long i0 = group_at(a, g);
+    const long long src0 = a.first ? i0 : (long long)a.anc[i0];
     stage_group<T, D1, D2, BULK>(a, stage0, &bars[0], src0);
-    if (tid == 0 && g + gridDim.x < N) src_next = a.first ? g + gridDim.x : (long long)a.anc[g + gridDim.x];
+    if (tid == 0 && g + gridDim.x < G) {
+      const long long i1 = group_at(a, g + gridDim.x);
+      src_next = a.first ? i1 : (long long)a.anc[i1];
+    }
   }
-  for (int k = 0; g < N; g += gridDim.x, ++k) {
-    const long long i = g;
+  for (int k = 0; g < G; g += gridDim.x, ++k) {
+    const long long i = group_at(a, g);
     const int sidx = k & 1;
     unsigned char* st = stage0 + (BULK ? sidx * a.stage_bytes : 0);
     if (BULK) {
       // prefetch the next group into the other stage (released at the end of the last group)
-      if (tid == 0 && g + gridDim.x < N) {
+      if (tid == 0 && g + gridDim.x < G) {
         stage_group<T, D1, D2, BULK>(a, stage0 + (sidx ^ 1) * a.stage_bytes, &bars[sidx ^ 1], src_next);
         const long long g2 = g + 2 * (long long)gridDim.x;
-        if (g2 < N) src_next = a.first ? g2 : (long long)a.anc[g2];
+        if (g2 < G) {
+          const long long i2 = group_at(a, g2);
+          src_next = a.first ? i2 : (long long)a.anc[i2];
+        }
       }
       int spins = 0;
       while (!mbar_test(&bars[sidx], (uint32_t)((k >> 1) & 1))) {
@@ -488,10 +514,14 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           break;
         }
       }
-    } else {
-      const long long src = a.first ? g : (long long)a.anc[g];
+    } else if (!(a.gskip && a.gskip[i])) {
+      const long long src = a.first ? i : (long long)a.anc[i];
       stage_group<T, D1, D2, BULK>(a, st, nullptr, src);
       __syncthreads();
+    }
+    if (a.gskip && a.gskip[i]) {  // every thread has left the stage wait before it is re-armed
+      __syncthreads();
+      continue;
     }
     T* sz = (T*)(st + a.off_sz);
     T* slq = (T*)(st + a.off_slq);

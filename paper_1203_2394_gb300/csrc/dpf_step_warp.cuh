@@ -261,13 +261,21 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 
   long long g = gfirst;
   long long src_next = -1;  // the same in every lane
+  if (a.glist) {
+    const long long G = group_count(a);
+    if (G < gend) gend = G;
+  }
   if (g < gend) {
-    warp_stage<T, D1, D2>(a, ws, bar, a.first ? g : (long long)a.anc[g], lane);
-    if (g + W < gend) src_next = a.first ? g + W : (long long)a.anc[g + W];
+    const long long i0 = group_at(a, g);
+    warp_stage<T, D1, D2>(a, ws, bar, a.first ? i0 : (long long)a.anc[i0], lane);
+    if (g + W < gend) {
+      const long long i1 = group_at(a, g + W);
+      src_next = a.first ? i1 : (long long)a.anc[i1];
+    }
   }
   __syncwarp();
   for (; g < gend; g += W, phase ^= 1u) {
-    const long long i = g;
+    const long long i = group_at(a, g);
     {  // wait for this group's rows (bounded)
       int spins = 0;
       while (!mbar_test(bar, phase)) {
@@ -276,6 +284,18 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
           break;
         }
       }
+    }
+    if (a.gskip && a.gskip[i]) {  // a group left untouched: pass its stage on
+      __syncwarp();
+      if (g + W < gend) {
+        warp_stage<T, D1, D2>(a, ws, bar, src_next, lane);
+        const long long g2 = g + 2 * W;
+        if (g2 < gend) {
+          const long long i2 = group_at(a, g2);
+          src_next = a.first ? i2 : (long long)a.anc[i2];
+        }
+      }
+      continue;
     }
     T x[D1];
     T zr[D2][PPL];  // this lane's inner particles z_{t-1}^(i, k0 + p)
@@ -525,7 +545,10 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
     if (g + W < gend) {
       warp_stage<T, D1, D2>(a, ws, bar, src_next, lane);
       const long long g2 = g + 2 * W;
-      if (g2 < gend) src_next = a.first ? g2 : (long long)a.anc[g2];
+      if (g2 < gend) {
+        const long long i2 = group_at(a, g2);
+        src_next = a.first ? i2 : (long long)a.anc[i2];
+      }
     }
 
     // ======== look-ahead of step t from (x, z, lq) with y_t ========

@@ -180,6 +180,9 @@ struct VariantImpl {
     a.logM = (T)std::log((double)x.M);
     a.logL = (T)std::log((double)x.L);
     a.log2M = ceil_log2_i(x.M);
+    a.glist = x.glist_cur;
+    a.gcount = x.gcount_cur;
+    a.gskip = x.gskip_cur;
   }
 
   static bool use_xz(const Ctx& x) { return XZM == 1 || x.hm.xz; }

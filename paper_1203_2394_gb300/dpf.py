@@ -76,6 +76,7 @@ SIGNATURES = [
     ("dpf_state_bytes", ctypes.c_int, [_P, _P]),
     ("dpf_get_state", ctypes.c_int, [_P, _P, _SZ]),
     ("dpf_set_state", ctypes.c_int, [_P, _P, _SZ]),
+    ("dpf_set_fallback", ctypes.c_int, [_P, ctypes.c_double]),
     ("dpf_bandit_create", ctypes.c_int, [_I32, _I32, ctypes.c_double, ctypes.c_double, _U64, _P]),
     ("dpf_bandit_probs", ctypes.c_int, [_P, _P]),
     ("dpf_bandit_choose", ctypes.c_int, [_P, _P]),
@@ -204,7 +205,7 @@ class Filter:
         "lw": lambda s: (s.N,), "lwhat": lambda s: (s.N, s.L), "xbb": lambda s: (s.N, s.L, s.d1),
         "anc": lambda s: (s.N,), "sel": lambda s: (s.N,), "wout": lambda s: (s.N,),
         "x": lambda s: (s.N, s.d1), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
-        "bidx": lambda s: (s.N, s.M),
+        "bidx": lambda s: (s.N, s.M), "fallback": lambda s: (s.N,),
         "head": lambda s: (s.N, s.M, s.proposal.dout),
         "afeat": lambda s: (s.N, 2 * s.d1 + s.dy + 2 * s.d2),
         "ahead": lambda s: (s.N, 2 * s.d2),
@@ -212,13 +213,17 @@ class Filter:
 
     def read(self, which: str) -> np.ndarray:
         shape = self._SHAPES[which](self)
-        dt = np.int32 if which in ("anc", "sel", "bidx") else self.dtype
+        dt = np.int32 if which in ("anc", "sel", "bidx", "fallback") else self.dtype
         out = np.zeros(shape, dtype=dt)
         check(self._lib.dpf_read(self.h, which.encode(), out.ctypes.data, out.nbytes))
         return out
 
     def set_debug(self, on=True):
         check(self._lib.dpf_set_debug(self.h, int(on)))
+
+    def set_fallback(self, frac):
+        """Learned proposal: groups with inner ESS below frac * M redo the plain update."""
+        check(self._lib.dpf_set_fallback(self.h, float(frac)))
 
     def set_tensor_cores(self, on=True):
         check(self._lib.dpf_set_tensor_cores(self.h, int(on)))

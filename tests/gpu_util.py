@@ -35,3 +35,23 @@ def check_lwhat(gpu, ref, tol, floor=40.0):
     dead = ~live
     if dead.any():
         assert np.all(gpu[dead] <= gmax.repeat(gpu.shape[1], 1)[dead] - floor / 2)
+
+
+def check_fallback(fb, z, lq, got, fin, frac=0.25, tol=1e-5):
+    """The learned inner update with the per-group fallback: the GPU's flags `fb` agree
+    with the oracle's rule on the oracle's learned weights (ESS < frac M), except for
+    groups whose ESS lies within 1e-4 M of the threshold (the GPU decides in FP32); the
+    groups that fell back match the oracle's plain update `fin`, the others its learned
+    update `got`. Returns the number of groups that fell back."""
+    from oracle import learned
+    fb = np.asarray(fb).astype(bool)
+    M = lq.shape[1]
+    ess = learned.inner_ess(got["lq"])
+    near = np.abs(ess - frac * M) <= 1e-4 * M
+    bad = (fb != (ess < frac * M)) & ~near
+    assert not bad.any(), (np.nonzero(bad)[0][:10], ess[bad][:10])
+    zr = np.where(fb[:, None, None], fin["z"], got["z"])
+    lqr = np.where(fb[:, None], fin["lq"], got["lq"])
+    np.testing.assert_allclose(z, zr, rtol=0, atol=tol)
+    assert np.max(rel(lq, lqr)) <= tol, np.max(rel(lq, lqr))
+    return int(fb.sum())

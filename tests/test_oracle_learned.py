@@ -234,3 +234,22 @@ def test_identity_affine_map_reproduces_the_plain_inner_update():
                                      normals=lambda t, i, p, j, n: oracle.normals(seed, 0, t, i, p, j, n, lib))
     np.testing.assert_allclose(got["z"], fin["z"], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(got["lq"], fin["lq"], rtol=1e-10, atol=1e-10)
+
+
+def test_inner_ess_and_the_fallback_rule():
+    """Inner ESS: M for equal weights, k for k equal weights and the rest zero, shift
+    invariant; weights (1, 1, 1, 3) give 6^2 / 12 = 3, so the strict rule ESS < frac M
+    falls back at frac 0.8 (3 < 3.2) and not at 0.75 (3 = 3)."""
+    M = 64
+    assert learned.inner_ess(np.zeros((1, M)))[0] == pytest.approx(M, rel=1e-15)
+    for k in (1, 5, 32):
+        lq = np.full((1, M), -np.inf)
+        lq[0, :k] = -3.0
+        assert learned.inner_ess(lq)[0] == pytest.approx(k, rel=1e-15)
+    rng = np.random.default_rng(0)
+    lq = rng.standard_normal((7, M))
+    np.testing.assert_allclose(learned.inner_ess(lq + 17.5), learned.inner_ess(lq), rtol=1e-13)
+    lq4 = np.log(np.array([[1.0, 1.0, 1.0, 3.0]]))
+    assert learned.inner_ess(lq4)[0] == pytest.approx(3.0, rel=1e-15)
+    assert learned.fallback_groups(lq4, 0.8)[0]
+    assert not learned.fallback_groups(lq4, 0.75)[0]
