@@ -84,6 +84,7 @@ struct StepArgs {
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
   uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
   uint32_t off_zmat, off_sb;           // wide z (d2 > 32): [A_zz K] rows and the combined sums
+  uint32_t off_proj;                   // wide z, tensor cores: [L_r^-1 H_z | H_z A_zz] columns
   int la_only;  // the inner update already ran (learned proposal): look-ahead from the materialised state
   // optional subset of the groups: positions 0 .. *gcount - 1 of glist (device), in
   // place of every group 0 .. N - 1 (the learned proposal's per-group fallback)
@@ -178,7 +179,8 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
                  alo = tc ? take(sizeof(float) * (size_t)np * D2) : 0u;
   // wide z: the rows [A_zz(r, .) K(r, .)] for the z-mean combine, one warp a row
   const uint32_t zmat = D2 > 32 ? take(sizeof(T) * (size_t)D2 * (D2 + DY)) : 0u,
-                 sbo = D2 > 32 ? take(sizeof(T) * (size_t)(D2 + DY)) : 0u;
+                 sbo = D2 > 32 ? take(sizeof(T) * (size_t)(D2 + DY)) : 0u,
+                 proj = (D2 > 32 && tc) ? take(sizeof(T) * (size_t)D2 * 2 * DY) : 0u;
   if (a) {
     a->tpm = tpm;
     a->rows = nt / tpm;
@@ -191,7 +193,7 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
     a->off_cum = cum; a->off_kd = kd; a->off_E = E; a->off_xw = xw;
     a->off_cw = cw; a->off_xbs = xbs; a->off_row = row; a->off_red = red; a->off_part = part;
     a->off_zlo = zlo; a->off_ahi = ahi; a->off_alo = alo;
-    a->off_zmat = zmat; a->off_sb = sbo;
+    a->off_zmat = zmat; a->off_sb = sbo; a->off_proj = proj;
   }
   return o;
 }
@@ -404,6 +406,10 @@ constexpr int TC_SPIN = 1 << 22;  // bounded wait for the tensor-core MMAs of on
 template <typename T, int D1, int D2, int DY, bool XZ, int PPT, bool BULK, bool TC>
 __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const StepArgs<T>& a) {
   static_assert(!TC || (sizeof(T) == 4 && PPT == 1 && !BULK && D2 % 8 == 0), "tensor-core step");
+  // one stage filled by bulk copies issued as soon as the stage is free (tensor-core
+  // step: right after the MMAs that read it), so the next group's rows arrive during
+  // the rest of this group
+  constexpr bool PF = TC;
   constexpr int NP = (D2 + 15) / 16 * 16;  // MMA N: A_zz rows padded to 16
   constexpr int KC16 = D2 * 4 / 16;        // 16-byte chunks per operand row
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -436,8 +442,9 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
   const int tid = threadIdx.x, lane = tid & 31;
   const T NEG = neg_inf<T>();
   const T LOG2E = (T)LOG2E_D, SQ = (T)SQ_D;
+  const RoundKeys rk = round_keys(a.key);  // (the tensor-core path's noise)
   if (blockIdx.x == 0 && tid == 0) *a.Csum = 0ull;
-  if (BULK && tid == 0) {
+  if ((BULK || PF) && tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     mbar_fence_init();
@@ -447,6 +454,13 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
     for (int e = tid; e < D2 * (D2 + DY); e += NT) {
       const int r = e / (D2 + DY), c = e % (D2 + DY);
       zmat[e] = c < D2 ? mc.Azz[r][c] : mc.K[r][c - D2];
+    }
+  }
+  if constexpr (TC && D2 > 32) {  // per coordinate r: (L_r^-1 H_z)[., r] then (H_z A_zz)[., r]
+    T* pj = (T*)(smem_raw + a.off_proj);
+    for (int e = tid; e < D2 * 2 * DY; e += NT) {
+      const int r = e / (2 * DY), q = e % (2 * DY);
+      pj[e] = q < DY ? mc.LrHz[q][r] : mc.HzAzz[q - DY][r];
     }
   }
   uint32_t taddr = 0, tc_phase = 0;
@@ -484,6 +498,12 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
   long long g = blockIdx.x;
   long long src_next = -1;
   const long long G = group_count(a);
+  // the source group of position q (the next one a stage is filled for)
+  auto source_of = [&](long long q) {
+    const long long iq = group_at(a, q);
+    return a.first ? iq : (long long)a.anc[iq];
+  };
+  if (PF && g < G) stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g));
   if (BULK && g < G) {
     const long long i0 = group_at(a, g);
     const long long src0 = a.first ? i0 : (long long)a.anc[i0];
@@ -514,16 +534,32 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           break;
         }
       }
+    } else if (PF) {
+      int spins = 0;
+      while (!mbar_test(&bars[0], (uint32_t)(k & 1))) {
+        if (++spins > MBAR_SPIN_LIMIT) {
+          if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+          break;
+        }
+      }
     } else if (!(a.gskip && a.gskip[i])) {
       const long long src = a.first ? i : (long long)a.anc[i];
       stage_group<T, D1, D2, BULK>(a, st, nullptr, src);
       __syncthreads();
     }
+    bool pf_issued = false;  // the next group's stage copy is under way
     if (a.gskip && a.gskip[i]) {  // every thread has left the stage wait before it is re-armed
       __syncthreads();
+      if (PF && tid == 0 && g + gridDim.x < G)
+        stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
       continue;
     }
     T* sz = (T*)(st + a.off_sz);
+    T* zsrc = sz;          // wide z: where the look-ahead's z sits for the z-mean
+    bool zstored = false;  // z_t already written (the rolled tensor-core epilogue)
+    T gz[DY];              // ... and its H_z A_zz z_t
+#pragma unroll
+    for (int q = 0; q < DY; ++q) gz[q] = T(0);
     T* slq = (T*)(st + a.off_slq);
     T* sx = (T*)(st + a.off_sx);
     T* slwh = (T*)(st + a.off_slwh);
@@ -747,6 +783,18 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         float zb2[D2];
 #pragma unroll
         for (int c = 0; c < D2; ++c) zb2[c] = (float)sz[c * M + b];
+        // A_zx x_a, the same for the whole group, and the diagonal of L_qz (part is free
+        // until the z-mean)
+        T* s_azx = part;
+        T* s_lqd = part + D2;
+        if (tid < D2) {
+          const int r = tid < D2 ? tid : 0;
+          T v = T(0);
+#pragma unroll
+          for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
+          s_azx[r] = v;
+          s_lqd[r] = mc.Lqz[r][r];
+        }
         __syncthreads();  // every gather is done: the staged z rows become the A operand
         unsigned char* zhi = (unsigned char*)sz;
         unsigned char* zlo = smem_raw + a.off_zlo;
@@ -783,15 +831,61 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           }
           tc::commit(&tcbar);
         }
-        // the propagation noise, drawn while the MMAs run
+        const uint32_t ta = taddr + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((j >> 7) * NP);
+        if constexpr (D2 > 32) zsrc = (T*)(smem_raw + a.off_zlo);  // the low parts are consumed
+        T qf = T(0);
+        if (mc.diag_qz) {
+          // diagonal Q_z: four coordinates at a time (a TMEM load, one Philox block of noise);
+          // z_t goes to the state and to shared memory, and the whitened y residual and the
+          // look-ahead's H_z A_zz z_t accumulate on the way (a rolled loop: small code)
+          const bool ok = tc::bar_wait(&tcbar, tc_phase, TC_SPIN);
+          tc_phase ^= 1u;
+          if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+          tc::fence_after();
+          // the MMAs have read the stage: the next group's rows may come in
+          if (tid == 0 && g + gridDim.x < G)
+            stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+          pf_issued = true;
+          const T* pj = (const T*)(smem_raw + a.off_proj);
+          T* zn = a.z_new + i * M + j;
+          T rl[DY];
+#pragma unroll
+          for (int q = 0; q < DY; ++q) rl[q] = yh[q];
+#pragma unroll 2
+          for (int cb = 0; cb < D2 / 4; ++cb) {
+            float a4[4];
+            tc::ld4(ta + (uint32_t)(4 * cb), a4);
+            T e[4];
+            normal_block_rk(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, cb, 4, e);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = 4 * cb + u;
+              const T v = ((ok ? (T)a4[u] : T(0)) + s_azx[r]) + s_lqd[r] * e[u];
+              zsrc[r * M + j] = v;
+              zn[(long long)r * NM] = v;
+              const T* pr = pj + r * 2 * DY;
+#pragma unroll
+              for (int q = 0; q < DY; ++q) rl[q] -= pr[q] * v;
+#pragma unroll
+              for (int q = 0; q < DY; ++q) gz[q] += pr[DY + q] * v;
+            }
+          }
+          tc::fence_before();
+#pragma unroll
+          for (int q = 0; q < DY; ++q) qf += rl[q] * rl[q];
+          zstored = true;
+        } else {
+        // a general L_qz: every coordinate's noise at once, drawn while the MMAs run
         T eps[D2];
-        normals<D2>(a.key, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
+        normals_rk<D2>(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, eps);
         const bool ok = tc::bar_wait(&tcbar, tc_phase, TC_SPIN);
         tc_phase ^= 1u;
         if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
         tc::fence_after();
+        if (tid == 0 && g + gridDim.x < G)
+          stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+        pf_issued = true;
         {
-          const uint32_t ta = taddr + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((j >> 7) * NP);
           float azz[(D2 + 15) / 16 * 16];
           if constexpr (NP == 64) {  // the whole padded row in one load
             tc::ld64(ta, *reinterpret_cast<float(*)[64]>(azz));
@@ -803,24 +897,19 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           // z_new = A_zz z_b + A_zx x_a + L_qz eps, one coordinate at a time
 #pragma unroll
           for (int r = 0; r < D2; ++r) {
-            T v = ok ? (T)azz[r] : T(0);
+            T v = (ok ? (T)azz[r] : T(0)) + s_azx[r];
 #pragma unroll
-            for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
-            if (mc.diag_qz) {
-              v += mc.Lqz[r][r] * eps[r];
-            } else {
-              for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
-            }
+            for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
             zr[0][r] = v;
           }
         }
-        T qf = T(0);
 #pragma unroll
         for (int q = 0; q < DY; ++q) {
           T v = yh[q];
 #pragma unroll
           for (int c = 0; c < D2; ++c) v -= mc.LrHz[q][c] * zr[0][c];
           qf += v * v;
+        }
         }
         ell[0] = T(-0.5) * qf;
         lmax = ell[0];
@@ -837,8 +926,14 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
       for (int p = 0; p < PPT; ++p) {
         if (tid + p * NT < M) {
           lqr[p] = ell[p] - lmax - llsum;
+          if (!zstored) {
 #pragma unroll
-          for (int c = 0; c < D2; ++c) zn[c * NM + p * NT] = zr[p][c];
+            for (int c = 0; c < D2; ++c) zn[c * NM + p * NT] = zr[p][c];
+            if constexpr (D2 > 32) {  // z_t for the z-mean (every gather from the stage is done)
+#pragma unroll
+              for (int c = 0; c < D2; ++c) zsrc[c * M + tid + p * NT] = zr[p][c];
+            }
+          }
           a.lq_new[i * M + tid + p * NT] = lqr[p];
         }
       }
@@ -867,8 +962,12 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           T v = e;
 #pragma unroll
           for (int c = 0; c < D1; ++c) v += mc.HzAzx[q][c] * x[c];
+          if (zstored) {
+            v += gz[q];
+          } else {
 #pragma unroll
-          for (int c = 0; c < D2; ++c) v += mc.HzAzz[q][c] * zr[p][c];
+            for (int c = 0; c < D2; ++c) v += mc.HzAzz[q][c] * zr[p][c];
+          }
           g_[q] = v;
         }
 #pragma unroll
@@ -1085,68 +1184,134 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
     }
     __syncthreads();
     // ---- z part: beta_k = sum_m coef_m E[m][k]; z-mean = A_zx x + A_zz sum beta z + K sum beta ep ----
-    T acc[D2 + DY];
-#pragma unroll
-    for (int c = 0; c < D2 + DY; ++c) acc[c] = T(0);
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      const int j = tid + p * NT;
-      if (j < M) {
-        T beta = T(0);
-        for (int m = 0; m < L; ++m) beta += coef[m] * E[m * stride + j];
-#pragma unroll
-        for (int c = 0; c < D2; ++c) acc[c] += beta * zr[p][c];
-#pragma unroll
-        for (int q = 0; q < DY; ++q) acc[D2 + q] += beta * ep[p][q];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < D2 + DY; ++c) acc[c] = warp_sum(acc[c]);
-    const int w = tid >> 5, nw = NT >> 5;
-    if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < D2 + DY; ++c) part[c * 32 + w] = acc[c];
-    }
-    __syncthreads();
     if constexpr (D2 > 32) {
-      // wide z: the D2 + DY sums over the warps, then one warp a row of [A_zz K] . sums
+      // wide z: beta to shared memory (the records are no longer read), the z sums one warp
+      // a column over the stage's z rows, the DY noise sums over the warps, then one warp a
+      // row of [A_zz K] . sums
+      T* sbeta = kd;
       T* sbs = (T*)(smem_raw + a.off_sb);
       const T* zmat = (const T*)(smem_raw + a.off_zmat);
-      if (tid < D2 + DY) {
-        T v = T(0);
-        for (int q = 0; q < nw; ++q) v += part[tid * 32 + q];
-        sbs[tid] = v;
-      }
-      __syncthreads();
-      for (int r = w; r < D2; r += nw) {
-        T v = T(0);
-        for (int c = lane; c < D2 + DY; c += 32) v += zmat[r * (D2 + DY) + c] * sbs[c];
-        v = warp_sum(v);
-        if (lane == 0) {
+      const int w = tid >> 5, nw = NT >> 5;
+      T acc[DY];
 #pragma unroll
-          for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * x[c];
-          a.zm[(long long)r * N + i] = v;
+      for (int q = 0; q < DY; ++q) acc[q] = T(0);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        const int j = tid + p * NT;
+        if (j < M) {
+          T beta = T(0);
+          for (int m = 0; m < L; ++m) beta += coef[m] * E[m * stride + j];
+          sbeta[j] = beta;
+#pragma unroll
+          for (int q = 0; q < DY; ++q) acc[q] += beta * ep[p][q];
         }
       }
-    } else if (tid < D2) {
-      const int r = tid;
-      T sb[D2 + DY];
 #pragma unroll
-      for (int c = 0; c < D2 + DY; ++c) {
-        T v = T(0);
-        for (int q = 0; q < nw; ++q) v += part[c * 32 + q];
-        sb[c] = v;
+      for (int q = 0; q < DY; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < DY; ++q) part[q * 32 + w] = acc[q];
       }
-      T v = T(0);
+      __syncthreads();
+      constexpr int CPW = 8;  // columns (rows below) a warp sums side by side
+      for (int c0 = w; c0 < D2; c0 += nw * CPW) {
+        T v[CPW];
 #pragma unroll
-      for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * x[c];
+        for (int u = 0; u < CPW; ++u) v[u] = T(0);
+        for (int k2 = lane; k2 < M; k2 += 32) {
+          const T bk = sbeta[k2];
 #pragma unroll
-      for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * sb[c];
+          for (int u = 0; u < CPW; ++u)
+            if (c0 + u * nw < D2) v[u] += bk * zsrc[(c0 + u * nw) * M + k2];
+        }
 #pragma unroll
-      for (int q = 0; q < DY; ++q) v += mc.K[r][q] * sb[D2 + q];
-      a.zm[(long long)r * N + i] = v;
+        for (int u = 0; u < CPW; ++u) v[u] = warp_sum(v[u]);
+        if (lane == 0) {
+#pragma unroll
+          for (int u = 0; u < CPW; ++u)
+            if (c0 + u * nw < D2) sbs[c0 + u * nw] = v[u];
+        }
+      }
+      if (tid < DY) {
+        T v = T(0);
+        for (int q = 0; q < nw; ++q) v += part[tid * 32 + q];
+        sbs[D2 + tid] = v;
+      }
+      __syncthreads();
+      for (int r0 = w; r0 < D2; r0 += nw * CPW) {
+        T v[CPW];
+#pragma unroll
+        for (int u = 0; u < CPW; ++u) v[u] = T(0);
+        for (int c = lane; c < D2 + DY; c += 32) {
+          const T sc = sbs[c];
+#pragma unroll
+          for (int u = 0; u < CPW; ++u)
+            if (r0 + u * nw < D2) v[u] += zmat[(r0 + u * nw) * (D2 + DY) + c] * sc;
+        }
+#pragma unroll
+        for (int u = 0; u < CPW; ++u) v[u] = warp_sum(v[u]);
+        if (lane == 0) {
+#pragma unroll
+          for (int u = 0; u < CPW; ++u) {
+            const int r = r0 + u * nw;
+            if (r < D2) {
+              T zv = v[u];
+#pragma unroll
+              for (int c = 0; c < D1; ++c) zv += mc.Azx[r][c] * x[c];
+              a.zm[(long long)r * N + i] = zv;
+            }
+          }
+        }
+      }
+      __syncthreads();  // the stage and the work buffers are free for the next group
+      if (PF && !pf_issued && tid == 0 && g + gridDim.x < G)
+        stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+    } else {
+      T acc[D2 + DY];
+#pragma unroll
+      for (int c = 0; c < D2 + DY; ++c) acc[c] = T(0);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        const int j = tid + p * NT;
+        if (j < M) {
+          T beta = T(0);
+          for (int m = 0; m < L; ++m) beta += coef[m] * E[m * stride + j];
+#pragma unroll
+          for (int c = 0; c < D2; ++c) acc[c] += beta * zr[p][c];
+#pragma unroll
+          for (int q = 0; q < DY; ++q) acc[D2 + q] += beta * ep[p][q];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < D2 + DY; ++c) acc[c] = warp_sum(acc[c]);
+      const int w = tid >> 5, nw = NT >> 5;
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < D2 + DY; ++c) part[c * 32 + w] = acc[c];
+      }
+      __syncthreads();
+      if (tid < D2) {
+        const int r = tid;
+        T sb[D2 + DY];
+#pragma unroll
+        for (int c = 0; c < D2 + DY; ++c) {
+          T v = T(0);
+          for (int q = 0; q < nw; ++q) v += part[c * 32 + q];
+          sb[c] = v;
+        }
+        T v = T(0);
+#pragma unroll
+        for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * x[c];
+#pragma unroll
+        for (int c = 0; c < D2; ++c) v += mc.Azz[r][c] * sb[c];
+#pragma unroll
+        for (int q = 0; q < DY; ++q) v += mc.K[r][q] * sb[D2 + q];
+        a.zm[(long long)r * N + i] = v;
+      }
+      __syncthreads();  // the stage and the work buffers are free for the next group
+      if (PF && !pf_issued && tid == 0 && g + gridDim.x < G)
+        stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
     }
-    __syncthreads();  // the stage and the work buffers are free for the next group
   }
   if constexpr (TC) {
     tc::fence_before();

@@ -27,51 +27,6 @@ constexpr int WARPS_PER_CTA = 4;
 template <int PPL, int D2>
 constexpr int warp_min_blocks() { return PPL * D2 >= 48 ? 2 : 4; }
 
-// Philox4x32-10 with the round keys precomputed (they are kernel-uniform).
-struct RoundKeys {
-  uint32_t k0[10], k1[10];
-};
-__device__ __forceinline__ RoundKeys round_keys(Key key) {
-  RoundKeys r;
-#pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    r.k0[q] = key.k0 + (uint32_t)q * 0x9E3779B9u;
-    r.k1[q] = key.k1 + (uint32_t)q * 0xBB67AE85u;
-  }
-  return r;
-}
-__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys& rk) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1,
-                   (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r], (uint32_t)p0);
-  }
-  return c;
-}
-// Normals 4b .. 4b+n-1 (n <= 4) of the draw (t, i, purpose, sub): one Philox
-// block, Box-Muller on its first pair and, when needed, its second.
-template <typename T>
-__device__ __forceinline__ void normal_block_rk(const RoundKeys& rk, uint32_t t, uint32_t i,
-                                                uint32_t purpose, uint32_t sub, int b, int n, T (&out)[4]) {
-  const uint4 w = philox_rk(ctr(t, i, purpose, sub, (uint32_t)b), rk);
-  box_muller(w.x, w.y, out[0], out[1]);
-  if (n > 2) box_muller(w.z, w.w, out[2], out[3]);
-}
-template <int N, typename T>
-__device__ __forceinline__ void normals_rk(const RoundKeys& rk, uint32_t t, uint32_t i,
-                                           uint32_t purpose, uint32_t sub, T (&out)[N]) {
-#pragma unroll
-  for (int b = 0; b < (N + 3) / 4; ++b) {
-    T e[4];
-    normal_block_rk(rk, t, i, purpose, sub, b, N - 4 * b, e);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (4 * b + j < N) out[4 * b + j] = e[j];
-  }
-}
-
 // Per-warp shared-memory carve-up (bytes from the warp's region), on the host.
 template <typename T, int D1, int D2, int DY, bool XZ>
 inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
