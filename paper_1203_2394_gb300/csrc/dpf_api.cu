@@ -299,7 +299,7 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   x->ppt = M >= 64 ? 2 : 1;
   if (const char* e = getenv("DPF_PPT")) x->ppt = atoi(e) == 2 ? 2 : 1;
   const size_t sm = x->var->step_smem(M, L, x->hm.xz, ((M + x->ppt - 1) / x->ppt + 31) / 32 * 32);
-  if (sm > 200 * 1024) {
+  if (sm > 226 * 1024) {  // 227 KB of dynamic shared memory a block, less the static part
     delete x;
     return set_error(DPF_E_UNSUPPORTED, "dpf_create: M * L too large for the step's shared memory");
   }

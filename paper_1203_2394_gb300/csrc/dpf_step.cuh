@@ -84,7 +84,7 @@ struct StepArgs {
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
   uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
   uint32_t off_zmat, off_sb;           // wide z (d2 > 32): [A_zz K] rows and the combined sums
-  uint32_t off_proj;                   // wide z, tensor cores: [L_r^-1 H_z | H_z A_zz] columns
+  uint32_t off_proj;  // wide z, tensor cores: [L_r^-1 H_z | H_z A_zz] columns, A_zx rows, diag L_qz
   int la_only;  // the inner update already ran (learned proposal): look-ahead from the materialised state
   // optional subset of the groups: positions 0 .. *gcount - 1 of glist (device), in
   // place of every group 0 .. N - 1 (the learned proposal's per-group fallback)
@@ -180,7 +180,7 @@ inline size_t step_geometry(int M, int L, int nt, StepArgs<T>* a, bool first = f
   // wide z: the rows [A_zz(r, .) K(r, .)] for the z-mean combine, one warp a row
   const uint32_t zmat = D2 > 32 ? take(sizeof(T) * (size_t)D2 * (D2 + DY)) : 0u,
                  sbo = D2 > 32 ? take(sizeof(T) * (size_t)(D2 + DY)) : 0u,
-                 proj = (D2 > 32 && tc) ? take(sizeof(T) * (size_t)D2 * 2 * DY) : 0u;
+                 proj = (D2 > 32 && tc) ? take(sizeof(T) * (size_t)D2 * (2 * DY + D1 + 1)) : 0u;
   if (a) {
     a->tpm = tpm;
     a->rows = nt / tpm;
@@ -361,8 +361,9 @@ __device__ __forceinline__ void bscan_planes(const uint32_t (&c)[PPT], uint32_t 
 // Stage the source rows of one group (its ancestor's, or its own on the first
 // step): the inner set z (d2 rows of M), its log-weights, its x row and the
 // ancestor's look-ahead products. BULK: one thread issues bulk copies that
-// complete on the stage's mbarrier; otherwise all threads copy directly.
-template <typename T, int D1, int D2, bool BULK>
+// complete on the stage's mbarrier (WARP: issued by the calling warp, one lane a
+// copy; otherwise by thread 0); otherwise all threads copy directly.
+template <typename T, int D1, int D2, bool BULK, bool WARP = false>
 __device__ __forceinline__ void stage_group(const StepArgs<T>& a, unsigned char* st, uint64_t* bar,
                                             long long src) {
   const int M = a.M, L = a.L;
@@ -372,7 +373,24 @@ __device__ __forceinline__ void stage_group(const StepArgs<T>& a, unsigned char*
   T* slwh = (T*)(st + a.off_slwh);
   T* sxbb = (T*)(st + a.off_sxbb);
   const long long NM = a.N * (long long)M;
-  if (BULK) {
+  if (BULK && WARP) {  // one warp: lane 0 arms the barrier, then one lane a copy
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_arrive_tx(bar, a.stage_tx);
+    for (int e = lane; e < D2 + 4; e += 32) {
+      if (e < D2) {
+        bulk_load(sz + e * M, a.z_old + e * NM + src * M, (uint32_t)(M * sizeof(T)), bar);
+      } else if (e == D2) {
+        bulk_load(slq, a.lq_old + src * M, (uint32_t)(M * sizeof(T)), bar);
+      } else if (e == D2 + 1) {
+        bulk_load(sx, a.x_old + src * a.xp, (uint32_t)(a.xp * sizeof(T)), bar);
+      } else if (!a.first) {
+        if (e == D2 + 2)
+          bulk_load(slwh, a.lwh_old + src * L, (uint32_t)(L * sizeof(T)), bar);
+        else
+          bulk_load(sxbb, a.xbb_old + src * L * D1, (uint32_t)(L * D1 * sizeof(T)), bar);
+      }
+    }
+  } else if (BULK) {
     if (threadIdx.x == 0) {
       mbar_arrive_tx(bar, a.stage_tx);
 #pragma unroll
@@ -456,12 +474,16 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
       zmat[e] = c < D2 ? mc.Azz[r][c] : mc.K[r][c - D2];
     }
   }
-  if constexpr (TC && D2 > 32) {  // per coordinate r: (L_r^-1 H_z)[., r] then (H_z A_zz)[., r]
+  if constexpr (TC && D2 > 32) {
+    // per coordinate r: (L_r^-1 H_z)[., r] then (H_z A_zz)[., r]; then the rows of A_zx
+    // and the diagonal of L_qz
     T* pj = (T*)(smem_raw + a.off_proj);
     for (int e = tid; e < D2 * 2 * DY; e += NT) {
       const int r = e / (2 * DY), q = e % (2 * DY);
       pj[e] = q < DY ? mc.LrHz[q][r] : mc.HzAzz[q - DY][r];
     }
+    for (int e = tid; e < D2 * D1; e += NT) pj[D2 * 2 * DY + e] = mc.Azx[e / D1][e % D1];
+    for (int r = tid; r < D2; r += NT) pj[D2 * (2 * DY + D1) + r] = mc.Lqz[r][r];
   }
   uint32_t taddr = 0, tc_phase = 0;
   constexpr uint32_t TC_COLS = TC ? (NP * 2 <= 32 ? 32 : NP * 2 <= 64 ? 64 : NP * 2 <= 128 ? 128 : 256) : 32;
@@ -503,7 +525,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
     const long long iq = group_at(a, q);
     return a.first ? iq : (long long)a.anc[iq];
   };
-  if (PF && g < G) stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g));
+  if (PF && g < G && tid < 32) stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g));
   if (BULK && g < G) {
     const long long i0 = group_at(a, g);
     const long long src0 = a.first ? i0 : (long long)a.anc[i0];
@@ -550,8 +572,8 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
     bool pf_issued = false;  // the next group's stage copy is under way
     if (a.gskip && a.gskip[i]) {  // every thread has left the stage wait before it is re-armed
       __syncthreads();
-      if (PF && tid == 0 && g + gridDim.x < G)
-        stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+      if (PF && tid < 32 && g + gridDim.x < G)
+        stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
       continue;
     }
     T* sz = (T*)(st + a.off_sz);
@@ -786,14 +808,13 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         // A_zx x_a, the same for the whole group, and the diagonal of L_qz (part is free
         // until the z-mean)
         T* s_azx = part;
-        T* s_lqd = part + D2;
+        const T* s_lqd = (const T*)(smem_raw + a.off_proj) + D2 * (2 * DY + D1);
         if (tid < D2) {
-          const int r = tid < D2 ? tid : 0;
+          const T* azr = (const T*)(smem_raw + a.off_proj) + D2 * 2 * DY + tid * D1;
           T v = T(0);
 #pragma unroll
-          for (int c = 0; c < D1; ++c) v += mc.Azx[r][c] * xa[c];
-          s_azx[r] = v;
-          s_lqd[r] = mc.Lqz[r][r];
+          for (int c = 0; c < D1; ++c) v += azr[c] * xa[c];
+          s_azx[tid] = v;
         }
         __syncthreads();  // every gather is done: the staged z rows become the A operand
         unsigned char* zhi = (unsigned char*)sz;
@@ -843,8 +864,8 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
           tc::fence_after();
           // the MMAs have read the stage: the next group's rows may come in
-          if (tid == 0 && g + gridDim.x < G)
-            stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+          if (tid < 32 && g + gridDim.x < G)
+            stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
           pf_issued = true;
           const T* pj = (const T*)(smem_raw + a.off_proj);
           T* zn = a.z_new + i * M + j;
@@ -882,8 +903,8 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         tc_phase ^= 1u;
         if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
         tc::fence_after();
-        if (tid == 0 && g + gridDim.x < G)
-          stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+        if (tid < 32 && g + gridDim.x < G)
+          stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
         pf_issued = true;
         {
           float azz[(D2 + 15) / 16 * 16];
@@ -1264,8 +1285,8 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         }
       }
       __syncthreads();  // the stage and the work buffers are free for the next group
-      if (PF && !pf_issued && tid == 0 && g + gridDim.x < G)
-        stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+      if (PF && !pf_issued && tid < 32 && g + gridDim.x < G)
+        stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
     } else {
       T acc[D2 + DY];
 #pragma unroll
@@ -1309,8 +1330,8 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         a.zm[(long long)r * N + i] = v;
       }
       __syncthreads();  // the stage and the work buffers are free for the next group
-      if (PF && !pf_issued && tid == 0 && g + gridDim.x < G)
-        stage_group<T, D1, D2, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
+      if (PF && !pf_issued && tid < 32 && g + gridDim.x < G)
+        stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
     }
   }
   if constexpr (TC) {
