@@ -864,9 +864,9 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
           tc::fence_after();
           // the MMAs have read the stage: the next group's rows may come in
-          if (tid < 32 && g + gridDim.x < G)
+          if (PF && tid < 32 && g + gridDim.x < G)
             stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
-          pf_issued = true;
+          pf_issued = PF;
           const T* pj = (const T*)(smem_raw + a.off_proj);
           T* zn = a.z_new + i * M + j;
           T rl[DY];
@@ -903,9 +903,9 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         tc_phase ^= 1u;
         if (!ok && tid == 0) atomicOr(a.err, ERR_TIMEOUT);
         tc::fence_after();
-        if (tid < 32 && g + gridDim.x < G)
+        if (PF && tid < 32 && g + gridDim.x < G)
           stage_group<T, D1, D2, true, true>(a, stage0, &bars[0], source_of(g + gridDim.x));
-        pf_issued = true;
+        pf_issued = PF;
         {
           float azz[(D2 + 15) / 16 * 16];
           if constexpr (NP == 64) {  // the whole padded row in one load
