@@ -424,6 +424,7 @@ constexpr int TC_SPIN = 1 << 22;  // bounded wait for the tensor-core MMAs of on
 template <typename T, int D1, int D2, int DY, bool XZ, int PPT, bool BULK, bool TC>
 __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const StepArgs<T>& a) {
   static_assert(!TC || (sizeof(T) == 4 && PPT == 1 && !BULK && D2 % 8 == 0), "tensor-core step");
+  static_assert(!TC || D2 <= 32 || DY % 4 == 0, "vector loads of the wide projections");
   // one stage filled by bulk copies issued as soon as the stage is free (tensor-core
   // step: right after the MMAs that read it), so the next group's rows arrive during
   // the rest of this group
@@ -872,23 +873,49 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           T rl[DY];
 #pragma unroll
           for (int q = 0; q < DY; ++q) rl[q] = yh[q];
-#pragma unroll 2
-          for (int cb = 0; cb < D2 / 4; ++cb) {
-            float a4[4];
-            tc::ld4(ta + (uint32_t)(4 * cb), a4);
-            T e[4];
-            normal_block_rk(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, cb, 4, e);
+#pragma unroll 1
+          for (int cb = 0; cb < D2 / 8; ++cb) {  // eight coordinates: one TMEM load, two noise blocks
+            float a8[8];
+            tc::ld8(ta + (uint32_t)(8 * cb), a8);
+            T e[8];
+            {
+              T e0[4], e1[4];
+              normal_block_rk(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, 2 * cb, 4, e0);
+              normal_block_rk(rk, a.t - 1, (uint32_t)i, P_PROP, (uint32_t)j, 2 * cb + 1, 4, e1);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int r = 4 * cb + u;
-              const T v = ((ok ? (T)a4[u] : T(0)) + s_azx[r]) + s_lqd[r] * e[u];
+              for (int u = 0; u < 4; ++u) {
+                e[u] = e0[u];
+                e[4 + u] = e1[u];
+              }
+            }
+            const float4* az4 = reinterpret_cast<const float4*>(s_azx + 8 * cb);
+            const float4* lq4 = reinterpret_cast<const float4*>(s_lqd + 8 * cb);
+            const float4 za = az4[0], zb = az4[1], la = lq4[0], lb = lq4[1];
+            const T azv[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+            const T lqv[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int r = 8 * cb + u;
+              const T v = ((ok ? (T)a8[u] : T(0)) + azv[u]) + lqv[u] * e[u];
               zsrc[r * M + j] = v;
               zn[(long long)r * NM] = v;
-              const T* pr = pj + r * 2 * DY;
+              const float4* pr = reinterpret_cast<const float4*>(pj + r * 2 * DY);
 #pragma unroll
-              for (int q = 0; q < DY; ++q) rl[q] -= pr[q] * v;
+              for (int h = 0; h < DY / 4; ++h) {
+                const float4 l4 = pr[h];
+                rl[4 * h + 0] -= l4.x * v;
+                rl[4 * h + 1] -= l4.y * v;
+                rl[4 * h + 2] -= l4.z * v;
+                rl[4 * h + 3] -= l4.w * v;
+              }
 #pragma unroll
-              for (int q = 0; q < DY; ++q) gz[q] += pr[DY + q] * v;
+              for (int h = 0; h < DY / 4; ++h) {
+                const float4 g4 = pr[DY / 4 + h];
+                gz[4 * h + 0] += g4.x * v;
+                gz[4 * h + 1] += g4.y * v;
+                gz[4 * h + 2] += g4.z * v;
+                gz[4 * h + 3] += g4.w * v;
+              }
             }
           }
           tc::fence_before();
