@@ -84,6 +84,7 @@ struct StepArgs {
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
   uint32_t off_zlo, off_ahi, off_alo;  // tensor-core operand tiles (block kernel, TC only)
   uint32_t off_zmat, off_sb;           // wide z (d2 > 32): [A_zz K] rows and the combined sums
+  uint32_t off_zrow;  // warp step: the rows [A_zx A_zz K] for the z-mean, one copy a warp
   uint32_t off_proj;  // wide z, tensor cores: [L_r^-1 H_z | H_z A_zz] columns, A_zx rows, diag L_qz
   int la_only;  // the inner update already ran (learned proposal): look-ahead from the materialised state
   // optional subset of the groups: positions 0 .. *gcount - 1 of glist (device), in

@@ -47,7 +47,8 @@ inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
   const uint32_t cum = take(sizeof(uint32_t) * M), fs = take(XZ ? sizeof(T) * D1 * M : 0),
                  xw = take(sizeof(T) * L * D1), cw = take(sizeof(T) * L * DY),
                  xbs = take(sizeof(T) * L * D1), row = take(sizeof(T) * L * 5),
-                 part = take(sizeof(T) * 2 * 33 * L);
+                 part = take(sizeof(T) * 2 * 33 * L),
+                 zrow = take(sizeof(T) * D2 * (D1 + D2 + DY));
   const size_t warp_bytes = r16(o);
   if (a) {
     a->xp = xp;
@@ -56,7 +57,7 @@ inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
     a->off_stage = 0; a->off_sz = sz; a->off_slq = slq; a->off_sx = sx; a->off_slwh = slwh;
     a->off_sxbb = sxbb;
     a->off_cum = cum; a->off_kd = fs; a->off_xw = xw; a->off_cw = cw; a->off_xbs = xbs;
-    a->off_row = row; a->off_part = part;
+    a->off_row = row; a->off_part = part; a->off_zrow = zrow;
   }
   return warp_bytes * WARPS_PER_CTA;
 }
@@ -206,6 +207,15 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
   T* shA = shS + L;
   T* coef = shA + L;
   T* part = (T*)(ws + a.off_part);  // [2L][33] lane partials (row stride 33: no bank conflicts)
+  // the rows [A_zx A_zz K] of the model, for the z-mean (lane r reads row r: shared memory
+  // serves the lanes' different rows at once, where the constant bank would serialise them)
+  constexpr int ZW = D1 + D2 + DY;
+  T* zrow = (T*)(ws + a.off_zrow);
+  for (int e = lane; e < D2 * ZW; e += 32) {
+    const int r = e / ZW, c = e % ZW;
+    zrow[e] = c < D1 ? mc.Azx[r][c] : (c < D1 + D2 ? mc.Azz[r][c - D1] : mc.K[r][c - D1 - D2]);
+  }
+  __syncwarp();
   const T NEG = neg_inf<T>();
   const T LOG2E = (T)LOG2E_D, SQ = (T)SQ_D, LN2 = (T)LN2_D;
   const RoundKeys rk = round_keys(a.key);
@@ -788,13 +798,14 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
     for (int c = 0; c < D2 + DY; ++c) acc[c] = warp_sum(acc[c]);
     if (lane < D2) {
       const int r = lane;
+      const T* row = zrow + r * ZW;
       T v = T(0);
 #pragma unroll
-      for (int c = 0; c < D1; ++c) v += mc.Azx[r < D2 ? r : 0][c] * x[c];
+      for (int c = 0; c < D1; ++c) v += row[c] * x[c];
 #pragma unroll
-      for (int c = 0; c < D2; ++c) v += mc.Azz[r < D2 ? r : 0][c] * acc[c];
+      for (int c = 0; c < D2; ++c) v += row[D1 + c] * acc[c];
 #pragma unroll
-      for (int q = 0; q < DY; ++q) v += mc.K[r < D2 ? r : 0][q] * acc[D2 + q];
+      for (int q = 0; q < DY; ++q) v += row[D1 + D2 + q] * acc[D2 + q];
       a.zm[(long long)r * N + i] = v;
     }
     __syncwarp();
