@@ -146,19 +146,21 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(spec, N, M, L, budget_s=15.0, n_sample=8192, seed=0):
+def cpu_oracle_rate(spec, N, M, L, budget_s=15.0, n_sample=65536, max_steps=16, seed=0):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload: the
-    first steps of a filter with n_sample outer particles (same M, L and model),
-    all host cores. Returns (particle-updates/s, threads, sample description)."""
+    first steps (at most max_steps, stopping after budget_s seconds) of a filter with
+    n_sample outer particles (same M, L and model), all host cores. Returns
+    (particle-updates/s, threads, sample description)."""
     from oracle import oracle
     from paper_1203_2394_gb300 import workloads
     threads = os.cpu_count() or 1
-    _, ys = workloads.simulate(spec, 8, 0)
+    n_sample = min(n_sample, N)
+    _, ys = workloads.simulate(spec, max_steps, 0)
     o = oracle.Oracle(oracle.OracleModel.from_spec(spec), n_sample, M, L, seed, nthreads=threads)
     x, z, lq = o.init()
     t0 = time.perf_counter()
     steps = 0
-    while steps < 8:
+    while steps < max_steps:
         r = o.step(steps + 1, ys[steps], x, z, lq)
         x, z, lq = r["x"], r["z"], r["lq"]
         steps += 1
