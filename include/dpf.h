@@ -205,6 +205,12 @@ dpf_status dpf_tc_matmul(const void* A, const void* B, float* D, int32_t M, int3
  * normalised W), the step counter t, and the last step's log p(y_t | y_1..t-1). */
 dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ_step);
 
+/* Inner diagnostics of the newest materialised state (the state of step t-1 after
+ * step t, see dpf_read): each group's inner effective sample size
+ * (sum_j W_j)^2 / sum_j W_j^2 with W = exp(lq), in [1, M]; their minimum and mean
+ * over the N groups (host doubles). Synchronises the stream. */
+dpf_status dpf_diag_inner(dpf_ctx* ctx, double* ess_min, double* ess_mean);
+
 /*
  * Read an internal device array into host memory (tests and checkpoints).
  * `which` names the array; `bytes` must equal its size exactly:

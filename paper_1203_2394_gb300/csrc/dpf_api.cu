@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "dpf_common.cuh"
 #include "dpf_internal.h"
 
 namespace dpf {
@@ -457,6 +458,78 @@ dpf_status dpf_diag(dpf_ctx* x, double* ess, int64_t* step, double* logz_step) {
   if (ess) *ess = h[2];
   if (step) *step = x->t;
   if (logz_step) *logz_step = h[1];
+  return DPF_OK;
+}
+
+}  // extern "C"
+
+// Inner effective sample size of each group of the materialised state,
+// (sum_j W_j)^2 / sum_j W_j^2 with W = exp(lq), one warp a group; the sum over the
+// groups and their minimum (positive doubles order as their bit patterns) accumulate
+// in acc[0] and acc[1].
+template <typename T>
+__global__ void inner_ess_kernel(const T* __restrict__ lq, long long N, int M, double* acc) {
+  __shared__ double s_sum[8];
+  __shared__ unsigned long long s_min[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+  double ess = 0.0;
+  unsigned long long key = ~0ull;
+  if (i < N) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = lane; k < M; k += 32) {
+      const double v = exp((double)lq[i * M + k]);
+      s1 += v;
+      s2 += v * v;
+    }
+    s1 = dpf::warp_sum(s1);
+    s2 = dpf::warp_sum(s2);
+    ess = s2 > 0.0 ? s1 * s1 / s2 : 0.0;
+    key = (unsigned long long)__double_as_longlong(ess);
+  }
+  if (lane == 0) {
+    s_sum[w] = ess;
+    s_min[w] = key;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long m = ~0ull;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      t += s_sum[q];
+      m = s_min[q] < m ? s_min[q] : m;
+    }
+    atomicAdd(&acc[0], t);
+    atomicMin(reinterpret_cast<unsigned long long*>(&acc[1]), m);
+  }
+}
+
+extern "C" {
+
+dpf_status dpf_diag_inner(dpf_ctx* x, double* ess_min, double* ess_mean) {
+  clear_error();
+  if (!x || !ess_min || !ess_mean) return set_error(DPF_E_INVALID, "dpf_diag_inner: null argument");
+  if (!x->diag_inner) {
+    dpf_status st = dalloc(*x, x->diag_inner, sizeof(double) * 2);
+    if (st) return st;
+  }
+  const long long t = x->t;
+  const int mat = t >= 2 ? (int)((t - 1) % 2) : 0;
+  const double init[2] = {0.0, __builtin_bit_cast(double, ~0ull)};
+  cudaError_t e = cudaMemcpyAsync(x->diag_inner, init, sizeof(init), cudaMemcpyHostToDevice, x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_diag_inner");
+  const unsigned blocks = (unsigned)((x->N + 7) / 8);
+  if (x->prec == DPF_F64)
+    inner_ess_kernel<double><<<blocks, 256, 0, x->stream>>>((const double*)x->lq[mat], x->N, x->M, x->diag_inner);
+  else
+    inner_ess_kernel<float><<<blocks, 256, 0, x->stream>>>((const float*)x->lq[mat], x->N, x->M, x->diag_inner);
+  double h[2];
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, x->diag_inner, sizeof(h), cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_error(e, "dpf_diag_inner");
+  *ess_mean = h[0] / (double)x->N;
+  *ess_min = h[1];
   return DPF_OK;
 }
 

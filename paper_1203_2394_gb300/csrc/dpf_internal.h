@@ -145,6 +145,7 @@ struct dpf_ctx {
   // small device block: reduction partials, statistics, counters, error word
   void* small = nullptr;
   double* stats = nullptr;          // [logZ_total, logZ_step, ess, s1, mean[d]]
+  double* diag_inner = nullptr;     // [sum of the groups' inner ESS, their minimum (as bits)]
   void* lwmax_t = nullptr;          // the largest log-weight of the step, as T
   unsigned long long* lwmax_key = nullptr;
   unsigned long long* Csum = nullptr;

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("dpf_tc_matmul", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _P]),
     ("dpf_check_bounded_wait", ctypes.c_int, [_P]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
+    ("dpf_diag_inner", ctypes.c_int, [_P, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_proposal_create", ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _P, _P]),
     ("dpf_proposal_create_amortised", ctypes.c_int, [_I32, _I32, _I32, _I32, _P, _P, _P]),
@@ -210,6 +211,12 @@ class Filter:
         "afeat": lambda s: (s.N, 2 * s.d1 + s.dy + 2 * s.d2),
         "ahead": lambda s: (s.N, 2 * s.d2),
     }
+
+    def diag_inner(self):
+        """Minimum and mean over the groups of the inner effective sample size."""
+        lo = ctypes.c_double(); mean = ctypes.c_double()
+        check(self._lib.dpf_diag_inner(self.h, ctypes.byref(lo), ctypes.byref(mean)))
+        return dict(ess_inner_min=lo.value, ess_inner_mean=mean.value)
 
     def read(self, which: str) -> np.ndarray:
         shape = self._SHAPES[which](self)
