@@ -359,7 +359,8 @@ def run_batched(args):
         d1s, Ns, Ms = d1s[:F], Ns[:F], Ms[:F]
     specs = [workloads.make_model("lg16", 1000 + f, d1=d1s[f]) for f in range(F)]
     models = [dpf.Model.from_spec(sp, dpf.DPF_F32) for sp in specs]
-    ys = np.stack([workloads.simulate(sp, T + args.warmup, 5 + f)[1] for f, sp in enumerate(specs)],
+    # enough observations for the timed run and for the subset comparison below (12 steps)
+    ys = np.stack([workloads.simulate(sp, max(T + args.warmup, 12), 5 + f)[1] for f, sp in enumerate(specs)],
                   axis=1).astype(np.float32)
     yd = torch.tensor(ys, device="cuda")
     stream = torch.cuda.Stream()
@@ -423,6 +424,13 @@ def run_batched(args):
     ms_o = time_batch(bo)
     bo.close()
     upd_sub = sum(Ns[f] * Ms[f] for f in sub) * steps_sub
+    # roofline of the whole step (every launch of the graph): the filters' algorithmic
+    # bytes against the step time
+    bytes_step = sum(b_alg(d1s[f], 16 - d1s[f], Ms[f], 4) * Ns[f] * Ms[f] for f in range(F))
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_step / (ms / T / 1e3) / 1e9
+    n_classes = len(report.get("classes", [])) if isinstance(report, dict) else 0
+    n_variants = len(set(d1s))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": T,
         "warmup": args.warmup, "ms_per_step": ms / T, "higher_is_better": True, "scaling": "weak",
@@ -431,6 +439,12 @@ def run_batched(args):
                                f"N~U[1024,65536], M in {{16..256}}, L={L}), one graph per run",
                    "filters": F, "share_of_512": F / 512, "particles_per_step": upd,
                    "l2": "state far larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "whole batched step (graph)",
+                     "bytes_per_step": bytes_step,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s"},
+        "gpu_launches": T * (n_classes + n_variants + 1) if n_classes else None,
         "autotune": report, "autotune_s": tune_s,
         "vs_one_by_one": {"filters": S, "steps": steps_sub, "batched_updates_per_s": upd_sub / (ms_b / 1e3),
                           "one_by_one_updates_per_s": upd_sub / (ms_s / 1e3), "speedup": ms_s / ms_b,
