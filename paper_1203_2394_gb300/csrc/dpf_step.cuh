@@ -277,7 +277,7 @@ __device__ __forceinline__ void init_body(const MC<T, D1, D2, DY>& mc, T* z, T* 
   for (int r = 0; r < D1; ++r) {
     T v = mc.m0x[r];
 #pragma unroll
-    for (int c = 0; c <= r; ++c) v += mc.Lp0x[r][c] * e1[c];
+    for (int c = 0; c < D1; ++c) if (c <= r) v += mc.Lp0x[r][c] * e1[c];
     xi[r] = v;
   }
   T e2[D2];
@@ -288,7 +288,7 @@ __device__ __forceinline__ void init_body(const MC<T, D1, D2, DY>& mc, T* z, T* 
 #pragma unroll
     for (int c = 0; c < D1; ++c) v += mc.G0[r][c] * (xi[c] - mc.m0x[c]);
 #pragma unroll
-    for (int c = 0; c <= r; ++c) v += mc.Lp0c[r][c] * e2[c];
+    for (int c = 0; c < D2; ++c) if (c <= r) v += mc.Lp0c[r][c] * e2[c];
     z[((long long)r * N + i) * M + j] = v;
   }
   lq[i * M + j] = -log_t((T)M);
@@ -676,7 +676,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         for (int r = 0; r < D1; ++r) {
           T v = T(0);
 #pragma unroll
-          for (int c = 0; c <= r; ++c) v += mc.LqxInv[r][c] * (x[c] - mxa[c]);
+          for (int c = 0; c < D1; ++c) if (c <= r) v += mc.LqxInv[r][c] * (x[c] - mxa[c]);
           wres[r] = v;
         }
       }
@@ -734,7 +734,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         for (int q = 0; q < DY; ++q) {
           T v = T(0);
 #pragma unroll
-          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+          for (int c = 0; c < DY; ++c) if (c <= q) v += mc.LrInv[q][c] * res[c];
           yh[q] = v;
         }
       }
@@ -766,7 +766,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
                   zr[p][r] += mc.Lqz[r][r] * eps[r];
                 } else {
 #pragma unroll
-                  for (int c = 0; c <= r; ++c) zr[p][r] += mc.Lqz[r][c] * eps[c];
+                  for (int c = 0; c < D2; ++c) if (c <= r) zr[p][r] += mc.Lqz[r][c] * eps[c];
                 }
               }
             } else {
@@ -782,7 +782,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
                   v += mc.Lqz[r][r] * eps[r];
                 } else {
 #pragma unroll
-                  for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+                  for (int c = 0; c < D2; ++c) if (c <= r) v += mc.Lqz[r][c] * eps[c];
                 }
                 zr[p][r] = v;
               }
@@ -948,7 +948,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           for (int r = 0; r < D2; ++r) {
             T v = (ok ? (T)azz[r] : T(0)) + s_azx[r];
 #pragma unroll
-            for (int c = 0; c <= r; ++c) v += mc.Lqz[r][c] * eps[c];
+            for (int c = 0; c < D2; ++c) if (c <= r) v += mc.Lqz[r][c] * eps[c];
             zr[0][r] = v;
           }
         }
@@ -1006,7 +1006,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         for (int q = 0; q < DY; ++q) {
           T e = T(0);
 #pragma unroll
-          for (int c = 0; c <= q; ++c) e += mc.Ls[q][c] * e2[c];
+          for (int c = 0; c < DY; ++c) if (c <= q) e += mc.Ls[q][c] * e2[c];
           ep[p][q] = e;
           T v = e;
 #pragma unroll
@@ -1023,7 +1023,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         for (int q = 0; q < DY; ++q) {
           T v = T(0);
 #pragma unroll
-          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * g_[c];
+          for (int c = 0; c < DY; ++c) if (c <= q) v += mc.LrInv[q][c] * g_[c];
           rec[1 + q] = SQ * v;
         }
         if (XZ) {
@@ -1066,7 +1066,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
       for (int r = 0; r < D1; ++r) {
         T v = mux[r];
 #pragma unroll
-        for (int c = 0; c <= r; ++c) v += mc.Lqx[r][c] * xwm[c];
+        for (int c = 0; c < D1; ++c) if (c <= r) v += mc.Lqx[r][c] * xwm[c];
         xb[r] = v;
         a.xbb_new[((long long)i * L + m) * D1 + r] = v;
         xbs[m * D1 + r] = v;
@@ -1080,7 +1080,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
       for (int q = 0; q < DY; ++q) {
         T v = T(0);
 #pragma unroll
-        for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+        for (int c = 0; c < DY; ++c) if (c <= q) v += mc.LrInv[q][c] * res[c];
         cw[m * DY + q] = SQ * v;
       }
     }

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstring>
+#include <type_traits>
 
 #include "dpf_step.cuh"
 
@@ -79,21 +80,44 @@ __device__ __forceinline__ int search_cum_fixed(const uint32_t* cum, int n, uint
   return b;
 }
 
-// Vector moves of P consecutive elements (16-byte chunks where possible).
+// Vector moves of P consecutive elements (16-byte chunks where possible). float and
+// double move as float4 / float2 / double2; 32-bit integers as uint4 / uint2 (the casts
+// between uint32_t and int32_t keep the bits).
 template <typename T, int P>
 __device__ __forceinline__ void vld(const T* src, T (&out)[P]) {
-  constexpr int B = (int)sizeof(T) * P;
-  if constexpr (B % 16 == 0) {
+  if constexpr (std::is_same<T, float>::value && P % 4 == 0) {
 #pragma unroll
-    for (int q = 0; q < B / 16; ++q) {
-      const uint4 v = reinterpret_cast<const uint4*>(src)[q];
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      memcpy(reinterpret_cast<char*>(out) + 16 * q, w, 16);
+    for (int q = 0; q < P / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(src)[q];
+      out[4 * q + 0] = v.x;
+      out[4 * q + 1] = v.y;
+      out[4 * q + 2] = v.z;
+      out[4 * q + 3] = v.w;
     }
-  } else if constexpr (B == 8) {
+  } else if constexpr (std::is_same<T, float>::value && P == 2) {
+    const float2 v = *reinterpret_cast<const float2*>(src);
+    out[0] = v.x;
+    out[1] = v.y;
+  } else if constexpr (std::is_same<T, double>::value && P % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) {
+      const double2 v = reinterpret_cast<const double2*>(src)[q];
+      out[2 * q + 0] = v.x;
+      out[2 * q + 1] = v.y;
+    }
+  } else if constexpr (std::is_integral<T>::value && sizeof(T) == 4 && P % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+      const uint4 v = reinterpret_cast<const uint4*>(src)[q];
+      out[4 * q + 0] = (T)v.x;
+      out[4 * q + 1] = (T)v.y;
+      out[4 * q + 2] = (T)v.z;
+      out[4 * q + 3] = (T)v.w;
+    }
+  } else if constexpr (std::is_integral<T>::value && sizeof(T) == 4 && P == 2) {
     const uint2 v = *reinterpret_cast<const uint2*>(src);
-    const uint32_t w[2] = {v.x, v.y};
-    memcpy(out, w, 8);
+    out[0] = (T)v.x;
+    out[1] = (T)v.y;
   } else {
 #pragma unroll
     for (int q = 0; q < P; ++q) out[q] = src[q];
@@ -101,18 +125,22 @@ __device__ __forceinline__ void vld(const T* src, T (&out)[P]) {
 }
 template <typename T, int P>
 __device__ __forceinline__ void vst(T* dst, const T (&in)[P]) {
-  constexpr int B = (int)sizeof(T) * P;
-  if constexpr (B % 16 == 0) {
+  if constexpr (std::is_same<T, float>::value && P % 4 == 0) {
 #pragma unroll
-    for (int q = 0; q < B / 16; ++q) {
-      uint32_t w[4];
-      memcpy(w, reinterpret_cast<const char*>(in) + 16 * q, 16);
-      reinterpret_cast<uint4*>(dst)[q] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-  } else if constexpr (B == 8) {
-    uint32_t w[2];
-    memcpy(w, in, 8);
-    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+    for (int q = 0; q < P / 4; ++q)
+      reinterpret_cast<float4*>(dst)[q] = make_float4(in[4 * q], in[4 * q + 1], in[4 * q + 2], in[4 * q + 3]);
+  } else if constexpr (std::is_same<T, float>::value && P == 2) {
+    *reinterpret_cast<float2*>(dst) = make_float2(in[0], in[1]);
+  } else if constexpr (std::is_same<T, double>::value && P % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(in[2 * q], in[2 * q + 1]);
+  } else if constexpr (std::is_integral<T>::value && sizeof(T) == 4 && P % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q)
+      reinterpret_cast<uint4*>(dst)[q] = make_uint4((uint32_t)in[4 * q], (uint32_t)in[4 * q + 1],
+                                                    (uint32_t)in[4 * q + 2], (uint32_t)in[4 * q + 3]);
+  } else if constexpr (std::is_integral<T>::value && sizeof(T) == 4 && P == 2) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)in[0], (uint32_t)in[1]);
   } else {
 #pragma unroll
     for (int q = 0; q < P; ++q) dst[q] = in[q];
@@ -345,7 +373,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
           for (int r = 0; r < D1; ++r) {
             T v = T(0);
 #pragma unroll
-            for (int c = 0; c <= r; ++c) v += mc.LqxInv[r][c] * (x[c] - mxa[c]);
+            for (int c = 0; c < D1; ++c) if (c <= r) v += mc.LqxInv[r][c] * (x[c] - mxa[c]);
             wres[r] = v;
           }
           T res[D1][PPL];
@@ -410,7 +438,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int q = 0; q < DY; ++q) {
           T v = T(0);
 #pragma unroll
-          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+          for (int c = 0; c < DY; ++c) if (c <= q) v += mc.LrInv[q][c] * res[c];
           yh[q] = v;
         }
       }
@@ -463,8 +491,11 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
             if (mc.diag_qz) {
               axpy<T, PPL>(mc.Lqz[c][c], e4[j], zr[c]);
             } else {
+              // constant bounds (not r = c ..) so that the loop unrolls before c is known
+              // and zr stays in registers
 #pragma unroll
-              for (int r = c; r < D2; ++r) axpy<T, PPL>(mc.Lqz[r][c], e4[j], zr[r]);
+              for (int r = 0; r < D2; ++r)
+                if (r >= c) axpy<T, PPL>(mc.Lqz[r][c], e4[j], zr[r]);
             }
           }
         }
@@ -541,7 +572,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 #pragma unroll
         for (int p = 0; p < PPL; ++p) ep[q][p] = T(0);
 #pragma unroll
-        for (int c = 0; c <= q; ++c) axpy<T, PPL>(mc.Ls[q][c], e2[c], ep[q]);
+        for (int c = 0; c < DY; ++c) if (c <= q) axpy<T, PPL>(mc.Ls[q][c], e2[c], ep[q]);
 #pragma unroll
         for (int p = 0; p < PPL; ++p) gg[q][p] = ep[q][p] + hx;
 #pragma unroll
@@ -552,7 +583,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 #pragma unroll
         for (int p = 0; p < PPL; ++p) ngk[q][p] = T(0);
 #pragma unroll
-        for (int c = 0; c <= q; ++c) axpy<T, PPL>(-SQ * mc.LrInv[q][c], gg[c], ngk[q]);
+        for (int c = 0; c < DY; ++c) if (c <= q) axpy<T, PPL>(-SQ * mc.LrInv[q][c], gg[c], ngk[q]);
       }
       if (XZ) {
 #pragma unroll
@@ -606,7 +637,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int r = 0; r < D1; ++r) {
           T v = mux[r];
 #pragma unroll
-          for (int c = 0; c <= r; ++c) v += mc.Lqx[r][c] * xwm[c];
+          for (int c = 0; c < D1; ++c) if (c <= r) v += mc.Lqx[r][c] * xwm[c];
           xb[r] = v;
           a.xbb_new[((long long)i * L + m) * D1 + r] = v;
           xbs[m * D1 + r] = v;
@@ -620,7 +651,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int q = 0; q < DY; ++q) {
           T v = T(0);
 #pragma unroll
-          for (int c = 0; c <= q; ++c) v += mc.LrInv[q][c] * res[c];
+          for (int c = 0; c < DY; ++c) if (c <= q) v += mc.LrInv[q][c] * res[c];
           cw[m * DY + q] = SQ * v;
         }
       }
