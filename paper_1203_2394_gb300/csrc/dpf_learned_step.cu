@@ -6,8 +6,8 @@
 //
 // Per tile, one thread per row: layer 1 (K = 16 padded inputs) and the head
 // (N = 32 padded outputs) have their weights resident in shared memory; the two
-// 256 x 256 layers stream their weights through a three-stage ring of 32 KB
-// chunks (64 K-columns each) copied by cp.async.bulk from a packed copy in global
+// 256 x 256 layers stream their weights through a three-stage ring of 16 KB
+// chunks (32 K-columns each) copied by cp.async.bulk from a packed copy in global
 // memory, so the copy of the next chunks overlaps the MMAs of the current ones.
 // Every hidden layer's accumulator (128 x 256 FP32, TMEM columns 0..255) is read
 // back row by row, biased, passed through ReLU, rounded to BF16 and written as
