@@ -448,14 +448,36 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
       {
         const uint64_t scale = (uint64_t)M << 16;
         const uint64_t u16 = uin >> 16;
-        int b = act ? search_cum_fixed(cum, M, scale, (((uint64_t)k0 << 16) + u16) * C, a.log2M) : 0;
-#pragma unroll
-        for (int p = 0; p < PPL; ++p) {
-          if (p > 0 && act) {
-            const uint64_t rhs = (((uint64_t)(k0 + p) << 16) + u16) * C;
-            while ((uint64_t)cum[b] * scale <= rhs) ++b;
+        if ((M & (M - 1)) == 0) {
+          // M a power of two: cum * 2^sh <= rhs exactly when cum <= rhs >> sh (a 32-bit
+          // bound: rhs < M 2^16 C and C < 2^31), so the search compares 32-bit words
+          const int sh = a.log2M + 16;
+          int b = 0;
+          if (act) {
+            const uint32_t thr = (uint32_t)(((((uint64_t)k0 << 16) + u16) * C) >> sh);
+            for (int st = a.log2M - 1; st >= 0; --st) {
+              const int nb = b + (1 << st);
+              if (nb <= M && cum[nb - 1] <= thr) b = nb;
+            }
           }
-          bidx[p] = b;
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) {
+            if (p > 0 && act) {
+              const uint32_t thr = (uint32_t)(((((uint64_t)(k0 + p) << 16) + u16) * C) >> sh);
+              while (cum[b] <= thr) ++b;
+            }
+            bidx[p] = b;
+          }
+        } else {
+          int b = act ? search_cum_fixed(cum, M, scale, (((uint64_t)k0 << 16) + u16) * C, a.log2M) : 0;
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) {
+            if (p > 0 && act) {
+              const uint64_t rhs = (((uint64_t)(k0 + p) << 16) + u16) * C;
+              while ((uint64_t)cum[b] * scale <= rhs) ++b;
+            }
+            bidx[p] = b;
+          }
         }
       }
       if (a.dbg_b && act) vst<int, PPL>(a.dbg_b + i * M + k0, bidx);
