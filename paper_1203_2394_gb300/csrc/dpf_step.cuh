@@ -874,7 +874,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
           T rl[DY];
 #pragma unroll
           for (int q = 0; q < DY; ++q) rl[q] = yh[q];
-#pragma unroll 1
+#pragma unroll 2
           for (int cb = 0; cb < D2 / 8; ++cb) {  // eight coordinates: one TMEM load, two noise blocks
             float a8[8];
             tc::ld8(ta + (uint32_t)(8 * cb), a8);
