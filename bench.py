@@ -146,14 +146,14 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(spec, N, M, L, budget_s=15.0, n_sample=65536, max_steps=16, seed=0):
+def cpu_oracle_rate(spec, N, M, L, budget_s=15.0, n_sample=65536, max_steps=16, seed=0, threads=None):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload: the
     first steps (at most max_steps, stopping after budget_s seconds) of a filter with
     n_sample outer particles (same M, L and model), all host cores. Returns
     (particle-updates/s, threads, sample description)."""
     from oracle import oracle
     from paper_1203_2394_gb300 import workloads
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     n_sample = min(n_sample, N)
     _, ys = workloads.simulate(spec, max_steps, 0)
     o = oracle.Oracle(oracle.OracleModel.from_spec(spec), n_sample, M, L, seed, nthreads=threads)
@@ -306,7 +306,9 @@ def run(args):
     cpu = None
     if ws == 1 and not args.no_cpu:
         r, threads, sample = cpu_oracle_rate(spec, N, M, L)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        r1, _, sample1 = cpu_oracle_rate(spec, N, M, L, budget_s=3.0, n_sample=1024, max_steps=4, threads=1)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": r1, "unit": UNIT, "sample": sample1}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
@@ -321,6 +323,7 @@ def run(args):
                      "bytes_per_update": per, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spec.dy * 4,
                 "d2h_bytes_per_step": (4 + spec.d) * 8 + 4},
+        "lookahead_evaluations_per_s": value * L,  # the N M L look-ahead pairs of every step
         "gpu_launches": 3 * K,
         "clocks": clk,
         "cpu_baseline": cpu,
