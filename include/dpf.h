@@ -205,6 +205,22 @@ dpf_status dpf_tc_matmul(const void* A, const void* B, float* D, int32_t M, int3
  * normalised W), the step counter t, and the last step's log p(y_t | y_1..t-1). */
 dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ_step);
 
+/*
+ * The bootstrap particle filter over the full state s = (x, z) (the baseline of the
+ * paper's Section 4.1): N particles, each propagated from its resampled ancestor by
+ * the model's transition, x_t = mu_x(x_{t-1}) + A_xz z_{t-1} + chol(Q_x) e_x and
+ * z_t = A_zx x_{t-1} + A_zz z_{t-1} + chol(Q_z) e_z (e_x, e_z the Philox normals of
+ * purposes 12 and 13 at counter (t, i, purpose, 0)), weighted by log N(y_t; h(s_t), R),
+ * then resampled by the global systematic rule of dpf_resample. The initial particles
+ * are the filter's initial draw with M = 1. Same model descriptor and variants as
+ * dpf_create; the context then takes dpf_step, dpf_step_async, dpf_diag (ESS of the
+ * weights), dpf_read ("x", "z": the particles of step t; "lw": their log-weights; "anc")
+ * and dpf_destroy. out_mean of dpf_step is the weighted mean of step t, out_logZ the
+ * cumulative log-evidence.
+ */
+dpf_status dpf_create_pf(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, uint64_t seed,
+                         void* stream, dpf_ctx** out);
+
 /* Inner diagnostics of the newest materialised state (the state of step t-1 after
  * step t, see dpf_read): each group's inner effective sample size
  * (sum_j W_j)^2 / sum_j W_j^2 with W = exp(lq), in [1, M]; their minimum and mean

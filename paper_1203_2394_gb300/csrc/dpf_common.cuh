@@ -16,7 +16,8 @@ constexpr unsigned FULL = 0xffffffffu;
 enum Purpose : uint32_t {
   P_INIT_X = 1, P_INIT_Z = 2, P_LA_J = 3, P_LA_X = 4, P_LA_Z = 5,
   P_OUTER = 6, P_SEL = 7, P_INNER = 8, P_PROP = 9,
-  P_LCOMP = 10  // mixture-component draw of the learned inner proposal
+  P_LCOMP = 10,  // mixture-component draw of the learned inner proposal
+  P_PF_X = 12, P_PF_Z = 13  // the bootstrap particle filter's x and z transition noise
 };
 
 // Device error word bits (latched with atomicOr, read by the host after a sync).

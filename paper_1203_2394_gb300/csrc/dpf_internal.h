@@ -88,6 +88,7 @@ struct Variant {
   dpf_status (*init)(Ctx&);
   dpf_status (*step)(Ctx&, int profile_slot);
   dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out, cudaStream_t s);
+  dpf_status (*pf_step)(Ctx&) = nullptr;  // the bootstrap particle filter's step (null: none)
   // the outer stage in parts, for many filters at once
   void (*outer_args)(Ctx&, double* mean_out, double* logz_out, void* oargs, void* gargs);
   dpf_status (*outer_batch)(const void* oargs, const int* bstart, int nblocks, int F, cudaStream_t s);
@@ -170,6 +171,7 @@ struct dpf_ctx {
   bool tensor_cores = true;  // tensor-core propagation where the variant has one
   dpf_proposal* proposal = nullptr;  // learned inner proposal (null: the prior)
   bool la_only = false;      // the next step kernel runs the look-ahead only
+  bool pf = false;           // a bootstrap particle filter (dpf_create_pf), not the LA-DPF
   // the learned proposal's per-group fallback to the plain inner update
   double fb_frac = 0.25;          // a group falls back when its inner ESS < fb_frac * M (0: never)
   int32_t* fb_flag = nullptr;     // [N] 1 where the last learned inner update fell back

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dpf_pf.cuh"
 #include "dpf_step_warp.cuh"
 
 namespace dpf {
@@ -322,8 +323,41 @@ struct VariantImpl {
     return cuda_error(cudaGetLastError(), "batched outer resample launch");
   }
 
+  // The bootstrap particle filter's step t (M = 1: the state slots hold one particle a
+  // group): propagation from the ancestors and the likelihood weights.
+  static dpf_status pf_step(Ctx& x) {
+    const long long t = x.t + 1;
+    PFArgs<T> a{};
+    const int so = (int)((t + 1) % 2), sn = (int)(t % 2);  // slot of step t-1 (t = 1: 0), of step t
+    a.x_old = (const T*)x.x[so];
+    a.z_old = (const T*)x.z[so];
+    a.x_new = (T*)x.x[sn];
+    a.z_new = (T*)x.z[sn];
+    a.lw = (T*)x.lw;
+    a.xm = (T*)x.xm;
+    a.zm = (T*)x.zm;
+    a.anc = x.anc;
+    a.y = (const T*)x.yb + (t % 2) * x.dy;
+    a.lwmax_key = x.lwmax_key;
+    a.Csum = x.Csum;
+    a.N = x.N;
+    a.xp = x.xp;
+    a.t = (uint32_t)t;
+    a.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    const HostModel& h = x.hm;
+    a.gcos = h.growth ? (T)(h.gc * std::cos(h.gw * (double)(t - 1))) : T(0);
+    a.first = t == 1 ? 1 : 0;
+    const unsigned blocks = (unsigned)std::min<long long>((x.N + 255) / 256, 152 * 8);
+    if (use_xz(x))
+      pf_kernel<T, D1, D2, DY, true><<<blocks, 256, 0, x.stream>>>(cst(x), a);
+    else
+      pf_kernel<T, D1, D2, DY, false><<<blocks, 256, 0, x.stream>>>(cst(x), a);
+    return cuda_error(cudaGetLastError(), "particle filter step launch");
+  }
+
   static Variant make(int prec) {
     Variant v;
+    v.pf_step = &pf_step;
     v.xpad = &xpad;
     v.prec = prec;
     v.d1 = D1;
