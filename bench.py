@@ -561,6 +561,69 @@ def run_highdim(args):
     return 0
 
 
+def run_compare(args):
+    """The paper's comparison (Section 4.1): the LA-DPF (N = 65536, M = 128, L = 16) against
+    the bootstrap particle filter with N (M + 1) = 8,454,144 particles (the paper sizes the
+    PF so), on the growth workload in FP32: time per step (device observations, CUDA events
+    over the timed steps) and RMSE of the filtered mean against the true state, per block."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    spec = workloads.make_model(WORKLOAD, 0)
+    sz = spec.sizes
+    N, M, L = sz["N"], sz["M"], sz["L"]
+    K, W = args.steps, args.warmup
+    T = W + K
+    s_true, ys = workloads.simulate(spec, T, 0)
+    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    yd = torch.tensor(ys.astype(np.float32), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(f, name):
+        means = torch.zeros((T, spec.d), dtype=torch.float64, device="cuda")
+        for k in range(W):
+            f.step_device(yd[k].data_ptr(), means[k].data_ptr())
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(W, T):
+            f.step_device(yd[k].data_ptr(), means[k].data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f.sync()
+        m = means.cpu().numpy()
+        err = m[W:] - s_true[W + 1:T + 1]  # the estimates of the timed steps against the truth
+        d1 = spec.d1
+        return {"ms_per_step": e0.elapsed_time(e1) / K,
+                "rmse_x": float(np.sqrt(np.mean(err[:, :d1] ** 2))),
+                "rmse_z": float(np.sqrt(np.mean(err[:, d1:] ** 2)))}
+
+    la = dpf.Filter(model, spec.d1, spec.d2, N, M, L, seed=0)
+    r_la = timed(la, "ladpf")
+    la.close()
+    Np = N * (M + 1)
+    pfl = dpf.ParticleFilter(model, spec.d1, spec.d2, Np, seed=0)
+    r_pf = timed(pfl, "pf")
+    pfl.close()
+    r_la["particle_updates_per_s"] = N * M / (r_la["ms_per_step"] / 1e3)
+    r_pf["particles"] = Np
+    r_pf["particle_updates_per_s"] = Np / (r_pf["ms_per_step"] / 1e3)
+    line = {
+        "metric": METRIC, "value": r_la["particle_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": r_la["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"comparison on {WORKLOAD}: LA-DPF N={N}, M={M}, L={L} against the "
+                               f"bootstrap PF with N(M+1)={Np} particles, FP32; RMSE over the {K} timed steps"},
+        "ladpf": r_la, "pf": r_pf,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args):
     """The learned-proposal workload: the lg4 model in FP32 with N = 262144 outer and
     M = 64 inner particles. A proposal (MLP 3 x 256 ReLU, 4-component mixture head, BF16
@@ -722,9 +785,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned"],
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare"],
                     help="the headline single-filter workload, the many-filter one, the d2 = 56 one, "
-                         "or the learned-proposal one")
+                         "the learned-proposal one, or the LA-DPF against the bootstrap PF")
     ap.add_argument("--filters", type=int, default=None,
                     help="filters of the batched (default 512) or high-dimensional (default 64) workload")
     args = ap.parse_args(argv)
@@ -740,6 +803,8 @@ def main(argv=None):
         return run_highdim(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "compare":
+        return run_compare(args)
     return run(args)
 
 
