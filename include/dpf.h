@@ -221,6 +221,22 @@ dpf_status dpf_diag(dpf_ctx* ctx, double* ess_outer, int64_t* step, double* logZ
 dpf_status dpf_create_pf(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, uint64_t seed,
                          void* stream, dpf_ctx** out);
 
+/*
+ * The decentralized particle filter without look-ahead (Fig. dpf, the filter the LA-DPF
+ * extends), with the prior as both proposals: each call t draws x_t of every outer
+ * particle from the mixture prior of its ancestor's inner set (the component by the
+ * one-draw local systematic rule on qbar, word (t, i, 3 = LA_J, 0); the normals of
+ * (t, i, 4 = LA_X, 0)), resamples the inner set locally by qbar p(x_t | x_{t-1}, z)
+ * (word (t, i, 8 = INNER, 0)), propagates it by the z prior (normals (t, i, 9 = PROP,
+ * j)), weighs it by p(y_t | x_t, z_t) (qbar = the normalised weights), gives the outer
+ * particle log w = log mean_j p(y_t | x_t, z_t^(j)) and resamples the outer set by the
+ * global systematic rule. The initial state is the filter's initial draw. Same model
+ * descriptor, variants and M limits as dpf_create (L is not used); dpf_step's out_mean is
+ * the weighted mean of step t; dpf_read ("x", "z", "lq") gives the state of step t.
+ */
+dpf_status dpf_create_std(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, int32_t M,
+                          uint64_t seed, void* stream, dpf_ctx** out);
+
 /* Inner diagnostics of the newest materialised state (the state of step t-1 after
  * step t, see dpf_read): each group's inner effective sample size
  * (sum_j W_j)^2 / sum_j W_j^2 with W = exp(lq), in [1, M]; their minimum and mean

@@ -371,6 +371,20 @@ dpf_status dpf_create_pf(const dpf_model_desc* model, int32_t d1, int32_t d2, in
   return DPF_OK;
 }
 
+dpf_status dpf_create_std(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, int32_t M,
+                          uint64_t seed, void* stream, dpf_ctx** out) {
+  clear_error();
+  dpf_status st = dpf_create(model, d1, d2, N, M, 1, seed, stream, out);
+  if (st) return st;
+  if (!(*out)->var->std_step) {
+    dpf_destroy(*out);
+    *out = nullptr;
+    return set_error(DPF_E_UNSUPPORTED, "dpf_create_std: this (d1, d2, dy) variant has no DPF step");
+  }
+  (*out)->std_dpf = true;
+  return DPF_OK;
+}
+
 static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
   const long long t = x->t + 1;
   if (x->profiling) {
@@ -384,8 +398,8 @@ static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
     cudaEventRecord(x->pev[x->pev_used], x->stream);
   }
   dpf_status st = DPF_OK;
-  if (x->pf) {  // bootstrap particle filter: propagate and weigh, then the shared outer stages
-    st = x->var->pf_step(*x);
+  if (x->pf || x->std_dpf) {  // bootstrap PF or DPF: their step, then the shared outer stages
+    st = x->pf ? x->var->pf_step(*x) : x->var->std_step(*x);
     if (!st) st = x->var->outer(*x, mean_out, logz_out, x->stream);
     if (st) return st;
     x->t = t;
@@ -651,7 +665,7 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   const long long t = x->t;
   const int cur = (int)(t % 2);                   // look-ahead products of step t
   // newest materialised state (the particle filter's particles of step t)
-  const int mat = x->pf ? cur : (t >= 2 ? (int)((t - 1) % 2) : 0);
+  const int mat = (x->pf || x->std_dpf) ? cur : (t >= 2 ? (int)((t - 1) % 2) : 0);
   const void* src = nullptr;
   size_t need = 0;
   std::string w(which);

@@ -89,6 +89,7 @@ struct Variant {
   dpf_status (*step)(Ctx&, int profile_slot);
   dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out, cudaStream_t s);
   dpf_status (*pf_step)(Ctx&) = nullptr;  // the bootstrap particle filter's step (null: none)
+  dpf_status (*std_step)(Ctx&) = nullptr;  // the DPF without look-ahead (null: none)
   // the outer stage in parts, for many filters at once
   void (*outer_args)(Ctx&, double* mean_out, double* logz_out, void* oargs, void* gargs);
   dpf_status (*outer_batch)(const void* oargs, const int* bstart, int nblocks, int F, cudaStream_t s);
@@ -172,6 +173,7 @@ struct dpf_ctx {
   dpf_proposal* proposal = nullptr;  // learned inner proposal (null: the prior)
   bool la_only = false;      // the next step kernel runs the look-ahead only
   bool pf = false;           // a bootstrap particle filter (dpf_create_pf), not the LA-DPF
+  bool std_dpf = false;      // the DPF without look-ahead (dpf_create_std)
   // the learned proposal's per-group fallback to the plain inner update
   double fb_frac = 0.25;          // a group falls back when its inner ESS < fb_frac * M (0: never)
   int32_t* fb_flag = nullptr;     // [N] 1 where the last learned inner update fell back

@@ -1139,7 +1139,8 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
     x->proposal = nullptr;
     return DPF_OK;
   }
-  if (x->pf) return set_error(DPF_E_INVALID, "dpf_set_proposal: a particle filter has no inner proposal");
+  if (x->pf || x->std_dpf)
+    return set_error(DPF_E_INVALID, "dpf_set_proposal: the learned proposal serves the LA-DPF only");
   if (x->prec != DPF_F32 || p->d1 != x->d1 || p->d2 != x->d2 || p->dy != x->dy)
     return set_error(DPF_E_INVALID, "dpf_set_proposal: the proposal's (d1, d2, dy) and FP32 must match the filter");
   if (p->kind == 0 && (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH || p->C != kFilterComponents ||

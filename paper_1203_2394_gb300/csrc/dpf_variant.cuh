@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "dpf_pf.cuh"
+#include "dpf_std.cuh"
 #include "dpf_step_warp.cuh"
 
 namespace dpf {
@@ -355,9 +356,51 @@ struct VariantImpl {
     return cuda_error(cudaGetLastError(), "particle filter step launch");
   }
 
+  // The DPF without look-ahead, call t (one CTA a group of M inner particles).
+  static dpf_status std_step(Ctx& x) {
+    const long long t = x.t + 1;
+    StdArgs<T> a{};
+    const int so = (int)((t + 1) % 2), sn = (int)(t % 2);
+    a.x_old = (const T*)x.x[so];
+    a.z_old = (const T*)x.z[so];
+    a.lq_old = (const T*)x.lq[so];
+    a.x_new = (T*)x.x[sn];
+    a.z_new = (T*)x.z[sn];
+    a.lq_new = (T*)x.lq[sn];
+    a.lw = (T*)x.lw;
+    a.xm = (T*)x.xm;
+    a.zm = (T*)x.zm;
+    a.anc = x.anc;
+    a.y = (const T*)x.yb + (t % 2) * x.dy;
+    a.lwmax_key = x.lwmax_key;
+    a.Csum = x.Csum;
+    a.err = x.err;
+    a.N = x.N;
+    a.M = x.M;
+    a.xp = x.xp;
+    a.t = (uint32_t)t;
+    a.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    const HostModel& h = x.hm;
+    a.gcos = h.growth ? (T)(h.gc * std::cos(h.gw * (double)(t - 1))) : T(0);
+    a.scaleM = (T)std::ldexp(1.0, 31 - ceil_log2_i(x.M));
+    a.logM = (T)std::log((double)x.M);
+    a.first = t == 1 ? 1 : 0;
+    const int nt = (x.M + 31) / 32 * 32;
+    const size_t sm = sizeof(T) * (size_t)D2 * x.M + 4 * (size_t)(x.M + 1) + sizeof(T) * 32 + 4 * 64 + 16;
+    const unsigned blocks = (unsigned)std::min<long long>(x.N, 152 * 8);
+    auto k = use_xz(x) ? std_dpf_kernel<T, D1, D2, DY, true> : std_dpf_kernel<T, D1, D2, DY, false>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+    }
+    k<<<blocks, nt, sm, x.stream>>>(cst(x), a);
+    return cuda_error(cudaGetLastError(), "DPF step launch");
+  }
+
   static Variant make(int prec) {
     Variant v;
     v.pf_step = &pf_step;
+    v.std_step = &std_step;
     v.xpad = &xpad;
     v.prec = prec;
     v.d1 = D1;

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_diag_inner", ctypes.c_int, [_P, _P, _P]),
     ("dpf_create_pf", ctypes.c_int, [_P, _I32, _I32, _I64, _U64, _P, _P]),
+    ("dpf_create_std", ctypes.c_int, [_P, _I32, _I32, _I64, _I32, _U64, _P, _P]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_proposal_create", ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _P, _P]),
     ("dpf_proposal_create_amortised", ctypes.c_int, [_I32, _I32, _I32, _I32, _P, _P, _P]),
@@ -311,6 +312,22 @@ class ParticleFilter(Filter):
         h = ctypes.c_void_p()
         check(self._lib.dpf_create_pf(ctypes.byref(model.desc), self.d1, self.d2, self.N,
                                       ctypes.c_uint64(seed), _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+
+
+class StandardDPF(Filter):
+    """The decentralized particle filter without look-ahead (``dpf_create_std``): N outer
+    particles with M inner particles each."""
+
+    def __init__(self, model: Model, d1: int, d2: int, N: int, M: int, seed: int = 0, stream=None):
+        self.model = model
+        self.d1, self.d2, self.N, self.M, self.L = int(d1), int(d2), int(N), int(M), 1
+        self.d, self.dy = model.d, model.dy
+        self.dtype = np.float64 if model.precision == DPF_F64 else np.float32
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        check(self._lib.dpf_create_std(ctypes.byref(model.desc), self.d1, self.d2, self.N, self.M,
+                                       ctypes.c_uint64(seed), _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
 
 
