@@ -630,6 +630,49 @@ def run_compare(args):
     return 0
 
 
+def run_table2(args):
+    """The Gaussian approximation of the mixture prior against its Monte Carlo evaluation
+    (Section 4.2, Table 2), as the paper runs it: the DPF without look-ahead with N = 100,
+    M = 19, 100 runs, here on lg4 (x depends on z) in FP32 over 50 steps; average RMSE of the
+    filtered mean against the true state, per block, and the time of a run."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    spec = workloads.make_model("lg4", 0)
+    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    N, M, T, R = 100, 19, 50, 100
+    d1 = spec.d1
+    res = {False: [], True: []}
+    t0 = time.perf_counter()
+    for r in range(R):
+        s_true, ys = workloads.simulate(spec, T, 1000 + r)
+        for gauss in (False, True):
+            f = dpf.StandardDPF(model, d1, spec.d2, N, M, seed=r)
+            f.set_gaussian_approx(gauss)
+            means = np.array([f.step(ys[t].astype(np.float32))[0] for t in range(T)])
+            f.close()
+            err = means - s_true[1:]
+            res[gauss].append((np.sqrt(np.mean(err[:, :d1] ** 2)), np.sqrt(np.mean(err[:, d1:] ** 2))))
+    wall = time.perf_counter() - t0
+    mc, ga = np.array(res[False]), np.array(res[True])
+    line = {
+        "metric": "RMSE against the true state (mean over runs)", "value": float(ga[:, 0].mean()),
+        "unit": "state units", "n_gpus": 1, "steps": T, "warmup": 0, "ms_per_step": wall / (2 * R * T) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Gaussian against Monte Carlo evaluation of the mixture prior: DPF without "
+                               f"look-ahead, lg4, N={N}, M={M}, {R} runs of {T} steps, FP32"},
+        "gaussian": {"rmse_x": float(ga[:, 0].mean()), "rmse_z": float(ga[:, 1].mean())},
+        "monte_carlo": {"rmse_x": float(mc[:, 0].mean()), "rmse_z": float(mc[:, 1].mean())},
+        "paper_table2_model1": {"gaussian": {"rmse_x": 1.3197, "rmse_z": 1.1705},
+                                "monte_carlo": {"rmse_x": 1.3216, "rmse_z": 1.1640}},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args):
     """The learned-proposal workload: the lg4 model in FP32 with N = 262144 outer and
     M = 64 inner particles. A proposal (MLP 3 x 256 ReLU, 4-component mixture head, BF16
@@ -791,7 +834,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare"],
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare", "table2"],
                     help="the headline single-filter workload, the many-filter one, the d2 = 56 one, "
                          "the learned-proposal one, or the LA-DPF against the bootstrap PF")
     ap.add_argument("--filters", type=int, default=None,
@@ -811,6 +854,8 @@ def main(argv=None):
         return run_learned(args)
     if args.workload == "compare":
         return run_compare(args)
+    if args.workload == "table2":
+        return run_table2(args)
     return run(args)
 
 

@@ -237,6 +237,16 @@ dpf_status dpf_create_pf(const dpf_model_desc* model, int32_t d1, int32_t d2, in
 dpf_status dpf_create_std(const dpf_model_desc* model, int32_t d1, int32_t d2, int64_t N, int32_t M,
                           uint64_t seed, void* stream, dpf_ctx** out);
 
+/*
+ * The Gaussian approximation of the mixture prior of x_t (Section 4.2, Table 2) in a
+ * context of dpf_create_std: on != 0 draws x_t from the Gaussian with the mixture's mean
+ * sum_j qbar_j m_j and covariance Q_x + sum_j qbar_j (m_j - mean)(m_j - mean)^T
+ * (m_j = E[x_t | x_{t-1}, z_j]), as mean + chol(covariance) e with the same normals e;
+ * everything else is unchanged (the component draw is then not used). A model whose x
+ * transition is free of z is not affected. DPF_E_INVALID for other contexts.
+ */
+dpf_status dpf_set_gaussian_approx(dpf_ctx* ctx, int32_t on);
+
 /* Inner diagnostics of the newest materialised state (the state of step t-1 after
  * step t, see dpf_read): each group's inner effective sample size
  * (sum_j W_j)^2 / sum_j W_j^2 with W = exp(lq), in [1, M]; their minimum and mean

@@ -14,6 +14,9 @@ step, then 1 and 3 with y_t; step 2 is the global systematic resampling that fol
   (7) z_t^(j) = E[z_t | x_{t-1}^a, z^(a,b_j)] + chol(Q_z) e_j, e_j the normals (t, i, PROP, j);
   (1) log w_i = log (1/M) sum_j p(y_t | x_t, z_t^(j));
   (3) log qbar_t^(j) = log p(y_t | x_t, z_t^(j)) - log sum_j p(y_t | x_t, z_t^(j)).
+With the Gaussian approximation of the mixture (Section 4.2, Table 2), step (4) draws
+x_t = mu + chol(S) e instead, mu = sum_j qbar_j m_j and S = Q_x + sum_j qbar_j (m_j - mu)
+(m_j - mu)^T with m_j = E[x_t | x_{t-1}^a, z^(a,j)]: the mixture's first two moments.
 """
 from __future__ import annotations
 
@@ -33,7 +36,7 @@ def _lse(v):
     return m + np.log(np.sum(np.exp(v - m)))
 
 
-def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None):
+def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, gauss=False):
     """One call from the state of step t-1: x_prev (N, d1), z_prev (N, M, d2), lq_prev
     (N, M) = log qbar. anc: the ancestors of the destinations (None at t = 1); dest: the
     destinations' indices (their random-number keys; default 0..n-1).
@@ -54,9 +57,17 @@ def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None):
         s = np.concatenate([np.repeat(x_prev[a][None, :], M, 0), z_prev[a]], axis=1)
         mean = transition_mean(model, s, t - 1)  # row j: E[s_t | x^a, z^(a,j)]
         qbar = np.exp(lq_prev[a] - lq_prev[a].max())
-        c = int(oracle.sys_local(qbar, 1, _word(seed, t, g, oracle.P_LA_J), lib)[0])
         e = oracle.normals(seed, 0, t, g, oracle.P_LA_X, 0, d1, lib)
-        xt = mean[c, :d1] + Lqx @ e
+        if gauss:
+            qn = qbar / qbar.sum()
+            mu = qn @ mean[:, :d1]
+            dev = mean[:, :d1] - mu
+            S = Qx + (dev * qn[:, None]).T @ dev
+            c = -1
+            xt = mu + np.linalg.cholesky(S) @ e
+        else:
+            c = int(oracle.sys_local(qbar, 1, _word(seed, t, g, oracle.P_LA_J), lib)[0])
+            xt = mean[c, :d1] + Lqx @ e
         # q_j = qbar_j N(x_t; mean_j, Q_x)
         q = lq_prev[a] + log_gauss(xt[None, :] - mean[:, :d1], Qx)
         b = oracle.sys_local(np.exp(q - q.max()), M, _word(seed, t, g, oracle.P_INNER), lib)

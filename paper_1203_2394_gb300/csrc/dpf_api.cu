@@ -385,6 +385,14 @@ dpf_status dpf_create_std(const dpf_model_desc* model, int32_t d1, int32_t d2, i
   return DPF_OK;
 }
 
+dpf_status dpf_set_gaussian_approx(dpf_ctx* x, int32_t on) {
+  clear_error();
+  if (!x || !x->std_dpf)
+    return set_error(DPF_E_INVALID, "dpf_set_gaussian_approx: needs a context from dpf_create_std");
+  x->std_gauss = on != 0;
+  return DPF_OK;
+}
+
 static dpf_status step_enqueue(dpf_ctx* x, double* mean_out, double* logz_out) {
   const long long t = x->t + 1;
   if (x->profiling) {

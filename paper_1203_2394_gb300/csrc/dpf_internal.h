@@ -174,6 +174,7 @@ struct dpf_ctx {
   bool la_only = false;      // the next step kernel runs the look-ahead only
   bool pf = false;           // a bootstrap particle filter (dpf_create_pf), not the LA-DPF
   bool std_dpf = false;      // the DPF without look-ahead (dpf_create_std)
+  bool std_gauss = false;    // ... drawing x_t from the mixture's moment-matched Gaussian
   // the learned proposal's per-group fallback to the plain inner update
   double fb_frac = 0.25;          // a group falls back when its inner ESS < fb_frac * M (0: never)
   int32_t* fb_flag = nullptr;     // [N] 1 where the last learned inner update fell back

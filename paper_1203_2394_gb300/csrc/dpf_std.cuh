@@ -12,7 +12,9 @@
 // The outer resampling of step 2 is the filter's global scan after the kernel, which
 // also gives the evidence and the weighted mean. Random words: the component (t, i,
 // LA_J, 0), the x noise (t, i, LA_X, 0), the local resampling (t, i, INNER, 0), the z
-// noise (t, i, PROP, j).
+// noise (t, i, PROP, j). With the Gaussian approximation of the mixture (Section 4.2),
+// step 4 draws x_t from the Gaussian with the mixture's mean and covariance instead, with
+// the same normals.
 #pragma once
 
 #include "dpf_step.cuh"
@@ -43,6 +45,7 @@ struct StdArgs {
   T scaleM;   // 2^(31 - ceil(log2 M)): the local rule's quantisation
   T logM;
   int first;  // t == 1: no ancestors yet
+  int gauss;  // draw x_t from the moment-matched Gaussian of the mixture (Section 4.2)
 };
 
 template <typename T, int D1, int D2, int DY, bool XZ>
@@ -86,14 +89,69 @@ __global__ void __launch_bounds__(1024)
     T xt[D1];
     {
       T w[D1];
+      if (XZ && a.gauss) {
+        // the mixture's moment-matched Gaussian, in the coordinates whitened by L_qx: with
+        // u_j = L_qx^-1 A_xz z_j, mean ubar = sum_j qbar_j u_j and covariance I + C,
+        // C = sum_j qbar_j (u_j - ubar)(u_j - ubar)^T; w = ubar + chol(I + C) e
+        T uj[D1];
 #pragma unroll
-      for (int r = 0; r < D1; ++r) {
-        T v = e1[r];
-        if (XZ) {
+        for (int r = 0; r < D1; ++r) {
+          T v = T(0);
+          if (act) {
 #pragma unroll
-          for (int c = 0; c < D2; ++c) v += mc.WAxz[r][c] * zs[c * M + jm];
+            for (int c = 0; c < D2; ++c) v += mc.WAxz[r][c] * zs[c * M + j];
+          }
+          uj[r] = v;
         }
-        w[r] = v;
+        const T qj = act ? exp_t<T>(lqj - mx) : T(0);
+        const T qs = bsum(qj, red);
+        T ub[D1];
+#pragma unroll
+        for (int r = 0; r < D1; ++r) ub[r] = bsum(qj * uj[r], red) / qs;
+        T G[D1][D1];
+#pragma unroll
+        for (int r = 0; r < D1; ++r)
+#pragma unroll
+          for (int c = 0; c < D1; ++c)
+            if (c <= r) G[r][c] = bsum(qj * (uj[r] - ub[r]) * (uj[c] - ub[c]), red) / qs + (r == c ? T(1) : T(0));
+        // Cholesky of I + C in place (lower triangle), the same in every thread
+#pragma unroll
+        for (int c = 0; c < D1; ++c) {
+          T d = G[c][c];
+#pragma unroll
+          for (int k = 0; k < D1; ++k)
+            if (k < c) d -= G[c][k] * G[c][k];
+          d = sqrt(d);
+          G[c][c] = d;
+#pragma unroll
+          for (int r = 0; r < D1; ++r) {
+            if (r > c) {
+              T v = G[r][c];
+#pragma unroll
+              for (int k = 0; k < D1; ++k)
+                if (k < c) v -= G[r][k] * G[c][k];
+              G[r][c] = v / d;
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          T v = ub[r];
+#pragma unroll
+          for (int c = 0; c < D1; ++c)
+            if (c <= r) v += G[r][c] * e1[c];
+          w[r] = v;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          T v = e1[r];
+          if (XZ) {
+#pragma unroll
+            for (int c = 0; c < D2; ++c) v += mc.WAxz[r][c] * zs[c * M + jm];
+          }
+          w[r] = v;
+        }
       }
 #pragma unroll
       for (int r = 0; r < D1; ++r) {

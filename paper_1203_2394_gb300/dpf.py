@@ -61,6 +61,7 @@ SIGNATURES = [
     ("dpf_diag_inner", ctypes.c_int, [_P, _P, _P]),
     ("dpf_create_pf", ctypes.c_int, [_P, _I32, _I32, _I64, _U64, _P, _P]),
     ("dpf_create_std", ctypes.c_int, [_P, _I32, _I32, _I64, _I32, _U64, _P, _P]),
+    ("dpf_set_gaussian_approx", ctypes.c_int, [_P, _I32]),
     ("dpf_read", ctypes.c_int, [_P, ctypes.c_char_p, _P, _SZ]),
     ("dpf_proposal_create", ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _P, _P]),
     ("dpf_proposal_create_amortised", ctypes.c_int, [_I32, _I32, _I32, _I32, _P, _P, _P]),
@@ -329,6 +330,10 @@ class StandardDPF(Filter):
         check(self._lib.dpf_create_std(ctypes.byref(model.desc), self.d1, self.d2, self.N, self.M,
                                        ctypes.c_uint64(seed), _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
+
+    def set_gaussian_approx(self, on=True):
+        """Draw x_t from the mixture's moment-matched Gaussian (Section 4.2)."""
+        check(self._lib.dpf_set_gaussian_approx(self.h, int(on)))
 
 
 class _Borrowed(Filter):

@@ -6,6 +6,7 @@
   most 1% of the groups differing, the rest within 2e-5 on the particles and 2e-4 on the
   log-weights, which the growth map's FP32 rounding reaches), and the outer
   ancestors equal the oracle's systematic resampling of the GPU's weights bit for bit.
+  The same in FP64 with the Gaussian approximation of the mixture prior of x_t.
 * FP64 tracks the Kalman filter on lg4.
 * The comparison workload's size (N = 65536, M = 128, FP32): sampled groups of one call.
 """
@@ -36,10 +37,13 @@ def _compare(gx, gz, glq, glw, ox, oz, olq, olw, tol, tol_l=None):
     return ok
 
 
-@pytest.mark.parametrize("name,prec,M", [("lg4", "f64", 32), ("growth_clg10", "f32", 64)])
-def test_std_teacher_forced(name, prec, M):
+@pytest.mark.parametrize("name,prec,M,gauss", [("lg4", "f64", 32, False), ("lg4", "f64", 32, True),
+                                                ("growth_clg10", "f32", 64, False)])
+def test_std_teacher_forced(name, prec, M, gauss):
     N, seed = 400, 9
     spec, f = _filter(name, prec, N, M, seed)
+    if gauss:
+        f.set_gaussian_approx(True)
     om = oracle.OracleModel.from_spec(spec)
     lib = oracle.load()
     dt = np.float64 if prec == "f64" else np.float32
@@ -57,7 +61,8 @@ def test_std_teacher_forced(name, prec, M):
         mean, _ = f.step(y)
         gx, gz, glq = state_from_gpu(f)
         glw = f.read("lw").astype(np.float64)
-        ex, ez, elq, elw, _, _ = std_dpf.std_step(om, seed, t, y.astype(np.float64), x, z, lq, anc, lib)
+        ex, ez, elq, elw, _, _ = std_dpf.std_step(om, seed, t, y.astype(np.float64), x, z, lq, anc, lib,
+                                                  gauss=gauss)
         ok = _compare(gx, gz, glq, glw, ex, ez, elq, elw, tol, tol_l)
         bad += int((~ok).sum())
         if prec == "f64":
