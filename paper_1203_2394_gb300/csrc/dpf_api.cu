@@ -583,7 +583,9 @@ struct StateHeader {
   int32_t version, prec, d1, d2, dy, M, L, xp;
   int64_t N, t;
   uint64_t seed;
+  int32_t kind, pad;  // 0 the LA-DPF, 1 the bootstrap particle filter, 2 the DPF without look-ahead
 };
+int32_t ctx_kind(const dpf_ctx& x) { return x.pf ? 1 : (x.std_dpf ? 2 : 0); }
 constexpr uint64_t kStateMagic = 0x4450465354415445ull;  // "DPFSTATE"
 struct StateLayout {
   size_t off[10];
@@ -608,7 +610,9 @@ StateLayout state_layout(const dpf_ctx& x) {
 // the device arrays of the sections (header excluded), in layout order
 void state_arrays(dpf_ctx& x, void* a[10]) {
   const long long t = x.t;
-  const int mat = t >= 2 ? (int)((t - 1) % 2) : 0, cur = (int)(t % 2);
+  const int cur = (int)(t % 2);
+  // the state the next step reads: the LA-DPF's materialised slot, the others' newest one
+  const int mat = (x.pf || x.std_dpf) ? cur : (t >= 2 ? (int)((t - 1) % 2) : 0);
   a[0] = nullptr;
   a[1] = x.x[mat];
   a[2] = x.z[mat];
@@ -634,7 +638,8 @@ dpf_status dpf_get_state(dpf_ctx* x, void* dst, size_t bytes) {
   if (!x || !dst) return set_error(DPF_E_INVALID, "dpf_get_state: null argument");
   const StateLayout l = state_layout(*x);
   if (bytes < l.total) return set_error(DPF_E_INVALID, "dpf_get_state: buffer smaller than dpf_state_bytes");
-  StateHeader h{kStateMagic, 1, x->prec, x->d1, x->d2, x->dy, x->M, x->L, x->xp, x->N, x->t, x->seed};
+  StateHeader h{kStateMagic, 2, x->prec, x->d1, x->d2, x->dy, x->M, x->L, x->xp, x->N, x->t, x->seed,
+                ctx_kind(*x), 0};
   void* a[10];
   state_arrays(*x, a);
   cudaError_t e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, x->stream);
@@ -653,9 +658,10 @@ dpf_status dpf_set_state(dpf_ctx* x, const void* src, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, x->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
   if (e != cudaSuccess) return cuda_error(e, "dpf_set_state");
-  if (h.magic != kStateMagic || h.version != 1 || h.prec != x->prec || h.d1 != x->d1 || h.d2 != x->d2 ||
-      h.dy != x->dy || h.M != x->M || h.L != x->L || h.xp != x->xp || h.N != x->N || h.t < 0)
-    return set_error(DPF_E_INVALID, "dpf_set_state: not a state of a filter of this precision and these sizes");
+  if (h.magic != kStateMagic || h.version != 2 || h.prec != x->prec || h.d1 != x->d1 || h.d2 != x->d2 ||
+      h.dy != x->dy || h.M != x->M || h.L != x->L || h.xp != x->xp || h.N != x->N || h.t < 0 ||
+      h.kind != ctx_kind(*x))
+    return set_error(DPF_E_INVALID, "dpf_set_state: not a state of a filter of this kind, precision and these sizes");
   x->t = h.t;
   void* a[10];
   state_arrays(*x, a);

@@ -46,3 +46,31 @@ def test_state_of_other_sizes_refused():
         b.set_state(big)
     with pytest.raises(dpf.DpfError):
         a.set_state(st[:100])
+
+
+@pytest.mark.parametrize("kind", ["pf", "std"])
+def test_restore_baselines_continue_bit_for_bit(kind):
+    """The bootstrap particle filter and the DPF without look-ahead restore from their own
+    checkpoints (the newest particles are the state they read next), and a state of another
+    kind of filter with the same sizes is refused."""
+    from paper_1203_2394_gb300 import dpf
+    spec = workloads.make_model("growth_clg10", 0)
+    m = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    _, ys = workloads.simulate(spec, 9, 0)
+    make = (lambda: dpf.ParticleFilter(m, 2, 8, 3000, seed=6)) if kind == "pf" else \
+        (lambda: dpf.StandardDPF(m, 2, 8, 500, 64, seed=6))
+    a = make()
+    for t in range(4):
+        a.step(ys[t].astype(np.float32))
+    st = a.get_state()
+    b = make()
+    b.set_state(st)
+    for t in range(4, 8):
+        ma, la = a.step(ys[t].astype(np.float32))
+        mb, lb = b.step(ys[t].astype(np.float32))
+        np.testing.assert_array_equal(ma, mb)
+        assert la == lb
+    if kind == "std":
+        other = dpf.Filter(m, 2, 8, 500, 64, 1, seed=6)
+        with pytest.raises(dpf.DpfError):
+            other.set_state(st)
