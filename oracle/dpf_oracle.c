@@ -125,6 +125,15 @@ void ora_normals(uint64_t seed, uint32_t filter_id, uint32_t t, uint32_t i, uint
   rng_normals(&r, t, i, purpose, sub, n, out);
 }
 
+/* Many keys at once: row q of out (n values) holds the normals of
+ * (t, idx[q], purpose, sub[q]); for the oracles written in numpy. */
+void ora_normals_many(uint64_t seed, uint32_t filter_id, uint32_t t, int64_t count,
+                      const uint32_t* idx, uint32_t purpose, const uint32_t* sub, int n,
+                      double* out) {
+  ora_rng r = rng_make(seed, filter_id);
+  for (int64_t q = 0; q < count; ++q) rng_normals(&r, t, idx[q], purpose, sub[q], n, out + q * n);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Systematic resampling ("standard resampling", steps 2 and 6 of the DPF,    */
 /* step 3 of the LA-DPF). The paper does not name the scheme; the systematic  */

@@ -78,6 +78,8 @@ def load(path: str | None = None):
         lib.ora_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_int, P]
+        lib.ora_normals_many.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_int64, P, ctypes.c_uint32, P, ctypes.c_int, P]
         lib.ora_sys_global.argtypes = [P, ctypes.c_int64, ctypes.c_uint32, P]
         lib.ora_sys_local.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, P]
         lib.ora_init.argtypes = [P, P, P, P, P]
@@ -216,6 +218,16 @@ def normals(seed, filter_id, t, i, purpose, sub, n, lib=None):
     lib = lib or load()
     o = np.zeros(n)
     lib.ora_normals(seed, filter_id, t, i, purpose, sub, n, _ptr(o))
+    return o
+
+
+def normals_many(seed, filter_id, t, idx, purpose, sub, n, lib=None):
+    """Row q: the n normals of (t, idx[q], purpose, sub[q])."""
+    lib = lib or load()
+    idx = np.ascontiguousarray(idx, dtype=np.uint32)
+    sub = np.ascontiguousarray(np.broadcast_to(np.asarray(sub, dtype=np.uint32), idx.shape))
+    o = np.zeros((len(idx), n))
+    lib.ora_normals_many(seed, filter_id, t, len(idx), _ptr(idx), purpose, _ptr(sub), n, _ptr(o))
     return o
 
 

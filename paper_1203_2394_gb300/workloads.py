@@ -138,6 +138,39 @@ def simulate(spec: ModelSpec, T: int, seed: int = 0):
     return s, ys
 
 
+def simulate_paper(kind: int, T: int, seed: int = 0):
+    """A trajectory of the paper's benchmark model 1 or 2 (Table 1): true states s_0..s_T
+    as (T + 1, d) with the x coordinates first, and observations y_1..y_T as (T, 1). The
+    sine and cosine take the step the transition leaves; s_0 ~ N(0, I)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 2_000_003))
+    d = 2 if kind == 1 else 4
+    if kind == 1:
+        Lv = np.linalg.cholesky(np.array([[1.0, 0.1], [0.1, 1.0]]))
+    else:
+        Sv = np.eye(4)
+        Sv[2:, 2:] = [[1.0, 0.1], [0.1, 10.0]]
+        Lv = np.linalg.cholesky(Sv)
+    s = np.zeros((T + 1, d))
+    s[0] = rng.standard_normal(d)
+    ys = np.zeros((T, 1))
+    for t in range(1, T + 1):
+        v = Lv @ rng.standard_normal(d)
+        p, u = s[t - 1], t - 1
+        if kind == 1:
+            x, z = p
+            s[t] = [x + z / (1 + z * z) + v[0],
+                    x + 0.5 * z + 25 * z / (1 + z * z) + 8 * np.cos(1.2 * u) + v[1]]
+            y = np.arctan(s[t, 0]) + s[t, 1] ** 2 / 20
+        else:
+            x1, x2, z1, z2 = p
+            z1n = z1 + z2 / (1 + z2 * z2) + v[2]
+            s[t] = [0.5 * x1 + 8 * np.sin(u) + v[0], 0.4 * x1 + 0.5 * x2 + v[1], z1n,
+                    z1n + 0.5 * z2 + 25 * z2 / (1 + z2 * z2) + 8 * np.cos(1.2 * u) + v[3]]
+            y = (s[t, 0] + s[t, 1]) / (1 + s[t, 0] ** 2) + np.arctan(s[t, 2]) + s[t, 3] ** 2 / 20
+        ys[t - 1, 0] = y + rng.standard_normal()
+    return s, ys
+
+
 def proposal_dims(spec, d1: int | None = None, components: int = 4, hidden: int = 256):
     """Sizes of the learned inner proposal for a model: inputs (x_{t-1}, x_t, z_{t-1}, y_t),
     hidden width, and the mixture head (logits, means, log standard deviations)."""
