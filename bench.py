@@ -673,6 +673,72 @@ def run_table2(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's comparison (Section 4.1) on its own benchmark models (Table 1): for
+    model 1 and model 2, the LA-DPF (N = 65536, M = 128, L = 16) and the bootstrap particle
+    filter with N (M + 1) = 8,454,144 particles, FP32, over R runs of 250 steps (the paper's
+    horizon) on seeded trajectories: the RMSE of the filtered mean against the true state per
+    block (x, z), averaged over the runs, and the time per step (device observations, CUDA
+    events over the steps after the first 10)."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    N, M, L, T, W0 = 65536, 128, 16, 250, 10
+    R = max(1, min(args.runs, 8))
+    stream = torch.cuda.current_stream()
+
+    def run(f, yd, s_true, d, d1):
+        means = torch.zeros((T, d), dtype=torch.float64, device="cuda")
+        for k in range(W0):
+            f.step_device(yd[k].data_ptr(), means[k].data_ptr())
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(W0, T):
+            f.step_device(yd[k].data_ptr(), means[k].data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f.sync()
+        err = means.cpu().numpy() - s_true[1:]
+        return (e0.elapsed_time(e1) / (T - W0), float(np.sqrt(np.mean(err[:, :d1] ** 2))),
+                float(np.sqrt(np.mean(err[:, d1:] ** 2))))
+
+    out = {}
+    for kind in (1, 2):
+        pm = dpf.PaperModel(kind)
+        res = {"ladpf": [], "pf": []}
+        for r in range(R):
+            s_true, ys = workloads.simulate_paper(kind, T, 100 + r)
+            yd = torch.tensor(ys.astype(np.float32), device="cuda")
+            f = dpf.Filter(pm, pm.d1, pm.d2, N, M, L, seed=r)
+            res["ladpf"].append(run(f, yd, s_true, pm.d, pm.d1))
+            f.close()
+            f = dpf.ParticleFilter(pm, pm.d1, pm.d2, N * (M + 1), seed=r)
+            res["pf"].append(run(f, yd, s_true, pm.d, pm.d1))
+            f.close()
+        out[f"model{kind}"] = {
+            k: {"ms_per_step": float(np.mean([v[0] for v in res[k]])),
+                "rmse_x": float(np.mean([v[1] for v in res[k]])),
+                "rmse_z": float(np.mean([v[2] for v in res[k]]))} for k in res}
+        out[f"model{kind}"]["pf"]["particles"] = N * (M + 1)
+    ms = out["model1"]["ladpf"]["ms_per_step"]
+    line = {
+        "metric": METRIC, "value": N * M / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": T - W0,
+        "warmup": W0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"the paper's models 1 and 2 (Table 1): LA-DPF N={N}, M={M}, L={L} against the "
+                               f"bootstrap PF with N(M+1)={N * (M + 1)} particles, FP32, {R} runs of {T} steps; "
+                               f"value: model 1's LA-DPF"},
+        **out,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args):
     """The learned-proposal workload: the lg4 model in FP32 with N = 262144 outer and
     M = 64 inner particles. A proposal (MLP 3 x 256 ReLU, 4-component mixture head, BF16
@@ -834,9 +900,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare", "table2"],
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare", "table2", "paper"],
                     help="the headline single-filter workload, the many-filter one, the d2 = 56 one, "
                          "the learned-proposal one, or the LA-DPF against the bootstrap PF")
+    ap.add_argument("--runs", type=int, default=3, help="runs per model of the paper workload (at most 8)")
     ap.add_argument("--filters", type=int, default=None,
                     help="filters of the batched (default 512) or high-dimensional (default 64) workload")
     args = ap.parse_args(argv)
@@ -856,6 +923,8 @@ def main(argv=None):
         return run_compare(args)
     if args.workload == "table2":
         return run_table2(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run(args)
 
 

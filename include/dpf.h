@@ -38,7 +38,8 @@ typedef enum {
 } dpf_status;
 
 enum { DPF_F32 = 0, DPF_F64 = 1 };          /* precision / dtype codes */
-enum { DPF_MODEL_CLG = 1 };                 /* conditionally linear-Gaussian family */
+enum { DPF_MODEL_CLG = 1,                  /* conditionally linear-Gaussian family */
+       DPF_MODEL_PAPER1 = 2, DPF_MODEL_PAPER2 = 3 }; /* the paper's models 1 and 2 (Table 1) */
 enum { DPF_SYS_GLOBAL = 0, DPF_SYS_LOCAL = 1 }; /* resampling rules, see dpf_resample */
 enum { DPF_TC_TF32 = 0, DPF_TC_TF32X3 = 1, DPF_TC_BF16 = 2 }; /* tensor-core operand modes */
 
@@ -78,6 +79,22 @@ typedef struct {
   double growth[4];
   double qc;
 } dpf_model_desc;
+
+/*
+ * The paper's benchmark models (Table 1), kind DPF_MODEL_PAPER1 or DPF_MODEL_PAPER2
+ * (FP32 only; the matrices, perm, growth and qc fields are not read; d and dy must be 2
+ * and 1 for model 1, 4 and 1 for model 2, with d1 = d2 = d / 2):
+ *   model 1: x' = x + z / (1 + z^2) + v_x, z' = x + 0.5 z + 25 z / (1 + z^2) + 8 cos(1.2 t) + v_z,
+ *            y = atan(x) + z^2 / 20 + e, (v_x, v_z) ~ N(0, [[1, 0.1], [0.1, 1]]);
+ *   model 2: x1' = 0.5 x1 + 8 sin t + v, x2' = 0.4 x1 + 0.5 x2 + v, z1' = z1 + z2 / (1 + z2^2) + v,
+ *            z2' = z1' + 0.5 z2 + 25 z2 / (1 + z2^2) + 8 cos(1.2 t) + v,
+ *            y = (x1 + x2) / (1 + x1^2) + atan(z1) + z2^2 / 20 + e, the z noises ~ N(0, [[1, 0.1], [0.1, 10]]),
+ *            the x noises ~ N(0, I);
+ * e ~ N(0, 1), s_0 ~ N(0, I); t in the sine and cosine is the source step of the
+ * transition. The inner draws are conditioned on x_t through the noise covariance. With
+ * these kinds dpf_create (L <= 32) and dpf_create_pf serve the models; the batched form,
+ * the learned proposal and dpf_create_std do not.
+ */
 
 /*
  * Create a filter: N outer particles of the x block (d1 coordinates), each with

@@ -273,12 +273,29 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   x->L = L;
   x->seed = seed;
   x->stream = (cudaStream_t)stream;
-  dpf_status st = prepare_model(model, d1, d2, x->perm, x->hm);
+  const bool paper = model->kind == DPF_MODEL_PAPER1 || model->kind == DPF_MODEL_PAPER2;
+  dpf_status st = DPF_OK;
+  if (paper) {  // the paper's models: fixed dimensions, FP32, identity coordinate order
+    const int want_d = model->kind == DPF_MODEL_PAPER1 ? 2 : 4;
+    if (model->d != want_d || model->dy != 1 || d1 != want_d / 2 || d2 != want_d / 2 || model->precision != DPF_F32) {
+      delete x;
+      return set_error(DPF_E_INVALID, "dpf_create: the paper's model 1 needs d = 2, model 2 d = 4, with dy = 1, "
+                                      "d1 = d2 = d / 2 and FP32");
+    }
+    x->perm.resize(want_d);
+    for (int c = 0; c < want_d; ++c) x->perm[c] = c;
+    x->hm.d1 = d1;
+    x->hm.d2 = d2;
+    x->hm.dy = 1;
+    x->hm.xz = true;
+  } else {
+    st = prepare_model(model, d1, d2, x->perm, x->hm);
+  }
   if (st) {
     delete x;
     return st;
   }
-  x->var = find_variant(x->prec, d1, d2, x->dy);
+  x->var = paper ? find_paper_variant(model->kind) : find_variant(x->prec, d1, d2, x->dy);
   if (!x->var) {
     delete x;
     return set_error(DPF_E_UNSUPPORTED,

@@ -51,7 +51,7 @@ struct StdArgs {
 template <typename T, int D1, int D2, int DY, bool XZ>
 __global__ void __launch_bounds__(1024)
     std_dpf_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc, const __grid_constant__ StdArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int M = a.M, tid = threadIdx.x, j = tid;
   const bool act = j < M;
   const long long N = a.N, NM = N * (long long)M;

@@ -13,6 +13,64 @@ namespace dpf {
 inline int threads_for(int M) { return ((M + 31) / 32) * 32; }
 
 // XZM: 0 = kernels for both x-transition kinds, 1 = only the general (x depends on z) kernels.
+// The outer stage of a step (the outer reduction, then the global resampling),
+// for every filter kind.
+template <typename T>
+void fill_outer_args(Ctx& x, double* mean_out, double* logz_out, void* ov, void* gv) {
+    OuterArgs<T>& o = *(OuterArgs<T>*)ov;
+    o = OuterArgs<T>{};
+    o.lw = (const T*)x.lw;
+    o.xm = (const T*)x.xm;
+    o.zm = (const T*)x.zm;
+    o.N = x.N;
+    o.d1 = x.d1;
+    o.d2 = x.d2;
+    o.lwmax_key = x.lwmax_key;
+    o.lwmax_t = (T*)x.lwmax_t;
+    o.Csum = x.Csum;
+    o.done = x.done;
+    o.partials = x.partials;
+    o.stats = x.stats;
+    o.perm = (const int*)(x.stats + 4 + x.d);  // the permutation lives after the statistics
+    o.mean_out = mean_out;
+    o.logz_out = logz_out;
+    o.err = x.err;
+    const long long t = x.t + 1;
+    const long long tiles = (x.N + SCAN_TILE - 1) / SCAN_TILE;
+    GlobalArgs<T>& g = *(GlobalArgs<T>*)gv;
+    g = GlobalArgs<T>{};
+    g.w = (const T*)x.lw;
+    g.lwmax = (const T*)x.lwmax_t;
+    g.w_out = (T*)x.wout;
+    g.n = x.N;
+    g.shift = 62 - ceil_log2_i(x.N);
+    g.shift_dev = nullptr;
+    g.C = x.Csum;
+    g.u_ptr = nullptr;
+    g.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    g.t = (uint32_t)t;
+    g.out = x.anc;
+    g.st = ScanState{x.flags, x.agg, x.incl, x.ticket};
+    g.ticket_base = x.ticket_next;
+    g.epoch = ++x.epoch;
+    g.err = x.err;
+    g.withhold = -1;
+    x.ticket_next += (unsigned long long)tiles;
+  }
+
+template <typename T, int D1, int D2>
+dpf_status outer_stage(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
+    OuterArgs<T> o;
+    GlobalArgs<T> g;
+    fill_outer_args<T>(x, mean_out, logz_out, &o, &g);
+    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, st>>>(o);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
+    global_scan_scatter<T, true><<<(unsigned)((x.N + SCAN_TILE - 1) / SCAN_TILE), SCAN_NT, 0, st>>>(g);
+    return cuda_error(cudaGetLastError(), "outer resample launch");
+  }
+
+
 template <typename T, int D1, int D2, int DY, int XZM = 0>
 struct VariantImpl {
   typedef MC<T, D1, D2, DY> Const;
@@ -259,56 +317,11 @@ struct VariantImpl {
   // and the global resampling (g). Advances the context's scan epoch and ticket
   // base, as the launches that use these arguments will consume them.
   static void outer_args(Ctx& x, double* mean_out, double* logz_out, void* ov, void* gv) {
-    OuterArgs<T>& o = *(OuterArgs<T>*)ov;
-    o = OuterArgs<T>{};
-    o.lw = (const T*)x.lw;
-    o.xm = (const T*)x.xm;
-    o.zm = (const T*)x.zm;
-    o.N = x.N;
-    o.d1 = x.d1;
-    o.d2 = x.d2;
-    o.lwmax_key = x.lwmax_key;
-    o.lwmax_t = (T*)x.lwmax_t;
-    o.Csum = x.Csum;
-    o.done = x.done;
-    o.partials = x.partials;
-    o.stats = x.stats;
-    o.perm = (const int*)(x.stats + 4 + x.d);  // the permutation lives after the statistics
-    o.mean_out = mean_out;
-    o.logz_out = logz_out;
-    o.err = x.err;
-    const long long t = x.t + 1;
-    const long long tiles = (x.N + SCAN_TILE - 1) / SCAN_TILE;
-    GlobalArgs<T>& g = *(GlobalArgs<T>*)gv;
-    g = GlobalArgs<T>{};
-    g.w = (const T*)x.lw;
-    g.lwmax = (const T*)x.lwmax_t;
-    g.w_out = (T*)x.wout;
-    g.n = x.N;
-    g.shift = 62 - ceil_log2_i(x.N);
-    g.shift_dev = nullptr;
-    g.C = x.Csum;
-    g.u_ptr = nullptr;
-    g.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
-    g.t = (uint32_t)t;
-    g.out = x.anc;
-    g.st = ScanState{x.flags, x.agg, x.incl, x.ticket};
-    g.ticket_base = x.ticket_next;
-    g.epoch = ++x.epoch;
-    g.err = x.err;
-    g.withhold = -1;
-    x.ticket_next += (unsigned long long)tiles;
+    fill_outer_args<T>(x, mean_out, logz_out, ov, gv);
   }
 
   static dpf_status outer(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
-    OuterArgs<T> o;
-    GlobalArgs<T> g;
-    outer_args(x, mean_out, logz_out, &o, &g);
-    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, st>>>(o);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
-    global_scan_scatter<T, true><<<(unsigned)((x.N + SCAN_TILE - 1) / SCAN_TILE), SCAN_NT, 0, st>>>(g);
-    return cuda_error(cudaGetLastError(), "outer resample launch");
+    return outer_stage<T, D1, D2>(x, mean_out, logz_out, st);
   }
 
   // The outer reductions of F filters of this variant in one launch (device

@@ -11,6 +11,8 @@ Variant make_v_f32_2_14_4();
 Variant make_v_f32_4_12_4();
 Variant make_v_f32_8_8_4();
 Variant make_v_f32_8_56_8();
+Variant make_v_paper1();
+Variant make_v_paper2();
 
 const Variant* find_variant(int prec, int d1, int d2, int dy) {
   static const Variant table[] = {make_v_f32_2_8_2(), make_v_f64_2_2_2(), make_v_f32_2_2_2(),
@@ -18,6 +20,13 @@ const Variant* find_variant(int prec, int d1, int d2, int dy) {
                                   make_v_f32_8_8_4(), make_v_f32_8_56_8()};
   for (const Variant& v : table)
     if (v.prec == prec && v.d1 == d1 && v.d2 == d2 && v.dy == dy) return &v;
+  return nullptr;
+}
+
+const Variant* find_paper_variant(int kind) {
+  static const Variant table[] = {make_v_paper1(), make_v_paper2()};
+  if (kind == DPF_MODEL_PAPER1) return &table[0];
+  if (kind == DPF_MODEL_PAPER2) return &table[1];
   return nullptr;
 }
 

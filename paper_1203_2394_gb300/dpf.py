@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libdpf.so")
 
 DPF_OK, DPF_E_INVALID, DPF_E_NOMEM, DPF_E_CUDA, DPF_E_TIMEOUT, DPF_E_NUMERIC, DPF_E_UNSUPPORTED = range(7)
 DPF_F32, DPF_F64 = 0, 1
-DPF_MODEL_CLG = 1
+DPF_MODEL_CLG, DPF_MODEL_PAPER1, DPF_MODEL_PAPER2 = 1, 2, 3
 DPF_SYS_GLOBAL, DPF_SYS_LOCAL = 0, 1
 STATUS_NAMES = {0: "DPF_OK", 1: "DPF_E_INVALID", 2: "DPF_E_NOMEM", 3: "DPF_E_CUDA",
                 4: "DPF_E_TIMEOUT", 5: "DPF_E_NUMERIC", 6: "DPF_E_UNSUPPORTED"}
@@ -156,6 +156,22 @@ class Model:
     def from_spec(cls, spec, precision=DPF_F32, perm=None):
         return cls(spec.d, spec.dy, spec.A, spec.Q, spec.H, spec.R, spec.m0, spec.P0, precision,
                    spec.growth, spec.qc, perm)
+
+
+class PaperModel(Model):
+    """The paper's benchmark model 1 (d = 2) or 2 (d = 4) of Table 1, FP32; the filter is
+    created with d1 = d2 = d / 2 (the matrices of the descriptor are not used)."""
+
+    def __init__(self, kind: int):
+        if kind not in (1, 2):
+            raise ValueError("kind must be 1 or 2")
+        self.arrays = []
+        self.perm = None
+        self.d, self.dy, self.precision = (2 if kind == 1 else 4), 1, DPF_F32
+        self.d1 = self.d2 = self.d // 2
+        g = (ctypes.c_double * 4)(0.0, 0.0, 0.0, 0.0)
+        self.desc = ModelDesc(DPF_MODEL_PAPER1 if kind == 1 else DPF_MODEL_PAPER2, self.d, self.dy,
+                              self.precision, 0, 0, None, None, None, None, None, None, None, g, 0.0)
 
 
 class Filter:
