@@ -39,6 +39,9 @@ The LA-DPF step t from the state of step t-1 (x, z, lq = log qbar), in Fig. 4's 
      from their conditional given x_t (normals (t, i, PROP, j)) and reweighted by y_t.
 The filtered mean is the look-ahead's: the pairs (i, m) weighted by exp(lwhat), with the
 z part sum_k softmax_k(alpha + ell) zhat_mk.
+
+Also the DPF without look-ahead (std_step) and the bootstrap particle filter (pf_step)
+for the same models, the filters the paper compares the LA-DPF with.
 """
 from __future__ import annotations
 
@@ -210,6 +213,62 @@ def run_la_dpf(model, seed, ys, N, M, L, lib):
         o = step(model, seed, t, float(np.ravel(y)[0]), x, z, lq, L, lib)
         x, z, lq = o["x"], o["z"], o["lq"]
         means.append(o["mean"]); lz.append(o["logZ"])
+    return np.array(means), np.array(lz)
+
+
+def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, gauss=False):
+    """The DPF without look-ahead (the paper's Fig. dpf with the prior as both proposals),
+    call t for the destinations dest (default 0..n-1) with ancestors anc (None at t = 1):
+      x_t ~ sum_j qbar_j N(f_x(x_a, z_aj), Q_xx): a component by the one-draw local rule
+            (word (t, i, LA_J, 0)), then f_x of it + chol(Q_xx) e (normals (t, i, LA_X, 0));
+            with gauss, the mixture's moment-matched Gaussian instead (Section 4.2): mean
+            mu = sum_j qbar_j f_x,j, covariance Q_xx + sum_j qbar_j (f_x,j - mu)(f_x,j - mu)^T;
+      b = local systematic resampling by lq_aj + log N(x_t; f_x,j, Q_xx) (word (t, i, INNER, 0));
+      z_t^j from the transition's conditional given x_t out of z_ab_j (normals (t, i, PROP, j));
+      lq = ell - LSE ell with ell = log p(y_t | x_t, z_t^j); log w = LSE ell - log M.
+    Returns x (n, d1), z (n, M, d2), lq (n, M), lw (n,)."""
+    d1, d2, M = model.d1, model.d2, z_prev.shape[1]
+    n = x_prev.shape[0] if anc is None else len(anc)
+    dest = np.arange(n) if dest is None else np.asarray(dest)
+    X = np.zeros((n, d1)); Z = np.zeros((n, M, d2)); LQ = np.zeros((n, M)); LW = np.zeros(n)
+    for r in range(n):
+        i = int(dest[r])
+        a = i if anc is None else int(anc[r])
+        fx, fz = model.transition(x_prev[a][None, :], z_prev[a], t - 1)
+        qbar = np.exp(lq_prev[a] - lq_prev[a].max())
+        e = oracle.normals(seed, 0, t, i, oracle.P_LA_X, 0, d1, lib)
+        if gauss:
+            qn = qbar / qbar.sum()
+            mu = qn @ fx
+            dev = fx - mu
+            xt = mu + np.linalg.cholesky(model.Qxx + (dev * qn[:, None]).T @ dev) @ e
+        else:
+            c = int(oracle.sys_local(qbar, 1, _word(seed, t, i, oracle.P_LA_J, 0, lib), lib)[0])
+            xt = model.draw_x(fx[c], e)
+        alpha = lq_prev[a] + model.log_px(xt[None, :], fx)
+        b = oracle.sys_local(np.exp(alpha - alpha.max()), M, _word(seed, t, i, oracle.P_INNER, 0, lib), lib)
+        eps = oracle.normals_many(seed, 0, t, np.full(M, i), oracle.P_PROP, np.arange(M), d2, lib)
+        zt = model.draw_z(fz[b], fx[b], xt[None, :], eps)
+        ell = model.log_py(y, np.broadcast_to(xt, (M, d1)), zt)
+        l = _lse(ell)
+        X[r], Z[r], LQ[r], LW[r] = xt, zt, ell - l, l - np.log(M)
+    return X, Z, LQ, LW
+
+
+def run_std(model, seed, ys, N, M, lib, gauss=False):
+    """Filtered means (T, d) and log-evidence increments of the DPF without look-ahead,
+    resampling the outer particles every call (word (t, 0, OUTER, 0)); the mean weighs
+    each outer particle by its weight, with the z part sum_j qbar_j z_j."""
+    x, z, lq = init(model, N, M, seed, lib)
+    anc = None
+    means, lz = [], []
+    for t, y in enumerate(ys, start=1):
+        x, z, lq, lw = std_step(model, seed, t, float(np.ravel(y)[0]), x, z, lq, anc, lib, gauss=gauss)
+        W = np.exp(lw - lw.max())
+        zm = np.einsum("nm,nmc->nc", np.exp(lq), z)
+        means.append(np.concatenate([W @ x, W @ zm]) / W.sum())
+        lz.append(_lse(lw) - np.log(N))
+        anc = oracle.sys_global(W, _word(seed, t, 0, oracle.P_OUTER, 0, lib), lib)
     return np.array(means), np.array(lz)
 
 

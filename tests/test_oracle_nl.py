@@ -15,6 +15,10 @@
   the LA-DPF miss it.
 * Model 2: the LA-DPF agrees with a bootstrap particle filter of many particles, in the
   filtered means and the log-evidence increments.
+* The DPF without look-ahead: model 1 against the grid filter, with the Monte Carlo
+  mixture prior and with its Gaussian approximation, and planted mistakes miss it; on model
+  2, whose x transition is free of z, the Gaussian approximation is the mixture itself, so
+  both forms give the same particles.
 """
 import numpy as np
 import pytest
@@ -173,3 +177,36 @@ def test_model2_la_dpf_agrees_with_pf(lib):
     ml, ll = nl.run_la_dpf(m, 4, ys, 600, 128, 8, lib)
     assert np.abs((ml - mp) / sp).max() < 0.15
     assert np.abs(ll - lp).max() < 0.15
+
+
+def _std_errors(model, ys, gm, gs, glz, lib, N=600, gauss=False):
+    ms, lz = nl.run_std(model, 3, ys, N, 32, lib, gauss=gauss)
+    return np.abs((ms - gm) / gs).max(), np.abs(lz - glz).max()
+
+
+@pytest.mark.parametrize("gauss", [False, True])
+def test_dpf_matches_the_grid_filter(grid1, lib, gauss):
+    ys, gm, gs, glz = grid1
+    # the Gaussian form approximates the mixture prior of x_t: more outer particles
+    em, ez = _std_errors(nl.PaperModel(1), ys, gm, gs, glz, lib, N=2000 if gauss else 600, gauss=gauss)
+    assert em < 0.2 and ez < 0.2, (em, ez)
+
+
+@pytest.mark.parametrize("name", ["no_px_factor", "no_coupling", "time_off_by_one"])
+def test_dpf_planted_mistake_misses_the_grid_filter(grid1, lib, name):
+    ys, gm, gs, glz = grid1
+    em, ez = _std_errors(_plant(name), ys, gm, gs, glz, lib)
+    assert em >= 0.2 or ez >= 0.2, (name, em, ez)
+
+
+def test_dpf_gaussian_form_is_exact_when_x_is_free_of_z(lib):
+    m = nl.PaperModel(2)
+    N, M, seed = 40, 16, 5
+    x, z, lq = nl.init(m, N, M, seed, lib)
+    lq = lq + np.random.default_rng(0).normal(size=lq.shape)  # unequal inner weights
+    lq -= np.log(np.exp(lq).sum(1, keepdims=True))
+    anc = np.random.default_rng(1).integers(0, N, N)
+    a = nl.std_step(m, seed, 3, 0.4, x, z, lq, anc, lib, gauss=False)
+    b = nl.std_step(m, seed, 3, 0.4, x, z, lq, anc, lib, gauss=True)
+    for u, v in zip(a, b):
+        np.testing.assert_allclose(u, v, rtol=0, atol=1e-12)
