@@ -633,39 +633,47 @@ def run_compare(args):
 def run_table2(args):
     """The Gaussian approximation of the mixture prior against its Monte Carlo evaluation
     (Section 4.2, Table 2), as the paper runs it: the DPF without look-ahead with N = 100,
-    M = 19, 100 runs, here on lg4 (x depends on z) in FP32 over 50 steps; average RMSE of the
-    filtered mean against the true state, per block, and the time of a run."""
+    M = 19 and 100 runs, in FP32, on the paper's model 1 (Table 1) over 250 steps, and on
+    lg4 (x depends on z linearly) over 50 steps. Reports the RMSE of the filtered mean against
+    the true state per block (x, z), averaged over the runs, and the time of a run."""
     import numpy as np
     import torch
 
     from paper_1203_2394_gb300 import dpf, workloads
 
     torch.cuda.set_device(0)
+    N, M, R = 100, 19, 100
     spec = workloads.make_model("lg4", 0)
-    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
-    N, M, T, R = 100, 19, 50, 100
-    d1 = spec.d1
-    res = {False: [], True: []}
-    t0 = time.perf_counter()
-    for r in range(R):
-        s_true, ys = workloads.simulate(spec, T, 1000 + r)
-        for gauss in (False, True):
-            f = dpf.StandardDPF(model, d1, spec.d2, N, M, seed=r)
-            f.set_gaussian_approx(gauss)
-            means = np.array([f.step(ys[t].astype(np.float32))[0] for t in range(T)])
-            f.close()
-            err = means - s_true[1:]
-            res[gauss].append((np.sqrt(np.mean(err[:, :d1] ** 2)), np.sqrt(np.mean(err[:, d1:] ** 2))))
-    wall = time.perf_counter() - t0
-    mc, ga = np.array(res[False]), np.array(res[True])
+    cases = [("model1", dpf.PaperModel(1), 1, 1, 250,
+              lambda r, T: workloads.simulate_paper(1, T, 1000 + r)),
+             ("lg4", dpf.Model.from_spec(spec, dpf.DPF_F32), spec.d1, spec.d2, 50,
+              lambda r, T: workloads.simulate(spec, T, 1000 + r))]
+    out, wall = {}, {}
+    for name, model, d1, d2, T, sim in cases:
+        res = {False: [], True: []}
+        t0 = time.perf_counter()
+        for r in range(R):
+            s_true, ys = sim(r, T)
+            for gauss in (False, True):
+                f = dpf.StandardDPF(model, d1, d2, N, M, seed=r)
+                f.set_gaussian_approx(gauss)
+                means = np.array([f.step(ys[t].astype(np.float32))[0] for t in range(T)])
+                f.close()
+                err = means - s_true[1:]
+                res[gauss].append((np.sqrt(np.mean(err[:, :d1] ** 2)), np.sqrt(np.mean(err[:, d1:] ** 2))))
+        wall[name] = time.perf_counter() - t0
+        mc, ga = np.array(res[False]), np.array(res[True])
+        out[name] = {"steps": T, "ms_per_step": wall[name] / (2 * R * T) * 1e3,
+                     "gaussian": {"rmse_x": float(ga[:, 0].mean()), "rmse_z": float(ga[:, 1].mean())},
+                     "monte_carlo": {"rmse_x": float(mc[:, 0].mean()), "rmse_z": float(mc[:, 1].mean())}}
     line = {
-        "metric": "RMSE against the true state (mean over runs)", "value": float(ga[:, 0].mean()),
-        "unit": "state units", "n_gpus": 1, "steps": T, "warmup": 0, "ms_per_step": wall / (2 * R * T) * 1e3,
+        "metric": "RMSE against the true state (mean over runs)", "value": out["model1"]["gaussian"]["rmse_x"],
+        "unit": "state units", "n_gpus": 1, "steps": 250, "warmup": 0, "ms_per_step": out["model1"]["ms_per_step"],
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"Gaussian against Monte Carlo evaluation of the mixture prior: DPF without "
-                               f"look-ahead, lg4, N={N}, M={M}, {R} runs of {T} steps, FP32"},
-        "gaussian": {"rmse_x": float(ga[:, 0].mean()), "rmse_z": float(ga[:, 1].mean())},
-        "monte_carlo": {"rmse_x": float(mc[:, 0].mean()), "rmse_z": float(mc[:, 1].mean())},
+                               f"look-ahead, N={N}, M={M}, {R} runs, FP32, on the paper's model 1 (250 steps) and "
+                               f"on lg4 (50 steps); value: model 1, Gaussian, RMSE of x"},
+        **out,
         "paper_table2_model1": {"gaussian": {"rmse_x": 1.3197, "rmse_z": 1.1705},
                                 "monte_carlo": {"rmse_x": 1.3216, "rmse_z": 1.1640}},
     }
@@ -675,8 +683,8 @@ def run_table2(args):
 
 def run_paper(args):
     """The paper's comparison (Section 4.1) on its own benchmark models (Table 1): for
-    model 1 and model 2, the LA-DPF (N = 65536, M = 128, L = 16) and the bootstrap particle
-    filter with N (M + 1) = 8,454,144 particles, FP32, over R runs of 250 steps (the paper's
+    model 1 and model 2, the LA-DPF (N = 65536, M = 128, L = 16), the DPF without look-ahead
+    (same N, M) and the bootstrap particle filter with N (M + 1) = 8,454,144 particles, FP32, over R runs of 250 steps (the paper's
     horizon) on seeded trajectories: the RMSE of the filtered mean against the true state per
     block (x, z), averaged over the runs, and the time per step (device observations, CUDA
     events over the steps after the first 10)."""
@@ -710,12 +718,15 @@ def run_paper(args):
     out = {}
     for kind in (1, 2):
         pm = dpf.PaperModel(kind)
-        res = {"ladpf": [], "pf": []}
+        res = {"ladpf": [], "dpf": [], "pf": []}
         for r in range(R):
             s_true, ys = workloads.simulate_paper(kind, T, 100 + r)
             yd = torch.tensor(ys.astype(np.float32), device="cuda")
             f = dpf.Filter(pm, pm.d1, pm.d2, N, M, L, seed=r)
             res["ladpf"].append(run(f, yd, s_true, pm.d, pm.d1))
+            f.close()
+            f = dpf.StandardDPF(pm, pm.d1, pm.d2, N, M, seed=r)
+            res["dpf"].append(run(f, yd, s_true, pm.d, pm.d1))
             f.close()
             f = dpf.ParticleFilter(pm, pm.d1, pm.d2, N * (M + 1), seed=r)
             res["pf"].append(run(f, yd, s_true, pm.d, pm.d1))
@@ -731,7 +742,7 @@ def run_paper(args):
         "warmup": W0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"the paper's models 1 and 2 (Table 1): LA-DPF N={N}, M={M}, L={L} against the "
-                               f"bootstrap PF with N(M+1)={N * (M + 1)} particles, FP32, {R} runs of {T} steps; "
+                               f"DPF without look-ahead (same N, M) and the bootstrap PF with N(M+1)={N * (M + 1)} particles, FP32, {R} runs of {T} steps; "
                                f"value: model 1's LA-DPF"},
         **out,
     }

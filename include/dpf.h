@@ -92,8 +92,9 @@ typedef struct {
  *            the x noises ~ N(0, I);
  * e ~ N(0, 1), s_0 ~ N(0, I); t in the sine and cosine is the source step of the
  * transition. The inner draws are conditioned on x_t through the noise covariance. With
- * these kinds dpf_create (L <= 32) and dpf_create_pf serve the models; the batched form,
- * the learned proposal and dpf_create_std do not.
+ * these kinds dpf_create (L <= 32), dpf_create_pf and dpf_create_std (with
+ * dpf_set_gaussian_approx) serve the models; the batched form and the learned proposal
+ * do not.
  */
 
 /*

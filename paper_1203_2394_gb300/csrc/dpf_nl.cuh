@@ -463,6 +463,189 @@ __global__ void __launch_bounds__(256) nl_pf_kernel(const __grid_constant__ NLAr
   }
 }
 
+// Bytes of shared memory of nl_std_kernel: the ancestor's z, f_x and f_z per inner
+// particle, cum (M words) and the reductions (32 floats, 64 words).
+__host__ __device__ constexpr size_t nl_std_smem_bytes(int D1, int D2, int M) {
+  return 4 * ((size_t)(2 * D2 + D1) * M + (size_t)((M + 3) & ~3) + 32 + 64) + 16;
+}
+
+// The DPF without look-ahead for these models (the paper's Fig. dpf with the prior as both
+// proposals), call t for each outer particle i with ancestor a (i itself at t = 1):
+//   x_t ~ sum_j qbar_j N(f_x(x_a, z_aj), Q_xx): the component by the one-draw local rule
+//         (word (t, i, LA_J, 0)), then the Gaussian draw (normals (t, i, LA_X, 0)); with the
+//         Gaussian approximation (Section 4.2) the mixture's moment-matched Gaussian instead,
+//         mean sum_j qbar_j f_x,j and covariance Q_xx + sum_j qbar_j (f_x,j - mu)(f_x,j - mu)^T;
+//   b = local resampling by lq_aj + log N(x_t; f_x,j, Q_xx) (word (t, i, INNER, 0));
+//   z_t^j = f_z,b + G (x_t - f_x,b) + chol(S) e_j (normals (t, i, PROP, j));
+//   lq = ell - LSE ell, ell = log p(y_t | x_t, z_t^j); log w = LSE ell - log M.
+template <class Mod>
+__global__ void __launch_bounds__(1024) nl_std_kernel(const __grid_constant__ NLArgs a, int gauss) {
+  constexpr int D1 = Mod::D1, D2 = Mod::D2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int M = a.M, tid = threadIdx.x;
+  const bool act = tid < M;
+  const long long N = a.N, NM = N * (long long)M;
+  float* zs = (float*)smem_raw;  // [D2][M] the ancestor's z
+  float* fxs = zs + D2 * M;      // [D1][M]
+  float* fzs = fxs + D1 * M;     // [D2][M]
+  uint32_t* cum = (uint32_t*)(fzs + D2 * M);  // [M]
+  float* red = (float*)(cum + ((M + 3) & ~3));
+  uint32_t* redU = (uint32_t*)(red + 32);
+  const float NEG = neg_inf<float>();
+  const float LOG2E = (float)LOG2E_D;
+  if (blockIdx.x == 0 && tid == 0) *a.Csum = 0ull;
+  for (long long i = blockIdx.x; i < N; i += gridDim.x) {
+    const long long g = a.first ? i : (long long)a.anc[i];
+    float xa[D1], fxj[D1], fzj[D2];
+#pragma unroll
+    for (int c = 0; c < D1; ++c) xa[c] = a.x_old[g * a.xp + c];
+    float lqj = NEG;
+#pragma unroll
+    for (int c = 0; c < D1; ++c) fxj[c] = 0.f;
+    if (act) {
+      float zj[D2];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) {
+        zj[c] = a.z_old[c * NM + g * M + tid];
+        zs[c * M + tid] = zj[c];
+      }
+      lqj = a.lq_old[g * M + tid];
+      Mod::fx(xa, zj, a.tt_cur, fxj);
+      Mod::fz(xa, zj, a.tt_cur, fzj);
+#pragma unroll
+      for (int c = 0; c < D1; ++c) fxs[c * M + tid] = fxj[c];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) fzs[c * M + tid] = fzj[c];
+    }
+    // ---- x_t from the mixture prior ----
+    const float mx = bmax(lqj, red);
+    {
+      uint32_t cw[1] = {act ? (uint32_t)floor(exp2f((lqj - mx) * LOG2E) * a.scaleM) : 0u}, incl[1];
+      bscan_planes<1>(cw, incl, redU);
+      if (act) cum[tid] = incl[0];
+    }
+    __syncthreads();
+    float e1[D1], xt[D1];
+    normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, 0u, e1);
+    if (gauss) {
+      const float qj = act ? expf(lqj - mx) : 0.f;
+      const float qs = bsum(qj, red);
+      float mu[D1];
+#pragma unroll
+      for (int r = 0; r < D1; ++r) mu[r] = bsum(qj * fxj[r], red) / qs;
+      float C[D1][D1];
+#pragma unroll
+      for (int r = 0; r < D1; ++r)
+#pragma unroll
+        for (int c = 0; c < D1; ++c)
+          if (c <= r) {
+            float q = 0.f;  // Q_xx = L_qx L_qx^T
+#pragma unroll
+            for (int k = 0; k < D1; ++k) q += Mod::Lqx(r, k) * Mod::Lqx(c, k);
+            C[r][c] = bsum(qj * (fxj[r] - mu[r]) * (fxj[c] - mu[c]), red) / qs + q;
+          }
+      // Cholesky of the covariance in place (lower triangle), the same in every thread
+#pragma unroll
+      for (int c = 0; c < D1; ++c) {
+        float d = C[c][c];
+#pragma unroll
+        for (int k = 0; k < D1; ++k)
+          if (k < c) d -= C[c][k] * C[c][k];
+        d = sqrtf(d);
+        C[c][c] = d;
+#pragma unroll
+        for (int r = 0; r < D1; ++r) {
+          if (r > c) {
+            float v = C[r][c];
+#pragma unroll
+            for (int k = 0; k < D1; ++k)
+              if (k < c) v -= C[r][k] * C[c][k];
+            C[r][c] = v / d;
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < D1; ++r) {
+        float v = mu[r];
+#pragma unroll
+        for (int c = 0; c < D1; ++c)
+          if (c <= r) v += C[r][c] * e1[c];
+        xt[r] = v;
+      }
+    } else {
+      const int jm = sys_local_pick(cum, M, cum[M - 1], 1, 0, rand_word(a.key, a.t, (uint32_t)i, P_LA_J, 0u));
+#pragma unroll
+      for (int r = 0; r < D1; ++r) {
+        float v = fxs[r * M + jm];
+#pragma unroll
+        for (int c = 0; c < D1; ++c)
+          if (c <= r) v += Mod::Lqx(r, c) * e1[c];
+        xt[r] = v;
+      }
+    }
+    // ---- local resampling by q = qbar p(x_t | x_{t-1}, z) ----
+    float alpha = NEG;
+    if (act) {
+      float r[D1];
+#pragma unroll
+      for (int c = 0; c < D1; ++c) r[c] = xt[c] - fxj[c];
+      alpha = lqj + nl_quad_x<Mod>(r);
+    }
+    const float amax = bmax(alpha, red);  // its barriers also end every read of cum above
+    {
+      uint32_t cw[1] = {act ? (uint32_t)floor(exp2f((alpha - amax) * LOG2E) * a.scaleM) : 0u}, incl[1];
+      bscan_planes<1>(cw, incl, redU);
+      if (act) cum[tid] = incl[0];
+    }
+    __syncthreads();
+    const uint32_t C = cum[M - 1];
+    const uint32_t uin = rand_word(a.key, a.t, (uint32_t)i, P_INNER, 0u);
+    // ---- propagation given x_t and the weights of y_t ----
+    float zn[D2];
+    float ell = NEG;
+#pragma unroll
+    for (int c = 0; c < D2; ++c) zn[c] = 0.f;
+    if (act) {
+      const int b = sys_local_pick(cum, M, C, M, tid, uin);
+      float fxb[D1], fzb[D2], e[D2];
+#pragma unroll
+      for (int c = 0; c < D1; ++c) fxb[c] = fxs[c * M + b];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) fzb[c] = fzs[c * M + b];
+      normals<D2>(a.key, a.t, (uint32_t)i, P_PROP, (uint32_t)tid, e);
+      nl_zdraw<Mod>(fzb, fxb, xt, e, zn);
+      ell = nl_loglik<Mod>(xt, zn, a.y_cur);
+    }
+    const float lmax = bmax(ell, red);
+    const float lsum = bsum(act ? expf(ell - lmax) : 0.f, red);
+    const float lse = lmax + logf(lsum);
+    const float W = act ? expf(ell - lse) : 0.f;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < D2; ++c) a.z_new[c * NM + i * M + tid] = zn[c];
+      a.lq_new[i * M + tid] = ell - lse;
+    }
+#pragma unroll
+    for (int c = 0; c < D2; ++c) {
+      const float v = bsum(W * zn[c], red);
+      if (tid == 0) a.zm[c * N + i] = v;
+    }
+    if (tid == 0) {
+      const float lwi = lse - a.logL;  // logL carries log M here
+#pragma unroll
+      for (int c = 0; c < D1; ++c) {
+        a.x_new[i * a.xp + c] = xt[c];
+        a.xm[c * N + i] = xt[c];
+      }
+      a.lw[i] = lwi;
+      if (lwi != lwi) atomicOr(a.err, ERR_NUMERIC);
+      const unsigned long long key = order_key(lwi);
+      if (lwi == lwi && key > *(volatile unsigned long long*)a.lwmax_key) atomicMax(a.lwmax_key, key);
+    }
+    __syncthreads();  // the staged rows are free for the next group
+  }
+}
+
 }  // namespace dpf
 
 #include "dpf_variant.cuh"
@@ -539,7 +722,13 @@ struct PaperVariant {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
     }
-    const unsigned blocks = (unsigned)std::min<long long>(x.N, 152 * 4);
+    // a persistent grid: every SM filled with as many CTAs as fit at once
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nt, sm);
+    const long long fill = (long long)std::max(occ, 1) * std::max(sms, 1);
+    const unsigned blocks = (unsigned)std::min<long long>(x.N, fill);
     k<<<blocks, nt, sm, x.stream>>>(a);
     return cuda_error(cudaGetLastError(), "paper-model step launch");
   }
@@ -570,6 +759,44 @@ struct PaperVariant {
     nl_pf_kernel<Mod><<<blocks, 256, 0, x.stream>>>(a);
     return cuda_error(cudaGetLastError(), "paper-model particle filter launch");
   }
+  static dpf_status std_step(Ctx& x) {
+    const long long t = x.t + 1;
+    const int so = (int)((t + 1) % 2), sn = (int)(t % 2);
+    NLArgs a{};
+    a.x_old = (const float*)x.x[so];
+    a.z_old = (const float*)x.z[so];
+    a.lq_old = (const float*)x.lq[so];
+    a.x_new = (float*)x.x[sn];
+    a.z_new = (float*)x.z[sn];
+    a.lq_new = (float*)x.lq[sn];
+    a.lw = (float*)x.lw;
+    a.xm = (float*)x.xm;
+    a.zm = (float*)x.zm;
+    a.anc = x.anc;
+    a.y_cur = (const float*)x.yb + (t % 2) * x.dy;
+    a.lwmax_key = x.lwmax_key;
+    a.Csum = x.Csum;
+    a.err = x.err;
+    a.N = x.N;
+    a.M = x.M;
+    a.xp = x.xp;
+    a.t = (uint32_t)t;
+    a.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    terms(t - 1, a.tt_cur);
+    a.scaleM = (float)std::ldexp(1.0, 31 - ceil_log2_i(x.M));
+    a.logL = (float)std::log((double)x.M);
+    a.first = t == 1 ? 1 : 0;
+    const int nt = (x.M + 31) / 32 * 32;
+    const size_t sm = nl_std_smem_bytes(D1, D2, x.M);
+    auto k = nl_std_kernel<Mod>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+    }
+    const unsigned blocks = (unsigned)std::min<long long>(x.N, 152 * 8);
+    k<<<blocks, nt, sm, x.stream>>>(a, x.std_gauss ? 1 : 0);
+    return cuda_error(cudaGetLastError(), "paper-model DPF step launch");
+  }
   static dpf_status outer(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
     return outer_stage<float, D1, D2>(x, mean_out, logz_out, st);
   }
@@ -584,6 +811,7 @@ struct PaperVariant {
     v.step = &step;
     v.outer = &outer;
     v.pf_step = &pf_step;
+    v.std_step = &std_step;
     v.outer_args = nullptr;
     v.outer_batch = nullptr;
     v.scan_batch = nullptr;

@@ -12,6 +12,9 @@ DPF_MODEL_PAPER1 / DPF_MODEL_PAPER2, FP32) against the oracle of oracle/nl.py.
   Cases with ragged M (45, 20 threads of a warp) and L (7) and the largest L (32).
 * The filtered mean equals the oracle's weighted look-ahead estimate.
 * The bootstrap particle filter, teacher-forced: the same particles and weights.
+* The DPF without look-ahead (dpf_create_std), teacher-forced, with the Monte Carlo mixture
+  prior and its Gaussian approximation: the same particles and weights in all but 1% of
+  the groups, the outer ancestors bit for bit.
 * The benchmark's size (N = 65536, M = 128, L = 16): sampled groups of two calls.
 """
 import numpy as np
@@ -162,6 +165,39 @@ def test_paper_benchmark_size_sampled(kind, lib):
     assert bad <= 3, bad
 
 
+@pytest.mark.parametrize("kind,M,gauss", [(1, 32, False), (1, 32, True), (2, 19, False), (2, 64, True)])
+def test_paper_dpf_teacher_forced(kind, M, gauss, lib):
+    from paper_1203_2394_gb300 import dpf
+    N, seed, T = 300, 9, 5
+    m = nl.PaperModel(kind)
+    pm = dpf.PaperModel(kind)
+    f = dpf.StandardDPF(pm, pm.d1, pm.d2, N, M, seed)
+    f.set_gaussian_approx(gauss)
+    _, ys = workloads.simulate_paper(kind, T, 2)
+    x, z, lq = state_from_gpu(f)
+    ox, oz, olq = nl.init(m, N, M, seed, lib)
+    assert np.max(rel(x, ox)) <= 2e-6 and np.max(rel(z, oz)) <= 2e-6
+    anc, bad = None, 0
+    for t in range(1, T + 1):
+        y = np.float32(ys[t - 1, 0])
+        mean, _ = f.step(np.array([y]))
+        gx, gz, glq = state_from_gpu(f)
+        glw = f.read("lw").astype(np.float64)
+        ex, ez, elq, elw = nl.std_step(m, seed, t, float(y), x, z, lq, anc, lib, gauss=gauss)
+        ok = (np.all(rel(gx, ex) <= 2e-5, axis=1) & np.all(rel(gz, ez) <= 2e-5, axis=(1, 2))
+              & np.all(rel(glq, elq) <= 2e-4, axis=1) & (rel(glw, elw) <= 2e-4))
+        bad += int((~ok).sum())
+        W = np.exp(glw - glw.max())
+        W /= W.sum()
+        zmean = np.einsum("nm,nmc->nc", np.exp(glq), gz)
+        assert np.max(rel(mean, np.concatenate([W @ gx, W @ zmean]))) <= 1e-4
+        anc = f.read("anc")
+        wout = f.read("wout").astype(np.float64)
+        np.testing.assert_array_equal(anc, oracle.sys_global(wout, word(seed, t, 0, oracle.P_OUTER), lib))
+        x, z, lq = gx, gz, glq
+    assert bad <= max(2, N * T // 100), bad
+
+
 def test_paper_model_rejections():
     from paper_1203_2394_gb300 import dpf
     pm = dpf.PaperModel(1)
@@ -169,5 +205,3 @@ def test_paper_model_rejections():
         dpf.Filter(pm, 1, 1, 100, 32, 33, 0)  # L > 32: the draws' weights are one warp's
     with pytest.raises(dpf.DpfError):
         dpf.Filter(pm, 2, 0, 100, 32, 8, 0)  # d1 = d2 = 1 for model 1
-    with pytest.raises(dpf.DpfError):
-        dpf.StandardDPF(pm, 1, 1, 100, 32, 0)  # no DPF step for these models
