@@ -5,7 +5,10 @@
 // x_{t+1} | s_t ~ N(f_x, Q_xx) and z_{t+1} | x_{t+1}, s_t ~ N(f_z + G (x_{t+1} - f_x), S),
 // G = Q_zx Q_xx^-1, S = Q_zz - G Q_xz. One CTA a group, one thread an inner particle; the
 // look-ahead's L x M pairs are evaluated pair by pair (the inner draw depends on the
-// look-ahead draw through G), then reduced a row a warp. The outer stages are the filter's.
+// look-ahead draw through G) into shared memory, then a warp a draw reduces both rows and
+// the row's softmax-weighted inner draws. The observation is h_x(x) + h_z(z), so h_x is
+// taken once a draw and, where G = 0, h_z once an inner particle. The outer stages are the
+// filter's.
 //
 // Readings: the sine and cosine terms take the source step of the transition (as the
 // growth map's cosine does); model 2's z_{2,t+1} adds z_{1,t+1}, noise included, so its z
@@ -26,9 +29,11 @@ struct PaperModel1 {
   __device__ static void fz(const float (&x)[1], const float (&z)[1], const float* tt, float (&o)[1]) {
     o[0] = x[0] + 0.5f * z[0] + 25.f * z[0] / (1.f + z[0] * z[0]) + tt[0];
   }
-  __device__ static void h(const float (&x)[1], const float (&z)[1], float (&o)[1]) {
-    o[0] = atanf(x[0]) + z[0] * z[0] / 20.f;
-  }
+  // y = h_x(x) + h_z(z) + e
+  __device__ static float hx(const float (&x)[1]) { return atanf(x[0]); }
+  __device__ static float hz(const float (&z)[1]) { return z[0] * z[0] / 20.f; }
+  __device__ static void h(const float (&x)[1], const float (&z)[1], float (&o)[1]) { o[0] = hx(x) + hz(z); }
+  static constexpr bool GZERO = false;  // the z draw depends on x_t (G != 0)
   // 8 cos(1.2 s) at the source step s (on the host, in double)
   static void terms(double s, float (&tt)[NT]) { tt[0] = (float)(8.0 * std::cos(1.2 * s)); }
   // chol(Q_xx), its inverse, G, chol(S), R^-1/2, and -1/2 log det(2 pi R)
@@ -55,9 +60,10 @@ struct PaperModel2 {
     o[0] = z1;
     o[1] = z1 + 0.5f * z[1] + 25.f * z[1] / (1.f + z[1] * z[1]) + tt[1];
   }
-  __device__ static void h(const float (&x)[2], const float (&z)[2], float (&o)[1]) {
-    o[0] = (x[0] + x[1]) / (1.f + x[0] * x[0]) + atanf(z[0]) + z[1] * z[1] / 20.f;
-  }
+  __device__ static float hx(const float (&x)[2]) { return (x[0] + x[1]) / (1.f + x[0] * x[0]); }
+  __device__ static float hz(const float (&z)[2]) { return atanf(z[0]) + z[1] * z[1] / 20.f; }
+  __device__ static void h(const float (&x)[2], const float (&z)[2], float (&o)[1]) { o[0] = hx(x) + hz(z); }
+  static constexpr bool GZERO = true;  // x and z noises independent: the z draw is free of x_t
   static void terms(double s, float (&tt)[NT]) {
     tt[0] = (float)(8.0 * std::sin(s));
     tt[1] = (float)(8.0 * std::cos(1.2 * s));
@@ -174,10 +180,12 @@ __global__ void nl_init_kernel(float* z, float* lq, float* x, long long N, int M
   }
 }
 
-// Bytes of shared memory of nl_step_kernel: the group's arrays, cum (max(M, L) words) and
-// the reductions (32 floats, 64 words).
+// Bytes of shared memory of nl_step_kernel: the group's per-inner-particle arrays (z, lq,
+// f_x, the draw's base, h_z), the two L x M pair arrays, the per-draw arrays (two draws of
+// d1, h_x, the ancestor's weights, the two row log-sum-exps, the z row means), cum
+// (max(M, L) words) and the reductions (32 floats, 64 words).
 __host__ __device__ constexpr size_t nl_smem_bytes(int D1, int D2, int M, int L) {
-  return 4 * ((size_t)(D2 * M + M + D1 * M + D2 * M + 2 * L * M + L * D1 + L + L * D1 + L + 2 * L) +
+  return 4 * ((size_t)(2 * D2 + D1 + 2) * M + 2 * (size_t)L * M + (size_t)(2 * D1 + D2 + 4) * L +
               (size_t)((((M > L ? M : L) + 3) & ~3)) + 32 + 64) + 16;
 }
 
@@ -189,18 +197,21 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
   const int M = a.M, L = a.L, tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   const bool act = tid < M;
   const long long N = a.N, NM = N * (long long)M;
-  float* zs = (float*)smem_raw;  // [D2][M] the ancestor's z, then the group's own
-  float* lqs = zs + D2 * M;      // [M]
+  static_assert(Mod::DY == 1, "the look-ahead's pair loop takes a scalar observation");
+  float* zs = (float*)smem_raw;  // [D2][M] the ancestor's z
+  float* lqs = zs + D2 * M;      // [M] the ancestor's lq, then the group's own
   float* fxk = lqs + M;          // [D1][M] f_x(x, z_k) of the look-ahead
-  float* fzk = fxk + D1 * M;     // [D2][M]
-  float* E1 = fzk + D2 * M;      // [L][M] alpha + ell
+  float* bk = fxk + D1 * M;      // [D2][M] f_z(x, z_k) + chol(S) e_k: the draw's base
+  float* hzk = bk + D2 * M;      // [M] h_z of the base (models with G = 0)
+  float* E1 = hzk + M;           // [L][M] alpha + ell of the pairs
   float* E2 = E1 + L * M;        // [L][M] alpha
   float* xbs = E2 + L * M;       // [L][D1] the look-ahead draws
-  float* lwhs = xbs + L * D1;    // [L] the ancestor's per-draw weights
+  float* hxs = xbs + L * D1;     // [L] h_x of the draws
+  float* lwhs = hxs + L;         // [L] the ancestor's per-draw weights
   float* xbbs = lwhs + L;        // [L][D1] the ancestor's draws
-  float* pis = xbbs + L * D1;    // [L] the draw weights
-  float* rowm = pis + L;         // [2L] LSE_k of E1 and E2 per draw
-  uint32_t* cum = (uint32_t*)(rowm + 2 * L);  // [max(M, L)]
+  float* rowm = xbbs + L * D1;   // [2L] LSE_k of alpha + ell and of alpha per draw
+  float* zrow = rowm + 2 * L;    // [L][D2] sum_k softmax_k(alpha + ell) zhat per draw
+  uint32_t* cum = (uint32_t*)(zrow + L * D2);  // [max(M, L)]
   float* red = (float*)(cum + (((M > L ? M : L) + 3) & ~3));
   uint32_t* redU = (uint32_t*)(red + 32);
   const float NEG = neg_inf<float>();
@@ -298,14 +309,26 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
       __syncthreads();  // every gather from the ancestor's rows is done
     }
     // ======== look-ahead of step t from (x, z, lq) with y_t ========
+    // per inner particle k: f_x, the base f_z + chol(S) e_k of its draw (the noise e_k shared
+    // by the L draws) and, when the draw is free of x_t, h_z of it
     if (act) {
-      float fxv[D1], fzv[D2];
+      float fxv[D1], fzv[D2], ek[D2], zb[D2];
       Mod::fx(x, zk, a.tt_cur, fxv);
       Mod::fz(x, zk, a.tt_cur, fzv);
+      normals<D2>(a.key, a.t, (uint32_t)i, P_LA_Z, (uint32_t)tid, ek);
+#pragma unroll
+      for (int r = 0; r < D2; ++r) {
+        float v = fzv[r];
+#pragma unroll
+        for (int c = 0; c < D2; ++c)
+          if (c <= r) v += Mod::LS(r, c) * ek[c];
+        zb[r] = v;
+        bk[r * M + tid] = v;
+      }
 #pragma unroll
       for (int c = 0; c < D1; ++c) fxk[c * M + tid] = fxv[c];
-#pragma unroll
-      for (int c = 0; c < D2; ++c) fzk[c * M + tid] = fzv[c];
+      if (Mod::GZERO) hzk[tid] = Mod::hz(zb);
+      lqs[tid] = lqk;
     }
     {
       const float mx = bmax(lqk, red);
@@ -317,7 +340,7 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
     if (tid < L) {  // draw m from the mixture: a component by qbar, then the Gaussian
       const int m = tid;
       const int jm = sys_local_pick(cum, M, cum[M - 1], 1, 0, rand_word(a.key, a.t, (uint32_t)i, P_LA_J, (uint32_t)m));
-      float e1[D1];
+      float e1[D1], xb[D1];
       normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, (uint32_t)m, e1);
 #pragma unroll
       for (int r = 0; r < D1; ++r) {
@@ -325,35 +348,47 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
 #pragma unroll
         for (int c = 0; c < D1; ++c)
           if (c <= r) v += Mod::Lqx(r, c) * e1[c];
+        xb[r] = v;
         xbs[m * D1 + r] = v;
         a.xbb_new[((long long)i * L + m) * D1 + r] = v;
       }
+      hxs[m] = Mod::hx(xb);
     }
     __syncthreads();
-    // the L x M pairs: alpha = lq + log p(xbb_m | x, z_k), zhat = f_z + G (xbb_m - f_x) +
-    // chol(S) e_k (e_k shared by the draws), ell = log p(y_t | xbb_m, zhat)
-    float ek[D2], fxv[D1], fzv[D2];
+    // the L x M pairs, a thread an inner particle k: alpha = lq_k + log p(xbb_m | x, z_k),
+    // zhat = base_k + G (xbb_m - f_x,k), ell = log p(y_t | xbb_m, zhat)
     if (act) {
-      normals<D2>(a.key, a.t, (uint32_t)i, P_LA_Z, (uint32_t)tid, ek);
+      float fxv[D1], zb[D2];
 #pragma unroll
       for (int c = 0; c < D1; ++c) fxv[c] = fxk[c * M + tid];
 #pragma unroll
-      for (int c = 0; c < D2; ++c) fzv[c] = fzk[c * M + tid];
+      for (int c = 0; c < D2; ++c) zb[c] = bk[c * M + tid];
+      const float hz0 = Mod::GZERO ? hzk[tid] : 0.f;
+      const float y0 = a.y_cur[0];
       for (int m = 0; m < L; ++m) {
-        float xb[D1], r[D1], zh[D2];
+        float r[D1], zh[D2];
 #pragma unroll
-        for (int c = 0; c < D1; ++c) {
-          xb[c] = xbs[m * D1 + c];
-          r[c] = xb[c] - fxv[c];
-        }
+        for (int c = 0; c < D1; ++c) r[c] = xbs[m * D1 + c] - fxv[c];
         const float al = lqk + nl_quad_x<Mod>(r);
-        nl_zdraw<Mod>(fzv, fxv, xb, ek, zh);
-        E1[m * M + tid] = al + nl_loglik<Mod>(xb, zh, a.y_cur);
+        float hzv = hz0;
+        if (!Mod::GZERO) {
+#pragma unroll
+          for (int q = 0; q < D2; ++q) {
+            float v = zb[q];
+#pragma unroll
+            for (int c = 0; c < D1; ++c) v += Mod::G(q, c) * r[c];
+            zh[q] = v;
+          }
+          hzv = Mod::hz(zh);
+        }
+        const float res = (y0 - hxs[m] - hzv) * Mod::LrInv(0, 0);
+        E1[m * M + tid] = al + Mod::lognorm_y - 0.5f * res * res;
         E2[m * M + tid] = al;
       }
     }
     __syncthreads();
-    for (int m = w; m < L; m += nw) {  // a warp a draw: LSE_k of both rows
+    // a warp a draw: the log-sum-exps of both rows and the softmax-weighted zhat of row 1
+    for (int m = w; m < L; m += nw) {
       float m1 = NEG, m2 = NEG;
       for (int k = lane; k < M; k += 32) {
         m1 = fmaxf(m1, E1[m * M + k]);
@@ -361,30 +396,54 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
       }
       m1 = warp_max(m1);
       m2 = warp_max(m2);
-      float s1 = 0.f, s2 = 0.f;
+      float xb[D1];
+#pragma unroll
+      for (int c = 0; c < D1; ++c) xb[c] = xbs[m * D1 + c];
+      float s1 = 0.f, s2 = 0.f, za[D2];
+#pragma unroll
+      for (int c = 0; c < D2; ++c) za[c] = 0.f;
       for (int k = lane; k < M; k += 32) {
-        s1 += expf(E1[m * M + k] - m1);
+        const float e = expf(E1[m * M + k] - m1);
+        s1 += e;
         s2 += expf(E2[m * M + k] - m2);
+        float r[D1];
+#pragma unroll
+        for (int c = 0; c < D1; ++c) r[c] = xb[c] - fxk[c * M + k];
+#pragma unroll
+        for (int q = 0; q < D2; ++q) {
+          float v = bk[q * M + k];
+#pragma unroll
+          for (int c = 0; c < D1; ++c) v += Mod::G(q, c) * r[c];
+          za[q] += e * v;
+        }
       }
       s1 = warp_sum(s1);
       s2 = warp_sum(s2);
+#pragma unroll
+      for (int c = 0; c < D2; ++c) za[c] = warp_sum(za[c]);
       if (lane == 0) {
         rowm[2 * m] = m1 + logf(s1);
         rowm[2 * m + 1] = m2 + logf(s2);
+#pragma unroll
+        for (int c = 0; c < D2; ++c) zrow[m * D2 + c] = za[c] / s1;
       }
     }
     __syncthreads();
-    if (tid < 32) {  // per-draw weights, the outer weight, the x part of the mean (L <= 32)
+    if (tid < 32) {  // per-draw weights, the outer weight and the filtered mean (L <= 32)
       const float lwm = tid < L ? rowm[2 * tid] - rowm[2 * tid + 1] : NEG;
       if (tid < L) a.lwh_new[i * L + tid] = lwm;
       const float mx = warp_max(lwm);
       const float p = tid < L ? expf(lwm - mx) : 0.f;
       const float ps = warp_sum(p);
-      if (tid < L) pis[tid] = p / ps;
 #pragma unroll
       for (int c = 0; c < D1; ++c) {
         const float v = warp_sum(tid < L ? p * xbs[tid * D1 + c] : 0.f) / ps;
         if (tid == 0) a.xm[c * N + i] = v;
+      }
+#pragma unroll
+      for (int c = 0; c < D2; ++c) {
+        const float v = warp_sum(tid < L ? p * zrow[tid * D2 + c] : 0.f) / ps;
+        if (tid == 0) a.zm[c * N + i] = v;
       }
       if (tid == 0) {
         const float lwi = mx + logf(ps) - a.logL;
@@ -394,28 +453,7 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
         if (lwi == lwi && key > *(volatile unsigned long long*)a.lwmax_key) atomicMax(a.lwmax_key, key);
       }
     }
-    __syncthreads();
-    // the z part of the mean: sum_m pi_m sum_k exp(E1[m][k] - LSE_m) zhat^(m,k)
-    float acc[D2];
-#pragma unroll
-    for (int c = 0; c < D2; ++c) acc[c] = 0.f;
-    if (act) {
-      for (int m = 0; m < L; ++m) {
-        float xb[D1], zh[D2];
-#pragma unroll
-        for (int c = 0; c < D1; ++c) xb[c] = xbs[m * D1 + c];
-        nl_zdraw<Mod>(fzv, fxv, xb, ek, zh);
-        const float wmk = pis[m] * expf(E1[m * M + tid] - rowm[2 * m]);
-#pragma unroll
-        for (int c = 0; c < D2; ++c) acc[c] += wmk * zh[c];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < D2; ++c) {
-      const float v = bsum(acc[c], red);
-      if (tid == 0) a.zm[c * N + i] = v;
-    }
-    __syncthreads();
+    __syncthreads();  // the group's arrays are free for the next group
   }
 }
 
