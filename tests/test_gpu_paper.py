@@ -9,7 +9,8 @@ DPF_MODEL_PAPER1 / DPF_MODEL_PAPER2, FP32) against the oracle of oracle/nl.py.
   next call's selection equals the oracle's (all but 0.2%), its x_t is the selected draw
   exactly, and its inner update matches the oracle's in all but 1% of the groups (an FP32
   weight that lands on the other side of a systematic point moves one inner particle).
-  Cases with ragged M (45, 20 threads of a warp) and L (7) and the largest L (32).
+  Cases with ragged M (45, 20 threads of a warp) and L (7), the largest L (32), and edge
+  sizes (N = M = L = 1; M = 1 with L = 32; M = 700).
 * The filtered mean equals the oracle's weighted look-ahead estimate.
 * The bootstrap particle filter, teacher-forced: the same particles and weights.
 * The DPF without look-ahead (dpf_create_std), teacher-forced, with the Monte Carlo mixture
@@ -51,6 +52,11 @@ CASES = [
     (1, 200, 45, 7, 5),
     (2, 300, 64, 8, 6),
     (2, 150, 20, 32, 4),
+    # edge sizes: one outer particle with one inner particle and one draw; one inner
+    # particle with the largest L; M = 700 (704 threads, 197 KB of shared memory)
+    (1, 1, 1, 1, 3),
+    (2, 5, 1, 32, 3),
+    (1, 3, 700, 32, 3),
 ]
 
 
@@ -198,6 +204,41 @@ def test_paper_dpf_teacher_forced(kind, M, gauss, lib):
     assert bad <= max(2, N * T // 100), bad
 
 
+@pytest.mark.parametrize("kind", [1, 2])
+def test_paper_dpf_and_pf_single_particle(kind, lib):
+    from paper_1203_2394_gb300 import dpf
+    m = nl.PaperModel(kind)
+    pm = dpf.PaperModel(kind)
+    _, ys = workloads.simulate_paper(kind, 3, 3)
+    f = dpf.StandardDPF(pm, pm.d1, pm.d2, 1, 1, 4)
+    x, z, lq = state_from_gpu(f)
+    anc = None
+    for t in range(1, 4):
+        y = np.float32(ys[t - 1, 0])
+        f.step(np.array([y]))
+        gx, gz, glq = state_from_gpu(f)
+        ex, ez, elq, elw = nl.std_step(m, 4, t, float(y), x, z, lq, anc, lib)
+        assert np.max(rel(gx, ex)) <= 2e-5 and np.max(rel(gz, ez)) <= 2e-5
+        assert np.max(rel(f.read("lw").astype(np.float64), elw)) <= 2e-4
+        anc = f.read("anc")
+        assert anc.tolist() == [0]
+        x, z, lq = gx, gz, glq
+    p = dpf.ParticleFilter(pm, pm.d1, pm.d2, 1, 4)
+    x = p.read("x").astype(np.float64)
+    z = p.read("z")[:, :, 0].T.astype(np.float64)
+    anc = None
+    for t in range(1, 4):
+        y = np.float32(ys[t - 1, 0])
+        mean, _ = p.step(np.array([y]))
+        gx = p.read("x").astype(np.float64)
+        gz = p.read("z")[:, :, 0].T.astype(np.float64)
+        ex, ez, elw = nl.pf_step(m, 4, t, float(y), x, z, anc, lib)
+        assert np.max(rel(gx, ex)) <= 2e-5 and np.max(rel(gz, ez)) <= 2e-5
+        assert np.max(rel(mean, np.concatenate([gx[0], gz[0]]))) <= 1e-6
+        anc = p.read("anc")
+        x, z = gx, gz
+
+
 def test_paper_model_rejections():
     from paper_1203_2394_gb300 import dpf
     pm = dpf.PaperModel(1)
@@ -205,3 +246,5 @@ def test_paper_model_rejections():
         dpf.Filter(pm, 1, 1, 100, 32, 33, 0)  # L > 32: the draws' weights are one warp's
     with pytest.raises(dpf.DpfError):
         dpf.Filter(pm, 2, 0, 100, 32, 8, 0)  # d1 = d2 = 1 for model 1
+    with pytest.raises(dpf.DpfError):
+        dpf.Filter(pm, 1, 1, 10, 1000, 32, 0)  # the pair arrays exceed the shared memory
