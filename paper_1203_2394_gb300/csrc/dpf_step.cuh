@@ -602,6 +602,8 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         const int j = tid + p * NT;
+#pragma unroll
+        for (int c = 0; c < D2; ++c) zr[p][c] = T(0);  // past M: zeros, never undefined
         if (j < M) {
 #pragma unroll
           for (int c = 0; c < D2; ++c) zr[p][c] = sz[c * M + j];

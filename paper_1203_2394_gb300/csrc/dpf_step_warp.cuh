@@ -300,6 +300,12 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
       for (int c = 0; c < D1; ++c) x[c] = sx[c];
 #pragma unroll
       for (int p = 0; p < PPL; ++p) lqr[p] = NEG;
+      // lanes past M hold zeros: their z enters the look-ahead's projections, whose
+      // weights are then masked, and an undefined register there could be a NaN
+#pragma unroll
+      for (int c = 0; c < D2; ++c)
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) zr[c][p] = T(0);
       if (act) {
 #pragma unroll
         for (int c = 0; c < D2; ++c) vld<T, PPL>(sz + c * M + k0, zr[c]);
