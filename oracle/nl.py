@@ -52,10 +52,15 @@ from oracle.pf import P_PF_X, P_PF_Z
 
 
 class PaperModel:
-    """One of the paper's two benchmark models (kind 1 or 2), vectorised over leading axes."""
+    """One of the paper's two benchmark models (kind 1 or 2), vectorised over leading axes.
+    swap (model 1 only) decomposes the state the other way, Section 4.3's second action: the
+    filter's x is the table's z and its z the table's x."""
 
-    def __init__(self, kind):
+    def __init__(self, kind, swap=False):
         self.kind = int(kind)
+        self.swap = bool(swap)
+        if self.swap and self.kind != 1:
+            raise ValueError("only model 1 is decomposed both ways")
         if self.kind == 1:
             self.d1 = self.d2 = 1
             self.J = np.eye(2)
@@ -72,6 +77,9 @@ class PaperModel:
         d1 = self.d1
         self.d = 2 * d1
         self.Q = self.J @ self.Sv @ self.J.T
+        # filter coordinate c is table coordinate perm[c]
+        self.perm = np.array([1, 0]) if self.swap else np.arange(self.d)
+        self.Q = self.Q[np.ix_(self.perm, self.perm)]
         Qxx, Qxz, Qzz = self.Q[:d1, :d1], self.Q[:d1, d1:], self.Q[d1:, d1:]
         self.Qxx = Qxx
         self.G = Qxz.T @ np.linalg.inv(Qxx)
@@ -80,10 +88,19 @@ class PaperModel:
         self.LS = np.linalg.cholesky(self.S)
 
     def transition(self, x, z, s, v=None):
-        """Table 1's equations from (x, z) at step s with the noise v (None: the mean)."""
+        """Table 1's equations from (x, z) at step s with the noise v (None: the mean), in the
+        filter's coordinates."""
         x = np.asarray(x, np.float64)
         z = np.asarray(z, np.float64)
         v = np.zeros(np.broadcast_shapes(x.shape[:-1], z.shape[:-1]) + (self.d,)) if v is None else v
+        if self.swap:  # the table's (x, z) is the filter's (z, x)
+            vt = np.empty_like(v)
+            vt[..., self.perm] = v
+            xn, zn = self._table_transition(z, x, s, vt)
+            return zn, xn
+        return self._table_transition(x, z, s, v)
+
+    def _table_transition(self, x, z, s, v):
         if self.kind == 1:
             xs, zs = x[..., 0], z[..., 0]
             xn = xs + zs / (1 + zs ** 2) + v[..., 0]
@@ -97,6 +114,8 @@ class PaperModel:
         return np.stack([x1n, x2n], -1), np.stack([z1n, z2n], -1)
 
     def h(self, x, z):
+        if self.swap:
+            x, z = z, x
         if self.kind == 1:
             return np.arctan(x[..., 0]) + z[..., 0] ** 2 / 20
         return (x[..., 0] + x[..., 1]) / (1 + x[..., 0] ** 2) + np.arctan(z[..., 0]) + z[..., 1] ** 2 / 20
