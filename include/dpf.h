@@ -82,8 +82,11 @@ typedef struct {
 
 /*
  * The paper's benchmark models (Table 1), kind DPF_MODEL_PAPER1 or DPF_MODEL_PAPER2
- * (FP32 only; the matrices, perm, growth and qc fields are not read; d and dy must be 2
- * and 1 for model 1, 4 and 1 for model 2, with d1 = d2 = d / 2):
+ * (FP32 only; the matrices, growth and qc fields are not read; d and dy must be 2 and 1
+ * for model 1, 4 and 1 for model 2, with d1 = d2 = d / 2; perm may be NULL or the
+ * identity, or for model 1 {1, 0}: the table's z as the outer block and its x as the
+ * inner one, the second decomposition of Section 4.3; the filtered mean comes back in the
+ * table's order either way):
  *   model 1: x' = x + z / (1 + z^2) + v_x, z' = x + 0.5 z + 25 z / (1 + z^2) + 8 cos(1.2 t) + v_z,
  *            y = atan(x) + z^2 / 20 + e, (v_x, v_z) ~ N(0, [[1, 0.1], [0.1, 1]]);
  *   model 2: x1' = 0.5 x1 + 8 sin t + v, x2' = 0.4 x1 + 0.5 x2 + v, z1' = z1 + z2 / (1 + z2^2) + v,

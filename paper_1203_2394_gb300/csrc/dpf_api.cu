@@ -275,15 +275,25 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   x->stream = (cudaStream_t)stream;
   const bool paper = model->kind == DPF_MODEL_PAPER1 || model->kind == DPF_MODEL_PAPER2;
   dpf_status st = DPF_OK;
-  if (paper) {  // the paper's models: fixed dimensions, FP32, identity coordinate order
+  bool swapped = false;
+  if (paper) {  // the paper's models: fixed dimensions, FP32
     const int want_d = model->kind == DPF_MODEL_PAPER1 ? 2 : 4;
     if (model->d != want_d || model->dy != 1 || d1 != want_d / 2 || d2 != want_d / 2 || model->precision != DPF_F32) {
       delete x;
       return set_error(DPF_E_INVALID, "dpf_create: the paper's model 1 needs d = 2, model 2 d = 4, with dy = 1, "
                                       "d1 = d2 = d / 2 and FP32");
     }
+    // the coordinate order: the table's, or for model 1 also (z, x) (perm = {1, 0})
     x->perm.resize(want_d);
-    for (int c = 0; c < want_d; ++c) x->perm[c] = c;
+    for (int c = 0; c < want_d; ++c) x->perm[c] = model->perm ? model->perm[c] : c;
+    bool ident = true;
+    for (int c = 0; c < want_d; ++c) ident = ident && x->perm[c] == c;
+    swapped = !ident;
+    if (swapped && !(model->kind == DPF_MODEL_PAPER1 && x->perm[0] == 1 && x->perm[1] == 0)) {
+      delete x;
+      return set_error(DPF_E_INVALID, "dpf_create: the paper's models take the table's coordinate order, "
+                                      "or {1, 0} for model 1");
+    }
     x->hm.d1 = d1;
     x->hm.d2 = d2;
     x->hm.dy = 1;
@@ -295,7 +305,7 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
     delete x;
     return st;
   }
-  x->var = paper ? find_paper_variant(model->kind) : find_variant(x->prec, d1, d2, x->dy);
+  x->var = paper ? find_paper_variant(model->kind, swapped) : find_variant(x->prec, d1, d2, x->dy);
   if (!x->var) {
     delete x;
     return set_error(DPF_E_UNSUPPORTED,

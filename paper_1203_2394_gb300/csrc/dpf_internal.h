@@ -107,7 +107,8 @@ struct Variant {
   bool xz_supported = true;  // serves models whose x transition depends on z
 };
 const Variant* find_variant(int prec, int d1, int d2, int dy);
-const Variant* find_paper_variant(int kind);  // the paper's models 1 and 2 (FP32)
+// the paper's models 1 and 2 (FP32); swapped: model 1 with the table's z as the outer block
+const Variant* find_paper_variant(int kind, bool swapped);
 dpf_status learned_inner_step(Ctx& x);
 dpf_status learned_fallback_lists(Ctx& x);  // dpf_learned_step.cu
 int dpf_proposal_dout(const dpf_proposal* p);  // head outputs of a proposal

@@ -45,6 +45,30 @@ struct PaperModel1 {
   static constexpr float lognorm_y = -0.91893853320467f;  // -log(2 pi) / 2
 };
 
+// Model 1 decomposed the other way (Section 4.3's second action): the outer particles carry
+// the table's z and the inner ones its x, so here x = z_table and z = x_table; the same
+// noise covariance (symmetric in the two coordinates).
+struct PaperModel1Swap {
+  static constexpr int D1 = 1, D2 = 1, DY = 1, NT = 1;
+  __device__ static void fx(const float (&x)[1], const float (&z)[1], const float* tt, float (&o)[1]) {
+    o[0] = z[0] + 0.5f * x[0] + 25.f * x[0] / (1.f + x[0] * x[0]) + tt[0];
+  }
+  __device__ static void fz(const float (&x)[1], const float (&z)[1], const float* tt, float (&o)[1]) {
+    o[0] = z[0] + x[0] / (1.f + x[0] * x[0]);
+  }
+  __device__ static float hx(const float (&x)[1]) { return x[0] * x[0] / 20.f; }
+  __device__ static float hz(const float (&z)[1]) { return atanf(z[0]); }
+  __device__ static void h(const float (&x)[1], const float (&z)[1], float (&o)[1]) { o[0] = hx(x) + hz(z); }
+  static constexpr bool GZERO = false;
+  static void terms(double s, float (&tt)[NT]) { tt[0] = (float)(8.0 * std::cos(1.2 * s)); }
+  __host__ __device__ static constexpr float Lqx(int, int) { return 1.f; }
+  __host__ __device__ static constexpr float LqxInv(int, int) { return 1.f; }
+  __host__ __device__ static constexpr float G(int, int) { return 0.1f; }
+  __host__ __device__ static constexpr float LS(int, int) { return 0.99498743710662f; }
+  __host__ __device__ static constexpr float LrInv(int, int) { return 1.f; }
+  static constexpr float lognorm_y = -0.91893853320467f;
+};
+
 // Model 2 (4-dimensional): x1' = 0.5 x1 + 8 sin t, x2' = 0.4 x1 + 0.5 x2, z1' = z1 + z2 /
 // (1 + z2^2), z2' = z1' + 0.5 z2 + 25 z2 / (1 + z2^2) + 8 cos(1.2 t),
 // y = (x1 + x2) / (1 + x1^2) + atan(z1) + z2^2 / 20; the noise of x is N(0, I), of

@@ -4,4 +4,5 @@
 namespace dpf {
 Variant make_v_paper1() { return PaperVariant<PaperModel1>::make(); }
 Variant make_v_paper2() { return PaperVariant<PaperModel2>::make(); }
+Variant make_v_paper1s() { return PaperVariant<PaperModel1Swap>::make(); }
 }  // namespace dpf

@@ -160,18 +160,20 @@ class Model:
 
 class PaperModel(Model):
     """The paper's benchmark model 1 (d = 2) or 2 (d = 4) of Table 1, FP32; the filter is
-    created with d1 = d2 = d / 2 (the matrices of the descriptor are not used)."""
+    created with d1 = d2 = d / 2 (the matrices of the descriptor are not used). perm = (1, 0)
+    decomposes model 1 the other way: the table's z outer, its x inner."""
 
-    def __init__(self, kind: int):
+    def __init__(self, kind: int, perm=None):
         if kind not in (1, 2):
             raise ValueError("kind must be 1 or 2")
         self.arrays = []
-        self.perm = None
+        self.perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
         self.d, self.dy, self.precision = (2 if kind == 1 else 4), 1, DPF_F32
         self.d1 = self.d2 = self.d // 2
         g = (ctypes.c_double * 4)(0.0, 0.0, 0.0, 0.0)
         self.desc = ModelDesc(DPF_MODEL_PAPER1 if kind == 1 else DPF_MODEL_PAPER2, self.d, self.dy,
-                              self.precision, 0, 0, None, None, None, None, None, None, None, g, 0.0)
+                              self.precision, 0, 0, None if self.perm is None else self.perm.ctypes.data,
+                              None, None, None, None, None, None, g, 0.0)
 
 
 class Filter:

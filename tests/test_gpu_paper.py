@@ -16,6 +16,8 @@ DPF_MODEL_PAPER1 / DPF_MODEL_PAPER2, FP32) against the oracle of oracle/nl.py.
 * The DPF without look-ahead (dpf_create_std), teacher-forced, with the Monte Carlo mixture
   prior and its Gaussian approximation: the same particles and weights in all but 1% of
   the groups, the outer ancestors bit for bit.
+* Model 1 decomposed the other way (perm = (1, 0)): the LA-DPF and the particle filter as
+  above, the filtered mean returned in the table's order.
 * The benchmark's size (N = 65536, M = 128, L = 16): sampled groups of two calls.
 """
 import numpy as np
@@ -34,9 +36,9 @@ def lib():
     return oracle.load()
 
 
-def _la(kind, N, M, L, seed):
+def _la(kind, N, M, L, seed, swap=False):
     from paper_1203_2394_gb300 import dpf
-    pm = dpf.PaperModel(kind)
+    pm = dpf.PaperModel(kind, perm=(1, 0) if swap else None)
     return dpf.Filter(pm, pm.d1, pm.d2, N, M, L, seed)
 
 
@@ -57,15 +59,19 @@ CASES = [
     (1, 1, 1, 1, 3),
     (2, 5, 1, 32, 3),
     (1, 3, 700, 32, 3),
+    # model 1 decomposed the other way (perm = (1, 0): the table's z outer)
+    (-1, 200, 64, 8, 5),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=[f"model{c[0]}-N{c[1]}-M{c[2]}-L{c[3]}" for c in CASES])
+@pytest.mark.parametrize("case", CASES, ids=[f"model{c[0]}-N{c[1]}-M{c[2]}-L{c[3]}".replace("model-1", "model1swap")
+                                              for c in CASES])
 def test_paper_la_dpf_teacher_forced(case, lib):
     kind, N, M, L, T = case
+    swap, kind = kind < 0, abs(kind)
     seed = 7
-    m = nl.PaperModel(kind)
-    f = _la(kind, N, M, L, seed)
+    m = nl.PaperModel(kind, swap=swap)
+    f = _la(kind, N, M, L, seed, swap)
     _, ys = workloads.simulate_paper(kind, T, 0)
     x0, z0, lq0 = state_from_gpu(f)
     ox, oz, olq = nl.init(m, N, M, seed, lib)
@@ -85,7 +91,8 @@ def test_paper_la_dpf_teacher_forced(case, lib):
         bad_draws += int((~same).sum())
         assert np.max(rel(lw[same], elw[same])) <= 2e-4, (t, np.max(rel(lw[same], elw[same])))
         check_lwhat(lwhat[same], elwhat[same], 2e-4)
-        em = _oracle_mean(elwhat, exbb, emu)
+        em = np.empty(m.d)
+        em[m.perm] = _oracle_mean(elwhat, exbb, emu)  # the mean comes back in the table's order
         assert np.max(rel(mean, em)) <= 2e-3, (t, mean, em)
         wout = f.read("wout").astype(np.float64)
         anc = f.read("anc")
@@ -108,12 +115,13 @@ def test_paper_la_dpf_teacher_forced(case, lib):
     assert bad_groups <= max(2, N * T // 100), bad_groups
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, -1])
 def test_paper_pf_teacher_forced(kind, lib):
     from paper_1203_2394_gb300 import dpf
     N, seed, T = 4000, 5, 6
-    m = nl.PaperModel(kind)
-    pm = dpf.PaperModel(kind)
+    swap, kind = kind < 0, abs(kind)
+    m = nl.PaperModel(kind, swap=swap)
+    pm = dpf.PaperModel(kind, perm=(1, 0) if swap else None)
     f = dpf.ParticleFilter(pm, pm.d1, pm.d2, N, seed)
     _, ys = workloads.simulate_paper(kind, T, 1)
     ox, oz, _ = nl.init(m, N, 1, seed, lib)
@@ -131,7 +139,9 @@ def test_paper_pf_teacher_forced(kind, lib):
         assert np.max(rel(gx, ex)) <= 2e-5 and np.max(rel(gz, ez)) <= 2e-5
         assert np.max(rel(lw, elw)) <= 2e-4
         W = np.exp(lw - lw.max())
-        assert np.max(rel(mean, np.concatenate([W @ gx, W @ gz]) / W.sum())) <= 1e-4
+        em = np.empty(m.d)
+        em[m.perm] = np.concatenate([W @ gx, W @ gz]) / W.sum()
+        assert np.max(rel(mean, em)) <= 1e-4
         anc = f.read("anc")
         wout = f.read("wout").astype(np.float64)
         np.testing.assert_array_equal(anc, oracle.sys_global(wout, word(seed, t, 0, oracle.P_OUTER), lib))
@@ -248,3 +258,6 @@ def test_paper_model_rejections():
         dpf.Filter(pm, 2, 0, 100, 32, 8, 0)  # d1 = d2 = 1 for model 1
     with pytest.raises(dpf.DpfError):
         dpf.Filter(pm, 1, 1, 10, 1000, 32, 0)  # the pair arrays exceed the shared memory
+    p2 = dpf.PaperModel(2, perm=(2, 3, 0, 1))
+    with pytest.raises(dpf.DpfError):
+        dpf.Filter(p2, 2, 2, 10, 32, 8, 0)  # model 2 takes the table's order only
