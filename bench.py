@@ -750,6 +750,91 @@ def run_paper(args):
     return 0
 
 
+def run_bandit(args):
+    """Automatic state decomposition on the paper's model 1 (Section 4.3): two actions, the
+    table's order (x outer, z inner) and the other way (perm = (1, 0)), each an LA-DPF in FP32
+    stepped on the same observations, at two sizes (N, M, L) = (100, 10, 8) and (1000, 32, 16).
+    Every step each action earns alpha / (alpha + eps^2), eps = y_t - yhat_t with yhat_t =
+    h(f(m_{t-1}, t-1)) from its own filtered mean; Hedge takes both rewards, Exp3 (gamma = 0.2,
+    eta = 0.5) only its chosen action's. The output at step t is the chosen action's filtered
+    mean (Hedge: its most probable action). Reports the RMSE against the true state of each
+    fixed action and of both bandits, and the final probabilities, averaged over R runs of T
+    steps."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    T, R = 1000, max(1, min(args.runs, 8))
+    ETA, GAMMA = 0.5, 0.2
+    alpha = float(args.alpha)
+
+    def f_mean(m, s):  # the table's transition mean at step s
+        x, z = m
+        return np.array([x + z / (1 + z * z), x + 0.5 * z + 25 * z / (1 + z * z) + 8 * np.cos(1.2 * s)])
+
+    def h(m):
+        return np.arctan(m[0]) + m[1] ** 2 / 20
+
+    def one_size(N, M, L):
+        res = {k: [] for k in ("action1", "action2", "hedge", "exp3")}
+        probs = {"hedge": [], "exp3": []}
+        chosen1 = []
+        for r in range(R):
+            s_true, ys = workloads.simulate_paper(1, T, 500 + r)
+            fs = [dpf.Filter(dpf.PaperModel(1, perm=p), 1, 1, N, M, L, seed=r) for p in (None, (1, 0))]
+            hedge = dpf.Bandit(dpf.DPF_HEDGE, 2, ETA, 0.0, seed=r)
+            exp3 = dpf.Bandit(dpf.DPF_EXP3, 2, ETA, GAMMA, seed=r)
+            prev = [np.zeros(2), np.zeros(2)]  # s_0 ~ N(0, I): the prior mean
+            err = {k: [] for k in res}
+            n1 = 0
+            for t in range(1, T + 1):
+                y = ys[t - 1].astype(np.float32)
+                rew = np.array([dpf.bandit_reward(y, [h(f_mean(prev[a], t - 1))], alpha) for a in range(2)])
+                a3 = exp3.choose()
+                ah = int(np.argmax(hedge.probs()))
+                means = [f.step(y)[0] for f in fs]
+                hedge.update(rew)
+                exp3.update(rew[a3:a3 + 1])  # Exp3 is told the tried action's reward only
+                n1 += a3 == 0
+                for k, mu in (("action1", means[0]), ("action2", means[1]), ("hedge", means[ah]),
+                              ("exp3", means[a3])):
+                    err[k].append(mu - s_true[t])
+                prev = means
+            for f in fs:
+                f.close()
+            for k in res:
+                res[k].append(np.sqrt(np.mean(np.array(err[k]) ** 2, axis=0)))
+            probs["hedge"].append(hedge.probs().tolist())
+            probs["exp3"].append(exp3.probs().tolist())
+            chosen1.append(n1 / T)
+            hedge.close()
+            exp3.close()
+        out = {k: {"rmse_x": float(np.mean([v[0] for v in res[k]])), "rmse_z": float(np.mean([v[1] for v in res[k]]))}
+               for k in res}
+        out["final_probs"] = {k: np.mean(v, axis=0).tolist() for k, v in probs.items()}
+        out["exp3_share_action1"] = float(np.mean(chosen1))
+        return out
+
+    t0 = time.perf_counter()
+    small = one_size(100, 10, 8)
+    large = one_size(1000, 32, 16)
+    wall = time.perf_counter() - t0
+    line = {
+        "metric": "RMSE against the true state (mean over runs)", "value": small["exp3"]["rmse_z"],
+        "unit": "state units", "n_gpus": 1, "steps": T, "warmup": 0, "ms_per_step": wall / (2 * R * T) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"automatic decomposition of the paper's model 1: two LA-DPFs (x outer / z outer), "
+                               f"FP32, Hedge and Exp3 (eta={ETA}, gamma={GAMMA}, alpha={alpha}), {R} runs of {T} "
+                               f"steps, at N, M, L = 100, 10, 8 and 1000, 32, 16; value: Exp3's RMSE of z at the "
+                               f"small size"},
+        "n100_m10_l8": small, "n1000_m32_l16": large,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args):
     """The learned-proposal workload: the lg4 model in FP32 with N = 262144 outer and
     M = 64 inner particles. A proposal (MLP 3 x 256 ReLU, 4-component mixture head, BF16
@@ -911,10 +996,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare", "table2", "paper"],
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare", "table2", "paper", "bandit"],
                     help="the headline single-filter workload, the many-filter one, the d2 = 56 one, "
                          "the learned-proposal one, or the LA-DPF against the bootstrap PF")
-    ap.add_argument("--runs", type=int, default=3, help="runs per model of the paper workload (at most 8)")
+    ap.add_argument("--runs", type=int, default=3, help="runs per model of the paper and bandit workloads (at most 8)")
+    ap.add_argument("--alpha", type=float, default=0.001, help="the bandit reward's alpha (the paper's 0.001)")
     ap.add_argument("--filters", type=int, default=None,
                     help="filters of the batched (default 512) or high-dimensional (default 64) workload")
     args = ap.parse_args(argv)
@@ -936,6 +1022,8 @@ def main(argv=None):
         return run_table2(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "bandit":
+        return run_bandit(args)
     return run(args)
 
 
