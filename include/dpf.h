@@ -300,8 +300,10 @@ dpf_status dpf_read(dpf_ctx* ctx, const char* which, void* host_dst, size_t byte
  * counter, with a header of the sizes. dpf_state_bytes gives its size;
  * dpf_get_state copies it into dst_device (device memory, caller-owned, at
  * least that many bytes); dpf_set_state loads one taken from a filter of the
- * same kind (LA-DPF, particle filter or DPF without look-ahead), precision and
- * sizes (d1, d2, dy, N, M, L; else DPF_E_INVALID). The steps
+ * same kind (LA-DPF, particle filter or DPF without look-ahead), model family
+ * (the conditionally linear-Gaussian family, or which of the paper's models in
+ * which decomposition), precision and sizes (d1, d2, dy, N, M, L; else
+ * DPF_E_INVALID). The steps
  * after a restore equal those of the original filter when both have the same
  * seed. Both synchronise the stream.
  */

@@ -306,6 +306,7 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
     return st;
   }
   x->var = paper ? find_paper_variant(model->kind, swapped) : find_variant(x->prec, d1, d2, x->dy);
+  x->model_id = paper ? model->kind + (swapped ? 2 : 0) : 0;
   if (!x->var) {
     delete x;
     return set_error(DPF_E_UNSUPPORTED,
@@ -610,7 +611,9 @@ struct StateHeader {
   int32_t version, prec, d1, d2, dy, M, L, xp;
   int64_t N, t;
   uint64_t seed;
-  int32_t kind, pad;  // 0 the LA-DPF, 1 the bootstrap particle filter, 2 the DPF without look-ahead
+  int32_t kind;   // 0 the LA-DPF, 1 the bootstrap particle filter, 2 the DPF without look-ahead
+  int32_t model;  // 0 a conditionally linear-Gaussian model; the paper's: 2 model 1, 3 model 2,
+                  // 4 model 1 decomposed the other way (states written before it hold 0)
 };
 int32_t ctx_kind(const dpf_ctx& x) { return x.pf ? 1 : (x.std_dpf ? 2 : 0); }
 constexpr uint64_t kStateMagic = 0x4450465354415445ull;  // "DPFSTATE"
@@ -666,7 +669,7 @@ dpf_status dpf_get_state(dpf_ctx* x, void* dst, size_t bytes) {
   const StateLayout l = state_layout(*x);
   if (bytes < l.total) return set_error(DPF_E_INVALID, "dpf_get_state: buffer smaller than dpf_state_bytes");
   StateHeader h{kStateMagic, 2, x->prec, x->d1, x->d2, x->dy, x->M, x->L, x->xp, x->N, x->t, x->seed,
-                ctx_kind(*x), 0};
+                ctx_kind(*x), x->model_id};
   void* a[10];
   state_arrays(*x, a);
   cudaError_t e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, x->stream);
@@ -687,8 +690,9 @@ dpf_status dpf_set_state(dpf_ctx* x, const void* src, size_t bytes) {
   if (e != cudaSuccess) return cuda_error(e, "dpf_set_state");
   if (h.magic != kStateMagic || h.version != 2 || h.prec != x->prec || h.d1 != x->d1 || h.d2 != x->d2 ||
       h.dy != x->dy || h.M != x->M || h.L != x->L || h.xp != x->xp || h.N != x->N || h.t < 0 ||
-      h.kind != ctx_kind(*x))
-    return set_error(DPF_E_INVALID, "dpf_set_state: not a state of a filter of this kind, precision and these sizes");
+      h.kind != ctx_kind(*x) || h.model != x->model_id)
+    return set_error(DPF_E_INVALID, "dpf_set_state: not a state of a filter of this kind, model, precision and "
+                                    "these sizes");
   x->t = h.t;
   void* a[10];
   state_arrays(*x, a);

@@ -126,6 +126,7 @@ struct dpf_ctx {
   std::vector<int> perm;
   dpf::HostModel hm;
   const dpf::Variant* var = nullptr;
+  int model_id = 0;  // 0 a conditionally linear-Gaussian model; 2, 3 the paper's models, 4 model 1 swapped
   std::vector<unsigned char> mconst;  // device-constant model block (variant layout)
   // device state (element type = precision)
   void* z[2] = {nullptr, nullptr};

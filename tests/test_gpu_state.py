@@ -1,5 +1,5 @@
 """Checkpoints: a filter restored from dpf_get_state continues exactly as the original
-(same seed), and states of other sizes are refused."""
+(same seed), and states of other sizes, kinds of filter or models are refused."""
 import numpy as np
 import pytest
 
@@ -74,3 +74,25 @@ def test_restore_baselines_continue_bit_for_bit(kind):
         other = dpf.Filter(m, 2, 8, 500, 64, 1, seed=6)
         with pytest.raises(dpf.DpfError):
             other.set_state(st)
+
+
+def test_restore_paper_model_and_refuse_the_other_decomposition():
+    """The LA-DPF of the paper's model 1 restores from its checkpoint and continues exactly;
+    the same sizes decomposed the other way (perm = (1, 0)) refuse that state."""
+    from paper_1203_2394_gb300 import dpf
+    _, ys = workloads.simulate_paper(1, 9, 0)
+    pm = dpf.PaperModel(1)
+    a = dpf.Filter(pm, 1, 1, 400, 32, 8, seed=6)
+    for t in range(4):
+        a.step(ys[t].astype(np.float32))
+    st = a.get_state()
+    b = dpf.Filter(pm, 1, 1, 400, 32, 8, seed=6)
+    b.set_state(st)
+    for t in range(4, 8):
+        ma, la = a.step(ys[t].astype(np.float32))
+        mb, lb = b.step(ys[t].astype(np.float32))
+        np.testing.assert_array_equal(ma, mb)
+        assert la == lb
+    swapped = dpf.Filter(dpf.PaperModel(1, perm=(1, 0)), 1, 1, 400, 32, 8, seed=6)
+    with pytest.raises(dpf.DpfError):
+        swapped.set_state(st)
