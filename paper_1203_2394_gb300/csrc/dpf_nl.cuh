@@ -31,7 +31,7 @@ struct PaperModel1 {
   }
   // y = h_x(x) + h_z(z) + e
   __device__ static float hx(const float (&x)[1]) { return atanf(x[0]); }
-  __device__ static float hz(const float (&z)[1]) { return z[0] * z[0] / 20.f; }
+  __device__ static float hz(const float (&z)[1]) { return z[0] * z[0] * 0.05f; }  // z^2 / 20
   __device__ static void h(const float (&x)[1], const float (&z)[1], float (&o)[1]) { o[0] = hx(x) + hz(z); }
   static constexpr bool GZERO = false;  // the z draw depends on x_t (G != 0)
   // 8 cos(1.2 s) at the source step s (on the host, in double)
@@ -56,7 +56,7 @@ struct PaperModel1Swap {
   __device__ static void fz(const float (&x)[1], const float (&z)[1], const float* tt, float (&o)[1]) {
     o[0] = z[0] + x[0] / (1.f + x[0] * x[0]);
   }
-  __device__ static float hx(const float (&x)[1]) { return x[0] * x[0] / 20.f; }
+  __device__ static float hx(const float (&x)[1]) { return x[0] * x[0] * 0.05f; }
   __device__ static float hz(const float (&z)[1]) { return atanf(z[0]); }
   __device__ static void h(const float (&x)[1], const float (&z)[1], float (&o)[1]) { o[0] = hx(x) + hz(z); }
   static constexpr bool GZERO = false;
@@ -85,7 +85,7 @@ struct PaperModel2 {
     o[1] = z1 + 0.5f * z[1] + 25.f * z[1] / (1.f + z[1] * z[1]) + tt[1];
   }
   __device__ static float hx(const float (&x)[2]) { return (x[0] + x[1]) / (1.f + x[0] * x[0]); }
-  __device__ static float hz(const float (&z)[2]) { return atanf(z[0]) + z[1] * z[1] / 20.f; }
+  __device__ static float hz(const float (&z)[2]) { return atanf(z[0]) + z[1] * z[1] * 0.05f; }
   __device__ static void h(const float (&x)[2], const float (&z)[2], float (&o)[1]) { o[0] = hx(x) + hz(z); }
   static constexpr bool GZERO = true;  // x and z noises independent: the z draw is free of x_t
   static void terms(double s, float (&tt)[NT]) {
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
   float* fxk = lqs + M;          // [D1][M] f_x(x, z_k) of the look-ahead
   float* bk = fxk + D1 * M;      // [D2][M] f_z(x, z_k) + chol(S) e_k: the draw's base
   float* hzk = bk + D2 * M;      // [M] h_z of the base (models with G = 0)
-  float* E1 = hzk + M;           // [L][M] alpha + ell of the pairs
-  float* E2 = E1 + L * M;        // [L][M] alpha
+  float* E1 = hzk + M;           // [L][M] alpha + ell of the pairs (log2 units)
+  float* E2 = E1 + L * M;        // [L][M] alpha (log2 units)
   float* xbs = E2 + L * M;       // [L][D1] the look-ahead draws
   float* hxs = xbs + L * D1;     // [L] h_x of the draws
   float* lwhs = hxs + L;         // [L] the ancestor's per-draw weights
@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
           hzv = Mod::hz(zh);
         }
         const float res = (y0 - hxs[m] - hzv) * Mod::LrInv(0, 0);
-        E1[m * M + tid] = al + Mod::lognorm_y - 0.5f * res * res;
-        E2[m * M + tid] = al;
+        E1[m * M + tid] = (al + Mod::lognorm_y - 0.5f * res * res) * LOG2E;  // log2 units
+        E2[m * M + tid] = al * LOG2E;
       }
     }
     __syncthreads();
@@ -427,9 +427,9 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
 #pragma unroll
       for (int c = 0; c < D2; ++c) za[c] = 0.f;
       for (int k = lane; k < M; k += 32) {
-        const float e = expf(E1[m * M + k] - m1);
+        const float e = exp2_t(E1[m * M + k] - m1);
         s1 += e;
-        s2 += expf(E2[m * M + k] - m2);
+        s2 += exp2_t(E2[m * M + k] - m2);
         float r[D1];
 #pragma unroll
         for (int c = 0; c < D1; ++c) r[c] = xb[c] - fxk[c * M + k];
@@ -445,9 +445,9 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
       s2 = warp_sum(s2);
 #pragma unroll
       for (int c = 0; c < D2; ++c) za[c] = warp_sum(za[c]);
-      if (lane == 0) {
-        rowm[2 * m] = m1 + logf(s1);
-        rowm[2 * m + 1] = m2 + logf(s2);
+      if (lane == 0) {  // back to natural-log units
+        rowm[2 * m] = (m1 + log2f(s1)) * (float)LN2_D;
+        rowm[2 * m + 1] = (m2 + log2f(s2)) * (float)LN2_D;
 #pragma unroll
         for (int c = 0; c < D2; ++c) zrow[m * D2 + c] = za[c] / s1;
       }
