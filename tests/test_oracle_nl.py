@@ -8,6 +8,8 @@
 * A look-ahead draw's weight, for an inner set of equal particles, is the Monte Carlo mean
   of p(y_t | xbb, z) over z from the transition's conditional given xbb: against that
   integral by quadrature of the joint Gaussian, within four standard errors.
+* The grid filter itself (tests/grid_filter.py) against the Kalman filter on a linear
+  two-dimensional model with correlated noise: means, standard deviations and evidence.
 * Model 1's filtered means and log-evidence increments, from the bootstrap particle filter
   and the LA-DPF, against the exact filter on a grid (tests/grid_filter.py), and planted
   mistakes (the p(x | x, z) factor of the pair weights dropped, the x-z coupling G dropped,
@@ -28,7 +30,8 @@ import pytest
 
 from oracle import nl, oracle
 from paper_1203_2394_gb300 import workloads
-from tests.grid_filter import model1_posterior_means
+from tests.grid_filter import model1_posterior_means, posterior_means
+from tests.kalman import kalman
 
 scipy_stats = pytest.importorskip("scipy.stats")
 scipy_integrate = pytest.importorskip("scipy.integrate")
@@ -114,6 +117,28 @@ def test_lookahead_weight_is_the_conditional_integral(lib):
         se = pk.std() / np.sqrt(M) / pk.mean()
         assert abs(lwhat[0, k] - np.log(ref)) < 4 * se + 1e-12, (k, lwhat[0, k], np.log(ref), se)
     np.testing.assert_allclose(lw[0], np.log(np.mean(np.exp(lwhat[0]))), rtol=1e-13)
+
+
+def test_grid_filter_is_the_kalman_filter_on_a_linear_model():
+    A = np.array([[0.9, 0.3], [-0.2, 0.8]])
+    Q = np.array([[1.0, 0.3], [0.3, 0.5]])
+    H = np.array([[1.0, -0.7]])
+    rng = np.random.default_rng(3)
+    s = rng.normal(size=2)
+    ys = []
+    for _ in range(6):
+        s = A @ s + np.linalg.cholesky(Q) @ rng.normal(size=2)
+        ys.append(H @ s + np.sqrt(0.5) * rng.normal(size=1))
+    ys = np.array(ys)
+    km, kP, kll = kalman(A, Q, H, 0.5 * np.eye(1), np.zeros(2), np.eye(2), ys)
+    gm, gs, glz, edge = posterior_means(
+        ys, np.arange(-12, 12 + 1e-9, 0.2), np.arange(-12, 12 + 1e-9, 0.2),
+        lambda x, z, t: (A[0, 0] * x + A[0, 1] * z, A[1, 0] * x + A[1, 1] * z),
+        lambda x, z: H[0, 0] * x + H[0, 1] * z, Q, r_var=0.5)
+    assert edge < 1e-12
+    np.testing.assert_allclose(gm, km, atol=1e-6)
+    np.testing.assert_allclose(gs, np.sqrt(np.stack([np.diag(P) for P in kP])), atol=1e-6)
+    np.testing.assert_allclose(glz, kll, atol=1e-6)
 
 
 GRID = dict(xg=np.arange(-15, 15 + 1e-9, 0.2), zg=np.arange(-36, 36 + 1e-9, 0.1), cut=1e-10)
