@@ -23,7 +23,8 @@
 * The DPF without look-ahead: model 1 against the grid filter, with the Monte Carlo
   mixture prior and with its Gaussian approximation, and planted mistakes miss it; on model
   2, whose x transition is free of z, the Gaussian approximation is the mixture itself, so
-  both forms give the same particles.
+  both forms give the same particles; on model 1 the two forms' draws of x_t for one group
+  over 4000 seeds have the same mean and variance (the moments the Gaussian form matches).
 """
 import numpy as np
 import pytest
@@ -261,3 +262,20 @@ def test_swapped_decomposition_matches_the_grid_filter(grid1, lib):
         table[:, m.perm] = mean
         assert np.abs((table - gm) / gs).max() < tm
         assert np.abs(lz - glz).max() < tz
+
+
+def test_dpf_gaussian_form_matches_the_mixture_moments(lib):
+    m = nl.PaperModel(1)
+    M, seeds = 8, 4000
+    x = np.array([[0.3]])
+    z = np.array([[[-2.0], [-0.5], [0.2], [0.9], [1.5], [3.0], [-4.0], [0.0]]])
+    lq = np.log(np.array([[0.05, 0.2, 0.1, 0.15, 0.2, 0.1, 0.1, 0.1]]))
+    draws = {False: [], True: []}
+    for seed in range(seeds):
+        for gauss in (False, True):
+            xt = nl.std_step(m, seed, 2, 0.1, x, z, lq, np.array([0]), lib, gauss=gauss)[0]
+            draws[gauss].append(xt[0, 0])
+    a, b = np.array(draws[False]), np.array(draws[True])
+    se = np.sqrt(a.var() / seeds + b.var() / seeds)
+    assert abs(a.mean() - b.mean()) < 4 * se, (a.mean(), b.mean(), se)
+    assert abs(a.var() / b.var() - 1) < 4 * np.sqrt(2 / seeds) * 1.5, (a.var(), b.var())
