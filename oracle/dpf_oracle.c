@@ -118,6 +118,23 @@ static void rng_normals(const ora_rng* r, uint32_t t, uint32_t i, uint32_t purpo
   }
 }
 
+/* The dy normals of the look-ahead's common inner draw of inner particle k (purpose
+ * LA_Z). For dy <= 2 two inner particles share one Philox block: particle k takes the
+ * Box-Muller pair of words 2(k mod 2), 2(k mod 2)+1 of block (t, i, LA_Z, k / 2) (dy = 1
+ * keeps its first normal); for dy > 2 they are the normals of (t, i, LA_Z, k). */
+static void rng_la_z(const ora_rng* r, uint32_t t, uint32_t i, uint32_t k, int dy, double* out) {
+  if (dy <= 2) {
+    uint32_t w[4];
+    rng_block(r, t, i, P_LA_Z, k >> 1, 0, w);
+    double a, b;
+    ora_box_muller(w[2 * (k & 1)], w[2 * (k & 1) + 1], &a, &b);
+    out[0] = a;
+    if (dy > 1) out[1] = b;
+  } else {
+    rng_normals(r, t, i, P_LA_Z, k, dy, out);
+  }
+}
+
 /* Exposed for the generator tests. */
 void ora_normals(uint64_t seed, uint32_t filter_id, uint32_t t, uint32_t i, uint32_t purpose,
                  uint32_t sub, int n, double* out) {
@@ -566,7 +583,7 @@ static double lookahead_group(const ora_model* m, const ora_dims* D, const ora_r
   for (int k = 0; k < M; ++k) {
     double fz[64], e[64], v[64];
     f_z(m, x_i, z_i + (size_t)k * d2, fz);
-    rng_normals(r, t, (uint32_t)i, P_LA_Z, (uint32_t)k, dy, e);
+    rng_la_z(r, t, (uint32_t)i, (uint32_t)k, dy, e);
     tri_mul(m->Ls, dy, e, v);
     for (int q = 0; q < dy; ++q) {
       double hz = 0.0;
@@ -630,11 +647,13 @@ static double lookahead_group(const ora_model* m, const ora_dims* D, const ora_r
  *     (the prior proposal p(z_t | x_{0:t}, y_{0:t-1}) of section 2.1, so r = 1);
  *   measurement update (eq. qbar): lq_t^(i,j) = ell_j - LSE_j ell,
  *     ell_j = log p(y_t | x_t^(i), z_t^(i,j)).
+ * bidx_in (optional): replay the given local resampling indices instead of drawing
+ * them (the rest of the step is unchanged); alpha_out (optional): the M weights alpha.
  */
 static int finalize_group(const ora_model* m, const ora_dims* D, const ora_rng* r, uint32_t t,
                           int64_t i, const double* xa, const double* za, const double* lqa,
                           const double* xn, const double* y, double* zn, double* lqn,
-                          int32_t* bidx) {
+                          int32_t* bidx, const int32_t* bidx_in, double* alpha_out) {
   int d2 = m->d2, M = D->M;
   double s = (double)t - 1.0;
   double* al = (double*)malloc(sizeof(double) * (size_t)M);
@@ -647,7 +666,17 @@ static int finalize_group(const ora_model* m, const ora_dims* D, const ora_rng* 
   double mx = -INFINITY;
   for (int k = 0; k < M; ++k) if (al[k] > mx) mx = al[k];
   for (int k = 0; k < M; ++k) W[k] = exp(al[k] - mx);
-  int st = ora_sys_local(W, M, M, rng_word(r, t, (uint32_t)i, P_INNER, 0), bidx);
+  if (alpha_out)
+    for (int k = 0; k < M; ++k) alpha_out[k] = al[k];
+  int st = ORA_OK;
+  if (bidx_in) { /* replay: the local resampling indices are given */
+    for (int j = 0; j < M; ++j) {
+      if (bidx_in[j] < 0 || bidx_in[j] >= M) { free(al); free(W); return ORA_E_INVALID; }
+      bidx[j] = bidx_in[j];
+    }
+  } else {
+    st = ora_sys_local(W, M, M, rng_word(r, t, (uint32_t)i, P_INNER, 0), bidx);
+  }
   if (st) { free(al); free(W); return st; }
   for (int j = 0; j < M; ++j) {
     double fz[64], e[64], v[64];
@@ -684,11 +713,12 @@ int ora_lookahead(const ora_model_in* min, const ora_dims* D, uint32_t t, const 
   return ORA_OK;
 }
 
-/* Step 4 for the given destinations only (for sampled comparisons at large N). */
+/* Step 4 for the given destinations only (for sampled comparisons at large N).
+ * bidx_in and alpha_out may be NULL (see finalize_group). */
 int ora_finalize(const ora_model_in* min, const ora_dims* D, uint32_t t, const double* y,
                  int64_t n_idx, const int64_t* idx, const int32_t* anc, const double* x_prev,
                  const double* z_prev, const double* lq_prev, const double* x_new, double* z_new,
-                 double* lq_new, int32_t* bidx) {
+                 double* lq_new, int32_t* bidx, const int32_t* bidx_in, double* alpha_out) {
   ora_model m;
   if (!dims_ok(D) || t < 1) return ORA_E_INVALID;
   int st = model_prepare(min, &m);
@@ -702,7 +732,8 @@ int ora_finalize(const ora_model_in* min, const ora_dims* D, uint32_t t, const d
     int64_t i = idx[q];
     int64_t a = anc[q];
     bad |= finalize_group(&m, D, &r, t, i, x_prev + a * d1, z_prev + a * M * d2, lq_prev + a * M,
-                          x_new + q * d1, y, z_new + q * M * d2, lq_new + q * M, bidx + q * M);
+                          x_new + q * d1, y, z_new + q * M * d2, lq_new + q * M, bidx + q * M,
+                          bidx_in ? bidx_in + q * M : NULL, alpha_out ? alpha_out + q * M : NULL);
   }
   return bad ? ORA_E_NUMERIC : ORA_OK;
 }
@@ -720,12 +751,15 @@ int ora_finalize(const ora_model_in* min, const ora_dims* D, uint32_t t, const d
  * The filtered mean is the importance-weighted look-ahead estimate taken before
  * resampling: sum over (i,m) of W^(i,m) [xbb^(i,m); mu^(i,m)], W proportional
  * to exp(lwhat). mean has d1 + d2 entries (x block first).
+ * Replay (anc_in, sel_in, bidx_in; each may be NULL): the outer ancestors, the
+ * selected draws and the local resampling indices are taken as given instead of
+ * drawn, every other quantity computed as above.
  */
 int ora_step(const ora_model_in* min, const ora_dims* D, uint32_t t, const double* y,
              const double* x_prev, const double* z_prev, const double* lq_prev, double* x_new,
              double* z_new, double* lq_new, double* lw, double* lwhat, double* xbb, int32_t* jla,
              int32_t* anc, int32_t* sel, int32_t* bidx, double* mean, double* logZ,
-             double* ess) {
+             double* ess, const int32_t* anc_in, const int32_t* sel_in, const int32_t* bidx_in) {
   ora_model m;
   if (!dims_ok(D) || t < 1) return ORA_E_INVALID;
   int st = model_prepare(min, &m);
@@ -769,7 +803,14 @@ int ora_step(const ora_model_in* min, const ora_dims* D, uint32_t t, const doubl
   double* W = (double*)malloc(sizeof(double) * (size_t)N);
   if (!W) return ORA_E_NOMEM;
   for (int64_t i = 0; i < N; ++i) W[i] = exp(lw[i] - lwmax);
-  st = ora_sys_global(W, N, rng_word(&r, t, 0, P_OUTER, 0), anc);
+  if (anc_in) {
+    for (int64_t i = 0; i < N; ++i) {
+      if (anc_in[i] < 0 || anc_in[i] >= N) { free(W); return ORA_E_INVALID; }
+      anc[i] = anc_in[i];
+    }
+  } else {
+    st = ora_sys_global(W, N, rng_word(&r, t, 0, P_OUTER, 0), anc);
+  }
   free(W);
   if (st) return st;
   /* step 4 */
@@ -781,11 +822,17 @@ int ora_step(const ora_model_in* min, const ora_dims* D, uint32_t t, const doubl
     for (int mm = 0; mm < L; ++mm) if (lwhat[a * L + mm] > mx) mx = lwhat[a * L + mm];
     for (int mm = 0; mm < L; ++mm) Wm[mm] = exp(lwhat[a * L + mm] - mx);
     int32_t mi = 0;
-    bad |= ora_sys_local(Wm, L, 1, rng_word(&r, t, (uint32_t)i, P_SEL, 0), &mi);
+    if (sel_in) {
+      mi = sel_in[i];
+      if (mi < 0 || mi >= L) { bad |= ORA_E_INVALID; mi = 0; }
+    } else {
+      bad |= ora_sys_local(Wm, L, 1, rng_word(&r, t, (uint32_t)i, P_SEL, 0), &mi);
+    }
     sel[i] = mi;
     for (int c = 0; c < d1; ++c) x_new[i * d1 + c] = xbb[(a * L + mi) * d1 + c];
     bad |= finalize_group(&m, D, &r, t, i, x_prev + a * d1, z_prev + a * M * d2, lq_prev + a * M,
-                          x_new + i * d1, y, z_new + i * M * d2, lq_new + i * M, bidx + i * M);
+                          x_new + i * d1, y, z_new + i * M * d2, lq_new + i * M, bidx + i * M,
+                          bidx_in ? bidx_in + i * M : NULL, NULL);
   }
   return bad ? ORA_E_NUMERIC : ORA_OK;
 }

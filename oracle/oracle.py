@@ -86,8 +86,8 @@ def load(path: str | None = None):
         lib.ora_lookahead.argtypes = [P, P, ctypes.c_uint32, P, ctypes.c_int64, P, P, P, P, P, P,
                                       P, P, P]
         lib.ora_finalize.argtypes = [P, P, ctypes.c_uint32, P, ctypes.c_int64, P, P, P, P, P, P,
-                                     P, P, P]
-        lib.ora_step.argtypes = [P, P, ctypes.c_uint32, P] + [P] * 16
+                                     P, P, P, P, P]
+        lib.ora_step.argtypes = [P, P, ctypes.c_uint32, P] + [P] * 19
         if path is None:
             _lib = lib
         return lib
@@ -149,9 +149,15 @@ class Oracle:
                                       _ptr(lq)), "init")
         return x, z, lq
 
-    def step(self, t, y, x, z, lq):
+    def step(self, t, y, x, z, lq, anc=None, sel=None, bidx=None):
+        """One full step from the state at t-1. anc, sel, bidx (optional): replay the
+        given outer ancestors (N), selected draws (N) and local resampling indices
+        (N, M) instead of drawing them."""
         m, N, M, L = self.m, self.N, self.M, self.L
         y = _f64(y); x = _f64(x); z = _f64(z); lq = _f64(lq)
+        anc_in = None if anc is None else np.ascontiguousarray(anc, dtype=np.int32)
+        sel_in = None if sel is None else np.ascontiguousarray(sel, dtype=np.int32)
+        bidx_in = None if bidx is None else np.ascontiguousarray(bidx, dtype=np.int32)
         out = dict(
             x=np.zeros((N, m.d1)), z=np.zeros((N, M, m.d2)), lq=np.zeros((N, M)),
             lw=np.zeros(N), lwhat=np.zeros((N, L)), xbb=np.zeros((N, L, m.d1)),
@@ -162,7 +168,8 @@ class Oracle:
                                _ptr(z), _ptr(lq), _ptr(out["x"]), _ptr(out["z"]), _ptr(out["lq"]),
                                _ptr(out["lw"]), _ptr(out["lwhat"]), _ptr(out["xbb"]),
                                _ptr(out["jla"]), _ptr(out["anc"]), _ptr(out["sel"]),
-                               _ptr(out["bidx"]), _ptr(out["mean"]), _ptr(logZ), _ptr(ess))
+                               _ptr(out["bidx"]), _ptr(out["mean"]), _ptr(logZ), _ptr(ess),
+                               _ptr(anc_in), _ptr(sel_in), _ptr(bidx_in))
         self._check(st, "step")
         out["logZ"] = float(logZ[0]); out["ess"] = float(ess[0])
         return out
@@ -180,19 +187,25 @@ class Oracle:
         self._check(st, "lookahead")
         return dict(lw=lw, jla=jla, xbb=xbb, lwhat=lwhat, mu=mu)
 
-    def finalize(self, t, y, idx, anc, x_prev, z_prev, lq_prev, x_new):
+    def finalize(self, t, y, idx, anc, x_prev, z_prev, lq_prev, x_new, bidx=None):
+        """Step 4 (local resampling, propagation, measurement update) for the outer
+        particles idx with ancestors anc. bidx (optional, (n, M)): replay these local
+        resampling indices. The result also holds alpha, the local resampling weights."""
         m, M = self.m, self.M
         idx = np.ascontiguousarray(idx, dtype=np.int64)
         anc = np.ascontiguousarray(anc, dtype=np.int32)
         n = len(idx)
         y = _f64(y); x_prev = _f64(x_prev); z_prev = _f64(z_prev); lq_prev = _f64(lq_prev)
         x_new = _f64(x_new)
+        bidx_in = None if bidx is None else np.ascontiguousarray(bidx, dtype=np.int32)
         z = np.zeros((n, M, m.d2)); lq = np.zeros((n, M)); bidx = np.zeros((n, M), np.int32)
+        alpha = np.zeros((n, M))
         st = self.lib.ora_finalize(ctypes.byref(m.s), ctypes.byref(self.dims), int(t), _ptr(y), n,
                                    _ptr(idx), _ptr(anc), _ptr(x_prev), _ptr(z_prev), _ptr(lq_prev),
-                                   _ptr(x_new), _ptr(z), _ptr(lq), _ptr(bidx))
+                                   _ptr(x_new), _ptr(z), _ptr(lq), _ptr(bidx), _ptr(bidx_in),
+                                   _ptr(alpha))
         self._check(st, "finalize")
-        return dict(z=z, lq=lq, bidx=bidx)
+        return dict(z=z, lq=lq, bidx=bidx, alpha=alpha)
 
     def run(self, ys, steps=None):
         """Free-running filter over ys[0..T-1] (y_1..y_T); returns per-step outputs."""

@@ -91,6 +91,9 @@ static dpf_status shape_class(dpf_batch& b, BatchClass& c) {
   c.launch.region = (uint32_t)region;
   c.launch.smem = region * 4;  // WARPS_PER_CTA warps per CTA
   c.launch.ppl = c.ppl;
+  bool full = true;  // every lane of every member holds ppl particles: the compile-time-M kernel
+  for (int f : c.members) full &= b.ctx[f]->M == 32 * c.ppl;
+  c.launch.mf = full ? 32 * c.ppl : 0;
   c.launch.xz = c.xz;
   c.launch.F = (int)c.members.size();
   c.launch.fstart = c.d_fstart;
@@ -243,12 +246,14 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
       return fail(set_error(DPF_E_UNSUPPORTED,
                             "dpf_batch_create: each M must be <= 256 with 16-byte rows (and L rows too)"));
   }
-  // classes: (variant, x-kind, PPL)
-  std::map<std::tuple<const Variant*, bool, int>, int> key2cls;
+  // classes: (variant, x-kind, PPL, M = 32 PPL): a filter steps with the same compiled
+  // kernel as when it runs alone, so a member reproduces the single filter bit for bit
+  std::map<std::tuple<const Variant*, bool, int, bool>, int> key2cls;
   for (int f = 0; f < F; ++f) {
     dpf_ctx* x = b->ctx[f];
     const bool xz = x->var->use_xz(*x);
-    const auto k = std::make_tuple(x->var, xz, x->var->ppl_for(x->M));
+    const int ppl = x->var->ppl_for(x->M);
+    const auto k = std::make_tuple(x->var, xz, ppl, x->M == 32 * ppl);
     auto it = key2cls.find(k);
     if (it == key2cls.end()) {
       BatchClass c;

@@ -93,28 +93,36 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 // Box-Muller: two words -> two independent standard normals,
 //   n0 = r cos(2 pi u_b), n1 = r sin(2 pi u_b),  r = sqrt(-2 ln u_a).
-// FP32: the radius uses the hardware log2 except for u_a > 1 - 1/64, where
-// -ln u_a = -ln(1 - v) with v = 1 - u_a (exact) is summed as its Taylor series
-// v + v^2/2 + v^3/3 + v^4/4 + v^5/5 (truncation below 2e-10 relative); the
-// angle uses the identity cos(2 pi u) = -cos(2 pi (u - 1/2)) (and likewise sin)
-// so the hardware sine and cosine see arguments in (-pi, pi). The accuracy is
-// verified exhaustively over all 2^23 values of each uniform.
+// FP32: the radius uses the hardware log2 except for u_a > 1 - 2^-10 (the top
+// 2^13 of the 2^23 values), where the hardware log2's absolute error would be
+// large relative to the small radius; there -ln u_a = -ln(1 - v) with v = 1 - u_a
+// (exact) is summed as its Taylor series v + v^2/2 + v^3/3 + v^4/4 (truncation
+// below 2^-41 relative). Below that band the hardware path's radius is within
+// 1.2e-6 of the exact one. The branch is taken by a warp of 32 independent draws
+// about 3% of the time. The angle uses the identity cos(2 pi u) = -cos(2 pi (u - 1/2))
+// (and likewise sin) so the hardware sine and cosine see arguments in (-pi, pi).
+// The accuracy is verified exhaustively over all 2^23 values of each uniform.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
   const uint32_t ka = wa >> 9;
   float r2;
-  if (ka >= (1u << 23) - (1u << 17)) {
+  if (__builtin_expect(ka >= (1u << 23) - (1u << 13), 0)) {
     const float v = fmaf((float)((1u << 23) - 1u - ka), 0x1p-23f, 0x1p-24f);
-    float s = fmaf(v, 0.2f, 0.25f);
-    s = fmaf(v, s, 0.333333333f);
+    float s = fmaf(v, 0.25f, 0.333333333f);
     s = fmaf(v, s, 0.5f);
     s = fmaf(v, s, 1.0f);
     r2 = 2.0f * v * s;
   } else {
-    r2 = -1.38629436f * lg2_approx(fmaf((float)ka, 0x1p-23f, 0x1p-24f));  // -2 ln 2 log2 u
+    // u_a = (ka + 1/2) 2^-23 = (1 + ka 2^-23) - (1 - 2^-24): the first term is ka placed in
+    // the mantissa of 1.0, and the difference is exact (Sterbenz); no integer conversion
+    const float ua = __int_as_float(0x3F800000u | ka) - 0x1.fffffep-1f;
+    r2 = -1.38629436f * lg2_approx(ua);  // -2 ln 2 log2 u
   }
   const float r = sqrt_approx(r2);
-  const float h = fmaf((float)(wb >> 9), 0x1p-23f, 0x1p-24f - 0.5f);  // u_b - 1/2, exact
-  const float th = h * 6.28318531f;
+  // the angle 2 pi (u_b - 1/2) with u_b - 1/2 = ((1 + kb 2^-23) - 3/2) + 2^-24: the
+  // difference is exact, and the fused multiply-add rounds 2 pi times the exact sum once
+  // (2 pi 2^-24 is the single-precision 2 pi scaled by a power of two, also exact)
+  const float th = fmaf(__int_as_float(0x3F800000u | (wb >> 9)) - 1.5f, 6.28318531f,
+                        0x1p-24f * 6.28318531f);
   n0 = -r * cos_approx(th);
   n1 = -r * sin_approx(th);
 }
@@ -189,6 +197,23 @@ __device__ __forceinline__ void normals_rk(const RoundKeys& rk, uint32_t t, uint
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if (4 * b + j < N) out[4 * b + j] = e[j];
+  }
+}
+
+// The dy normals of the look-ahead's common inner draw of inner particle k (purpose
+// LA_Z). For dy <= 2 two inner particles share one Philox block: particle k takes the
+// Box-Muller pair of words 2(k mod 2), 2(k mod 2)+1 of block (t, i, LA_Z, k / 2); for
+// dy > 2 they are the normals of draw (t, i, LA_Z, k).
+template <int DY, typename T>
+__device__ __forceinline__ void la_z_normals(Key key, uint32_t t, uint32_t i, uint32_t k, T (&out)[DY]) {
+  if constexpr (DY <= 2) {
+    const uint4 w = philox(ctr(t, i, P_LA_Z, k >> 1, 0u), key);
+    T a0, a1;
+    box_muller((k & 1u) ? w.z : w.x, (k & 1u) ? w.w : w.y, a0, a1);
+    out[0] = a0;
+    if constexpr (DY > 1) out[1] = a1;
+  } else {
+    normals<DY>(key, t, i, P_LA_Z, k, out);
   }
 }
 

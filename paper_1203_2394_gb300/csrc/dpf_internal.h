@@ -72,6 +72,7 @@ struct BatchLaunch {
   uint32_t region;          // bytes of shared memory per warp
   size_t smem;              // bytes per CTA
   int ppl;
+  int mf;                   // 32 ppl when every filter of the class has M = 32 ppl, else 0
   bool xz;
   int grid;
 };

@@ -78,7 +78,6 @@ struct StepArgs {
   int xp;        // padded length of an x row (16-byte rows)
   T scaleM, scaleL;  // 2^(31 - ceil(log2 M)) and 2^(31 - ceil(log2 L)): the local-rule scalings
   T logM, logL;      // log M, log L
-  int log2M;         // ceil(log2 M): halving steps of a search over M entries
   uint32_t stage_bytes, stage_tx;
   uint32_t off_stage, off_sz, off_slq, off_sx, off_slwh, off_sxbb;
   uint32_t off_cum, off_kd, off_E, off_xw, off_cw, off_xbs, off_row, off_red, off_part;
@@ -1002,7 +1001,7 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
         T* rec = kd + j * REC;
         rec[0] = (lqr[p] - sigma) * LOG2E;
         T e2[DY];
-        normals<DY>(a.key, a.t, (uint32_t)i, P_LA_Z, (uint32_t)j, e2);
+        la_z_normals<DY>(a.key, a.t, (uint32_t)i, (uint32_t)j, e2);
         T g_[DY];
 #pragma unroll
         for (int q = 0; q < DY; ++q) {

@@ -68,18 +68,6 @@ inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
 __device__ __forceinline__ float log2_fast(float x) { return lg2_approx(x); }
 __device__ __forceinline__ double log2_fast(double x) { return log2(x); }
 
-// First index k in [0, n) with cum[k] * scale > rhs, as a fixed number of
-// branch-free halving steps (cum is non-decreasing and cum[n-1] * scale > rhs).
-__device__ __forceinline__ int search_cum_fixed(const uint32_t* cum, int n, uint64_t scale,
-                                                uint64_t rhs, int steps) {
-  int b = 0;  // invariant: every index below b has cum * scale <= rhs
-  for (int s = steps - 1; s >= 0; --s) {
-    const int nb = b + (1 << s);
-    if (nb <= n && (uint64_t)cum[nb - 1] * scale <= rhs) b = nb;
-  }
-  return b;
-}
-
 // Vector moves of P consecutive elements (16-byte chunks where possible). float and
 // double move as float4 / float2 / double2; 32-bit integers as uint4 / uint2 (the casts
 // between uint32_t and int32_t keep the bits).
@@ -147,6 +135,72 @@ __device__ __forceinline__ void vst(T* dst, const T (&in)[P]) {
   }
 }
 
+// Local systematic resampling of M particles into M by offspring ranges. With the
+// integer rule out[j] = min{ k : cum_k M 2^16 > (j 2^16 + u16) C }, source k is
+// chosen by the destinations j in [J(cum_{k-1}), J(cum_k)), where
+//   J(c) = #{ j in [0, M) : (j 2^16 + u16) C < c M 2^16 }
+// counts the systematic points below the cumulative weight c. J is estimated in
+// single precision (within one of the count: c M / C <= M carries a relative error
+// of a few 2^-24) and settled by one exact 64-bit comparison on each side.
+__device__ __forceinline__ int sys_points_below(uint32_t c, uint32_t C, int M, uint32_t u16,
+                                                float m_over_C, float u_frac) {
+  int J = __float2int_ru(fmaf(__uint2float_rn(c), m_over_C, -u_frac));
+  J = min(max(J, 0), M);
+  const uint64_t R = ((uint64_t)c * (uint32_t)M) << 16;
+  if (J > 0 && ((((uint64_t)(J - 1)) << 16) + u16) * C >= R)
+    --J;
+  else if (J < M && ((((uint64_t)J) << 16) + u16) * C < R)
+    ++J;
+  return J;
+}
+
+// The ancestors bidx of this lane's destinations j = k0 .. k0 + P - 1, from the
+// inclusive cumulative weights loc of its sources k0 .. k0 + P - 1 (the same k).
+// Source k marks slot J(cum_k) with k + 1 when it is the last source with that count;
+// out[j] = #{ k : J(cum_k) <= j } is then the running maximum of the slots. `slot`
+// is M words of the warp's shared memory. Warp-wide; every lane takes part.
+template <int P>
+__device__ __forceinline__ void sys_local_offspring(const uint32_t (&loc)[P], uint32_t C, int M,
+                                                    uint32_t u16, int k0, bool act, int lane,
+                                                    int* slot, int (&bidx)[P]) {
+  const float m_over_C = __fdividef((float)M, __uint2float_rn(C));
+  const float u_frac = (float)u16 * 0x1p-16f;
+  int J[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) J[p] = act ? sys_points_below(loc[p], C, M, u16, m_over_C, u_frac) : M;
+  int Jn = __shfl_down_sync(FULL, J[0], 1);
+  if (lane == 31) Jn = M;
+  int zero[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) zero[p] = 0;
+  if (act) vst<int, P>(slot + k0, zero);
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int nxt = p + 1 < P ? J[p + 1] : Jn;
+    if (J[p] < nxt && J[p] < M) slot[J[p]] = k0 + p + 1;
+  }
+  __syncwarp();
+  int s[P];
+  if (act) vld<int, P>(slot + k0, s);
+  else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) s[p] = 0;
+  }
+#pragma unroll
+  for (int p = 1; p < P; ++p) s[p] = max(s[p], s[p - 1]);
+  int v = s[P - 1];  // inclusive warp max-scan of the lanes' running maxima
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v = max(v, n);
+  }
+  int before = __shfl_up_sync(FULL, v, 1);
+  if (lane == 0) before = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) bidx[p] = min(max(s[p], before), M - 1);
+}
+
 // acc[p] += a * x[p] for all p: packed FP32x2 FMAs on float pairs, scalar otherwise.
 template <typename T, int P>
 __device__ __forceinline__ void axpy(T a, const T (&x)[P], T (&acc)[P]) {
@@ -211,12 +265,15 @@ __device__ __forceinline__ void warp_stage(const StepArgs<T>& a, unsigned char* 
 // Steps groups gfirst, gfirst + W, ... (< gend) of one filter with one warp:
 // `mc` and `a` may live in kernel parameters or in global memory; `ws` is the
 // warp's shared-memory region, `bar` its stage barrier, `phase` its parity.
-template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
+// MF = 32 PPL when the launch has M = 32 PPL (every lane holds PPL particles: M is a
+// compile-time constant and no lane is idle), else 0 (M from the arguments).
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL, int MF = 0>
 __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const StepArgs<T>& a,
                                          long long gfirst, long long gend, long long W,
                                          unsigned char* ws, uint64_t* bar, uint32_t& phase) {
+  static_assert(MF == 0 || MF == 32 * PPL, "MF is 0 or 32 PPL");
   const int lane = threadIdx.x & 31;
-  const int M = a.M, L = a.L;
+  const int M = MF ? MF : a.M, L = a.L;
   const long long N = a.N;
   const long long NM = N * (long long)M;
   T* sz = (T*)(ws + a.off_sz);
@@ -249,7 +306,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
   const RoundKeys rk = round_keys(a.key);
   // this lane's inner particles are k0 .. k0 + PPL - 1 (consecutive)
   const int k0 = PPL * lane;
-  const bool act = k0 < M;
+  const bool act = MF ? true : k0 < M;
   if (gfirst == 0 && lane == 0) *a.Csum = 0ull;  // the outer reduction of this step sums into it
 
   long long g = gfirst;
@@ -329,22 +386,27 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
       int msel;
       uint32_t uin;
       {
+        // draws m = lane and (when L > 32, a warp-uniform branch) m = lane + 32
+        const bool two = L > 32;
         const T l0 = lane < L ? slwh[lane] : NEG;
-        const T l1 = lane + 32 < L ? slwh[lane + 32] : NEG;
+        const T l1 = two && lane + 32 < L ? slwh[lane + 32] : NEG;
         const T mx = warp_max(fmax(l0, l1));
         const uint32_t c0 = lane < L ? (uint32_t)floor(exp2_t((l0 - mx) * LOG2E) * a.scaleL) : 0u;
-        const uint32_t c1 =
-            lane + 32 < L ? (uint32_t)floor(exp2_t((l1 - mx) * LOG2E) * a.scaleL) : 0u;
-        uint32_t s0 = c0, s1 = c1;
+        uint32_t s0 = c0, s1 = 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
-          if (lane >= o) {
-            s0 += n0;
-            s1 += n1;
+          const uint32_t n0 = __shfl_up_sync(FULL, s0, o);
+          if (lane >= o) s0 += n0;
+        }
+        if (two) {
+          s1 = lane + 32 < L ? (uint32_t)floor(exp2_t((l1 - mx) * LOG2E) * a.scaleL) : 0u;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n1 = __shfl_up_sync(FULL, s1, o);
+            if (lane >= o) s1 += n1;
           }
         }
-        const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
+        const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = two ? __shfl_sync(FULL, s1, 31) : 0u;
         const uint64_t C = (uint64_t)tot0 + tot1;
         const uint32_t w =
             philox_rk(ctr(a.t - 1, (uint32_t)i, lane == 0 ? P_SEL : P_INNER, 0u, 0u), rk).x;
@@ -352,7 +414,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         uin = __shfl_sync(FULL, w, 1);
         const uint64_t rhs = (uint64_t)usel * C;
         const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
-        const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
+        const unsigned b1 = two ? __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs) : 0u;
         msel = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
         if (C == 0 || msel >= L) {
           if (lane == 0) atomicOr(a.err, ERR_NUMERIC);
@@ -404,6 +466,8 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 #pragma unroll
       for (int p = 0; p < PPL; ++p) amax = fmax(amax, alpha[p]);
       amax = warp_max(amax);
+      // ancestors of the lane's destinations by offspring ranges (sys_local_offspring)
+      int bidx[PPL];
       {
         uint32_t loc[PPL];
         uint32_t run = 0;
@@ -421,11 +485,11 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         const uint32_t base = v - run;
 #pragma unroll
         for (int p = 0; p < PPL; ++p) loc[p] += base;
-        if (act) vst<uint32_t, PPL>(cum + k0, loc);
+        const uint32_t C = __shfl_sync(FULL, v, 31);
+        if (C == 0u && lane == 0) atomicOr(a.err, ERR_NUMERIC);
+        sys_local_offspring<PPL>(loc, C, M, uin >> 16, k0, act, lane, (int*)cum, bidx);
       }
-      __syncwarp();
       // ---- propagation and the y_{t-1} update (eq. qbar) ----
-      const uint32_t C = cum[M - 1];
       T azx[D2];
 #pragma unroll
       for (int r = 0; r < D2; ++r) {
@@ -446,44 +510,6 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 #pragma unroll
           for (int c = 0; c < DY; ++c) if (c <= q) v += mc.LrInv[q][c] * res[c];
           yh[q] = v;
-        }
-      }
-      // ancestors of the lane's destinations: a binary search for the first, then
-      // a forward walk (the systematic points are increasing)
-      int bidx[PPL];
-      {
-        const uint64_t scale = (uint64_t)M << 16;
-        const uint64_t u16 = uin >> 16;
-        if ((M & (M - 1)) == 0) {
-          // M a power of two: cum * 2^sh <= rhs exactly when cum <= rhs >> sh (a 32-bit
-          // bound: rhs < M 2^16 C and C < 2^31), so the search compares 32-bit words
-          const int sh = a.log2M + 16;
-          int b = 0;
-          if (act) {
-            const uint32_t thr = (uint32_t)(((((uint64_t)k0 << 16) + u16) * C) >> sh);
-            for (int st = a.log2M - 1; st >= 0; --st) {
-              const int nb = b + (1 << st);
-              if (nb <= M && cum[nb - 1] <= thr) b = nb;
-            }
-          }
-#pragma unroll
-          for (int p = 0; p < PPL; ++p) {
-            if (p > 0 && act) {
-              const uint32_t thr = (uint32_t)(((((uint64_t)(k0 + p) << 16) + u16) * C) >> sh);
-              while (cum[b] <= thr) ++b;
-            }
-            bidx[p] = b;
-          }
-        } else {
-          int b = act ? search_cum_fixed(cum, M, scale, (((uint64_t)k0 << 16) + u16) * C, a.log2M) : 0;
-#pragma unroll
-          for (int p = 0; p < PPL; ++p) {
-            if (p > 0 && act) {
-              const uint64_t rhs = (((uint64_t)(k0 + p) << 16) + u16) * C;
-              while ((uint64_t)cum[b] * scale <= rhs) ++b;
-            }
-            bidx[p] = b;
-          }
         }
       }
       if (a.dbg_b && act) vst<int, PPL>(a.dbg_b + i * M + k0, bidx);
@@ -584,12 +610,40 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
     for (int p = 0; p < PPL; ++p) ak[p] = act ? (lqr[p] - sigma) * LOG2E : NEG;
     {
       T e2[DY][PPL];
+      if constexpr (DY <= 2 && PPL % 2 == 0) {
+        // the lane's particles k0 + p, k0 + p + 1 (k0 + p even) share one Philox block
+        // (la_z_normals): its first word pair for the first, its second for the other
 #pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        T e[DY];
-        normals_rk<DY>(rk, a.t, (uint32_t)i, P_LA_Z, (uint32_t)(k0 + p), e);
+        for (int p = 0; p < PPL; p += 2) {
+          const uint4 w = philox_rk(ctr(a.t, (uint32_t)i, P_LA_Z, (uint32_t)(k0 + p) >> 1, 0u), rk);
+          T n0, n1, n2, n3;
+          box_muller(w.x, w.y, n0, n1);
+          box_muller(w.z, w.w, n2, n3);
+          e2[0][p] = n0;
+          e2[0][p + 1] = n2;
+          if constexpr (DY > 1) {
+            e2[1][p] = n1;
+            e2[1][p + 1] = n3;
+          }
+        }
+      } else if constexpr (DY <= 2) {
 #pragma unroll
-        for (int q = 0; q < DY; ++q) e2[q][p] = e[q];
+        for (int p = 0; p < PPL; ++p) {
+          const uint32_t k = (uint32_t)(k0 + p);
+          const uint4 w = philox_rk(ctr(a.t, (uint32_t)i, P_LA_Z, k >> 1, 0u), rk);
+          T n0, n1;
+          box_muller((k & 1u) ? w.z : w.x, (k & 1u) ? w.w : w.y, n0, n1);
+          e2[0][p] = n0;
+          if constexpr (DY > 1) e2[1][p] = n1;
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          T e[DY];
+          normals_rk<DY>(rk, a.t, (uint32_t)i, P_LA_Z, (uint32_t)(k0 + p), e);
+#pragma unroll
+          for (int q = 0; q < DY; ++q) e2[q][p] = e[q];
+        }
       }
       T gg[DY][PPL];
 #pragma unroll
@@ -692,6 +746,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
     bool general = XZ;
     if (!XZ) {
       // one pass: e(m,k) = 2^(a_k - |c'_m - g'_k|^2), S_m = sum_k e, B_k = sum_m e
+#pragma unroll 4
       for (int m = 0; m < L; ++m) {
         T v[PPL];
 #pragma unroll
@@ -782,24 +837,29 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
       }
     }
     // ---- per-draw weights, the outer weight and the x part of the filtered mean ----
+    // draws m = lane and (L > 32, a warp-uniform branch) m = lane + 32
+    const bool two = L > 32;
     T lw0 = NEG, lw1 = NEG;
-    if (lane < L)
+    if (lane < L) {
       lw0 = mc.lognorm_y + LN2 * ((log2_fast(rowS[lane]) + shS[lane]) - (log2_fast(rowA[lane]) + shA[lane]));
-    if (lane + 32 < L)
+      a.lwh_new[i * L + lane] = lw0;
+    }
+    if (two && lane + 32 < L) {
       lw1 = mc.lognorm_y + LN2 * ((log2_fast(rowS[lane + 32]) + shS[lane + 32]) -
                                   (log2_fast(rowA[lane + 32]) + shA[lane + 32]));
-    if (lane < L) a.lwh_new[i * L + lane] = lw0;
-    if (lane + 32 < L) a.lwh_new[i * L + lane + 32] = lw1;
-    const T mx = warp_max(fmax(lw0, lw1));
+      a.lwh_new[i * L + lane + 32] = lw1;
+    }
+    const T mx = warp_max(two ? fmax(lw0, lw1) : lw0);
     const T p0 = lane < L ? exp2_t((lw0 - mx) * LOG2E) : T(0);
-    const T p1 = lane + 32 < L ? exp2_t((lw1 - mx) * LOG2E) : T(0);
+    const T p1 = two && lane + 32 < L ? exp2_t((lw1 - mx) * LOG2E) : T(0);
     const T psum = warp_sum(p0 + p1);
     const T lwi = mx + LN2 * log2_fast(psum) - a.logL;
+    const T ipsum = T(1) / psum;
 #pragma unroll
     for (int c = 0; c < D1; ++c) {
-      T v = (lane < L ? p0 * xbs[lane * D1 + c] : T(0)) +
-            (lane + 32 < L ? p1 * xbs[(lane + 32) * D1 + c] : T(0));
-      v = warp_sum(v) / psum;
+      T v = lane < L ? p0 * xbs[lane * D1 + c] : T(0);
+      if (two && lane + 32 < L) v += p1 * xbs[(lane + 32) * D1 + c];
+      v = warp_sum(v) * ipsum;
       if (lane == 0) a.xm[(long long)c * N + i] = v;
     }
     if (lane == 0) {
@@ -872,7 +932,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
 }
 
 
-template <typename T, int D1, int D2, int DY, bool XZ, int PPL>
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL, int MF>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>())
     step_warp_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc,
                      const __grid_constant__ StepArgs<T> a) {
@@ -885,7 +945,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>()
   }
   __syncwarp();
   uint32_t phase = 0;
-  warp_run<T, D1, D2, DY, XZ, PPL>(mc, a, (long long)blockIdx.x * WARPS_PER_CTA + wib, a.N,
+  warp_run<T, D1, D2, DY, XZ, PPL, MF>(mc, a, (long long)blockIdx.x * WARPS_PER_CTA + wib, a.N,
                                    (long long)gridDim.x * WARPS_PER_CTA,
                                    smem_raw + (size_t)wib * a.stage_bytes, &bars[wib], phase);
 }
@@ -895,7 +955,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>()
 // first item of filter f) and each warp steps a contiguous chunk of them.
 // With SHARED every filter of the launch has the same model constants, passed
 // by value (read through the constant cache); otherwise they come from mcs[f].
-template <typename T, int D1, int D2, int DY, bool XZ, int PPL, bool SHARED>
+template <typename T, int D1, int D2, int DY, bool XZ, int PPL, bool SHARED, int MF>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>())
     step_warp_batch_kernel(const __grid_constant__ MC<T, D1, D2, DY> mc1,
                            const MC<T, D1, D2, DY>* __restrict__ mcs,
@@ -923,7 +983,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>()
   while (item < iend) {
     while (fstart[f + 1] <= item) ++f;
     const long long seg_end = iend < fstart[f + 1] ? iend : fstart[f + 1];
-    warp_run<T, D1, D2, DY, XZ, PPL>(SHARED ? mc1 : mcs[f], descs[f], item - fstart[f],
+    warp_run<T, D1, D2, DY, XZ, PPL, MF>(SHARED ? mc1 : mcs[f], descs[f], item - fstart[f],
                                      seg_end - fstart[f], 1, ws, &bars[wib], phase);
     item = seg_end;
   }

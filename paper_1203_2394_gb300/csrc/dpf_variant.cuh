@@ -166,9 +166,9 @@ struct VariantImpl {
     return cuda_error(cudaGetLastError(), "step kernel launch");
   }
 
-  template <bool XZ, int PPL>
-  static dpf_status launch_warp(Ctx& x, StepArgs<T>& a) {
-    auto k = step_warp_kernel<T, D1, D2, DY, XZ, PPL>;
+  template <bool XZ, int PPL, int MF>
+  static dpf_status launch_warp_mf(Ctx& x, StepArgs<T>& a) {
+    auto k = step_warp_kernel<T, D1, D2, DY, XZ, PPL, MF>;
     static bool attr_done = false;
     if (!attr_done) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -187,6 +187,12 @@ struct VariantImpl {
     const long long grid = std::min<long long>((x.N + WARPS_PER_CTA - 1) / WARPS_PER_CTA, x.grid_step);
     k<<<(unsigned)grid, WARPS_PER_CTA * 32, sm, x.stream>>>(cst(x), a);
     return cuda_error(cudaGetLastError(), "step kernel launch");
+  }
+  // M = 32 PPL (every lane full) takes the kernel compiled for that M
+  template <bool XZ, int PPL>
+  static dpf_status launch_warp(Ctx& x, StepArgs<T>& a) {
+    if (x.M == 32 * PPL) return launch_warp_mf<XZ, PPL, 32 * PPL>(x, a);
+    return launch_warp_mf<XZ, PPL, 0>(x, a);
   }
 
   template <bool XZ>
@@ -239,7 +245,6 @@ struct VariantImpl {
     a.scaleL = (T)std::ldexp(1.0, 31 - ceil_log2_i(x.L));
     a.logM = (T)std::log((double)x.M);
     a.logL = (T)std::log((double)x.L);
-    a.log2M = ceil_log2_i(x.M);
     a.glist = x.glist_cur;
     a.gcount = x.gcount_cur;
     a.gskip = x.gskip_cur;
@@ -274,9 +279,9 @@ struct VariantImpl {
                : warp_geometry<T, D1, D2, DY, false>(M, L, nullptr)) / WARPS_PER_CTA;
   }
 
-  template <bool XZ, int PPL, bool SHARED>
+  template <bool XZ, int PPL, bool SHARED, int MF>
   static dpf_status batch_kernel(const BatchLaunch& b, cudaStream_t s, int* occ) {
-    auto k = step_warp_batch_kernel<T, D1, D2, DY, XZ, PPL, SHARED>;
+    auto k = step_warp_batch_kernel<T, D1, D2, DY, XZ, PPL, SHARED, MF>;
     static bool attr_done = false;
     if (!attr_done) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -294,13 +299,17 @@ struct VariantImpl {
                                                 b.fstart, b.F, b.chunk, b.region);
     return cuda_error(cudaGetLastError(), "batch step kernel launch");
   }
+  template <bool XZ, int PPL, bool SHARED>
+  static dpf_status batch_mf(const BatchLaunch& b, cudaStream_t s, int* occ) {
+    return b.mf ? batch_kernel<XZ, PPL, SHARED, 32 * PPL>(b, s, occ) : batch_kernel<XZ, PPL, SHARED, 0>(b, s, occ);
+  }
   template <bool XZ, bool SHARED>
   static dpf_status batch_ppl2(const BatchLaunch& b, cudaStream_t s, int* occ) {
     switch (b.ppl) {
-      case 1: return batch_kernel<XZ, 1, SHARED>(b, s, occ);
-      case 2: return batch_kernel<XZ, 2, SHARED>(b, s, occ);
-      case 4: return batch_kernel<XZ, 4, SHARED>(b, s, occ);
-      default: return batch_kernel<XZ, 8, SHARED>(b, s, occ);
+      case 1: return batch_mf<XZ, 1, SHARED>(b, s, occ);
+      case 2: return batch_mf<XZ, 2, SHARED>(b, s, occ);
+      case 4: return batch_mf<XZ, 4, SHARED>(b, s, occ);
+      default: return batch_mf<XZ, 8, SHARED>(b, s, occ);
     }
   }
   template <bool XZ>
