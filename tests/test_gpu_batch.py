@@ -5,7 +5,9 @@
   their own model constants or share one set.
 * A graph-captured run equals step-by-step stepping.
 * Members of the d = 16 variants (splits 1/15 and 8/8, dy = 4) agree with the
-  FP64 oracle, teacher-forced, within the FP32 tolerances.
+  FP64 oracle, teacher-forced, within the FP32 tolerances: every selection and
+  local resampling index equal or an explained flip, every group's inner state
+  (z and lq) equal to the oracle's given the member's indices.
 * After autotuning (which may change the launch shape, hence rounding) the
   results stay within those tolerances.
 """
@@ -14,7 +16,7 @@ import pytest
 
 from oracle import oracle
 from paper_1203_2394_gb300 import workloads
-from tests.gpu_util import check_lwhat, rel, state_from_gpu, word
+from tests.gpu_util import check_inner_step, check_lwhat, check_selection, rel, state_from_gpu, word
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -95,6 +97,7 @@ def test_members_match_oracle_teacher_forced(f):
     d1, N, M = MEMBERS[f]
     seed = SEED0 + f
     ora = oracle.Oracle(oracle.OracleModel.from_spec(specs[f], d1), N, M, L, seed, nthreads=8)
+    b.filter(f).set_debug(True)
     prev = None
     for t in range(1, T + 1):
         b.step_device(yd[t - 1].data_ptr())
@@ -109,11 +112,15 @@ def test_members_match_oracle_teacher_forced(f):
             m.read("anc"), oracle.sys_global(m.read("wout").astype(np.float64),
                                              word(seed, t, 0, oracle.P_OUTER)))
         if prev is not None:
-            pa, px, pz, plq = prev
-            fin = ora.finalize(t - 1, ys[t - 2, f], np.arange(N), pa, px, pz, plq, x)
-            close = np.all(rel(z, fin["z"]) <= 1e-5, axis=(1, 2))
-            assert close.mean() >= 0.95, close.mean()
-        prev = (m.read("anc"), x, z, lq)
+            # the inner step of t-1 ran at the start of this call (lg16: x depends on z)
+            pa, px, pz, plq, plwhat, pxbb = prev
+            sel = m.read("sel")
+            check_selection(seed, t - 1, pa, plwhat, sel)
+            np.testing.assert_allclose(x, pxbb[pa, sel], rtol=0, atol=0)
+            check_inner_step(ora, seed, t - 1, ys[t - 2, f], pa, px, pz, plq, x, z, lq, m.read("bidx"),
+                             x_in_alpha=True)
+        prev = (m.read("anc"), x, z, lq, m.read("lwhat").astype(np.float64),
+                m.read("xbb").astype(np.float64))
 
 
 def test_autotune_keeps_results_within_tolerance():

@@ -6,15 +6,22 @@ output within 1e-9.
 FP32 (the growth/linear-Gaussian workload and lg4 in FP32, several tiles and a
 ragged M): teacher-forced per step, i.e. the oracle starts each step from the
 GPU's state: log-weights within 1e-5 relative (floor 1), means within 1e-4,
-outer ancestors bit-exact given the weights the GPU fed to the resampler,
-inner steps exact wherever the local resampling indices agree.
+outer ancestors bit-exact given the weights the GPU fed to the resampler. Every
+selection and local resampling index the GPU took equals the oracle's, or its
+systematic point lies within the derived FP32 bound of a cumulative-weight
+boundary (an explained flip; tests/gpu_util.explain_flips); the inner state of
+every group matches the oracle's given the GPU's indices.
+Replay (FP32, 10 steps): the oracle runs free from its own FP64 state but takes
+the GPU's outer ancestors, selections and local resampling indices; the GPU's
+filtered means stay within 1e-4 relative of the oracle's.
 """
 import numpy as np
 import pytest
 
 from oracle import oracle
 from paper_1203_2394_gb300 import workloads
-from tests.gpu_util import check_lwhat, rel, state_from_gpu, word
+from tests.gpu_util import (LOG2E, check_inner_step, check_lwhat, check_selection, explain_flips,
+                            fp32_weight_relerr, rel, state_from_gpu, word)
 
 pytestmark = pytest.mark.gpu
 
@@ -71,8 +78,8 @@ def test_fp64_free_running_lg4_full_size():
 
 CASES = [
     # (workload, d1, N, M, L, steps)
-    ("growth_clg10", 2, 384, 128, 16, 8),
-    ("growth_clg10", 2, 300, 100, 8, 6),   # ragged M: 100 of 128 threads active
+    ("growth_clg10", 2, 384, 128, 16, 10),
+    ("growth_clg10", 2, 300, 100, 8, 10),  # ragged M: 100 of 128 threads active
     ("lg4", 2, 256, 64, 8, 8),             # x transition depends on z (the general path)
     ("lg4", 2, 200, 20, 5, 6),             # M below a warp
 ]
@@ -87,7 +94,6 @@ def test_fp32_teacher_forced(case):
     seed = 7
     f, o = _mk(spec, dpf.DPF_F32, N, M, L, seed)
     f.set_debug(True)
-    flips_inner = 0
     prev = None
     for t in range(1, T + 1):
         mean, _ = f.step(ys[t - 1].astype(np.float32))
@@ -108,25 +114,56 @@ def test_fp32_teacher_forced(case):
             # the inner step of t-1 ran at the start of this call
             pa, px, pz, plq, plwhat, pxbb = prev
             sel = f.read("sel")
-            ref_sel = np.array([oracle.sys_local(np.exp(plwhat[pa[i]] - plwhat[pa[i]].max()), 1,
-                                                 word(seed, t - 1, i, oracle.P_SEL))[0]
-                                for i in range(N)])
-            assert np.mean(sel != ref_sel) <= 0.002
-            xsel = pxbb[pa, sel]
-            np.testing.assert_allclose(x, xsel, rtol=0, atol=0)
-            fin = o.finalize(t - 1, ys[t - 2].astype(np.float32), np.arange(N), pa, px, pz, plq, x)
-            bidx = f.read("bidx")
-            same = np.all(bidx == fin["bidx"], axis=1)
-            flips_inner += int((~same).sum())
-            assert np.max(rel(z[same], fin["z"][same])) <= 1e-5
-            assert np.max(rel(lq[same], fin["lq"][same])) <= 1e-5
+            check_selection(seed, t - 1, pa, plwhat, sel)
+            np.testing.assert_allclose(x, pxbb[pa, sel], rtol=0, atol=0)
+            check_inner_step(o, seed, t - 1, ys[t - 2].astype(np.float32), pa, px, pz, plq, x, z, lq,
+                             f.read("bidx"), x_in_alpha=(name == "lg4"))
         prev = (anc, x, z, lq, f.read("lwhat").astype(np.float64), xbb)
-    assert flips_inner <= max(2, N * T // 200), flips_inner
+
+
+REPLAY = [  # (workload, N, M, L)
+    ("growth_clg10", 384, 128, 16),
+    ("lg4", 256, 64, 8),
+]
+
+
+@pytest.mark.parametrize("case", REPLAY, ids=[f"{c[0]}-N{c[1]}-M{c[2]}-L{c[3]}" for c in REPLAY])
+def test_fp32_replay_10_steps(case):
+    """The FP32 GPU filter against the FP64 oracle over the first 10 steps: the oracle keeps
+    its own state and takes only the GPU's discrete decisions (outer ancestors, selected
+    draws, local resampling indices); the filtered means stay within 1e-4 relative."""
+    from paper_1203_2394_gb300 import dpf
+    name, N, M, L = case
+    T = 10
+    spec = workloads.make_model(name, 0)
+    _, ys = workloads.simulate(spec, T + 2, 0)
+    ys = ys.astype(np.float32)
+    seed = 3
+    f, o = _mk(spec, dpf.DPF_F32, N, M, L, seed)
+    f.set_debug(True)
+    means, anc, sel, bidx = {}, {}, {}, {}
+    for t in range(1, T + 2):
+        mean, _ = f.step(ys[t - 1])
+        if t <= T:
+            means[t], anc[t] = mean, f.read("anc")
+        if t >= 2:  # the inner step of t-1 ran at the start of call t
+            sel[t - 1], bidx[t - 1] = f.read("sel"), f.read("bidx")
+    x, z, lq = o.init()
+    worst = 0.0
+    for t in range(1, T + 1):
+        r = o.step(t, ys[t - 1], x, z, lq, anc=anc[t], sel=sel[t], bidx=bidx[t])
+        err = np.max(rel(means[t], r["mean"]))
+        worst = max(worst, err)
+        assert err <= 1e-4, (t, err, means[t], r["mean"])
+        x, z, lq = r["x"], r["z"], r["lq"]
+    assert worst > 0.0  # FP32 against FP64: the two really differ
 
 
 def test_full_size_growth_clg10_sampled():
     """The benchmark's own workload and launch shape (N=65536, M=128, L=16): sampled
-    groups against the oracle, the outer resampling bit-exact on all N."""
+    groups against the oracle (look-ahead weights, then their selection, local
+    resampling, propagation and update one call later), the outer resampling
+    bit-exact on all N."""
     from paper_1203_2394_gb300 import dpf
     spec = workloads.make_model("growth_clg10", 0)
     sz = spec.sizes
@@ -135,17 +172,41 @@ def test_full_size_growth_clg10_sampled():
     f, o = _mk(spec, dpf.DPF_F32, N, M, L, seed)
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(N, 256, replace=False))
-    for t in range(1, 4):
+    f.set_debug(True)
+    prev = None
+    for t in range(1, 5):
         f.step(ys[t - 1].astype(np.float32))
         x, z, lq = state_from_gpu(f)
-        ref = o.lookahead(t, ys[t - 1].astype(np.float32), idx, x, z, lq)
-        lw = f.read("lw").astype(np.float64)
-        assert np.max(rel(lw[idx], ref["lw"])) <= 1e-5
-        check_lwhat(f.read("lwhat").astype(np.float64)[idx], ref["lwhat"], 1e-5)
-        wout = f.read("wout").astype(np.float64)
-        np.testing.assert_array_equal(f.read("anc"),
-                                      oracle.sys_global(wout, word(seed, t, 0, oracle.P_OUTER)))
-        assert np.all(np.isfinite(lw))
+        if t <= 3:
+            ref = o.lookahead(t, ys[t - 1].astype(np.float32), idx, x, z, lq)
+            lw = f.read("lw").astype(np.float64)
+            assert np.max(rel(lw[idx], ref["lw"])) <= 1e-5
+            check_lwhat(f.read("lwhat").astype(np.float64)[idx], ref["lwhat"], 1e-5)
+            wout = f.read("wout").astype(np.float64)
+            np.testing.assert_array_equal(f.read("anc"),
+                                          oracle.sys_global(wout, word(seed, t, 0, oracle.P_OUTER)))
+            assert np.all(np.isfinite(lw))
+        if prev is not None:
+            # the inner step of t-1 (selection, local resampling, propagation, update) of
+            # the sampled destinations, from the full state of t-2
+            pa, px, pz, plq, plwhat, pxbb = prev
+            sel = f.read("sel")
+            check_selection(seed, t - 1, pa[idx], plwhat, sel[idx], idx)
+            np.testing.assert_allclose(x[idx], pxbb[pa[idx], sel[idx]], rtol=0, atol=0)
+            bidx = f.read("bidx")[idx]
+            own = o.finalize(t - 1, ys[t - 2].astype(np.float32), idx, pa[idx], px, pz, plq, x[idx])
+            rep = o.finalize(t - 1, ys[t - 2].astype(np.float32), idx, pa[idx], px, pz, plq, x[idx],
+                             bidx=bidx)
+            for q in np.nonzero(np.any(bidx != own["bidx"], axis=1))[0]:
+                al = own["alpha"][q]
+                explain_flips(np.exp(al - al.max()), bidx[q], own["bidx"][q],
+                              word(seed, t - 1, int(idx[q]), oracle.P_INNER), M,
+                              fp32_weight_relerr((al - al.max()) * LOG2E))
+            assert np.max(rel(z[idx], rep["z"])) <= 1e-5
+            assert np.max(rel(lq[idx], rep["lq"])) <= 1e-5
+        if t <= 3:
+            prev = (f.read("anc"), x, z, lq, f.read("lwhat").astype(np.float64),
+                    f.read("xbb").astype(np.float64))
 
 
 def test_errors_are_status_codes():
