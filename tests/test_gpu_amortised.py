@@ -12,7 +12,7 @@ import pytest
 
 from oracle import learned, oracle
 from paper_1203_2394_gb300 import workloads
-from tests.gpu_util import check_fallback, rel, state_from_gpu, word
+from tests.gpu_util import check_fallback, check_selection, rel, state_from_gpu, word
 from tests.kalman import kalman
 
 pytestmark = pytest.mark.gpu
@@ -81,6 +81,7 @@ def test_amortised_inner_update_teacher_forced():
         if prev is not None:
             pa, px, pz, plq, plwhat, pxbb = prev
             sel = f.read("sel")
+            check_selection(seed, t - 1, pa, plwhat, sel)  # every flip explained
             np.testing.assert_array_equal(x, pxbb[pa, sel])
             fin = o.finalize(t - 1, ys[t - 2].astype(np.float32), np.arange(N), pa, px, pz, plq, x)
             bidx = f.read("bidx")

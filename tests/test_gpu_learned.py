@@ -18,7 +18,7 @@ import pytest
 
 from oracle import learned, oracle
 from paper_1203_2394_gb300 import workloads
-from tests.gpu_util import check_fallback, check_lwhat, rel, state_from_gpu, word
+from tests.gpu_util import check_fallback, check_lwhat, check_selection, rel, state_from_gpu, word
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -216,9 +216,7 @@ def test_learned_inner_update_teacher_forced():
         if prev is not None and t >= 2:
             pa, px, pz, plq, plwhat, pxbb = prev
             sel = f.read("sel")
-            ref_sel = np.array([oracle.sys_local(np.exp(plwhat[pa[i]] - plwhat[pa[i]].max()), 1,
-                                                 word(seed, t - 1, i, oracle.P_SEL))[0] for i in range(N)])
-            assert np.mean(sel != ref_sel) <= 0.01
+            check_selection(seed, t - 1, pa, plwhat, sel)  # every flip explained
             np.testing.assert_array_equal(x, pxbb[pa, sel])
             fin = o.finalize(t - 1, ys[t - 2].astype(np.float32), np.arange(N), pa, px, pz, plq, x)
             bidx = f.read("bidx")
