@@ -59,6 +59,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_tflops():
+    """The measured dense BF16 burst rate (TFLOP/s) of this machine's GPUs."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -146,6 +154,33 @@ def barrier(ws: int):
         dist.barrier()
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_median(spec, N, M, L, runs=3, **kw):
+    """cpu_oracle_rate run `runs` times: (median rate, threads, sample, all rates)."""
+    rates, threads, sample = [], None, None
+    for _ in range(runs):
+        r, threads, sample = cpu_oracle_rate(spec, N, M, L, **kw)
+        rates.append(r)
+    return statistics.median(rates), threads, sample, rates
+
+
 def cpu_oracle_rate(spec, N, M, L, budget_s=15.0, n_sample=65536, max_steps=16, seed=0, threads=None):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload: the
     first steps (at most max_steps, stopping after budget_s seconds) of a filter with
@@ -211,8 +246,8 @@ def run_reference(args):
         "config": {"workload": f"{WORKLOAD}: growth-map x (d1=2), linear-Gaussian z (d2=8), dy=2, "
                                f"N={sz['N']}, M={M}, L={L}",
                    "reference": f"FP64 C oracle on a {n_sample}-outer-particle sample per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cpu": cpu_model(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -305,10 +340,13 @@ def run(args):
             traffic = tj.get("dram_bytes_per_launch")
     cpu = None
     if ws == 1 and not args.no_cpu:
-        r, threads, sample = cpu_oracle_rate(spec, N, M, L)
-        r1, _, sample1 = cpu_oracle_rate(spec, N, M, L, budget_s=3.0, n_sample=1024, max_steps=4, threads=1)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
-               "single_thread": {"value": r1, "unit": UNIT, "sample": sample1}}
+        r, threads, sample, rs = cpu_oracle_median(spec, N, M, L, budget_s=10.0, max_steps=12)
+        r1, _, sample1, rs1 = cpu_oracle_median(spec, N, M, L, budget_s=3.0, n_sample=1024, max_steps=4,
+                                                threads=1)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle",
+               "sample": sample + "; median of 3 runs", "runs": rs,
+               "single_thread": {"value": r1, "unit": UNIT, "sample": sample1 + "; median of 3 runs",
+                                 "runs": rs1}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
@@ -328,12 +366,35 @@ def run(args):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line))
     f.close()
+    if ws == 1 and not args.no_legs:
+        line.update(secondary_legs())
+    print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def secondary_legs():
+    """Short runs of the other configurations, reported beside the headline (one GPU):
+    the 512-filter batched workload (10 graph-captured steps), the learned proposals at
+    N = 262144, M = 64 (10 steps each form, with RMSE and inner ESS), and one filter of
+    the high-dimensional workload (10 steps). Each carries its own roofline and clocks."""
+    import torch
+    out = {}
+    legs = [("batched", run_batched, dict(filters=512, steps=10, warmup=3)),
+            ("learned", run_learned, dict(steps=10, warmup=3)),
+            ("highdim", run_highdim, dict(filters=1, steps=10, warmup=3))]
+    for name, fn, kw in legs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(argparse.Namespace(**kw))
+        except Exception as e:  # a leg that fails is reported, the headline stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["leg_wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args):
@@ -376,10 +437,16 @@ def run_batched(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    w0 = time.monotonic()
     e0.record(stream)
     b.run_device(yd[args.warmup:].data_ptr(), T, graph=True)
     e1.record(stream)
     torch.cuda.synchronize()
+    w1 = time.monotonic()
+    clk = clocks.stop(window=(w0, w1))
     ms = e0.elapsed_time(e1)
     value = upd * T / (ms / 1e3)
     b.close()
@@ -452,9 +519,9 @@ def run_batched(args):
         "vs_one_by_one": {"filters": S, "steps": steps_sub, "batched_updates_per_s": upd_sub / (ms_b / 1e3),
                           "one_by_one_updates_per_s": upd_sub / (ms_s / 1e3), "speedup": ms_s / ms_b,
                           "one_system_batched_updates_per_s": upd_sub / (ms_o / 1e3)},
+        "clocks": clk,
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_highdim(args):
@@ -557,8 +624,7 @@ def run_highdim(args):
         "gpu_launches": 3 * K * F,
         "clocks": clk,
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_compare(args):
@@ -983,9 +1049,15 @@ def run_learned(args):
         "gpu_launches": 4 * K,
         "clocks": clk,
     }
-    print(json.dumps(line))
+    tf_peak, tf_kind = measured_tflops()
+    line["roofline"] = {"bound": "tensor", "achieved": line["tensor"]["mlp_tflops"], "peak": tf_peak,
+                        "unit": "TFLOP/s", "frac": line["tensor"]["mlp_tflops"] / tf_peak, "traffic": None,
+                        "kernel": "whole step with the mixture proposal (learned_kernel dominates)",
+                        "flop_per_update": mlp_flop,
+                        "peak_source": f"{tf_kind} (MEASURED_PEAKS.json bf16_tflops)"}
     prop.close()
     aprop.close()
+    return line
     return 0
 
 
@@ -1003,6 +1075,8 @@ def main(argv=None):
     ap.add_argument("--alpha", type=float, default=0.001, help="the bandit reward's alpha (the paper's 0.001)")
     ap.add_argument("--filters", type=int, default=None,
                     help="filters of the batched (default 512) or high-dimensional (default 64) workload")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the short batched, learned and high-dimensional legs of the default run")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -1011,11 +1085,14 @@ def main(argv=None):
     if args.workload == "batched":
         if args.filters is None:
             args.filters = 512
-        return run_batched(args)
+        print(json.dumps(run_batched(args)))
+        return 0
     if args.workload == "highdim":
-        return run_highdim(args)
+        print(json.dumps(run_highdim(args)))
+        return 0
     if args.workload == "learned":
-        return run_learned(args)
+        print(json.dumps(run_learned(args)))
+        return 0
     if args.workload == "compare":
         return run_compare(args)
     if args.workload == "table2":

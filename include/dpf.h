@@ -491,6 +491,17 @@ dpf_status dpf_record_tuples_amortised(dpf_ctx* ctx, int64_t i0, int64_t n_outer
 dpf_status dpf_check_bounded_wait(void* stream);
 
 /*
+ * A check of the allocation-failure path; the paper has no counterpart. Arms a
+ * host-side countdown: of the device allocations that contexts, batches and
+ * proposals make from now on (dpf_create, dpf_create_pf, dpf_create_std,
+ * dpf_set_debug, dpf_batch_create, dpf_proposal_create ...), the n-th fails as
+ * if the device had no memory left, and the countdown is then spent. The call
+ * that owns it returns DPF_E_NOMEM and releases whatever it had allocated.
+ * n = 0 disarms; n < 0: DPF_E_INVALID. Process-wide; not for concurrent use.
+ */
+dpf_status dpf_fail_allocation_after(int64_t n);
+
+/*
  * ---- Automatic state decomposition (Section "Automatic State Decomposition",
  * Fig. hedge) ----
  * Online bandits over K candidate decompositions (arms). Host code; no device.

@@ -2,6 +2,7 @@
 // context, step sequencing and the small utility entry points.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -212,10 +213,25 @@ static dpf_status prepare_model(const dpf_model_desc* m, int d1, int d2, std::ve
   return DPF_OK;
 }
 
+// Armed by dpf_fail_allocation_after: the count of device allocations still to
+// succeed before one fails (0: nothing armed).
+static std::atomic<long long> g_alloc_countdown{0};
+
+cudaError_t device_malloc(void** p, size_t bytes) {
+  long long c = g_alloc_countdown.load();
+  while (c > 0 && !g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 1) {  // this call is the armed one
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 template <class P>
 static dpf_status dalloc(Ctx& x, P*& p, size_t bytes) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  cudaError_t e = device_malloc(&q, bytes < 16 ? 16 : bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(DPF_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
@@ -814,3 +830,10 @@ void dpf_destroy(dpf_ctx* x) {
 }
 
 }  // extern "C"
+
+extern "C" dpf_status dpf_fail_allocation_after(int64_t n) {
+  dpf::clear_error();
+  if (n < 0) return dpf::set_error(DPF_E_INVALID, "dpf_fail_allocation_after: n must be >= 0");
+  dpf::g_alloc_countdown.store(n);
+  return DPF_OK;
+}

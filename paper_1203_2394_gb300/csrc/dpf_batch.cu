@@ -75,7 +75,7 @@ struct dpf_batch {
 namespace dpf {
 
 static dpf_status balloc(dpf_batch& b, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  cudaError_t e = device_malloc(p, bytes < 16 ? 16 : bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(DPF_E_NOMEM, "batch: device allocation failed");

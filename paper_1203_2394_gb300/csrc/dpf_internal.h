@@ -16,6 +16,10 @@ dpf_status set_error(dpf_status st, const std::string& msg);
 void clear_error();
 dpf_status cuda_error(cudaError_t e, const char* what);
 
+// cudaMalloc for the allocations a context, batch or proposal owns; fails with
+// cudaErrorMemoryAllocation when dpf_fail_allocation_after has armed it for this call.
+cudaError_t device_malloc(void** p, size_t bytes);
+
 // Look-back state of one scan: per-tile flag words and values, and the
 // monotone ticket counter that hands out tile indices in launch order.
 struct ScanState {

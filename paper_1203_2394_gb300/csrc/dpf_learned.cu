@@ -294,7 +294,7 @@ __global__ void quantize_params_kernel(const float* W, float* Wq, long long n, A
 
 // ---- host side ----
 static dpf_status palloc(dpf_proposal& p, void** ptr, size_t bytes) {
-  cudaError_t e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
+  cudaError_t e = device_malloc(ptr, bytes < 16 ? 16 : bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *ptr = nullptr;

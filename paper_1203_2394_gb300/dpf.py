@@ -57,6 +57,7 @@ SIGNATURES = [
     ("dpf_box_muller", ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     ("dpf_tc_matmul", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _P]),
     ("dpf_check_bounded_wait", ctypes.c_int, [_P]),
+    ("dpf_fail_allocation_after", ctypes.c_int, [ctypes.c_int64]),
     ("dpf_diag", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_diag_inner", ctypes.c_int, [_P, _P, _P]),
     ("dpf_create_pf", ctypes.c_int, [_P, _I32, _I32, _I64, _U64, _P, _P]),
@@ -596,6 +597,12 @@ def check_bounded_wait(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     check(lib().dpf_check_bounded_wait(s))
+
+
+def fail_allocation_after(n: int):
+    """Arm the library's allocation-failure countdown (``dpf_fail_allocation_after``): the
+    n-th device allocation of a context, batch or proposal from now fails; 0 disarms."""
+    check(lib().dpf_fail_allocation_after(int(n)))
 
 
 DPF_HEDGE, DPF_EXP3 = 0, 1

@@ -23,3 +23,44 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert idx.shape[0] == 10000
     assert int(idx.min()) >= 0 and int(idx.max()) < 10000
     assert np.all(np.diff(idx.cpu().numpy()) >= 0)
+
+
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_allocation_failure_returns_nomem_and_frees_everything():
+    """A device allocation that fails part-way through dpf_create (or dpf_batch_create)
+    makes the call return DPF_E_NOMEM and release everything it had allocated: the
+    device's free memory afterwards equals the free memory before. The failure is made
+    on the host (dpf_fail_allocation_after), not by exhausting the GPU."""
+    from paper_1203_2394_gb300 import dpf, workloads
+    spec = workloads.make_model("growth_clg10", 0)
+    m = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    N, M, L = 4096, 128, 16
+    dpf.Filter(m, 2, 8, N, M, L, 1).close()  # warm-up: the library's modules load once
+    b = dpf.Batch([m, m], [2, 2], [512, 300], [64, 128], 8, [1, 2])
+    b.close()
+    before = _free_bytes()
+    # dpf_create makes 28 device allocations: the first, some in between, the last
+    for k in (1, 2, 7, 15, 28):
+        dpf.fail_allocation_after(k)
+        with pytest.raises(dpf.DpfError) as e:
+            dpf.Filter(m, 2, 8, N, M, L, 1)
+        assert e.value.status == dpf.DPF_E_NOMEM, (k, e.value)
+        assert _free_bytes() == before, k
+    # a batch: inside its first member's context, and in the batch's own allocations
+    for k in (5, 60):
+        dpf.fail_allocation_after(k)
+        with pytest.raises(dpf.DpfError) as e:
+            dpf.Batch([m, m], [2, 2], [512, 300], [64, 128], 8, [1, 2])
+        assert e.value.status == dpf.DPF_E_NOMEM, (k, e.value)
+        assert _free_bytes() == before, k
+    dpf.fail_allocation_after(0)
+    f = dpf.Filter(m, 2, 8, N, M, L, 1)  # and the library works normally afterwards
+    _, ys = workloads.simulate(spec, 2, 0)
+    mean, _ = f.step(ys[0].astype(np.float32))
+    assert np.all(np.isfinite(mean))
+    f.close()
+    assert _free_bytes() == before

@@ -1,4 +1,5 @@
-"""The allocation-free resampler (dpf_resample_noalloc) against dpf_resample.
+"""The allocation-free resampler (dpf_resample_noalloc) against dpf_resample and,
+bit for bit, against the oracle's global systematic rule (oracle.sys_global).
 
 It exists for callers that cannot allocate device memory while they resample
 (a loop that must not allocate after start-up, or a process whose framework
@@ -32,6 +33,20 @@ def test_noalloc_matches_resample_twice_in_a_row():
             ref = dpf.resample(w, u, dpf.DPF_SYS_GLOBAL, 1)
             got = dpf.resample_noalloc(w, u)
             assert torch.equal(got, ref), (w.numel(), w.dtype)
+
+
+def test_noalloc_matches_the_oracle_bit_for_bit():
+    """Independent of the library's other resampling path: the oracle's exact integer
+    rule on the same weights (widened exactly to FP64) and the same uniform, at the
+    largest accepted size and at a size that is not a multiple of the 2048-weight tile."""
+    from oracle import oracle
+    from paper_1203_2394_gb300 import dpf
+    rng = np.random.default_rng(1)
+    for n, dt in [(1 << 22, np.float32), (1_000_003, np.float64)]:
+        w, u = _case(rng, n, dt)
+        got = dpf.resample_noalloc(w, u).cpu().numpy()
+        ref = oracle.sys_global(w.cpu().numpy().astype(np.float64), int(u.cpu().numpy().view(np.uint32)[0]))
+        np.testing.assert_array_equal(got, ref, err_msg=f"n={n}")
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
