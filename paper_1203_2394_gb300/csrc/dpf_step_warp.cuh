@@ -21,6 +21,9 @@
 namespace dpf {
 
 constexpr int WARPS_PER_CTA = 4;
+// Row stride (elements) of the lane-partials table part[row][PART_STRIDE]: rows start on
+// 16 bytes (vector loads of a row) and a row's 32 lane entries fall on distinct banks.
+constexpr int PART_STRIDE = 36;
 
 // CTAs per SM the register allocation aims for: 4 (128 registers a thread)
 // unless a lane holds many coordinates of many particles, where 2 (255) avoids
@@ -48,7 +51,7 @@ inline size_t warp_geometry(int M, int L, StepArgs<T>* a, bool first = false) {
   const uint32_t cum = take(sizeof(uint32_t) * M), fs = take(XZ ? sizeof(T) * D1 * M : 0),
                  xw = take(sizeof(T) * L * D1), cw = take(sizeof(T) * L * DY),
                  xbs = take(sizeof(T) * L * D1), row = take(sizeof(T) * L * 5),
-                 part = take(sizeof(T) * 2 * 33 * L),
+                 part = take(sizeof(T) * 2 * PART_STRIDE * L),
                  zrow = take(sizeof(T) * D2 * (D1 + D2 + DY));
   const size_t warp_bytes = r16(o);
   if (a) {
@@ -237,6 +240,39 @@ __device__ __forceinline__ void sub_sq(T c, const T (&g)[P], T (&acc)[P]) {
   }
 }
 
+// acc[p] += x[p] (packed FP32x2 adds on float pairs)
+template <typename T, int P>
+__device__ __forceinline__ void add_to(const T (&x)[P], T (&acc)[P]) {
+  if constexpr (sizeof(T) == 4 && P % 2 == 0) {
+#pragma unroll
+    for (int p = 0; p < P; p += 2) {
+      const float2 r = __fadd2_rn(make_float2(acc[p], acc[p + 1]), make_float2(x[p], x[p + 1]));
+      acc[p] = r.x;
+      acc[p + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) acc[p] += x[p];
+  }
+}
+// Sum of P values as a pairwise tree (halves added element by element, packed on float
+// pairs), P a power of two.
+template <typename T, int P>
+__device__ __forceinline__ T tree_sum(const T (&x)[P]) {
+  if constexpr (P == 1) {
+    return x[0];
+  } else {
+    T h[P / 2];
+#pragma unroll
+    for (int p = 0; p < P / 2; ++p) h[p] = x[p];
+    T u[P / 2];
+#pragma unroll
+    for (int p = 0; p < P / 2; ++p) u[p] = x[P / 2 + p];
+    add_to<T, P / 2>(u, h);
+    return tree_sum<T, P / 2>(h);
+  }
+}
+
 // Issue the bulk copies of one group's source rows into a warp's stage (lane 0).
 template <typename T, int D1, int D2>
 __device__ __forceinline__ void warp_stage(const StepArgs<T>& a, unsigned char* st, uint64_t* bar,
@@ -291,7 +327,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
   T* shS = rowA + L;
   T* shA = shS + L;
   T* coef = shA + L;
-  T* part = (T*)(ws + a.off_part);  // [2L][33] lane partials (row stride 33: no bank conflicts)
+  T* part = (T*)(ws + a.off_part);  // [2L][PART_STRIDE] lane partials
   // the rows [A_zx A_zz K] of the model, for the z-mean (lane r reads row r: shared memory
   // serves the lanes' different rows at once, where the constant bank would serialise them)
   constexpr int ZW = D1 + D2 + DY;
@@ -753,25 +789,41 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int p = 0; p < PPL; ++p) v[p] = ak[p];
 #pragma unroll
         for (int q = 0; q < DY; ++q) sub_sq<T, PPL>(cw[m * DY + q], ngk[q], v);
-        T sp = T(0);
+        T e[PPL];
 #pragma unroll
-        for (int p = 0; p < PPL; ++p) {
-          const T e = exp2_t(v[p]);
-          B[p] += e;
-          sp += e;
-        }
-        part[m * 33 + lane] = sp;
+        for (int p = 0; p < PPL; ++p) e[p] = exp2_t(v[p]);
+        add_to<T, PPL>(e, B);
+        part[m * PART_STRIDE + lane] = tree_sum<T, PPL>(e);
       }
       __syncwarp();
-      // row sums (lane m adds the 32 lane partials of row m)
-      for (int m = lane; m < L; m += 32) {
-        T s = T(0);
-#pragma unroll 8
-        for (int l = 0; l < 32; ++l) s += part[m * 33 + l];
-        rowS[m] = s;
-        rowA[m] = SA0;
-        shS[m] = T(0);
-        shA[m] = T(0);
+      // row sums of the 32 lane partials: for L <= 16 lanes m and m + 16 each add half of
+      // row m (vector loads) and combine by one shuffle; else lane m adds all of row m
+      if (L <= 16) {
+        const int m = lane & 15, h = lane >> 4;
+        T sum = T(0);
+        if (m < L) {
+          T r[16];
+          vld<T, 16>(part + m * PART_STRIDE + 16 * h, r);
+          sum = tree_sum<T, 16>(r);
+        }
+        sum += __shfl_xor_sync(FULL, sum, 16);
+        if (h == 0 && m < L) {
+          rowS[m] = sum;
+          rowA[m] = SA0;
+          shS[m] = T(0);
+          shA[m] = T(0);
+        }
+      } else {
+        for (int m = lane; m < L; m += 32) {
+          T r[16];
+          vld<T, 16>(part + m * PART_STRIDE, r);
+          const T lo = tree_sum<T, 16>(r);
+          vld<T, 16>(part + m * PART_STRIDE + 16, r);
+          rowS[m] = lo + tree_sum<T, 16>(r);
+          rowA[m] = SA0;
+          shS[m] = T(0);
+          shA[m] = T(0);
+        }
       }
       __syncwarp();
       const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-290);
@@ -810,19 +862,19 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
               }
             }
           }
-          part[m * 33 + lane] = pa;
-          part[(L + m) * 33 + lane] = ps;
+          part[m * PART_STRIDE + lane] = pa;
+          part[(L + m) * PART_STRIDE + lane] = ps;
         }
         __syncwarp();
         for (int m = lane; m < L; m += 32) {
           T ra = pass ? T(0) : NEG, rs = pass ? T(0) : NEG;
           for (int l = 0; l < 32; ++l) {
             if (pass == 0) {
-              ra = fmax(ra, part[m * 33 + l]);
-              rs = fmax(rs, part[(L + m) * 33 + l]);
+              ra = fmax(ra, part[m * PART_STRIDE + l]);
+              rs = fmax(rs, part[(L + m) * PART_STRIDE + l]);
             } else {
-              ra += part[m * 33 + l];
-              rs += part[(L + m) * 33 + l];
+              ra += part[m * PART_STRIDE + l];
+              rs += part[(L + m) * PART_STRIDE + l];
             }
           }
           if (pass == 0) {
