@@ -159,8 +159,9 @@ def init(model, N, M, seed, lib):
     return x, z, np.full((N, M), -np.log(M))
 
 
-def lookahead(model, seed, t, y, x, z, lq, L, idx, lib):
+def lookahead(model, seed, t, y, x, z, lq, L, idx, lib, jla_in=None):
     """Steps 1-2 of Fig. 4 for the outer particles idx from the state of step t-1.
+    jla_in (optional, (n, L)): replay these mixture components instead of drawing them.
     Returns lw (n,), lwhat (n, L), xbb (n, L, d1), jla (n, L), mu (n, L, d2)."""
     d1, d2, M = model.d1, model.d2, z.shape[1]
     n = len(idx)
@@ -171,7 +172,10 @@ def lookahead(model, seed, t, y, x, z, lq, L, idx, lib):
         fx, fz = model.transition(x[i][None, :], z[i], t - 1)  # (M, d1), (M, d2)
         qbar = np.exp(lq[i] - lq[i].max())
         for m in range(L):
-            jla[q, m] = oracle.sys_local(qbar, 1, _word(seed, t, i, oracle.P_LA_J, m, lib), lib)[0]
+            if jla_in is not None:
+                jla[q, m] = int(jla_in[q][m])
+            else:
+                jla[q, m] = oracle.sys_local(qbar, 1, _word(seed, t, i, oracle.P_LA_J, m, lib), lib)[0]
         e = oracle.normals_many(seed, 0, t, np.full(L, i), oracle.P_LA_X, np.arange(L), d1, lib)
         xb = model.draw_x(fx[jla[q]], e)  # (L, d1)
         ek = oracle.normals_many(seed, 0, t, np.full(M, i), oracle.P_LA_Z, np.arange(M), d2, lib)
@@ -186,21 +190,31 @@ def lookahead(model, seed, t, y, x, z, lq, L, idx, lib):
     return lw, lwhat, xbb, jla, mu
 
 
-def finalize(model, seed, t, y, idx, anc, x_prev, z_prev, lq_prev, x_new, lib):
+def finalize(model, seed, t, y, idx, anc, x_prev, z_prev, lq_prev, x_new, lib, bidx_in=None,
+             return_alpha=False):
     """Step 4's inner update for the destinations idx with ancestors anc and new x_t.
-    Returns z (n, M, d2), lq (n, M), bidx (n, M)."""
+    bidx_in (optional, (n, M)): replay these local resampling indices.
+    Returns z (n, M, d2), lq (n, M), bidx (n, M) and, with return_alpha, the local
+    resampling weights alpha (n, M)."""
     d2, M = model.d2, z_prev.shape[1]
     n = len(idx)
     Z = np.zeros((n, M, d2)); LQ = np.zeros((n, M)); B = np.zeros((n, M), np.int64)
+    AL = np.zeros((n, M))
     for q in range(n):
         i, a = int(idx[q]), int(anc[q])
         fx, fz = model.transition(x_prev[a][None, :], z_prev[a], t - 1)
         alpha = lq_prev[a] + model.log_px(x_new[q][None, :], fx)
-        b = oracle.sys_local(np.exp(alpha - alpha.max()), M, _word(seed, t, i, oracle.P_INNER, 0, lib), lib)
+        AL[q] = alpha
+        if bidx_in is not None:
+            b = np.asarray(bidx_in[q], np.int64)
+        else:
+            b = oracle.sys_local(np.exp(alpha - alpha.max()), M, _word(seed, t, i, oracle.P_INNER, 0, lib), lib)
         e = oracle.normals_many(seed, 0, t, np.full(M, i), oracle.P_PROP, np.arange(M), d2, lib)
         zt = model.draw_z(fz[b], fx[b], x_new[q][None, :], e)
         ell = model.log_py(y, np.broadcast_to(x_new[q], (M, model.d1)), zt)
         Z[q], LQ[q], B[q] = zt, ell - _lse(ell), b
+    if return_alpha:
+        return Z, LQ, B, AL
     return Z, LQ, B
 
 

@@ -749,6 +749,9 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   else if (w == "bidx") {
     if (!x->dbg_b) return set_error(DPF_E_INVALID, "dpf_read: bidx needs dpf_set_debug(ctx, 1)");
     src = x->dbg_b; need = 4 * N * M;
+  } else if (w == "jla") {
+    if (!x->dbg_j) return set_error(DPF_E_INVALID, "dpf_read: jla needs dpf_set_debug(ctx, 1)");
+    src = x->dbg_j; need = 4 * N * L;
   } else if (w == "afeat" || w == "ahead") {
     if (!x->proposal || !x->oa_feat || dpf_proposal_kind(x->proposal) != 1)
       return set_error(DPF_E_INVALID, "dpf_read: afeat/ahead need an outer-amortised proposal");
@@ -783,6 +786,7 @@ dpf_status dpf_set_debug(dpf_ctx* x, int32_t enable) {
   if (enable && !x->dbg_b) {
     dpf_status st = dalloc(*x, x->dbg_b, (size_t)4 * x->N * x->M);
     if (!st) st = dalloc(*x, x->anc_prev, (size_t)4 * x->N);
+    if (!st) st = dalloc(*x, x->dbg_j, (size_t)4 * x->N * x->L);
     if (!st && x->prec == DPF_F32) st = dalloc(*x, x->dbg_head, (size_t)4 * x->N * x->M * 32);
     if (st) return st;
   }

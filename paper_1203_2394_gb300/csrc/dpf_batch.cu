@@ -89,7 +89,10 @@ static dpf_status shape_class(dpf_batch& b, BatchClass& c) {
   size_t region = 0;
   for (int f : c.members) region = std::max(region, c.var->region_bytes(b.ctx[f]->M, b.ctx[f]->L, c.xz));
   c.launch.region = (uint32_t)region;
-  c.launch.smem = region * 4;  // WARPS_PER_CTA warps per CTA
+  // WARPS_PER_CTA warps per CTA, then one filter's launch arguments and, unless the
+  // class shares one set, its model constants
+  c.launch.smem = region * 4 + (c.var->args_size + 15) / 16 * 16 +
+                  (c.shared_mc.empty() ? (c.var->const_size + 15) / 16 * 16 : 0);
   c.launch.ppl = c.ppl;
   bool full = true;  // every lane of every member holds ppl particles: the compile-time-M kernel
   for (int f : c.members) full &= b.ctx[f]->M == 32 * c.ppl;

@@ -147,6 +147,7 @@ struct dpf_ctx {
   int32_t* anc = nullptr;
   int32_t* sel = nullptr;
   int32_t* dbg_b = nullptr;
+  int32_t* dbg_j = nullptr;     // debug: the look-ahead's mixture components (N x L; Table 1 models)
   int32_t* anc_prev = nullptr;  // debug: the ancestors the last inner update used
   void* dbg_head = nullptr;     // debug: the learned proposal's head outputs of the last inner update
   void* oa_bidx = nullptr;      // amortised proposal: local resampling indices, group features, head outputs

@@ -132,6 +132,8 @@ struct NLArgs {
   float tt_cur[2];   // ... into step t
   float scaleM, scaleL, logL;
   int first;
+  int32_t* dbg_b;  // debug (or null): the local resampling indices of the inner update, N x M
+  int32_t* dbg_j;  // debug (or null): the mixture component of each look-ahead draw, N x L
 };
 
 // log N(r; 0, Q_xx) up to the constant: -|L_qx^-1 r|^2 / 2
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
       float ell = NEG;
       if (act) {
         const int b = sys_local_pick(cum, M, C, M, tid, uin);
+        if (a.dbg_b) a.dbg_b[i * M + tid] = b;
         float zb[D2], fxb[D1], fzb[D2], e[D2];
 #pragma unroll
         for (int c = 0; c < D2; ++c) zb[c] = zs[c * M + b];
@@ -364,6 +367,7 @@ __global__ void __launch_bounds__(1024) nl_step_kernel(const __grid_constant__ N
     if (tid < L) {  // draw m from the mixture: a component by qbar, then the Gaussian
       const int m = tid;
       const int jm = sys_local_pick(cum, M, cum[M - 1], 1, 0, rand_word(a.key, a.t, (uint32_t)i, P_LA_J, (uint32_t)m));
+      if (a.dbg_j) a.dbg_j[i * L + m] = jm;
       float e1[D1], xb[D1];
       normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, (uint32_t)m, e1);
 #pragma unroll
@@ -776,6 +780,8 @@ struct PaperVariant {
     a.scaleL = (float)std::ldexp(1.0, 31 - ceil_log2_i(x.L));
     a.logL = (float)std::log((double)x.L);
     a.first = first ? 1 : 0;
+    a.dbg_b = x.debug ? x.dbg_b : nullptr;
+    a.dbg_j = x.debug ? x.dbg_j : nullptr;
     const int big = x.M > x.L ? x.M : x.L;
     const int nt = (big < 32 ? 32 : (big + 31) / 32 * 32);
     const size_t sm = nl_smem_bytes(D1, D2, x.M, x.L);

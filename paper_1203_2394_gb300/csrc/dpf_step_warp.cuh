@@ -622,7 +622,14 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int c = 0; c < D2; ++c) vst<T, PPL>(a.z_new + c * NM + i * M + k0, zr[c]);
         vst<T, PPL>(a.lq_new + i * M + k0, lqr);
       }
-      if (lane < D1) a.x_new[i * a.xp + lane] = x[lane < D1 ? lane : 0];
+      {  // lane c < D1 stores x[c] (a select chain: a register array indexed by the lane
+         // would be placed in local memory)
+        T xo = x[0];
+#pragma unroll
+        for (int c = 1; c < D1; ++c)
+          if (lane == c) xo = x[c];
+        if (lane < D1) a.x_new[i * a.xp + lane] = xo;
+      }
       sigma = -llsum;
       SA0 = lsum;
     }
@@ -1022,21 +1029,43 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, warp_min_blocks<PPL, D2>()
   }
   __syncwarp();
   const long long total = fstart[F];
-  long long item = ((long long)blockIdx.x * WARPS_PER_CTA + wib) * chunk;
-  const long long iend = item + chunk < total ? item + chunk : total;
+  uint32_t phase = 0;
+  unsigned char* ws = smem_raw + (size_t)wib * region;
+  // The CTA takes WARPS_PER_CTA chunks in a row and walks them filter by filter. Each
+  // filter's launch arguments (and its model constants, unless the launch shares one
+  // set as a parameter) are staged once in shared memory after the warps' regions, so
+  // the step reads them from there instead of holding global-memory copies in
+  // registers; the filter's groups are dealt to the four warps in turn.
+  using Const = MC<T, D1, D2, DY>;
+  constexpr size_t kArgs = (sizeof(StepArgs<T>) + 15) / 16 * 16;
+  StepArgs<T>* sa = reinterpret_cast<StepArgs<T>*>(smem_raw + (size_t)WARPS_PER_CTA * region);
+  Const* smc = reinterpret_cast<Const*>(smem_raw + (size_t)WARPS_PER_CTA * region + kArgs);
+  long long item = (long long)blockIdx.x * WARPS_PER_CTA * chunk;
+  const long long cend = item + WARPS_PER_CTA * chunk;
+  const long long iend = cend < total ? cend : total;
   int lo = 0, hi = F;  // the filter holding `item`: last f with fstart[f] <= item
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (fstart[mid] <= item) lo = mid; else hi = mid;
   }
   int f = lo;
-  uint32_t phase = 0;
-  unsigned char* ws = smem_raw + (size_t)wib * region;
   while (item < iend) {
     while (fstart[f + 1] <= item) ++f;
     const long long seg_end = iend < fstart[f + 1] ? iend : fstart[f + 1];
-    warp_run<T, D1, D2, DY, XZ, PPL, MF>(SHARED ? mc1 : mcs[f], descs[f], item - fstart[f],
-                                     seg_end - fstart[f], 1, ws, &bars[wib], phase);
+    __syncthreads();  // the previous filter's arguments and constants are no longer read
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(descs + f);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(sa);
+      for (int e = threadIdx.x; e < (int)(sizeof(StepArgs<T>) / 4); e += WARPS_PER_CTA * 32) dst[e] = src[e];
+    }
+    if (!SHARED) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(mcs + f);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(smc);
+      for (int e = threadIdx.x; e < (int)(sizeof(Const) / 4); e += WARPS_PER_CTA * 32) dst[e] = src[e];
+    }
+    __syncthreads();
+    warp_run<T, D1, D2, DY, XZ, PPL, MF>(SHARED ? mc1 : *smc, *sa, item - fstart[f] + wib,
+                                         seg_end - fstart[f], WARPS_PER_CTA, ws, &bars[wib], phase);
     item = seg_end;
   }
 }

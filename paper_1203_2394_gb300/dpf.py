@@ -228,7 +228,7 @@ class Filter:
         "lw": lambda s: (s.N,), "lwhat": lambda s: (s.N, s.L), "xbb": lambda s: (s.N, s.L, s.d1),
         "anc": lambda s: (s.N,), "sel": lambda s: (s.N,), "wout": lambda s: (s.N,),
         "x": lambda s: (s.N, s.d1), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
-        "bidx": lambda s: (s.N, s.M), "fallback": lambda s: (s.N,),
+        "bidx": lambda s: (s.N, s.M), "fallback": lambda s: (s.N,), "jla": lambda s: (s.N, s.L),
         "head": lambda s: (s.N, s.M, s.proposal.dout),
         "afeat": lambda s: (s.N, 2 * s.d1 + s.dy + 2 * s.d2),
         "ahead": lambda s: (s.N, 2 * s.d2),
@@ -242,7 +242,7 @@ class Filter:
 
     def read(self, which: str) -> np.ndarray:
         shape = self._SHAPES[which](self)
-        dt = np.int32 if which in ("anc", "sel", "bidx", "fallback") else self.dtype
+        dt = np.int32 if which in ("anc", "sel", "bidx", "fallback", "jla") else self.dtype
         out = np.zeros(shape, dtype=dt)
         check(self._lib.dpf_read(self.h, which.encode(), out.ctypes.data, out.nbytes))
         return out
