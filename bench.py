@@ -269,6 +269,8 @@ def run(args):
     spec = workloads.make_model(WORKLOAD, 0)
     sz = spec.sizes
     N, M, L, T = sz["N"], sz["M"], sz["L"], sz["T"]
+    if args.outer:  # a smaller case of the same kernel (profiling); stated in the config
+        N = int(args.outer)
     K, W = args.steps, args.warmup
     _, ys = workloads.simulate(spec, max(T, K + W + 1), 0)
     stream = torch.cuda.Stream(device=dev)
@@ -356,7 +358,7 @@ def run(args):
         "config": {"workload": f"{WORKLOAD}: growth-map x (d1=2), linear-Gaussian z (d2=8), dy=2, "
                                f"N={N}, M={M}, L={L}, FP32",
                    "N": N, "M": M, "L": L, "d1": spec.d1, "d2": spec.d2, "dy": spec.dy,
-                   "l2": "state (2 x 302 MB) larger than L2; no flush"},
+                   "l2": f"state (2 x {N * M * (spec.d2 + 1) * 4 / 1e6:.0f} MB) larger than L2; no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "step_warp_kernel", "kernel_ms": kern_avg_s * 1e3,
@@ -1077,6 +1079,9 @@ def main(argv=None):
     ap.add_argument("--alpha", type=float, default=0.001, help="the bandit reward's alpha (the paper's 0.001)")
     ap.add_argument("--filters", type=int, default=None,
                     help="filters of the batched (default 512) or high-dimensional (default 64) workload")
+    ap.add_argument("--outer", type=int, default=None,
+                    help="outer particles of the headline workload (default its 65536; for profiling a "
+                         "smaller case of the same kernel)")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the short batched, learned and high-dimensional legs of the default run")
     args = ap.parse_args(argv)

@@ -249,7 +249,8 @@ def run_la_dpf(model, seed, ys, N, M, L, lib):
     return np.array(means), np.array(lz)
 
 
-def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, gauss=False):
+def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, gauss=False, comp_in=None,
+             bidx_in=None, return_picks=False, x_in=None):
     """The DPF without look-ahead (the paper's Fig. dpf with the prior as both proposals),
     call t for the destinations dest (default 0..n-1) with ancestors anc (None at t = 1):
       x_t ~ sum_j qbar_j N(f_x(x_a, z_aj), Q_xx): a component by the one-draw local rule
@@ -259,11 +260,16 @@ def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, ga
       b = local systematic resampling by lq_aj + log N(x_t; f_x,j, Q_xx) (word (t, i, INNER, 0));
       z_t^j from the transition's conditional given x_t out of z_ab_j (normals (t, i, PROP, j));
       lq = ell - LSE ell with ell = log p(y_t | x_t, z_t^j); log w = LSE ell - log M.
-    Returns x (n, d1), z (n, M, d2), lq (n, M), lw (n,)."""
+    comp_in (n,) and bidx_in (n, M), optional: replay these components and local indices;
+    x_in (n, d1), optional: take these x_t instead of the draws.
+    Returns x (n, d1), z (n, M, d2), lq (n, M), lw (n,); with return_picks also the
+    components (n,; -1 for the Gaussian form), the local indices (n, M) and the local
+    resampling weights alpha (n, M)."""
     d1, d2, M = model.d1, model.d2, z_prev.shape[1]
     n = x_prev.shape[0] if anc is None else len(anc)
     dest = np.arange(n) if dest is None else np.asarray(dest)
     X = np.zeros((n, d1)); Z = np.zeros((n, M, d2)); LQ = np.zeros((n, M)); LW = np.zeros(n)
+    COMP = np.full(n, -1, np.int64); B = np.zeros((n, M), np.int64); AL = np.zeros((n, M))
     for r in range(n):
         i = int(dest[r])
         a = i if anc is None else int(anc[r])
@@ -276,15 +282,28 @@ def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, ga
             dev = fx - mu
             xt = mu + np.linalg.cholesky(model.Qxx + (dev * qn[:, None]).T @ dev) @ e
         else:
-            c = int(oracle.sys_local(qbar, 1, _word(seed, t, i, oracle.P_LA_J, 0, lib), lib)[0])
+            if comp_in is not None:
+                c = int(comp_in[r])
+            else:
+                c = int(oracle.sys_local(qbar, 1, _word(seed, t, i, oracle.P_LA_J, 0, lib), lib)[0])
+            COMP[r] = c
             xt = model.draw_x(fx[c], e)
+        if x_in is not None:
+            xt = np.asarray(x_in[r], np.float64)
         alpha = lq_prev[a] + model.log_px(xt[None, :], fx)
-        b = oracle.sys_local(np.exp(alpha - alpha.max()), M, _word(seed, t, i, oracle.P_INNER, 0, lib), lib)
+        AL[r] = alpha
+        if bidx_in is not None:
+            b = np.asarray(bidx_in[r], np.int64)
+        else:
+            b = oracle.sys_local(np.exp(alpha - alpha.max()), M, _word(seed, t, i, oracle.P_INNER, 0, lib), lib)
+        B[r] = b
         eps = oracle.normals_many(seed, 0, t, np.full(M, i), oracle.P_PROP, np.arange(M), d2, lib)
         zt = model.draw_z(fz[b], fx[b], xt[None, :], eps)
         ell = model.log_py(y, np.broadcast_to(xt, (M, d1)), zt)
         l = _lse(ell)
         X[r], Z[r], LQ[r], LW[r] = xt, zt, ell - l, l - np.log(M)
+    if return_picks:
+        return X, Z, LQ, LW, COMP, B, AL
     return X, Z, LQ, LW
 
 

@@ -36,11 +36,15 @@ def _lse(v):
     return m + np.log(np.sum(np.exp(v - m)))
 
 
-def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, gauss=False):
+def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, gauss=False, comp_in=None,
+             bidx_in=None, return_q=False, x_in=None):
     """One call from the state of step t-1: x_prev (N, d1), z_prev (N, M, d2), lq_prev
     (N, M) = log qbar. anc: the ancestors of the destinations (None at t = 1); dest: the
-    destinations' indices (their random-number keys; default 0..n-1).
-    Returns x (n, d1), z (n, M, d2), lq (n, M), lw (n,), bidx (n, M), comp (n,)."""
+    destinations' indices (their random-number keys; default 0..n-1). comp_in (n,) and
+    bidx_in (n, M), optional: replay these mixture components and local resampling
+    indices instead of drawing them; x_in (n, d1), optional: take these x_t instead.
+    Returns x (n, d1), z (n, M, d2), lq (n, M), lw (n,), bidx (n, M), comp (n,), and with
+    return_q also the local resampling weights log q (n, M)."""
     d1, d2 = model.d1, model.d2
     M = z_prev.shape[1]
     n = x_prev.shape[0] if anc is None else len(anc)
@@ -50,7 +54,7 @@ def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, ga
     Qx = model.Q[:d1, :d1]
     y = np.asarray(y, np.float64)
     X = np.zeros((n, d1)); Z = np.zeros((n, M, d2)); LQ = np.zeros((n, M)); LW = np.zeros(n)
-    B = np.zeros((n, M), np.int64); COMP = np.zeros(n, np.int64)
+    B = np.zeros((n, M), np.int64); COMP = np.zeros(n, np.int64); QW = np.zeros((n, M))
     for r in range(n):
         g = int(dest[r])
         a = g if anc is None else int(anc[r])
@@ -66,15 +70,26 @@ def std_step(model, seed, t, y, x_prev, z_prev, lq_prev, anc, lib, dest=None, ga
             c = -1
             xt = mu + np.linalg.cholesky(S) @ e
         else:
-            c = int(oracle.sys_local(qbar, 1, _word(seed, t, g, oracle.P_LA_J), lib)[0])
+            if comp_in is not None:
+                c = int(comp_in[r])
+            else:
+                c = int(oracle.sys_local(qbar, 1, _word(seed, t, g, oracle.P_LA_J), lib)[0])
             xt = mean[c, :d1] + Lqx @ e
+        if x_in is not None:
+            xt = np.asarray(x_in[r], np.float64)
         # q_j = qbar_j N(x_t; mean_j, Q_x)
         q = lq_prev[a] + log_gauss(xt[None, :] - mean[:, :d1], Qx)
-        b = oracle.sys_local(np.exp(q - q.max()), M, _word(seed, t, g, oracle.P_INNER), lib)
+        QW[r] = q
+        if bidx_in is not None:
+            b = np.asarray(bidx_in[r], np.int64)
+        else:
+            b = oracle.sys_local(np.exp(q - q.max()), M, _word(seed, t, g, oracle.P_INNER), lib)
         eps = np.stack([oracle.normals(seed, 0, t, g, oracle.P_PROP, j, d2, lib) for j in range(M)])
         zt = mean[b, d1:] + eps @ Lqz.T
         st = np.concatenate([np.repeat(xt[None, :], M, 0), zt], axis=1)
         ell = log_gauss(y[None, :] - obs_mean(model, st), model.R)
         lse = _lse(ell)
         X[r], Z[r], LQ[r], LW[r], B[r], COMP[r] = xt, zt, ell - lse, lse - np.log(M), b, c
+    if return_q:
+        return X, Z, LQ, LW, B, COMP, QW
     return X, Z, LQ, LW, B, COMP

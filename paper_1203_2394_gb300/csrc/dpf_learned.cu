@@ -21,89 +21,173 @@
 #include <vector>
 
 #include "dpf_learned.h"
+#include "dpf_tc.cuh"
 
 namespace dpf {
 
-// ---- tiled FP32 GEMM: C[M x N] = op(A) op(B) with an epilogue ----
+// ---- the training products: C[M x N] = op(A) op(B) with an epilogue ----
 // A(m, k) = TA ? A[k lda + m] : A[m lda + k];  B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].
 // EPI: 0 store; 1 bias, ReLU and optional bfloat16 rounding; 2 bias; 3 multiply by
 // (mask(m, n) > 0), mask with leading dimension ldc.
-constexpr int GT = 64, GK = 16;
-
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(256)
-    sgemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
-                 int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias,
-                 const float* __restrict__ mask, int round) {
-  __shared__ float As[GK][GT + 4];
-  __shared__ float Bs[GK][GT + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    // 64 x 16 of A and 16 x 64 of B, 4 elements a thread each
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + q * 256;
-      const int r = e / GK, c = e % GK;  // A tile: row r (m), column c (k)
-      const int m = m0 + r, k = k0 + c;
-      float v = 0.f;
-      if (m < M && k < K) v = TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k];
-      As[c][r] = v;
-      const int kb = e / GT, nb = e % GT;  // B tile: row kb (k), column nb (n)
-      const int k2 = k0 + kb, n = n0 + nb;
-      float w = 0.f;
-      if (k2 < K && n < N) w = TB ? B[(long long)n * ldb + k2] : B[(long long)k2 * ldb + n];
-      Bs[kb][nb] = w;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty + 16 * i;
-    if (m >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx + 16 * j;
-      if (n >= N) continue;
-      float v = acc[i][j];
-      if (EPI == 1) {
-        v = fmaxf(v + bias[n], 0.f);
-        if (round) v = round_bf16(v);
-      } else if (EPI == 2) {
-        v += bias[n];
-      } else if (EPI == 3) {
-        v = mask[(long long)m * ldc + n] > 0.f ? v : 0.f;
-      }
-      C[(long long)m * ldc + n] = v;
-    }
+// On the tensor cores (tcgen05):
+// One CTA of 128 threads per 128-row tile of C, all N <= 256 columns in one TMEM
+// accumulator (FP32). K is taken in chunks of 128 bytes a row (64 BF16 or 32 TF32
+// values): the threads load op(A) and op(B)^T from global memory, round them to the
+// operand format and write them in the K-major layout without swizzle; one thread
+// issues the MMAs (four 32-byte K steps a chunk) and commits them to an mbarrier that
+// every thread waits on (bounded; the CTA agrees on the outcome before it reuses the
+// tiles); thread r then reads row r of the accumulator for the epilogue.
+// PREC 0: BF16 operands (kind::f16), the forward pass's own rounding; PREC 1: 3xTF32
+// (A_hi B_hi + A_hi B_lo + A_lo B_hi, kind::tf32), about FP32 accuracy.
+constexpr int TG_NT = 128;
+constexpr int TG_ROWB = 128;        // bytes of one K chunk of a row
+constexpr int TG_KC16 = TG_ROWB / 16;
+constexpr int TG_SPIN = 1 << 22;
+
+template <int PREC>
+__device__ __forceinline__ void tg_put(unsigned char* hi, unsigned char* lo, int r, int c, float v) {
+  if (PREC == 0) {
+    *(__nv_bfloat16*)(hi + tc::kmajor_offset(r, 2 * c, TG_KC16)) = __float2bfloat16_rn(v);
+  } else {
+    float h, l;
+    tc::split_tf32(v, h, l);
+    *(float*)(hi + tc::kmajor_offset(r, 4 * c, TG_KC16)) = h;
+    *(float*)(lo + tc::kmajor_offset(r, 4 * c, TG_KC16)) = l;
   }
 }
 
+template <bool TA, bool TB, int EPI, int PREC>
+__global__ void __launch_bounds__(TG_NT)
+    tgemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+                 float* __restrict__ C, int ldc, const float* __restrict__ bias, const float* __restrict__ mask,
+                 int round, int npad, uint32_t ncols, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_taddr;
+  constexpr int KC = PREC == 0 ? TG_ROWB / 2 : TG_ROWB / 4;  // K values a chunk
+  const int tid = threadIdx.x, w = tid >> 5;
+  const uint32_t a_bytes = 128u * TG_ROWB, b_bytes = (uint32_t)npad * TG_ROWB;
+  unsigned char* a_hi = sm;
+  unsigned char* b_hi = sm + a_bytes;
+  unsigned char* a_lo = sm + a_bytes + b_bytes;  // 3xTF32 only
+  unsigned char* b_lo = a_lo + a_bytes;
+  const long long m0 = (long long)blockIdx.x * 128;
+  if (w == 0) {
+    tc::tmem_alloc(&s_taddr, ncols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = s_taddr;
+  const uint32_t idesc = tc::instr_desc(PREC == 0 ? tc::FMT_BF16 : tc::FMT_TF32, 128, npad);
+  int ok = 1;
+  uint32_t phase = 0;
+  for (int k0 = 0; k0 < K && ok; k0 += KC) {
+    // op(A) rows m0 .. m0 + 127 and op(B)^T rows 0 .. npad - 1, K columns k0 .. k0 + KC - 1;
+    // the index runs fastest along the operand's contiguous dimension
+    for (int e = tid; e < 128 * KC; e += TG_NT) {
+      const int r = TA ? e % 128 : e / KC, c = TA ? e / 128 : e % KC;
+      const long long m = m0 + r;
+      const int k = k0 + c;
+      float v = 0.f;
+      if (m < M && k < K) v = TA ? A[(long long)k * lda + m] : A[m * lda + k];
+      tg_put<PREC>(a_hi, a_lo, r, c, v);
+    }
+    for (int e = tid; e < npad * KC; e += TG_NT) {
+      const int n = TB ? e / KC : e % npad, c = TB ? e % KC : e / npad;
+      const int k = k0 + c;
+      float v = 0.f;
+      if (n < N && k < K) v = TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n];
+      tg_put<PREC>(b_hi, b_lo, n, c, v);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+      const uint32_t sah = smem_addr(a_hi), sbh = smem_addr(b_hi), sal = smem_addr(a_lo), sbl = smem_addr(b_lo);
+#pragma unroll
+      for (int ks = 0; ks < TG_ROWB / 32; ++ks) {
+        const uint32_t off = (uint32_t)ks * 256;
+        const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+        if (PREC == 0) {
+          tc::mma_f16(taddr, tc::smem_desc(sah + off, TG_KC16), tc::smem_desc(sbh + off, TG_KC16), idesc, acc);
+        } else {  // small terms first, then the leading one
+          tc::mma_tf32(taddr, tc::smem_desc(sal + off, TG_KC16), tc::smem_desc(sbh + off, TG_KC16), idesc, acc);
+          tc::mma_tf32(taddr, tc::smem_desc(sah + off, TG_KC16), tc::smem_desc(sbl + off, TG_KC16), idesc, 1);
+          tc::mma_tf32(taddr, tc::smem_desc(sah + off, TG_KC16), tc::smem_desc(sbh + off, TG_KC16), idesc, 1);
+        }
+      }
+      tc::commit(&bar);
+    }
+    const bool done = tc::bar_wait(&bar, phase, TG_SPIN);
+    phase ^= 1u;
+    tc::fence_after();
+    ok = __syncthreads_and(done ? 1 : 0);  // every thread saw the MMAs finish before the tiles change
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+    tc::bar_wait(&bar, phase ^ 1u, TG_SPIN);  // give MMAs still in flight a second bound
+  } else {
+    const long long m = m0 + tid;
+    for (int c0 = 0; c0 < npad; c0 += 16) {
+      float v[16];
+      tc::ld16(taddr + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          if (n >= N) break;
+          float x = v[j];
+          if (EPI == 1) {
+            x = fmaxf(x + bias[n], 0.f);
+            if (round) x = round_bf16(x);
+          } else if (EPI == 2) {
+            x += bias[n];
+          } else if (EPI == 3) {
+            x = mask[m * ldc + n] > 0.f ? x : 0.f;
+          }
+          C[m * ldc + n] = x;
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(taddr, ncols);
+}
+
+// C = op(A) op(B) with the epilogue EPI on the tensor cores (N <= 256): BF16 operands
+// when the proposal trains in its BF16 form, 3xTF32 otherwise.
 template <bool TA, bool TB, int EPI>
-static void sgemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
-                  float* C, int ldc, const float* bias = nullptr, const float* mask = nullptr, int round = 0) {
-  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-  sgemm_kernel<TA, TB, EPI><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round);
+static void tgemm(cudaStream_t s, int prec_bf16, int* err, int M, int N, int K, const float* A, int lda,
+                  const float* B, int ldb, float* C, int ldc, const float* bias = nullptr,
+                  const float* mask = nullptr, int round = 0) {
+  const int npad = (N + 15) / 16 * 16;
+  uint32_t ncols = 32;
+  while ((int)ncols < npad) ncols <<= 1;
+  const unsigned grid = (unsigned)((M + 127) / 128);
+  // at most 512 / ncols CTAs may hold TMEM on an SM at once: the shared memory a CTA asks
+  // for keeps the rest from becoming resident (they would wait inside the allocation)
+  const size_t floor_smem = ncols >= 256 ? 100 * 1024 : ncols >= 128 ? 57 * 1024 : 0;
+  if (prec_bf16) {
+    const size_t smem = std::max((size_t)(128 + npad) * TG_ROWB, floor_smem);
+    auto k = tgemm_kernel<TA, TB, EPI, 0>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, TG_NT, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round, npad, ncols, err);
+  } else {
+    const size_t smem = std::max((size_t)2 * (128 + npad) * TG_ROWB, floor_smem);
+    auto k = tgemm_kernel<TA, TB, EPI, 1>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, TG_NT, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round, npad, ncols, err);
+  }
 }
 
 // ---- the mixture head: loss and d(loss)/d(out) per row ----
@@ -348,10 +432,10 @@ static dpf_status fwd_bwd(dpf_proposal& p, int nb, double* loss_dev, float* grad
   const float *W1 = Wq + p.offW[0], *W2 = Wq + p.offW[1], *W3 = Wq + p.offW[2], *W4 = Wq + p.offW[3];
   const float *b1 = Wq + p.offB[0], *b2 = Wq + p.offB[1], *b3 = Wq + p.offB[2], *b4 = Wq + p.offB[3];
   // forward: h_l = round(relu(h_{l-1} W_l^T + b_l)), out = h3 W4^T + b4
-  sgemm<false, true, 1>(s, nb, H, din, p.Fb, din, W1, din, p.h1, H, b1, nullptr, rd);
-  sgemm<false, true, 1>(s, nb, H, H, p.h1, H, W2, H, p.h2, H, b2, nullptr, rd);
-  sgemm<false, true, 1>(s, nb, H, H, p.h2, H, W3, H, p.h3, H, b3, nullptr, rd);
-  sgemm<false, true, 2>(s, nb, dO, H, p.h3, H, W4, H, p.ob, dO, b4);
+  tgemm<false, true, 1>(s, p.bf16 ? 1 : 0, p.err_d, nb, H, din, p.Fb, din, W1, din, p.h1, H, b1, nullptr, rd);
+  tgemm<false, true, 1>(s, p.bf16 ? 1 : 0, p.err_d, nb, H, H, p.h1, H, W2, H, p.h2, H, b2, nullptr, rd);
+  tgemm<false, true, 1>(s, p.bf16 ? 1 : 0, p.err_d, nb, H, H, p.h2, H, W3, H, p.h3, H, b3, nullptr, rd);
+  tgemm<false, true, 2>(s, p.bf16 ? 1 : 0, p.err_d, nb, dO, H, p.h3, H, W4, H, p.ob, dO, b4);
   wsum_kernel<<<1, 256, 0, s>>>(p.wb, nb, p.wsum_d);
   if (p.kind == 0) {
     HeadArgs ha{p.ob, p.Zb, p.wb, p.wsum_d, p.dO, loss_dev, nb, p.d2, p.C, dO};
@@ -368,19 +452,19 @@ static dpf_status fwd_bwd(dpf_proposal& p, int nb, double* loss_dev, float* grad
   float *gW1 = grad + p.offW[0], *gW2 = grad + p.offW[1], *gW3 = grad + p.offW[2], *gW4 = grad + p.offW[3];
   float *gb1 = grad + p.offB[0], *gb2 = grad + p.offB[1], *gb3 = grad + p.offB[2], *gb4 = grad + p.offB[3];
   // layer 4: dW4 = dO^T h3, db4 = colsum dO, d3 = (dO W4) * (h3 > 0)
-  sgemm<true, false, 0>(s, dO, H, nb, p.dO, dO, p.h3, H, gW4, H);
+  tgemm<true, false, 0>(s, p.bf16 ? 1 : 0, p.err_d, dO, H, nb, p.dO, dO, p.h3, H, gW4, H);
   colsum_kernel<<<(dO + 127) / 128, 128, 0, s>>>(p.dO, nb, dO, gb4);
-  sgemm<false, false, 3>(s, nb, H, dO, p.dO, dO, W4, H, p.dA, H, nullptr, p.h3);
+  tgemm<false, false, 3>(s, p.bf16 ? 1 : 0, p.err_d, nb, H, dO, p.dO, dO, W4, H, p.dA, H, nullptr, p.h3);
   // layer 3
-  sgemm<true, false, 0>(s, H, H, nb, p.dA, H, p.h2, H, gW3, H);
+  tgemm<true, false, 0>(s, p.bf16 ? 1 : 0, p.err_d, H, H, nb, p.dA, H, p.h2, H, gW3, H);
   colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dA, nb, H, gb3);
-  sgemm<false, false, 3>(s, nb, H, H, p.dA, H, W3, H, p.dB, H, nullptr, p.h2);
+  tgemm<false, false, 3>(s, p.bf16 ? 1 : 0, p.err_d, nb, H, H, p.dA, H, W3, H, p.dB, H, nullptr, p.h2);
   // layer 2
-  sgemm<true, false, 0>(s, H, H, nb, p.dB, H, p.h1, H, gW2, H);
+  tgemm<true, false, 0>(s, p.bf16 ? 1 : 0, p.err_d, H, H, nb, p.dB, H, p.h1, H, gW2, H);
   colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dB, nb, H, gb2);
-  sgemm<false, false, 3>(s, nb, H, H, p.dB, H, W2, H, p.dA, H, nullptr, p.h1);
+  tgemm<false, false, 3>(s, p.bf16 ? 1 : 0, p.err_d, nb, H, H, p.dB, H, W2, H, p.dA, H, nullptr, p.h1);
   // layer 1
-  sgemm<true, false, 0>(s, H, din, nb, p.dA, H, p.Fb, din, gW1, din);
+  tgemm<true, false, 0>(s, p.bf16 ? 1 : 0, p.err_d, H, din, nb, p.dA, H, p.Fb, din, gW1, din);
   colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dA, nb, H, gb1);
   return cuda_error(cudaGetLastError(), "proposal backward");
 }
@@ -447,10 +531,11 @@ static dpf_status proposal_make(int kind, int32_t d1, int32_t d2, int32_t dy, in
   if (palloc(*p, (void**)&p->W, bytes) || palloc(*p, (void**)&p->Wq, bytes) ||
       palloc(*p, (void**)&p->am, bytes) || palloc(*p, (void**)&p->av, bytes) ||
       palloc(*p, (void**)&p->grad, bytes) || palloc(*p, (void**)&p->loss_d, sizeof(double)) ||
-      palloc(*p, (void**)&p->wsum_d, sizeof(double))) {
+      palloc(*p, (void**)&p->wsum_d, sizeof(double)) || palloc(*p, (void**)&p->err_d, sizeof(int))) {
     dpf_proposal_destroy(p);
     return DPF_E_NOMEM;
   }
+  cudaMemsetAsync(p->err_d, 0, sizeof(int), p->stream);
   cudaMemsetAsync(p->W, 0, bytes, p->stream);
   cudaMemsetAsync(p->Wq, 0, bytes, p->stream);
   cudaMemsetAsync(p->am, 0, bytes, p->stream);
@@ -560,6 +645,19 @@ dpf_status dpf_proposal_get_weights(const dpf_proposal* p, float* params, int64_
   return cuda_error(e, "dpf_proposal_get_weights");
 }
 
+// The training products' error word: DPF_E_TIMEOUT (and cleared) if a wait gave up.
+static dpf_status training_err(dpf_proposal& p, const char* what) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, p.err_d, sizeof(int), cudaMemcpyDeviceToHost, p.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  if (h) {
+    cudaMemsetAsync(p.err_d, 0, sizeof(int), p.stream);
+    return set_error(DPF_E_TIMEOUT, std::string(what) + ": a tensor-core product did not complete in time");
+  }
+  return DPF_OK;
+}
+
 dpf_status dpf_proposal_loss_grad(dpf_proposal* p, const float* F, const float* Z, const float* w, int64_t n,
                                   double* loss, float* grad_dev) {
   clear_error();
@@ -579,6 +677,8 @@ dpf_status dpf_proposal_loss_grad(dpf_proposal* p, const float* F, const float* 
   cudaError_t e = cudaMemcpyAsync(&h, p->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_error(e, "dpf_proposal_loss_grad");
+  st = training_err(*p, "dpf_proposal_loss_grad");
+  if (st) return st;
   if (loss) *loss = h;
   return DPF_OK;
 }
@@ -642,6 +742,7 @@ dpf_status dpf_proposal_train(dpf_proposal* p, const float* F, const float* Z, c
   }
   cudaFreeAsync(perm_dev, s);
   cudaFreeAsync(eloss_d, s);
+  if (!st) st = training_err(*p, "dpf_proposal_train");
   if (!st && losses)
     for (int ep = 0; ep < epochs; ++ep) losses[ep] = ep_loss[ep] / (double)nbatches;
   return st;

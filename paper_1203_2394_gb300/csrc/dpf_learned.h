@@ -40,6 +40,7 @@ struct dpf_proposal {
   float* grad = nullptr;
   double* loss_d = nullptr;
   double* wsum_d = nullptr;
+  int* err_d = nullptr;    // device error word of the training products (bounded waits)
   int adam_t = 0;
   // minibatch workspace
   int ws_rows = 0;

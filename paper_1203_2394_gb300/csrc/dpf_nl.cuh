@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(1024) nl_std_kernel(const __grid_constant__ NL
     float e1[D1], xt[D1];
     normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, 0u, e1);
     if (gauss) {
+      if (a.dbg_j && tid == 0) a.dbg_j[i] = -1;
       const float qj = act ? expf(lqj - mx) : 0.f;
       const float qs = bsum(qj, red);
       float mu[D1];
@@ -640,6 +641,7 @@ __global__ void __launch_bounds__(1024) nl_std_kernel(const __grid_constant__ NL
       }
     } else {
       const int jm = sys_local_pick(cum, M, cum[M - 1], 1, 0, rand_word(a.key, a.t, (uint32_t)i, P_LA_J, 0u));
+      if (a.dbg_j && tid == 0) a.dbg_j[i] = jm;
 #pragma unroll
       for (int r = 0; r < D1; ++r) {
         float v = fxs[r * M + jm];
@@ -673,6 +675,7 @@ __global__ void __launch_bounds__(1024) nl_std_kernel(const __grid_constant__ NL
     for (int c = 0; c < D2; ++c) zn[c] = 0.f;
     if (act) {
       const int b = sys_local_pick(cum, M, C, M, tid, uin);
+      if (a.dbg_b) a.dbg_b[i * M + tid] = b;
       float fxb[D1], fzb[D2], e[D2];
 #pragma unroll
       for (int c = 0; c < D1; ++c) fxb[c] = fxs[c * M + b];
@@ -854,6 +857,8 @@ struct PaperVariant {
     a.scaleM = (float)std::ldexp(1.0, 31 - ceil_log2_i(x.M));
     a.logL = (float)std::log((double)x.M);
     a.first = t == 1 ? 1 : 0;
+    a.dbg_b = x.debug ? x.dbg_b : nullptr;
+    a.dbg_j = x.debug ? x.dbg_j : nullptr;
     const int nt = (x.M + 31) / 32 * 32;
     const size_t sm = nl_std_smem_bytes(D1, D2, x.M);
     auto k = nl_std_kernel<Mod>;

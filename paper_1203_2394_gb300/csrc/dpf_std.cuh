@@ -46,6 +46,8 @@ struct StdArgs {
   T logM;
   int first;  // t == 1: no ancestors yet
   int gauss;  // draw x_t from the moment-matched Gaussian of the mixture (Section 4.2)
+  int32_t* dbg_b;  // debug (or null): the local resampling indices, N x M
+  int32_t* dbg_j;  // debug (or null): the mixture component of x_t (-1 for the Gaussian form), N
 };
 
 template <typename T, int D1, int D2, int DY, bool XZ>
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(1024)
     }
     __syncthreads();  // the staged rows and the component weights are complete
     const int jm = sys_local_pick(cum, M, cum[M - 1], 1, 0, rand_word(a.key, a.t, (uint32_t)i, P_LA_J, 0u));
+    if (a.dbg_j && j == 0) a.dbg_j[i] = (XZ && a.gauss) ? -1 : jm;
     T e1[D1];
     normals<D1>(a.key, a.t, (uint32_t)i, P_LA_X, 0u, e1);
     T mux[D1];
@@ -213,6 +216,7 @@ __global__ void __launch_bounds__(1024)
     T ell = NEG;
     if (act) {
       const int b = sys_local_pick(cum, M, C, M, j, uin);
+      if (a.dbg_b) a.dbg_b[i * M + j] = b;
       T eps[D2];
       normals<D2>(a.key, a.t, (uint32_t)i, P_PROP, (uint32_t)j, eps);
 #pragma unroll

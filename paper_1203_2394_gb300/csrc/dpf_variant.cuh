@@ -408,6 +408,8 @@ struct VariantImpl {
     a.logM = (T)std::log((double)x.M);
     a.first = t == 1 ? 1 : 0;
     a.gauss = x.std_gauss ? 1 : 0;
+    a.dbg_b = x.debug ? x.dbg_b : nullptr;
+    a.dbg_j = x.debug ? x.dbg_j : nullptr;
     const int nt = (x.M + 31) / 32 * 32;
     const size_t sm = sizeof(T) * (size_t)D2 * x.M + 4 * (size_t)(x.M + 1) + sizeof(T) * 32 + 4 * 64 + 16;
     const unsigned blocks = (unsigned)std::min<long long>(x.N, 152 * 8);
