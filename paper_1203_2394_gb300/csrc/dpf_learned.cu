@@ -32,13 +32,16 @@ namespace dpf {
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // On the tensor cores (tcgen05):
-// One CTA of 128 threads per 128-row tile of C, all N <= 256 columns in one TMEM
-// accumulator (FP32). K is taken in chunks of 128 bytes a row (64 BF16 or 32 TF32
-// values): the threads load op(A) and op(B)^T from global memory, round them to the
-// operand format and write them in the K-major layout without swizzle; one thread
-// issues the MMAs (four 32-byte K steps a chunk) and commits them to an mbarrier that
-// every thread waits on (bounded; the CTA agrees on the outcome before it reuses the
-// tiles); thread r then reads row r of the accumulator for the epilogue.
+// One CTA of 128 threads per 128-row x npad-column tile of C (npad <= 64 columns of a
+// TMEM accumulator in FP32; blockIdx.y picks the column tile) and one slice of K
+// (blockIdx.z; the slices of a long K add their partial products into C, which the
+// caller has zeroed, with atomic adds: the plain-store epilogue only). K is taken in
+// chunks of 128 bytes a row (64 BF16 or 32 TF32 values): the threads load op(A) and
+// op(B)^T from global memory, round them to the operand format and write them in the
+// K-major layout without swizzle; one thread issues the MMAs (four 32-byte K steps a
+// chunk) and commits them to an mbarrier that every thread waits on (bounded; the CTA
+// agrees on the outcome before it reuses the tiles); thread r then reads row r of the
+// accumulator for the epilogue.
 // PREC 0: BF16 operands (kind::f16), the forward pass's own rounding; PREC 1: 3xTF32
 // (A_hi B_hi + A_hi B_lo + A_lo B_hi, kind::tf32), about FP32 accuracy.
 constexpr int TG_NT = 128;
@@ -62,7 +65,7 @@ template <bool TA, bool TB, int EPI, int PREC>
 __global__ void __launch_bounds__(TG_NT)
     tgemm_kernel(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
                  float* __restrict__ C, int ldc, const float* __restrict__ bias, const float* __restrict__ mask,
-                 int round, int npad, uint32_t ncols, int* err) {
+                 int round, int npad, uint32_t ncols, int kslice, int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_taddr;
@@ -74,6 +77,10 @@ __global__ void __launch_bounds__(TG_NT)
   unsigned char* a_lo = sm + a_bytes + b_bytes;  // 3xTF32 only
   unsigned char* b_lo = a_lo + a_bytes;
   const long long m0 = (long long)blockIdx.x * 128;
+  const int n0 = blockIdx.y * npad;                      // this CTA's first column
+  const int kbeg = blockIdx.z * kslice;                  // and its slice of K
+  const int kend = kbeg + kslice < K ? kbeg + kslice : K;
+  const bool split = gridDim.z > 1;
   if (w == 0) {
     tc::tmem_alloc(&s_taddr, ncols);
     tc::tmem_relinquish();
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(TG_NT)
   const uint32_t idesc = tc::instr_desc(PREC == 0 ? tc::FMT_BF16 : tc::FMT_TF32, 128, npad);
   int ok = 1;
   uint32_t phase = 0;
-  for (int k0 = 0; k0 < K && ok; k0 += KC) {
+  for (int k0 = kbeg; k0 < kend && ok; k0 += KC) {
     // op(A) rows m0 .. m0 + 127 and op(B)^T rows 0 .. npad - 1, K columns k0 .. k0 + KC - 1;
     // the index runs fastest along the operand's contiguous dimension
     for (int e = tid; e < 128 * KC; e += TG_NT) {
@@ -97,15 +104,15 @@ __global__ void __launch_bounds__(TG_NT)
       const long long m = m0 + r;
       const int k = k0 + c;
       float v = 0.f;
-      if (m < M && k < K) v = TA ? A[(long long)k * lda + m] : A[m * lda + k];
+      if (m < M && k < kend) v = TA ? A[(long long)k * lda + m] : A[m * lda + k];
       tg_put<PREC>(a_hi, a_lo, r, c, v);
     }
     for (int e = tid; e < npad * KC; e += TG_NT) {
-      const int n = TB ? e / KC : e % npad, c = TB ? e % KC : e / npad;
-      const int k = k0 + c;
+      const int nl = TB ? e / KC : e % npad, c = TB ? e % KC : e / npad;
+      const int n = n0 + nl, k = k0 + c;
       float v = 0.f;
-      if (n < N && k < K) v = TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n];
-      tg_put<PREC>(b_hi, b_lo, n, c, v);
+      if (n < N && k < kend) v = TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n];
+      tg_put<PREC>(b_hi, b_lo, nl, c, v);
     }
     tc::fence_proxy_async();
     tc::fence_before();
@@ -116,7 +123,7 @@ __global__ void __launch_bounds__(TG_NT)
 #pragma unroll
       for (int ks = 0; ks < TG_ROWB / 32; ++ks) {
         const uint32_t off = (uint32_t)ks * 256;
-        const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+        const uint32_t acc = (k0 > kbeg || ks > 0) ? 1u : 0u;
         if (PREC == 0) {
           tc::mma_f16(taddr, tc::smem_desc(sah + off, TG_KC16), tc::smem_desc(sbh + off, TG_KC16), idesc, acc);
         } else {  // small terms first, then the leading one
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(TG_NT)
       if (m < M) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j;
+          const int n = n0 + c0 + j;
           if (n >= N) break;
           float x = v[j];
           if (EPI == 1) {
@@ -154,7 +161,10 @@ __global__ void __launch_bounds__(TG_NT)
           } else if (EPI == 3) {
             x = mask[m * ldc + n] > 0.f ? x : 0.f;
           }
-          C[m * ldc + n] = x;
+          if (split)
+            atomicAdd(C + m * ldc + n, x);
+          else
+            C[m * ldc + n] = x;
         }
       }
     }
@@ -164,29 +174,38 @@ __global__ void __launch_bounds__(TG_NT)
   if (w == 0) tc::tmem_dealloc(taddr, ncols);
 }
 
-// C = op(A) op(B) with the epilogue EPI on the tensor cores (N <= 256): BF16 operands
-// when the proposal trains in its BF16 form, 3xTF32 otherwise.
+// C = op(A) op(B) with the epilogue EPI on the tensor cores: BF16 operands when the
+// proposal trains in its BF16 form, 3xTF32 otherwise. Column tiles of up to 64; a long
+// K (the batch dimension of a weight gradient) is split over CTAs that accumulate into C.
 template <bool TA, bool TB, int EPI>
 static void tgemm(cudaStream_t s, int prec_bf16, int* err, int M, int N, int K, const float* A, int lda,
                   const float* B, int ldb, float* C, int ldc, const float* bias = nullptr,
                   const float* mask = nullptr, int round = 0) {
-  const int npad = (N + 15) / 16 * 16;
-  uint32_t ncols = 32;
-  while ((int)ncols < npad) ncols <<= 1;
-  const unsigned grid = (unsigned)((M + 127) / 128);
-  // at most 512 / ncols CTAs may hold TMEM on an SM at once: the shared memory a CTA asks
-  // for keeps the rest from becoming resident (they would wait inside the allocation)
-  const size_t floor_smem = ncols >= 256 ? 100 * 1024 : ncols >= 128 ? 57 * 1024 : 0;
+  const int npad = std::min(64, (N + 15) / 16 * 16);
+  const uint32_t ncols = npad <= 32 ? 32u : 64u;
+  const int mt = (M + 127) / 128, nt = (N + npad - 1) / npad;
+  const int kc = prec_bf16 ? TG_ROWB / 2 : TG_ROWB / 4;
+  // slices of at least 4 chunks, enough of them for about 152 CTAs (plain-store products)
+  int ks = 1;
+  if (EPI == 0)
+    while (ks < 16 && (long long)mt * nt * ks * 2 <= 152 && K / (2 * ks) >= 4 * kc) ks *= 2;
+  const int kslice = (K + ks - 1) / ks / kc * kc + ((K + ks - 1) / ks % kc ? kc : 0);
+  ks = (K + kslice - 1) / kslice;  // every slice holds part of K
+  if (ks > 1) cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * ldc, s);
+  const dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)ks);
+  // at most 512 / ncols CTAs can hold TMEM on an SM at once: a CTA asks for enough shared
+  // memory that no more become resident (they would wait inside the allocation)
+  const size_t floor_smem = ncols >= 64 ? 29 * 1024 : 0;
   if (prec_bf16) {
     const size_t smem = std::max((size_t)(128 + npad) * TG_ROWB, floor_smem);
     auto k = tgemm_kernel<TA, TB, EPI, 0>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, TG_NT, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round, npad, ncols, err);
+    k<<<grid, TG_NT, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round, npad, ncols, kslice, err);
   } else {
     const size_t smem = std::max((size_t)2 * (128 + npad) * TG_ROWB, floor_smem);
     auto k = tgemm_kernel<TA, TB, EPI, 1>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, TG_NT, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round, npad, ncols, err);
+    k<<<grid, TG_NT, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, round, npad, ncols, kslice, err);
   }
 }
 
