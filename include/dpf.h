@@ -482,11 +482,13 @@ dpf_status dpf_record_tuples_amortised(dpf_ctx* ctx, int64_t i0, int64_t n_outer
 
 /*
  * A check of the failure path of the bounded waits; the paper has no
- * counterpart. Runs the global resampling's scan on 3 x 2048 unit weights with
- * tile 0 publishing nothing, so that the look-back waits of the other tiles
- * can never be satisfied: they give up after their bound (a few tenths of a
- * second), the call returns DPF_E_TIMEOUT, and the context stays usable.
- * Synchronises the stream.
+ * counterpart. Runs (1) the global resampling's scan on 3 x 2048 unit weights
+ * with tile 0 publishing nothing, so that the look-back waits of the other
+ * tiles can never be satisfied, and (2) a step's outer stage (3 CTAs of one
+ * cooperative launch) with CTA 0 never reaching the grid-wide barrier. In both
+ * the waits give up after their bound (a few tenths of a second) and the device
+ * stays usable; the call returns DPF_E_TIMEOUT when both waits ran out as they
+ * should, and another status otherwise. Synchronises the stream.
  */
 dpf_status dpf_check_bounded_wait(void* stream);
 

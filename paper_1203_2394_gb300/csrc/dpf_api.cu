@@ -29,7 +29,7 @@ dpf_status cuda_error(cudaError_t e, const char* what) {
   return set_error(DPF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-static dpf_status err_word_status(int w, const char* what) {
+dpf_status err_word_status(int w, const char* what) {
   if (w & 2) return set_error(DPF_E_TIMEOUT, std::string(what) + ": a device wait timed out");
   if (w & 1) return set_error(DPF_E_NUMERIC, std::string(what) + ": no positive or a NaN weight");
   if (w) return set_error(DPF_E_CUDA, std::string(what) + ": device bounds check failed");
@@ -353,8 +353,7 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   const size_t s = x->prec == DPF_F64 ? 8 : 4;
   const size_t NM = (size_t)N * M;
   const int d = x->d;
-  x->n_red_blocks = (int)std::min<long long>((N + 255) / 256, 2 * 152);
-  const long long tiles = (N + 2047) / 2048;
+  const long long out_ctas = std::min<long long>((N + OF_CHUNK - 1) / OF_CHUNK, OF_MAX_CTAS);
   const size_t ssz = sizeof(double) * (4 + 2 * d);
   bool ok = true;
   for (int q = 0; q < 2 && ok; ++q) {
@@ -369,9 +368,8 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
        !dalloc(*x, x->yb, s * 2 * x->dy) && !dalloc(*x, x->anc, 4 * N) && !dalloc(*x, x->sel, 4 * N) &&
        !dalloc(*x, x->stats, ssz) && !dalloc(*x, x->lwmax_t, 8) && !dalloc(*x, x->lwmax_key, 8) &&
        !dalloc(*x, x->Csum, 8) && !dalloc(*x, x->done, 8) && !dalloc(*x, x->err, 8) &&
-       !dalloc(*x, x->partials, sizeof(double) * x->n_red_blocks * (4 + d)) &&
-       !dalloc(*x, x->flags, 4 * tiles) && !dalloc(*x, x->agg, 8 * tiles) &&
-       !dalloc(*x, x->incl, 8 * tiles) && !dalloc(*x, x->ticket, 8);
+       !dalloc(*x, x->partials, sizeof(double) * out_ctas * (4 + d)) &&
+       !dalloc(*x, x->ctot, sizeof(unsigned long long) * out_ctas);
   if (!ok) {
     std::string msg = g_err;
     free_all(x);
@@ -385,8 +383,6 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
   cudaMemsetAsync(x->Csum, 0, 8, sr);
   cudaMemsetAsync(x->done, 0, 8, sr);
   cudaMemsetAsync(x->err, 0, 8, sr);
-  cudaMemsetAsync(x->flags, 0, 4 * tiles, sr);
-  cudaMemsetAsync(x->ticket, 0, 8, sr);
   cudaMemsetAsync(x->anc, 0, 4 * N, sr);
   cudaMemsetAsync(x->sel, 0, 4 * N, sr);
   st = x->var->init(*x);

@@ -41,9 +41,9 @@ struct BatchClass {
 struct OuterGroup {
   const Variant* var = nullptr;
   std::vector<int> members;      // filter indices
-  int nblocks = 0;               // blocks of the launch: the members' reduction blocks
-  int* d_bstart = nullptr;       // prefix of the members' block counts
-  void* d_oargs = nullptr;       // a ring of argument sets, one OuterArgs per member
+  int nblocks = 0;               // CTAs of the sums launch: the members' outer-stage CTAs
+  int* d_bstart = nullptr;       // prefix of the members' CTA counts
+  void* d_oargs = nullptr;       // a ring of argument sets, one FusedOuterArgs per member
   size_t set_bytes = 0;
   const void* cur = nullptr;     // the set the next launch reads
 };
@@ -57,9 +57,9 @@ struct dpf_batch {
   std::vector<dpf_ctx*> ctx;
   std::vector<dpf::BatchClass> cls;
   std::vector<dpf::OuterGroup> og;
-  int* d_tstart = nullptr;      // prefix of the filters' resampling tile counts
-  int ntiles = 0;
-  void* d_gargs = nullptr;      // a ring of sets of F resampling arguments
+  int* d_tstart = nullptr;      // prefix of the filters' outer-stage CTA counts
+  int ntiles = 0;               // their sum: CTAs of the resampling launch
+  void* d_gargs = nullptr;      // a ring of sets of F outer-stage arguments, in filter order
   size_t gset_bytes = 0;
   const void* gcur = nullptr;
   int oring = 0;                // sets in the outer-argument rings
@@ -144,10 +144,10 @@ static void fill_outer(dpf_batch& b, double* means_dev, double* logz_dev,
     OuterGroup& g = b.og[gi];
     for (size_t q = 0; q < g.members.size(); ++q) {
       const int f = g.members[q];
+      unsigned char* dst = oh[gi].data() + k * g.set_bytes + q * g.var->oargs_size;
       g.var->outer_args(*b.ctx[f], means_dev ? means_dev + (size_t)f * b.d : nullptr,
-                        logz_dev ? logz_dev + f : nullptr,
-                        oh[gi].data() + k * g.set_bytes + q * g.var->oargs_size,
-                        gh.data() + k * b.gset_bytes + (size_t)f * g.var->gargs_size);
+                        logz_dev ? logz_dev + f : nullptr, dst);
+      memcpy(gh.data() + k * b.gset_bytes + (size_t)f * g.var->oargs_size, dst, g.var->oargs_size);
     }
   }
 }
@@ -306,7 +306,7 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
   b->oring = 2;
   for (OuterGroup& g : b->og) {
     std::vector<int> bs(1, 0);
-    for (int f : g.members) bs.push_back(bs.back() + b->ctx[f]->n_red_blocks);
+    for (int f : g.members) bs.push_back(bs.back() + g.var->outer_ctas(b->ctx[f]->N));
     g.nblocks = bs.back();
     g.set_bytes = g.var->oargs_size * g.members.size();
     if (balloc(*b, (void**)&g.d_bstart, sizeof(int) * bs.size()) ||
@@ -317,13 +317,13 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
   }
   std::vector<int> ts(1, 0);
   for (int f = 0; f < F; ++f) {
-    const long long tiles = (b->ctx[f]->N + SCAN_TILE - 1) / SCAN_TILE;
-    if (ts.back() + tiles > (long long)INT32_MAX)
+    const long long ctas = b->ctx[f]->var->outer_ctas(b->ctx[f]->N);
+    if (ts.back() + ctas > (long long)INT32_MAX)
       return fail(set_error(DPF_E_UNSUPPORTED, "dpf_batch_create: too many outer particles in all"));
-    ts.push_back(ts.back() + (int)tiles);
+    ts.push_back(ts.back() + (int)ctas);
   }
   b->ntiles = ts.back();
-  b->gset_bytes = b->og[0].var->gargs_size * (size_t)F;
+  b->gset_bytes = b->og[0].var->oargs_size * (size_t)F;
   if (balloc(*b, (void**)&b->d_tstart, sizeof(int) * ts.size()) ||
       balloc(*b, &b->d_gargs, b->gset_bytes * b->oring))
     return fail(DPF_E_NOMEM);

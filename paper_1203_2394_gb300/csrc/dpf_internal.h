@@ -42,6 +42,11 @@ dpf_status scratch_alloc(Scratch& sc, long long tiles, cudaStream_t s);
 void scratch_free(Scratch& sc, cudaStream_t s);
 // Synchronise, read the device error word, free, and map it to a status.
 dpf_status scratch_finish(Scratch& sc, cudaStream_t s, const char* what);
+// The status a device error word maps to (0: DPF_OK).
+dpf_status err_word_status(int w, const char* what);
+// The outer stage with one CTA that never reaches the grid barrier: the waits run
+// out and the status is DPF_E_TIMEOUT (dpf_check_bounded_wait).
+dpf_status check_outer_barrier(cudaStream_t s);
 
 // Launch the global systematic-resampling kernels on caller-provided scratch
 // (laid out as by scratch_alloc and zeroed); no allocation, no synchronisation.
@@ -86,6 +91,14 @@ struct BatchLaunch {
 constexpr int SCAN_NT = 256;   // threads per scan tile
 constexpr int SCAN_IPT = 8;    // items per thread
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
+// the outer stage of a step (dpf_outer.cuh): threads a CTA, items a thread in one
+// chunk, items a chunk, the bound on its grid (rows of partial sums, count totals),
+// and the sums a filter: W, W^2 and the d <= 64 weighted means
+constexpr int OF_NT = 256;
+constexpr int OF_IPT = 2;
+constexpr int OF_CHUNK = OF_NT * OF_IPT;
+constexpr int OF_MAX_CTAS = 1024;
+constexpr int OF_MAX_NV = 2 + 64;
 
 struct Variant {
   int prec, d1, d2, dy;
@@ -95,10 +108,13 @@ struct Variant {
   dpf_status (*outer)(Ctx&, double* mean_out, double* logz_out, cudaStream_t s);
   dpf_status (*pf_step)(Ctx&) = nullptr;  // the bootstrap particle filter's step (null: none)
   dpf_status (*std_step)(Ctx&) = nullptr;  // the DPF without look-ahead (null: none)
-  // the outer stage in parts, for many filters at once
-  void (*outer_args)(Ctx&, double* mean_out, double* logz_out, void* oargs, void* gargs);
-  dpf_status (*outer_batch)(const void* oargs, const int* bstart, int nblocks, int F, cudaStream_t s);
-  dpf_status (*scan_batch)(const void* gargs, const int* tstart, int ntiles, int F, cudaStream_t s);
+  // the outer stage in two launches, for many filters at once: the per-filter
+  // arguments, the filter's CTA count, the sums (one variant), then the
+  // resampling and statistics (any variant of the precision)
+  void (*outer_args)(Ctx&, double* mean_out, double* logz_out, void* args);
+  int (*outer_ctas)(long long N) = nullptr;
+  dpf_status (*outer_batch)(const void* args, const int* cstart, int nctas, int F, cudaStream_t s);
+  dpf_status (*scan_batch)(const void* args, const int* cstart, int nctas, int F, cudaStream_t s);
   size_t (*step_smem)(int M, int L, bool xz, int nt);
   int (*xpad)();
   void (*batch_args)(Ctx&, const void* y_prev, const void* y_cur, bool xz, void* out);
@@ -106,7 +122,7 @@ struct Variant {
   dpf_status (*batch_launch)(const BatchLaunch&, cudaStream_t, int* occ);
   bool (*use_xz)(const Ctx&);
   int (*ppl_for)(int M);
-  size_t args_size, const_size, oargs_size, gargs_size;
+  size_t args_size, const_size, oargs_size;
   int max_m = 1024;       // largest M the variant's kernels accept
   bool has_tc = false;    // has a tensor-core propagation (see dpf_set_tensor_cores)
   bool xz_supported = true;  // serves models whose x transition depends on z
@@ -161,16 +177,9 @@ struct dpf_ctx {
   unsigned long long* lwmax_key = nullptr;
   unsigned long long* Csum = nullptr;
   unsigned int* done = nullptr;
-  double* partials = nullptr;       // per reduction block
-  int n_red_blocks = 0;
+  double* partials = nullptr;       // the outer stage's sums, one row a CTA
+  unsigned long long* ctot = nullptr;  // ... and its quantised count totals
   int* err = nullptr;
-  // scan state of the outer resampling
-  uint32_t* flags = nullptr;
-  unsigned long long* agg = nullptr;
-  unsigned long long* incl = nullptr;
-  unsigned long long* ticket = nullptr;
-  unsigned long long ticket_next = 0;
-  uint32_t epoch = 0;
   // step counter (number of completed steps)
   long long t = 0;
   bool debug = false;

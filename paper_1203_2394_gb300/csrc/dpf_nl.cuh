@@ -897,8 +897,7 @@ struct PaperVariant {
     v.ppl_for = nullptr;
     v.args_size = sizeof(NLArgs);
     v.const_size = 0;
-    v.oargs_size = sizeof(OuterArgs<float>);
-    v.gargs_size = sizeof(GlobalArgs<float>);
+    v.oargs_size = sizeof(FusedOuterArgs<float>);
     v.max_m = 1024;
     v.xz_supported = true;
     return v;

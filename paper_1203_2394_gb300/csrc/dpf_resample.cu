@@ -191,6 +191,12 @@ extern "C" dpf_status dpf_check_bounded_wait(void* stream) {
   cudaFreeAsync(w, s);
   cudaFreeAsync(out, s);
   cudaFreeAsync(u, s);
+  if (st != DPF_E_TIMEOUT)
+    return st ? st : set_error(DPF_E_CUDA, "dpf_check_bounded_wait: the scan's wait did not run out");
+  // the same for the grid barrier of a step's outer stage (CTA 0 never arrives)
+  st = check_outer_barrier(s);
+  if (st != DPF_E_TIMEOUT)
+    return st ? st : set_error(DPF_E_CUDA, "dpf_check_bounded_wait: the outer stage's barrier wait did not run out");
   return st;
 }
 

@@ -228,18 +228,4 @@ __global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) 
   global_scan_scatter_body<T, FROM_LOG>(a, gridDim.x);
 }
 
-// The outer resamplings of many filters in one launch: blocks tstart[f] ..
-// tstart[f+1]-1 serve filter f, each taking its tile from that filter's ticket
-// counter (so a tile's predecessor is always held by a block already running).
-template <typename T>
-__global__ void __launch_bounds__(SCAN_NT)
-    global_scan_scatter_batch(const GlobalArgs<T>* __restrict__ args, const int* __restrict__ tstart, int F) {
-  __shared__ int s_f;
-  if (threadIdx.x == 0) s_f = find_segment(tstart, F, (int)blockIdx.x);
-  __syncthreads();
-  const int f = s_f;
-  const GlobalArgs<T> a = args[f];
-  global_scan_scatter_body<T, true>(a, tstart[f + 1] - tstart[f]);
-}
-
 }  // namespace dpf

@@ -1,6 +1,6 @@
 // The LA-DPF step kernels.
 //
-// One call t runs three kernels on the context's stream:
+// One call t runs two kernels on the context's stream:
 //  1. step_kernel (one CTA per outer particle i): the deferred inner step of
 //     step t-1 for destination i (the selection of x_{t-1} among the
 //     ancestor's look-ahead draws, local systematic resampling of the
@@ -8,10 +8,10 @@
 //     weights; Fig. 4 step 4, DPF step 6, eq. qbar), then the look-ahead of step
 //     t on the fresh inner set held in shared memory (Fig. 4 steps 1-2, eqs.
 //     approx1, qnobar, weightsMC). The inner set is read once and written once.
-//  2. outer_reduce_kernel: evidence, ESS, the filtered mean and the quantised
-//     total C of the outer weights (eq. weightsopt).
-//  3. global_scan_scatter: global systematic resampling of the outer set
-//     (Fig. 4 step 3) with a single-pass decoupled look-back scan.
+//  2. fused_outer_kernel (dpf_outer.cuh, one cooperative launch): evidence, ESS,
+//     the filtered mean and the quantised total C of the outer weights (eq.
+//     weightsopt), then the global systematic resampling of the outer set (Fig. 4
+//     step 3) after one grid-wide barrier.
 //
 // Device layout (structure of arrays, element type T):
 //   z[c][n][j] (d2 x N x M), lq[n][j], x[c][n] (d1 x N)   two slots each
@@ -1378,7 +1378,7 @@ __global__ void __launch_bounds__(MAXNT)
 }
 
 
-// ---- outer reduction: evidence, ESS, filtered mean, quantised total ----
+// ---- the outer stage's inputs and outputs: evidence, ESS, filtered mean, quantised total ----
 template <typename T>
 struct OuterArgs {
   const T* lw;
@@ -1390,122 +1390,12 @@ struct OuterArgs {
   T* lwmax_t;
   unsigned long long* Csum;
   unsigned int* done;
-  double* partials;  // one row of 2 + d sums per reducing block
+  double* partials;  // one row of 2 + d sums a CTA
   double* stats;     // [logZ_total, logZ_step, ess, s1, mean[d]]
   const int* perm;   // device, d
   double* mean_out;  // optional device outputs
   double* logz_out;
   int* err;
 };
-
-constexpr int RED_NT = 256;
-
-// Block `bid` of the `nb` blocks that reduce one filter.
-template <typename T, int D1, int D2>
-__device__ __forceinline__ void outer_reduce_body(const OuterArgs<T>& a, int bid, int nb) {
-  constexpr int D = D1 + D2, NV = 2 + D;  // sum W, sum W^2, sum W * mean pieces
-  __shared__ double sh[NV][RED_NT / 32];
-  __shared__ bool last;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  T lwmax;
-  order_decode(*a.lwmax_key, lwmax);
-  const T sS = (T)ldexp(1.0, 62 - ceil_log2_i(a.N));
-  // per-thread and per-warp sums in the working precision (a few hundred terms
-  // of W in [0, 1]), the cross-block combine in double
-  T v[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = T(0);
-  unsigned long long cc = 0;
-  for (long long i = bid * (long long)RED_NT + tid; i < a.N; i += (long long)nb * RED_NT) {
-    const T W = exp_t<T>(a.lw[i] - lwmax);
-    cc += (unsigned long long)floor(W * sS);  // exact: a power-of-two scaling, then a floor
-    v[0] += W;
-    v[1] += W * W;
-#pragma unroll
-    for (int c = 0; c < D1; ++c) v[2 + c] += W * a.xm[(long long)c * a.N + i];
-#pragma unroll
-    for (int c = 0; c < D2; ++c) v[2 + D1 + c] += W * a.zm[(long long)c * a.N + i];
-  }
-#pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(FULL, cc, o);
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q][w] = (double)v[q];
-    if (cc) atomicAdd(a.Csum, cc);
-  }
-  __syncthreads();
-  if (tid < NV) {
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < RED_NT / 32; ++q) s += sh[tid][q];
-    a.partials[(long long)bid * NV + tid] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) last = (atomicAdd(a.done, 1u) == (unsigned)nb - 1u);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // the last block combines the per-block partials in parallel (fixed order)
-  double vd[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) vd[q] = 0.0;
-  for (int b = tid; b < nb; b += RED_NT) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) vd[q] += a.partials[(long long)b * NV + q];
-  }
-#pragma unroll
-  for (int q = 0; q < NV; ++q) vd[q] = warp_sum(vd[q]);
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q][w] = vd[q];
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double tot[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      tot[q] = 0.0;
-      for (int u = 0; u < RED_NT / 32; ++u) tot[q] += sh[q][u];
-    }
-    const double t1 = tot[0], t2 = tot[1];
-    const bool bad = !(lwmax > neg_inf<T>()) || lwmax != lwmax || !(t1 > 0);
-    if (bad) atomicOr(a.err, ERR_NUMERIC);
-    const double lz = (double)lwmax + log(t1) - log((double)a.N);
-    a.stats[0] += lz;
-    a.stats[1] = lz;
-    a.stats[2] = t1 * t1 / t2;
-    a.stats[3] = t1;
-#pragma unroll
-    for (int c = 0; c < D; ++c) a.stats[4 + a.perm[c]] = tot[2 + c] / t1;
-    *a.lwmax_t = lwmax;
-    if (a.mean_out)
-      for (int c = 0; c < D; ++c) a.mean_out[c] = a.stats[4 + c];
-    if (a.logz_out) *a.logz_out = a.stats[0];
-    *a.lwmax_key = 0ull;
-    *a.done = 0u;
-  }
-}
-
-template <typename T, int D1, int D2>
-__global__ void __launch_bounds__(RED_NT) outer_reduce_kernel(OuterArgs<T> a) {
-  outer_reduce_body<T, D1, D2>(a, blockIdx.x, gridDim.x);
-}
-
-// The outer reductions of many filters in one launch: blocks bstart[f] ..
-// bstart[f+1]-1 reduce filter f, exactly as the single launch above would.
-template <typename T, int D1, int D2>
-__global__ void __launch_bounds__(RED_NT)
-    outer_reduce_batch_kernel(const OuterArgs<T>* __restrict__ args, const int* __restrict__ bstart, int F) {
-  __shared__ int s_f;
-  if (threadIdx.x == 0) s_f = find_segment(bstart, F, (int)blockIdx.x);
-  __syncthreads();
-  const int f = s_f;
-  const OuterArgs<T> a = args[f];
-  outer_reduce_body<T, D1, D2>(a, (int)blockIdx.x - bstart[f], bstart[f + 1] - bstart[f]);
-}
 
 }  // namespace dpf

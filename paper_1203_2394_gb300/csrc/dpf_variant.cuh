@@ -7,18 +7,20 @@
 #include "dpf_pf.cuh"
 #include "dpf_std.cuh"
 #include "dpf_step_warp.cuh"
+#include "dpf_outer.cuh"
 
 namespace dpf {
 
 inline int threads_for(int M) { return ((M + 31) / 32) * 32; }
 
-// XZM: 0 = kernels for both x-transition kinds, 1 = only the general (x depends on z) kernels.
-// The outer stage of a step (the outer reduction, then the global resampling),
-// for every filter kind.
+// The outer stage of a step (the outer reduction and the global resampling, in one
+// cooperative launch: fused_outer_kernel), for every filter kind. `arrive` is the
+// grid barrier's counter (null for the two-launch batched form).
 template <typename T>
-void fill_outer_args(Ctx& x, double* mean_out, double* logz_out, void* ov, void* gv) {
-    OuterArgs<T>& o = *(OuterArgs<T>*)ov;
-    o = OuterArgs<T>{};
+void fill_outer_args(Ctx& x, double* mean_out, double* logz_out, unsigned int* arrive, void* out) {
+    FusedOuterArgs<T>& a = *(FusedOuterArgs<T>*)out;
+    a = FusedOuterArgs<T>{};
+    OuterArgs<T>& o = a.o;
     o.lw = (const T*)x.lw;
     o.xm = (const T*)x.xm;
     o.zm = (const T*)x.zm;
@@ -35,42 +37,26 @@ void fill_outer_args(Ctx& x, double* mean_out, double* logz_out, void* ov, void*
     o.mean_out = mean_out;
     o.logz_out = logz_out;
     o.err = x.err;
-    const long long t = x.t + 1;
-    const long long tiles = (x.N + SCAN_TILE - 1) / SCAN_TILE;
-    GlobalArgs<T>& g = *(GlobalArgs<T>*)gv;
-    g = GlobalArgs<T>{};
-    g.w = (const T*)x.lw;
-    g.lwmax = (const T*)x.lwmax_t;
-    g.w_out = (T*)x.wout;
-    g.n = x.N;
-    g.shift = 62 - ceil_log2_i(x.N);
-    g.shift_dev = nullptr;
-    g.C = x.Csum;
-    g.u_ptr = nullptr;
-    g.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
-    g.t = (uint32_t)t;
-    g.out = x.anc;
-    g.st = ScanState{x.flags, x.agg, x.incl, x.ticket};
-    g.ticket_base = x.ticket_next;
-    g.epoch = ++x.epoch;
-    g.err = x.err;
-    g.withhold = -1;
-    x.ticket_next += (unsigned long long)tiles;
+    a.w_out = (T*)x.wout;
+    a.anc = x.anc;
+    a.ctot = x.ctot;
+    a.arrive = arrive;
+    a.shift = 62 - ceil_log2_i(x.N);
+    a.logN = std::log((double)x.N);
+    a.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
+    a.t = (uint32_t)(x.t + 1);
+    a.withhold = -1;
   }
 
 template <typename T, int D1, int D2>
 dpf_status outer_stage(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
-    OuterArgs<T> o;
-    GlobalArgs<T> g;
-    fill_outer_args<T>(x, mean_out, logz_out, &o, &g);
-    outer_reduce_kernel<T, D1, D2><<<x.n_red_blocks, RED_NT, 0, st>>>(o);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "outer reduce launch");
-    global_scan_scatter<T, true><<<(unsigned)((x.N + SCAN_TILE - 1) / SCAN_TILE), SCAN_NT, 0, st>>>(g);
-    return cuda_error(cudaGetLastError(), "outer resample launch");
+    FusedOuterArgs<T> a;
+    fill_outer_args<T>(x, mean_out, logz_out, x.done + 1, &a);
+    return cuda_error(fused_outer_launch<T, D1, D2>(a, fused_outer_grid<T, D1, D2>(x.N), st),
+                      "outer stage launch");
   }
 
-
+// XZM: 0 = kernels for both x-transition kinds, 1 = only the general (x depends on z) kernels.
 template <typename T, int D1, int D2, int DY, int XZM = 0>
 struct VariantImpl {
   typedef MC<T, D1, D2, DY> Const;
@@ -322,27 +308,29 @@ struct VariantImpl {
     else return b.xz ? batch_ppl<true>(b, s, occ) : batch_ppl<false>(b, s, occ);
   }
 
-  // Arguments of the outer stage that follows the coming step: the reduction (o)
-  // and the global resampling (g). Advances the context's scan epoch and ticket
-  // base, as the launches that use these arguments will consume them.
-  static void outer_args(Ctx& x, double* mean_out, double* logz_out, void* ov, void* gv) {
-    fill_outer_args<T>(x, mean_out, logz_out, ov, gv);
+  // Arguments of the outer stage that follows the coming step (both of its
+  // batched launches read them).
+  static void outer_args(Ctx& x, double* mean_out, double* logz_out, void* out) {
+    fill_outer_args<T>(x, mean_out, logz_out, nullptr, out);
   }
+
+  // CTAs of the filter's outer stage (the same in the single and batched forms).
+  static int outer_ctas(long long N) { return fused_outer_grid<T, D1, D2>(N); }
 
   static dpf_status outer(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
     return outer_stage<T, D1, D2>(x, mean_out, logz_out, st);
   }
 
-  // The outer reductions of F filters of this variant in one launch (device
-  // arguments, bstart[F] blocks in all).
-  static dpf_status outer_batch(const void* oargs, const int* bstart, int nblocks, int F, cudaStream_t st) {
-    outer_reduce_batch_kernel<T, D1, D2><<<nblocks, RED_NT, 0, st>>>((const OuterArgs<T>*)oargs, bstart, F);
-    return cuda_error(cudaGetLastError(), "batched outer reduce launch");
+  // The outer sums of F filters of this variant in one launch (device arguments,
+  // cstart[F] CTAs in all).
+  static dpf_status outer_batch(const void* args, const int* cstart, int nctas, int F, cudaStream_t st) {
+    outer_sums_batch_kernel<T, D1, D2><<<nctas, OF_NT, 0, st>>>((const FusedOuterArgs<T>*)args, cstart, F);
+    return cuda_error(cudaGetLastError(), "batched outer sums launch");
   }
 
-  // The outer resamplings of F filters of this precision in one launch.
-  static dpf_status scan_batch(const void* gargs, const int* tstart, int ntiles, int F, cudaStream_t st) {
-    global_scan_scatter_batch<T><<<ntiles, SCAN_NT, 0, st>>>((const GlobalArgs<T>*)gargs, tstart, F);
+  // The outer resamplings and statistics of F filters of this precision in one launch.
+  static dpf_status scan_batch(const void* args, const int* cstart, int nctas, int F, cudaStream_t st) {
+    outer_scatter_batch_kernel<T><<<nctas, OF_NT, 0, st>>>((const FusedOuterArgs<T>*)args, cstart, F);
     return cuda_error(cudaGetLastError(), "batched outer resample launch");
   }
 
@@ -438,8 +426,8 @@ struct VariantImpl {
     v.outer_args = &outer_args;
     v.outer_batch = &outer_batch;
     v.scan_batch = &scan_batch;
-    v.oargs_size = sizeof(OuterArgs<T>);
-    v.gargs_size = sizeof(GlobalArgs<T>);
+    v.outer_ctas = &outer_ctas;
+    v.oargs_size = sizeof(FusedOuterArgs<T>);
     v.step_smem = &smem;
     v.batch_args = &batch_args;
     v.region_bytes = &region_bytes;

@@ -68,6 +68,7 @@ struct WideVariantImpl {
     v.step = &step;
     v.outer = &Base::outer;
     v.outer_args = &Base::outer_args;
+    v.outer_ctas = &Base::outer_ctas;
     v.outer_batch = &Base::outer_batch;
     v.scan_batch = &Base::scan_batch;
     v.step_smem = &smem;
@@ -78,8 +79,7 @@ struct WideVariantImpl {
     v.ppl_for = &Base::ppl_for;
     v.args_size = sizeof(StepArgs<T>);
     v.const_size = sizeof(Const);
-    v.oargs_size = sizeof(OuterArgs<T>);
-    v.gargs_size = sizeof(GlobalArgs<T>);
+    v.oargs_size = sizeof(FusedOuterArgs<T>);
     v.max_m = MAX_M;
     v.has_tc = tc_shape(256);
     v.xz_supported = false;
