@@ -13,7 +13,10 @@
 //   C. each CTA scans its items' counts chunk by chunk, turns each cumulative
 //      count into the number of systematic points below it, and writes the
 //      ancestor of every point that falls in the chunk;
-//   D. the last CTA to finish combines the partial sums into the statistics.
+//   D. one CTA combines the partial sums into the statistics (an extra CTA with no
+//      items where the grid has room for it, so that this serial double-precision
+//      work overlaps the others' scatter), and the last CTA to finish resets the
+//      counters for the next step.
 // Many filters run the same phases in two ordinary launches (A, then B-D), the
 // launch boundary standing in for the barrier, with each filter's partition
 // unchanged, so their results are bit-identical to the single launch's.
@@ -38,6 +41,7 @@ struct FusedOuterArgs {
   int32_t* anc;                 // the N ancestors
   unsigned long long* ctot;     // one count total a CTA
   unsigned int* arrive;         // barrier arrivals, reset by the last CTA (null: no barrier)
+  int nwork;                    // CTAs that own items; one more, if launched, only computes statistics
   int shift;                    // S = 62 - ceil(log2 N)
   double logN;                  // log N
   Key key;                      // u = rand_word(key, t, 0, P_OUTER, 0)
@@ -113,13 +117,13 @@ __device__ __forceinline__ void outer_sums(const FusedOuterArgs<T>& a, int bid, 
     su[w] = cc;
   }
   __syncthreads();
-  for (int q = tid; q < NV; q += OF_NT) {
-    T s = T(0);
+  if (tid == 0) {  // one thread publishes the CTA's row (so that one fence covers it)
+    for (int q = 0; q < NV; ++q) {
+      T s = T(0);
 #pragma unroll
-    for (int r = 0; r < NW; ++r) s += sv[q][r];
-    o.partials[(long long)bid * NV + q] = (double)s;
-  }
-  if (tid == 0) {
+      for (int r = 0; r < NW; ++r) s += sv[q][r];
+      o.partials[(long long)bid * NV + q] = (double)s;
+    }
     unsigned long long s = 0;
 #pragma unroll
     for (int r = 0; r < NW; ++r) s += su[r];
@@ -229,23 +233,16 @@ __device__ __forceinline__ void outer_scatter(const FusedOuterArgs<T>& a, int bi
   }
 }
 
-// ---- D: the last of the filter's `nb` CTAs to get here combines the partial sums
-// into the statistics and resets the counters for the next step ----
+// ---- D: the statistics from the `nb` CTAs' partial sums, by one CTA once they are
+// all in place ----
 template <typename T>
-__device__ __forceinline__ void outer_finish(const FusedOuterArgs<T>& a, int nb, T lwmax,
-                                             unsigned long long C) {
+__device__ __forceinline__ void outer_stats(const FusedOuterArgs<T>& a, int nb, T lwmax,
+                                            unsigned long long C) {
   constexpr int NW = OF_NT / 32;
-  __shared__ int s_last;
   __shared__ double sd[OF_MAX_NV];
   const OuterArgs<T>& o = a.o;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int D = o.d1 + o.d2, NV = 2 + D;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = atomicAdd(o.done, 1u) == (unsigned)nb - 1u;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
   for (int q = w; q < NV; q += NW) {
     double s = 0.0;
     for (int b = lane; b < nb; b += 32) s += __ldcg(o.partials + (long long)b * NV + q);
@@ -271,8 +268,17 @@ __device__ __forceinline__ void outer_finish(const FusedOuterArgs<T>& a, int nb,
     if (o.logz_out) *o.logz_out = o.stats[0];
     *o.lwmax_t = lwmax;
     *o.Csum = C;
-    *o.lwmax_key = 0ull;
-    *o.done = 0u;
+  }
+}
+
+// The last of the `nb` CTAs to get here resets the counters for the next step: by
+// then every CTA has read the largest log-weight's key and passed the barrier.
+template <typename T>
+__device__ __forceinline__ void outer_done(const FusedOuterArgs<T>& a, int nb) {
+  __syncthreads();
+  if (threadIdx.x == 0 && atomicAdd(a.o.done, 1u) == (unsigned)nb - 1u) {
+    *a.o.lwmax_key = 0ull;
+    *a.o.done = 0u;
     if (a.arrive) *a.arrive = 0u;
   }
 }
@@ -281,14 +287,14 @@ __device__ __forceinline__ void outer_finish(const FusedOuterArgs<T>& a, int nb,
 template <typename T, int D1, int D2>
 __global__ void __launch_bounds__(OF_NT) fused_outer_kernel(const __grid_constant__ FusedOuterArgs<T> a) {
   __shared__ int s_ok;
-  const int tid = threadIdx.x, bid = blockIdx.x, nb = gridDim.x;
+  const int tid = threadIdx.x, bid = blockIdx.x, nb = gridDim.x, nw = a.nwork;
   T lwmax;
   order_decode(*a.o.lwmax_key, lwmax);
-  outer_sums<T, D1, D2>(a, bid, nb, lwmax);
-  __threadfence();
+  if (bid < nw) outer_sums<T, D1, D2>(a, bid, nw, lwmax);
   __syncthreads();
   // grid-wide barrier: every CTA is resident, and the wait is bounded all the same
   if (tid == 0) {
+    __threadfence();  // the CTA's partial row and count total, written by this thread
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> arr(*a.arrive);
     if (bid != a.withhold) arr.fetch_add(1u, cuda::memory_order_release);
     bool ok = arr.load(cuda::memory_order_acquire) >= (unsigned)nb;
@@ -303,9 +309,10 @@ __global__ void __launch_bounds__(OF_NT) fused_outer_kernel(const __grid_constan
   }
   __syncthreads();
   unsigned long long pre, C;
-  count_prefix(a.ctot, bid, nb, pre, C);
-  if (s_ok && C > 0) outer_scatter<T>(a, bid, nb, lwmax, pre, C);  // else the ancestors stay as they were
-  outer_finish<T>(a, nb, lwmax, C);
+  count_prefix(a.ctot, bid < nw ? bid : nw, nw, pre, C);
+  if (bid == (nb > nw ? nw : nw - 1)) outer_stats<T>(a, nw, lwmax, C);
+  if (bid < nw && s_ok && C > 0) outer_scatter<T>(a, bid, nw, lwmax, pre, C);  // else the ancestors stay
+  outer_done<T>(a, nb);
 }
 
 // The same stage for many filters in two launches, CTAs cstart[f] .. cstart[f+1]-1
@@ -338,29 +345,40 @@ __global__ void __launch_bounds__(OF_NT)
   unsigned long long pre, C;
   count_prefix(a.ctot, bid, nb, pre, C);
   if (C > 0) outer_scatter<T>(a, bid, nb, lwmax, pre, C);
-  outer_finish<T>(a, nb, lwmax, C);
+  if (bid == nb - 1) outer_stats<T>(a, nb, lwmax, C);
+  outer_done<T>(a, nb);
 }
 
-// CTAs of a filter's outer stage over N items: one a chunk, at most as many as are
-// resident on the device at once (and OF_MAX_CTAS).
+// CTAs resident on the device at once for the single-filter launch.
 template <typename T, int D1, int D2>
-int fused_outer_grid(long long N) {
+int fused_outer_cap() {
   static const int cap = [] {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused_outer_kernel<T, D1, D2>, OF_NT, 0);
     const int c = occ * sms;
-    return c < 1 ? 1 : (c < OF_MAX_CTAS ? c : OF_MAX_CTAS);
+    return c < 2 ? 2 : c;
   }();
-  const long long nch = (N + OF_CHUNK - 1) / OF_CHUNK;
-  return (int)(nch < cap ? nch : cap);
+  return cap;
 }
 
+// CTAs that own items in a filter's outer stage over N items: one a chunk, at most
+// OF_MAX_CTAS and one fewer than the resident capacity (the same in the single and
+// batched forms, so that their partitions agree).
 template <typename T, int D1, int D2>
-cudaError_t fused_outer_launch(const FusedOuterArgs<T>& a, int grid, cudaStream_t st) {
+int fused_outer_grid(long long N) {
+  const long long cap = fused_outer_cap<T, D1, D2>() - 1;
+  const long long lim = cap < OF_MAX_CTAS ? cap : OF_MAX_CTAS;
+  const long long nch = (N + OF_CHUNK - 1) / OF_CHUNK;
+  return (int)(nch < lim ? nch : lim);
+}
+
+// The single-filter launch: a.nwork CTAs with items and one for the statistics.
+template <typename T, int D1, int D2>
+cudaError_t fused_outer_launch(const FusedOuterArgs<T>& a, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
+  cfg.gridDim = dim3((unsigned)a.nwork + 1u);
   cfg.blockDim = dim3(OF_NT);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;

@@ -9,10 +9,11 @@
 
 namespace dpf {
 
-// The cooperative outer stage over 3 chunks of zero log-weights (d1 = d2 = 1) with
-// CTA 0 never arriving at the grid barrier: the waits of all three CTAs run out,
-// the error word reports the timeout, the scatter is skipped, and the last CTA
-// still resets the counters. Returns the status the error word maps to.
+// The cooperative outer stage over 3 chunks of zero log-weights (d1 = d2 = 1; 3 CTAs
+// with items and one for the statistics) with CTA 0 never arriving at the grid
+// barrier: the waits of all four CTAs run out, the error word reports the timeout,
+// the scatter is skipped, and the last CTA still resets the counters. Returns the
+// status the error word maps to.
 dpf_status check_outer_barrier(cudaStream_t s) {
   const long long n = 3 * OF_CHUNK;
   const size_t fb = sizeof(float) * n;
@@ -51,7 +52,8 @@ dpf_status check_outer_barrier(cudaStream_t s) {
   a.key = Key{1u, 0u};
   a.t = 1;
   a.withhold = 0;
-  if (e == cudaSuccess) e = fused_outer_launch<float, 1, 1>(a, 3, s);
+  a.nwork = 3;
+  if (e == cudaSuccess) e = fused_outer_launch<float, 1, 1>(a, s);
   int w = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&w, o.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

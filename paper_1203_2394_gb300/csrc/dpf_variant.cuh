@@ -52,8 +52,8 @@ template <typename T, int D1, int D2>
 dpf_status outer_stage(Ctx& x, double* mean_out, double* logz_out, cudaStream_t st) {
     FusedOuterArgs<T> a;
     fill_outer_args<T>(x, mean_out, logz_out, x.done + 1, &a);
-    return cuda_error(fused_outer_launch<T, D1, D2>(a, fused_outer_grid<T, D1, D2>(x.N), st),
-                      "outer stage launch");
+    a.nwork = fused_outer_grid<T, D1, D2>(x.N);
+    return cuda_error(fused_outer_launch<T, D1, D2>(a, st), "outer stage launch");
   }
 
 // XZM: 0 = kernels for both x-transition kinds, 1 = only the general (x depends on z) kernels.
