@@ -366,7 +366,7 @@ def run(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spec.dy * 4,
                 "d2h_bytes_per_step": (4 + spec.d) * 8 + 4},
         "lookahead_evaluations_per_s": value * L,  # the N M L look-ahead pairs of every step
-        "gpu_launches": 3 * K,
+        "gpu_launches": 2 * K,  # the step kernel and the outer stage, each step
         "clocks": clk,
         "cpu_baseline": cpu,
     }
