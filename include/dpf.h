@@ -340,7 +340,8 @@ void dpf_destroy(dpf_ctx* ctx);
  * share d, dy, precision and L). Filter f uses seeds[f] (it reproduces a
  * single filter created with that seed). The filters of one compiled
  * (precision, d1, d2, dy) variant and inner-particles-per-lane class share one
- * persistent launch of the step kernel; the outer stages of the filters run
+ * persistent launch of the step kernel (or one launch each, where
+ * dpf_batch_autotune finds that faster); the outer stages of the filters run
  * concurrently. Each M must be at most 256 with M, L and L*d1 rows of whole
  * 16-byte units. models, d1, N, M, seeds: host arrays of F entries.
  */
@@ -362,10 +363,20 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
 
 /* Time the launch-shape candidates of every class on the live state (reps
  * launches each, without advancing the filters) and keep the fastest; a JSON
- * report of the choices is written to report (report_bytes, may be NULL).
+ * report of the choices is written to report (report_bytes, may be NULL). The
+ * candidates are two inner-particles-per-lane counts, each as one launch for the
+ * class (each filter's model constants staged in shared memory) or, for a class
+ * of several filters, one launch a filter (its constants a launch parameter); the
+ * results are the same under every choice.
  * DPF_E_INVALID before the first step: that step has no inner update, so its
  * launches would not time the steady-state kernel. */
 dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t report_bytes);
+
+/* Set the schedule of every class of several filters by hand, at the classes'
+ * current inner-particles-per-lane: split != 0 one launch a filter, 0 one launch
+ * a class (the schedule until dpf_batch_autotune chooses). The results are the
+ * same under both; only the time differs. */
+dpf_status dpf_batch_set_split(dpf_batch* b, int32_t split);
 
 /* Borrow filter f's context (for dpf_read, dpf_diag); owned by the batch. */
 dpf_status dpf_batch_filter(dpf_batch* b, int32_t f, dpf_ctx** out);

@@ -35,6 +35,13 @@ struct BatchClass {
   std::vector<unsigned char> shared_mc;  // the constants, when all members share them
   int occ = 0;                   // CTAs per SM at this launch shape
   double tuned_us = 0.0;
+  // the other schedule the autotuner may pick: one launch a member of the single-filter
+  // step kernel, its launch arguments and model constants launch parameters (read as
+  // constant-bank operands), instead of one launch for the class with each filter's
+  // arguments and constants staged in shared memory; the results are the same
+  bool split = false;
+  std::vector<unsigned char> host_descs;   // the descriptor set of the coming step, host copy
+  const unsigned char* host_cur = nullptr; // the set the next launch reads (split)
 };
 
 // The filters of one variant, whose outer reductions share a launch.
@@ -114,11 +121,24 @@ static dpf_status shape_class(dpf_batch& b, BatchClass& c) {
   return DPF_OK;
 }
 
+// The step kernel launches of one class (its descriptors at c.launch.descs, and at
+// c.host_cur on the host).
+static dpf_status class_launch(dpf_batch& b, BatchClass& c, cudaStream_t s) {
+  if (!c.split) return c.var->batch_launch(c.launch, s, nullptr);
+  for (size_t q = 0; q < c.members.size(); ++q) {
+    dpf_status st = c.var->single_launch(*b.ctx[c.members[q]], c.host_cur + q * c.var->args_size, c.ppl,
+                                         c.xz, s);
+    if (st) return st;
+  }
+  return DPF_OK;
+}
+
 // Fill descriptor set `slot` of every class for the coming step (y rows given).
 static dpf_status upload_descs(dpf_batch& b, const void* y_prev_rows, const void* y_cur_rows,
                                int slot, cudaStream_t s) {
   for (BatchClass& c : b.cls) {
-    std::vector<unsigned char> host(c.desc_bytes);
+    std::vector<unsigned char>& host = c.host_descs;
+    host.assign(c.desc_bytes, 0);
     const size_t as = c.var->args_size;
     for (size_t q = 0; q < c.members.size(); ++q) {
       const int f = c.members[q];
@@ -129,8 +149,10 @@ static dpf_status upload_descs(dpf_batch& b, const void* y_prev_rows, const void
     void* dst = (char*)c.d_descs + (size_t)slot * c.desc_bytes;
     cudaError_t e = cudaMemcpyAsync(dst, host.data(), c.desc_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_error(e, "batch: descriptor upload");
-    // pageable source: the copy is staged before cudaMemcpyAsync returns, so `host` may go
+    // pageable source: the copy is staged before cudaMemcpyAsync returns; the host copy
+    // stays for the split schedule's launches, which take the arguments as parameters
     c.launch.descs = dst;
+    c.host_cur = host.data();
   }
   return DPF_OK;
 }
@@ -187,7 +209,7 @@ static dpf_status step_launch(dpf_batch& b) {
     cudaEventRecord(b.pev[b.pev_used], b.stream);
   }
   for (BatchClass& c : b.cls) {
-    dpf_status st = c.var->batch_launch(c.launch, b.stream, nullptr);
+    dpf_status st = class_launch(b, c, b.stream);
     if (st) return st;
   }
   if (b.profiling) {
@@ -428,7 +450,11 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
   }
   dpf_status st = DPF_OK;
   for (long long k = 0; k < T && !st; ++k) {
-    for (BatchClass& c : b->cls) c.launch.descs = (char*)c.d_descs + (size_t)k * c.desc_bytes;
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+      BatchClass& c = b->cls[ci];
+      c.launch.descs = (char*)c.d_descs + (size_t)k * c.desc_bytes;
+      c.host_cur = sets[ci].data() + (size_t)k * c.desc_bytes;
+    }
     for (OuterGroup& g : b->og) g.cur = (const char*)g.d_oargs + (size_t)k * g.set_bytes;
     b->gcur = (const char*)b->d_gargs + (size_t)k * b->gset_bytes;
     st = step_launch(*b);
@@ -459,6 +485,7 @@ dpf_status dpf_batch_run(dpf_batch* b, const void* ys_dev, int64_t T, double* me
   }
   for (BatchClass& c : b->cls) {  // back to the two-set ring of dpf_batch_step
     c.launch.descs = c.d_descs;
+    c.host_cur = nullptr;  // the next dpf_batch_step rebuilds its host copy
   }
   return st ? st : dpf_batch_sync(b);
 }
@@ -482,9 +509,10 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
     return set_error(DPF_E_INVALID,
                      "dpf_batch_autotune: step the batch once first (the first step has no inner update)");
   // candidates per class: the smallest inner-particles-per-lane that fits M, and twice
-  // that (more instruction-level parallelism per lane, fewer lanes busy); each is timed
-  // on the live state with the next step's arguments, which only rewrites the outputs
-  // the next real step rewrites anyway
+  // that (more instruction-level parallelism per lane, fewer lanes busy), each as one
+  // launch for the class or (a class of several filters) one launch a filter; each is
+  // timed on the live state with the next step's arguments, which only rewrites the
+  // outputs the next real step rewrites anyway
   const long long t = b->t + 1;
   const size_t rows = (size_t)b->F * b->dy * b->s;
   char* cur = (char*)b->yhist + (t % 2) * rows;  // the candidate runs read whatever y is there
@@ -506,33 +534,39 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
       if (ok) cand.push_back(cand[0] * 2);
     }
     int best = c.ppl;
+    bool best_split = false;
     double best_us = 1e300;
     std::string tried;
     for (int ppl : cand) {
-      c.ppl = ppl;
-      st = shape_class(*b, c);
-      if (st) break;
-      c.var->batch_launch(c.launch, b->stream, nullptr);  // warm-up
-      cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < reps; ++r) c.var->batch_launch(c.launch, b->stream, nullptr);
-      cudaEventRecord(e1, b->stream);
-      cudaError_t ce = cudaEventSynchronize(e1);
-      if (ce != cudaSuccess) {
-        st = cuda_error(ce, "dpf_batch_autotune");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double us = ms * 1e3 / reps;
-      tried += (tried.empty() ? "" : ", ") + std::string("{\"ppl\": ") + std::to_string(ppl) +
-               ", \"us\": " + std::to_string(us) + "}";
-      if (us < best_us) {
-        best_us = us;
-        best = ppl;
+      for (int split = 0; split < (c.members.size() > 1 ? 2 : 1) && !st; ++split) {
+        c.ppl = ppl;
+        c.split = split != 0;
+        st = shape_class(*b, c);
+        if (st) break;
+        class_launch(*b, c, b->stream);  // warm-up
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps; ++r) class_launch(*b, c, b->stream);
+        cudaEventRecord(e1, b->stream);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+          st = cuda_error(ce, "dpf_batch_autotune");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double us = ms * 1e3 / reps;
+        tried += (tried.empty() ? "" : ", ") + std::string("{\"ppl\": ") + std::to_string(ppl) +
+                 ", \"split\": " + (c.split ? "true" : "false") + ", \"us\": " + std::to_string(us) + "}";
+        if (us < best_us) {
+          best_us = us;
+          best = ppl;
+          best_split = c.split;
+        }
       }
     }
     if (st) break;
     c.ppl = best;
+    c.split = best_split;
     c.tuned_us = best_us;
     st = shape_class(*b, c);
     if (st) break;
@@ -540,6 +574,7 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
            ", \"d2\": " + std::to_string(c.var->d2) + ", \"xz\": " + (c.xz ? "true" : "false") +
            ", \"filters\": " + std::to_string(c.members.size()) + ", \"groups\": " +
            std::to_string(c.fstart.back()) + ", \"chosen_ppl\": " + std::to_string(c.ppl) +
+           ", \"split\": " + (c.split ? "true" : "false") +
            ", \"grid\": " + std::to_string(c.launch.grid) + ", \"chunk\": " +
            std::to_string(c.launch.chunk) + ", \"tried\": [" + tried + "]}";
   }
@@ -553,6 +588,15 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
     memcpy(report, rep.data(), n);
     report[n] = 0;
   }
+  return DPF_OK;
+}
+
+dpf_status dpf_batch_set_split(dpf_batch* b, int32_t split) {
+  clear_error();
+  if (!b) return set_error(DPF_E_INVALID, "dpf_batch_set_split: null batch");
+  cudaError_t e = cudaStreamSynchronize(b->stream);  // no launch in flight reads the shapes
+  if (e != cudaSuccess) return cuda_error(e, "dpf_batch_set_split");
+  for (BatchClass& c : b->cls) c.split = split != 0 && c.members.size() > 1;
   return DPF_OK;
 }
 

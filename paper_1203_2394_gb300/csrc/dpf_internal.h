@@ -120,6 +120,8 @@ struct Variant {
   void (*batch_args)(Ctx&, const void* y_prev, const void* y_cur, bool xz, void* out);
   size_t (*region_bytes)(int M, int L, bool xz);
   dpf_status (*batch_launch)(const BatchLaunch&, cudaStream_t, int* occ);
+  // a batched member's step as its own launch of the single-filter kernel
+  dpf_status (*single_launch)(Ctx&, const void* args, int ppl, bool xz, cudaStream_t s) = nullptr;
   bool (*use_xz)(const Ctx&);
   int (*ppl_for)(int M);
   size_t args_size, const_size, oargs_size;
@@ -186,6 +188,7 @@ struct dpf_ctx {
   int ppt = 1;        // inner particles per thread of the step kernel
   int xp = 4;         // padded x row length (elements; 16-byte rows)
   int grid_step = 0;  // persistent grid of the step kernel (0 = not yet sized)
+  const void* grid_kernel = nullptr;  // ... the warp-step kernel it was sized for
   void* d_mconst = nullptr;  // the model constants in device memory (variants that read them there)
   bool tensor_cores = true;  // tensor-core propagation where the variant has one
   dpf_proposal* proposal = nullptr;  // learned inner proposal (null: the prior)

@@ -153,7 +153,7 @@ struct VariantImpl {
   }
 
   template <bool XZ, int PPL, int MF>
-  static dpf_status launch_warp_mf(Ctx& x, StepArgs<T>& a) {
+  static dpf_status launch_warp_mf(Ctx& x, StepArgs<T>& a, cudaStream_t stream = nullptr) {
     auto k = step_warp_kernel<T, D1, D2, DY, XZ, PPL, MF>;
     static bool attr_done = false;
     if (!attr_done) {
@@ -162,16 +162,18 @@ struct VariantImpl {
       attr_done = true;
     }
     const size_t sm = warp_geometry<T, D1, D2, DY, XZ>(x.M, x.L, &a, a.first != 0);
-    if (x.grid_step == 0) {  // persistent grid: as many CTAs as fit on the device at once
+    if (x.grid_step == 0 || x.grid_kernel != (const void*)k) {
+      // persistent grid: as many CTAs of this kernel as fit on the device at once
       int nb = 0, dev = 0, nsm = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, WARPS_PER_CTA * 32, sm);
       if (e == cudaSuccess) e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess) return cuda_error(e, "step kernel occupancy");
       x.grid_step = (nb > 0 ? nb : 1) * nsm;
+      x.grid_kernel = (const void*)k;
     }
     const long long grid = std::min<long long>((x.N + WARPS_PER_CTA - 1) / WARPS_PER_CTA, x.grid_step);
-    k<<<(unsigned)grid, WARPS_PER_CTA * 32, sm, x.stream>>>(cst(x), a);
+    k<<<(unsigned)grid, WARPS_PER_CTA * 32, sm, stream ? stream : x.stream>>>(cst(x), a);
     return cuda_error(cudaGetLastError(), "step kernel launch");
   }
   // M = 32 PPL (every lane full) takes the kernel compiled for that M
@@ -247,6 +249,24 @@ struct VariantImpl {
 
   // ---- many filters of this variant in one launch per PPL class ----
   static int ppl_for(int M) { return M <= 32 ? 1 : M <= 64 ? 2 : M <= 128 ? 4 : 8; }
+
+  // A batched member's step as its own launch of the single-filter kernel on stream s,
+  // from its batched launch arguments, at `ppl` inner particles per lane.
+  template <bool XZ>
+  static dpf_status single_xz(Ctx& x, StepArgs<T>& a, int ppl, cudaStream_t s) {
+    switch (ppl) {
+      case 1: return x.M == 32 ? launch_warp_mf<XZ, 1, 32>(x, a, s) : launch_warp_mf<XZ, 1, 0>(x, a, s);
+      case 2: return x.M == 64 ? launch_warp_mf<XZ, 2, 64>(x, a, s) : launch_warp_mf<XZ, 2, 0>(x, a, s);
+      case 4: return x.M == 128 ? launch_warp_mf<XZ, 4, 128>(x, a, s) : launch_warp_mf<XZ, 4, 0>(x, a, s);
+      default: return x.M == 256 ? launch_warp_mf<XZ, 8, 256>(x, a, s) : launch_warp_mf<XZ, 8, 0>(x, a, s);
+    }
+  }
+  static dpf_status single_launch(Ctx& x, const void* args, int ppl, bool xz, cudaStream_t s) {
+    StepArgs<T> a;
+    memcpy(&a, args, sizeof(a));
+    if constexpr (XZM == 1) return single_xz<true>(x, a, ppl, s);
+    else return xz ? single_xz<true>(x, a, ppl, s) : single_xz<false>(x, a, ppl, s);
+  }
 
   // Per-filter launch arguments for a batched step (y rows given by the batch).
   static void batch_args(Ctx& x, const void* y_prev, const void* y_cur, bool xz, void* out) {
@@ -427,6 +447,7 @@ struct VariantImpl {
     v.outer_batch = &outer_batch;
     v.scan_batch = &scan_batch;
     v.outer_ctas = &outer_ctas;
+    v.single_launch = &single_launch;
     v.oargs_size = sizeof(FusedOuterArgs<T>);
     v.step_smem = &smem;
     v.batch_args = &batch_args;

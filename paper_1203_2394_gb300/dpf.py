@@ -97,6 +97,7 @@ SIGNATURES = [
     ("dpf_batch_step", ctypes.c_int, [_P, _P, _P, _P]),
     ("dpf_batch_run", ctypes.c_int, [_P, _P, _I64, _P, _P, _I32]),
     ("dpf_batch_autotune", ctypes.c_int, [_P, _I32, ctypes.c_char_p, _SZ]),
+    ("dpf_batch_set_split", ctypes.c_int, [_P, _I32]),
     ("dpf_batch_filter", ctypes.c_int, [_P, _I32, _P]),
     ("dpf_batch_sync", ctypes.c_int, [_P]),
     ("dpf_batch_profile", ctypes.c_int, [_P, _I32]),
@@ -417,6 +418,11 @@ class Batch:
         check(self._lib.dpf_batch_autotune(self.h, int(reps), buf, len(buf)))
         import json
         return json.loads(buf.value.decode())
+
+    def set_split(self, split=True):
+        """Every class of several filters as one launch a filter (True) or one launch
+        (False), by hand; the results do not depend on it."""
+        check(self._lib.dpf_batch_set_split(self.h, int(bool(split))))
 
     def profile(self, on=True):
         check(self._lib.dpf_batch_profile(self.h, int(on)))

@@ -3,7 +3,8 @@
 * Every member reproduces, bit for bit, the single filter created with its seed
   (same kernels, same random-number keys), whether the members of a launch read
   their own model constants or share one set.
-* A graph-captured run equals step-by-step stepping.
+* A graph-captured run equals step-by-step stepping, and one launch a filter (the
+  autotuner's other schedule) equals one launch a class.
 * Members of the d = 16 variants (splits 1/15 and 8/8, dy = 4) agree with the
   FP64 oracle, teacher-forced, within the FP32 tolerances: every selection and
   local resampling index equal or an explained flip, every group's inner state
@@ -67,6 +68,35 @@ def test_members_equal_single_filters_bitwise(one_system):
             for name in ("lw", "lwhat", "anc", "sel", "x", "z", "lq"):
                 np.testing.assert_array_equal(m.read(name), s.read(name), err_msg=f"{name} f={f} t={t}")
             np.testing.assert_array_equal(means[f].cpu().numpy(), ms)
+
+
+def test_split_schedule_equals_fused():
+    """One launch a filter (each filter's constants a launch parameter) gives the same
+    bits as one launch a class (at the same inner particles per lane), stepped and in a
+    graph."""
+    specs, models = _models()
+    ys = _ys(specs).astype(np.float32)
+    yd = torch.tensor(ys, device="cuda")
+    F = len(MEMBERS)
+    runs = []
+    for mode in ("fused", "split"):
+        b = _batch(models)
+        m = torch.zeros((T, F, 16), dtype=torch.float64, device="cuda")
+        lz = torch.zeros((T, F), dtype=torch.float64, device="cuda")
+        b.step_device(yd[0].data_ptr(), m[0].data_ptr(), lz[0].data_ptr())
+        b.sync()
+        if mode == "split":
+            b.set_split(True)
+        for t in range(1, T // 2):
+            b.step_device(yd[t].data_ptr(), m[t].data_ptr(), lz[t].data_ptr())
+        b.run_device(yd[T // 2:].data_ptr(), T - T // 2, m[T // 2:].data_ptr(), lz[T // 2:].data_ptr(), graph=True)
+        runs.append((m, lz, [{k: b.filter(f).read(k) for k in ("z", "lq", "x", "anc", "lw")} for f in range(F)]))
+        b.close()
+    for m, lz, st in runs[1:]:
+        assert torch.equal(m, runs[0][0]) and torch.equal(lz, runs[0][1])
+        for f in range(F):
+            for k in st[f]:
+                np.testing.assert_array_equal(st[f][k], runs[0][2][f][k], err_msg=f"{k} f={f}")
 
 
 def test_graph_run_equals_stepping():
