@@ -20,6 +20,8 @@
 
 namespace dpf {
 
+constexpr int BATCH_AUX_STREAMS = 3;  // streams beside the batch's own for a step's launches
+
 struct BatchClass {
   const Variant* var = nullptr;
   bool xz = false;
@@ -76,6 +78,12 @@ struct dpf_batch {
   bool profiling = false;
   std::vector<cudaEvent_t> pev;
   size_t pev_used = 0;
+  // streams beside `stream` over which a step's kernel launches are spread (the filters
+  // are independent, so one launch can take the SMs another's tail leaves idle), and
+  // the events that fork them from `stream` and join them back
+  std::vector<cudaStream_t> aux;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
   std::vector<void*> allocs;
 };
 
@@ -122,12 +130,13 @@ static dpf_status shape_class(dpf_batch& b, BatchClass& c) {
 }
 
 // The step kernel launches of one class (its descriptors at c.launch.descs, and at
-// c.host_cur on the host).
-static dpf_status class_launch(dpf_batch& b, BatchClass& c, cudaStream_t s) {
-  if (!c.split) return c.var->batch_launch(c.launch, s, nullptr);
+// c.host_cur on the host), each on the stream `next` returns.
+template <typename Next>
+static dpf_status class_launch(dpf_batch& b, BatchClass& c, Next next) {
+  if (!c.split) return c.var->batch_launch(c.launch, next(), nullptr);
   for (size_t q = 0; q < c.members.size(); ++q) {
     dpf_status st = c.var->single_launch(*b.ctx[c.members[q]], c.host_cur + q * c.var->args_size, c.ppl,
-                                         c.xz, s);
+                                         c.xz, next());
     if (st) return st;
   }
   return DPF_OK;
@@ -208,9 +217,22 @@ static dpf_status step_launch(dpf_batch& b) {
       }
     cudaEventRecord(b.pev[b.pev_used], b.stream);
   }
+  // the launches go round the batch's stream and its auxiliary streams, forked from and
+  // joined back to the batch's stream
+  const int S = 1 + (int)b.aux.size();
+  if (S > 1) {
+    cudaEventRecord(b.fork_ev, b.stream);
+    for (cudaStream_t s : b.aux) cudaStreamWaitEvent(s, b.fork_ev, 0);
+  }
+  int k = 0;
+  auto next = [&]() { const int q = k++ % S; return q == 0 ? b.stream : b.aux[q - 1]; };
   for (BatchClass& c : b.cls) {
-    dpf_status st = class_launch(b, c, b.stream);
+    dpf_status st = class_launch(b, c, next);
     if (st) return st;
+  }
+  for (size_t q = 0; q < b.aux.size(); ++q) {
+    cudaEventRecord(b.join_ev[q], b.aux[q]);
+    cudaStreamWaitEvent(b.stream, b.join_ev[q], 0);
   }
   if (b.profiling) {
     cudaEventRecord(b.pev[b.pev_used + 1], b.stream);
@@ -255,6 +277,18 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return fail(cuda_error(cudaGetLastError(), "dpf_batch_create: event"));
+  for (int q = 0; q < BATCH_AUX_STREAMS; ++q) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(cuda_error(cudaGetLastError(), "dpf_batch_create: stream"));
+    b->aux.push_back(s);
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(cuda_error(cudaGetLastError(), "dpf_batch_create: event"));
+    b->join_ev.push_back(e);
+  }
   for (int f = 0; f < F; ++f) {
     if (!models[f] || models[f]->d != b->d || models[f]->dy != b->dy || models[f]->precision != b->prec)
       return fail(set_error(DPF_E_INVALID, "dpf_batch_create: all filters need the same d, dy and precision"));
@@ -543,9 +577,10 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
         c.split = split != 0;
         st = shape_class(*b, c);
         if (st) break;
-        class_launch(*b, c, b->stream);  // warm-up
+        auto one = [&]() { return b->stream; };
+        class_launch(*b, c, one);  // warm-up
         cudaEventRecord(e0, b->stream);
-        for (int r = 0; r < reps; ++r) class_launch(*b, c, b->stream);
+        for (int r = 0; r < reps; ++r) class_launch(*b, c, one);
         cudaEventRecord(e1, b->stream);
         cudaError_t ce = cudaEventSynchronize(e1);
         if (ce != cudaSuccess) {
@@ -634,6 +669,12 @@ dpf_status dpf_batch_profile_read(dpf_batch* b, double* ms, int64_t* launches) {
 void dpf_batch_destroy(dpf_batch* b) {
   if (!b) return;
   if (b->stream || !b->ctx.empty()) cudaStreamSynchronize(b->stream);
+  for (cudaStream_t s : b->aux) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t e : b->join_ev) cudaEventDestroy(e);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   for (cudaEvent_t e : b->pev) cudaEventDestroy(e);
   for (dpf_ctx* x : b->ctx) dpf_destroy(x);
   for (void* p : b->allocs) cudaFree(p);
