@@ -363,8 +363,10 @@ def run(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "step_warp_kernel", "kernel_ms": kern_avg_s * 1e3,
                      "bytes_per_update": per, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        # e2e: y_t in (dy floats); out, the statistics and the error word (4 + d + 1
+        # doubles) that the outer stage writes to the context's pinned host mirror
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": spec.dy * 4,
-                "d2h_bytes_per_step": (4 + spec.d) * 8 + 4},
+                "d2h_bytes_per_step": (5 + spec.d) * 8},
         "lookahead_evaluations_per_s": value * L,  # the N M L look-ahead pairs of every step
         "gpu_launches": 2 * K,  # the step kernel and the outer stage, each step
         "clocks": clk,

@@ -245,6 +245,8 @@ static dpf_status dalloc(Ctx& x, P*& p, size_t bytes) {
 static void free_all(Ctx* x) {
   for (void* p : x->allocs) cudaFree(p);
   x->allocs.clear();
+  if (x->hstats) cudaFreeHost(x->hstats);
+  x->hstats = x->hstats_dev = nullptr;
   for (cudaEvent_t e : x->pev) cudaEventDestroy(e);
   x->pev.clear();
 }
@@ -376,6 +378,16 @@ dpf_status dpf_create(const dpf_model_desc* model, int32_t d1, int32_t d2, int64
     delete x;
     return set_error(DPF_E_NOMEM, "dpf_create: " + msg);
   }
+  // the host mirror of the statistics (pinned and mapped; without it dpf_step copies them)
+  if (cudaHostAlloc((void**)&x->hstats, sizeof(double) * (5 + d), cudaHostAllocMapped) == cudaSuccess) {
+    if (cudaHostGetDevicePointer((void**)&x->hstats_dev, x->hstats, 0) != cudaSuccess) {
+      cudaFreeHost(x->hstats);
+      x->hstats = x->hstats_dev = nullptr;
+    }
+  } else {
+    x->hstats = nullptr;
+  }
+  cudaGetLastError();  // a failed pinned allocation only disables the mirror
   cudaStream_t sr = x->stream;
   cudaMemsetAsync(x->stats, 0, ssz, sr);
   cudaMemcpyAsync((int*)(x->stats + 4 + d), x->perm.data(), sizeof(int) * d, cudaMemcpyHostToDevice, sr);
@@ -511,9 +523,23 @@ dpf_status dpf_step(dpf_ctx* x, const void* y_t, int32_t y_on_device, double* ou
                                   y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   x->stream);
   if (e != cudaSuccess) return cuda_error(e, "dpf_step: y copy");
+  const bool outs = out_mean || out_logZ;
+  x->host_out = outs && x->hstats;
   dpf_status st = step_enqueue(x, nullptr, nullptr);
+  const bool mirrored = x->host_out;
+  x->host_out = false;
   if (st) return st;
-  if (!out_mean && !out_logZ) return DPF_OK;
+  if (!outs) return DPF_OK;
+  if (mirrored) {  // the outer stage wrote the statistics and the error word to the mirror
+    e = cudaStreamSynchronize(x->stream);
+    if (e != cudaSuccess) return cuda_error(e, "dpf_step");
+    const volatile double* hs = x->hstats;
+    if (hs[4 + x->d] != 0.0) return read_err(*x, "dpf_step");  // reads and clears the word
+    if (out_mean)
+      for (int c = 0; c < x->d; ++c) out_mean[c] = hs[4 + c];
+    if (out_logZ) *out_logZ = hs[0];
+    return DPF_OK;
+  }
   std::vector<double> h(4 + x->d);
   e = cudaMemcpyAsync(h.data(), x->stats, sizeof(double) * (4 + x->d), cudaMemcpyDeviceToHost,
                       x->stream);

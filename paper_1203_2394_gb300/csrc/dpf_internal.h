@@ -174,6 +174,12 @@ struct dpf_ctx {
   // small device block: reduction partials, statistics, counters, error word
   void* small = nullptr;
   double* stats = nullptr;          // [logZ_total, logZ_step, ess, s1, mean[d]]
+  // pinned, mapped host mirror of the statistics and the error word (4 + d + 1 doubles),
+  // written by the outer stage of a dpf_step call with host outputs, so that the call
+  // reads them after one synchronisation instead of two device-to-host copies
+  double* hstats = nullptr;
+  double* hstats_dev = nullptr;     // ... its device address
+  bool host_out = false;            // the coming outer stage writes the mirror
   double* diag_inner = nullptr;     // [sum of the groups' inner ESS, their minimum (as bits)]
   void* lwmax_t = nullptr;          // the largest log-weight of the step, as T
   unsigned long long* lwmax_key = nullptr;

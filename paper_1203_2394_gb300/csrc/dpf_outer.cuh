@@ -47,6 +47,7 @@ struct FusedOuterArgs {
   Key key;                      // u = rand_word(key, t, 0, P_OUTER, 0)
   uint32_t t;
   int withhold;                 // a CTA that never arrives (a check of the bounded wait); -1: none
+  double* host_stats;           // a pinned host mirror of stats[0 .. 4 + d) and the error word, or null
 };
 
 template <typename T>
@@ -268,6 +269,11 @@ __device__ __forceinline__ void outer_stats(const FusedOuterArgs<T>& a, int nb, 
     if (o.logz_out) *o.logz_out = o.stats[0];
     *o.lwmax_t = lwmax;
     *o.Csum = C;
+  }
+  if (a.host_stats) {  // the mirror: the statistics as written above, then the error word
+    __syncthreads();
+    for (int q = tid; q < 4 + D; q += OF_NT) a.host_stats[q] = o.stats[q];
+    if (tid == 0) a.host_stats[4 + D] = (double)*(volatile int*)o.err;
   }
 }
 

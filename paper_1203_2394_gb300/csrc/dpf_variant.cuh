@@ -46,6 +46,7 @@ void fill_outer_args(Ctx& x, double* mean_out, double* logz_out, unsigned int* a
     a.key = Key{(uint32_t)x.seed, (uint32_t)(x.seed >> 32)};
     a.t = (uint32_t)(x.t + 1);
     a.withhold = -1;
+    a.host_stats = x.host_out ? x.hstats_dev : nullptr;
   }
 
 template <typename T, int D1, int D2>
