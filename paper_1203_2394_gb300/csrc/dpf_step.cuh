@@ -1217,12 +1217,18 @@ __device__ __forceinline__ void step_body(const MC<T, D1, D2, DY>& mc, const Ste
       const T lwi = mx + log_t(ps) - log_t((T)L);
       if (lane < L) coef[lane] = p0 / ps / rowS[lane];
       if (lane + 32 < L) coef[lane + 32] = p1 / ps / rowS[lane + 32];
+      // the x part of the filtered mean: every reduction first, then the stores (a store
+      // through a generic pointer between them held up the next reduction's loads)
+      T xmv[D1];
 #pragma unroll
       for (int c = 0; c < D1; ++c) {
         T v = (lane < L ? p0 * xbs[lane * D1 + c] : T(0)) +
               (lane + 32 < L ? p1 * xbs[(lane + 32) * D1 + c] : T(0));
-        v = warp_sum(v) / ps;
-        if (lane == 0) a.xm[(long long)c * N + i] = v;
+        xmv[c] = warp_sum(v) / ps;
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < D1; ++c) a.xm[(long long)c * N + i] = xmv[c];
       }
       if (lane == 0) {
         a.lw[i] = lwi;
