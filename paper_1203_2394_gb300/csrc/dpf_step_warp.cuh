@@ -272,6 +272,45 @@ __device__ __forceinline__ T tree_sum(const T (&x)[P]) {
     return tree_sum<T, P / 2>(h);
   }
 }
+// Largest of P values as a pairwise tree, P a power of two.
+template <typename T, int P>
+__device__ __forceinline__ T tree_max(const T (&x)[P]) {
+  if constexpr (P == 1) {
+    return x[0];
+  } else {
+    T h[P / 2];
+#pragma unroll
+    for (int p = 0; p < P / 2; ++p) h[p] = fmax(x[p], x[P / 2 + p]);
+    return tree_max<T, P / 2>(h);
+  }
+}
+// Reduce each row m < L of the 32 lane partials part[m][0..31] (stride PART_STRIDE) to
+// out[m], by their maximum (MAXR) or sum: for L <= 16 lanes m and m + 16 each take half of
+// row m (vector loads) and combine by one shuffle, else lane m takes all of row m.
+template <typename T, bool MAXR>
+__device__ __forceinline__ void reduce_rows(const T* part, int L, int lane, T* out) {
+  if (L <= 16) {
+    const int m = lane & 15, h = lane >> 4;
+    T r = MAXR ? neg_inf<T>() : T(0);
+    if (m < L) {
+      T x[16];
+      vld<T, 16>(part + m * PART_STRIDE + 16 * h, x);
+      r = MAXR ? tree_max<T, 16>(x) : tree_sum<T, 16>(x);
+    }
+    const T o = __shfl_xor_sync(FULL, r, 16);
+    r = MAXR ? fmax(r, o) : r + o;
+    if (h == 0 && m < L) out[m] = r;
+  } else {
+    for (int m = lane; m < L; m += 32) {
+      T x[16];
+      vld<T, 16>(part + m * PART_STRIDE, x);
+      const T lo = MAXR ? tree_max<T, 16>(x) : tree_sum<T, 16>(x);
+      vld<T, 16>(part + m * PART_STRIDE + 16, x);
+      const T hi = MAXR ? tree_max<T, 16>(x) : tree_sum<T, 16>(x);
+      out[m] = MAXR ? fmax(lo, hi) : lo + hi;
+    }
+  }
+}
 
 // Issue the bulk copies of one group's source rows into a warp's stage (lane 0).
 template <typename T, int D1, int D2>
@@ -838,9 +877,42 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
       for (int m = lane; m < L; m += 32) bad |= rowS[m] < tiny;
       general = __any_sync(FULL, bad);
     }
-    if (general) {
-      // robust path (x transition depends on z, or a row underflowed): row maxima,
-      // row sums relative to them, then beta with the coefficients pi_m / S_m
+    if (general && !XZ) {
+      // robust path of a model whose x transition does not depend on z (a row
+      // underflowed): the alpha sums are then the same for every draw (SA0, whose largest
+      // term is 2^0), so only the rows of e need their maxima: row maxima, row sums
+      // relative to them, then beta with the coefficients pi_m / S_m
+      for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 4
+        for (int m = 0; m < L; ++m) {
+          const T hs = pass ? shS[m] : T(0);
+          T vl[PPL];
+#pragma unroll
+          for (int p = 0; p < PPL; ++p) vl[p] = ak[p];
+#pragma unroll
+          for (int q = 0; q < DY; ++q) sub_sq<T, PPL>(cw[m * DY + q], ngk[q], vl);
+          T ps = pass ? T(0) : NEG;
+          if (act) {
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) ps = pass ? ps + exp2_t(vl[p] - hs) : fmax(ps, vl[p]);
+          }
+          part[m * PART_STRIDE + lane] = ps;
+        }
+        __syncwarp();
+        if (pass == 0) {
+          reduce_rows<T, true>(part, L, lane, shS);
+        } else {
+          reduce_rows<T, false>(part, L, lane, rowS);
+          for (int m = lane; m < L; m += 32) {
+            rowA[m] = SA0;
+            shA[m] = T(0);
+          }
+        }
+        __syncwarp();
+      }
+    } else if (general) {
+      // robust path (x transition depends on z): row maxima, row sums relative to them,
+      // then beta with the coefficients pi_m / S_m
       for (int pass = 0; pass < 2; ++pass) {
         for (int m = 0; m < L; ++m) {
           const T ha = pass ? shA[m] : T(0), hs = pass ? shS[m] : T(0);
