@@ -877,15 +877,21 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
       for (int m = lane; m < L; m += 32) bad |= rowS[m] < tiny;
       general = __any_sync(FULL, bad);
     }
+    T gmax = T(0);  // the largest row maximum (robust path without x-z coupling; else 0)
     if (general && !XZ) {
       // robust path of a model whose x transition does not depend on z (a row
       // underflowed): the alpha sums are then the same for every draw (SA0, whose largest
-      // term is 2^0), so only the rows of e need their maxima: row maxima, row sums
-      // relative to them, then beta with the coefficients pi_m / S_m
+      // term is 2^0), so only the rows of e need their maxima. Pass 0 takes the row
+      // maxima h_m; pass 1 the row sums relative to them and, since pi_m / S_m is then
+      // proportional to 2^(h_m), beta_k up to normalisation as sum_m 2^(h_m - gmax) e'(m,k)
+      // (the same weights as the fast path's sum_m e(m,k), relative to the largest row)
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) B[p] = T(0);
       for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll 4
         for (int m = 0; m < L; ++m) {
           const T hs = pass ? shS[m] : T(0);
+          const T wm = pass ? exp2_t(hs - gmax) : T(0);
           T vl[PPL];
 #pragma unroll
           for (int p = 0; p < PPL; ++p) vl[p] = ak[p];
@@ -894,13 +900,25 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
           T ps = pass ? T(0) : NEG;
           if (act) {
 #pragma unroll
-            for (int p = 0; p < PPL; ++p) ps = pass ? ps + exp2_t(vl[p] - hs) : fmax(ps, vl[p]);
+            for (int p = 0; p < PPL; ++p) {
+              if (pass) {
+                const T e = exp2_t(vl[p] - hs);
+                ps += e;
+                B[p] = fma(wm, e, B[p]);
+              } else {
+                ps = fmax(ps, vl[p]);
+              }
+            }
           }
           part[m * PART_STRIDE + lane] = ps;
         }
         __syncwarp();
         if (pass == 0) {
           reduce_rows<T, true>(part, L, lane, shS);
+          __syncwarp();
+          T g = NEG;
+          for (int m = lane; m < L; m += 32) g = fmax(g, shS[m]);
+          gmax = warp_max(g);
         } else {
           reduce_rows<T, false>(part, L, lane, rowS);
           for (int m = lane; m < L; m += 32) {
@@ -1001,7 +1019,7 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         atomicMax(a.lwmax_key, key);
     }
     // ---- z part of the filtered mean: beta_k = sum_m pi_m e(m,k) / S_m ----
-    if (general) {
+    if (general && XZ) {
 #pragma unroll
       for (int p = 0; p < PPL; ++p) B[p] = T(0);
       if (lane < L) coef[lane] = p0 / psum / rowS[lane];
@@ -1022,8 +1040,10 @@ __device__ __forceinline__ void warp_run(const MC<T, D1, D2, DY>& mc, const Step
         for (int p = 0; p < PPL; ++p) B[p] += act ? cf * exp2_t(v[p] - hs) : T(0);
       }
     } else {
+      // normalise sum_m e(m,k) by sum_(m,k) e(m,k), both relative to the largest row
+      // (gmax = 0 and every shS = 0 on the fast path)
       T tot = T(0);
-      for (int m = lane; m < L; m += 32) tot += rowS[m];
+      for (int m = lane; m < L; m += 32) tot += general ? rowS[m] * exp2_t(shS[m] - gmax) : rowS[m];
       tot = warp_sum(tot);
       const T inv = T(1) / tot;
 #pragma unroll
