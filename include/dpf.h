@@ -399,8 +399,10 @@ void dpf_batch_destroy(dpf_batch* b);
  * an MLP of three hidden ReLU layers (width `hidden`) with a head of
  * components (1 + 2 d2) outputs: logits, the means (component-major), then the
  * raw log standard deviations, clamped to [-7, 5] where used. Weights are FP32
- * master copies; the forward pass uses bfloat16 weights and activations with
- * FP32 accumulation (dpf_proposal_set_bf16(p, 0) makes training plain FP32).
+ * master copies; every training product (forward and backward) runs on the tensor
+ * cores with FP32 accumulation, on bfloat16 weights and activations by default, or
+ * after dpf_proposal_set_bf16(p, 0) on FP32 operands as three TF32 products each
+ * (about FP32 accuracy).
  *
  * Parameters (dpf_proposal_get/set_weights, host float arrays of num_params):
  *   W1 (hidden x din), b1, W2 (hidden x hidden), b2, W3, b3, W4 (dout x hidden), b4,
