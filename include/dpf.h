@@ -279,6 +279,9 @@ dpf_status dpf_diag_inner(dpf_ctx* ctx, double* ess_min, double* ess_mean);
  * `which` names the array; `bytes` must equal its size exactly:
  *   "lw" (N), "lwhat" (N*L), "xbb" (N*L*d1, [n][m][c]), "anc" (N int32),
  *   "sel" (N int32), "wout" (N, the outer weights fed to the resampler),
+ *   "xm" (d1*N, [c][n]) and "zm" (d2*N, [c][n]): each outer particle's part of
+ *   the filtered mean of the last step before the outer weighting (the weighted
+ *   sum over its look-ahead draws), in the internal x-first coordinates,
  *   "x" (N*d1, [n][c]), "z" (d2*N*M, [c][n][j]), "lq" (N*M) - x/z/lq are the
  *   newest materialised state, which is that of step t-1 after step t (the
  *   inner update of step t runs at the start of step t+1), and "sel" holds the

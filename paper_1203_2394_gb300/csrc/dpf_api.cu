@@ -758,6 +758,8 @@ dpf_status dpf_read(dpf_ctx* x, const char* which, void* dst, size_t bytes) {
   else if (w == "anc") { src = x->anc; need = 4 * N; }
   else if (w == "sel") { src = x->sel; need = 4 * N; }
   else if (w == "wout") { src = x->wout; need = s * N; }
+  else if (w == "xm") { src = x->xm; need = s * N * x->d1; }
+  else if (w == "zm") { src = x->zm; need = s * N * x->d2; }
   else if (w == "x") {  // rows are padded to xp elements on the device; returned packed
     if (bytes != s * N * x->d1)
       return set_error(DPF_E_INVALID, "dpf_read: 'x' needs " + std::to_string(s * N * x->d1) + " bytes");

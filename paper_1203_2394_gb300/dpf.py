@@ -228,6 +228,7 @@ class Filter:
     _SHAPES = {
         "lw": lambda s: (s.N,), "lwhat": lambda s: (s.N, s.L), "xbb": lambda s: (s.N, s.L, s.d1),
         "anc": lambda s: (s.N,), "sel": lambda s: (s.N,), "wout": lambda s: (s.N,),
+        "xm": lambda s: (s.d1, s.N), "zm": lambda s: (s.d2, s.N),
         "x": lambda s: (s.N, s.d1), "z": lambda s: (s.d2, s.N, s.M), "lq": lambda s: (s.N, s.M),
         "bidx": lambda s: (s.N, s.M), "fallback": lambda s: (s.N,), "jla": lambda s: (s.N, s.L),
         "head": lambda s: (s.N, s.M, s.proposal.dout),

@@ -1,0 +1,47 @@
+"""The outer stage of a step (one cooperative launch: sums, a grid barrier, the scan and
+scatter of the global systematic resampling, the statistics) at sizes where every CTA
+walks several chunks of outer particles, and at a ragged small size.
+
+Checked per step against quantities computed here from the filter's own outputs:
+* the ancestors, bit for bit, against the oracle's integer global rule (oracle.sys_global)
+  on the weights W_i the stage fed to it and the step's uniform word;
+* W_i = exp(lw_i - max lw) to FP32 rounding;
+* the evidence increment, the ESS and the filtered mean (returned by the step) against
+  double-precision sums of the same W_i and per-particle mean parts.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1203_2394_gb300 import workloads
+from tests.gpu_util import word
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("N", [1_048_576 + 37, 3001])
+def test_outer_stage_many_chunks_per_cta(N):
+    from paper_1203_2394_gb300 import dpf
+    spec = workloads.make_model("lg4", 0)
+    M, L, seed, T = 32, 4, 11, 3
+    _, ys = workloads.simulate(spec, T, 3)
+    f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), spec.d1, spec.d2, N, M, L, seed)
+    for t in range(1, T + 1):
+        mean, _ = f.step(ys[t - 1].astype(np.float32))
+        lw = f.read("lw").astype(np.float64)
+        wout = f.read("wout").astype(np.float64)
+        np.testing.assert_array_equal(f.read("anc"), oracle.sys_global(wout, word(seed, t, 0, oracle.P_OUTER)))
+        # W = exp(lw - max) in FP32: the difference rounds to half an ulp of itself, the
+        # exponential to about an ulp
+        ref = np.exp(lw - lw.max())
+        assert np.all(np.abs(wout - ref) <= (np.abs(lw - lw.max()) * 2.0 ** -23 + 2.0 ** -21) * ref + 1e-38)
+        parts = np.concatenate([f.read("xm"), f.read("zm")]).astype(np.float64)  # (d, N), x first
+        s1, s2 = wout.sum(), (wout ** 2).sum()
+        mean_ref = parts @ wout / s1  # internal order; the model's permutation is the identity
+        # FP32 partial sums (a few terms a thread, then warp and block trees) combined in double
+        np.testing.assert_allclose(mean, mean_ref, rtol=1e-5, atol=1e-5 * np.abs(parts).max())
+        d = f.diag()
+        assert d["ess"] == pytest.approx(s1 * s1 / s2, rel=1e-5)
+        assert d["logZ_step"] == pytest.approx(lw.max() + np.log(s1) - np.log(N), rel=0, abs=1e-5)
+    f.close()
