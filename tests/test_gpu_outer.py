@@ -45,3 +45,30 @@ def test_outer_stage_many_chunks_per_cta(N):
         assert d["ess"] == pytest.approx(s1 * s1 / s2, rel=1e-5)
         assert d["logZ_step"] == pytest.approx(lw.max() + np.log(s1) - np.log(N), rel=0, abs=1e-5)
     f.close()
+
+
+def test_batched_outer_stage_equals_single_filters():
+    """The batched form runs the same stage in two launches (sums, then prefix, scatter and
+    statistics) over each member's own CTAs with the single launch's partition: at the
+    same sizes its members' ancestors, weights and means equal the single filters' bit
+    for bit."""
+    from paper_1203_2394_gb300 import dpf
+    spec = workloads.make_model("lg4", 0)
+    m = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    Ns, M, L, seeds, T = [1_048_576 + 37, 3001], 32, 4, [21, 22], 3
+    ys = np.stack([workloads.simulate(spec, T, 7 + f)[1] for f in range(2)], axis=1).astype(np.float32)
+    b = dpf.Batch([m, m], [spec.d1] * 2, Ns, [M] * 2, L, seeds)
+    singles = [dpf.Filter(m, spec.d1, spec.d2, N, M, L, s) for N, s in zip(Ns, seeds)]
+    yd = torch.tensor(ys, device="cuda")
+    means = torch.zeros((2, spec.d), dtype=torch.float64, device="cuda")
+    for t in range(T):
+        b.step_device(yd[t].data_ptr(), means.data_ptr())
+        b.sync()
+        for f, s in enumerate(singles):
+            ms, _ = s.step(ys[t, f])
+            for name in ("anc", "lw", "wout"):
+                np.testing.assert_array_equal(b.filter(f).read(name), s.read(name), err_msg=f"{name} f={f} t={t}")
+            np.testing.assert_array_equal(means[f].cpu().numpy(), ms)
+    for s in singles:
+        s.close()
+    b.close()
