@@ -344,8 +344,9 @@ void dpf_destroy(dpf_ctx* ctx);
  * single filter created with that seed). The filters of one compiled
  * (precision, d1, d2, dy) variant and inner-particles-per-lane class share one
  * persistent launch of the step kernel (or one launch each, where
- * dpf_batch_autotune finds that faster); the outer stages of the filters run
- * concurrently. Each M must be at most 256 with M, L and L*d1 rows of whole
+ * dpf_batch_autotune finds that faster; always one each, on the batch's stream, for
+ * the (8, 56, 8) variant, whose step reads its model from a shared constant
+ * bank); the outer stages of the filters run concurrently. Each M must be at most 256 with M, L and L*d1 rows of whole
  * 16-byte units. models, d1, N, M, seeds: host arrays of F entries.
  */
 typedef struct dpf_batch dpf_batch;

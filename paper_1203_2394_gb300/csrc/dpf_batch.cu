@@ -99,8 +99,13 @@ static dpf_status balloc(dpf_batch& b, void** p, size_t bytes) {
   return DPF_OK;
 }
 
-// Grid and chunking of one class at its current PPL.
+// Grid and chunking of one class at its current PPL (nothing to shape for a variant
+// without a launch for a whole class, whose members always launch one by one).
 static dpf_status shape_class(dpf_batch& b, BatchClass& c) {
+  if (!c.var->batch_launch) {
+    c.split = true;
+    return DPF_OK;
+  }
   size_t region = 0;
   for (int f : c.members) region = std::max(region, c.var->region_bytes(b.ctx[f]->M, b.ctx[f]->L, c.xz));
   c.launch.region = (uint32_t)region;
@@ -226,8 +231,9 @@ static dpf_status step_launch(dpf_batch& b) {
   }
   int k = 0;
   auto next = [&]() { const int q = k++ % S; return q == 0 ? b.stream : b.aux[q - 1]; };
+  auto own = [&]() { return b.stream; };
   for (BatchClass& c : b.cls) {
-    dpf_status st = class_launch(b, c, next);
+    dpf_status st = c.var->batch_serial ? class_launch(b, c, own) : class_launch(b, c, next);
     if (st) return st;
   }
   for (size_t q = 0; q < b.aux.size(); ++q) {
@@ -296,7 +302,7 @@ dpf_status dpf_batch_create(const dpf_model_desc* const* models, const int32_t* 
     dpf_status st = dpf_create(models[f], d1[f], models[f]->d - d1[f], N[f], M[f], L, seeds[f], stream, &x);
     if (st) return fail(st);
     b->ctx.push_back(x);
-    if (!x->var->batch_launch)
+    if (!x->var->batch_launch && !x->var->single_launch)
       return fail(set_error(DPF_E_UNSUPPORTED, "dpf_batch_create: this (d1, d2, dy) variant has no batched form"));
     const size_t sz = b->s;
     const int ppl = x->var->ppl_for(M[f]);
@@ -562,7 +568,7 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
     int maxM = 0;
     for (int f : c.members) maxM = std::max(maxM, b->ctx[f]->M);
     std::vector<int> cand = {c.var->ppl_for(maxM)};
-    if (cand[0] * 2 <= 8) {
+    if (cand[0] * 2 <= 8 && c.var->batch_launch) {
       bool ok = true;
       for (int f : c.members) ok &= (b->ctx[f]->M % (cand[0] * 2) == 0);
       if (ok) cand.push_back(cand[0] * 2);
@@ -572,7 +578,8 @@ dpf_status dpf_batch_autotune(dpf_batch* b, int32_t reps, char* report, size_t r
     double best_us = 1e300;
     std::string tried;
     for (int ppl : cand) {
-      for (int split = 0; split < (c.members.size() > 1 ? 2 : 1) && !st; ++split) {
+      const int split0 = c.var->batch_launch ? 0 : 1;  // no shared launch to try for the class
+      for (int split = split0; split < (c.var->batch_launch && c.members.size() > 1 ? 2 : 1) + split0 && !st; ++split) {
         c.ppl = ppl;
         c.split = split != 0;
         st = shape_class(*b, c);
@@ -631,7 +638,7 @@ dpf_status dpf_batch_set_split(dpf_batch* b, int32_t split) {
   if (!b) return set_error(DPF_E_INVALID, "dpf_batch_set_split: null batch");
   cudaError_t e = cudaStreamSynchronize(b->stream);  // no launch in flight reads the shapes
   if (e != cudaSuccess) return cuda_error(e, "dpf_batch_set_split");
-  for (BatchClass& c : b->cls) c.split = split != 0 && c.members.size() > 1;
+  for (BatchClass& c : b->cls) c.split = !c.var->batch_launch || (split != 0 && c.members.size() > 1);
   return DPF_OK;
 }
 

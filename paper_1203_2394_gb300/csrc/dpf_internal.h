@@ -122,6 +122,7 @@ struct Variant {
   dpf_status (*batch_launch)(const BatchLaunch&, cudaStream_t, int* occ);
   // a batched member's step as its own launch of the single-filter kernel
   dpf_status (*single_launch)(Ctx&, const void* args, int ppl, bool xz, cudaStream_t s) = nullptr;
+  bool batch_serial = false;  // its launches share state (a constant bank): one stream
   bool (*use_xz)(const Ctx&);
   int (*ppl_for)(int M);
   size_t args_size, const_size, oargs_size;

@@ -2,5 +2,5 @@
 #include "dpf_wide_launch.cuh"
 
 namespace dpf {
-template dpf_status wide_launch<float, 8, 56, 8, false>(Ctx&, StepArgs<float>&);
+template dpf_status wide_launch<float, 8, 56, 8, false>(Ctx&, StepArgs<float>&, cudaStream_t);
 }  // namespace dpf

@@ -13,7 +13,7 @@ namespace dpf {
 // the tensor-core propagation; each is instantiated in a translation unit of its
 // own (dpf_wide_launch.cuh), so that the two large kernels compile in parallel.
 template <typename T, int D1, int D2, int DY, bool TC>
-dpf_status wide_launch(Ctx& x, StepArgs<T>& a);
+dpf_status wide_launch(Ctx& x, StepArgs<T>& a, cudaStream_t s);
 
 template <typename T, int D1, int D2, int DY>
 struct WideVariantImpl {
@@ -49,11 +49,30 @@ struct WideVariantImpl {
     return cuda_error(cudaGetLastError(), "init kernel launch");
   }
 
+  static dpf_status launch(Ctx& x, StepArgs<T>& a, cudaStream_t s) {
+    return x.tensor_cores && tc_shape(x.M) ? wide_launch<T, D1, D2, DY, true>(x, a, s)
+                                           : wide_launch<T, D1, D2, DY, false>(x, a, s);
+  }
+
   static dpf_status step(Ctx& x, int) {
     StepArgs<T> a{};
     Base::fill_args(x, a);
-    return x.tensor_cores && tc_shape(x.M) ? wide_launch<T, D1, D2, DY, true>(x, a)
-                                           : wide_launch<T, D1, D2, DY, false>(x, a);
+    return launch(x, a, x.stream);
+  }
+
+  // A batched member's step (its own launch, on the batch's stream s) from the
+  // arguments batch_args filled with the batch's observation rows.
+  static void batch_args(Ctx& x, const void* y_prev, const void* y_cur, bool, void* out) {
+    StepArgs<T> a{};
+    Base::fill_args(x, a);
+    a.y_prev = (const T*)y_prev;
+    a.y_cur = (const T*)y_cur;
+    memcpy(out, &a, sizeof(a));
+  }
+  static dpf_status single_launch(Ctx& x, const void* args, int, bool, cudaStream_t s) {
+    StepArgs<T> a;
+    memcpy(&a, args, sizeof(a));
+    return launch(x, a, s);
   }
 
   static Variant make(int prec) {
@@ -72,7 +91,11 @@ struct WideVariantImpl {
     v.outer_batch = &Base::outer_batch;
     v.scan_batch = &Base::scan_batch;
     v.step_smem = &smem;
-    v.batch_args = nullptr;  // no batched form
+    // batched: one launch a filter (no shared launch for a class), all on the batch's
+    // stream, since the launches share the translation unit's constant bank
+    v.batch_args = &batch_args;
+    v.single_launch = &single_launch;
+    v.batch_serial = true;
     v.region_bytes = nullptr;
     v.batch_launch = nullptr;
     v.use_xz = &Base::use_xz;

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256)
 }
 
 template <typename T, int D1, int D2, int DY, bool TC>
-dpf_status wide_launch(Ctx& x, StepArgs<T>& a) {
+dpf_status wide_launch(Ctx& x, StepArgs<T>& a, cudaStream_t s) {
   static_assert(sizeof(T) == 4 && D1 == 8 && D2 == 56 && DY == 8, "the compiled wide variant");
   constexpr int MAX_M = WideVariantImpl<T, D1, D2, DY>::MAX_M;
   static_assert(MAX_M == 256, "launch bounds of step_kernel_wide");
@@ -42,10 +42,10 @@ dpf_status wide_launch(Ctx& x, StepArgs<T>& a) {
     x.grid_step = (nb > 0 ? nb : 1) * nsm;
   }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_wide_mc, x.d_mconst, sizeof(MC<float, 8, 56, 8>), 0,
-                                          cudaMemcpyDeviceToDevice, x.stream);
+                                          cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_error(e, "model constants to the constant bank");
   const long long grid = std::min<long long>(x.N, x.grid_step);
-  k<<<(unsigned)grid, nt, sm, x.stream>>>(a);
+  k<<<(unsigned)grid, nt, sm, s>>>(a);
   return cuda_error(cudaGetLastError(), "step kernel launch");
 }
 

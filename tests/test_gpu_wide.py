@@ -129,6 +129,30 @@ def test_wide_limits_refused():
     with pytest.raises(dpf.DpfError) as e:
         dpf.Filter(m, 8, 56, 16, 512, 8)  # one inner particle a thread: M <= 256
     assert e.value.status == dpf.DPF_E_UNSUPPORTED
-    with pytest.raises(dpf.DpfError) as e:
-        dpf.Batch([m], [8], [64], [128], 8, [0])  # no batched form
-    assert e.value.status == dpf.DPF_E_UNSUPPORTED
+
+
+def test_wide_batch_equals_single_filters():
+    """Filters of the wide variant in one batch (each its own launch of the wide step,
+    with its own model, on the batch's stream; the outer stages batched): every member
+    equals, bit for bit, the single filter with its seed, stepped and in a graph."""
+    from paper_1203_2394_gb300 import dpf
+    specs = [workloads.make_model("growth_clg64", s) for s in (0, 1)]
+    models = [dpf.Model.from_spec(sp, dpf.DPF_F32) for sp in specs]
+    Ns, Ms, L, seeds, T = [300, 157], [256, 128], 16, [31, 32], 4
+    ys = np.stack([workloads.simulate(sp, T, 9 + f)[1] for f, sp in enumerate(specs)], axis=1).astype(np.float32)
+    yd = torch.tensor(ys, device="cuda")
+    b = dpf.Batch(models, [8, 8], Ns, Ms, L, seeds)
+    singles = [dpf.Filter(models[f], 8, 56, Ns[f], Ms[f], L, seeds[f]) for f in range(2)]
+    means = torch.zeros((T, 2, 64), dtype=torch.float64, device="cuda")
+    for t in range(T // 2):
+        b.step_device(yd[t].data_ptr(), means[t].data_ptr())
+    b.run_device(yd[T // 2:].data_ptr(), T - T // 2, means[T // 2:].data_ptr(), graph=True)
+    for t in range(T):
+        for f, s in enumerate(singles):
+            ms, _ = s.step(ys[t, f])
+            np.testing.assert_array_equal(means[t, f].cpu().numpy(), ms, err_msg=f"mean f={f} t={t}")
+    for f, s in enumerate(singles):
+        for name in ("anc", "lw", "lwhat", "x", "z", "lq"):
+            np.testing.assert_array_equal(b.filter(f).read(name), s.read(name), err_msg=f"{name} f={f}")
+        s.close()
+    b.close()
