@@ -385,13 +385,13 @@ def run(args):
 def secondary_legs():
     """Short runs of the other configurations, reported beside the headline (one GPU):
     the 512-filter batched workload (10 graph-captured steps), the learned proposals at
-    N = 262144, M = 64 (10 steps each form, with RMSE and inner ESS), and one filter of
-    the high-dimensional workload (10 steps). Each carries its own roofline and clocks."""
+    N = 262144, M = 64 (10 steps each form, with RMSE and inner ESS), and four filters of
+    the high-dimensional workload as one batch (10 graph-captured steps). Each carries its own roofline and clocks."""
     import torch
     out = {}
     legs = [("batched", run_batched, dict(filters=512, steps=10, warmup=3)),
             ("learned", run_learned, dict(steps=10, warmup=3)),
-            ("highdim", run_highdim, dict(filters=1, steps=10, warmup=3))]
+            ("highdim", run_highdim, dict(filters=4, steps=10, warmup=3))]
     for name, fn, kw in legs:
         t0 = time.perf_counter()
         try:
@@ -536,8 +536,10 @@ def run_batched(args):
 def run_highdim(args):
     """The high-dimensional workload: growth_clg64 (x of dim 8 with the growth map, z of
     dim 56 with a dense A_zz, dy = 8), F filters of N = 32768, M = 256, L = 16, FP32,
-    every filter's state resident; a step steps all F filters one after another on one
-    stream. Then the tensor-core propagation against the CUDA-core one on one filter."""
+    every filter's state resident, stepped as one batch (each filter's own tensor-core step
+    launch on the batch's stream, the outer stages of all filters in two launches), the
+    timed steps one captured graph. Then the tensor-core propagation against the CUDA-core
+    one on one member stepped alone."""
     import numpy as np
     import torch
 
@@ -558,62 +560,48 @@ def run_highdim(args):
         F = F2
     stream = torch.cuda.Stream()
     model = dpf.Model.from_spec(spec, dpf.DPF_F32)
-    filt = [dpf.Filter(model, spec.d1, spec.d2, N, M, L, seed=f, stream=stream) for f in range(F)]
+    b = dpf.Batch([model] * F, [spec.d1] * F, [N] * F, [M] * F, L, list(range(F)), stream=stream)
     ys = np.stack([workloads.simulate(spec, W + K + 1, 5 + f)[1] for f in range(F)], axis=1)
     yd = torch.tensor(ys.astype(np.float32), device="cuda")  # (T, F, dy)
-    with torch.cuda.stream(stream):
-        for k in range(W):
-            for f in range(F):
-                filt[f].step_device(yd[k, f].data_ptr())
-        for fl in filt:
-            fl.sync()
-            fl.profile(True)
-            fl.profile_read()
-        torch.cuda.synchronize()
-        clocks = ClockSampler(0)
-        clocks.start()
-        time.sleep(0.3)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        w0 = time.monotonic()
-        e0.record(stream)
-        for k in range(W, W + K):
-            for f in range(F):
-                filt[f].step_device(yd[k, f].data_ptr())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        w1 = time.monotonic()
-        ms = e0.elapsed_time(e1)
-        kms, kn = 0.0, 0
-        for fl in filt:
-            fl.sync()
-            a, b = fl.profile_read()
-            fl.profile(False)
-            kms, kn = kms + a, kn + b
-        clk = clocks.stop(window=(w0, w1))
+    b.run_device(yd.data_ptr(), W, graph=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.monotonic()
+    e0.record(stream)
+    b.run_device(yd[W:].data_ptr(), K, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.monotonic()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop(window=(w0, w1))
     value = F * N * M * K / (ms / 1e3)
-    # tensor cores against CUDA cores on filter 0 (same state, next steps)
+    # the step kernel alone, and the tensor cores against the CUDA cores, on member 0
+    # stepped on its own after the batched run (same state, next steps)
     cmp = {}
+    f0 = b.filter(0)
+    y0 = yd[W + K - 1, 0]
     with torch.cuda.stream(stream):
         for tc in (True, False):
-            f0 = filt[0]
             f0.set_tensor_cores(tc)
-            f0.step_device(yd[W + K - 1, 0].data_ptr())  # settle the launch shape
+            f0.step_device(y0.data_ptr())  # settle the launch shape
             f0.sync()
             f0.profile(True)
             f0.profile_read()
             for r in range(3):
-                f0.step_device(yd[W + K - 1, 0].data_ptr())
+                f0.step_device(y0.data_ptr())
             f0.sync()
-            a, b = f0.profile_read()
+            a, n = f0.profile_read()
             f0.profile(False)
-            cmp["tensor_cores" if tc else "cuda_cores"] = a / max(1, b)
-        filt[0].set_tensor_cores(True)
-    for fl in filt:
-        fl.close()
+            cmp["tensor_cores" if tc else "cuda_cores"] = a / max(1, n)
+        f0.set_tensor_cores(True)
+    b.close()
     peak, peak_kind = measured_peaks()
     per = b_alg(spec.d1, spec.d2, M, 4)
-    kern_s = kms / 1e3 / max(1, kn)
+    kern_s = cmp["tensor_cores"] / 1e3  # the step kernel, CUDA events around each launch
     achieved = per * N * M / kern_s / 1e9
     mma_flop = 3 * 2 * N * M * 64 * spec.d2  # 3xTF32, A_zz padded to 64 rows
     line = {
@@ -621,7 +609,7 @@ def run_highdim(args):
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"growth_clg64: growth-map x (d1=8), linear-Gaussian z (d2=56, dense A_zz), "
-                               f"dy=8, {F} filters of N={N}, M={M}, L={L}, FP32",
+                               f"dy=8, {F} filters of N={N}, M={M}, L={L}, FP32, one batch, one graph per run",
                    "filters": F, "share_of_64": F / 64 if share == 1.0 else share,
                    "l2": "state far larger than L2; no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -630,7 +618,8 @@ def run_highdim(args):
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "tensor": {"mma_tflops": mma_flop / kern_s / 1e12, "mma_flop_per_launch": mma_flop},
         "propagation_kernel_ms": cmp,
-        "gpu_launches": 2 * K * F,  # the step kernel and the outer stage, each filter step
+        # each step: a step launch a filter, the outer-sums and the resampling launches
+        "gpu_launches": K * (F + 2),
         "clocks": clk,
     }
     return line

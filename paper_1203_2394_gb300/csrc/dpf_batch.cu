@@ -213,7 +213,12 @@ static void outer_host_sets(dpf_batch& b, size_t nsets, std::vector<std::vector<
 
 // One batched step whose descriptors are already in place.
 static dpf_status step_launch(dpf_batch& b) {
-  if (b.profiling) {
+  // the profiling events time live launches only: an event recorded while a stream is
+  // being captured into a graph becomes a dependency, not a timestamp
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(b.stream, &cs);
+  const bool prof = b.profiling && cs == cudaStreamCaptureStatusNone;
+  if (prof) {
     if (b.pev_used + 2 > b.pev.size())
       for (int q = 0; q < 64; ++q) {
         cudaEvent_t e;
@@ -240,7 +245,7 @@ static dpf_status step_launch(dpf_batch& b) {
     cudaEventRecord(b.join_ev[q], b.aux[q]);
     cudaStreamWaitEvent(b.stream, b.join_ev[q], 0);
   }
-  if (b.profiling) {
+  if (prof) {
     cudaEventRecord(b.pev[b.pev_used + 1], b.stream);
     b.pev_used += 2;
   }
@@ -664,8 +669,10 @@ dpf_status dpf_batch_profile_read(dpf_batch* b, double* ms, int64_t* launches) {
   double tot = 0.0;
   for (size_t q = 0; q + 1 < b->pev_used; q += 2) {
     float f = 0.f;
-    cudaEventElapsedTime(&f, b->pev[q], b->pev[q + 1]);
-    tot += f;
+    if (cudaEventElapsedTime(&f, b->pev[q], b->pev[q + 1]) == cudaSuccess)
+      tot += f;
+    else
+      cudaGetLastError();  // a pair that holds no time leaves no error behind
   }
   if (ms) *ms = tot;
   if (launches) *launches = (int64_t)(b->pev_used / 2);
