@@ -122,7 +122,7 @@ static void launch_global(const T* w, long long n, const uint32_t* u, int32_t* o
   a.err = sc.err;
   a.withhold = withhold;
   const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-  global_scan_scatter<T, false><<<(unsigned)tiles, SCAN_NT, 0, s>>>(a);
+  global_scan_scatter<T><<<(unsigned)tiles, SCAN_NT, 0, s>>>(a);
 }
 
 // Launch the global-rule pipeline on scratch the caller has laid out (and zeroed).

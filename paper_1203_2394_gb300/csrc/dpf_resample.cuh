@@ -36,16 +36,13 @@ __device__ __forceinline__ long long points_below(unsigned long long c, long lon
   return k >= n ? n : k;
 }
 
-// Inputs of the scan-and-scatter pass. With from_log the weights are
-// W_i = exp(lw_i - lwmax) (so max W = 1 exactly and e = 0); otherwise they are
-// read directly and e = floor(log2 max W) is given.
+// Inputs of the scan-and-scatter pass: the weights W_i, with e = floor(log2 max W)
+// given through the shift S - e.
 template <typename T>
 struct GlobalArgs {
-  const T* w;              // n weights, or log-weights when from_log
-  const T* lwmax;          // device scalar (from_log)
-  T* w_out;                // from_log: the W fed to the rule (may be null)
+  const T* w;              // n weights
   long long n;
-  int shift;               // S - e (from_log: S, since e = 0)
+  int shift;               // S - e
   const int* shift_dev;    // if non-null, read S - e from here instead
   const unsigned long long* C;  // device scalar: the quantised total
   const uint32_t* u_ptr;   // device scalar uniform word, or null
@@ -75,7 +72,7 @@ __device__ __forceinline__ unsigned long long quantize_u64(double W, int shift) 
 }
 
 // One tile of the `ntiles` tiles of one resampling, the tile taken by ticket.
-template <typename T, bool FROM_LOG>
+template <typename T>
 __device__ __forceinline__ void global_scan_scatter_body(const GlobalArgs<T>& a, long long ntiles) {
   __shared__ unsigned long long cum[SCAN_TILE];
   __shared__ unsigned long long wsum[SCAN_NT / 32];
@@ -96,8 +93,6 @@ __device__ __forceinline__ void global_scan_scatter_body(const GlobalArgs<T>& a,
   const unsigned long long C = *a.C;
   const int shift = a.shift_dev ? *a.shift_dev : a.shift;
   const uint32_t u = a.u_ptr ? *a.u_ptr : rand_word(a.key, a.t, 0, P_OUTER, 0);
-  T lwmax = T(0);
-  if (FROM_LOG) lwmax = *a.lwmax;
 
   // quantise this thread's items (blocked arrangement) and sum them
   unsigned long long c[SCAN_IPT];
@@ -107,12 +102,7 @@ __device__ __forceinline__ void global_scan_scatter_body(const GlobalArgs<T>& a,
     const long long i = base + (long long)tid * SCAN_IPT + q;
     unsigned long long ci = 0;
     if (i < a.n) {
-      T W = a.w[i];
-      if (FROM_LOG) {
-        W = exp_t<T>(W - lwmax);
-        if (a.w_out) a.w_out[i] = W;
-      }
-      ci = quantize_u64(W, shift);
+      ci = quantize_u64(a.w[i], shift);
     }
     c[q] = ci;
     tsum += ci;
@@ -223,9 +213,9 @@ __device__ __forceinline__ void global_scan_scatter_body(const GlobalArgs<T>& a,
   }
 }
 
-template <typename T, bool FROM_LOG>
+template <typename T>
 __global__ void __launch_bounds__(SCAN_NT) global_scan_scatter(GlobalArgs<T> a) {
-  global_scan_scatter_body<T, FROM_LOG>(a, gridDim.x);
+  global_scan_scatter_body<T>(a, gridDim.x);
 }
 
 }  // namespace dpf
