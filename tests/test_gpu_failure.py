@@ -64,3 +64,34 @@ def test_allocation_failure_returns_nomem_and_frees_everything():
     assert np.all(np.isfinite(mean))
     f.close()
     assert _free_bytes() == before
+
+
+def test_step_with_a_nan_observation_reports_numeric():
+    """A NaN observation makes every look-ahead weight NaN: the step kernel and the outer
+    stage flag it (no resampling is applied), dpf_step returns DPF_E_NUMERIC through the
+    statistics mirror, the asynchronous step reports it at dpf_sync, and a new filter on
+    the same device works normally."""
+    from paper_1203_2394_gb300 import dpf, workloads
+    spec = workloads.make_model("growth_clg10", 0)
+    m = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    _, ys = workloads.simulate(spec, 3, 0)
+    bad = np.full(spec.dy, np.nan, dtype=np.float32)
+    f = dpf.Filter(m, 2, 8, 256, 128, 16, 1)
+    f.step(ys[0].astype(np.float32))
+    with pytest.raises(dpf.DpfError) as e:
+        f.step(bad)
+    assert e.value.status == dpf.DPF_E_NUMERIC
+    f.close()
+    g = dpf.Filter(m, 2, 8, 256, 128, 16, 2)
+    g.step(ys[0].astype(np.float32))
+    yd = torch.tensor(bad, device="cuda")
+    g.step_device(yd.data_ptr())
+    with pytest.raises(dpf.DpfError) as e:
+        g.sync()
+    assert e.value.status == dpf.DPF_E_NUMERIC
+    g.close()
+    h = dpf.Filter(m, 2, 8, 256, 128, 16, 3)
+    for t in range(3):
+        mean, _ = h.step(ys[t].astype(np.float32))
+        assert np.all(np.isfinite(mean))
+    h.close()
