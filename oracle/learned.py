@@ -217,8 +217,10 @@ def learned_finalize(model, W, C, seed, t, y, anc, x_prev, z_prev, x_new, bidx, 
 #   A_zx x_{t-1}^(a) + A_zz z_{t-1}^(a, b_ij), m_i their mean and v_i their variance
 #   (per coordinate, over j); head (log s_i, c_i) (d2 each, log s clamped to [-7, 5]);
 #   zhat_ij = mu_ij + L_qz eps_ij (the prior draw, PROP noise), and
-#   z_ij = m_i + c_i + s_i * (zhat_ij - m_i),
-#   log q(z_ij) = log N(zhat_ij; mu_ij, Q_z) - sum log s_i.
+#   z_ij = k_ij + c_i + s_i * (zhat_ij - k_ij),
+#   log q(z_ij) = log N(zhat_ij; mu_ij, Q_z) - sum log s_i,
+#   with the centre k_ij = m_i (the group's mean prior mean) or k_ij = mu_ij (the
+#   particle's own prior mean: the map then scales only the transition noise).
 # ---------------------------------------------------------------------------
 def inner_ess(lq):
     """Inner effective sample size of each group, (sum_j W_j)^2 / sum_j W_j^2 with
@@ -280,10 +282,11 @@ def amortised_features(model, x_prev_a, x_new, y, zb):
 
 
 def amortised_finalize(model, W, seed, t, y, anc, x_prev, z_prev, x_new, bidx, normals, bf16_mode=False,
-                       head_out=None):
+                       head_out=None, centre="group"):
     """The inner update of step t with the outer-amortised proposal (see above) for
     destinations 0..n-1, bidx from the plain local resampling. head_out: (n, >= 2 d2)
-    network outputs to use instead of evaluating it. Returns z, lq, feats, out."""
+    network outputs to use instead of evaluating it. centre: "group" (k = m) or
+    "particle" (k = mu). Returns z, lq, feats, out."""
     d1, d2, dy = model.d1, model.d2, model.dy
     Q, H, R = model.Q, model.H, model.R
     Qz = Q[d1:, d1:]
@@ -305,7 +308,8 @@ def amortised_finalize(model, W, seed, t, y, anc, x_prev, z_prev, x_new, bidx, n
         eps = np.stack([normals(t, i, 9, j, d2) for j in range(M)])  # P_PROP
         zhat = mus[i] + eps @ Lqz.T
         s = np.exp(ls[i])
-        z = ms[i] + c[i] + s * (zhat - ms[i])
+        k = mus[i] if centre == "particle" else ms[i]
+        z = k + c[i] + s * (zhat - k)
         def lgauss(v, L):
             u = np.linalg.solve(L, v.T).T
             return -0.5 * np.sum(u * u, 1) - np.sum(np.log(np.diag(L))) - 0.5 * L.shape[0] * LOG2PI

@@ -253,3 +253,49 @@ def test_inner_ess_and_the_fallback_rule():
     assert learned.inner_ess(lq4)[0] == pytest.approx(3.0, rel=1e-15)
     assert learned.fallback_groups(lq4, 0.8)[0]
     assert not learned.fallback_groups(lq4, 0.75)[0]
+
+
+def test_particle_centred_map_weights_by_its_density():
+    """With the centre at the particle's own prior mean the map's draw is
+    z = mu_j + c + s (zhat - mu_j), zhat ~ N(mu_j, Q_z), so its proposal density is
+    N(z; mu_j + c, S Q_z S): the oracle's log-weights, evaluated by change of
+    variables, must equal log N(z; mu_j, Q_z) - log N(z; mu_j + c, S Q_z S)
+    + log N(y; H_x x + H_z z, R) normalised over the group (scipy's densities); the
+    identity map (s = 1, c = 0) reproduces the plain inner update."""
+    stats = pytest.importorskip("scipy.stats")
+    spec = workloads.make_model("lg4", 0)
+    om = oracle.OracleModel.from_spec(spec)
+    N, M, L, seed = 6, 16, 4, 5
+    o = oracle.Oracle(om, N, M, L, seed)
+    _, ys = workloads.simulate(spec, 3, 0)
+    x, z, lq = o.init()
+    r1 = o.step(1, ys[0], x, z, lq)
+    r2 = o.step(2, ys[1], r1["x"], r1["z"], r1["lq"])
+    fin = o.finalize(2, ys[1], np.arange(N), r2["anc"], r1["x"], r1["z"], r1["lq"], r2["x"])
+    lib = oracle.load()
+    d1, d2 = om.d1, om.d2
+    din = 2 * d1 + om.dy + 2 * d2
+    W = workloads.init_mlp_weights(din, 16, 2 * d2, seed=1)
+    W["W4"][:] = 0.0
+    W["b4"][:] = 0.0
+    nrm = lambda t, i, p, j, n: oracle.normals(seed, 0, t, i, p, j, n, lib)  # noqa: E731
+    ident = learned.amortised_finalize(om, W, seed, 2, ys[1], r2["anc"], r1["x"], r1["z"], r2["x"], fin["bidx"],
+                                       normals=nrm, centre="particle")
+    np.testing.assert_allclose(ident["z"], fin["z"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(ident["lq"], fin["lq"], rtol=1e-10, atol=1e-10)
+    rng = np.random.default_rng(8)
+    head = np.concatenate([rng.uniform(-0.4, 0.4, (N, d2)), 0.3 * rng.standard_normal((N, d2))], axis=1)
+    got = learned.amortised_finalize(om, W, seed, 2, ys[1], r2["anc"], r1["x"], r1["z"], r2["x"], fin["bidx"],
+                                     normals=nrm, head_out=head, centre="particle")
+    Qz, Hx, Hz = om.Q[d1:, d1:], om.H[:, :d1], om.H[:, d1:]
+    for i in range(N):
+        a = r2["anc"][i]
+        mu = r1["x"][a] @ om.A[d1:, :d1].T + r1["z"][a][fin["bidx"][i]] @ om.A[d1:, d1:].T
+        s, c = np.exp(head[i, :d2]), head[i, d2:]
+        S = np.diag(s)
+        lr = np.array([stats.multivariate_normal.logpdf(got["z"][i, j], mu[j], Qz)
+                       - stats.multivariate_normal.logpdf(got["z"][i, j], mu[j] + c, S @ Qz @ S)
+                       + stats.multivariate_normal.logpdf(ys[1], Hx @ r2["x"][i] + Hz @ got["z"][i, j], om.R)
+                       for j in range(M)])
+        lr -= lr.max()
+        np.testing.assert_allclose(got["lq"][i], lr - np.log(np.exp(lr).sum()), rtol=1e-9, atol=1e-9)
