@@ -385,13 +385,16 @@ def run(args):
 def secondary_legs():
     """Short runs of the other configurations, reported beside the headline (one GPU):
     the 512-filter batched workload (10 graph-captured steps), the learned proposals at
-    N = 262144, M = 64 (10 steps each form, with RMSE and inner ESS), and four filters of
-    the high-dimensional workload as one batch (10 graph-captured steps). Each carries its own roofline and clocks."""
+    N = 262144, M = 64 (10 steps each form, with RMSE and inner ESS), four filters of
+    the high-dimensional workload as one batch (10 graph-captured steps), and the
+    outer-amortised proposal at the high-dimensional size against the plain filter (10
+    steps each form, with RMSE and inner ESS). Each carries its own clocks."""
     import torch
     out = {}
     legs = [("batched", run_batched, dict(filters=512, steps=10, warmup=3)),
             ("learned", run_learned, dict(steps=10, warmup=3)),
-            ("highdim", run_highdim, dict(filters=4, steps=10, warmup=3))]
+            ("highdim", run_highdim, dict(filters=4, steps=10, warmup=3)),
+            ("highdim_learned", run_highdim_learned, dict(steps=10, warmup=3))]
     for name, fn, kw in legs:
         t0 = time.perf_counter()
         try:
@@ -625,6 +628,179 @@ def run_highdim(args):
         "propagation_kernel_ms": cmp,
         # each step: a step launch a filter, the outer-sums and the resampling launches
         "gpu_launches": K * (F + 2),
+        "clocks": clk,
+    }
+    return line
+
+
+def run_highdim_learned(args):
+    """The learned proposal at the high-dimensional size: growth_clg64 (d1 = 8, d2 = 56,
+    dy = 8), N = 32768, L = 16, FP32. The outer-amortised form (one network row per
+    group: MLP 3 x 256 ReLU, an affine head of 2 d2 = 112 outputs, BF16 weights, FP32
+    accumulation) is trained on the GPU on 1,048,576 rows the plain filter records
+    (4 steps x 1024 groups x M = 256), centred at each particle's own prior mean (and, for
+    comparison, at the group's mean prior mean); then the filter with it and the plain filter are
+    timed over the same steps at M = 256 and M = 128 (the learned form without the
+    per-group fallback, and at M = 256 also with it), and their accuracy (RMSE of the
+    filtered mean against the simulated states, inner ESS) is measured on an untimed run."""
+    import numpy as np
+    import torch
+
+    from paper_1203_2394_gb300 import dpf, workloads
+
+    torch.cuda.set_device(0)
+    spec = workloads.make_model("growth_clg64", 0)
+    sz = spec.sizes
+    N, M, L = sz["N"], sz["M"], sz["L"]
+    d1, d2, dy = spec.d1, spec.d2, spec.dy
+    K, W = args.steps, args.warmup
+    model = dpf.Model.from_spec(spec, dpf.DPF_F32)
+    if getattr(args, "profile_run", False):
+        # one plain step, then two learned steps (prepare, four network products, update,
+        # the look-ahead step and the outer stage each)
+        pr = dpf.Proposal(d1, d2, dy, hidden=256, amortised_Qz=spec.Q[d1:, d1:])
+        W0 = workloads.init_mlp_weights(2 * d1 + dy + 2 * d2, 256, 2 * d2, seed=0)
+        W0["W4"] *= 0.1
+        pr.set_weights(W0)
+        pr.set_centre(True)
+        f = dpf.Filter(model, d1, d2, N, M, L, seed=3)
+        f.set_proposal(pr)
+        f.set_fallback(0.0)
+        _, ys = workloads.simulate(spec, 3, 0)
+        for t in range(3):
+            f.step(ys[t].astype(np.float32))
+        torch.cuda.synchronize()
+        f.close()
+        pr.close()
+        return {"workload": "highdim_learned profile run", "steps": 3, "N": N, "M": M, "L": L}
+    stream = torch.cuda.Stream()
+    # ---- training rows and training ----
+    t0 = time.perf_counter()
+    n_rec, t_rec = 1024, 4
+    _, ys_tr = workloads.simulate(spec, t_rec + 2, 100)
+    rec = dpf.Filter(model, d1, d2, n_rec, M, L, seed=1, stream=stream)
+    rec.set_debug(True)
+    rows = []
+    for t in range(t_rec + 1):
+        rec.step(ys_tr[t].astype(np.float32))
+        if t >= 1:
+            rows.append(rec.record_amortised())
+    rec.close()
+    G = torch.cat([r[0] for r in rows]); Zm = torch.cat([r[1] for r in rows]); wm = torch.cat([r[2] for r in rows])
+    del rows
+    din, dout = 2 * d1 + dy + 2 * d2, 2 * d2
+    A0 = workloads.init_mlp_weights(din, 256, dout, seed=0)
+    A0["W4"][:] = 0.0
+    A0["b4"][:] = 0.0  # start at the identity map (the prior)
+    props, losses = {}, {}
+    for centre in ("particle", "group"):
+        pr = dpf.Proposal(d1, d2, dy, hidden=256, stream=stream, amortised_Qz=spec.Q[d1:, d1:])
+        pr.set_centre(centre == "particle")
+        pr.set_weights(A0)
+        Zc = Zm
+        if centre == "particle":  # the rows' centre block: the particle's own prior mean
+            Zc = Zm.clone()
+            Zc[:, 2 * d2:] = Zm[:, d2:2 * d2]
+        losses[centre] = [float(v) for v in pr.train(G, Zc, wm, batch=2048, epochs=3, lr=1e-3, seed=2)]
+        props[centre] = pr
+        del Zc
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    n_rows = int(G.shape[0])
+    prop = props["particle"]
+    del G, Zm, wm
+    torch.cuda.empty_cache()
+    # ---- timing ----
+    _, ys = workloads.simulate(spec, W + K + 1, 0)
+    yd = torch.tensor(ys.astype(np.float32), device="cuda")
+
+    def timed(m_inner, use_prop, frac=0.0):
+        f = dpf.Filter(model, d1, d2, N, m_inner, L, seed=3, stream=stream)
+        if use_prop:
+            f.set_proposal(use_prop)
+            f.set_fallback(frac)
+        with torch.cuda.stream(stream):
+            for k in range(W):
+                f.step_device(yd[k].data_ptr())
+            f.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(W, W + K):
+                f.step_device(yd[k].data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f.sync()
+        f.close()
+        return e0.elapsed_time(e1) / K
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    w0 = time.monotonic()
+    ms = {("learned", M, 0.0): timed(M, prop)}
+    w1 = time.monotonic()
+    clk = clocks.stop(window=(w0, w1))
+    ms[("plain", M, None)] = timed(M, None)
+    ms[("learned", M // 2, 0.0)] = timed(M // 2, prop)
+    ms[("plain", M // 2, None)] = timed(M // 2, None)
+    ms[("learned", M, 0.25)] = timed(M, prop, 0.25)
+    ms[("learned_group_centre", M, 0.0)] = timed(M, props["group"])
+    # ---- accuracy on an untimed run ----
+    T = 20
+    s_true, ya = workloads.simulate(spec, T, 200)
+
+    def accuracy(m_inner, use_prop, frac):
+        f = dpf.Filter(model, d1, d2, N, m_inner, L, seed=5, stream=stream)
+        if use_prop:
+            f.set_proposal(use_prop)
+            f.set_fallback(frac)
+        err, ess, fb = [], [], []
+        for t in range(T):
+            m, _ = f.step(ya[t].astype(np.float32))
+            err.append(m - s_true[t + 1])
+            if t >= 1:
+                lq = torch.tensor(f.read("lq"), device="cuda", dtype=torch.float64)
+                Wt = torch.exp(lq - lq.max(dim=1, keepdim=True).values)
+                ess.append(float((Wt.sum(1) ** 2 / (Wt * Wt).sum(1)).mean()) / m_inner)
+                if use_prop:
+                    fb.append(float(np.mean(f.read("fallback"))))
+        f.close()
+        return {"rmse_vs_truth": float(np.sqrt(np.mean(np.square(err)))), "inner_ess": float(np.mean(ess)),
+                "fallback_share": float(np.mean(fb)) if fb else None}
+
+    acc = {}
+    for kind, m_inner, frac in ms:
+        use = {"learned": prop, "learned_group_centre": props["group"]}.get(kind)
+        acc[(kind, m_inner, frac)] = accuracy(m_inner, use, frac)
+    for pr in props.values():
+        pr.close()
+
+    def form_name(kind, m_inner, frac):
+        return f"{kind}_M{m_inner}" + (f"_fallback{frac}" if frac else "")
+    forms = {form_name(kind, m_inner, frac): {"M": m_inner, "fallback_threshold": frac, "ms_per_step": v,
+                                              "value": N * m_inner / (v / 1e3), **acc[(kind, m_inner, frac)]}
+             for (kind, m_inner, frac), v in ms.items()}
+    v_l = forms[f"learned_M{M}"]["ms_per_step"]
+    mlp_flop = 2 * (din * 256 + 2 * 256 * 256 + 256 * dout)  # per group
+    line = {
+        "metric": METRIC, "value": N * M / (v_l / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": v_l, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 filter, bf16 MLP", "data": "synthetic",
+        "config": {"workload": f"learned proposal at the high-dimensional size: growth_clg64 (d1={d1}, d2={d2}, "
+                               f"dy={dy}), N={N}, M={M}, L={L}, FP32; outer-amortised MLP 3x256 ReLU, affine "
+                               "head, BF16 weights, FP32 accumulate; one filter",
+                   "centre": "learned forms: the particle's own prior mean; learned_group_centre: the group's "
+                             "mean prior mean",
+                   "training_rows": n_rows, "training_epochs": 3, "training_batch": 2048,
+                   "training_s_both": train_s, "training_losses": losses,
+                   "l2": "state far larger than L2; no flush"},
+        "forms": forms,
+        "accuracy_steps": T,
+        "network_flop_per_group": mlp_flop,
+        # the headline form (no fallback) each step: the prepare pass, four network
+        # products, the update pass, the look-ahead step and the outer stage
+        "gpu_launches": 8 * K,
         "clocks": clk,
     }
     return line
@@ -1073,7 +1249,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "learned", "compare", "table2", "paper", "bandit"],
+    ap.add_argument("--workload", default="growth_clg10", choices=["growth_clg10", "batched", "highdim", "highdim_learned", "learned", "compare", "table2", "paper",
+                             "bandit"],
                     help="the headline single-filter workload, the many-filter one, the d2 = 56 one, "
                          "the learned-proposal one, or the LA-DPF against the bootstrap PF")
     ap.add_argument("--runs", type=int, default=3, help="runs per model of the paper and bandit workloads (at most 8)")
@@ -1083,6 +1260,9 @@ def main(argv=None):
     ap.add_argument("--outer", type=int, default=None,
                     help="outer particles of the headline workload (default its 65536; for profiling a "
                          "smaller case of the same kernel)")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="highdim_learned: only three steps of the learned filter (untrained network, no "
+                         "fallback), no timing: the launches a profiler captures")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the short batched, learned and high-dimensional legs of the default run")
     args = ap.parse_args(argv)
@@ -1100,6 +1280,9 @@ def main(argv=None):
         return 0
     if args.workload == "learned":
         print(json.dumps(run_learned(args)))
+        return 0
+    if args.workload == "highdim_learned":
+        print(json.dumps(run_highdim_learned(args)))
         return 0
     if args.workload == "compare":
         return run_compare(args)

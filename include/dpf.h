@@ -452,22 +452,39 @@ dpf_status dpf_proposal_train(dpf_proposal* p, const float* F, const float* Z, c
  * z = m + c + s (zhat - m), weighted by log N(z; mu_j, Q_z) - log N(zhat; mu_j, Q_z)
  * + sum log s + log p(y_t | x_t, z). Qz: host, d2 x d2 (row-major), for the
  * training loss. Training rows (dpf_proposal_train, dpf_proposal_loss_grad):
- * F = the group features, Z = (z_t, mu_j, m) (3 d2 floats a row).
+ * F = the group features, Z = (z_t, mu_j, m) (3 d2 floats a row). d2 up to 64 and
+ * din up to 160 (the mixture form: d2 up to 8, din up to 16).
  */
 dpf_status dpf_proposal_create_amortised(int32_t d1, int32_t d2, int32_t dy, int32_t hidden, const double* Qz,
                                          void* stream, dpf_proposal** out);
+/*
+ * The centre k of the outer-amortised map z = k + c + s (zhat - k): 0 (default)
+ * the group's mean prior mean m, 1 the particle's own prior mean mu_j (the map then
+ * scales only the transition noise, which suits groups whose prior means spread
+ * far wider than that noise). The weight keeps its form. Training rows then carry
+ * the centre in their third block: Z = (z_t, mu_j, mu_j) (the recorded m replaced
+ * by mu_j). DPF_E_INVALID for a mixture proposal or a value other than 0 or 1.
+ */
+dpf_status dpf_proposal_set_centre(dpf_proposal* p, int32_t per_particle);
 /* The head outputs (n x dout floats, device) of n device feature rows by the
- * tensor-core forward pass the filter step uses. Synchronises. */
+ * tensor-core forward pass the filter step uses at d = 4 (din <= 16, dout <= 32,
+ * hidden 256; DPF_E_UNSUPPORTED otherwise). Synchronises. */
 dpf_status dpf_proposal_forward(dpf_proposal* p, const float* F, int64_t n, float* out);
 void dpf_proposal_destroy(dpf_proposal* p);
 
 /*
  * Use `p` as the inner proposal of ctx from the next step on (NULL: the prior
- * again). Needs an FP32 context with d1, d2, dy equal to the proposal's and M
- * in {32, 64, 128}; the look-ahead is unchanged. The inner update then draws
+ * again). Needs an FP32 context with d1, d2, dy equal to the proposal's; the
+ * look-ahead is unchanged. The mixture form: (d1, d2, dy) = (2, 2, 2), hidden
+ * 256, 4 components and M in {32, 64, 128}; the inner update then draws
  * z_t^(i,j) ~ q_phi(. | f) (component by the one-draw local systematic rule,
  * Philox purpose 10 = LCOMP, the normal noise from the PROP stream) and weights
  * it by log r = log p(z_t | z_{t-1}, x_{t-1}) - log q_phi(z_t | f) + log p(y_t | x_t, z_t).
+ * The outer-amortised form (see dpf_proposal_create_amortised): (2, 2, 2) with
+ * hidden 256 and M in {32, 64, 128, 256}, or (8, 56, 8) with an x transition free
+ * of z and M a multiple of 32 up to 256 (the network's four products then run on
+ * the tensor cores over the N group rows, any hidden width a multiple of 16).
+ * DPF_E_UNSUPPORTED for other shapes.
  */
 dpf_status dpf_set_proposal(dpf_ctx* ctx, dpf_proposal* p);
 
@@ -494,7 +511,7 @@ dpf_status dpf_set_fallback(dpf_ctx* ctx, double frac);
 dpf_status dpf_record_tuples(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* F, float* Z, float* w);
 /* The same rows for the outer-amortised form: G (n_outer M x (2 d1 + dy + 2 d2)),
  * Z (n_outer M x 3 d2: z_t, mu_j, m), w (n_outer M). Compiled for (d1, d2, dy) =
- * (2, 2, 2) and M a multiple of 32 up to 256. */
+ * (2, 2, 2) and (8, 56, 8), M a multiple of 32 up to 256. */
 dpf_status dpf_record_tuples_amortised(dpf_ctx* ctx, int64_t i0, int64_t n_outer, float* G, float* Z, float* w);
 
 /*

@@ -134,6 +134,9 @@ const Variant* find_variant(int prec, int d1, int d2, int dy);
 // the paper's models 1 and 2 (FP32); swapped: model 1 with the table's z as the outer block
 const Variant* find_paper_variant(int kind, bool swapped);
 dpf_status learned_inner_step(Ctx& x);
+bool oa_wide_shape(const Ctx& x);  // the amortised proposal's wide pass serves this filter
+dpf_status oa_wide_step(Ctx& x, dpf_proposal& p);
+dpf_status oa_wide_record(Ctx& x, long long i0, long long n_outer, float* G, float* Z, float* w);
 dpf_status learned_fallback_lists(Ctx& x);  // dpf_learned_step.cu
 int dpf_proposal_dout(const dpf_proposal* p);  // head outputs of a proposal
 int dpf_proposal_kind(const dpf_proposal* p);  // 0 mixture, 1 outer-amortised
@@ -172,6 +175,8 @@ struct dpf_ctx {
   void* oa_bidx = nullptr;      // amortised proposal: local resampling indices, group features, head outputs
   void* oa_feat = nullptr;
   void* oa_out = nullptr;
+  void* oa_hidden = nullptr;    // ... and at the wide size, two N x hidden buffers of the network's layers
+  void* oa_mu = nullptr;        // ... and the prior means of the inner particles, [d2][N M]
   // small device block: reduction partials, statistics, counters, error word
   void* small = nullptr;
   double* stats = nullptr;          // [logZ_total, logZ_step, ess, s1, mean[d]]

@@ -279,7 +279,7 @@ struct AffineArgs {
   float* dout;
   double* loss;
   int n, d2;
-  float qinv[kMaxD2 * kMaxD2];
+  const float* qinv;  // d2 x d2, row-major (device)
   float half_logdet;
 };
 
@@ -290,7 +290,7 @@ __global__ void head_affine_kernel(AffineArgs a) {
   const float* o = a.out + (long long)b * 2 * d2;
   const float* zr = a.Z + (long long)b * 3 * d2;
   float* g = a.dout + (long long)b * 2 * d2;
-  float r[kMaxD2], u[kMaxD2], ls[kMaxD2];
+  float r[kMaxD2Amortised], u[kMaxD2Amortised], ls[kMaxD2Amortised];
   float sum_ls = 0.f;
   for (int d = 0; d < d2; ++d) {
     ls[d] = fminf(fmaxf(o[d], kLogSigMin), kLogSigMax);
@@ -300,7 +300,7 @@ __global__ void head_affine_kernel(AffineArgs a) {
     sum_ls += ls[d];
   }
   float quad = 0.f;
-  float gz[kMaxD2];
+  float gz[kMaxD2Amortised];
   for (int d = 0; d < d2; ++d) {
     float v = 0.f;
     for (int e = 0; e < d2; ++e) v += a.qinv[d * d2 + e] * r[e];
@@ -463,7 +463,7 @@ static dpf_status fwd_bwd(dpf_proposal& p, int nb, double* loss_dev, float* grad
     AffineArgs aa{};
     aa.out = p.ob; aa.Z = p.Zb; aa.w = p.wb; aa.wsum = p.wsum_d; aa.dout = p.dO; aa.loss = loss_dev;
     aa.n = nb; aa.d2 = p.d2;
-    memcpy(aa.qinv, p.qinv, sizeof(aa.qinv));
+    aa.qinv = p.qinv_d;
     aa.half_logdet = p.half_logdet;
     head_affine_kernel<<<(nb + 127) / 128, 128, 0, s>>>(aa);
   }
@@ -486,6 +486,22 @@ static dpf_status fwd_bwd(dpf_proposal& p, int nb, double* loss_dev, float* grad
   tgemm<true, false, 0>(s, p.bf16 ? 1 : 0, p.err_d, H, din, nb, p.dA, H, p.Fb, din, gW1, din);
   colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(p.dA, nb, H, gb1);
   return cuda_error(cudaGetLastError(), "proposal backward");
+}
+
+dpf_status proposal_forward_rows(dpf_proposal& p, const float* F, long long n, float* hidden, float* out, int* err,
+                                 cudaStream_t s) {
+  if (n < 1) return DPF_OK;
+  if (n > (1LL << 30)) return set_error(DPF_E_INVALID, "proposal forward: too many rows");
+  const int H = p.hidden, din = p.din, dO = p.dout, m = (int)n;
+  const int pb = p.bf16 ? 1 : 0;
+  const float* Wq = p.Wq;
+  float* ha = hidden;
+  float* hb = hidden + (size_t)n * H;
+  tgemm<false, true, 1>(s, pb, err, m, H, din, F, din, Wq + p.offW[0], din, ha, H, Wq + p.offB[0], nullptr, pb);
+  tgemm<false, true, 1>(s, pb, err, m, H, H, ha, H, Wq + p.offW[1], H, hb, H, Wq + p.offB[1], nullptr, pb);
+  tgemm<false, true, 1>(s, pb, err, m, H, H, hb, H, Wq + p.offW[2], H, ha, H, Wq + p.offB[2], nullptr, pb);
+  tgemm<false, true, 2>(s, pb, err, m, dO, H, ha, H, Wq + p.offW[3], H, out, dO, Wq + p.offB[3]);
+  return cuda_error(cudaGetLastError(), "proposal forward");
 }
 
 static dpf_status adam(dpf_proposal& p, const float* grad, float lr) {
@@ -518,10 +534,13 @@ static uint64_t splitmix64(uint64_t& s) {
 
 static dpf_status proposal_make(int kind, int32_t d1, int32_t d2, int32_t dy, int32_t hidden, int32_t components,
                                 int din, int dout, int zw, void* stream, dpf_proposal** out) {
-  if (d1 < 1 || d2 < 1 || dy < 1 || din > kMaxDin || d2 > kMaxD2 || hidden < 16 || hidden > kMaxHidden ||
+  const int max_din = kind == 1 ? kMaxDinAmortised : kMaxDin;
+  const int max_d2 = kind == 1 ? kMaxD2Amortised : kMaxD2;
+  if (d1 < 1 || d2 < 1 || dy < 1 || din > max_din || d2 > max_d2 || hidden < 16 || hidden > kMaxHidden ||
       hidden % 16 || components < 1 || components > kMaxComponents || dout > kMaxDout)
-    return set_error(DPF_E_INVALID, "dpf_proposal_create: unsupported sizes (din <= 16, d2 <= 8, hidden a "
-                                    "multiple of 16 up to 256, components 1..8, head <= 128)");
+    return set_error(DPF_E_INVALID, "dpf_proposal_create: unsupported sizes (mixture: din <= 16, d2 <= 8; "
+                                    "amortised: din <= 160, d2 <= 64; hidden a multiple of 16 up to 256, "
+                                    "components 1..8, head <= 128)");
   dpf_proposal* p = new dpf_proposal();
   p->kind = kind;
   p->d1 = d1;
@@ -588,7 +607,8 @@ dpf_status dpf_proposal_create_amortised(int32_t d1, int32_t d2, int32_t dy, int
   clear_error();
   if (!out || !Qz) return set_error(DPF_E_INVALID, "dpf_proposal_create_amortised: null argument");
   *out = nullptr;
-  if (d2 < 1 || d2 > kMaxD2) return set_error(DPF_E_INVALID, "dpf_proposal_create_amortised: d2 in 1..8");
+  if (d2 < 1 || d2 > kMaxD2Amortised)
+    return set_error(DPF_E_INVALID, "dpf_proposal_create_amortised: d2 in 1..64");
   // Q_z^-1 and log det(2 pi Q_z) by a Cholesky factorisation on the host
   std::vector<double> Lc(d2 * d2, 0.0), inv(d2 * d2, 0.0);
   for (int r = 0; r < d2; ++r)
@@ -621,7 +641,25 @@ dpf_status dpf_proposal_create_amortised(int32_t d1, int32_t d2, int32_t dy, int
   dpf_status st = dpf::proposal_make(1, d1, d2, dy, hidden, 1, 2 * d1 + dy + 2 * d2, 2 * d2, 3 * d2, stream, out);
   if (st) return st;
   for (int q = 0; q < d2 * d2; ++q) (*out)->qinv[q] = (float)inv[q];
+  dpf_proposal* p = *out;
+  cudaError_t e = cudaErrorMemoryAllocation;
+  if (palloc(*p, (void**)&p->qinv_d, sizeof(float) * (size_t)d2 * d2) == DPF_OK)
+    e = cudaMemcpyAsync(p->qinv_d, p->qinv, sizeof(float) * (size_t)d2 * d2, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    dpf_proposal_destroy(p);
+    *out = nullptr;
+    return e == cudaErrorMemoryAllocation ? DPF_E_NOMEM : cuda_error(e, "dpf_proposal_create_amortised");
+  }
   (*out)->half_logdet = (float)(0.5 * (logdet + d2 * std::log(2.0 * M_PI)));
+  return DPF_OK;
+}
+
+dpf_status dpf_proposal_set_centre(dpf_proposal* p, int32_t per_particle) {
+  clear_error();
+  if (!p || p->kind != 1 || (per_particle != 0 && per_particle != 1))
+    return set_error(DPF_E_INVALID, "dpf_proposal_set_centre: an outer-amortised proposal and 0 or 1");
+  p->centre = per_particle;
   return DPF_OK;
 }
 

@@ -14,19 +14,28 @@ constexpr int kLayers = 4;           // three hidden layers and the head
 constexpr int kMaxComponents = 8;
 constexpr int kMaxDin = 16;          // inputs, padded to one BF16 MMA K step
 constexpr int kMaxD2 = 8;
+constexpr int kMaxDinAmortised = 160;  // the outer-amortised form: 2 d1 + dy + 2 d2 inputs
+constexpr int kMaxD2Amortised = 64;
 constexpr int kMaxHidden = 256;
 constexpr int kMaxDout = 128;
 constexpr float kLogSigMin = -7.f, kLogSigMax = 5.f;
 
 dpf_status proposal_requantize(dpf_proposal& p);
+// The network over n feature rows F (n x din) into out (n x dout) on the tensor cores,
+// rounded as the training forward pass rounds; hidden holds 2 n x hidden floats. A
+// bounded wait that gives up sets ERR_TIMEOUT in *err.
+dpf_status proposal_forward_rows(dpf_proposal& p, const float* F, long long n, float* hidden, float* out, int* err,
+                                 cudaStream_t s);
 
 }  // namespace dpf
 
 struct dpf_proposal {
   int kind = 0;  // 0: mixture of Gaussians per inner particle; 1: per-group affine map of the prior draws
   int d1 = 0, d2 = 0, dy = 0, din = 0, hidden = 0, C = 0, dout = 0;
-  int zw = 0;    // floats per training target row: d2 (kind 0) or 3 d2 (z, prior mean, group centre)
-  float qinv[dpf::kMaxD2 * dpf::kMaxD2] = {};  // kind 1: Q_z^-1 (row-major) for the training loss
+  int zw = 0;    // floats per training target row: d2 (kind 0) or 3 d2 (z, prior mean, centre)
+  int centre = 0;  // kind 1: the map's centre, 0 the group's mean prior mean m, 1 the particle's own mu
+  float qinv[dpf::kMaxD2Amortised * dpf::kMaxD2Amortised] = {};  // kind 1: Q_z^-1 (row-major), the training loss
+  float* qinv_d = nullptr;                      // ... its device copy
   float half_logdet = 0.f;                      // kind 1: 1/2 log det(2 pi Q_z)
   long long nparams = 0;
   long long offW[dpf::kLayers] = {}, offB[dpf::kLayers] = {};

@@ -623,7 +623,7 @@ static uint32_t scale_for(int n) {
 // Group features (x_{t-1} of the ancestor, x_t, y_t, m, v) with mu_ij = A_zx x_{t-1} +
 // A_zz z_{t-1}^(a, b_ij), m and v their mean and variance over j; the head gives the
 // group's (raw log s, c); the particle draws zhat = mu + L_qz eps (PROP noise) and
-// takes z = m + c + s (zhat - m), weighted by log N(z; mu, Q_z) - log N(zhat; mu, Q_z)
+// takes z = k + c + s (zhat - k) about the centre k (m, or the particle's own mu), weighted by log N(z; mu, Q_z) - log N(zhat; mu, Q_z)
 // + sum log s + log p(y_t | x_t, z).
 
 // Selection, local resampling and the group features; one warp per outer particle,
@@ -785,7 +785,7 @@ template <int D1, int D2, int DY, int PP>
 __global__ void __launch_bounds__(128)
     oa_update_kernel(const __grid_constant__ MC<float, D1, D2, DY> mc, const __grid_constant__ StepArgs<float> a,
                      const int32_t* __restrict__ bidx, const float* __restrict__ feat, const float* __restrict__ out,
-                     int din, int dout) {
+                     int din, int dout, int centre) {
   constexpr int M = 32 * PP;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long g = blockIdx.x * 4LL + w;
@@ -837,7 +837,8 @@ __global__ void __launch_bounds__(128)
       float zh = mu[r];
 #pragma unroll
       for (int c = 0; c <= r; ++c) zh += mc.Lqz[r][c] * eps[c];
-      z[p][r] = m[r] + cc[r] + sc[r] * (zh - m[r]);
+      const float k = centre ? mu[r] : m[r];
+      z[p][r] = k + cc[r] + sc[r] * (zh - k);
       e2 += eps[r] * eps[r];
     }
     // log N(z; mu, Q_z) by forward substitution with L_qz
@@ -989,7 +990,7 @@ static dpf_status oa_step_pp(Ctx& x, const MC<float, 2, 2, 2>& mc, StepArgs<floa
   if (st) return st;
   oa_update_kernel<2, 2, 2, PP><<<blocks, 128, 0, x.stream>>>(mc, a, (const int32_t*)x.oa_bidx,
                                                                (const float*)x.oa_feat, (const float*)x.oa_out,
-                                                               p.din, p.dout);
+                                                               p.din, p.dout, p.centre);
   return cuda_error(cudaGetLastError(), "amortised update launch");
 }
 
@@ -1034,6 +1035,7 @@ dpf_status learned_fallback_lists(Ctx& x) {
 // (FP32, 2, 2, 2)); then the look-ahead runs alone from the materialised state.
 dpf_status learned_inner_step(Ctx& x) {
   dpf_proposal& p = *x.proposal;
+  if (p.kind == 1 && oa_wide_shape(x)) return oa_wide_step(x, p);
   dpf_status st = pack(p);
   if (st) return st;
   typedef VariantImpl<float, 2, 2, 2, 0> V;
@@ -1147,10 +1149,13 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
                        !(x->M == 32 || x->M == 64 || x->M == 128)))
     return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: compiled for (d1, d2, dy) = (2, 2, 2), hidden 256, "
                                         "4 components and M in {32, 64, 128}");
-  if (p->kind == 1 && (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH ||
-                       !(x->M == 32 || x->M == 64 || x->M == 128 || x->M == 256)))
+  const bool wide = p->kind == 1 && oa_wide_shape(*x);
+  if (p->kind == 1 && !wide &&
+      (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || p->hidden != LH ||
+       !(x->M == 32 || x->M == 64 || x->M == 128 || x->M == 256)))
     return set_error(DPF_E_UNSUPPORTED, "dpf_set_proposal: the amortised pass is compiled for (d1, d2, dy) = "
-                                        "(2, 2, 2), hidden 256 and M in {32, 64, 128, 256}");
+                                        "(2, 2, 2), hidden 256 and M in {32, 64, 128, 256}, and for (8, 56, 8) "
+                                        "with x free of z and M a multiple of 32 up to 256");
   auto grow = [&](void** q, size_t bytes) -> cudaError_t {
     if (*q) return cudaSuccess;
     cudaError_t e = cudaMalloc(q, bytes);
@@ -1166,8 +1171,10 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
   }
   if (p->kind == 1) {
     cudaError_t e = grow(&x->oa_bidx, sizeof(int32_t) * (size_t)x->N * x->M);
-    if (e == cudaSuccess) e = grow(&x->oa_feat, sizeof(float) * (size_t)x->N * LDIN);
-    if (e == cudaSuccess) e = grow(&x->oa_out, sizeof(float) * (size_t)x->N * LNP);
+    if (e == cudaSuccess) e = grow(&x->oa_feat, sizeof(float) * (size_t)x->N * std::max(LDIN, p->din));
+    if (e == cudaSuccess) e = grow(&x->oa_out, sizeof(float) * (size_t)x->N * std::max(LNP, p->dout));
+    if (e == cudaSuccess && wide) e = grow(&x->oa_hidden, sizeof(float) * 2 * (size_t)x->N * p->hidden);
+    if (e == cudaSuccess && wide) e = grow(&x->oa_mu, sizeof(float) * (size_t)x->d2 * x->N * x->M);
     if (e != cudaSuccess) return cuda_error(e, "dpf_set_proposal: amortised buffers");
   }
   x->proposal = p;
@@ -1189,8 +1196,14 @@ dpf_status dpf_record_tuples_amortised(dpf_ctx* x, int64_t i0, int64_t n_outer, 
   if (x->t < 2 || !x->dbg_b || !x->anc_prev || x->prec != DPF_F32)
     return set_error(DPF_E_INVALID, "dpf_record_tuples_amortised: needs an FP32 filter stepped at least twice "
                                     "with debug recording on");
+  if (oa_wide_shape(*x)) {
+    dpf_status st = oa_wide_record(*x, i0, n_outer, G, Z, w);
+    if (st) return st;
+    return cuda_error(cudaStreamSynchronize(x->stream), "dpf_record_tuples_amortised");
+  }
   if (!(x->d1 == 2 && x->d2 == 2 && x->dy == 2) || x->M % 32 || x->M > 256)
-    return set_error(DPF_E_UNSUPPORTED, "dpf_record_tuples_amortised: compiled for (2, 2, 2), M in {32, ..., 256}");
+    return set_error(DPF_E_UNSUPPORTED, "dpf_record_tuples_amortised: compiled for (2, 2, 2) and (8, 56, 8), "
+                                        "M a multiple of 32 up to 256");
   const long long t = x->t;
   const MC<float, 2, 2, 2>& mc = *reinterpret_cast<const MC<float, 2, 2, 2>*>(x->mconst.data());
   const unsigned blocks = (unsigned)((n_outer + 3) / 4);

@@ -70,6 +70,7 @@ SIGNATURES = [
     ("dpf_proposal_set_weights", ctypes.c_int, [_P, _P, _I64]),
     ("dpf_proposal_get_weights", ctypes.c_int, [_P, _P, _I64]),
     ("dpf_proposal_set_bf16", ctypes.c_int, [_P, _I32]),
+    ("dpf_proposal_set_centre", ctypes.c_int, [_P, _I32]),
     ("dpf_proposal_loss_grad", ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
     ("dpf_proposal_adam_step", ctypes.c_int, [_P, _P, ctypes.c_float]),
     ("dpf_proposal_train", ctypes.c_int, [_P, _P, _P, _P, _I64, _I32, _I32, ctypes.c_float, _U64, _P]),
@@ -569,6 +570,12 @@ class Proposal:
 
     def set_bf16(self, on=True):
         check(self._lib.dpf_proposal_set_bf16(self.h, int(on)))
+
+    def set_centre(self, per_particle=True):
+        """The outer-amortised map's centre: the particle's own prior mean (True) or the
+        group's mean prior mean (False, the default); see ``dpf_proposal_set_centre``."""
+        check(self._lib.dpf_proposal_set_centre(self.h, int(per_particle)))
+        self.centre = "particle" if per_particle else "group"
 
     def loss_grad(self, F, Z, w, grad=True):
         """Weighted NLL and (optionally) its gradient (device tensor of num_params)."""

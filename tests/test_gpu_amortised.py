@@ -56,7 +56,8 @@ def test_affine_loss_and_gradients_match_the_oracle():
         assert d <= 1e-4 * np.max(np.abs(ref_g[k])) + 1e-7, (k, d)
 
 
-def test_amortised_inner_update_teacher_forced():
+@pytest.mark.parametrize("centre", ["group", "particle"])
+def test_amortised_inner_update_teacher_forced(centre):
     from paper_1203_2394_gb300 import dpf
     spec = _spec()
     N, M, L, seed = 200, 64, 4, 3
@@ -65,6 +66,7 @@ def test_amortised_inner_update_teacher_forced():
     p, om = _prop(spec)
     W = workloads.init_mlp_weights(DIN, H, DOUT, seed=33)
     p.set_weights(W)
+    p.set_centre(centre == "particle")
     Wq = p.get_weights()
     o = oracle.Oracle(om, N, M, L, seed, nthreads=8)
     lib = oracle.load()
@@ -91,7 +93,8 @@ def test_amortised_inner_update_teacher_forced():
             yprev = ys[t - 2].astype(np.float32).astype(np.float64)
             got = learned.amortised_finalize(
                 om, Wq, seed, t - 1, yprev, pa, px, pz, x, bidx,
-                normals=lambda tt, i, pp, j, n: oracle.normals(seed, 0, tt, i, pp, j, n, lib), head_out=head)
+                normals=lambda tt, i, pp, j, n: oracle.normals(seed, 0, tt, i, pp, j, n, lib), head_out=head,
+                centre=centre)
             assert np.max(rel(feats, got["feats"])) <= 1e-5
             href, cache = learned.forward(Wq, feats, bf16_mode=True)
             scale = np.abs(cache["h3"]) @ np.abs(learned.bf16(Wq["W4"])).T + np.abs(Wq["b4"])

@@ -1,0 +1,252 @@
+"""The outer-amortised learned proposal at the wide size (growth_clg64: d1 = 8, d2 = 56,
+dy = 8) on the GPU against the oracle.
+
+* Training: the affine head's loss and gradients at d2 = 56 (136 inputs, 112 outputs)
+  against the oracle, with the products in 3xTF32 (plain FP32 accuracy).
+* The filter's inner update with it, teacher-forced per step: every selection and local
+  resampling index equal to the oracle's or an explained flip (the plain rule, taken by
+  the wide pass itself); the group features within 1e-5 (relative, floor 1); the network
+  outputs within the bfloat16 bound; z within 1e-5 and lq within 1e-4 of the oracle fed
+  the GPU's indices and network outputs (lq takes the bound of the plain wide step: its
+  terms are 56- and 8-component FP32 quadratic forms, about 56 u |r|^2 ~ 5e-5 absolute);
+  the groups that fall back match the oracle's plain update; the look-ahead that follows
+  (run alone from the materialised state) matches the oracle's.
+* The training rows the filter records equal the oracle's features and targets.
+* The launch configuration of the high-dimensional workload (N = 32768, M = 256,
+  L = 16), checked on sampled groups.
+"""
+import numpy as np
+import pytest
+
+from oracle import learned, oracle
+from paper_1203_2394_gb300 import workloads
+from tests.gpu_util import (LOG2E, check_lwhat, check_selection, explain_flips, fp32_weight_relerr, rel,
+                            state_from_gpu, word)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+D1, D2, DY, H = 8, 56, 8, 256
+DIN, DOUT = 2 * D1 + DY + 2 * D2, 2 * D2
+Z_TOL, LQ_TOL, FEAT_TOL = 1e-5, 1e-4, 1e-5
+
+
+def _spec(seed=0, full_qz=False):
+    """growth_clg64; full_qz: its diagonal Q_z replaced by 0.1 I + B B^T (B entries
+    N(0, 0.02^2)), so that the update takes its full-covariance path."""
+    spec = workloads.make_model("growth_clg64", seed)
+    if full_qz:
+        import dataclasses
+        B = 0.02 * np.random.default_rng(77).standard_normal((D2, D2))
+        Q = spec.Q.copy()
+        Q[D1:, D1:] = 0.1 * np.eye(D2) + B @ B.T
+        spec = dataclasses.replace(spec, Q=Q)
+    return spec
+
+
+def _prop(spec, head_scale, seed=40):
+    from paper_1203_2394_gb300 import dpf
+    om = oracle.OracleModel.from_spec(spec)
+    p = dpf.Proposal(D1, D2, DY, hidden=H, amortised_Qz=om.Q[D1:, D1:])
+    W = workloads.init_mlp_weights(DIN, H, DOUT, seed=seed)
+    W["W4"] *= head_scale
+    W["b4"] = head_scale * 0.2 * np.random.default_rng(seed + 1).standard_normal(DOUT)
+    p.set_weights(W)
+    return p, om
+
+
+def test_affine_loss_and_gradients_at_d2_56():
+    spec = _spec()
+    p, om = _prop(spec, 1.0)
+    p.set_bf16(False)
+    Wf = p.get_weights()
+    rng = np.random.default_rng(32)
+    n = 300
+    G = rng.standard_normal((n, DIN)).astype(np.float32).astype(np.float64)
+    Z = rng.standard_normal((n, 3 * D2)).astype(np.float32).astype(np.float64)
+    w = rng.uniform(0.1, 1, n).astype(np.float32).astype(np.float64)
+    dev = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in (G, Z, w)]
+    loss, g = p.loss_grad(*dev)
+    ref_loss, ref_g = learned.affine_nll_and_grad(Wf, G, Z[:, :D2], Z[:, D2:2 * D2], Z[:, 2 * D2:],
+                                                  om.Q[D1:, D1:], w)
+    assert loss == pytest.approx(ref_loss, rel=1e-5, abs=1e-6)
+    Gg = p.unflatten(g.cpu().numpy().astype(np.float64))
+    for k in Gg:
+        d = np.max(np.abs(Gg[k] - ref_g[k]))
+        assert d <= 1e-4 * np.max(np.abs(ref_g[k])) + 1e-7, (k, d)
+    p.close()
+
+
+def _check_bidx(seed, t, bidx, own):
+    """The wide pass's local resampling indices equal the oracle's plain rule on its own
+    FP64 weights, or are explained flips."""
+    M = bidx.shape[1]
+    flips = 0
+    for i in np.nonzero(np.any(bidx != own["bidx"], axis=1))[0]:
+        al = own["alpha"][i]
+        v = (al - al.max()) * LOG2E
+        n, _, _ = explain_flips(np.exp(al - al.max()), bidx[i], own["bidx"][i], word(seed, t, i, oracle.P_INNER),
+                                M, fp32_weight_relerr(v))
+        flips += n
+    return flips
+
+
+def _check_learned_update(om, Wq, lib, seed, t, yprev, pa, px, pz, plq, x, z, lq, f, o, frac, groups=None,
+                          centre="group"):
+    """The inner update of step t against the oracle given the GPU's indices and network
+    outputs; returns the number of groups that fell back. groups: the sampled outer
+    particles (default all); z, lq, x are then those groups' rows."""
+    N = f.N
+    gi = np.arange(N) if groups is None else np.asarray(groups)
+    bidx = f.read("bidx")[gi]
+    own = o.finalize(t, yprev, gi, pa[gi], px, pz, plq, x)
+    flips = _check_bidx(seed, t, bidx, own)
+    feats = f.read("afeat").astype(np.float64)[gi]
+    head = f.read("ahead").astype(np.float64)[gi]
+    got = learned.amortised_finalize(
+        om, Wq, seed, t, yprev, pa[gi], px, pz, x, bidx,
+        normals=lambda tt, i, pp, j, n: oracle.normals(seed, 0, tt, int(gi[i]), pp, j, n, lib), head_out=head,
+        centre=centre)
+    assert np.max(rel(feats, got["feats"])) <= FEAT_TOL, np.max(rel(feats, got["feats"]))
+    href, cache = learned.forward(Wq, feats, bf16_mode=True)
+    scale = np.abs(cache["h3"]) @ np.abs(learned.bf16(Wq["W4"])).T + np.abs(Wq["b4"])
+    assert np.all(np.abs(head - href) <= 2.0 ** -6 * scale + 1e-5), np.max(np.abs(head - href) / (scale + 1e-5))
+    fb = f.read("fallback").astype(bool)[gi]
+    ess = learned.inner_ess(got["lq"])
+    near = np.abs(ess - frac * f.M) <= 1e-4 * f.M
+    bad = (fb != (ess < frac * f.M)) & ~near
+    assert not bad.any(), (np.nonzero(bad)[0][:10], ess[bad][:10])
+    rep = o.finalize(t, yprev, gi, pa[gi], px, pz, plq, x, bidx=bidx) if fb.any() else None
+    zr = np.where(fb[:, None, None], rep["z"], got["z"]) if fb.any() else got["z"]
+    lqr = np.where(fb[:, None], rep["lq"], got["lq"]) if fb.any() else got["lq"]
+    assert np.max(rel(z, zr)) <= Z_TOL, np.max(rel(z, zr))
+    assert np.max(rel(lq, lqr)) <= LQ_TOL, np.max(rel(lq, lqr))
+    return int(fb.sum()), flips
+
+
+# (N, M, L, head scale, fallback threshold, centre). At growth_clg64 the plain inner
+# update's ESS is about 0.2 M, so with the default threshold 0.25 most groups fall back:
+# cases with threshold 0 have every group take the learned update, 0.1 gives a mix.
+# The last case has a full Q_z (the update's triangular path).
+CASES = [
+    (96, 128, 8, 0.1, 0.0, "group", False),
+    (77, 256, 16, 1.0, 0.0, "group", False),
+    (64, 64, 4, 0.3, 0.1, "group", False),
+    (50, 256, 16, 0.1, 0.25, "group", False),
+    (88, 256, 16, 1.0, 0.0, "particle", False),
+    (45, 96, 8, 0.3, 0.1, "particle", False),
+    (70, 128, 8, 0.3, 0.0, "particle", True),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"N{c[0]}-M{c[1]}-L{c[2]}-s{c[3]}-fb{c[4]}-{c[5]}"
+                                             + ("-fullq" if c[6] else "") for c in CASES])
+def test_amortised_wide_teacher_forced(case):
+    from paper_1203_2394_gb300 import dpf
+    N, M, L, hs, frac, centre, full_qz = case
+    spec = _spec(full_qz=full_qz)
+    seed, T = 3, 5
+    f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), D1, D2, N, M, L, seed)
+    f.set_debug(True)
+    p, om = _prop(spec, hs)
+    p.set_centre(centre == "particle")
+    Wq = p.get_weights()
+    o = oracle.Oracle(om, N, M, L, seed, nthreads=16)
+    lib = oracle.load()
+    _, ys = workloads.simulate(spec, T + 1, 0)
+    prev = None
+    n_fb, n_learned = 0, 0
+    for t in range(1, T + 1):
+        if t == 2:
+            f.set_proposal(p)
+            f.set_fallback(frac)
+        y = ys[t - 1].astype(np.float32)
+        f.step(y)
+        x, z, lq = state_from_gpu(f)
+        ref = o.lookahead(t, y, np.arange(N), x, z, lq)
+        assert np.max(rel(f.read("lw"), ref["lw"])) <= 1e-5
+        check_lwhat(f.read("lwhat").astype(np.float64), ref["lwhat"], 1e-5)
+        if prev is not None:
+            pa, px, pz, plq, plwhat, pxbb = prev
+            sel = f.read("sel")
+            check_selection(seed, t - 1, pa, plwhat, sel)
+            np.testing.assert_array_equal(x, pxbb[pa, sel])
+            nf, _ = _check_learned_update(om, Wq, lib, seed, t - 1, ys[t - 2].astype(np.float32), pa, px, pz, plq,
+                                          x, z, lq, f, o, frac, centre=centre)
+            n_fb += nf
+            n_learned += N - nf
+        prev = (f.read("anc"), x, z, lq, f.read("lwhat").astype(np.float64), f.read("xbb").astype(np.float64))
+    print(f"amortised wide {case}: learned groups {n_learned}, fallback groups {n_fb}")
+    if frac == 0.0:
+        assert n_fb == 0 and n_learned == N * (T - 1)
+    f.close()
+    p.close()
+
+
+def test_amortised_wide_records_the_oracle_rows():
+    """dpf_record_tuples_amortised at the wide size: per inner particle the group
+    features, (z_t, mu, m) and exp(lq_t) / N of the last inner update, against the
+    oracle's features and prior means for the parents the update took."""
+    from paper_1203_2394_gb300 import dpf
+    spec = _spec()
+    N, M, L, seed = 40, 128, 8, 9
+    f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), D1, D2, N, M, L, seed)
+    f.set_debug(True)
+    om = oracle.OracleModel.from_spec(spec)
+    _, ys = workloads.simulate(spec, 4, 2)
+    for t in range(3):
+        f.step(ys[t].astype(np.float32))
+        if t == 1:  # the ancestors and the state the third step's inner update reads
+            pa = f.read("anc")
+            px, pz, _ = state_from_gpu(f)
+    i0, n = 5, 20
+    G, Z, w = (a.cpu().numpy().astype(np.float64) for a in f.record_amortised(i0, n))
+    x, z, lq = state_from_gpu(f)
+    bidx = f.read("bidx")
+    assert G.shape == (n * M, DIN) and Z.shape == (n * M, 3 * D2) and w.shape == (n * M,)
+    np.testing.assert_allclose(w, np.exp(lq[i0:i0 + n].reshape(-1)) / N, rtol=1e-6, atol=0)
+    np.testing.assert_array_equal(Z[:, :D2], z[i0:i0 + n].reshape(-1, D2))
+    yprev = ys[1].astype(np.float32).astype(np.float64)
+    for q in range(n):
+        i = i0 + q
+        rows = G[q * M:(q + 1) * M]
+        assert np.all(rows == rows[0])  # the group's features, the same for every inner particle
+        feats, mu, m = learned.amortised_features(om, px[pa[i]], x[i], yprev, pz[pa[i]][bidx[i]])
+        assert np.max(rel(rows[0], feats)) <= FEAT_TOL, np.max(rel(rows[0], feats))
+        assert np.max(rel(Z[q * M:(q + 1) * M, D2:2 * D2], mu)) <= FEAT_TOL
+        assert np.max(rel(Z[q * M:(q + 1) * M, 2 * D2:], np.broadcast_to(m, (M, D2)))) <= FEAT_TOL
+    f.close()
+
+
+def test_amortised_wide_full_size_sampled():
+    """The high-dimensional workload's launch configuration (N = 32768, M = 256, L = 16):
+    one learned inner update checked on 48 sampled groups."""
+    from paper_1203_2394_gb300 import dpf
+    spec = _spec()
+    sz = spec.sizes
+    N, M, L, seed = sz["N"], sz["M"], sz["L"], 0
+    f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), D1, D2, N, M, L, seed)
+    f.set_debug(True)
+    p, om = _prop(spec, 0.3)
+    p.set_centre(True)
+    Wq = p.get_weights()
+    o = oracle.Oracle(om, N, M, L, seed, nthreads=16)
+    lib = oracle.load()
+    _, ys = workloads.simulate(spec, 3, 0)
+    f.step(ys[0].astype(np.float32))
+    f.step(ys[1].astype(np.float32))
+    pa = f.read("anc")
+    plwhat = f.read("lwhat").astype(np.float64)
+    px, pz, plq = state_from_gpu(f)
+    f.set_proposal(p)
+    f.set_fallback(0.0)
+    f.step(ys[2].astype(np.float32))
+    gi = np.sort(np.random.default_rng(4).choice(N, 48, replace=False))
+    sel = f.read("sel")
+    check_selection(seed, 2, pa[gi], plwhat, sel[gi], idx=gi)
+    x, z, lq = state_from_gpu(f)
+    nf, _ = _check_learned_update(om, Wq, lib, seed, 2, ys[1].astype(np.float32), pa, px, pz, plq,
+                                  x[gi], z[gi], lq[gi], f, o, 0.0, groups=gi, centre="particle")
+    print(f"amortised wide full size: {nf} of 48 sampled groups fell back")
+    f.close()
+    p.close()
