@@ -1158,7 +1158,7 @@ dpf_status dpf_set_proposal(dpf_ctx* x, dpf_proposal* p) {
                                         "with x free of z and M a multiple of 32 up to 256");
   auto grow = [&](void** q, size_t bytes) -> cudaError_t {
     if (*q) return cudaSuccess;
-    cudaError_t e = cudaMalloc(q, bytes);
+    cudaError_t e = device_malloc(q, bytes);
     if (e == cudaSuccess) x->allocs.push_back(*q);
     if (e == cudaSuccess) e = cudaMemsetAsync(*q, 0, bytes, x->stream);
     return e;
