@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "dpf_learned.h"
+#include "dpf_tc.cuh"
 #include "dpf_variant.cuh"
 
 namespace dpf {
@@ -183,6 +184,83 @@ struct OwShared {
   uint32_t s_uin;
 };
 
+// The plain rule's selection of x_{t-1}^(i) among the ancestor's look-ahead draws and
+// the local systematic resampling of the ancestor's inner set (its own weights: the x
+// transition is free of z); writes sel, x_new, the indices (and the debug copy) and
+// returns this thread's parent b. Every thread of the CTA (one a particle) calls it.
+__device__ __forceinline__ int ow_select_resample(const StepArgs<float>& a, long long i, long long anc,
+                                                  int32_t* __restrict__ bidx_out, OwShared& sh) {
+  const int M = a.M, j = threadIdx.x, lane = j & 31;
+  const float NEG = -INFINITY;
+  const float LOG2E = (float)LOG2E_D;
+  if (j < 32) {
+    const int L = a.L;
+    const float l0 = lane < L ? a.lwh_old[anc * L + lane] : NEG;
+    const float l1 = lane + 32 < L ? a.lwh_old[anc * L + lane + 32] : NEG;
+    const float mx = warp_max(fmaxf(l0, l1));
+    const uint32_t c0 = lane < L ? (uint32_t)floorf(exp2_t((l0 - mx) * LOG2E) * a.scaleL) : 0u;
+    const uint32_t c1 = lane + 32 < L ? (uint32_t)floorf(exp2_t((l1 - mx) * LOG2E) * a.scaleL) : 0u;
+    uint32_t s0 = c0, s1 = c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
+      if (lane >= o) {
+        s0 += n0;
+        s1 += n1;
+      }
+    }
+    const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
+    const uint64_t C = (uint64_t)tot0 + tot1;
+    const uint32_t wsel = philox(ctr(a.t - 1, (uint32_t)i, lane == 0 ? P_SEL : P_INNER, 0u, 0u), a.key).x;
+    const uint32_t usel = __shfl_sync(FULL, wsel, 0);
+    const uint64_t rhs = (uint64_t)usel * C;
+    const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
+    const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
+    if (lane == 0) {
+      int m = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
+      if (C == 0 || m >= L) {
+        atomicOr(a.err, ERR_NUMERIC);
+        m = L - 1;
+      }
+      sh.s_msel = m;
+      a.sel[i] = m;
+    }
+    if (lane == 1) sh.s_uin = wsel;
+  }
+  __syncthreads();
+  const int msel = sh.s_msel;
+  if (j < a.xp) a.x_new[i * a.xp + j] = j < OW_D1 ? a.xbb_old[(anc * a.L + msel) * OW_D1 + j] : 0.f;
+  const float al = a.lq_old[anc * M + j];
+  const float amax = bmax(al, sh.red);
+  uint32_t cw[1] = {(uint32_t)floorf(exp2_t((al - amax) * LOG2E) * a.scaleM)}, incl[1];
+  bscan_planes<1>(cw, incl, sh.redU);
+  sh.cum[j] = incl[0];
+  __syncthreads();
+  const uint32_t C = sh.cum[M - 1];
+  if (C == 0 && j == 0) atomicOr(a.err, ERR_NUMERIC);
+  const int b = sys_local_pick(sh.cum, M, C, M, j, sh.s_uin);
+  bidx_out[i * M + j] = b;
+  if (a.dbg_b) a.dbg_b[i * M + j] = b;
+  return b;
+}
+
+// The group's feature row (x_{t-1} of the ancestor, x_t, y_t, m, v) once the moments
+// are in sh.
+__device__ __forceinline__ void ow_features(const StepArgs<float>& a, long long i, long long anc,
+                                            float* __restrict__ feat, const OwShared& sh) {
+  const int j = threadIdx.x;
+  float* f = feat + i * OW_DIN;
+  if (j < OW_D1) {
+    f[j] = a.x_old[anc * a.xp + j];
+    f[OW_D1 + j] = a.xbb_old[(anc * a.L + sh.s_msel) * OW_D1 + j];
+  }
+  if (j < OW_DY) f[2 * OW_D1 + j] = a.y_prev[j];
+  if (j < OW_D2) {
+    f[2 * OW_D1 + OW_DY + j] = sh.s_m[j];
+    f[2 * OW_D1 + OW_DY + OW_D2 + j] = sh.s_v[j];
+  }
+}
+
 // Stage 1: selection, local resampling, prior means and the group features (two CTAs
 // of 256 threads an SM: at most 128 registers a thread).
 __global__ void __launch_bounds__(256, 2)
@@ -191,10 +269,8 @@ __global__ void __launch_bounds__(256, 2)
   // [A_zz^T (56 x 56)][the staged set (56 x M)][half of mu (28 x M)]
   extern __shared__ __align__(16) float ow_sz[];
   __shared__ OwShared sh;
-  const int M = a.M, j = threadIdx.x, lane = j & 31;
+  const int M = a.M, j = threadIdx.x;
   const long long NM = a.N * (long long)M;
-  const float NEG = -INFINITY;
-  const float LOG2E = (float)LOG2E_D;
   float* sAt = ow_sz;
   float* sz = ow_sz + OW_AT_FLOATS;
   float* smu = sz + OW_D2 * M;
@@ -202,59 +278,10 @@ __global__ void __launch_bounds__(256, 2)
   for (long long i = blockIdx.x; i < a.N; i += gridDim.x) {
     const long long anc = a.anc[i];
     ow_stage(a.z_old, NM, anc, M, sz);
-    // ---- selection of x_{t-1}^(i) among the ancestor's look-ahead draws (the plain rule) ----
-    if (j < 32) {
-      const int L = a.L;
-      const float l0 = lane < L ? a.lwh_old[anc * L + lane] : NEG;
-      const float l1 = lane + 32 < L ? a.lwh_old[anc * L + lane + 32] : NEG;
-      const float mx = warp_max(fmaxf(l0, l1));
-      const uint32_t c0 = lane < L ? (uint32_t)floorf(exp2_t((l0 - mx) * LOG2E) * a.scaleL) : 0u;
-      const uint32_t c1 = lane + 32 < L ? (uint32_t)floorf(exp2_t((l1 - mx) * LOG2E) * a.scaleL) : 0u;
-      uint32_t s0 = c0, s1 = c1;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t n0 = __shfl_up_sync(FULL, s0, o), n1 = __shfl_up_sync(FULL, s1, o);
-        if (lane >= o) {
-          s0 += n0;
-          s1 += n1;
-        }
-      }
-      const uint32_t tot0 = __shfl_sync(FULL, s0, 31), tot1 = __shfl_sync(FULL, s1, 31);
-      const uint64_t C = (uint64_t)tot0 + tot1;
-      const uint32_t wsel = philox(ctr(a.t - 1, (uint32_t)i, lane == 0 ? P_SEL : P_INNER, 0u, 0u), a.key).x;
-      const uint32_t usel = __shfl_sync(FULL, wsel, 0);
-      const uint64_t rhs = (uint64_t)usel * C;
-      const unsigned b0 = __ballot_sync(FULL, ((uint64_t)s0 << 32) > rhs);
-      const unsigned b1 = __ballot_sync(FULL, ((uint64_t)(s1 + tot0) << 32) > rhs);
-      if (lane == 0) {
-        int m = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : L - 1);
-        if (C == 0 || m >= L) {
-          atomicOr(a.err, ERR_NUMERIC);
-          m = L - 1;
-        }
-        sh.s_msel = m;
-        a.sel[i] = m;
-      }
-      if (lane == 1) sh.s_uin = wsel;
-    }
-    __syncthreads();
-    const int msel = sh.s_msel;
     float xa[OW_D1];
 #pragma unroll
     for (int c = 0; c < OW_D1; ++c) xa[c] = a.x_old[anc * a.xp + c];
-    if (j < a.xp) a.x_new[i * a.xp + j] = j < OW_D1 ? a.xbb_old[(anc * a.L + msel) * OW_D1 + j] : 0.f;
-    // ---- local resampling of the ancestor's inner set (its own weights: no x term) ----
-    const float al = a.lq_old[anc * M + j];
-    const float amax = bmax(al, sh.red);
-    uint32_t cw[1] = {(uint32_t)floorf(exp2_t((al - amax) * LOG2E) * a.scaleM)}, incl[1];
-    bscan_planes<1>(cw, incl, sh.redU);
-    sh.cum[j] = incl[0];
-    __syncthreads();
-    const uint32_t C = sh.cum[M - 1];
-    if (C == 0 && j == 0) atomicOr(a.err, ERR_NUMERIC);
-    const int b = sys_local_pick(sh.cum, M, C, M, j, sh.s_uin);
-    bidx_out[i * M + j] = b;
-    if (a.dbg_b) a.dbg_b[i * M + j] = b;
+    const int b = ow_select_resample(a, i, anc, bidx_out, sh);
     // ---- prior means and the group features ----
     for (int h = 0; h < 2; ++h) {
       ow_prior_mean_half(h, xa, sz, sAt, M, b, mu_out + i * M + j, NM, smu);
@@ -262,18 +289,151 @@ __global__ void __launch_bounds__(256, 2)
       ow_half_moments(h, smu, M, sh.s_m, sh.s_v);
       __syncthreads();  // smu is rewritten by the next half
     }
-    float* f = feat + i * OW_DIN;
-    if (j < OW_D1) {
-      f[j] = a.x_old[anc * a.xp + j];
-      f[OW_D1 + j] = a.xbb_old[(anc * a.L + msel) * OW_D1 + j];
-    }
-    if (j < OW_DY) f[2 * OW_D1 + j] = a.y_prev[j];
-    if (j < OW_D2) {
-      f[2 * OW_D1 + OW_DY + j] = sh.s_m[j];
-      f[2 * OW_D1 + OW_DY + OW_D2 + j] = sh.s_v[j];
-    }
+    ow_features(a, i, anc, feat, sh);
     __syncthreads();  // the staged set and the shared words are reused by the next group
   }
+}
+
+// Stage 1 with the product A_zz z_b on the tensor cores (M = 128 or 256; used at 256). Per group the
+// gathered parents z_b form the A operand (one row a particle; K = the 56 coordinates,
+// padded to 64, in two chunks of 32), A_zz the B operand (N = 56 padded to 64, staged
+// once per CTA), 3xTF32 (kind::tf32: A_lo B_hi + A_hi B_lo + A_hi B_hi) into an FP32
+// accumulator in TMEM, 64 columns a 128-row tile; thread j then reads its row. Operands
+// are K-major without swizzle (the layout of dpf_tc.cuh). A wait that gives up sets
+// ERR_TIMEOUT, waits once more for the MMAs in flight, releases the TMEM and returns.
+constexpr int OWT_KC16 = 8;                  // 16-byte chunks of one 128-byte operand row (32 TF32)
+constexpr int OWT_SPIN = 1 << 22;
+constexpr uint32_t OWT_B_BYTES = 64u * 128u;  // one K chunk of B: 64 rows x 128 bytes
+constexpr uint32_t OWT_TILE_BYTES = 128u * 128u;  // one K chunk of a 128-row A tile
+
+__global__ void __launch_bounds__(256, 2)
+    oaw_prepare_tc_kernel(const __grid_constant__ StepArgs<float> a, int32_t* __restrict__ bidx_out,
+                          float* __restrict__ feat, float* __restrict__ mu_out) {
+  // [A hi (M rows x 128 B)][A lo][B hi (2 chunks x 64 rows x 128 B)][B lo]; the A region
+  // doubles as the staging tile of the group moments once the MMAs have completed
+  extern __shared__ __align__(1024) unsigned char owt_sm[];
+  __shared__ OwShared sh;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_taddr;
+  const int M = a.M, j = threadIdx.x, w = j >> 5;
+  const long long NM = a.N * (long long)M;
+  const uint32_t a_bytes = (uint32_t)M * 128u;
+  unsigned char* a_hi = owt_sm;
+  unsigned char* a_lo = owt_sm + a_bytes;
+  unsigned char* b_hi = owt_sm + 2 * a_bytes;
+  unsigned char* b_lo = b_hi + 2 * OWT_B_BYTES;
+  const uint32_t ncols = (uint32_t)(M / 128) * 64u;
+  if (w == 0) {
+    tc::tmem_alloc(&s_taddr, ncols);
+    tc::tmem_relinquish();
+  }
+  if (j == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  for (int e = j; e < 64 * 64; e += blockDim.x) {  // B = A_zz, zero-padded to 64 x 64
+    const int n = e >> 6, k = e & 63;
+    const float v = (n < OW_D2 && k < OW_D2) ? c_ow.Azz[n][k] : 0.f;
+    float h, l;
+    tc::split_tf32(v, h, l);
+    const uint32_t off = (uint32_t)(k >> 5) * OWT_B_BYTES + tc::kmajor_offset(n, 4 * (k & 31), OWT_KC16);
+    *(float*)(b_hi + off) = h;
+    *(float*)(b_lo + off) = l;
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = s_taddr;
+  const uint32_t idesc = tc::instr_desc(tc::FMT_TF32, 128, 64);
+  uint32_t phase = 0;
+  int ok = 1;
+  for (long long i = blockIdx.x; i < a.N; i += gridDim.x) {
+    const long long anc = a.anc[i];
+    float xa[OW_D1];
+#pragma unroll
+    for (int c = 0; c < OW_D1; ++c) xa[c] = a.x_old[anc * a.xp + c];
+    const int b = ow_select_resample(a, i, anc, bidx_out, sh);
+    const float* zp = a.z_old + anc * M + b;  // the parent's coordinate c at zp[c NM]
+    for (int q = 0; q < 2 && ok; ++q) {
+      // this thread's operand row of chunk q: coordinates 32 q .. 32 q + 31 (zeros past 55)
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const int c0 = 32 * q + 4 * c4;
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = c0 + u < OW_D2 ? zp[(long long)(c0 + u) * NM] : 0.f;
+        float4 hi, lo;
+        tc::split_tf32(v[0], hi.x, lo.x);
+        tc::split_tf32(v[1], hi.y, lo.y);
+        tc::split_tf32(v[2], hi.z, lo.z);
+        tc::split_tf32(v[3], hi.w, lo.w);
+        const uint32_t off = tc::kmajor_offset(j, 16 * c4, OWT_KC16);
+        *(float4*)(a_hi + off) = hi;
+        *(float4*)(a_lo + off) = lo;
+      }
+      tc::fence_proxy_async();
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      if (j == 0) {
+        const uint32_t sbh = smem_addr(b_hi) + (uint32_t)q * OWT_B_BYTES;
+        const uint32_t sbl = smem_addr(b_lo) + (uint32_t)q * OWT_B_BYTES;
+        for (int t = 0; t < M / 128; ++t) {
+          const uint32_t sah = smem_addr(a_hi) + (uint32_t)t * OWT_TILE_BYTES;
+          const uint32_t sal = smem_addr(a_lo) + (uint32_t)t * OWT_TILE_BYTES;
+          const uint32_t d = taddr + (uint32_t)(64 * t);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t off = (uint32_t)ks * 256u;
+            const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
+            tc::mma_tf32(d, tc::smem_desc(sal + off, OWT_KC16), tc::smem_desc(sbh + off, OWT_KC16), idesc, acc);
+            tc::mma_tf32(d, tc::smem_desc(sah + off, OWT_KC16), tc::smem_desc(sbl + off, OWT_KC16), idesc, 1);
+            tc::mma_tf32(d, tc::smem_desc(sah + off, OWT_KC16), tc::smem_desc(sbh + off, OWT_KC16), idesc, 1);
+          }
+        }
+        tc::commit(&bar);
+      }
+      const bool done = tc::bar_wait(&bar, phase, OWT_SPIN);
+      phase ^= 1u;
+      tc::fence_after();
+      ok = __syncthreads_and(done ? 1 : 0);  // every thread saw the MMAs finish before the tiles change
+    }
+    if (!ok) break;
+    // this thread's row of mu: the accumulator, then + A_zx x_{t-1}
+    float mu[OW_D2];
+    {
+      const uint32_t row = taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * (j >> 7));
+      float v[16];
+#pragma unroll
+      for (int c0 = 0; c0 < 48; c0 += 16) {
+        tc::ld16(row + (uint32_t)c0, v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) mu[c0 + u] = v[u];
+      }
+      float v8[8];
+      tc::ld8(row + 48u, v8);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mu[48 + u] = v8[u];
+    }
+#pragma unroll
+    for (int r = 0; r < OW_D2; ++r) {
+#pragma unroll
+      for (int c = 0; c < OW_D1; ++c) mu[r] += c_ow.Azx[r][c] * xa[c];
+      mu_out[r * NM + i * M + j] = mu[r];
+    }
+    tc::fence_before();  // the TMEM reads are ordered before the barriers that follow
+    ow_group_moments(mu, (float*)owt_sm, M, sh.s_m, sh.s_v);
+    ow_features(a, i, anc, feat, sh);
+    __syncthreads();  // the A region and the shared words are reused by the next group
+  }
+  if (!ok) {
+    if (j == 0) atomicOr(a.err, ERR_TIMEOUT);
+    tc::bar_wait(&bar, phase ^ 1u, OWT_SPIN);  // a second bound for MMAs still in flight
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(taddr, ncols);
 }
 
 // Stage 3: the mapped draws and their normalised importance weights. DIAG: Q_z is
@@ -482,12 +642,24 @@ dpf_status oa_wide_step(Ctx& x, dpf_proposal& p) {
   a.xp = x.xp;
   cudaError_t e = cudaMemcpyToSymbolAsync(c_ow, x.d_mconst, sizeof(OwConst), 0, cudaMemcpyDeviceToDevice, x.stream);
   if (e != cudaSuccess) return cuda_error(e, "amortised wide step: model constants");
-  const size_t sm = sizeof(float) * ((size_t)(OW_D2 + OW_H) * x.M + OW_AT_FLOATS);
-  e = ow_attr(oaw_prepare_kernel, sm);
   unsigned grid = 0, grid_u = 0;
-  if (e == cudaSuccess) e = ow_grid(oaw_prepare_kernel, x.M, sm, x.N, &grid);
-  if (e != cudaSuccess) return cuda_error(e, "amortised wide step: launch shape");
-  oaw_prepare_kernel<<<grid, x.M, sm, x.stream>>>(a, (int32_t*)x.oa_bidx, (float*)x.oa_feat, (float*)x.oa_mu);
+  // A_zz z_b on the tensor cores at M = 256 (as fast as the CUDA-core form there: the pass
+  // is bound by its per-group chain of dependent steps, not by the product; at M = 128 the
+  // tensor-core form, three CTAs an SM, was the slower)
+  if (x.tensor_cores && x.M == 256) {
+    const size_t sm = 2 * (size_t)x.M * 128 + 4 * (size_t)OWT_B_BYTES;
+    e = ow_attr(oaw_prepare_tc_kernel, sm);
+    if (e == cudaSuccess) e = ow_grid(oaw_prepare_tc_kernel, x.M, sm, x.N, &grid);
+    if (e != cudaSuccess) return cuda_error(e, "amortised wide step: launch shape");
+    oaw_prepare_tc_kernel<<<grid, x.M, sm, x.stream>>>(a, (int32_t*)x.oa_bidx, (float*)x.oa_feat,
+                                                      (float*)x.oa_mu);
+  } else {
+    const size_t sm = sizeof(float) * ((size_t)(OW_D2 + OW_H) * x.M + OW_AT_FLOATS);
+    e = ow_attr(oaw_prepare_kernel, sm);
+    if (e == cudaSuccess) e = ow_grid(oaw_prepare_kernel, x.M, sm, x.N, &grid);
+    if (e != cudaSuccess) return cuda_error(e, "amortised wide step: launch shape");
+    oaw_prepare_kernel<<<grid, x.M, sm, x.stream>>>(a, (int32_t*)x.oa_bidx, (float*)x.oa_feat, (float*)x.oa_mu);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "amortised wide prepare launch");
   dpf_status st = proposal_forward_rows(p, (const float*)x.oa_feat, x.N, (float*)x.oa_hidden, (float*)x.oa_out,

@@ -127,27 +127,32 @@ def _check_learned_update(om, Wq, lib, seed, t, yprev, pa, px, pz, plq, x, z, lq
 # (N, M, L, head scale, fallback threshold, centre). At growth_clg64 the plain inner
 # update's ESS is about 0.2 M, so with the default threshold 0.25 most groups fall back:
 # cases with threshold 0 have every group take the learned update, 0.1 gives a mix.
-# The last case has a full Q_z (the update's triangular path).
+# The seventh case has a full Q_z (the update's triangular path). At M = 256 the prepare
+# pass runs A_zz z_b on the tensor cores unless they are switched off (the last case);
+# at other M on the CUDA cores.
 CASES = [
-    (96, 128, 8, 0.1, 0.0, "group", False),
-    (77, 256, 16, 1.0, 0.0, "group", False),
-    (64, 64, 4, 0.3, 0.1, "group", False),
-    (50, 256, 16, 0.1, 0.25, "group", False),
-    (88, 256, 16, 1.0, 0.0, "particle", False),
-    (45, 96, 8, 0.3, 0.1, "particle", False),
-    (70, 128, 8, 0.3, 0.0, "particle", True),
+    (96, 128, 8, 0.1, 0.0, "group", False, True),
+    (77, 256, 16, 1.0, 0.0, "group", False, True),
+    (64, 64, 4, 0.3, 0.1, "group", False, True),
+    (50, 256, 16, 0.1, 0.25, "group", False, True),
+    (88, 256, 16, 1.0, 0.0, "particle", False, True),
+    (45, 96, 8, 0.3, 0.1, "particle", False, True),
+    (70, 128, 8, 0.3, 0.0, "particle", True, True),
+    (66, 256, 16, 1.0, 0.0, "particle", False, False),
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"N{c[0]}-M{c[1]}-L{c[2]}-s{c[3]}-fb{c[4]}-{c[5]}"
-                                             + ("-fullq" if c[6] else "") for c in CASES])
+                                             + ("-fullq" if c[6] else "") + ("" if c[7] else "-cc")
+                                             for c in CASES])
 def test_amortised_wide_teacher_forced(case):
     from paper_1203_2394_gb300 import dpf
-    N, M, L, hs, frac, centre, full_qz = case
+    N, M, L, hs, frac, centre, full_qz, tc = case
     spec = _spec(full_qz=full_qz)
     seed, T = 3, 5
     f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), D1, D2, N, M, L, seed)
     f.set_debug(True)
+    f.set_tensor_cores(tc)
     p, om = _prop(spec, hs)
     p.set_centre(centre == "particle")
     Wq = p.get_weights()
@@ -249,4 +254,36 @@ def test_amortised_wide_full_size_sampled():
                                   x[gi], z[gi], lq[gi], f, o, 0.0, groups=gi, centre="particle")
     print(f"amortised wide full size: {nf} of 48 sampled groups fell back")
     f.close()
+    p.close()
+
+
+def test_amortised_wide_tensor_and_cuda_cores_agree():
+    """The prepare pass with A_zz z_b on the tensor cores (3xTF32) and on the CUDA cores:
+    the same indices, features and network outputs within rounding, so the same
+    learned update up to it."""
+    from paper_1203_2394_gb300 import dpf
+    spec = _spec()
+    N, M, L, seed = 120, 256, 16, 6
+    _, ys = workloads.simulate(spec, 3, 3)
+    p, _ = _prop(spec, 0.3)
+    p.set_centre(True)
+    out = []
+    for tc in (True, False):
+        f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), D1, D2, N, M, L, seed)
+        f.set_debug(True)
+        f.set_tensor_cores(tc)
+        f.set_proposal(p)
+        f.set_fallback(0.0)
+        for t in range(2):  # one plain step, then the first learned update (same inputs on both)
+            f.step(ys[t].astype(np.float32))
+        out.append({k: f.read(k).astype(np.float64) for k in ("bidx", "afeat", "ahead", "lq")})
+        out[-1]["z"] = f.read("z").astype(np.float64)
+        f.close()
+    a, b = out
+    np.testing.assert_array_equal(a["bidx"], b["bidx"])
+    assert np.max(rel(a["afeat"], b["afeat"])) <= FEAT_TOL
+    assert np.max(np.abs(a["ahead"] - b["ahead"])) <= 1e-3 * max(1.0, np.max(np.abs(b["ahead"])))
+    assert np.max(rel(a["z"], b["z"])) <= 1e-4
+    assert np.max(rel(a["lq"], b["lq"])) <= 1e-3
+    assert np.max(np.abs(a["afeat"] - b["afeat"])) > 0  # the two products really differ
     p.close()
