@@ -16,9 +16,10 @@
 //      group's mean prior mean m, or the particle's own mu), and the importance
 //      weight log N(z; mu, Q_z) - log N(zhat; mu, Q_z) + sum log s + log p(y_t | x_t, z)
 //      normalised over the group.
-// Stage 1 stages the ancestor's inner set (56 rows of M values) in shared memory; the
-// model constants sit in this translation unit's constant bank, so every
-// product with A, L_qz and H_z reads uniform constant-bank operands.
+// Stage 1 forms A_zz z_b either on the CUDA cores, from the ancestor's inner set (56 rows
+// of M values) and A_zz^T staged in shared memory, or at M = 256 on the tensor cores
+// (oaw_prepare_tc_kernel). The other model constants (A_zx, L_qz, H_z, L_R^-1) sit in
+// this translation unit's constant bank and are read as uniform constant-bank operands.
 #include <cuda_runtime.h>
 
 #include <algorithm>
