@@ -747,7 +747,7 @@ def run_highdim_learned(args):
     ms[("learned", M, 0.25)] = timed(M, prop, 0.25)
     ms[("learned_group_centre", M, 0.0)] = timed(M, props["group"])
     # ---- accuracy on an untimed run ----
-    T = 20
+    T = 50
     s_true, ya = workloads.simulate(spec, T, 200)
 
     def accuracy(m_inner, use_prop, frac):

@@ -24,6 +24,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "dpf_learned.h"
 #include "dpf_tc.cuh"
@@ -606,13 +609,24 @@ __global__ void __launch_bounds__(256) oaw_record_kernel(const __grid_constant__
   }
 }
 
+// The dynamic shared memory a launch of k needs: raised per kernel (never lowered, so
+// that a launch already made with more keeps its size), the largest request remembered
+// per kernel function (kernels of one signature share no cache).
 template <typename K>
 cudaError_t ow_attr(K k, size_t smem) {
-  static size_t done = 0;
-  if (smem <= done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) done = smem;
-  return e;
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> set;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : set)
+    if (e.first == (const void*)k) {
+      if (smem <= e.second) return cudaSuccess;
+      const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (r == cudaSuccess) e.second = smem;
+      return r;
+    }
+  const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (r == cudaSuccess) set.emplace_back((const void*)k, smem);
+  return r;
 }
 
 // A persistent grid: as many CTAs as fit on the device at once (each copies A_zz^T
