@@ -287,3 +287,33 @@ def test_amortised_wide_tensor_and_cuda_cores_agree():
     assert np.max(rel(a["lq"], b["lq"])) <= 1e-3
     assert np.max(np.abs(a["afeat"] - b["afeat"])) > 0  # the two products really differ
     p.close()
+
+
+def test_prepare_forms_in_either_order_in_a_fresh_process():
+    """The tensor-core prepare (M = 256) and then the CUDA-core one (M = 128) in one fresh
+    process: each kernel gets its own dynamic shared-memory size (a launch-size cache
+    shared by kernels of one signature once made the second launch fail)."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np
+from paper_1203_2394_gb300 import dpf, workloads
+spec = workloads.make_model("growth_clg64", 0)
+p = dpf.Proposal(8, 56, 8, hidden=256, amortised_Qz=spec.Q[8:, 8:])
+W = workloads.init_mlp_weights(136, 256, 112, seed=1)
+W["W4"] *= 0.1
+p.set_weights(W)
+_, ys = workloads.simulate(spec, 2, 0)
+for M in (256, 128):
+    f = dpf.Filter(dpf.Model.from_spec(spec, dpf.DPF_F32), 8, 56, 40, M, 8, 2)
+    f.set_proposal(p)
+    for t in range(2):
+        f.step(ys[t].astype(np.float32))
+    assert np.all(np.isfinite(f.read("lq")))
+    f.close()
+print("ok")
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
