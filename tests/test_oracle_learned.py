@@ -299,3 +299,40 @@ def test_particle_centred_map_weights_by_its_density():
                        for j in range(M)])
         lr -= lr.max()
         np.testing.assert_allclose(got["lq"][i], lr - np.log(np.exp(lr).sum()), rtol=1e-9, atol=1e-9)
+
+
+def test_particle_centred_map_at_d2_56():
+    """The same density check at the high-dimensional size (growth_clg64: d1 = 8,
+    d2 = 56, dy = 8, observations quadratic in x), on three groups of 16."""
+    stats = pytest.importorskip("scipy.stats")
+    spec = workloads.make_model("growth_clg64", 0)
+    om = oracle.OracleModel.from_spec(spec)
+    N, M, L, seed = 3, 16, 4, 7
+    o = oracle.Oracle(om, N, M, L, seed)
+    _, ys = workloads.simulate(spec, 3, 0)
+    x, z, lq = o.init()
+    r1 = o.step(1, ys[0], x, z, lq)
+    r2 = o.step(2, ys[1], r1["x"], r1["z"], r1["lq"])
+    fin = o.finalize(2, ys[1], np.arange(N), r2["anc"], r1["x"], r1["z"], r1["lq"], r2["x"])
+    lib = oracle.load()
+    d1, d2 = om.d1, om.d2
+    W = workloads.init_mlp_weights(2 * d1 + om.dy + 2 * d2, 16, 2 * d2, seed=1)
+    rng = np.random.default_rng(9)
+    head = np.concatenate([rng.uniform(-0.2, 0.2, (N, d2)), 0.1 * rng.standard_normal((N, d2))], axis=1)
+    got = learned.amortised_finalize(om, W, seed, 2, ys[1], r2["anc"], r1["x"], r1["z"], r2["x"], fin["bidx"],
+                                     normals=lambda t, i, p, j, n: oracle.normals(seed, 0, t, i, p, j, n, lib),
+                                     head_out=head, centre="particle")
+    Qz, Hz = om.Q[d1:, d1:], om.H[:, d1:]
+    for i in range(N):
+        a = r2["anc"][i]
+        mu = r1["x"][a] @ om.A[d1:, :d1].T + r1["z"][a][fin["bidx"][i]] @ om.A[d1:, d1:].T
+        s, c = np.exp(head[i, :d2]), head[i, d2:]
+        S = np.diag(s)
+        xn = r2["x"][i]
+        hx = om.H[:, :d1] @ xn + (om.qc * xn[:om.dy] ** 2 if om.qc is not None else 0.0)
+        lr = np.array([stats.multivariate_normal.logpdf(got["z"][i, j], mu[j], Qz)
+                       - stats.multivariate_normal.logpdf(got["z"][i, j], mu[j] + c, S @ Qz @ S)
+                       + stats.multivariate_normal.logpdf(ys[1], hx + Hz @ got["z"][i, j], om.R)
+                       for j in range(M)])
+        lr -= lr.max()
+        np.testing.assert_allclose(got["lq"][i], lr - np.log(np.exp(lr).sum()), rtol=1e-8, atol=1e-8)
